@@ -1,0 +1,534 @@
+/*
+ * oracle.c -- plain, slow, fp64 CPU oracle for the NNFFT (type-3 nonuniform FFT)
+ * with sinh-type windows and for the discrete / fast sinc transform of
+ * Kircheis, Potts and Tasche, "Nonuniform fast Fourier transforms with
+ * nonequispaced spatial and frequency data and fast sinc transforms".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file; only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline
+ * leg use it.  It shares no code, header, helper or table with the CUDA library.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - orc_expsum        the exponential sum of eq. (f(xj)) (and, with the sign
+ *                       flipped and the node roles swapped, its adjoint), by
+ *                       its definition: an O(Min*Mout) direct sum.
+ *   - orc_sinc_direct   the discrete sinc transform, eq. (discretesinctransf), directly.
+ *   - orc_gauss_legendre, orc_sinc_gl
+ *                       Gauss-Legendre nodes/weights on [-1/2,1/2] and the
+ *                       quadrature-factorised sinc transform of eq. (approxsinctrafo) with
+ *                       Gauss-Legendre in place of Clenshaw-Curtis (the variant
+ *                       Section 6 attributes to earlier work), by direct sums.
+ *   - orc_omega_sinh, orc_omega_sinh_hat
+ *                       the sinh-type window of Example 2.1 and its Fourier
+ *                       transform, eq. (hatomegasinh), with the I1 power series.
+ *   - orc_make_params   N*, N1, N2, a, beta_j of Section 2 (eq. (consta), the
+ *                       rescaling after eq. (condvk)) and Section 4, under the
+ *                       readings listed in the design doc (N1 rounded up to even,
+ *                       N2 rounded up to an even 7-smooth length).
+ *   - orc_nnfft_alg22 / orc_nnfft_alg22_adjoint
+ *                       Algorithm 2.2 step by step (a naive DFT for step 3) and
+ *                       its exact transpose.
+ *   - orc_bound_sinh    the error constant E(phi_sinh) of Theorem 4.1.
+ *   - orc_cc_weights, orc_cc_bound
+ *                       Clenshaw-Curtis weights, eq. (wk=), and the bound of
+ *                       Theorem 5.3.
+ *
+ * Equations are cited by their LaTeX labels, e.g. eq. (gell).
+ * Complex arrays are interleaved (re, im) doubles.  A centered index set
+ * I_M = {-M/2, ..., M/2-1} is stored with array index i = l + M/2.
+ *
+ * Pins: tests/test_oracle_pins.py (closed forms, library routines used as
+ * independent cross-checks, invariants, brute force at higher precision, and
+ * the few numbers the paper prints).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef long long i64;
+
+/* ------------------------------------------------------------------------ */
+/* compensated (Neumaier) accumulation                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct { double s, c; } ksum;
+static inline void kadd(ksum *k, double x) {
+    double t = k->s + x;
+    if (fabs(k->s) >= fabs(x)) k->c += (k->s - t) + x;
+    else                       k->c += (x - t) + k->s;
+    k->s = t;
+}
+static inline double kval(const ksum *k) { return k->s + k->c; }
+
+/* N*a*b reduced mod 1 to about [-1/2, 1/2].  The products a*b and N*(a*b) are
+ * carried exactly with fma-based error-free transformations, so the phase of
+ * exp(-2 pi i N a b) is accurate to a few ulps of 1 even when N*a*b is large. */
+static double phase_mod1(i64 N, double a, double b) {
+    double p  = a * b;
+    double pe = fma(a, b, -p);            /* a*b = p + pe exactly            */
+    double Nd = (double)N;                /* exact for N < 2^53              */
+    double t  = Nd * p;
+    double te = fma(Nd, p, -t);           /* Nd*p = t + te exactly           */
+    double r  = t - nearbyint(t);         /* exact                           */
+    return r + (te + Nd * pe);
+}
+
+static int use_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) return nthreads;
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+int orc_num_threads(void) { return use_threads(0); }
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (1.2): out_j = sum_k c_k exp(sign * 2 pi i N a_k b_j).                */
+/* sign = -1 is the NNFFT of eq. (f(xj)) (a = v frequency nodes, b = x spatial */
+/* nodes); sign = +1 with a = x, b = v, c = g is its adjoint                 */
+/* z_k = sum_j g_j exp(+2 pi i N v_k x_j).                                   */
+/* rows == NULL evaluates every output; otherwise only outputs rows[r],      */
+/* r < nrows, written to out[2r], out[2r+1].                                 */
+/* ------------------------------------------------------------------------ */
+int orc_expsum(i64 N, i64 Min, const double *a, const double *c,
+               i64 Mout, const double *b, int sign,
+               const i64 *rows, i64 nrows, double *out, int nthreads) {
+    if (N < 0 || Min < 0 || Mout < 0 || (sign != 1 && sign != -1)) return 1;
+    i64 nr = rows ? nrows : Mout;
+    int nt = use_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+    for (i64 r = 0; r < nr; ++r) {
+        i64 j = rows ? rows[r] : r;
+        ksum sre = {0, 0}, sim = {0, 0};
+        if (j >= 0 && j < Mout) {
+            double bj = b[j];
+            for (i64 k = 0; k < Min; ++k) {
+                double fr = phase_mod1(N, a[k], bj);
+                double ang = 2.0 * M_PI * fr;
+                double cs = cos(ang), sn = sign * sin(ang);
+                double cr = c[2 * k], ci = c[2 * k + 1];
+                kadd(&sre, cr * cs - ci * sn);
+                kadd(&sim, cr * sn + ci * cs);
+            }
+        }
+        out[2 * r]     = kval(&sre);
+        out[2 * r + 1] = kval(&sim);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sinc(pi N (b - a)) of eq. (sinc): sin(pi u)/(pi u), value 1 at u = 0.       */
+/* d = b - a is carried as a double-double and u = N d is reduced exactly     */
+/* modulo 2 before the sine, so large N*d loses no accuracy.                 */
+/* ------------------------------------------------------------------------ */
+double orc_sinc_Npi(i64 N, double b, double a) {
+    double s  = b - a;                       /* two-sum of b + (-a)          */
+    double bp = s - b;
+    double ap = s - bp;
+    double se = (b - ap) + (-a - bp);        /* b - a = s + se exactly       */
+    double Nd = (double)N;
+    double t  = Nd * s;
+    double te = fma(Nd, s, -t) + Nd * se;    /* N*(b-a) = t + te             */
+    double u  = t + te;
+    if (fabs(u) < 1e-5) {
+        double x2 = (M_PI * u) * (M_PI * u);
+        return 1.0 - x2 / 6.0 + x2 * x2 / 120.0;
+    }
+    double k2 = 2.0 * nearbyint(0.5 * t);    /* even integer nearest t       */
+    double r  = (t - k2) + te;               /* u - k2, |r| <= 1 (+tiny)     */
+    return sin(M_PI * r) / (M_PI * u);
+}
+
+/* Eq. (discretesinctransf): h(b_l) = sum_k c_k sinc(N pi (b_l - a_k)), c complex. */
+int orc_sinc_direct(i64 N, i64 L1, const double *a, const double *c,
+                    i64 L2, const double *b, const i64 *rows, i64 nrows,
+                    double *h, int nthreads) {
+    if (N < 0 || L1 < 0 || L2 < 0) return 1;
+    i64 nr = rows ? nrows : L2;
+    int nt = use_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nt)
+    for (i64 r = 0; r < nr; ++r) {
+        i64 l = rows ? rows[r] : r;
+        ksum sre = {0, 0}, sim = {0, 0};
+        if (l >= 0 && l < L2) {
+            for (i64 k = 0; k < L1; ++k) {
+                double s = orc_sinc_Npi(N, b[l], a[k]);
+                kadd(&sre, c[2 * k] * s);
+                kadd(&sim, c[2 * k + 1] * s);
+            }
+        }
+        h[2 * r]     = kval(&sre);
+        h[2 * r + 1] = kval(&sim);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre rule with n nodes on [-1/2, 1/2] (sum of weights = 1):    */
+/* Newton's method on the Legendre three-term recurrence; the weights are    */
+/* 2/((1-t^2) P_n'(t)^2) on [-1,1], halved by the map tau = t/2.  Nodes are  */
+/* returned in increasing order.                                             */
+/* ------------------------------------------------------------------------ */
+int orc_gauss_legendre(i64 n, double *tau, double *w) {
+    if (n <= 0) return 1;
+    for (i64 i = 0; i < (n + 1) / 2; ++i) {
+        /* i-th largest root; classical initial guess */
+        double t = cos(M_PI * ((double)i + 0.75) / ((double)n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (i64 k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
+                p0 = p1; p1 = p2;
+            }
+            double pn = (n == 1) ? t : p1, pm = (n == 1) ? 1.0 : p0;
+            dp = (double)n * (t * pn - pm) / (t * t - 1.0);
+            double dt = pn / dp;
+            t -= dt;
+            if (fabs(dt) < 1e-17) break;
+        }
+        /* recompute P_n' at the converged node for the weight */
+        {
+            double p0 = 1.0, p1 = t;
+            for (i64 k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
+                p0 = p1; p1 = p2;
+            }
+            double pn = (n == 1) ? t : p1, pm = (n == 1) ? 1.0 : p0;
+            dp = (double)n * (t * pn - pm) / (t * t - 1.0);
+        }
+        double wt = 2.0 / ((1.0 - t * t) * dp * dp);
+        /* largest roots first: place symmetric pairs */
+        tau[n - 1 - i] = 0.5 * t;
+        tau[i]         = -0.5 * t;
+        w[n - 1 - i]   = 0.5 * wt;
+        w[i]           = 0.5 * wt;
+    }
+    if (n % 2 == 1) tau[n / 2] = 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. (approxsinctrafo) with a Gauss-Legendre rule (tau_j, w_j), j < n, on [-1/2,1/2]:   */
+/*   g_j   = sum_k c_k exp(+2 pi i N tau_j a_k)                              */
+/*   h_l   = sum_j w_j g_j exp(-2 pi i N tau_j b_l)                          */
+/* which is the quadrature of sinc(N pi (b-a)) = int_{-1/2}^{1/2}             */
+/* exp(-2 pi i N tau (b - a)) d tau (proof of Theorem 5.1).  Direct sums.     */
+/* ------------------------------------------------------------------------ */
+int orc_sinc_gl(i64 N, i64 n, i64 L1, const double *a, const double *c,
+                i64 L2, const double *b, const i64 *rows, i64 nrows,
+                double *h, int nthreads) {
+    if (n <= 0) return 1;
+    double *tau = (double *)malloc(sizeof(double) * n);
+    double *w   = (double *)malloc(sizeof(double) * n);
+    double *g   = (double *)malloc(sizeof(double) * 2 * n);
+    if (!tau || !w || !g) { free(tau); free(w); free(g); return 2; }
+    orc_gauss_legendre(n, tau, w);
+    /* g_j = sum_k c_k exp(+2 pi i N a_k tau_j) */
+    orc_expsum(N, L1, a, c, n, tau, +1, NULL, 0, g, nthreads);
+    for (i64 j = 0; j < n; ++j) { g[2 * j] *= w[j]; g[2 * j + 1] *= w[j]; }
+    /* h_l = sum_j (w_j g_j) exp(-2 pi i N tau_j b_l) */
+    orc_expsum(N, n, tau, g, L2, b, -1, rows, nrows, h, nthreads);
+    free(tau); free(w); free(g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sinh-type window, Example 2.1 and Section 4:                                */
+/*   omega(x) = sinh(beta sqrt(1-x^2)) / sinh(beta) on [-1,1], 0 outside.    */
+/* Evaluated as exp(beta(s-1)) (1-exp(-2 beta s)) / (1-exp(-2 beta)), which  */
+/* is the same quotient without overflow.                                    */
+/* ------------------------------------------------------------------------ */
+double orc_omega_sinh(double x, double beta) {
+    if (!(fabs(x) < 1.0)) return 0.0;
+    double s = sqrt(1.0 - x * x);
+    return exp(beta * (s - 1.0)) * (-expm1(-2.0 * beta * s)) / (-expm1(-2.0 * beta));
+}
+
+/* Eq. (hatomegasinh): Fourier transform of omega_sinh.
+ *   |v| <  beta/(2 pi): (pi beta / sinh beta) * q^{-1/2} I1(sqrt q), q = beta^2 - 4 pi^2 v^2,
+ *                       with q^{-1/2} I1(sqrt q) = (1/2) sum_k q^k / (4^k k! (k+1)!)
+ *                       (the power series printed after eq. (hatomegasinh); all terms positive);
+ *   |v| == beta/(2 pi): (pi beta / sinh beta) / 2;
+ *   |v| >  beta/(2 pi): (pi beta / sinh beta) * q'^{-1/2} J1(sqrt q'), q' = 4 pi^2 v^2 - beta^2
+ *                       (libm j1 used as the Bessel primitive).
+ * The threshold m(1 - 1/(2 sigma)) of eq. (hatomegasinh) equals beta/(2 pi). */
+double orc_omega_sinh_hat(double v, double beta) {
+    double pref = M_PI * beta / sinh(beta);
+    double q = beta * beta - 4.0 * M_PI * M_PI * v * v;
+    if (q > 0.0) {
+        double term = 1.0, sum = 1.0;
+        for (int k = 0; k < 2000; ++k) {
+            term *= q / (4.0 * (k + 1.0) * (k + 2.0));
+            sum += term;
+            if (term < 1e-18 * sum) break;
+        }
+        return pref * 0.5 * sum;
+    }
+    if (q == 0.0) return pref * 0.5;
+    double r = sqrt(-q);
+    return pref * j1(r) / r;
+}
+
+/* Scaled windows of eq. (twowindows): phi(t) = omega(N t / m), phihat(v) = (m/N) omegahat(m v / N). */
+double orc_phi(double t, i64 Nj, int m, double beta) {
+    return orc_omega_sinh((double)Nj * t / (double)m, beta);
+}
+double orc_phi_hat(double v, i64 Nj, int m, double beta) {
+    return ((double)m / (double)Nj) * orc_omega_sinh_hat((double)m * v / (double)Nj, beta);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parameters of Algorithm 2.2 for v_k, x_j in [-1/2, 1/2] (Section 2):       */
+/*   N*  = N + ceil(2 m1 / sigma1)   (rescaling after eq. (condvk))              */
+/*   N1  = sigma1 N*, rounded up to an even integer; sigma1,eff = N1/N*       */
+/*   K1  = N1 + 2 m1 = a N1           (eq. (consta))                          */
+/*   N2  = sigma2 K1, rounded up to an even 2^a 3^b 5^c 7^d;                  */
+/*         sigma2,eff = N2/K1                                                 */
+/*   beta_j = 2 pi m_j (1 - 1/(2 sigma_j,eff))   (Section 4)                  */
+/* Returns 0, or 1 when the input violates m_j >= 2, sigma_j > 1, N >= 1 or   */
+/* the step-4 condition 2 m2 <= (1 - 1/sigma1) N2.                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    i64 N, Nstar, N1, K1, N2;
+    int m1, m2;
+    double sigma1, sigma2;   /* effective */
+    double beta1, beta2, a;
+} orc_params;
+
+static int is_7smooth(i64 n) {
+    if (n <= 0) return 0;
+    const i64 p[4] = {2, 3, 5, 7};
+    for (int i = 0; i < 4; ++i) while (n % p[i] == 0) n /= p[i];
+    return n == 1;
+}
+
+int orc_make_params(i64 N, double sigma1, double sigma2, int m1, int m2, orc_params *P) {
+    if (N < 1 || m1 < 2 || m2 < 2 || !(sigma1 > 1.0) || !(sigma2 > 1.0)) return 1;
+    memset(P, 0, sizeof(*P));
+    P->N = N; P->m1 = m1; P->m2 = m2;
+    i64 c = (i64)ceil(2.0 * m1 / sigma1 - 1e-12);
+    P->Nstar = N + c;
+    i64 n1 = (i64)ceil(sigma1 * (double)P->Nstar - 1e-9);
+    if (n1 % 2) n1 += 1;
+    P->N1 = n1;
+    P->K1 = n1 + 2 * m1;
+    i64 n2 = (i64)ceil(sigma2 * (double)P->K1 - 1e-9);
+    if (n2 % 2) n2 += 1;
+    while (!is_7smooth(n2)) n2 += 2;
+    P->N2 = n2;
+    P->sigma1 = (double)P->N1 / (double)P->Nstar;
+    P->sigma2 = (double)P->N2 / (double)P->K1;
+    P->beta1 = 2.0 * M_PI * m1 * (1.0 - 1.0 / (2.0 * P->sigma1));
+    P->beta2 = 2.0 * M_PI * m2 * (1.0 - 1.0 / (2.0 * P->sigma2));
+    P->a = (double)P->K1 / (double)P->N1;
+    if ((double)(2 * m2) > (1.0 - 1.0 / P->sigma1) * (double)P->N2) return 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 2.2 (NNFFT), step by step, for v_k, x_j in [-1/2,1/2]:           */
+/*   rescale v*_k = (N/N*) v_k so that N v_k = N* v*_k (after eq. (condvk));      */
+/*   step 1: g_l = (1/N1) sum_k f_k phi1(l/N1 - v*_k), l in I_{K1} (eq. (gell)) */
+/*   step 2: ghat_l = g_l / phi2hat(l)  (phi2hat at the integer l; see DESIGN) */
+/*   step 3: h_s = (1/N2) sum_l ghat_l exp(-2 pi i l s / N2), s in I_{N2}      */
+/*           (a naive DFT with the index product reduced mod N2 in integers)   */
+/*   step 4: s1_j = sum_{s in I''(x_j)} h_s phi2(x_j/sigma1 - s/N2)            */
+/*   output: s1_j / phi1hat(N* x_j).                                           */
+/* Optional g (K1 complex) and h (N2 complex) receive the step-1 and step-3    */
+/* arrays.  Windows are evaluated exactly (no tables, no polynomial).          */
+/* ------------------------------------------------------------------------ */
+static void alg22_spread_v(const orc_params *P, i64 M1, const double *v, const double *f,
+                           double *g) {
+    i64 K1 = P->K1, N1 = P->N1;
+    int m1 = P->m1;
+    memset(g, 0, sizeof(double) * 2 * K1);
+    for (i64 k = 0; k < M1; ++k) {
+        double vs = ((double)P->N * v[k]) / (double)P->Nstar;   /* v*_k */
+        double u = (double)N1 * vs;
+        i64 lo = (i64)ceil(u - m1), hi = (i64)floor(u + m1);
+        for (i64 l = lo; l <= hi; ++l) {
+            if (l < -K1 / 2 || l >= K1 / 2) continue;      /* outside I_{K1} */
+            double w = orc_phi((double)l / (double)N1 - vs, N1, m1, P->beta1);
+            g[2 * (l + K1 / 2)]     += f[2 * k] * w / (double)N1;
+            g[2 * (l + K1 / 2) + 1] += f[2 * k + 1] * w / (double)N1;
+        }
+    }
+}
+
+static void dft_centered(i64 Nin, i64 Nout, i64 Nmod, int sign, const double *in, double *out,
+                         int nthreads) {
+    int nt = use_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (i64 so = 0; so < Nout; ++so) {
+        i64 s = so - Nout / 2;
+        ksum re = {0, 0}, im = {0, 0};
+        for (i64 li = 0; li < Nin; ++li) {
+            i64 l = li - Nin / 2;
+            i64 r = ((l * s) % Nmod + Nmod) % Nmod;
+            double ang = 2.0 * M_PI * (double)r / (double)Nmod;
+            double cs = cos(ang), sn = sign * sin(ang);
+            double xr = in[2 * li], xi = in[2 * li + 1];
+            kadd(&re, xr * cs - xi * sn);
+            kadd(&im, xr * sn + xi * cs);
+        }
+        out[2 * so] = kval(&re);
+        out[2 * so + 1] = kval(&im);
+    }
+}
+
+int orc_nnfft_alg22(const orc_params *P, i64 M1, const double *v, const double *f,
+                    i64 M2, const double *x, double *out, double *g_out, double *h_out,
+                    int nthreads) {
+    i64 K1 = P->K1, N1 = P->N1, N2 = P->N2;
+    double *g = (double *)calloc(2 * K1, sizeof(double));
+    double *h = (double *)calloc(2 * N2, sizeof(double));
+    if (!g || !h) { free(g); free(h); return 2; }
+    /* step 1 */
+    alg22_spread_v(P, M1, v, f, g);
+    if (g_out) memcpy(g_out, g, sizeof(double) * 2 * K1);
+    /* step 2: ghat_l = g_l / phi2hat(l) */
+    for (i64 li = 0; li < K1; ++li) {
+        double ph = orc_phi_hat((double)(li - K1 / 2), N2, P->m2, P->beta2);
+        g[2 * li] /= ph; g[2 * li + 1] /= ph;
+    }
+    /* step 3: h_s = (1/N2) sum_l ghat_l exp(-2 pi i l s / N2) */
+    dft_centered(K1, N2, N2, -1, g, h, nthreads);
+    for (i64 i = 0; i < 2 * N2; ++i) h[i] /= (double)N2;
+    if (h_out) memcpy(h_out, h, sizeof(double) * 2 * N2);
+    /* step 4 and output */
+    int m2 = P->m2;
+    for (i64 j = 0; j < M2; ++j) {
+        double xs = x[j] * (double)P->Nstar / (double)N1;     /* x_j / sigma1 */
+        double u = (double)N2 * xs;
+        i64 lo = (i64)ceil(u - m2), hi = (i64)floor(u + m2);
+        double sr = 0, si = 0;
+        for (i64 s = lo; s <= hi; ++s) {
+            double w = orc_phi(xs - (double)s / (double)N2, N2, m2, P->beta2);
+            i64 si_ = ((s % N2) + N2 + N2 / 2) % N2;          /* centered index of s mod N2 */
+            sr += h[2 * si_] * w;
+            si += h[2 * si_ + 1] * w;
+        }
+        double ph1 = orc_phi_hat((double)P->Nstar * x[j], N1, P->m1, P->beta1);
+        out[2 * j] = sr / ph1;
+        out[2 * j + 1] = si / ph1;
+    }
+    free(g); free(h);
+    return 0;
+}
+
+/* Exact transpose (conjugate transpose; every window and transform is real) of
+ * the map f -> out of orc_nnfft_alg22, step by step in reverse order:
+ *   g'_j = g_j / phi1hat(N* x_j);  H_s = sum_j g'_j phi2(x_j/sigma1 - s/N2);
+ *   G_l = (1/N2) sum_s H_s exp(+2 pi i l s/N2), l in I_{K1};  G_l /= phi2hat(l);
+ *   z_k = (1/N1) sum_l G_l phi1(l/N1 - v*_k).
+ * It approximates z_k = sum_j g_j exp(+2 pi i N v_k x_j). */
+int orc_nnfft_alg22_adjoint(const orc_params *P, i64 M1, const double *v, i64 M2,
+                            const double *x, const double *gin, double *z, int nthreads) {
+    i64 K1 = P->K1, N1 = P->N1, N2 = P->N2;
+    int m1 = P->m1, m2 = P->m2;
+    double *H = (double *)calloc(2 * N2, sizeof(double));
+    double *G = (double *)calloc(2 * K1, sizeof(double));
+    if (!H || !G) { free(H); free(G); return 2; }
+    for (i64 j = 0; j < M2; ++j) {
+        double ph1 = orc_phi_hat((double)P->Nstar * x[j], N1, m1, P->beta1);
+        double gr = gin[2 * j] / ph1, gi = gin[2 * j + 1] / ph1;
+        double xs = x[j] * (double)P->Nstar / (double)N1;
+        double u = (double)N2 * xs;
+        i64 lo = (i64)ceil(u - m2), hi = (i64)floor(u + m2);
+        for (i64 s = lo; s <= hi; ++s) {
+            double w = orc_phi(xs - (double)s / (double)N2, N2, m2, P->beta2);
+            i64 si_ = ((s % N2) + N2 + N2 / 2) % N2;
+            H[2 * si_] += gr * w;
+            H[2 * si_ + 1] += gi * w;
+        }
+    }
+    dft_centered(N2, K1, N2, +1, H, G, nthreads);
+    for (i64 li = 0; li < K1; ++li) {
+        double ph = orc_phi_hat((double)(li - K1 / 2), N2, m2, P->beta2);
+        G[2 * li] /= ((double)N2 * ph);
+        G[2 * li + 1] /= ((double)N2 * ph);
+    }
+    for (i64 k = 0; k < M1; ++k) {
+        double vs = ((double)P->N * v[k]) / (double)P->Nstar;
+        double u = (double)N1 * vs;
+        i64 lo = (i64)ceil(u - m1), hi = (i64)floor(u + m1);
+        double zr = 0, zi = 0;
+        for (i64 l = lo; l <= hi; ++l) {
+            if (l < -K1 / 2 || l >= K1 / 2) continue;
+            double w = orc_phi((double)l / (double)N1 - vs, N1, m1, P->beta1);
+            zr += G[2 * (l + K1 / 2)] * w;
+            zi += G[2 * (l + K1 / 2) + 1] * w;
+        }
+        z[2 * k] = zr / (double)N1;
+        z[2 * k + 1] = zi / (double)N1;
+    }
+    free(H); free(G);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Theorem 4.1: E(phi_sinh) =                                                */
+/*   (24 m1^{3/2} + 10) exp(-2 pi m1 sqrt(1 - 1/sigma1))                      */
+/* + (24 m2^{3/2} + 10) (2 N1 + 4 m1)/sqrt(2 pi m1)                           */
+/*     * exp(2 pi m1 (1 - sqrt(1 - 1/sigma1) - 1/(2 sigma1)))                 */
+/*     * exp(-2 pi m2 sqrt(1 - 1/sigma2)).                                    */
+/* term[0], term[1] receive the two summands when term != NULL.              */
+/* ------------------------------------------------------------------------ */
+double orc_bound_sinh(i64 N1, int m1, int m2, double sigma1, double sigma2, double *term) {
+    double s1 = sqrt(1.0 - 1.0 / sigma1), s2 = sqrt(1.0 - 1.0 / sigma2);
+    double t1 = (24.0 * pow(m1, 1.5) + 10.0) * exp(-2.0 * M_PI * m1 * s1);
+    double t2 = (24.0 * pow(m2, 1.5) + 10.0) * (2.0 * N1 + 4.0 * m1) / sqrt(2.0 * M_PI * m1)
+              * exp(2.0 * M_PI * m1 * (1.0 - s1 - 1.0 / (2.0 * sigma1)))
+              * exp(-2.0 * M_PI * m2 * s2);
+    if (term) { term[0] = t1; term[1] = t2; }
+    return t1 + t2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Clenshaw-Curtis weights of eq. (wk=) for the rule                         */
+/*   (1/2) int_{-1}^{1} F(t) dt ~ sum_{k=0}^{n} w_k F(z_k), z_k = cos(k pi/n), */
+/* w_k = (1/n) eps(k)^2 sum_{j=0}^{floor(n/2)} eps(2j)^2 2/(1-4j^2) cos(2jk pi/n) */
+/* with eps(0) = eps(n) = sqrt(2)/2 and eps(j) = 1 otherwise (eps(2j) for    */
+/* 2j > n is not used).  Explicit O(n^2) sum.                                */
+/* ------------------------------------------------------------------------ */
+int orc_cc_weights(i64 n, double *z, double *w) {
+    if (n < 1) return 1;
+    for (i64 k = 0; k <= n; ++k) {
+        double ek2 = (k == 0 || k == n) ? 0.5 : 1.0;
+        ksum s = {0, 0};
+        for (i64 j = 0; 2 * j <= n; ++j) {
+            double ej2 = (2 * j == 0 || 2 * j == n) ? 0.5 : 1.0;
+            i64 r = (2 * j * k) % (2 * n);                  /* cos(2 j k pi / n) exactly reduced */
+            kadd(&s, ej2 * 2.0 / (1.0 - 4.0 * (double)j * (double)j) * cos(M_PI * (double)r / (double)n));
+        }
+        w[k] = ek2 * kval(&s) / (double)n;
+        z[k] = cos(M_PI * (double)k / (double)n);
+    }
+    return 0;
+}
+
+/* Theorem 5.3: |sinc(N pi x) - sum_k w_k exp(-pi i N z_k x)| <=
+ *   36 (1 + exp(-2 C N)) / (35 (e^2 - 1)) * exp(-N (nu - C)),  C = pi (e^2-1)/(2e), n = nu N. */
+double orc_cc_constant(void) {
+    double e = exp(1.0);
+    return M_PI * (e * e - 1.0) / (2.0 * e);
+}
+double orc_cc_bound(double N, double nu) {
+    double e = exp(1.0), C = orc_cc_constant();
+    return 36.0 * (1.0 + exp(-2.0 * C * N)) / (35.0 * (e * e - 1.0)) * exp(-N * (nu - C));
+}

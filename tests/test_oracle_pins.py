@@ -1,0 +1,312 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Every oracle function is checked against at least one of: a library routine used
+as an independent route (numpy FFT, numpy Gauss-Legendre, scipy Bessel functions
+and quadrature), a closed form or invariant the paper states, brute force at
+higher precision (mpmath), or a number the paper prints (tests/golden/).
+A plausible slip in the oracle -- a dropped term, a wrong sign, a swapped index or
+a missing scale -- fails at least one test here.  No GPU is needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_02671_gb300 import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+
+
+# --------------------------------------------------------------------------------------
+# eq. (f(xj)): the direct exponential sum
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [8, 16, 30])
+def test_expsum_equispaced_is_the_dft(N):
+    """v_k = k/N, x_j = j/N (k, j in I_N) turn eq. (f(xj)) into a length-N DFT (numpy FFT)."""
+    rng = np.random.default_rng(N)
+    k = np.arange(-N // 2, N - N // 2)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    y = oracle.nnfft_direct(N, k / N, f, k / N)
+    # sum_{k in I_N} f_k e^{-2 pi i k j / N} = e^{2 pi i (N//2) j / N} * FFT(f in natural order)[j mod N]
+    F = np.fft.fft(f)          # f[i] is the coefficient of k = i - N//2
+    ref = np.exp(2j * np.pi * (N // 2) * k / N) * F[np.mod(k, N)]
+    assert np.max(np.abs(y - ref)) < 1e-13 * np.sum(np.abs(f))
+
+
+def test_expsum_single_term_matches_high_precision():
+    """One coefficient at large N: exp(-2 pi i N v x) against 50-digit mpmath."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(3)
+    N = 1 << 22
+    v = rng.uniform(-0.5, 0.5, 5)
+    x = rng.uniform(-0.5, 0.5, 7)
+    for k in range(5):
+        f = np.zeros(5, complex); f[k] = 1.0
+        y = oracle.nnfft_direct(N, v, f, x)
+        for j in range(7):
+            ph = -2 * mp.pi * N * mp.mpf(float(v[k])) * mp.mpf(float(x[j]))
+            ref = complex(mp.cos(ph), mp.sin(ph))
+            assert abs(y[j] - ref) < 5e-15
+
+
+def test_expsum_linearity_and_rows():
+    rng = np.random.default_rng(5)
+    v, x, f = W.nnfft_inputs(40, 33, 1)
+    g = rng.standard_normal(40) + 1j * rng.standard_normal(40)
+    N = 100
+    y = oracle.nnfft_direct(N, v, 2.5 * f - 1j * g, x)
+    ref = 2.5 * oracle.nnfft_direct(N, v, f, x) - 1j * oracle.nnfft_direct(N, v, g, x)
+    assert np.max(np.abs(y - ref)) < 1e-12
+    rows = np.array([32, 0, 7])
+    assert np.allclose(oracle.nnfft_direct(N, v, f, x, rows=rows), oracle.nnfft_direct(N, v, f, x)[rows],
+                       rtol=0, atol=1e-13)
+
+
+def test_adjoint_identity_of_direct_sums():
+    """<A f, g> = <f, A* g> with A from eq. (f(xj)) and A* its conjugate transpose."""
+    v, x, f = W.nnfft_inputs(50, 70, 2)
+    g = W.adjoint_inputs(70, 2)
+    N = 300
+    Af = oracle.nnfft_direct(N, v, f, x)
+    Ag = oracle.nnfft_adjoint_direct(N, v, x, g)
+    lhs = np.vdot(g, Af)
+    rhs = np.vdot(Ag, f)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # the adjoint is not the forward with swapped roles and the same sign
+    wrong = oracle.expsum(N, x, g, v, -1)
+    assert np.max(np.abs(wrong - Ag)) > 1e-3
+
+
+# --------------------------------------------------------------------------------------
+# eq. (discretesinctransf) and eq. (approxsinctrafo)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [16, 64, 127])
+def test_sinc_shannon_identity(N):
+    """a_k = b_k = k/N: sinc(pi (l - k)) is the identity matrix, so h(l/N) = c_l."""
+    rng = np.random.default_rng(N)
+    k = np.arange(-(N // 2), N - N // 2) / N
+    c = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    h = oracle.sinc_direct(N, k, c, k)
+    assert np.max(np.abs(h - c)) < 1e-13
+
+
+def test_sinc_single_term_matches_high_precision():
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    rng = np.random.default_rng(11)
+    for N in (7, 1024, 1 << 20):
+        a = rng.uniform(-0.5, 0.5, 4)
+        b = np.concatenate([rng.uniform(-0.5, 0.5, 4), a[:1], a[1:2] + 1e-12])
+        c = np.eye(4)[0].astype(complex)
+        h = oracle.sinc_direct(N, a, c, b)
+        for l in range(len(b)):
+            d = mp.mpf(float(b[l])) - mp.mpf(float(a[0]))
+            ref = mp.mpf(1) if d == 0 else mp.sin(mp.pi * N * d) / (mp.pi * N * d)
+            assert abs(h[l] - complex(ref)) < 1e-15
+
+
+def test_gauss_legendre_rule():
+    """Sum of weights 1; exact for monomials up to degree 2n-1; numpy's leggauss as a cross-check."""
+    for n in (1, 2, 5, 64, 2048):
+        tau, w = oracle.gauss_legendre(n)
+        assert abs(w.sum() - 1) < 1e-14
+        assert np.all(np.diff(tau) > 0)
+        assert np.max(np.abs(tau + tau[::-1])) < 1e-15
+        t_np, w_np = np.polynomial.legendre.leggauss(n)
+        assert np.max(np.abs(tau - t_np / 2)) < 1e-14
+        assert np.max(np.abs(w - w_np / 2)) < 1e-14 * max(1.0, n / 64)
+    tau, w = oracle.gauss_legendre(12)
+    for p in range(0, 24, 2):   # int_{-1/2}^{1/2} t^p dt = 2 (1/2)^{p+1}/(p+1)
+        exact = 2 * 0.5 ** (p + 1) / (p + 1)
+        assert abs(np.sum(w * tau ** p) - exact) < 1e-15
+    assert abs(np.sum(w * tau ** 25)) < 1e-16
+
+
+@pytest.mark.parametrize("N", [64, 256])
+def test_sinc_gl_definition_approximates_direct(N):
+    """The 2N-node Gauss-Legendre factorisation reproduces the direct sinc sum (N >= 64)."""
+    a, c, b = W.sinc_inputs(300, 200, 4)
+    h = oracle.sinc_direct(N, a, c, b)
+    hg = oracle.sinc_gl(N, a, c, b)
+    err = np.max(np.abs(h - hg)) / np.sum(np.abs(c))
+    assert err < 1e-12
+    # far too few nodes must visibly fail: the check has teeth
+    hbad = oracle.sinc_gl(N, a, c, b, n=N // 2)
+    assert np.max(np.abs(h - hbad)) / np.sum(np.abs(c)) > 1e-6
+
+
+# --------------------------------------------------------------------------------------
+# Example 2.1 / eq. (hatomegasinh): the sinh-type window and its Fourier transform
+# --------------------------------------------------------------------------------------
+def test_omega_sinh_properties():
+    beta = 2 * math.pi * 8 * 0.75
+    xs = np.linspace(0, 1, 1001)
+    w = oracle.omega_sinh(xs, beta)
+    assert w[0] == 1.0 and w[-1] == 0.0
+    assert np.all(np.diff(w) <= 0)
+    assert np.allclose(oracle.omega_sinh(-xs, beta), w, rtol=0, atol=0)
+    assert oracle.omega_sinh(1.5, beta) == 0.0
+    # the overflow-safe quotient equals sinh(beta sqrt(1-x^2))/sinh(beta) where both are finite
+    for beta in (3.0, 18.8, 37.7):
+        x = np.linspace(-0.99, 0.99, 37)
+        ref = np.sinh(beta * np.sqrt(1 - x ** 2)) / np.sinh(beta)
+        assert np.max(np.abs(oracle.omega_sinh(x, beta) - ref) / np.maximum(ref, 1e-300)) < 8e-15
+
+
+@pytest.mark.parametrize("m,sigma", [(4, 2.0), (8, 2.0), (6, 1.5), (2, 1.25)])
+def test_omega_sinh_hat_against_quadrature_and_scipy(m, sigma):
+    """eq. (hatomegasinh) against 2 int_0^1 omega(x) cos(2 pi v x) dx (Section 2) and scipy's I1, J1."""
+    integrate = pytest.importorskip("scipy.integrate")
+    special = pytest.importorskip("scipy.special")
+    beta = 2 * math.pi * m * (1 - 1 / (2 * sigma))
+    vb = beta / (2 * math.pi)                 # = m (1 - 1/(2 sigma)), the branch point
+    for v in [0.0, 0.3 * vb, m / (2 * sigma), 0.999 * vb, vb, 1.2 * vb, 2.5 * vb]:
+        quad, _ = integrate.quad(lambda t: 2 * oracle.omega_sinh(t, beta) * math.cos(2 * math.pi * v * t),
+                                 0, 1, limit=400, epsabs=1e-16, epsrel=1e-13)
+        val = oracle.omega_sinh_hat(v, beta)
+        assert abs(val - quad) < 1e-11 * max(1.0, abs(quad)) + 1e-15
+        q = beta ** 2 - 4 * math.pi ** 2 * v ** 2
+        pref = math.pi * beta / math.sinh(beta)
+        if q > 0:
+            ref = pref * special.i1(math.sqrt(q)) / math.sqrt(q)
+        elif q == 0:
+            ref = pref * GOLD["sinh_hat_boundary"]["value_over_prefactor"]
+        else:
+            ref = pref * special.j1(math.sqrt(-q)) / math.sqrt(-q)
+        assert abs(val - ref) < 1e-13 * abs(ref) + 1e-16
+
+
+def test_phi_hat_is_fourier_transform_of_phi():
+    """phihat(v) = int phi(t) e^{-2 pi i v t} dt for the scaled window (proof of Theorem 3.4)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    m, Nj = 5, 300
+    beta = 2 * math.pi * m * (1 - 1 / 4)
+    for v in (0.0, 17.0, 61.5, 140.0):
+        quad, _ = integrate.quad(lambda t: 2 * oracle.phi(t, Nj, m, beta) * math.cos(2 * math.pi * v * t),
+                                 0, m / Nj, limit=400, epsabs=1e-18, epsrel=1e-13)
+        assert abs(oracle.phi_hat(v, Nj, m, beta) - quad) < 1e-12 * abs(quad)
+
+
+# --------------------------------------------------------------------------------------
+# Section 2: parameters; Algorithm 2.2 and its transpose; Theorem 4.1
+# --------------------------------------------------------------------------------------
+def test_params_follow_section_2():
+    P = oracle.make_params(64, 2, 2, 4, 4)
+    assert (P.Nstar, P.N1, P.K1, P.N2) == (68, 136, 144, 288)      # N2 = sigma2 (N1 + 2 m1) already 7-smooth
+    P = oracle.make_params(4096, 2, 2, 8, 8)
+    assert (P.Nstar, P.N1, P.K1) == (4104, 8208, 8224)
+    assert P.N2 >= 2 * P.K1 and P.N2 % 2 == 0 and P.N2 == 16464   # 16448 = 2^6*257 rounded to 2^4*3*7^3
+    for N, s1, s2, m1, m2 in [(64, 2, 2, 4, 4), (1000, 1.5, 1.25, 6, 3), (77, 1.3, 2.2, 2, 5)]:
+        P = oracle.make_params(N, s1, s2, m1, m2)
+        a = 1 + 2 * m1 / P.N1                                        # eq. (consta)
+        assert abs(P.a - a) < 1e-15 and P.K1 == P.N1 + 2 * m1
+        assert P.N1 % 2 == 0 and P.N1 >= s1 * P.Nstar - 1e-9
+        # eq. (condvk): v in [-1/2, 1/2] rescaled by N/N* lands in [-1/(2a), 1/(2a)]
+        assert 0.5 * N / P.Nstar <= 1 / (2 * a) + 1e-15
+        assert 2 * m2 <= (1 - 1 / P.sigma1) * P.N2                   # step 4 condition
+        assert abs(P.beta1 - 2 * math.pi * m1 * (1 - 1 / (2 * P.sigma1))) < 1e-13
+    with pytest.raises(ValueError):
+        oracle.make_params(64, 2, 2, 1, 4)
+    with pytest.raises(ValueError):
+        oracle.make_params(64, 1.0, 2, 4, 4)
+    with pytest.raises(ValueError):
+        oracle.make_params(4, 1.05, 1.05, 2, 9)     # 2 m2 > (1 - 1/sigma1) N2
+
+
+@pytest.mark.parametrize("N,M1,M2,m", [(64, 128, 128, 4), (64, 100, 90, 6), (200, 300, 257, 8)])
+def test_alg22_within_theorem_4_1(N, M1, M2, m):
+    """Algorithm 2.2 approximates the direct sum within the bound of Theorem 4.1."""
+    v, x, f = W.nnfft_inputs(M1, M2, 0)
+    P = oracle.make_params(N, 2, 2, m, m)
+    y = oracle.nnfft_direct(N, v, f, x)
+    ya = oracle.nnfft_alg22(P, v, f, x)
+    err = oracle.relative_error(ya, y, f)
+    E, _, _ = oracle.bound_sinh(P.N1, m, m, P.sigma1, P.sigma2)
+    assert err <= E
+    if m == 8:
+        assert err < 1e-13
+
+
+def test_alg22_error_decays_exponentially_in_m():
+    N, M = 128, 400
+    v, x, f = W.nnfft_inputs(M, M, 7, nodes="chebyshev")
+    y = oracle.nnfft_direct(N, v, f, x)
+    errs = []
+    for m in (2, 3, 4, 5, 6, 7):
+        P = oracle.make_params(N, 2, 2, m, m)
+        errs.append(oracle.relative_error(oracle.nnfft_alg22(P, v, f, x), y, f))
+    assert all(e2 < 0.3 * e1 for e1, e2 in zip(errs, errs[1:]))
+    # roughly exp(-2 pi m sqrt(1 - 1/sigma)) per step: at least a factor 20 per unit of m
+    assert errs[-1] < errs[0] * 20.0 ** -5
+
+
+def test_alg22_stages():
+    """Step 1: sum_l g_l = phi1hat(0) sum_k f_k up to aliasing (Poisson summation);
+    step 3: h is the zero-padded DFT of g/phi2hat (numpy FFT)."""
+    N, M, m = 64, 50, 6
+    v, x, f = W.nnfft_inputs(M, 9, 8)
+    P = oracle.make_params(N, 2, 2, m, m)
+    out, g, h = oracle.nnfft_alg22(P, v, f, x, return_stages=True)
+    ph0 = oracle.phi_hat(0.0, P.N1, m, P.beta1)
+    assert abs(g.sum() - ph0 * f.sum()) < 1e-9 * np.sum(np.abs(f))
+    K1, N2 = P.K1, P.N2
+    ell = np.arange(-K1 // 2, K1 // 2)
+    ghat = g / oracle.phi_hat(ell.astype(float), N2, m, P.beta2)
+    pad = np.zeros(N2, complex)
+    pad[np.mod(ell, N2)] = ghat
+    Hs = np.fft.fft(pad) / N2                     # index s mod N2, sign e^{-2 pi i l s / N2}
+    s = np.arange(-N2 // 2, N2 // 2)
+    assert np.max(np.abs(h - Hs[np.mod(s, N2)])) < 1e-12 * np.max(np.abs(Hs))
+
+
+def test_alg22_adjoint_is_exact_transpose():
+    for (N, M1, M2, m) in [(64, 40, 60, 4), (100, 77, 31, 7)]:
+        v, x, f = W.nnfft_inputs(M1, M2, 3)
+        g = W.adjoint_inputs(M2, 3)
+        P = oracle.make_params(N, 2, 2, m, m)
+        Af = oracle.nnfft_alg22(P, v, f, x)
+        Ag = oracle.nnfft_alg22_adjoint(P, v, x, g)
+        lhs, rhs = np.vdot(g, Af), np.vdot(Ag, f)
+        assert abs(lhs - rhs) < 1e-13 * np.sum(np.abs(f)) * np.sum(np.abs(g))
+        z = oracle.nnfft_adjoint_direct(N, v, x, g)
+        E, _, _ = oracle.bound_sinh(P.N1, m, m, P.sigma1, P.sigma2)
+        assert oracle.relative_error(Ag, z, g) <= E
+
+
+# --------------------------------------------------------------------------------------
+# Section 5: Clenshaw-Curtis weights eq. (wk=) and Theorem 5.3
+# --------------------------------------------------------------------------------------
+def test_cc_weights():
+    for n in (1, 2, 3, 8, 16, 33, 256):
+        z, w = oracle.cc_weights(n)
+        assert abs(w.sum() - GOLD["cc_weights_sum"]["value"]) < 1e-14
+        assert np.max(np.abs(w - w[::-1])) < 1e-15 and np.max(np.abs(z + z[::-1])) < 1e-15
+        assert np.all(w > 0)
+        # (1/2) int_{-1}^{1} t^p dt exact for p <= n
+        for p in range(0, n + 1):
+            exact = 0.0 if p % 2 else 1.0 / (p + 1)
+            assert abs(np.sum(w * z ** p) - exact) < 1e-13
+    z, w = oracle.cc_weights(2)                    # Simpson's rule halved: 1/6, 2/3, 1/6
+    assert np.max(np.abs(w - np.array([1, 4, 1]) / 6)) < 1e-15
+
+
+def test_cc_constant_and_worked_example():
+    g = GOLD["cc_constant"]
+    assert round(oracle.cc_constant(), g["digits"]) == g["value"]
+    ex = GOLD["cc_n_ge_4N_for_N_ge_54"]
+    assert oracle.cc_bound(ex["N_min"], ex["nu"]) < ex["epsilon"]
+    assert oracle.cc_bound(ex["N_min"] - 1, ex["nu"]) > ex["epsilon"]
+
+
+@pytest.mark.parametrize("N,nu", [(8, 4), (16, 5), (32, 6)])
+def test_cc_sinc_error_below_theorem_5_3(N, nu):
+    n = nu * N
+    z, w = oracle.cc_weights(n)
+    x = np.linspace(-1, 1, 2001)
+    approx = (w[None, :] * np.exp(-1j * np.pi * N * z[None, :] * x[:, None])).sum(1)
+    exact = np.array([oracle.sinc_Npi(N, t, 0.0) for t in x])
+    assert np.max(np.abs(approx - exact)) <= oracle.cc_bound(N, nu) + 1e-14
