@@ -1,0 +1,438 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 NNFFT library.
+
+One step = one pass of the whole hot path on a fresh node set:
+  nnfft_set_nodes (binning + sort of both node sets, Algorithm 2.2 step 0)
+  + nnfft_exec (steps 1-4, forward) + nnfft_adjoint (its transpose)
+at N = 4096, M1 = M2 = 2^20 uniform nodes, complex128, sigma1 = sigma2 = 2,
+m1 = m2 = 8 (the fp64 / 1e-12 workload).  The metric counts M1 + M2 points per
+transform, so a step processes 2 (M1 + M2) points.  Inputs are resident in HBM;
+L2 is flushed (512 MB write) between timed steps and every step is timed with
+CUDA events on the plan stream.
+
+Also reported (same JSON line): per-stage device times, the roofline of the
+dominant kernel, the fp32 path (m = 4), Chebyshev nodes, exec-only throughput
+with a resident plan, the fast sinc transform (N = 1024, L1 = L2 = 2^18), the
+end-to-end number through the host-buffer C ABI calls, and the CPU oracle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NNFFT nonuniform pts/sec (M1+M2)/s at 1e-12 FP64 vs 2e-5 FP32 batched; p99 latency"
+N_BW, M_PTS = 4096, 1 << 20
+SINC_N, SINC_L = 1024, 1 << 18
+L2_FLUSH_BYTES = 512 << 20
+WORKLOAD = ("nnfft_fp64 N=4096 M1=M2=2^20 uniform nodes sigma=2 m=8: "
+            "set_nodes + forward + adjoint per step")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 FMA peak of GB300: the profiling recipe lists 1.25 TFLOP/s FP64, i.e. 152 SMs x
+# 2 FP64 FMA per clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------------------------------------
+# the CPU oracle (baseline leg and reference arm)
+# -------------------------------------------------------------------------------------------
+def oracle_sample(seconds_target=12.0, seed=0):
+    """Time the oracle's direct sums on a bounded row sample of the workload; extrapolate."""
+    import oracle
+    from paper_2107_02671_gb300 import workloads as W
+    v, x, f = W.nnfft_inputs(M_PTS, M_PTS, seed)
+    g = W.adjoint_inputs(M_PTS, seed)
+    cores = oracle.num_threads()
+    probe = 8
+    t0 = time.perf_counter()
+    oracle.nnfft_direct(N_BW, v, f, x, rows=np.arange(probe))
+    per_row = (time.perf_counter() - t0) / probe
+    J = int(max(16, min(M_PTS, seconds_target / 2 / max(per_row, 1e-9))))
+    rows = W.sample_rows(M_PTS, J, seed)
+    t0 = time.perf_counter()
+    oracle.nnfft_direct(N_BW, v, f, x, rows=rows)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.nnfft_adjoint_direct(N_BW, v, x, g, rows=rows)
+    t_adj = time.perf_counter() - t0
+    full = (t_fwd + t_adj) * M_PTS / len(rows)
+    return {"value": 4 * M_PTS / full, "unit": "pts/s", "cores": cores, "kind": "oracle",
+            "sample": (f"direct fp64 sums for {len(rows)} sampled output rows of the forward and "
+                       f"of the adjoint at N=4096, M1=M2=2^20 (each row sums all 2^20 terms); "
+                       f"extrapolated x{M_PTS / len(rows):.0f} to the full step"),
+            "seconds": t_fwd + t_adj}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_2107_02671_gb300 import workloads as W
+    v, x, f = W.nnfft_inputs(M_PTS, M_PTS, 0)
+    g = W.adjoint_inputs(M_PTS, 0)
+    cores = oracle.num_threads()
+    probe = 4
+    t0 = time.perf_counter()
+    oracle.nnfft_direct(N_BW, v, f, x, rows=np.arange(probe))
+    per_row = (time.perf_counter() - t0) / probe
+    total_budget = 150.0   # seconds for warmup + timed steps together
+    J = int(max(4, min(4096, total_budget / (args.steps + args.warmup) / 2 / max(per_row, 1e-9))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = W.sample_rows(M_PTS, J, 100 + s)
+        t0 = time.perf_counter()
+        oracle.nnfft_direct(N_BW, v, f, x, rows=rows)
+        oracle.nnfft_adjoint_direct(N_BW, v, x, g, rows=rows)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt * M_PTS / len(rows))          # extrapolated full-step seconds
+    full = float(np.mean(times))
+    value = 4 * M_PTS / full
+    sample = (f"per step: direct fp64 forward and adjoint sums for {J} sampled output rows "
+              f"(all 2^20 terms each), extrapolated x{M_PTS / J:.0f} to the full step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_BW, "M1": M_PTS, "M2": M_PTS,
+                                        "m": 8, "sigma": 2.0, "nodes": "uniform"},
+        "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------------------------------
+# our arm
+# -------------------------------------------------------------------------------------------
+def flops_per_point(D, with_r, NR=8):
+    """fp64 flops one point costs in the moments / evaluation kernels (FMA = 2 flops)."""
+    fma = (D - 2) + 2 * D + (NR if with_r else 0)
+    return 2 * fma + (2 if with_r else 0)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2107_02671_gb300 import nnfft as B
+    from paper_2107_02671_gb300 import workloads as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    B.load_library()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    # ---- headline workload -----------------------------------------------------------------
+    v, x, f = W.nnfft_inputs(M_PTS, M_PTS, rank)
+    g = W.adjoint_inputs(M_PTS, rank)
+    vd, xd, fd, gd = to_dev(v), to_dev(x), to_dev(f), to_dev(g)
+    y = torch.empty(M_PTS, dtype=torch.complex128, device=dev)
+    z = torch.empty(M_PTS, dtype=torch.complex128, device=dev)
+    plan = B.Plan(N_BW, M_PTS, M_PTS, 2.0, 2.0, 8, 8, dtype=torch.complex128)
+    info = plan.info
+
+    def step(p=plan, vv=vd, xx=xd, ff=fd, gg=gd, yy=y, zz=z):
+        p.set_nodes(vv, xx)
+        p.exec(ff, yy)
+        p.adjoint(gg, zz)
+
+    def timed(stepfn, k, pl=None, flush_l2=True):
+        """Per-step CUDA-event timing on the plan stream, L2 flushed between steps."""
+        evs = []
+        torch.cuda.synchronize()
+        barrier()
+        if pl is not None:
+            pl.timing(True)
+            pl.timing_read(reset=True)
+        l0 = B.launch_count()
+        for _ in range(k):
+            if flush_l2:
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stepfn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        launches = B.launch_count() - l0
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        stages = None
+        if pl is not None:
+            stages = pl.timing_read(reset=True)
+            pl.timing(False)
+        return ms, launches, stages
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.sync()
+    with ClockSampler(local) as clk:
+        ms, launches, stages = timed(step, args.steps, plan)
+    plan.sync()
+    total_ms = float(np.sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pts_step = 2 * (M_PTS + M_PTS)
+    value = world * args.steps * pts_step / (total_ms / 1e3)
+
+    # ---- accuracy on sampled rows (rank 0) --------------------------------------------------
+    acc = None
+    if rank == 0:
+        try:
+            import oracle
+            rows = W.sample_rows(M_PTS, 16, 99)
+            yh = y.cpu().numpy()
+            ex = oracle.nnfft_direct(N_BW, v, f, x, rows=rows)
+            acc = float(np.max(np.abs(yh[rows] - ex)) / np.sum(np.abs(f)))
+        except Exception as e:  # accuracy is reported, the tests enforce it
+            acc = f"unavailable: {e}"
+
+    # ---- roofline of the dominant kernel ----------------------------------------------------
+    stage_ms = {k: (tot / max(n, 1), n) for k, (tot, n) in stages.items() if n}
+    dom = max(stage_ms, key=lambda k: stage_ms[k][0] * stage_ms[k][1])
+    avg_ms = stage_ms[dom][0]
+    D1, D2 = info["D1"], info["D2"]
+    kernel_flops = {"fwd_moments": flops_per_point(D1, False) * M_PTS,
+                    "adj_eval": flops_per_point(D1, False) * M_PTS,
+                    "fwd_eval": flops_per_point(D2, True) * M_PTS,
+                    "adj_moments": flops_per_point(D2, True) * M_PTS}
+    pk, pk_kind = peaks()
+    if dom in kernel_flops:
+        achieved = kernel_flops[dom] / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA pipe, nominal 1.25 TFLOP/s (152 SMs x 2 FMA/clk x 2.07 GHz)",
+                "algorithmic_flops_per_launch": kernel_flops[dom],
+                "hbm_view": {"algorithmic_bytes_per_launch": 24 * M_PTS,
+                             "achieved_gbs": 24 * M_PTS / (avg_ms / 1e3) / 1e9,
+                             "peak_gbs": pk["hbm_gbs"],
+                             "frac": 24 * M_PTS / (avg_ms / 1e3) / 1e9 / pk["hbm_gbs"]}}
+    else:
+        roof = {"bound": "latency", "kernel": dom, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+
+    extra = {}
+    # ---- exec-only with a resident plan (fp64) ------------------------------------------------
+    def fwd_adj():
+        plan.exec(fd, y)
+        plan.adjoint(gd, z)
+    ms_e, _, _ = timed(fwd_adj, max(3, args.steps // 2))
+    extra["exec_only_fp64"] = {"value": pts_step / (np.mean(ms_e) / 1e3), "unit": "pts/s",
+                               "ms_per_step": float(np.mean(ms_e)),
+                               "what": "forward + adjoint with resident plan (nodes already set)"}
+
+    # ---- Chebyshev nodes (fp64) ----------------------------------------------------------------
+    vc, xc, _ = W.nnfft_inputs(M_PTS, M_PTS, rank, nodes="chebyshev")
+    vcd, xcd = to_dev(vc), to_dev(xc)
+    step_c = lambda: step(vv=vcd, xx=xcd)   # noqa: E731
+    step_c(); torch.cuda.synchronize()
+    ms_c, _, _ = timed(step_c, max(3, args.steps // 2))
+    plan.sync()
+    extra["chebyshev_fp64"] = {"value": pts_step / (np.mean(ms_c) / 1e3), "unit": "pts/s",
+                               "ms_per_step": float(np.mean(ms_c))}
+    del vcd, xcd
+
+    # ---- fp32 path (m = 4) -------------------------------------------------------------------
+    f32 = fd.to(torch.complex64)
+    g32 = gd.to(torch.complex64)
+    y32 = torch.empty(M_PTS, dtype=torch.complex64, device=dev)
+    z32 = torch.empty(M_PTS, dtype=torch.complex64, device=dev)
+    plan32 = B.Plan(N_BW, M_PTS, M_PTS, 2.0, 2.0, 4, 4, dtype=torch.complex64)
+    step32 = lambda: step(p=plan32, ff=f32, gg=g32, yy=y32, zz=z32)   # noqa: E731
+    for _ in range(2):
+        step32()
+    ms32, _, st32 = timed(step32, max(3, args.steps // 2), plan32)
+    plan32.sync()
+    st32ms = {k: tot / max(n, 1) for k, (tot, n) in st32.items() if n}
+    hbm32 = {}
+    for kname, nbytes in (("fwd_moments", 16 * M_PTS), ("fwd_eval", 16 * M_PTS),
+                          ("adj_moments", 16 * M_PTS), ("adj_eval", 16 * M_PTS)):
+        if kname in st32ms:
+            gbs = nbytes / (st32ms[kname] / 1e3) / 1e9
+            hbm32[kname] = {"ms": st32ms[kname], "achieved_gbs": gbs,
+                            "frac": gbs / pk["hbm_gbs"]}
+    extra["fp32_m4"] = {"value": pts_step / (np.mean(ms32) / 1e3), "unit": "pts/s",
+                        "ms_per_step": float(np.mean(ms32)), "D": plan32.info["D1"],
+                        "stage_ms": st32ms, "hbm_roofline_point_kernels": hbm32,
+                        "algorithmic_bytes_per_point": 16}
+    del plan32
+
+    # ---- fast sinc transform (config N=1024, L1=L2=2^18) ----------------------------------------
+    a, c, bb = W.sinc_inputs(SINC_L, SINC_L, rank)
+    ad, cd, bd = to_dev(a), to_dev(c), to_dev(bb)
+    hd = torch.empty(SINC_L, dtype=torch.float64, device=dev)
+    cd32 = cd.to(torch.float32)
+    hd32 = torch.empty(SINC_L, dtype=torch.float32, device=dev)
+    for name, cc, hh, m in (("sinc_fp64_m8", cd, hd, 8), ("sinc_fp32_m4", cd32, hd32, 4)):
+        fn = lambda cc=cc, hh=hh, m=m: B.sinc(SINC_N, ad, cc, bd, m=m, out=hh)   # noqa: E731
+        fn(); fn(); B.sinc_sync()
+        ms_s, _, _ = timed(fn, max(3, args.steps // 2))
+        B.sinc_sync()
+        extra[name] = {"value": 2 * SINC_L / (np.mean(ms_s) / 1e3), "unit": "pts/s (L1+L2)/s",
+                       "ms_per_call": float(np.mean(ms_s))}
+    B.sinc_release()
+
+    # ---- end to end through the host-buffer C ABI calls -----------------------------------------
+    import torch as _t
+    vh = _t.from_numpy(v).pin_memory().numpy()
+    xh = _t.from_numpy(x).pin_memory().numpy()
+    fh = _t.from_numpy(f).pin_memory().numpy()
+    gh = _t.from_numpy(g).pin_memory().numpy()
+    yh = _t.empty(M_PTS, dtype=_t.complex128).pin_memory().numpy()
+    zh = _t.empty(M_PTS, dtype=_t.complex128).pin_memory().numpy()
+
+    def e2e_step():
+        plan.set_nodes_host(vh, xh)
+        plan.exec_host(fh, yh)
+        plan.adjoint_host(gh, zh)
+    e2e_step()
+    k_e2e = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    t_e2e = (time.perf_counter() - t0) / k_e2e
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * pts_step / t_e2e, "unit": "pts/s",
+           "h2d_bytes_per_step": int(vh.nbytes + xh.nbytes + fh.nbytes + gh.nbytes),
+           "d2h_bytes_per_step": int(yh.nbytes + zh.nbytes),
+           "what": "nnfft_set_nodes_host + nnfft_exec_host + nnfft_adjoint_host from pinned host "
+                   "buffers, results copied back, wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_BW, "M1": M_PTS, "M2": M_PTS, "m": 8,
+                       "sigma": 2.0, "nodes": "uniform", "points_per_step": pts_step,
+                       "l2": "flushed between timed steps (512 MB device write, outside the events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "plan": {k: info[k] for k in ("N1", "K1", "N2", "D1", "D2", "fft_n1",
+                                                     "fft_n2")}},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "stage_ms": {k: v_[0] for k, v_ in stage_ms.items()},
+            "max_rel_err_sampled": acc,
+            "peaks_source": pk_kind,
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * nnfft.h -- C ABI of the GB300 (sm_103a) NNFFT library.
+ *
+ * The library evaluates the NNFFT (nonuniform FFT with nonequispaced spatial
+ * and frequency data, "type 3") of Kircheis, Potts and Tasche,
+ *
+ *     y_j = sum_{k < M1} f_k exp(-2 pi i N v_k x_j),   j < M2,      (eq. (f(xj)))
+ *
+ * for frequency nodes v_k and spatial nodes x_j in [-1/2, 1/2], by Algorithm 2.2
+ * with two sinh-type windows (Example 2.1, Section 4), its adjoint
+ *
+ *     z_k = sum_{j < M2} g_j exp(+2 pi i N v_k x_j),   k < M1,
+ *
+ * and the fast sinc transform of Algorithm 6.1 (Section 6),
+ *
+ *     h_l = sum_{k < L1} c_k sinc(N pi (b_l - a_k)),   l < L2.      (eq. (discretesinctransf))
+ *
+ * Conventions shared by every entry point:
+ *   - Index sets are 0-based arrays; outputs are in the caller's order.
+ *   - Complex data is interleaved (re, im) in the plan's real type: float for
+ *     NNFFT_C64, double for NNFFT_C128.  Nodes are always double.
+ *   - Pointers named *_dev are device pointers; *_host are host pointers
+ *     (pinned memory gives full copy bandwidth; pageable memory works).
+ *   - The caller owns every buffer it passes.  A plan owns its tables, its
+ *     sorted copies of the nodes and its work buffers, all in device memory.
+ *   - Every call is asynchronous on the plan's stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) except the *_host calls and
+ *     nnfft_sync, which return after the stream has drained.
+ *   - Errors detectable on the host are returned at once.  Errors found by a
+ *     kernel (a node outside [-1/2, 1/2] or NaN) set a status word in the plan
+ *     that the next nnfft_sync (or *_host call) returns.
+ *   - There is no CPU fallback: without a usable CUDA device the calls fail
+ *     with NNFFT_ECUDA.
+ *   - A plan must not be used from two host threads at once.
+ */
+#ifndef NNFFT_GB300_H
+#define NNFFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnfft_plan_s *nnfft_plan_t;
+
+/* coefficient / output type; nodes are always float64 */
+typedef enum { NNFFT_C64 = 0, NNFFT_C128 = 1 } nnfft_dtype;
+
+/* status codes */
+enum {
+    NNFFT_OK = 0,
+    NNFFT_EINVAL = 1,   /* invalid argument or parameter combination              */
+    NNFFT_ERANGE = 2,   /* a node outside [-1/2, 1/2] or NaN (reported by kernels) */
+    NNFFT_ENOMEM = 3,   /* device or host allocation failed                      */
+    NNFFT_ECUDA = 4,    /* CUDA runtime error (no device, launch failure, ...)   */
+    NNFFT_ETIMEOUT = 5, /* a bounded device-side wait gave up                    */
+    NNFFT_ESTATE = 6    /* call out of order (e.g. exec before set_nodes)        */
+};
+
+/* Parameters a plan derived from its arguments (Section 2 and Section 4). */
+typedef struct {
+    int64_t N, Nstar, N1, K1, N2;   /* N* = N + ceil(2 m1/sigma1); N1 = sigma1 N* rounded up to
+                                       even; K1 = N1 + 2 m1 (= a N1, eq. (consta)); N2 = sigma2 K1
+                                       rounded up to an even 2^a 3^b 5^c 7^d                  */
+    int64_t M1, M2;
+    int m1, m2;
+    double sigma1, sigma2;           /* effective oversampling N1/N*, N2/K1                   */
+    double beta1, beta2;             /* 2 pi m_j (1 - 1/(2 sigma_j))                          */
+    int dtype;                       /* nnfft_dtype                                           */
+    int D1, D2;                      /* Chebyshev degrees + 1 of the piecewise window fits    */
+    double fit_err1, fit_err2;       /* max abs error of those fits on [-1,1] (window max 1)  */
+    int64_t ncell1, ncell2;          /* node cells (bins) of the v side and the x side        */
+    int64_t fft_n1, fft_n2;          /* N2 = fft_n1 * fft_n2 (four-step split)                */
+} nnfft_info;
+
+/*
+ * nnfft_params: derive the plan parameters without touching a GPU.
+ * Same rules and validation as nnfft_plan (EINVAL on: N < 1, M1 < 0, M2 < 0,
+ * sigma_j <= 1 or > 16, m_j < 2 or m_j > 16, M_j > 2^30, N2 > 2^20, or
+ * 2 m2 > (1 - 1/sigma1) N2,
+ * the condition of step 4 of Algorithm 2.2).  fit_err*, D* are filled too.
+ */
+int nnfft_params(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2,
+                 int m1, int m2, nnfft_dtype dtype, nnfft_info *out);
+
+/*
+ * nnfft_plan: create a plan for M1 frequency nodes, M2 spatial nodes,
+ * bandwidth N (Algorithm 2.2, input line), oversampling sigma1, sigma2 > 1,
+ * truncation m1, m2 in [2, 16] and dtype.  Allocates the plan's device
+ * tables and work buffers (O(M1 + M2 + N2) bytes) and uploads the window
+ * tables.  stream: cudaStream_t (or NULL) used by every later call.
+ * On success *out receives the plan; on failure *out is set to NULL.
+ */
+int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2,
+               double sigma1, double sigma2, int m1, int m2, nnfft_dtype dtype,
+               void *stream);
+
+/* nnfft_plan_info: copy the derived parameters of a plan. */
+int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
+
+/*
+ * nnfft_set_nodes: step 0 of Algorithm 2.2 for a new node set.
+ * v_dev: M1 doubles, x_dev: M2 doubles, both device pointers, values in
+ * [-1/2, 1/2].  Either may be NULL to keep that side's previous nodes.
+ * The nodes are rescaled (v* = N v / N*, after eq. (condvk)), binned by grid
+ * cell and sorted (stable), and the plan keeps the sorted local coordinates
+ * and the permutation; the caller's arrays are not referenced afterwards.
+ * Out-of-range or NaN nodes set NNFFT_ERANGE in the status word.
+ */
+int nnfft_set_nodes(nnfft_plan_t p, const double *v_dev, const double *x_dev);
+
+/*
+ * nnfft_exec: the NNFFT, y_j ~ sum_k f_k exp(-2 pi i N v_k x_j)
+ * (Algorithm 2.2 steps 1-4 and the output division).
+ * f_dev: M1 complex values, y_dev: M2 complex values (device, plan dtype).
+ */
+int nnfft_exec(nnfft_plan_t p, const void *f_dev, void *y_dev);
+
+/*
+ * nnfft_adjoint: z_k ~ sum_j g_j exp(+2 pi i N v_k x_j), computed as the exact
+ * transpose of the fast forward map (every step of Algorithm 2.2 reversed).
+ * g_dev: M2 complex values, z_dev: M1 complex values (device, plan dtype).
+ */
+int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev);
+
+/*
+ * Host-buffer variants of set_nodes / exec / adjoint.  Same arguments as above
+ * but host pointers: the call copies the inputs into plan-owned device
+ * staging buffers, runs the transform, copies the result back and waits for
+ * the stream.  Returns any pending kernel status like nnfft_sync.
+ */
+int nnfft_set_nodes_host(nnfft_plan_t p, const double *v_host, const double *x_host);
+int nnfft_exec_host(nnfft_plan_t p, const void *f_host, void *y_host);
+int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host);
+
+/* nnfft_sync: wait for the plan's stream; return and clear the kernel status. */
+int nnfft_sync(nnfft_plan_t p);
+
+/* nnfft_destroy: free the plan (waits for its stream first).  NULL is a no-op. */
+int nnfft_destroy(nnfft_plan_t p);
+
+/*
+ * sinc_exec: fast sinc transform, Algorithm 6.1 with an n = 2N node
+ * Gauss-Legendre rule on [-1/2, 1/2] in place of Clenshaw-Curtis:
+ *   g_j     = sum_k c_k exp(+2 pi i N tau_j a_k)        (NNFFT #1, nodes a -> -tau)
+ *   alpha_j = w_j g_j                                    (step 2)
+ *   h_l     = sum_j alpha_j exp(-2 pi i N tau_j b_l)    (NNFFT #2, nodes tau -> b)
+ * which approximates h_l = sum_k c_k sinc(N pi (b_l - a_k)).
+ * Both NNFFTs use sigma1 = sigma2 = 2 and m1 = m2 = m.
+ * a_dev: L1 doubles, b_dev: L2 doubles in [-1/2, 1/2] (device).
+ * c_dev / h_dev: L1 / L2 values in the dtype's real type when is_complex = 0
+ * (h is then the real part; it is real up to rounding for real c because the
+ * rule is symmetric), or interleaved complex when is_complex = 1.
+ * The call keeps an internal plan cache keyed by (N, L1, L2, m, dtype, stream);
+ * stream as in nnfft_plan.  Asynchronous like nnfft_exec; call sinc_sync to wait
+ * and to collect a kernel status.
+ */
+int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype,
+              const double *a_dev, const void *c_dev, const double *b_dev, void *h_dev,
+              int is_complex, void *stream);
+
+/* sinc_sync: wait for `stream` and return/clear the status of the cached sinc plans on it. */
+int sinc_sync(void *stream);
+
+/* sinc_release: free every cached sinc plan (all streams). */
+int sinc_release(void);
+
+/*
+ * nnfft_gauss_legendre: the library's n-point Gauss-Legendre rule on [-1/2, 1/2]
+ * (increasing nodes tau, weights w summing to 1), as used by sinc_exec.  Host
+ * arrays of length n.  No GPU needed.
+ */
+int nnfft_gauss_legendre(int64_t n, double *tau_host, double *w_host);
+
+/*
+ * Per-stage device timing (tracing).  When enabled, every stage of set_nodes /
+ * exec / adjoint is bracketed by CUDA events recorded on the plan stream; the
+ * elapsed times accumulate until nnfft_timing_read (which waits for the stream).
+ * Stage ids (index into ms[] / count[]):
+ *   0 v-side node binning + sort     1 x-side node binning + sort
+ *   2 forward cell moments (v)       3 forward spread convolution
+ *   4 forward FFT (both passes)      5 forward gather convolution
+ *   6 forward point evaluation (x)   7 adjoint cell moments (x)
+ *   8 adjoint spread convolution     9 adjoint FFT
+ *  10 adjoint gather convolution    11 adjoint point evaluation (v)
+ */
+#define NNFFT_NSTAGES 12
+typedef struct {
+    double ms[16];      /* accumulated milliseconds per stage */
+    int64_t count[16];  /* number of timed executions per stage */
+} nnfft_timing;
+int nnfft_timing_enable(nnfft_plan_t p, int enable);
+int nnfft_timing_read(nnfft_plan_t p, nnfft_timing *out, int reset);
+
+/* nnfft_launch_count: number of kernels this library has launched in the process. */
+int64_t nnfft_launch_count(void);
+
+/* nnfft_last_error: thread-local message describing the last non-OK status. */
+const char *nnfft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NNFFT_GB300_H */

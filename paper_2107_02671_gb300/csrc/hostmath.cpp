@@ -1,0 +1,193 @@
+// hostmath.cpp -- see hostmath.h.
+#include "hostmath.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+namespace nnfft {
+namespace hm {
+
+double omega_sinh(double x, double beta) {
+    if (!(std::fabs(x) < 1.0)) return 0.0;
+    const double s = std::sqrt(1.0 - x * x);
+    // sinh(beta s)/sinh(beta) written without overflow
+    return std::exp(beta * (s - 1.0)) * (-std::expm1(-2.0 * beta * s)) /
+           (-std::expm1(-2.0 * beta));
+}
+
+double omega_sinh_hat(double v, double beta) {
+    const double pref = PI * beta / std::sinh(beta);
+    const double q = beta * beta - 4.0 * PI * PI * v * v;
+    if (q > 0.0) {
+        // (1/2) sum_k q^k / (4^k k! (k+1)!), positive terms, compensated sum
+        double term = 1.0, sum = 1.0, comp = 0.0;
+        for (int k = 0; k < 4000; ++k) {
+            term *= q / (4.0 * (k + 1) * (k + 2));
+            const double t = sum + term;
+            comp += (sum - t) + term;
+            sum = t;
+            if (term < 1e-18 * sum) break;
+        }
+        return pref * 0.5 * (sum + comp);
+    }
+    if (q == 0.0) return 0.5 * pref;
+    const double r = std::sqrt(-q);
+    return pref * ::j1(r) / r;
+}
+
+static bool smooth7(int64_t n) {
+    if (n <= 0) return false;
+    const int64_t p[4] = {2, 3, 5, 7};
+    for (int i = 0; i < 4; ++i)
+        while (n % p[i] == 0) n /= p[i];
+    return n == 1;
+}
+
+const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *o) {
+    if (N < 1) return "N must be >= 1";
+    if (!(sigma1 > 1.0) || !(sigma2 > 1.0)) return "sigma1 and sigma2 must be > 1";
+    if (!(sigma1 <= 16.0) || !(sigma2 <= 16.0)) return "sigma1 and sigma2 must be <= 16";
+    if (m1 < 2 || m2 < 2) return "m1 and m2 must be >= 2";
+    if (m1 > 16 || m2 > 16) return "m1 and m2 must be <= 16";
+    if (N > (int64_t(1) << 28)) return "N too large";
+    o->N = N;
+    o->m1 = m1;
+    o->m2 = m2;
+    // N* = N + ceil(2 m1 / sigma1): frequencies v in [-1/2,1/2] become v* = N v / N*
+    // inside [-1/(2a), 1/(2a)] (rescaling after eq. (condvk)).
+    o->Nstar = N + (int64_t)std::ceil(2.0 * m1 / sigma1 - 1e-12);
+    int64_t n1 = (int64_t)std::ceil(sigma1 * (double)o->Nstar - 1e-9);
+    if (n1 % 2) ++n1;                                   // N1 in 2N
+    o->N1 = n1;
+    o->K1 = n1 + 2 * m1;                                // a N1 = N1 + 2 m1, eq. (consta)
+    int64_t n2 = (int64_t)std::ceil(sigma2 * (double)o->K1 - 1e-9);
+    if (n2 % 2) ++n2;
+    while (!smooth7(n2)) n2 += 2;                       // even 2^a 3^b 5^c 7^d
+    o->N2 = n2;
+    o->sigma1 = (double)o->N1 / (double)o->Nstar;
+    o->sigma2 = (double)o->N2 / (double)o->K1;
+    o->beta1 = 2.0 * PI * m1 * (1.0 - 1.0 / (2.0 * o->sigma1));
+    o->beta2 = 2.0 * PI * m2 * (1.0 - 1.0 / (2.0 * o->sigma2));
+    if (o->N2 > (int64_t(1) << 20)) return "N2 exceeds 2^20 (N too large for the grid FFT)";
+    if ((double)(2 * m2) > (1.0 - 1.0 / o->sigma1) * (double)o->N2)
+        return "step 4 of Algorithm 2.2 needs 2 m2 <= (1 - 1/sigma1) N2";
+    return nullptr;
+}
+
+double window_error_term(int m, double sigma) {
+    return (24.0 * std::pow((double)m, 1.5) + 10.0) *
+           std::exp(-2.0 * PI * m * std::sqrt(1.0 - 1.0 / sigma));
+}
+
+double cheb_eval(const double *c, int n, double y) {
+    // Clenshaw recurrence
+    double b1 = 0.0, b2 = 0.0;
+    for (int d = n - 1; d >= 1; --d) {
+        const double b0 = 2.0 * y * b1 - b2 + c[d];
+        b2 = b1;
+        b1 = b0;
+    }
+    return y * b1 - b2 + c[0];
+}
+
+double fit_taps(int m, double beta, int D, std::vector<double> &coef) {
+    coef.assign((size_t)2 * m * D, 0.0);
+    double err = 0.0;
+    constexpr int G = 241;
+    for (int t = 0; t < 2 * m; ++t) {
+        auto f = [&](double y) {
+            const double z = 0.5 * (y + 1.0);
+            return omega_sinh((t - m + 1 - z) / m, beta);
+        };
+        double *c = coef.data() + (size_t)t * D;
+        cheb_interp(f, D, c);
+        for (int g = 0; g < G; ++g) {
+            const double y = -1.0 + 2.0 * g / (G - 1);
+            err = std::fmax(err, std::fabs(cheb_eval(c, D, y) - f(y)));
+        }
+    }
+    return err;
+}
+
+int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
+                  std::vector<double> &coef) {
+    static const int cand[] = {8, 10, 12, 14, 16, 20};
+    std::vector<double> tmp;
+    const double floor_err = fit_taps(m, beta, 24, tmp);
+    const double e1 = window_error_term(m, sigma);
+    const double target = fp64 ? 1e-3 * e1 : std::fmax(1e-2 * e1, 5e-8);
+    const double accept = std::fmax(target, 1.5 * floor_err);
+    for (int D : cand) {
+        const double err = fit_taps(m, beta, D, coef);
+        if (err <= accept || D == 20) {
+            *fit_err = err;
+            return D;
+        }
+    }
+    return 20;
+}
+
+void gauss_legendre(int64_t n, double *tau, double *w) {
+    for (int64_t i = 0; i < (n + 1) / 2; ++i) {
+        double t = std::cos(PI * ((double)i + 0.75) / ((double)n + 0.5));
+        double pn = 0.0, pm = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int64_t k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
+                p0 = p1;
+                p1 = p2;
+            }
+            pn = n == 1 ? t : p1;
+            pm = n == 1 ? 1.0 : p0;
+            const double dp = (double)n * (t * pn - pm) / (t * t - 1.0);
+            const double dt = pn / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int64_t k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
+            p0 = p1;
+            p1 = p2;
+        }
+        pn = n == 1 ? t : p1;
+        pm = n == 1 ? 1.0 : p0;
+        const double dp = (double)n * (t * pn - pm) / (t * t - 1.0);
+        const double wt = 1.0 / ((1.0 - t * t) * dp * dp);   // 2/(...) halved for [-1/2,1/2]
+        tau[n - 1 - i] = 0.5 * t;
+        tau[i] = -0.5 * t;
+        w[n - 1 - i] = wt;
+        w[i] = wt;
+    }
+    if (n % 2 == 1) tau[n / 2] = 0.0;
+}
+
+bool split_fft(int64_t N2, int maxf, int *n1, int *n2) {
+    int best1 = 0;
+    for (int64_t a = 1; a <= maxf; ++a) {
+        if (N2 % a) continue;
+        const int64_t b = N2 / a;
+        if (b > maxf) continue;
+        if (!smooth7(a) || !smooth7(b)) continue;
+        if (best1 == 0 || std::llabs(a - b) < std::llabs(best1 - N2 / best1)) best1 = (int)a;
+    }
+    if (best1 == 0) return false;
+    *n1 = best1;
+    *n2 = (int)(N2 / best1);
+    return true;
+}
+
+int radices(int n, int *r, int maxr) {
+    int k = 0;
+    while (n % 4 == 0 && k < maxr) { r[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < maxr) { r[k++] = 2; n /= 2; }
+    while (n % 3 == 0 && k < maxr) { r[k++] = 3; n /= 3; }
+    while (n % 5 == 0 && k < maxr) { r[k++] = 5; n /= 5; }
+    while (n % 7 == 0 && k < maxr) { r[k++] = 7; n /= 7; }
+    return n == 1 ? k : -1;
+}
+
+}  // namespace hm
+}  // namespace nnfft

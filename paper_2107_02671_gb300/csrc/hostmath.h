@@ -1,0 +1,63 @@
+// hostmath.h -- host-side numerics of the plan: parameter rules, the sinh window
+// and its Fourier transform, Chebyshev fits of the window taps and of 1/phihat1,
+// the Gauss-Legendre rule and the FFT factorisation.  No GPU calls.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+namespace nnfft {
+namespace hm {
+
+constexpr double PI = 3.141592653589793238462643383279502884;
+
+// Sinh-type window of Example 2.1 / Section 4 on [-1, 1] (0 outside).
+double omega_sinh(double x, double beta);
+// Its Fourier transform, eq. (hatomegasinh), for |v| <= beta/(2 pi) via the I1 power
+// series (all terms positive); beyond the branch point via J1.
+double omega_sinh_hat(double v, double beta);
+
+struct Derived {
+    int64_t N, Nstar, N1, K1, N2;
+    int m1, m2;
+    double sigma1, sigma2, beta1, beta2;
+};
+// Section 2 / Section 4 parameter rules; returns an error message or nullptr.
+const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *out);
+
+// Theorem 4.1's first term (24 m^{3/2} + 10) exp(-2 pi m sqrt(1 - 1/sigma)).
+double window_error_term(int m, double sigma);
+
+// Chebyshev interpolation of f at n first-kind points on [-1, 1]:
+// coefficients c[0..n-1] with f(y) ~ sum_d c[d] T_d(y).
+template <class F> void cheb_interp(const F &f, int n, double *c) {
+    const double pi = 3.141592653589793238462643383279502884;
+    std::vector<double> fy(n);
+    for (int i = 0; i < n; ++i) fy[i] = f(std::cos(pi * (i + 0.5) / n));
+    for (int d = 0; d < n; ++d) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += fy[i] * std::cos(pi * d * (i + 0.5) / n);
+        c[d] = s * 2.0 / n;
+    }
+    c[0] *= 0.5;
+}
+double cheb_eval(const double *c, int n, double y);
+
+// Fit the 2m tap functions w_t(y) = omega((t - m + 1 - (y+1)/2)/m) with D
+// coefficients each (row-major [t][d]); returns the max abs error on a test grid.
+double fit_taps(int m, double beta, int D, std::vector<double> &coef);
+// Pick the coefficient count D for a window: the smallest supported D whose fit
+// error is below the target for the dtype (or at the window's floor).
+int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
+                  std::vector<double> &coef);
+
+// n-point Gauss-Legendre rule on [-1/2, 1/2] (Newton on the Legendre recurrence).
+void gauss_legendre(int64_t n, double *tau, double *w);
+
+// N2 = n1 * n2 with n1, n2 <= maxf and 7-smooth, as square as possible; radix lists.
+bool split_fft(int64_t N2, int maxf, int *n1, int *n2);
+int radices(int n, int *r, int maxr);
+
+}  // namespace hm
+}  // namespace nnfft

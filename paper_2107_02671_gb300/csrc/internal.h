@@ -1,0 +1,118 @@
+// internal.h -- declarations shared by the translation units of the NNFFT
+// library (kernels + host orchestration).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <atomic>
+#include <cstdint>
+#include <type_traits>
+
+#include "nnfft.h"
+
+namespace nnfft {
+
+// Coefficients of the per-cell Chebyshev fit of 1/phihat1(N* x) on the x side.
+constexpr int NR = 8;
+// A work item is a run of at most ITEM_CAP sorted points of one cell.
+constexpr int ITEM_CAP = 256;
+// Radix sort: 8-bit digits, tiles of SORT_TILE keys per block (8 warps x 512).
+constexpr int SORT_TILE = 4096;
+constexpr int SORT_THREADS = 256;
+// Largest supported FFT factor (one CTA transforms a column in shared memory).
+constexpr int FFT_MAX_FACTOR = 1024;
+constexpr int FFT_MAX_STAGES = 12;
+
+// Kernel status bits (OR-ed into the plan's device status word).
+constexpr int STATUS_RANGE = 1;      // node outside [-1/2, 1/2] or NaN
+constexpr int STATUS_INTERNAL = 2;   // inconsistent cell assignment (should not happen)
+
+// Kernels launched by this library (nnfft_launch_count); bumped by every launch wrapper.
+void count_launches(int n);
+long long launches_so_far();
+
+template <typename Real> struct Cplx;
+template <> struct Cplx<double> { using T = double2; };
+template <> struct Cplx<float> { using T = float2; };
+template <typename Real> using C2 = typename Cplx<Real>::T;
+
+// Everything a spread / gather kernel needs to know about one node side.
+//   v side: frequency nodes v_k, window phi1 (m1, beta1), grid I_{K1}
+//   x side: spatial nodes x_j,   window phi2 (m2, beta2), grid I_{N2}
+// A point with u = node * uscale lies in cell c = floor(u) (c_lo <= c < c_lo + ncell)
+// and has local coordinate y = 2 (u - c) - 1 in [-1, 1).  Its 2m taps hit grid
+// positions p = c - m + 1 + t, t = 0..2m-1, with weights
+//   w_t(y) = omega((t - m + 1 - z)/m), z = (y + 1)/2,  ~  sum_d coef[t*D + d] T_d(y).
+template <typename Real> struct SideK {
+    int m, D, ncell;
+    long long c_lo;
+    const Real *coef;      // [2m][D] Chebyshev coefficients of the taps
+    const Real *rfit;      // [ncell][NR] or nullptr (x side: 1/phihat1 per cell)
+    const int *perm;       // [M] sorted position -> caller index
+    const Real *ys;        // [M] sorted local coordinates
+    const int *item_off;   // [ncell + 1] first work item of each cell
+    const int *item_cell;  // [max_items]
+    const int *item_pb;    // [max_items] first sorted point of the item
+    const int *item_pe;    // [max_items] one past its last point
+    const int *nitems;     // device scalar: number of items
+    int max_items;
+};
+
+struct FftPlanDev {
+    int N2, n1, n2;
+    int nr1, nr2;
+    int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
+    const void *tw1, *tw2, *twN;   // C2<Real>: exp(-2 pi i k / n) for n = n1, n2, N2
+};
+
+// ---- kern_nodes.cu ----------------------------------------------------------------
+cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,
+                             int ncell, uint32_t *keys, int *vals, int *status,
+                             cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) by the low key_bits bits.  Uses the
+// *_alt buffers and hist (>= 256 * ceil(n / SORT_TILE) + 1 ints) as scratch.
+// On return *keys_sorted / *vals_sorted point at whichever buffers hold the result.
+cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                             int *hist, int n, int key_bits, cudaStream_t s,
+                             uint32_t **keys_sorted, int **vals_sorted);
+size_t radix_sort_hist_len(int n);
+cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
+                                cudaStream_t s);
+cudaError_t launch_build_items(const int *cell_off, int ncell, int *item_cnt, int *item_off,
+                               int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                               cudaStream_t s);
+template <typename Real>
+cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
+                                 const uint32_t *keys_sorted, int n, double uscale,
+                                 long long c_lo, Real *ys, int *status, cudaStream_t s);
+cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
+
+// ---- kern_spread.cu ---------------------------------------------------------------
+template <typename Real>
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *scale,
+                               long long scale_off, long long scale_len, int N2, void *out,
+                               cudaStream_t s);
+template <typename Real>
+cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
+                               long long scale_off, long long scale_len, int N2, void *Q,
+                               cudaStream_t s);
+template <typename Real>
+cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s);
+bool supported_degree(int D);
+
+// ---- kern_fft.cu ------------------------------------------------------------------
+template <typename Real>
+cudaError_t launch_fft(const FftPlanDev &F, const void *in, void *tmp, void *out, int sign,
+                       cudaStream_t s);
+
+// ---- kern_misc.cu -----------------------------------------------------------------
+template <typename Real>
+cudaError_t launch_real_to_complex(const Real *in, int n, void *out, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_scale_by_weights(void *vals, const double *w, int n, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_t s);
+cudaError_t launch_negate(const double *in, int n, double *out, cudaStream_t s);
+
+}  // namespace nnfft

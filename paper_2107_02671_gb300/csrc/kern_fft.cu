@@ -1,0 +1,183 @@
+// kern_fft.cu -- step 3 of Algorithm 2.2: the length-N2 FFT on the oversampled
+// grid, h_s = sum_l ghat_l exp(sign 2 pi i l s / N2), written as a four-step
+// transform N2 = n1 * n2 with index maps n = n2 a + b, k = c + n1 d:
+//   pass 1 (one CTA per column b):  Z[b][c] = w_N2^{b c} * sum_a X[n2 a + b] w_n1^{a c}
+//   pass 2 (one CTA per column c):  Y[c + n1 d] = sum_b Z[b][c] w_n2^{b d}
+// Each column transform is a Stockham autosort FFT in shared memory with radices
+// 2, 3, 4, 5, 7 (and 8), so no bit reversal is needed.  Twiddles come from
+// host-computed tables exp(-2 pi i k / n); sign = +1 uses their conjugates.
+// The whole grid (N2 <= 2^20 points) stays resident in L2 between the passes.
+#include "internal.h"
+
+namespace nnfft {
+
+namespace {
+
+template <typename Real>
+__device__ __forceinline__ C2<Real> cadd(C2<Real> a, C2<Real> b) {
+    C2<Real> r; r.x = a.x + b.x; r.y = a.y + b.y; return r;
+}
+template <typename Real>
+__device__ __forceinline__ C2<Real> csub(C2<Real> a, C2<Real> b) {
+    C2<Real> r; r.x = a.x - b.x; r.y = a.y - b.y; return r;
+}
+template <typename Real>
+__device__ __forceinline__ C2<Real> cmul(C2<Real> a, C2<Real> b) {
+    C2<Real> r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// twiddle exp(sign 2 pi i idx / n) from the table of exp(-2 pi i idx / n)
+template <typename Real>
+__device__ __forceinline__ C2<Real> twid(const C2<Real> *tw, int idx, int sign) {
+    C2<Real> w = tw[idx];
+    if (sign > 0) w.y = -w.y;
+    return w;
+}
+// multiply by exp(sign * i pi/2) = i*sign
+template <typename Real>
+__device__ __forceinline__ C2<Real> mul_isign(C2<Real> a, int sign) {
+    C2<Real> r;
+    r.x = sign > 0 ? -a.y : a.y;
+    r.y = sign > 0 ? a.x : -a.x;
+    return r;
+}
+
+// One Stockham stage of radix R over a length-n sequence held in shared memory:
+// butterfly j (0 <= j < n/R), k = j mod L,
+//   a_q = src[j + q n/R] * w_{L R}^{q k},  b_p = sum_q a_q w_R^{p q},
+//   dst[(j - k) R + k + p L] = b_p,
+// where L is the product of the radices of the earlier stages.
+template <typename Real, int R>
+__device__ __forceinline__ void stage(const C2<Real> *src, C2<Real> *dst, int n, int L,
+                                      const C2<Real> *tw, int sign) {
+    const int nr = n / R;
+    const int tstep = n / (L * R);
+    for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        const int k = j % L;
+        C2<Real> a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            a[q] = src[j + q * nr];
+            if (q > 0 && k > 0) a[q] = cmul<Real>(a[q], twid<Real>(tw, q * k * tstep, sign));
+        }
+        C2<Real> b[R];
+        if (R == 2) {
+            b[0] = cadd<Real>(a[0], a[1]);
+            b[1] = csub<Real>(a[0], a[1]);
+        } else if (R == 4) {
+            const C2<Real> s02 = cadd<Real>(a[0], a[2]), d02 = csub<Real>(a[0], a[2]);
+            const C2<Real> s13 = cadd<Real>(a[1], a[3]);
+            const C2<Real> d13 = mul_isign<Real>(csub<Real>(a[1], a[3]), sign);
+            b[0] = cadd<Real>(s02, s13);
+            b[1] = cadd<Real>(d02, d13);
+            b[2] = csub<Real>(s02, s13);
+            b[3] = csub<Real>(d02, d13);
+        } else {
+#pragma unroll
+            for (int p = 0; p < R; ++p) {
+                C2<Real> acc = a[0];
+#pragma unroll
+                for (int q = 1; q < R; ++q)
+                    acc = cadd<Real>(acc, cmul<Real>(a[q], twid<Real>(tw, ((p * q) % R) * nr, sign)));
+                b[p] = acc;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < R; ++p) dst[(j - k) * R + k + p * L] = b[p];
+    }
+}
+
+// Stockham FFT of length n (= product of radices) in shared memory; returns the
+// buffer that holds the natural-order result (A or B).
+template <typename Real>
+__device__ C2<Real> *stockham(C2<Real> *A, C2<Real> *B, int n, const int *radices, int nr,
+                              const C2<Real> *tw, int sign) {
+    int L = 1;
+    C2<Real> *src = A, *dst = B;
+    for (int s = 0; s < nr; ++s) {
+        const int R = radices[s];
+        switch (R) {
+            case 2: stage<Real, 2>(src, dst, n, L, tw, sign); break;
+            case 3: stage<Real, 3>(src, dst, n, L, tw, sign); break;
+            case 4: stage<Real, 4>(src, dst, n, L, tw, sign); break;
+            case 5: stage<Real, 5>(src, dst, n, L, tw, sign); break;
+            case 7: stage<Real, 7>(src, dst, n, L, tw, sign); break;
+            case 8: stage<Real, 8>(src, dst, n, L, tw, sign); break;
+            default: break;
+        }
+        __syncthreads();
+        L *= R;
+        C2<Real> *t = src; src = dst; dst = t;
+    }
+    return src;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_fft_pass1(const C2<Real> *__restrict__ X, C2<Real> *__restrict__ Z, FftPlanDev F, int sign) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = F.n1;
+    C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
+    C2<Real> *B = A + n;
+    C2<Real> *tw = B + n;
+    const C2<Real> *tw1 = static_cast<const C2<Real> *>(F.tw1);
+    const C2<Real> *twN = static_cast<const C2<Real> *>(F.twN);
+    const int b = blockIdx.x;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        A[a] = X[(long long)F.n2 * a + b];
+        tw[a] = tw1[a];
+    }
+    __syncthreads();
+    const C2<Real> *res = stockham<Real>(A, B, n, F.r1, F.nr1, tw, sign);
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        Z[(long long)b * n + c] = cmul<Real>(res[c], twid<Real>(twN, b * c, sign));
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_fft_pass2(const C2<Real> *__restrict__ Z, C2<Real> *__restrict__ Y, FftPlanDev F, int sign) {
+    extern __shared__ unsigned char smem_raw[];
+    const int n = F.n2;
+    C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
+    C2<Real> *B = A + n;
+    C2<Real> *tw = B + n;
+    const C2<Real> *tw2 = static_cast<const C2<Real> *>(F.tw2);
+    const int c = blockIdx.x;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        A[b] = Z[(long long)b * F.n1 + c];
+        tw[b] = tw2[b];
+    }
+    __syncthreads();
+    const C2<Real> *res = stockham<Real>(A, B, n, F.r2, F.nr2, tw, sign);
+    for (int d = threadIdx.x; d < n; d += blockDim.x) Y[c + (long long)F.n1 * d] = res[d];
+}
+
+}  // namespace
+
+template <typename Real>
+cudaError_t launch_fft(const FftPlanDev &F, const void *in, void *tmp, void *out, int sign,
+                       cudaStream_t s) {
+    const size_t sm1 = 3 * sizeof(C2<Real>) * F.n1;
+    const size_t sm2 = 3 * sizeof(C2<Real>) * F.n2;
+    if (sm1 > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_pass1<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm1);
+    if (sm2 > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_pass2<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm2);
+    k_fft_pass1<Real><<<F.n2, 256, sm1, s>>>(static_cast<const C2<Real> *>(in),
+                                             static_cast<C2<Real> *>(tmp), F, sign);
+    k_fft_pass2<Real><<<F.n1, 256, sm2, s>>>(static_cast<const C2<Real> *>(tmp),
+                                             static_cast<C2<Real> *>(out), F, sign);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fft<double>(const FftPlanDev &, const void *, void *, void *, int,
+                                        cudaStream_t);
+template cudaError_t launch_fft<float>(const FftPlanDev &, const void *, void *, void *, int,
+                                       cudaStream_t);
+
+}  // namespace nnfft

@@ -1,0 +1,289 @@
+// kern_nodes.cu -- step 0 of Algorithm 2.2 for one node side: bin every node by
+// the grid cell it falls in, sort the nodes by cell (stable LSD radix sort with
+// 8-bit digits), and build the per-cell offsets and the work items that the
+// spread / gather kernels walk.  Deterministic: no order depends on timing.
+#include "internal.h"
+
+namespace nnfft {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Cell index of a node: c = floor(node * uscale) - c_lo.  The same expression is
+// used by k_sorted_coords so both kernels agree on every cell boundary.
+__device__ __forceinline__ double node_u(double x, double uscale) { return x * uscale; }
+
+__global__ void k_node_keys(const double *__restrict__ nodes, int n, double uscale,
+                            long long c_lo, int ncell, uint32_t *__restrict__ keys,
+                            int *__restrict__ vals, int *status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = nodes[i];
+    long long ic = 0;
+    if (!(x >= -0.5 && x <= 0.5)) {          // also catches NaN
+        atomicOr(status, STATUS_RANGE);
+    } else {
+        double u = node_u(x, uscale);
+        ic = (long long)floor(u) - c_lo;
+        if (ic < 0 || ic >= ncell) {
+            atomicOr(status, STATUS_INTERNAL);
+            ic = ic < 0 ? 0 : ncell - 1;
+        }
+    }
+    keys[i] = (uint32_t)ic;
+    vals[i] = i;
+}
+
+// ---- radix sort ------------------------------------------------------------------
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
+               int *__restrict__ hist) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    long long base = (long long)blockIdx.x * SORT_TILE;
+    for (int i = threadIdx.x; i < SORT_TILE; i += SORT_THREADS) {
+        long long idx = base + i;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter.  Warp w of a block owns 512 consecutive keys of the tile and
+// visits them in 16 rounds of 32 in index order; within a round lanes with the
+// same digit are ranked by lane (match_any), across rounds by a per-warp digit
+// counter, and across warps by an exclusive scan of those counters.  So keys
+// with equal digits keep their input order.
+__global__ void __launch_bounds__(SORT_THREADS)
+k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+               uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
+               int nblocks, const int *__restrict__ hist_scanned) {
+    constexpr int WARPS = SORT_THREADS / 32;
+    constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 16
+    __shared__ int cnt[WARPS][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    const long long base = (long long)blockIdx.x * SORT_TILE + (long long)w * (32 * ROUNDS);
+    uint32_t key[ROUNDS];
+    int val[ROUNDS], rank[ROUNDS];
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        long long idx = base + r * 32 + lane;
+        bool valid = idx < n;
+        key[r] = valid ? kin[idx] : 0u;
+        val[r] = valid ? vin[idx] : 0;
+        unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int before = valid ? cnt[w][d] : 0;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) cnt[w][d] += __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {   // digit threadIdx.x: exclusive scan over warps plus the block's global base
+        int d = threadIdx.x;
+        int run = hist_scanned[(long long)d * nblocks + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < WARPS; ++ww) {
+            int t = cnt[ww][d];
+            cnt[ww][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        long long idx = base + r * 32 + lane;
+        if (idx < n) {
+            unsigned d = (key[r] >> shift) & 255u;
+            int pos = cnt[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+// Single-block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total.
+// in and out may alias.
+__global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out, int n) {
+    __shared__ int warp_tot[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int chunk = (n + 1023) / 1024;
+    const long long lo = (long long)tid * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    int s = 0;
+    for (long long i = lo; i < hi; ++i) s += in[i];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int t = warp_tot[lane];
+        int ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += u;
+        }
+        warp_tot[lane] = ti - t;          // exclusive prefix of warp totals
+        if (lane == 31) carry = ti;        // grand total
+    }
+    __syncthreads();
+    int run = warp_tot[w] + incl - s;
+    for (long long i = lo; i < hi; ++i) {
+        int v = in[i];
+        out[i] = run;
+        run += v;
+    }
+    if (tid == 0) out[n] = carry;
+}
+
+__global__ void k_cell_offsets(const uint32_t *__restrict__ keys, int n, int ncell,
+                               int *__restrict__ off) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    int prev = i == 0 ? -1 : (int)keys[i - 1];
+    int cur = i == n ? ncell : (int)keys[i];
+    for (int c = prev + 1; c <= cur; ++c) off[c] = i;
+}
+
+__global__ void k_item_counts(const int *__restrict__ off, int ncell, int *__restrict__ cnt) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int np = off[c + 1] - off[c];
+    cnt[c] = (np + ITEM_CAP - 1) / ITEM_CAP;
+}
+
+__global__ void k_item_fill(const int *__restrict__ off, const int *__restrict__ item_off,
+                            int ncell, int *__restrict__ item_cell, int *__restrict__ item_pb,
+                            int *__restrict__ item_pe, int *__restrict__ nitems) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *nitems = item_off[ncell];
+    if (c >= ncell) return;
+    int i0 = item_off[c], i1 = item_off[c + 1];
+    int p0 = off[c], p1 = off[c + 1];
+    for (int j = 0; j < i1 - i0; ++j) {
+        int pb = p0 + j * ITEM_CAP;
+        int pe = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
+        item_cell[i0 + j] = c;
+        item_pb[i0 + j] = pb;
+        item_pe[i0 + j] = pe;
+    }
+}
+
+template <typename Real>
+__global__ void k_sorted_coords(const double *__restrict__ nodes, const int *__restrict__ perm,
+                                const uint32_t *__restrict__ keys, int n, double uscale,
+                                long long c_lo, Real *__restrict__ ys, int *status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = nodes[perm[i]];
+    double y = 0.0;
+    if (x >= -0.5 && x <= 0.5) {
+        double u = node_u(x, uscale);
+        double c = floor(u);
+        y = 2.0 * (u - c) - 1.0;
+        if ((long long)c - c_lo != (long long)keys[i]) atomicOr(status, STATUS_INTERNAL);
+    }
+    ys[i] = (Real)y;
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,
+                             int ncell, uint32_t *keys, int *vals, int *status,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_node_keys<<<cdiv(n, 256), 256, 0, s>>>(nodes, n, uscale, c_lo, ncell, keys, vals, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+size_t radix_sort_hist_len(int n) {
+    long long nb = n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1;
+    return (size_t)(256 * nb + 1);
+}
+
+cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s) {
+    k_scan_exclusive<<<1, 1024, 0, s>>>(in, out, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                             int *hist, int n, int key_bits, cudaStream_t s,
+                             uint32_t **keys_sorted, int **vals_sorted) {
+    uint32_t *ka = keys, *kb = keys_alt;
+    int *va = vals, *vb = vals_alt;
+    if (n > 1) {
+        int nblocks = cdiv(n, SORT_TILE);
+        for (int shift = 0; shift < key_bits; shift += 8) {
+            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist);
+            k_scan_exclusive<<<1, 1024, 0, s>>>(hist, hist, 256 * nblocks);
+            k_sort_scatter<<<nblocks, SORT_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nblocks,
+                                                            hist);
+            count_launches(3);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            uint32_t *tk = ka; ka = kb; kb = tk;
+            int *tv = va; va = vb; vb = tv;
+        }
+    }
+    *keys_sorted = ka;
+    *vals_sorted = va;
+    return cudaSuccess;
+}
+
+cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
+                                cudaStream_t s) {
+    k_cell_offsets<<<cdiv((long long)n + 1, 256), 256, 0, s>>>(keys_sorted, n, ncell, off);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_items(const int *cell_off, int ncell, int *item_cnt, int *item_off,
+                               int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                               cudaStream_t s) {
+    k_item_counts<<<cdiv(ncell, 256), 256, 0, s>>>(cell_off, ncell, item_cnt);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(item_cnt, item_off, ncell);
+    k_item_fill<<<cdiv(ncell, 256), 256, 0, s>>>(cell_off, item_off, ncell, item_cell, item_pb,
+                                                  item_pe, nitems);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
+                                 const uint32_t *keys_sorted, int n, double uscale,
+                                 long long c_lo, Real *ys, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_sorted_coords<Real><<<cdiv(n, 256), 256, 0, s>>>(nodes, perm, keys_sorted, n, uscale,
+                                                       c_lo, ys, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sorted_coords<double>(const double *, const int *,
+                                                  const uint32_t *, int, double, long long,
+                                                  double *, int *, cudaStream_t);
+template cudaError_t launch_sorted_coords<float>(const double *, const int *, const uint32_t *,
+                                                 int, double, long long, float *, int *,
+                                                 cudaStream_t);
+
+}  // namespace nnfft

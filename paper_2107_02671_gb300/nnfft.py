@@ -1,0 +1,299 @@
+"""Thin Python binding of the C ABI in include/nnfft.h.
+
+Argument marshalling only: every step of the transforms runs in the CUDA
+library ``_build/libnnfft_gb300.so``.  PyTorch supplies device memory and the
+stream; tensors are passed by pointer.  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+NNFFT_C64, NNFFT_C128 = 0, 1
+_CODES = {0: "OK", 1: "EINVAL", 2: "ERANGE", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ESTATE"}
+
+
+STAGES = ("nodes_v", "nodes_x", "fwd_moments", "fwd_spread_conv", "fwd_fft", "fwd_gather_conv",
+          "fwd_eval", "adj_moments", "adj_spread_conv", "adj_fft", "adj_gather_conv", "adj_eval")
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("count", ctypes.c_int64 * 16)]
+
+
+class NNFFTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int64), ("Nstar", ctypes.c_int64), ("N1", ctypes.c_int64),
+        ("K1", ctypes.c_int64), ("N2", ctypes.c_int64),
+        ("M1", ctypes.c_int64), ("M2", ctypes.c_int64),
+        ("m1", ctypes.c_int), ("m2", ctypes.c_int),
+        ("sigma1", ctypes.c_double), ("sigma2", ctypes.c_double),
+        ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+        ("dtype", ctypes.c_int), ("D1", ctypes.c_int), ("D2", ctypes.c_int),
+        ("fit_err1", ctypes.c_double), ("fit_err2", ctypes.c_double),
+        ("ncell1", ctypes.c_int64), ("ncell2", ctypes.c_int64),
+        ("fft_n1", ctypes.c_int64), ("fft_n2", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library and declare its signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"NNFFT CUDA library not built: {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, i64, cint, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        P = ctypes.POINTER
+        lib.nnfft_params.argtypes = [i64, i64, i64, dbl, dbl, cint, cint, cint, P(Info)]
+        lib.nnfft_plan.argtypes = [P(vp), i64, i64, i64, dbl, dbl, cint, cint, cint, vp]
+        lib.nnfft_plan_info.argtypes = [vp, P(Info)]
+        lib.nnfft_set_nodes.argtypes = [vp, vp, vp]
+        lib.nnfft_exec.argtypes = [vp, vp, vp]
+        lib.nnfft_adjoint.argtypes = [vp, vp, vp]
+        lib.nnfft_set_nodes_host.argtypes = [vp, vp, vp]
+        lib.nnfft_exec_host.argtypes = [vp, vp, vp]
+        lib.nnfft_adjoint_host.argtypes = [vp, vp, vp]
+        lib.nnfft_sync.argtypes = [vp]
+        lib.nnfft_destroy.argtypes = [vp]
+        lib.sinc_exec.argtypes = [i64, i64, i64, cint, cint, vp, vp, vp, vp, cint, vp]
+        lib.sinc_sync.argtypes = [vp]
+        lib.sinc_release.argtypes = []
+        lib.nnfft_gauss_legendre.argtypes = [i64, vp, vp]
+        lib.nnfft_timing_enable.argtypes = [vp, cint]
+        lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
+        lib.nnfft_launch_count.argtypes = []
+        lib.nnfft_launch_count.restype = i64
+        lib.nnfft_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != 0:
+        msg = _lib.nnfft_last_error().decode(errors="replace")
+        raise NNFFTError(rc, msg)
+
+
+def _dtype_code(dtype):
+    import torch
+    if dtype in (torch.complex128, np.complex128, "complex128", "c128", NNFFT_C128):
+        return NNFFT_C128
+    if dtype in (torch.complex64, np.complex64, "complex64", "c64", NNFFT_C64):
+        return NNFFT_C64
+    raise ValueError(f"unsupported dtype {dtype!r}")
+
+
+def params(N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype="complex128") -> dict:
+    """Derived plan parameters (no GPU needed)."""
+    lib = load_library()
+    info = Info()
+    m2 = m1 if m2 is None else m2
+    _check(lib.nnfft_params(int(N), int(M1), int(M2), float(sigma1), float(sigma2), int(m1),
+                            int(m2), _dtype_code(dtype), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def gauss_legendre(n):
+    """The library's n-point Gauss-Legendre rule on [-1/2, 1/2] (host arrays)."""
+    lib = load_library()
+    tau = np.zeros(int(n)); w = np.zeros(int(n))
+    _check(lib.nnfft_gauss_legendre(int(n), tau.ctypes.data, w.ctypes.data))
+    return tau, w
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(t, dtype, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr() if n > 0 else 0)
+
+
+class Plan:
+    """NNFFT plan (Algorithm 2.2): y = A f with A_jk = exp(-2 pi i N v_k x_j), and A^H.
+
+    dtype torch.complex128 runs the fp64 path, torch.complex64 the fp32 path.
+    Nodes are float64 CUDA tensors in [-1/2, 1/2].
+    """
+
+    def __init__(self, N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype=None,
+                 stream=None):
+        import torch
+        lib = load_library()
+        dtype = torch.complex128 if dtype is None else dtype
+        self.dtype = dtype
+        self.cdtype = torch.complex128 if _dtype_code(dtype) == NNFFT_C128 else torch.complex64
+        self.np_cdtype = np.complex128 if self.cdtype == torch.complex128 else np.complex64
+        self.M1, self.M2, self.N = int(M1), int(M2), int(N)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._h = ctypes.c_void_p()
+        m2 = m1 if m2 is None else m2
+        _check(lib.nnfft_plan(ctypes.byref(self._h), int(N), int(M1), int(M2), float(sigma1),
+                              float(sigma2), int(m1), int(m2), _dtype_code(dtype),
+                              _stream_ptr(self.stream)))
+        self._lib = lib
+
+    @property
+    def info(self) -> dict:
+        info = Info()
+        _check(self._lib.nnfft_plan_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def set_nodes(self, v=None, x=None):
+        import torch
+        pv = _dev_tensor(v, torch.float64, self.M1, "v") if v is not None else None
+        px = _dev_tensor(x, torch.float64, self.M2, "x") if x is not None else None
+        _check(self._lib.nnfft_set_nodes(self._h, pv, px))
+        return self
+
+    def exec(self, f, out=None):
+        import torch
+        pf = _dev_tensor(f, self.cdtype, self.M1, "f")
+        if out is None:
+            out = torch.empty(self.M2, dtype=self.cdtype, device=f.device)
+        po = _dev_tensor(out, self.cdtype, self.M2, "out")
+        _check(self._lib.nnfft_exec(self._h, pf, po))
+        return out
+
+    def adjoint(self, g, out=None):
+        import torch
+        pg = _dev_tensor(g, self.cdtype, self.M2, "g")
+        if out is None:
+            out = torch.empty(self.M1, dtype=self.cdtype, device=g.device)
+        po = _dev_tensor(out, self.cdtype, self.M1, "out")
+        _check(self._lib.nnfft_adjoint(self._h, pg, po))
+        return out
+
+    # host-buffer variants (numpy in, numpy out; copies inside the call)
+    def set_nodes_host(self, v=None, x=None):
+        args = []
+        for arr, n in ((v, self.M1), (x, self.M2)):
+            if arr is None:
+                args.append(None)
+                continue
+            if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.size == n
+                    and arr.flags.c_contiguous):
+                raise TypeError("host nodes must be contiguous float64 numpy arrays of the plan size")
+            args.append(ctypes.c_void_p(arr.ctypes.data))
+        _check(self._lib.nnfft_set_nodes_host(self._h, *args))
+        return self
+
+    def _host_arr(self, arr, n, name):
+        if not (isinstance(arr, np.ndarray) and arr.dtype == self.np_cdtype and arr.size == n
+                and arr.flags.c_contiguous):
+            raise TypeError(f"{name} must be a contiguous {np.dtype(self.np_cdtype)} numpy array of {n}")
+        return ctypes.c_void_p(arr.ctypes.data)
+
+    def exec_host(self, f, out=None):
+        out = np.empty(self.M2, dtype=self.np_cdtype) if out is None else out
+        _check(self._lib.nnfft_exec_host(self._h, self._host_arr(f, self.M1, "f"),
+                                         self._host_arr(out, self.M2, "out")))
+        return out
+
+    def adjoint_host(self, g, out=None):
+        out = np.empty(self.M1, dtype=self.np_cdtype) if out is None else out
+        _check(self._lib.nnfft_adjoint_host(self._h, self._host_arr(g, self.M2, "g"),
+                                            self._host_arr(out, self.M1, "out")))
+        return out
+
+    def sync(self):
+        _check(self._lib.nnfft_sync(self._h))
+
+    def timing(self, enable=True):
+        """Bracket every stage with CUDA events on the plan stream (tracing)."""
+        _check(self._lib.nnfft_timing_enable(self._h, int(bool(enable))))
+
+    def timing_read(self, reset=True) -> dict:
+        """{stage: (total_ms, count)} accumulated since the last reset (waits for the stream)."""
+        t = Timing()
+        _check(self._lib.nnfft_timing_read(self._h, ctypes.byref(t), int(bool(reset))))
+        return {name: (t.ms[i], int(t.count[i])) for i, name in enumerate(STAGES)}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.nnfft_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sinc(N, a, c, b, m=8, out=None, stream=None):
+    """Fast sinc transform (Algorithm 6.1, Gauss-Legendre rule with 2N nodes).
+
+    a: L1 float64 CUDA nodes, c: L1 coefficients (float64/float32 real or
+    complex128/complex64), b: L2 float64 CUDA targets.  Returns h (L2) of c's type.
+    fp64 types use the fp64 path, fp32 types the fp32 path.
+    """
+    import torch
+    lib = load_library()
+    L1, L2 = a.numel(), b.numel()
+    is_complex = c.is_complex()
+    dbl = c.dtype in (torch.float64, torch.complex128)
+    code = NNFFT_C128 if dbl else NNFFT_C64
+    pa = _dev_tensor(a, torch.float64, L1, "a")
+    pb = _dev_tensor(b, torch.float64, L2, "b")
+    pc = _dev_tensor(c, c.dtype, L1, "c")
+    if out is None:
+        out = torch.empty(L2, dtype=c.dtype, device=b.device)
+    po = _dev_tensor(out, c.dtype, L2, "out")
+    _check(lib.sinc_exec(int(N), int(L1), int(L2), int(m), code, pa, pc, pb, po, int(is_complex),
+                         _stream_ptr(stream)))
+    return out
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load_library().nnfft_launch_count())
+
+
+def sinc_sync(stream=None):
+    lib = load_library()
+    _check(lib.sinc_sync(_stream_ptr(stream)))
+
+
+def sinc_release():
+    lib = load_library()
+    _check(lib.sinc_release())

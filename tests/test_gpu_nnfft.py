@@ -1,0 +1,303 @@
+"""GPU parity of the NNFFT (forward and adjoint) against the CPU oracle.
+
+Every case calls the CUDA library through the C ABI (Python binding) and compares
+element by element with the oracle on the same seeded inputs:
+  * the direct sum of eq. (f(xj)) (and its adjoint) with the tolerances
+    ||err||_inf / ||f||_1 <= 1e-12 (fp64, m = 8, sigma = 2) and <= 2e-5 (fp32, m = 4);
+  * Algorithm 2.2 step by step (oracle.nnfft_alg22), which isolates implementation
+    error from the window error at small m;
+  * at the full 2^20-point size, a seeded sample of output rows plus the extreme rows.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2107_02671_gb300 import nnfft as B  # noqa: E402
+from paper_2107_02671_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load_library()
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def run_forward(N, v, x, f, m, dtype, sigma=2.0):
+    plan = B.Plan(N, len(v), len(x), sigma, sigma, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    y = plan.exec(dev(f, dtype))
+    plan.sync()
+    return y.cpu().numpy().astype(np.complex128), plan
+
+
+def run_adjoint(N, v, x, g, m, dtype, sigma=2.0):
+    plan = B.Plan(N, len(v), len(x), sigma, sigma, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    z = plan.adjoint(dev(g, dtype))
+    plan.sync()
+    return z.cpu().numpy().astype(np.complex128), plan
+
+
+# ------------------------------------------------------------------------------------------
+# small configurations, full comparison
+# ------------------------------------------------------------------------------------------
+def test_config1_plain_fp64():
+    """N = 64, M1 = M2 = 128, m = 4, sigma = 2, seed 0 (complex128)."""
+    v, x, f = W.nnfft_inputs(128, 128, 0)
+    y, plan = run_forward(64, v, x, f, 4, torch.complex128)
+    exact = oracle.nnfft_direct(64, v, f, x)
+    P = oracle.make_params(64, 2, 2, 4, 4)
+    alg = oracle.nnfft_alg22(P, v, f, x)
+    E, _, _ = oracle.bound_sinh(P.N1, 4, 4, P.sigma1, P.sigma2)
+    assert oracle.relative_error(y, exact, f) <= E
+    # same algorithm as Algorithm 2.2 up to the window fit (5e-9 at m = 4) and rounding
+    assert oracle.relative_error(y, alg, f) < 2e-7
+    assert oracle.relative_error(y, exact, f) < 2 * oracle.relative_error(alg, exact, f) + 1e-7
+
+
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+@pytest.mark.parametrize("N,M1,M2", [(256, 3000, 2500), (64, 1000, 333), (1000, 4097, 129)])
+def test_fp64_m8_within_1e12(N, M1, M2, nodes):
+    v, x, f = W.nnfft_inputs(M1, M2, 1, nodes=nodes)
+    y, _ = run_forward(N, v, x, f, 8, torch.complex128)
+    exact = oracle.nnfft_direct(N, v, f, x)
+    assert oracle.relative_error(y, exact, f) <= 1e-12
+
+
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_fp64_m8_matches_algorithm_2_2(nodes):
+    N, M1, M2 = 200, 700, 600
+    v, x, f = W.nnfft_inputs(M1, M2, 2, nodes=nodes)
+    y, _ = run_forward(N, v, x, f, 8, torch.complex128)
+    P = oracle.make_params(N, 2, 2, 8, 8)
+    alg = oracle.nnfft_alg22(P, v, f, x)
+    assert oracle.relative_error(y, alg, f) < 1e-13
+
+
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+@pytest.mark.parametrize("N,M1,M2", [(256, 3000, 2500), (64, 128, 128), (1024, 5000, 4000)])
+def test_fp32_m4_within_2e5(N, M1, M2, nodes):
+    v, x, f = W.nnfft_inputs(M1, M2, 3, nodes=nodes)
+    y, _ = run_forward(N, v, x, f.astype(np.complex64), 4, torch.complex64)
+    exact = oracle.nnfft_direct(N, v, f.astype(np.complex64).astype(np.complex128), x)
+    assert oracle.relative_error(y, exact, f) <= 2e-5
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5),
+                                         (torch.complex128, 4, 1e-5)])
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_adjoint_against_direct(dtype, m, tol, nodes):
+    N, M1, M2 = 300, 2000, 1700
+    v, x, _ = W.nnfft_inputs(M1, M2, 4, nodes=nodes)
+    g = W.adjoint_inputs(M2, 4)
+    if dtype == torch.complex64:
+        g = g.astype(np.complex64).astype(np.complex128)
+    z, _ = run_adjoint(N, v, x, g, m, dtype)
+    exact = oracle.nnfft_adjoint_direct(N, v, x, g)
+    assert oracle.relative_error(z, exact, g) <= tol
+
+
+def test_adjoint_matches_transpose_of_algorithm_2_2():
+    N, M1, M2 = 64, 300, 250
+    v, x, _ = W.nnfft_inputs(M1, M2, 5)
+    g = W.adjoint_inputs(M2, 5)
+    z, _ = run_adjoint(N, v, x, g, 4, torch.complex128)
+    P = oracle.make_params(N, 2, 2, 4, 4)
+    za = oracle.nnfft_alg22_adjoint(P, v, x, g)
+    assert oracle.relative_error(z, za, g) < 2e-7
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-13), (torch.complex64, 1e-5)])
+def test_adjoint_identity_on_gpu(dtype, tol):
+    """<A f, g> = <f, A^H g> for the fast maps themselves (exact transpose construction)."""
+    N, M1, M2 = 512, 5000, 3000
+    v, x, f = W.nnfft_inputs(M1, M2, 6, nodes="chebyshev")
+    g = W.adjoint_inputs(M2, 6)
+    plan = B.Plan(N, M1, M2, 2, 2, 8 if dtype == torch.complex128 else 4, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    Af = plan.exec(dev(f, dtype)).cpu().numpy().astype(np.complex128)
+    Ag = plan.adjoint(dev(g, dtype)).cpu().numpy().astype(np.complex128)
+    plan.sync()
+    lhs = np.vdot(g, Af)
+    rhs = np.vdot(Ag, f)
+    assert abs(lhs - rhs) <= tol * np.sum(np.abs(f)) * np.sum(np.abs(g)) / np.sqrt(M1 * M2)
+
+
+def test_linearity_and_single_coefficient():
+    """One nonzero f_k gives exp(-2 pi i N v_k x_j) (a pure exponential)."""
+    N, M1, M2 = 777, 50, 4000
+    v, x, _ = W.nnfft_inputs(M1, M2, 7)
+    f = np.zeros(M1, complex)
+    f[17] = 1.0
+    y, _ = run_forward(N, v, x, f, 8, torch.complex128)
+    exact = oracle.nnfft_direct(N, v, f, x)
+    assert np.max(np.abs(y - exact)) < 1e-12
+    assert np.max(np.abs(np.abs(y) - 1)) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("M1,M2", [(1, 1), (1, 37), (33, 1), (255, 257), (0, 10), (10, 0), (0, 0)])
+def test_ragged_and_empty_sizes(M1, M2):
+    N = 48
+    v, x, f = W.nnfft_inputs(M1, M2, 8)
+    g = W.adjoint_inputs(M2, 8)
+    plan = B.Plan(N, M1, M2, 2, 2, 8, dtype=torch.complex128)
+    plan.set_nodes(dev(v) if M1 else torch.empty(0, dtype=torch.float64, device="cuda"),
+                   dev(x) if M2 else torch.empty(0, dtype=torch.float64, device="cuda"))
+    y = plan.exec(dev(f, torch.complex128) if M1 else torch.empty(0, dtype=torch.complex128, device="cuda"))
+    z = plan.adjoint(dev(g, torch.complex128) if M2 else torch.empty(0, dtype=torch.complex128, device="cuda"))
+    plan.sync()
+    if M2:
+        exact = oracle.nnfft_direct(N, v, f, x) if M1 else np.zeros(M2)
+        assert np.max(np.abs(y.cpu().numpy() - exact)) <= 1e-12 * max(1.0, np.sum(np.abs(f)))
+    if M1:
+        exact = oracle.nnfft_adjoint_direct(N, v, x, g) if M2 else np.zeros(M1)
+        assert np.max(np.abs(z.cpu().numpy() - exact)) <= 1e-12 * max(1.0, np.sum(np.abs(g)))
+
+
+def test_boundary_nodes_and_one_cell():
+    """Nodes at exactly -1/2 and +1/2, and every node of one side in a single cell."""
+    N = 100
+    rng = np.random.default_rng(9)
+    v = np.concatenate([[-0.5, 0.5, 0.0], 0.123 + 1e-5 * rng.random(600)])
+    x = np.concatenate([[-0.5, 0.5, 0.0, 0.25], rng.uniform(-0.5, 0.5, 300)])
+    f = W.draw_complex(rng, len(v))
+    y, _ = run_forward(N, v, x, f, 8, torch.complex128)
+    exact = oracle.nnfft_direct(N, v, f, x)
+    assert oracle.relative_error(y, exact, f) <= 1e-12
+
+
+def test_heavy_cells_split_into_items():
+    """Chebyshev nodes at small N put thousands of points in the edge cells (> ITEM_CAP)."""
+    N, M1, M2 = 32, 60000, 50000
+    v, x, f = W.nnfft_inputs(M1, M2, 10, nodes="chebyshev")
+    y, _ = run_forward(N, v, x, f, 8, torch.complex128)
+    rows = W.sample_rows(M2, 400, 10, extremes=[int(np.argmin(x)), int(np.argmax(x))])
+    exact = oracle.nnfft_direct(N, v, f, x, rows=rows)
+    assert np.max(np.abs(y[rows] - exact)) / np.sum(np.abs(f)) <= 1e-12
+    g = W.adjoint_inputs(M2, 10)
+    z, _ = run_adjoint(N, v, x, g, 8, torch.complex128)
+    rows = W.sample_rows(M1, 400, 11, extremes=[int(np.argmin(v)), int(np.argmax(v))])
+    exact = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows)
+    assert np.max(np.abs(z[rows] - exact)) / np.sum(np.abs(g)) <= 1e-12
+
+
+def test_unequal_parameters():
+    """m1 != m2 and sigma1 != sigma2 (Section 4 recommends m2 > m1, sigma2 >= sigma1)."""
+    N, M1, M2 = 300, 2000, 1500
+    v, x, f = W.nnfft_inputs(M1, M2, 12)
+    plan = B.Plan(N, M1, M2, 1.5, 2.5, 6, 9, dtype=torch.complex128)
+    plan.set_nodes(dev(v), dev(x))
+    y = plan.exec(dev(f)).cpu().numpy()
+    plan.sync()
+    exact = oracle.nnfft_direct(N, v, f, x)
+    P = oracle.make_params(N, 1.5, 2.5, 6, 9)
+    alg = oracle.nnfft_alg22(P, v, f, x)
+    assert oracle.relative_error(y, alg, f) < 1e-12
+    E, _, _ = oracle.bound_sinh(P.N1, 6, 9, P.sigma1, P.sigma2)
+    assert oracle.relative_error(y, exact, f) <= E
+
+
+def test_deterministic_repeat():
+    N, M1, M2 = 512, 20000, 20000
+    v, x, f = W.nnfft_inputs(M1, M2, 13, nodes="chebyshev")
+    plan = B.Plan(N, M1, M2, 2, 2, 8, dtype=torch.complex128)
+    plan.set_nodes(dev(v), dev(x))
+    ft = dev(f)
+    y1 = plan.exec(ft).clone()
+    plan.set_nodes(dev(v), dev(x))
+    y2 = plan.exec(ft).clone()
+    plan.sync()
+    assert torch.equal(y1, y2)
+
+
+def test_host_buffer_api_matches_device_api():
+    N, M1, M2 = 256, 3000, 2000
+    v, x, f = W.nnfft_inputs(M1, M2, 14)
+    g = W.adjoint_inputs(M2, 14)
+    plan = B.Plan(N, M1, M2, 2, 2, 8, dtype=torch.complex128)
+    plan.set_nodes_host(v, x)
+    yh = plan.exec_host(f)
+    zh = plan.adjoint_host(g)
+    plan.set_nodes(dev(v), dev(x))
+    yd = plan.exec(dev(f)).cpu().numpy()
+    zd = plan.adjoint(dev(g)).cpu().numpy()
+    plan.sync()
+    assert np.array_equal(yh, yd) and np.array_equal(zh, zd)
+
+
+# ------------------------------------------------------------------------------------------
+# error reporting
+# ------------------------------------------------------------------------------------------
+def test_out_of_range_and_nan_nodes_report_erange():
+    for bad in (0.5000001, -0.75, np.nan):
+        v = np.array([0.1, bad, -0.2])
+        x = np.array([0.0, 0.3])
+        plan = B.Plan(32, 3, 2, 2, 2, 4, dtype=torch.complex128)
+        plan.set_nodes(dev(v), dev(x))
+        plan.exec(dev(np.ones(3, complex)))
+        with pytest.raises(B.NNFFTError) as ei:
+            plan.sync()
+        assert ei.value.code == 2
+        plan.sync()   # status is cleared after being reported
+
+
+def test_exec_before_set_nodes_is_a_state_error():
+    plan = B.Plan(32, 3, 2, 2, 2, 4, dtype=torch.complex128)
+    with pytest.raises(B.NNFFTError) as ei:
+        plan.exec(dev(np.ones(3, complex)))
+    assert ei.value.code == 6
+
+
+def test_wrong_tensor_types_rejected():
+    plan = B.Plan(32, 3, 2, 2, 2, 4, dtype=torch.complex128)
+    with pytest.raises(TypeError):
+        plan.set_nodes(torch.zeros(3, dtype=torch.float32, device="cuda"), None)
+    with pytest.raises(ValueError):
+        plan.set_nodes(torch.zeros(4, dtype=torch.float64, device="cuda"), None)
+
+
+# ------------------------------------------------------------------------------------------
+# the full-size workload: N = 4096, M1 = M2 = 2^20, sigma = 2, m = 8 (fp64) and m = 4 (fp32)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_full_size_fp64_sampled_rows(nodes):
+    N, M = 4096, 1 << 20
+    v, x, f = W.nnfft_inputs(M, M, 0, nodes=nodes)
+    g = W.adjoint_inputs(M, 0)
+    plan = B.Plan(N, M, M, 2, 2, 8, dtype=torch.complex128)
+    plan.set_nodes(dev(v), dev(x))
+    y = plan.exec(dev(f)).cpu().numpy()
+    z = plan.adjoint(dev(g)).cpu().numpy()
+    plan.sync()
+    rows = W.sample_rows(M, 96, 1, extremes=[int(np.argmin(x)), int(np.argmax(x))])
+    exact = oracle.nnfft_direct(N, v, f, x, rows=rows)
+    assert np.max(np.abs(y[rows] - exact)) / np.sum(np.abs(f)) <= 1e-12
+    rows = W.sample_rows(M, 96, 2, extremes=[int(np.argmin(v)), int(np.argmax(v))])
+    exact = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows)
+    assert np.max(np.abs(z[rows] - exact)) / np.sum(np.abs(g)) <= 1e-12
+
+
+def test_full_size_fp32_sampled_rows():
+    N, M = 4096, 1 << 20
+    v, x, f = W.nnfft_inputs(M, M, 0, dtype=np.complex64)
+    plan = B.Plan(N, M, M, 2, 2, 4, dtype=torch.complex64)
+    plan.set_nodes(dev(v), dev(x))
+    y = plan.exec(dev(f)).cpu().numpy().astype(np.complex128)
+    plan.sync()
+    rows = W.sample_rows(M, 96, 3)
+    exact = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
+    assert np.max(np.abs(y[rows] - exact)) / np.sum(np.abs(f)) <= 2e-5
