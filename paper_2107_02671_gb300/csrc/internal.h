@@ -15,8 +15,8 @@ namespace nnfft {
 constexpr int NR = 8;
 // A work item is a run of at most ITEM_CAP sorted points of one cell.
 constexpr int ITEM_CAP = 256;
-// Radix sort: 8-bit digits, tiles of SORT_TILE keys per block (8 warps x 512).
-constexpr int SORT_TILE = 4096;
+// Radix sort: 8-bit digits, tiles of SORT_TILE keys per block (8 warps x 256).
+constexpr int SORT_TILE = 2048;
 constexpr int SORT_THREADS = 256;
 // Largest supported FFT factor (one CTA transforms a column in shared memory).
 constexpr int FFT_MAX_FACTOR = 1024;
@@ -69,7 +69,7 @@ cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long lon
                              int ncell, uint32_t *keys, int *vals, int *status,
                              cudaStream_t s);
 // Stable LSD radix sort of (keys, vals) by the low key_bits bits.  Uses the
-// *_alt buffers and hist (>= 256 * ceil(n / SORT_TILE) + 1 ints) as scratch.
+// *_alt buffers and hist (radix_sort_hist_len(n) ints) as scratch.
 // On return *keys_sorted / *vals_sorted point at whichever buffers hold the result.
 cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
                              int *hist, int n, int key_bits, cudaStream_t s,
@@ -87,8 +87,11 @@ cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
 cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
 
 // ---- kern_spread.cu ---------------------------------------------------------------
+// Cell moments of vals over the sorted points (per work item into P), then the
+// per-cell fold (item sum and, with S.rfit, the 1/phihat1 factor) into Pc.
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s);
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, void *Pc,
+                           cudaStream_t s);
 template <typename Real>
 cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *out,

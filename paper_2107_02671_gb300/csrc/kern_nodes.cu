@@ -42,7 +42,7 @@ __global__ void k_node_keys(const double *__restrict__ nodes, int n, double usca
 // ---- radix sort ------------------------------------------------------------------
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
-               int *__restrict__ hist) {
+               int *__restrict__ hist, int *__restrict__ digit_tot) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -53,10 +53,56 @@ k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
     }
     __syncthreads();
     hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    if (h[threadIdx.x]) atomicAdd(&digit_tot[threadIdx.x], h[threadIdx.x]);   // integer: order-free
 }
 
-// Stable scatter.  Warp w of a block owns 512 consecutive keys of the tile and
-// visits them in 16 rounds of 32 in index order; within a round lanes with the
+// Exclusive scan of the digit-major histogram: block d scans row d (the counts of
+// digit d in every tile, coalesced tiles of 256) starting from the number of keys
+// with a smaller digit, sum_{d' < d} digit_tot[d'].
+__global__ void __launch_bounds__(256)
+k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ digit_tot) {
+    __shared__ int wsum[8];
+    __shared__ int carry;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int t = tid < d ? digit_tot[tid] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) wsum[w] = t;
+    __syncthreads();
+    if (tid == 0) {
+        int b = 0;
+        for (int i = 0; i < 8; ++i) b += wsum[i];
+        carry = b;
+    }
+    __syncthreads();
+    int *row = hist + (long long)d * nblocks;
+    for (int base = 0; base < nblocks; base += 256) {
+        const int i = base + tid;
+        const int v = i < nblocks ? row[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        __syncthreads();
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int wpre = 0, tot = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            wpre += k < w ? wsum[k] : 0;
+            tot += wsum[k];
+        }
+        const int c0 = carry;
+        if (i < nblocks) row[i] = c0 + wpre + incl - v;
+        __syncthreads();
+        if (tid == 0) carry = c0 + tot;
+    }
+}
+
+// Stable scatter.  Warp w of a block owns 32 * ROUNDS consecutive keys of the
+// tile and visits them in ROUNDS rounds of 32 in index order; within a round lanes with the
 // same digit are ranked by lane (match_any), across rounds by a per-warp digit
 // counter, and across warps by an exclusive scan of those counters.  So keys
 // with equal digits keep their input order.
@@ -65,7 +111,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
                int nblocks, const int *__restrict__ hist_scanned) {
     constexpr int WARPS = SORT_THREADS / 32;
-    constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 16
+    constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 8
     __shared__ int cnt[WARPS][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
@@ -113,41 +159,41 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
 }
 
 // Single-block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total.
+// Coalesced tiles of 1024 (one element per thread) with a running carry.
 // in and out may alias.
 __global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out, int n) {
-    __shared__ int warp_tot[32];
+    __shared__ int wsum[32];
     __shared__ int carry;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int chunk = (n + 1023) / 1024;
-    const long long lo = (long long)tid * chunk;
-    const long long hi = lo + chunk < n ? lo + chunk : n;
-    int s = 0;
-    for (long long i = lo; i < hi; ++i) s += in[i];
-    int incl = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) warp_tot[w] = incl;
+    if (tid == 0) carry = 0;
     __syncthreads();
-    if (w == 0) {
-        int t = warp_tot[lane];
-        int ti = t;
+    for (long long base = 0; base < n; base += 1024) {
+        const long long i = base + tid;
+        const int v = i < n ? in[i] : 0;
+        int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += u;
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        warp_tot[lane] = ti - t;          // exclusive prefix of warp totals
-        if (lane == 31) carry = ti;        // grand total
-    }
-    __syncthreads();
-    int run = warp_tot[w] + incl - s;
-    for (long long i = lo; i < hi; ++i) {
-        int v = in[i];
-        out[i] = run;
-        run += v;
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int x = wsum[lane];
+            int xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
+            }
+            wsum[lane] = xi - x;           // exclusive prefix of the warp totals
+        }
+        __syncthreads();
+        const int c0 = carry;
+        if (i < n) out[i] = c0 + wsum[w] + incl - v;
+        __syncthreads();
+        if (tid == 1023) carry = c0 + wsum[31] + incl;   // last thread: tile total
+        __syncthreads();
     }
     if (tid == 0) out[n] = carry;
 }
@@ -217,7 +263,7 @@ cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long lon
 
 size_t radix_sort_hist_len(int n) {
     long long nb = n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1;
-    return (size_t)(256 * nb + 1);
+    return (size_t)(256 * nb + 1 + 256);   // histogram, total, digit totals
 }
 
 cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s) {
@@ -233,9 +279,12 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     int *va = vals, *vb = vals_alt;
     if (n > 1) {
         int nblocks = cdiv(n, SORT_TILE);
+        int *digit_tot = hist + 256LL * nblocks + 1;
         for (int shift = 0; shift < key_bits; shift += 8) {
-            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist);
-            k_scan_exclusive<<<1, 1024, 0, s>>>(hist, hist, 256 * nblocks);
+            cudaError_t e0 = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
+            if (e0 != cudaSuccess) return e0;
+            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist, digit_tot);
+            k_sort_scan_rows<<<256, 256, 0, s>>>(hist, nblocks, digit_tot);
             k_sort_scatter<<<nblocks, SORT_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nblocks,
                                                             hist);
             count_launches(3);

@@ -50,111 +50,199 @@ __device__ __forceinline__ void cheb(Real y, Real (&T)[D]) {
 }
 
 // ---------------------------------------------------------------------------------
-// Cell moments (spread, step 1).  One warp per work item (<= ITEM_CAP sorted
-// points of one cell): lanes stride over the points, accumulate
-// sum_k val_k * T_d(y_k) in registers, and the warp reduces the D complex sums.
-// HAS_R: the values are first multiplied by the cell's fit of 1/phihat1
-// (adjoint: the division by phihat1(N* x_j) that precedes the transposed gather).
+// Warp reduce-scatter of 32 values per lane: after the five halving steps lane L
+// holds the warp-wide sum of value L (31 adds per lane instead of 5 x 32).
 // ---------------------------------------------------------------------------------
-template <typename Real, int D, bool HAS_R>
+template <typename Real, int O>
+__device__ __forceinline__ void rs_step(Real (&v)[32], int lane) {
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int i = 0; i < O; ++i) {
+        const Real send = up ? v[i] : v[O + i];
+        const Real keep = up ? v[O + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Cell moments (spread, step 1).  One warp per work item (<= ITEM_CAP sorted
+// points of one cell): lanes stride over the points and accumulate
+// sum_k val_k T_d(y_k) in registers; the warp then reduces the D complex sums.
+// ---------------------------------------------------------------------------------
+template <typename Real, int D>
 __global__ void __launch_bounds__(256)
 k_moments(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict__ P) {
     const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (item >= *S.nitems) return;
-    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
-    Real r[NR];
-    if (HAS_R) {
-#pragma unroll
-        for (int e = 0; e < NR; ++e) r[e] = S.rfit[(long long)c * NR + e];
-    }
+    const int pb = S.item_pb[item], pe = S.item_pe[item];
     Real ar[D], ai[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
     for (int p = pb + lane; p < pe; p += 32) {
         const Real y = S.ys[p];
-        C2<Real> v = vals[S.perm[p]];
+        const C2<Real> v = vals[S.perm[p]];
         Real T[D];
         cheb<Real, D>(y, T);
-        if (HAS_R) {
-            Real sc = Real(0);
-#pragma unroll
-            for (int e = 0; e < NR; ++e) sc = fma(r[e], T[e], sc);
-            v.x *= sc;
-            v.y *= sc;
-        }
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             ar[d] = fma(v.x, T[d], ar[d]);
             ai[d] = fma(v.y, T[d], ai[d]);
         }
     }
+    if constexpr (2 * D <= 32) {
+        Real vv[32];
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-        ar[d] = warp_sum(ar[d]);
-        ai[d] = warp_sum(ai[d]);
+        for (int i = 0; i < 32; ++i) vv[i] = Real(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            vv[d] = ar[d];
+            vv[D + d] = ai[d];
+        }
+        rs_step<Real, 16>(vv, lane);
+        rs_step<Real, 8>(vv, lane);
+        rs_step<Real, 4>(vv, lane);
+        rs_step<Real, 2>(vv, lane);
+        rs_step<Real, 1>(vv, lane);
+        Real *Pr = reinterpret_cast<Real *>(P + (long long)item * D);
+        if (lane < D) Pr[2 * lane] = vv[0];
+        else if (lane < 2 * D) Pr[2 * (lane - D) + 1] = vv[0];
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            ar[d] = warp_sum(ar[d]);
+            ai[d] = warp_sum(ai[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+            if (lane == d) P[(long long)item * D + d] = mk2<Real>(ar[d], ai[d]);
     }
-#pragma unroll
-    for (int d = 0; d < D; ++d)
-        if (lane == d) P[(long long)item * D + d] = mk2<Real>(ar[d], ai[d]);
 }
 
 // ---------------------------------------------------------------------------------
-// Spread convolution: one thread per FFT-buffer index q in [0, N2).  Sums the
-// taps of every cell whose support covers a grid position p == q (mod N2):
-//   g_p = scale(p) * sum_t sum_d coef[t][d] * sum_{items of cell p+m-1-t} P[item][d].
-// v side (forward): scale = 1/(N1 N2 phihat2(l)) (steps 2-3 factors folded in).
-// x side (adjoint): scale = 1.  Positions outside every support give 0, which
-// is the zero padding of step 3.
+// Cell fold: one thread per cell sums its items' moments (fixed order) into
+// Pc[cell][d].  With a 1/phihat1 fit r (adjoint, x side) it also applies the
+// per-point factor R(y) = sum_j r_j T_j(y) exactly in the Chebyshev basis,
+//   sum_k g_k R(y_k) T_d(y_k) = sum_j r_j (M_{d+j} + M_{|d-j|}) / 2,
+// truncated at degree D (the dropped moments carry weight below 1e-16).
 // ---------------------------------------------------------------------------------
-template <typename Real>
+template <typename Real, int D>
 __global__ void __launch_bounds__(128)
-k_spread_conv(SideK<Real> S, const C2<Real> *__restrict__ P, const Real *__restrict__ scale,
+k_cell_fold(SideK<Real> S, const C2<Real> *__restrict__ P, C2<Real> *__restrict__ Pc) {
+    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= S.ncell) return;
+    Real mr[D], mi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { mr[d] = Real(0); mi[d] = Real(0); }
+    const int i0 = S.item_off[ic], i1 = S.item_off[ic + 1];
+    for (int it = i0; it < i1; ++it) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const C2<Real> v = P[(long long)it * D + d];
+            mr[d] += v.x;
+            mi[d] += v.y;
+        }
+    }
+    if (S.rfit != nullptr) {
+        Real r[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) r[j] = Real(0.5) * S.rfit[(long long)ic * NR + j];
+        Real orr[D], oi[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            Real a = Real(0), b = Real(0);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int hi = d + j, lo = d > j ? d - j : j - d;
+                if (hi < D) { a = fma(r[j], mr[hi], a); b = fma(r[j], mi[hi], b); }
+                if (lo < D) { a = fma(r[j], mr[lo], a); b = fma(r[j], mi[lo], b); }
+            }
+            orr[d] = a;
+            oi[d] = b;
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) Pc[(long long)ic * D + d] = mk2<Real>(orr[d], oi[d]);
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) Pc[(long long)ic * D + d] = mk2<Real>(mr[d], mi[d]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Spread convolution.  Thread i handles grid position p = p_lo + i (centered
+// coordinates; the taps of all cells cover [p_lo, p_hi], which is never wider
+// than N2) and writes buffer index p mod N2:
+//   g_p = scale(p) * sum_t sum_d coef[t][d] * Pc[p + m - 1 - t][d],
+// and 0 for p > p_hi (the zero padding of step 3).  The block's cell range is
+// staged in shared memory ([d][cell] layout), coef is broadcast from shared
+// memory, and the D partial sums are independent accumulator chains.
+// v side (forward): scale = 1/(N1 N2 phihat2(l)); x side (adjoint): scale = 1.
+// ---------------------------------------------------------------------------------
+constexpr int SC_THREADS = 64;
+
+template <typename Real, int D>
+__global__ void __launch_bounds__(SC_THREADS)
+k_spread_conv(SideK<Real> S, const C2<Real> *__restrict__ Pc, const Real *__restrict__ scale,
               long long scale_off, long long scale_len, int N2, C2<Real> *__restrict__ out) {
     extern __shared__ unsigned char smem_raw[];
+    const int m = S.m, ntap = 2 * S.m;
+    const int ncl = SC_THREADS + ntap - 1;                    // staged cells
     Real *coef = reinterpret_cast<Real *>(smem_raw);
-    const int m = S.m, D = S.D, ntap = 2 * S.m;
-    for (int i = threadIdx.x; i < ntap * D; i += blockDim.x) coef[i] = S.coef[i];
-    __syncthreads();
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= N2) return;
-    const long long qc = q < N2 / 2 ? q : (long long)q - N2;
+    C2<Real> *Ps = reinterpret_cast<C2<Real> *>(coef + ((ntap * D + 1) & ~1));   // [D][ncl]
     const long long p_lo = S.c_lo - m + 1, p_hi = S.c_lo + S.ncell - 1 + m;
-    Real accr = Real(0), acci = Real(0);
-    for (int wrap = -1; wrap <= 1; ++wrap) {
-        const long long p = qc + (long long)wrap * N2;
-        if (p < p_lo || p > p_hi) continue;
-        Real gr = Real(0), gi = Real(0);
-        for (int t = 0; t < ntap; ++t) {
-            const long long ic = p + m - 1 - t - S.c_lo;
-            if (ic < 0 || ic >= S.ncell) continue;
-            const int i0 = S.item_off[ic], i1 = S.item_off[ic + 1];
-            const Real *ct = coef + t * D;
-            for (int it = i0; it < i1; ++it) {
-                const C2<Real> *Pi = P + (long long)it * D;
-                for (int d = 0; d < D; ++d) {
-                    const C2<Real> pv = Pi[d];
-                    gr = fma(ct[d], pv.x, gr);
-                    gi = fma(ct[d], pv.y, gi);
-                }
-            }
-        }
-        if (scale != nullptr) {
-            const long long si = p + scale_off;
-            const Real sc = (si >= 0 && si < scale_len) ? scale[si] : Real(0);
-            gr *= sc;
-            gi *= sc;
-        }
-        accr += gr;
-        acci += gi;
+    const long long p0 = p_lo + (long long)blockIdx.x * SC_THREADS;
+    const long long cbase = p0 - m;                           // cell of local index 0
+    for (int i = threadIdx.x; i < ntap * D; i += SC_THREADS) coef[i] = S.coef[i];
+    for (int i = threadIdx.x; i < ncl * D; i += SC_THREADS) {
+        const int lc = i / D, d = i - lc * D;
+        const long long ic = cbase + lc - S.c_lo;
+        C2<Real> v = mk2<Real>(Real(0), Real(0));
+        if (ic >= 0 && ic < S.ncell) v = Pc[ic * D + d];
+        Ps[d * ncl + lc] = v;
     }
-    out[q] = mk2<Real>(accr, acci);
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
+    if (i >= N2) return;
+    const long long p = p_lo + i;
+    long long q = p % N2;
+    if (q < 0) q += N2;
+    if (p > p_hi) {
+        out[q] = mk2<Real>(Real(0), Real(0));
+        return;
+    }
+    Real ar[D], ai[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
+    const int lbase = threadIdx.x + ntap - 1;                 // local cell of tap t = 0
+    for (int t = 0; t < ntap; ++t) {
+        const int lc = lbase - t;
+        const Real *ct = coef + t * D;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const C2<Real> pv = Ps[d * ncl + lc];
+            ar[d] = fma(ct[d], pv.x, ar[d]);
+            ai[d] = fma(ct[d], pv.y, ai[d]);
+        }
+    }
+    Real gr = Real(0), gi = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) { gr += ar[d]; gi += ai[d]; }
+    if (scale != nullptr) {
+        const long long si = p + scale_off;
+        const Real sc = (si >= 0 && si < scale_len) ? scale[si] : Real(0);
+        gr *= sc;
+        gi *= sc;
+    }
+    out[q] = mk2<Real>(gr, gi);
 }
 
 // ---------------------------------------------------------------------------------
 // Gather convolution: one thread per cell c of the gathering side,
 //   Q_c[d] = sum_t coef[t][d] * scale(p) * buf[p mod N2],  p = c - m + 1 + t.
-// x side (forward): buf = h of step 3, scale = 1.
+// x side (forward): buf = h of step 3, scale = 1, and the output division by
+// phihat1(N* x) is folded in per cell: with R(y) = sum_j r_j T_j(y),
+//   R(y) sum_i Q_i T_i(y) = sum_n Q'_n T_n(y),  Q'_n = sum_{i,j} r_j Q_i [n = i+j or |i-j|] / 2,
+// truncated at degree D.
 // v side (adjoint): buf = the +sign FFT of the x-side spread, scale = 1/(N1 N2 phihat2(l)).
 // ---------------------------------------------------------------------------------
 template <typename Real, int D>
@@ -190,17 +278,37 @@ k_gather_conv(SideK<Real> S, const C2<Real> *__restrict__ buf, const Real *__res
             qi[d] = fma(ct[d], h.y, qi[d]);
         }
     }
+    if (S.rfit != nullptr) {
+        Real r[NR];
 #pragma unroll
-    for (int d = 0; d < D; ++d) Q[(long long)ic * D + d] = mk2<Real>(qr[d], qi[d]);
+        for (int j = 0; j < NR; ++j) r[j] = Real(0.5) * S.rfit[(long long)ic * NR + j];
+        Real orr[D], oi[D];
+#pragma unroll
+        for (int n = 0; n < D; ++n) { orr[n] = Real(0); oi[n] = Real(0); }
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int hi = i + j, lo = i > j ? i - j : j - i;
+                if (hi < D) { orr[hi] = fma(r[j], qr[i], orr[hi]); oi[hi] = fma(r[j], qi[i], oi[hi]); }
+                if (lo < D) { orr[lo] = fma(r[j], qr[i], orr[lo]); oi[lo] = fma(r[j], qi[i], oi[lo]); }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) Q[(long long)ic * D + d] = mk2<Real>(orr[d], oi[d]);
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) Q[(long long)ic * D + d] = mk2<Real>(qr[d], qi[d]);
+    }
 }
 
 // ---------------------------------------------------------------------------------
 // Point evaluation (gather, step 4 and the output division).  One warp per work
-// item; the cell's D complex window coefficients are loaded once (uniform loads)
-// and every lane evaluates sum_d T_d(y) Q_c[d] for its points.  HAS_R: multiply by
-// the cell's fit of 1/phihat1(N* x) (forward output division).
+// item; the cell's D complex coefficients are loaded once (uniform loads) and
+// every lane evaluates sum_d T_d(y) Q_c[d] for its points, scattered to the
+// caller's order.
 // ---------------------------------------------------------------------------------
-template <typename Real, int D, bool HAS_R>
+template <typename Real, int D>
 __global__ void __launch_bounds__(256)
 k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
     const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
@@ -214,11 +322,6 @@ k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out
         qr[d] = q.x;
         qi[d] = q.y;
     }
-    Real r[NR];
-    if (HAS_R) {
-#pragma unroll
-        for (int e = 0; e < NR; ++e) r[e] = S.rfit[(long long)c * NR + e];
-    }
     for (int p = pb + lane; p < pe; p += 32) {
         const Real y = S.ys[p];
         Real T[D];
@@ -228,13 +331,6 @@ k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out
         for (int d = 0; d < D; ++d) {
             sr = fma(qr[d], T[d], sr);
             si = fma(qi[d], T[d], si);
-        }
-        if (HAS_R) {
-            Real sc = Real(0);
-#pragma unroll
-            for (int e = 0; e < NR; ++e) sc = fma(r[e], T[e], sc);
-            sr *= sc;
-            si *= sc;
         }
         out[S.perm[p]] = mk2<Real>(sr, si);
     }
@@ -261,28 +357,34 @@ bool supported_degree(int D) {
     }
 
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s) {
-    if (S.max_items <= 0) return cudaSuccess;
-    const int blocks = cdiv((long long)S.max_items * 32, 256);
-    const C2<Real> *v = static_cast<const C2<Real> *>(vals);
-    C2<Real> *Pp = static_cast<C2<Real> *>(P);
-    if (S.rfit) {
-        NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD, true><<<blocks, 256, 0, s>>>(S, v, Pp)));
-    } else {
-        NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD, false><<<blocks, 256, 0, s>>>(S, v, Pp)));
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, void *Pc,
+                           cudaStream_t s) {
+    if (S.max_items > 0) {
+        const int blocks = cdiv((long long)S.max_items * 32, 256);
+        const C2<Real> *v = static_cast<const C2<Real> *>(vals);
+        C2<Real> *Pp = static_cast<C2<Real> *>(P);
+        NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
+        count_launches(1);
     }
-    count_launches(1);
+    if (S.ncell > 0) {
+        NNFFT_DISPATCH_D(S.D, (k_cell_fold<Real, DD><<<cdiv(S.ncell, 128), 128, 0, s>>>(
+                                  S, static_cast<const C2<Real> *>(P), static_cast<C2<Real> *>(Pc))));
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *scale,
+cudaError_t launch_spread_conv(const SideK<Real> &S, const void *Pc, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *out,
                                cudaStream_t s) {
-    const size_t sm = sizeof(Real) * 2 * S.m * S.D;
-    k_spread_conv<Real><<<cdiv(N2, 128), 128, sm, s>>>(
-        S, static_cast<const C2<Real> *>(P), scale, scale_off, scale_len, N2,
-        static_cast<C2<Real> *>(out));
+    const int ntap = 2 * S.m;
+    const size_t sm = sizeof(Real) * (size_t)((ntap * S.D + 1) & ~1) +
+                      sizeof(C2<Real>) * (size_t)S.D * (SC_THREADS + ntap - 1);
+    const C2<Real> *pc = static_cast<const C2<Real> *>(Pc);
+    C2<Real> *o = static_cast<C2<Real> *>(out);
+    NNFFT_DISPATCH_D(S.D, (k_spread_conv<Real, DD><<<cdiv(N2, SC_THREADS), SC_THREADS, sm, s>>>(
+                              S, pc, scale, scale_off, scale_len, N2, o)));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -307,17 +409,13 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
     const int blocks = cdiv((long long)S.max_items * 32, 256);
     const C2<Real> *q = static_cast<const C2<Real> *>(Q);
     C2<Real> *o = static_cast<C2<Real> *>(out);
-    if (S.rfit) {
-        NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD, true><<<blocks, 256, 0, s>>>(S, q, o)));
-    } else {
-        NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD, false><<<blocks, 256, 0, s>>>(S, q, o)));
-    }
+    NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));
     count_launches(1);
     return cudaGetLastError();
 }
 
 #define NNFFT_INST(R)                                                                      \
-    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *,         \
+    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *, void *, \
                                            cudaStream_t);                                  \
     template cudaError_t launch_spread_conv<R>(const SideK<R> &, const void *, const R *,  \
                                                long long, long long, int, void *,         \

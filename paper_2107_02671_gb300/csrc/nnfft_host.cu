@@ -76,7 +76,8 @@ struct nnfft_plan_s {
     void *dec2 = nullptr;
     FftPlanDev fft{};
     void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;
-    void *P = nullptr, *Q = nullptr;
+    void *P = nullptr;   // per-item moments
+    void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
     int *status = nullptr;
     int *status_host = nullptr;   // pinned
     // host-API staging (allocated on first use)
@@ -349,11 +350,11 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 2);
-        NN_CUDA(launch_moments<Real>(sv, f, p->P, st), "spread moments");
+        NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
     }
     {
         StageTimer t(p, 3);
-        NN_CUDA(launch_spread_conv<Real>(sv, p->P, static_cast<const Real *>(p->dec2), K1 / 2, K1,
+        NN_CUDA(launch_spread_conv<Real>(sv, p->Q, static_cast<const Real *>(p->dec2), K1 / 2, K1,
                                          N2, p->bufA, st),
                 "spread convolution");
     }
@@ -383,11 +384,11 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 7);
-        NN_CUDA(launch_moments<Real>(sx, g, p->P, st), "adjoint spread moments");
+        NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
     }
     {
         StageTimer t(p, 8);
-        NN_CUDA(launch_spread_conv<Real>(sx, p->P, nullptr, 0, 0, N2, p->bufA, st),
+        NN_CUDA(launch_spread_conv<Real>(sx, p->Q, nullptr, 0, 0, N2, p->bufA, st),
                 "adjoint spread convolution");
     }
     {
