@@ -134,6 +134,26 @@ int nnfft_set_nodes_host(nnfft_plan_t p, const double *v_host, const double *x_h
 int nnfft_exec_host(nnfft_plan_t p, const void *f_host, void *y_host);
 int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host);
 
+/*
+ * nnfft_exec_host_noalloc: nnfft_exec_host without any device allocation.
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory when they call the library -- code whose GPU memory is
+ * owned by another allocator (a framework's caching allocator that has reserved
+ * nearly all of the device, where a cudaMalloc would fail or fragment it) and
+ * latency-bound serving loops that must not stall on an allocation.
+ * nnfft_exec_host allocates its device staging on first use; this call stages
+ * f and y in one static 4 MiB device array of the library instead (held on every
+ * GPU that loads the library until exit), so M1 and M2 complex values of the
+ * plan's type must fit in 4 MiB (f's part rounded up to 256 bytes): about
+ * 262,000 points in total for complex128.  Larger plans get NNFFT_EINVAL.
+ * Same arguments and result as nnfft_exec_host (host pointers; returns after the
+ * stream has drained, with any pending kernel status).  All calls on a device
+ * share the array; calls whose GPU work overlaps race on it, so serialise them.
+ * The first call on each device looks up the array's address (with that device
+ * current); make that first call before any stream capture.
+ */
+int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void *y_host);
+
 /* nnfft_sync: wait for the plan's stream; return and clear the kernel status. */
 int nnfft_sync(nnfft_plan_t p);
 

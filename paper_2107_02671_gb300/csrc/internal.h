@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <atomic>
 #include <cstdint>
+#include <string>
 #include <type_traits>
 
 #include "nnfft.h"
@@ -63,6 +64,12 @@ struct FftPlanDev {
     int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
     const void *tw1, *tw2, *twN;   // C2<Real>: exp(-2 pi i k / n) for n = n1, n2, N2
 };
+
+// ---- nnfft_host.cu (for the other translation units) -------------------------------
+// Record a status code and message for nnfft_last_error; returns code.
+int report_error(int code, const std::string &msg);
+// The stream a plan was created with.
+cudaStream_t plan_stream(nnfft_plan_t p);
 
 // ---- kern_nodes.cu ----------------------------------------------------------------
 cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,

@@ -436,6 +436,11 @@ void free_plan(nnfft_plan_s *p) {
 
 }  // namespace
 
+namespace nnfft {
+int report_error(int code, const std::string &msg) { return fail(code, msg); }
+cudaStream_t plan_stream(nnfft_plan_t p) { return p->stream; }
+}  // namespace nnfft
+
 // =====================================================================================
 // C ABI
 // =====================================================================================
