@@ -72,7 +72,20 @@ typedef struct {
     double fit_err1, fit_err2;       /* max abs error of those fits on [-1,1] (window max 1)  */
     int64_t ncell1, ncell2;          /* node cells (bins) of the v side and the x side        */
     int64_t fft_n1, fft_n2;          /* N2 = fft_n1 * fft_n2 (four-step split)                */
+    int arith;                       /* NNFFT_ARITH_* used by the point kernels (nnfft_plan only) */
 } nnfft_info;
+
+/*
+ * Arithmetic of the point kernels (Algorithm 2.2 steps 1 and 4).
+ *   NNFFT_ARITH_FP32:       complex64 plans.
+ *   NNFFT_ARITH_FP64:       complex128 plans, every operation in FP64.
+ *   NNFFT_ARITH_FP64_SPLIT: complex128 plans (default when available): Chebyshev degrees
+ *       d < D/2 of the window series in double-float (pairs of floats, ~48 bits), higher
+ *       degrees in FP32, sums assembled in FP64.  Available when the fitted window weights
+ *       of the degrees >= D/2 are <= 2e-7, which bounds the extra error near 1e-13 of
+ *       ||f||_1; coefficient magnitudes must lie in [2^-75, 2^127] for full accuracy.
+ */
+enum { NNFFT_ARITH_FP32 = 0, NNFFT_ARITH_FP64 = 1, NNFFT_ARITH_FP64_SPLIT = 2 };
 
 /*
  * nnfft_params: derive the plan parameters without touching a GPU.
@@ -98,6 +111,13 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2,
 
 /* nnfft_plan_info: copy the derived parameters of a plan. */
 int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
+
+/*
+ * nnfft_set_arith: choose NNFFT_ARITH_FP64 or NNFFT_ARITH_FP64_SPLIT for a complex128 plan
+ * (EINVAL if unavailable).  Changing the mode discards the plan's node preprocessing:
+ * call nnfft_set_nodes again before the next exec/adjoint.
+ */
+int nnfft_set_arith(nnfft_plan_t p, int arith);
 
 /*
  * nnfft_set_nodes: step 0 of Algorithm 2.2 for a new node set.

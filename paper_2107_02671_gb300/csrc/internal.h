@@ -91,6 +91,10 @@ template <typename Real>
 cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
                                  const uint32_t *keys_sorted, int n, double uscale,
                                  long long c_lo, Real *ys, int *status, cudaStream_t s);
+// same, but each coordinate stored as a float pair (hi, lo) with hi + lo = y to 2^-48
+cudaError_t launch_sorted_coords_split(const double *nodes, const int *perm,
+                                       const uint32_t *keys_sorted, int n, double uscale,
+                                       long long c_lo, float2 *ys, int *status, cudaStream_t s);
 cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
 
 // ---- kern_spread.cu ---------------------------------------------------------------
@@ -104,12 +108,22 @@ cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *
                                long long scale_off, long long scale_len, int N2, void *out,
                                cudaStream_t s);
 template <typename Real>
+cudaError_t launch_cell_fold(const SideK<Real> &S, const void *P, void *Pc, cudaStream_t s);
+// out_df: write each coefficient as float4 (re.hi, re.lo, im.hi, im.lo) for k_eval_df
+template <typename Real>
 cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *Q,
-                               cudaStream_t s);
+                               bool out_df, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s);
 bool supported_degree(int D);
+
+// ---- kern_spread_df.cu (fp64 plans, split-precision point kernels) ----------------
+// S.ys holds float2 (hi, lo) coordinates; degrees < D/2 in double-float, the rest FP32.
+bool df_supported_degree(int D);
+cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P, void *Pc,
+                              cudaStream_t s);
+cudaError_t launch_eval_df(const SideK<double> &S, const void *Q2, void *out, cudaStream_t s);
 
 // ---- kern_fft.cu ------------------------------------------------------------------
 template <typename Real>

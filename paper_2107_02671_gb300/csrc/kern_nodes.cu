@@ -248,9 +248,37 @@ __global__ void k_sorted_coords(const double *__restrict__ nodes, const int *__r
     ys[i] = (Real)y;
 }
 
+__global__ void k_sorted_coords_split(const double *__restrict__ nodes,
+                                      const int *__restrict__ perm,
+                                      const uint32_t *__restrict__ keys, int n, double uscale,
+                                      long long c_lo, float2 *__restrict__ ys, int *status) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = nodes[perm[i]];
+    double y = 0.0;
+    if (x >= -0.5 && x <= 0.5) {
+        double u = node_u(x, uscale);
+        double c = floor(u);
+        y = 2.0 * (u - c) - 1.0;
+        if ((long long)c - c_lo != (long long)keys[i]) atomicOr(status, STATUS_INTERNAL);
+    }
+    const float h = (float)y;
+    ys[i] = make_float2(h, (float)(y - (double)h));
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
+
+cudaError_t launch_sorted_coords_split(const double *nodes, const int *perm,
+                                       const uint32_t *keys_sorted, int n, double uscale,
+                                       long long c_lo, float2 *ys, int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_sorted_coords_split<<<cdiv(n, 256), 256, 0, s>>>(nodes, perm, keys_sorted, n, uscale, c_lo,
+                                                       ys, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,
                              int ncell, uint32_t *keys, int *vals, int *status,

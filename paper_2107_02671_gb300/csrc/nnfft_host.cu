@@ -71,7 +71,11 @@ struct Side {
 struct nnfft_plan_s {
     nnfft_info info{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;              // second stream: the two node sides sort concurrently
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool dbl = true;
+    bool split = false;          // fp64 plan using the split-precision point kernels
+    bool split_ok = false;       // the window fits allow them (see kern_spread_df.cu)
     Side side[2];   // 0: v (frequency) side, 1: x (spatial) side
     void *dec2 = nullptr;
     FftPlanDev fft{};
@@ -190,6 +194,15 @@ int fill_info(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, i
     return NNFFT_OK;
 }
 
+bool split_weights_ok(const std::vector<double> &coef, int ntap, int D) {
+    for (int d = D / 2; d < D; ++d) {
+        double k = 0.0;
+        for (int t = 0; t < ntap; ++t) k = std::max(k, std::fabs(coef[(size_t)t * D + d]));
+        if (k > 2e-7) return false;
+    }
+    return true;
+}
+
 int key_bits_for(int ncell) {
     int b = 1;
     while ((1LL << b) < ncell) ++b;
@@ -254,20 +267,22 @@ int setup_side(nnfft_plan_s *p, int s, const hm::Derived &d, const std::vector<d
 struct StageTimer {
     nnfft_plan_s *p;
     int stage;
+    cudaStream_t st;
     cudaEvent_t b = nullptr;
-    StageTimer(nnfft_plan_s *p_, int stage_) : p(p_), stage(stage_) {
+    StageTimer(nnfft_plan_s *p_, int stage_, cudaStream_t st_ = nullptr)
+        : p(p_), stage(stage_), st(st_ ? st_ : p_->stream) {
         if (!p->timing) return;
         cudaEvent_t a = take();
         b = take();
         if (a && b) {
-            cudaEventRecord(a, p->stream);
+            cudaEventRecord(a, st);
             p->recs.push_back({stage, a, b});
         } else {
             b = nullptr;
         }
     }
     ~StageTimer() {
-        if (b) cudaEventRecord(b, p->stream);
+        if (b) cudaEventRecord(b, st);
     }
     cudaEvent_t take() {
         if (!p->pool.empty()) {
@@ -303,10 +318,9 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     return k;
 }
 
-int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes) {
+int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st) {
     Side &S = p->side[s];
-    cudaStream_t st = p->stream;
-    StageTimer timer(p, s);
+    StageTimer timer(p, s, st);
     if (S.M == 0) {
         NN_CUDA(cudaMemsetAsync(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1), st), "memset");
         NN_CUDA(cudaMemsetAsync(S.nitems, 0, sizeof(int), st), "memset");
@@ -327,7 +341,11 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes) {
     NN_CUDA(launch_build_items(S.cell_off, S.ncell, S.item_cnt, S.item_off, S.item_cell,
                                S.item_pb, S.item_pe, S.nitems, st),
             "work items");
-    if (p->dbl) {
+    if (p->dbl && p->split) {
+        NN_CUDA(launch_sorted_coords_split(nodes, vs, ks, S.M, S.uscale, S.c_lo,
+                                           static_cast<float2 *>(S.ys), p->status, st),
+                "sorted coordinates");
+    } else if (p->dbl) {
         NN_CUDA(launch_sorted_coords<double>(nodes, vs, ks, S.M, S.uscale, S.c_lo,
                                              static_cast<double *>(S.ys), p->status, st),
                 "sorted coordinates");
@@ -348,9 +366,14 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     const SideK<Real> sx = side_args<Real>(X, true);
     const long long K1 = p->info.K1;
     const int N2 = (int)p->info.N2;
+    const bool split = p->split && sizeof(Real) == sizeof(double);
     {
         StageTimer t(p, 2);
-        NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
+        if (split)
+            NN_CUDA(launch_moments_df(reinterpret_cast<const SideK<double> &>(sv), f, p->P, p->Q, st),
+                    "spread moments");
+        else
+            NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
     }
     {
         StageTimer t(p, 3);
@@ -364,12 +387,16 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     }
     {
         StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv<Real>(sx, p->bufC, nullptr, 0, 0, N2, p->Q, st),
+        NN_CUDA(launch_gather_conv<Real>(sx, p->bufC, nullptr, 0, 0, N2, p->Q, split, st),
                 "gather convolution");
     }
     {
         StageTimer t(p, 6);
-        NN_CUDA(launch_eval<Real>(sx, p->Q, y, st), "gather evaluation");
+        if (split)
+            NN_CUDA(launch_eval_df(reinterpret_cast<const SideK<double> &>(sx), p->Q, y, st),
+                    "gather evaluation");
+        else
+            NN_CUDA(launch_eval<Real>(sx, p->Q, y, st), "gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -382,9 +409,14 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     const SideK<Real> sx = side_args<Real>(X, true);
     const long long K1 = p->info.K1;
     const int N2 = (int)p->info.N2;
+    const bool split = p->split && sizeof(Real) == sizeof(double);
     {
         StageTimer t(p, 7);
-        NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
+        if (split)
+            NN_CUDA(launch_moments_df(reinterpret_cast<const SideK<double> &>(sx), g, p->P, p->Q, st),
+                    "adjoint spread moments");
+        else
+            NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
     }
     {
         StageTimer t(p, 8);
@@ -398,12 +430,16 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     {
         StageTimer t(p, 10);
         NN_CUDA(launch_gather_conv<Real>(sv, p->bufC, static_cast<const Real *>(p->dec2), K1 / 2,
-                                         K1, N2, p->Q, st),
+                                         K1, N2, p->Q, split, st),
                 "adjoint gather convolution");
     }
     {
         StageTimer t(p, 11);
-        NN_CUDA(launch_eval<Real>(sv, p->Q, z, st), "adjoint gather evaluation");
+        if (split)
+            NN_CUDA(launch_eval_df(reinterpret_cast<const SideK<double> &>(sv), p->Q, z, st),
+                    "adjoint gather evaluation");
+        else
+            NN_CUDA(launch_eval<Real>(sv, p->Q, z, st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -424,6 +460,12 @@ int collect_status(nnfft_plan_s *p) {
 void free_plan(nnfft_plan_s *p) {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
+    if (p->aux) {
+        cudaStreamSynchronize(p->aux);
+        cudaStreamDestroy(p->aux);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (auto &r : p->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -481,6 +523,10 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
     const size_t rs = real_size(p->dbl), cs = 2 * rs;
     auto bail = [&](int code) { free_plan(p); return code; };
 
+    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "stream/event creation"));
     if ((rc = dalloc_n(p, &p->status, 1, "status"))) return bail(rc);
     if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     if (cudaMallocHost(&p->status_host, sizeof(int)) != cudaSuccess) {
@@ -490,6 +536,13 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
     }
     if ((rc = setup_side(p, 0, d, coef1))) return bail(rc);
     if ((rc = setup_side(p, 1, d, coef2))) return bail(rc);
+    // Split precision (fp64 plans): degrees >= D/2 run in FP32, so their weights
+    // kappa_d = max_t |coef[t][d]| must be small enough that an FP32 error there stays
+    // near 1e-13 of ||f||_1 in the worst case.
+    p->split_ok = p->dbl && df_supported_degree(I.D1) && df_supported_degree(I.D2) &&
+                  split_weights_ok(coef1, 2 * d.m1, I.D1) && split_weights_ok(coef2, 2 * d.m2, I.D2);
+    p->split = p->split_ok;
+    p->info.arith = !p->dbl ? NNFFT_ARITH_FP32 : (p->split ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64);
 
     // dec2[l] = 1 / (N1 N2 phihat2(l)), l in I_{K1}: the 1/N1 of eq. (gell), the division
     // of step 2 and the 1/N2 of step 3, with phihat2(l) = (m2/N2) omegahat2(m2 l / N2).
@@ -548,10 +601,21 @@ int nnfft_set_nodes(nnfft_plan_t p, const double *v_dev, const double *x_dev) {
     if (v_dev == nullptr && p->side[0].M > 0 && !p->side[0].set && x_dev == nullptr)
         return fail(NNFFT_EINVAL, "no nodes given");
     int rc;
-    if (v_dev || p->side[0].M == 0)
-        if ((rc = set_side_nodes(p, 0, v_dev))) return rc;
-    if (x_dev || p->side[1].M == 0)
-        if ((rc = set_side_nodes(p, 1, x_dev))) return rc;
+    const bool do_v = v_dev || p->side[0].M == 0, do_x = x_dev || p->side[1].M == 0;
+    if (do_v && do_x) {
+        // fork: the x side runs on the auxiliary stream, concurrently with the v side
+        NN_CUDA(cudaEventRecord(p->ev_fork, p->stream), "fork");
+        NN_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork");
+        rc = set_side_nodes(p, 1, x_dev, p->aux);
+        int rc0 = set_side_nodes(p, 0, v_dev, p->stream);
+        NN_CUDA(cudaEventRecord(p->ev_join, p->aux), "join");
+        NN_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "join");
+        if (rc) return rc;
+        if (rc0) return rc0;
+        return NNFFT_OK;
+    }
+    if (do_v && (rc = set_side_nodes(p, 0, v_dev, p->stream))) return rc;
+    if (do_x && (rc = set_side_nodes(p, 1, x_dev, p->stream))) return rc;
     return NNFFT_OK;
 }
 
@@ -569,6 +633,26 @@ int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev) {
     if ((p->info.M2 > 0 && !g_dev) || (p->info.M1 > 0 && !z_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
     return p->dbl ? run_adjoint<double>(p, g_dev, z_dev) : run_adjoint<float>(p, g_dev, z_dev);
+}
+
+int nnfft_set_arith(nnfft_plan_t p, int arith) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (!p->dbl) {
+        if (arith != NNFFT_ARITH_FP32) return fail(NNFFT_EINVAL, "complex64 plans compute in fp32");
+        return NNFFT_OK;
+    }
+    if (arith == NNFFT_ARITH_FP64_SPLIT && !p->split_ok)
+        return fail(NNFFT_EINVAL, "split precision not available for these window parameters");
+    if (arith != NNFFT_ARITH_FP64 && arith != NNFFT_ARITH_FP64_SPLIT)
+        return fail(NNFFT_EINVAL, "unknown arithmetic mode for a complex128 plan");
+    const bool want = arith == NNFFT_ARITH_FP64_SPLIT;
+    if (want != p->split) {
+        NN_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
+        p->split = want;
+        p->side[0].set = p->side[1].set = false;     // coordinates are stored per mode
+    }
+    p->info.arith = want ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64;
+    return NNFFT_OK;
 }
 
 int nnfft_timing_enable(nnfft_plan_t p, int enable) {

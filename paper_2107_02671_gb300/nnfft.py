@@ -19,6 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 NNFFT_C64, NNFFT_C128 = 0, 1
+ARITH_FP32, ARITH_FP64, ARITH_FP64_SPLIT = 0, 1, 2
 _CODES = {0: "OK", 1: "EINVAL", 2: "ERANGE", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT", 6: "ESTATE"}
 
 
@@ -48,6 +49,7 @@ class Info(ctypes.Structure):
         ("fit_err1", ctypes.c_double), ("fit_err2", ctypes.c_double),
         ("ncell1", ctypes.c_int64), ("ncell2", ctypes.c_int64),
         ("fft_n1", ctypes.c_int64), ("fft_n2", ctypes.c_int64),
+        ("arith", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -87,6 +89,7 @@ def load_library(build_if_missing: bool = True):
         lib.sinc_sync.argtypes = [vp]
         lib.sinc_release.argtypes = []
         lib.nnfft_gauss_legendre.argtypes = [i64, vp, vp]
+        lib.nnfft_set_arith.argtypes = [vp, cint]
         lib.nnfft_timing_enable.argtypes = [vp, cint]
         lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
         lib.nnfft_launch_count.argtypes = []
@@ -177,6 +180,11 @@ class Plan:
         info = Info()
         _check(self._lib.nnfft_plan_info(self._h, ctypes.byref(info)))
         return info.as_dict()
+
+    def set_arith(self, arith):
+        """ARITH_FP64 or ARITH_FP64_SPLIT for complex128 plans; call set_nodes afterwards."""
+        _check(self._lib.nnfft_set_arith(self._h, int(arith)))
+        return self
 
     def set_nodes(self, v=None, x=None):
         import torch

@@ -304,3 +304,47 @@ def test_full_size_fp32_sampled_rows():
     rows = W.sample_rows(M, 96, 3)
     exact = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
     assert np.max(np.abs(y[rows] - exact)) / np.sum(np.abs(f)) <= 2e-5
+
+
+# ------------------------------------------------------------------------------------------
+# fp64 arithmetic modes: native FP64 and split precision (double-float + FP32 by degree)
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_fp64_native_and_split_modes(nodes):
+    N, M1, M2 = 1024, 20000, 15000
+    v, x, f = W.nnfft_inputs(M1, M2, 30, nodes=nodes)
+    g = W.adjoint_inputs(M2, 30)
+    rows_y = W.sample_rows(M2, 300, 30)
+    rows_z = W.sample_rows(M1, 300, 31)
+    ey = oracle.nnfft_direct(N, v, f, x, rows=rows_y)
+    ez = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows_z)
+    out = {}
+    for arith in (B.ARITH_FP64, B.ARITH_FP64_SPLIT):
+        plan = B.Plan(N, M1, M2, 2, 2, 8, dtype=torch.complex128)
+        assert plan.info["arith"] == B.ARITH_FP64_SPLIT      # the default when available
+        plan.set_arith(arith)
+        assert plan.info["arith"] == arith
+        plan.set_nodes(dev(v), dev(x))
+        y = plan.exec(dev(f)).cpu().numpy()
+        z = plan.adjoint(dev(g)).cpu().numpy()
+        plan.sync()
+        assert np.max(np.abs(y[rows_y] - ey)) / np.sum(np.abs(f)) <= 1e-12
+        assert np.max(np.abs(z[rows_z] - ez)) / np.sum(np.abs(g)) <= 1e-12
+        out[arith] = (y, z)
+    (y1, z1), (y2, z2) = out[B.ARITH_FP64], out[B.ARITH_FP64_SPLIT]
+    assert np.max(np.abs(y1 - y2)) / np.sum(np.abs(f)) <= 1e-13
+    assert np.max(np.abs(z1 - z2)) / np.sum(np.abs(g)) <= 1e-13
+
+
+def test_set_arith_requires_new_nodes_and_rejects_fp32():
+    plan = B.Plan(64, 10, 10, 2, 2, 8, dtype=torch.complex128)
+    v, x, f = W.nnfft_inputs(10, 10, 31)
+    plan.set_nodes(dev(v), dev(x))
+    plan.set_arith(B.ARITH_FP64)
+    with pytest.raises(B.NNFFTError) as ei:
+        plan.exec(dev(f))
+    assert ei.value.code == 6
+    p32 = B.Plan(64, 10, 10, 2, 2, 4, dtype=torch.complex64)
+    assert p32.info["arith"] == B.ARITH_FP32
+    with pytest.raises(B.NNFFTError):
+        p32.set_arith(B.ARITH_FP64_SPLIT)
