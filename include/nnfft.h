@@ -62,7 +62,7 @@ enum {
 typedef struct {
     int64_t N, Nstar, N1, K1, N2;   /* N* = N + ceil(2 m1/sigma1); N1 = sigma1 N* rounded up to
                                        even; K1 = N1 + 2 m1 (= a N1, eq. (consta)); N2 = sigma2 K1
-                                       rounded up to an even 2^a 3^b 5^c 7^d                  */
+                                       rounded up to an even 2^a 3^b 5^c                      */
     int64_t M1, M2;
     int m1, m2;
     double sigma1, sigma2;           /* effective oversampling N1/N*, N2/K1                   */

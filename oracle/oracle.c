@@ -24,7 +24,7 @@
  *   - orc_make_params   N*, N1, N2, a, beta_j of Section 2 (eq. (consta), the
  *                       rescaling after eq. (condvk)) and Section 4, under the
  *                       readings listed in the design doc (N1 rounded up to even,
- *                       N2 rounded up to an even 7-smooth length).
+ *                       N2 rounded up to an even 5-smooth length).
  *   - orc_nnfft_alg22 / orc_nnfft_alg22_adjoint
  *                       Algorithm 2.2 step by step (a naive DFT for step 3) and
  *                       its exact transpose.
@@ -296,7 +296,7 @@ double orc_phi_hat(double v, i64 Nj, int m, double beta) {
 /*   N*  = N + ceil(2 m1 / sigma1)   (rescaling after eq. (condvk))              */
 /*   N1  = sigma1 N*, rounded up to an even integer; sigma1,eff = N1/N*       */
 /*   K1  = N1 + 2 m1 = a N1           (eq. (consta))                          */
-/*   N2  = sigma2 K1, rounded up to an even 2^a 3^b 5^c 7^d;                  */
+/*   N2  = sigma2 K1, rounded up to an even 2^a 3^b 5^c;                      */
 /*         sigma2,eff = N2/K1                                                 */
 /*   beta_j = 2 pi m_j (1 - 1/(2 sigma_j,eff))   (Section 4)                  */
 /* Returns 0, or 1 when the input violates m_j >= 2, sigma_j > 1, N >= 1 or   */
@@ -309,10 +309,10 @@ typedef struct {
     double beta1, beta2, a;
 } orc_params;
 
-static int is_7smooth(i64 n) {
+static int is_5smooth(i64 n) {
     if (n <= 0) return 0;
-    const i64 p[4] = {2, 3, 5, 7};
-    for (int i = 0; i < 4; ++i) while (n % p[i] == 0) n /= p[i];
+    const i64 p[3] = {2, 3, 5};
+    for (int i = 0; i < 3; ++i) while (n % p[i] == 0) n /= p[i];
     return n == 1;
 }
 
@@ -328,7 +328,7 @@ int orc_make_params(i64 N, double sigma1, double sigma2, int m1, int m2, orc_par
     P->K1 = n1 + 2 * m1;
     i64 n2 = (i64)ceil(sigma2 * (double)P->K1 - 1e-9);
     if (n2 % 2) n2 += 1;
-    while (!is_7smooth(n2)) n2 += 2;
+    while (!is_5smooth(n2)) n2 += 2;
     P->N2 = n2;
     P->sigma1 = (double)P->N1 / (double)P->Nstar;
     P->sigma2 = (double)P->N2 / (double)P->K1;

@@ -36,10 +36,10 @@ double omega_sinh_hat(double v, double beta) {
     return pref * ::j1(r) / r;
 }
 
-static bool smooth7(int64_t n) {
+static bool smooth5(int64_t n) {
     if (n <= 0) return false;
-    const int64_t p[4] = {2, 3, 5, 7};
-    for (int i = 0; i < 4; ++i)
+    const int64_t p[3] = {2, 3, 5};
+    for (int i = 0; i < 3; ++i)
         while (n % p[i] == 0) n /= p[i];
     return n == 1;
 }
@@ -63,7 +63,7 @@ const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Deri
     o->K1 = n1 + 2 * m1;                                // a N1 = N1 + 2 m1, eq. (consta)
     int64_t n2 = (int64_t)std::ceil(sigma2 * (double)o->K1 - 1e-9);
     if (n2 % 2) ++n2;
-    while (!smooth7(n2)) n2 += 2;                       // even 2^a 3^b 5^c 7^d
+    while (!smooth5(n2)) n2 += 2;                       // even 2^a 3^b 5^c
     o->N2 = n2;
     o->sigma1 = (double)o->N1 / (double)o->Nstar;
     o->sigma2 = (double)o->N2 / (double)o->K1;
@@ -170,7 +170,7 @@ bool split_fft(int64_t N2, int maxf, int *n1, int *n2) {
         if (N2 % a) continue;
         const int64_t b = N2 / a;
         if (b > maxf) continue;
-        if (!smooth7(a) || !smooth7(b)) continue;
+        if (!smooth5(a) || !smooth5(b)) continue;
         if (best1 == 0 || std::llabs(a - b) < std::llabs(best1 - N2 / best1)) best1 = (int)a;
     }
     if (best1 == 0) return false;
@@ -185,7 +185,6 @@ int radices(int n, int *r, int maxr) {
     while (n % 2 == 0 && k < maxr) { r[k++] = 2; n /= 2; }
     while (n % 3 == 0 && k < maxr) { r[k++] = 3; n /= 3; }
     while (n % 5 == 0 && k < maxr) { r[k++] = 5; n /= 5; }
-    while (n % 7 == 0 && k < maxr) { r[k++] = 7; n /= 7; }
     return n == 1 ? k : -1;
 }
 

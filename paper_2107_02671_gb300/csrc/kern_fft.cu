@@ -4,7 +4,7 @@
 //   pass 1 (one CTA per column b):  Z[b][c] = w_N2^{b c} * sum_a X[n2 a + b] w_n1^{a c}
 //   pass 2 (one CTA per column c):  Y[c + n1 d] = sum_b Z[b][c] w_n2^{b d}
 // Each column transform is a Stockham autosort FFT in shared memory with radices
-// 2, 3, 4, 5, 7 (and 8), so no bit reversal is needed.  Twiddles come from
+// 2, 3, 4, 5, so no bit reversal is needed.  Twiddles come from
 // host-computed tables exp(-2 pi i k / n); sign = +1 uses their conjugates.
 // The whole grid (N2 <= 2^20 points) stays resident in L2 between the passes.
 #include "internal.h"

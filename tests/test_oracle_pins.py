@@ -196,10 +196,10 @@ def test_phi_hat_is_fourier_transform_of_phi():
 # --------------------------------------------------------------------------------------
 def test_params_follow_section_2():
     P = oracle.make_params(64, 2, 2, 4, 4)
-    assert (P.Nstar, P.N1, P.K1, P.N2) == (68, 136, 144, 288)      # N2 = sigma2 (N1 + 2 m1) already 7-smooth
+    assert (P.Nstar, P.N1, P.K1, P.N2) == (68, 136, 144, 288)      # N2 = sigma2 (N1 + 2 m1) already 5-smooth
     P = oracle.make_params(4096, 2, 2, 8, 8)
     assert (P.Nstar, P.N1, P.K1) == (4104, 8208, 8224)
-    assert P.N2 >= 2 * P.K1 and P.N2 % 2 == 0 and P.N2 == 16464   # 16448 = 2^6*257 rounded to 2^4*3*7^3
+    assert P.N2 >= 2 * P.K1 and P.N2 % 2 == 0 and P.N2 == 17280   # 16448 = 2^6*257 rounded to 2^7*3^3*5
     for N, s1, s2, m1, m2 in [(64, 2, 2, 4, 4), (1000, 1.5, 1.25, 6, 3), (77, 1.3, 2.2, 2, 5)]:
         P = oracle.make_params(N, s1, s2, m1, m2)
         a = 1 + 2 * m1 / P.N1                                        # eq. (consta)
