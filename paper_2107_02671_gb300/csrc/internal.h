@@ -58,6 +58,19 @@ template <typename Real> struct SideK {
     int max_items;
 };
 
+// Double-float tables of one side for the split-precision grid kernels.
+struct SideDf {
+    const float2 *coef;   // [2m][D] (hi, lo) of the Chebyshev coefficients of the taps
+    const float2 *rfit;   // [ncell][NR] (hi, lo) of r_j / 2 (x side) or nullptr
+};
+
+struct FftDf {
+    int N2, n1, n2;
+    int nr1, nr2;
+    int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
+    const float4 *tw1, *tw2, *twN;   // exp(-2 pi i k / n) as (re.h, re.l, im.h, im.l)
+};
+
 struct FftPlanDev {
     int N2, n1, n2;
     int nr1, nr2;
@@ -109,21 +122,30 @@ cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *
                                cudaStream_t s);
 template <typename Real>
 cudaError_t launch_cell_fold(const SideK<Real> &S, const void *P, void *Pc, cudaStream_t s);
-// out_df: write each coefficient as float4 (re.hi, re.lo, im.hi, im.lo) for k_eval_df
 template <typename Real>
 cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *Q,
-                               bool out_df, cudaStream_t s);
+                               cudaStream_t s);
 template <typename Real>
 cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s);
 bool supported_degree(int D);
 
-// ---- kern_spread_df.cu (fp64 plans, split-precision point kernels) ----------------
-// S.ys holds float2 (hi, lo) coordinates; degrees < D/2 in double-float, the rest FP32.
+// ---- kern_spread_df.cu / kern_grid_df.cu (fp64 plans, split precision) ------------
+// S.ys holds float2 (hi, lo) coordinates; degrees < D/2 in double-float, the rest FP32;
+// all intermediate complex arrays are float4 (re.h, re.l, im.h, im.l).
 bool df_supported_degree(int D);
-cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P, void *Pc,
-                              cudaStream_t s);
-cudaError_t launch_eval_df(const SideK<double> &S, const void *Q2, void *out, cudaStream_t s);
+cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4, cudaStream_t s);
+cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, cudaStream_t s);
+cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
+                                void *Pc4, cudaStream_t s);
+cudaError_t launch_spread_conv_df(const SideK<double> &S, const SideDf &T, const void *Pc4,
+                                  const float2 *scale, long long scale_off, long long scale_len,
+                                  int N2, void *out, cudaStream_t s);
+cudaError_t launch_fft_df(const FftDf &F, const void *in, void *tmp, void *out, int sign,
+                          cudaStream_t s);
+cudaError_t launch_gather_conv_df(const SideK<double> &S, const SideDf &T, const void *buf,
+                                  const float2 *scale, long long scale_off, long long scale_len,
+                                  int N2, void *Q4, cudaStream_t s);
 
 // ---- kern_fft.cu ------------------------------------------------------------------
 template <typename Real>

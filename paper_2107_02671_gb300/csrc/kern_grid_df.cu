@@ -1,0 +1,395 @@
+// kern_grid_df.cu -- the grid stage of Algorithm 2.2 (cell fold, spread convolution
+// with the step-2 deconvolution, the step-3 FFT and the step-4 gather convolution)
+// in double-float arithmetic (df.cuh) for fp64 plans in split precision.
+//
+// Same decompositions as the FP64 kernels in kern_spread.cu / kern_fft.cu; every
+// complex value is a float4 (re.h, re.l, im.h, im.l).  Window degrees d >= B = D/2
+// (weights <= 2e-7) are accumulated in FP32 from the high parts, as in the point
+// kernels.  The FFT butterflies run fully in double-float.
+#include "df.cuh"
+#include "internal.h"
+
+namespace nnfft {
+
+namespace {
+
+using namespace dfa;
+
+// ---------------------------------------------------------------------------------
+// Cell fold: sum of the items' moments per cell; with a 1/phihat1 fit (x side,
+// adjoint) the factor R(y) = sum_j r_j T_j(y) is applied in the Chebyshev basis,
+// out_d = sum_j (r_j/2) (M_{d+j} + M_{|d-j|}), truncated at degree D.
+// rh holds r_j / 2 as (hi, lo) floats.
+// ---------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(64)
+k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
+               float4 *__restrict__ Pc4) {
+    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= S.ncell) return;
+    cdf m[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) m[d] = czero();
+    const int i0 = S.item_off[ic], i1 = S.item_off[ic + 1];
+    for (int it = i0; it < i1; ++it) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) m[d] = cadd(m[d], ld(P4 + (long long)it * D + d));
+    }
+    if (T.rfit != nullptr) {
+        df r[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float2 v = T.rfit[(long long)ic * NR + j];
+            r[j] = mk(v.x, v.y);
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            df ar = mk(0.f), ai = mk(0.f);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int hi = d + j, lo = d > j ? d - j : j - d;
+                if (hi < D) { acc(ar, mul_u(r[j], m[hi < D ? hi : 0].re)); acc(ai, mul_u(r[j], m[hi < D ? hi : 0].im)); }
+                if (lo < D) { acc(ar, mul_u(r[j], m[lo].re)); acc(ai, mul_u(r[j], m[lo].im)); }
+            }
+            cdf o;
+            o.re = norm(ar);
+            o.im = norm(ai);
+            st(Pc4 + (long long)ic * D + d, o);
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) st(Pc4 + (long long)ic * D + d, m[d]);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Spread convolution (thread i -> grid position p = p_lo + i, buffer index p mod N2):
+//   g_p = scale(p) * sum_t sum_d coef[t][d] * Pc_{p+m-1-t}[d],  0 beyond p_hi.
+// ---------------------------------------------------------------------------------
+constexpr int SCD_THREADS = 32;
+
+template <int D>
+__global__ void __launch_bounds__(SCD_THREADS)
+k_spread_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ Pc4,
+                 const float2 *__restrict__ scale, long long scale_off, long long scale_len,
+                 int N2, float4 *__restrict__ out) {
+    constexpr int B = D / 2;
+    extern __shared__ float4 smem4[];
+    const int m = S.m, ntap = 2 * S.m;
+    const int ncl = SCD_THREADS + ntap - 1;
+    float4 *Ps = smem4;                                           // [D][ncl]
+    float2 *coef = reinterpret_cast<float2 *>(smem4 + D * ncl);  // [ntap][D]
+    const long long p_lo = S.c_lo - m + 1, p_hi = S.c_lo + S.ncell - 1 + m;
+    const long long p0 = p_lo + (long long)blockIdx.x * SCD_THREADS;
+    const long long cbase = p0 - m;
+    for (int i = threadIdx.x; i < ntap * D; i += SCD_THREADS) coef[i] = T.coef[i];
+    for (int i = threadIdx.x; i < ncl * D; i += SCD_THREADS) {
+        const int lc = i / D, d = i - lc * D;
+        const long long ic = cbase + lc - S.c_lo;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ic >= 0 && ic < S.ncell) v = Pc4[ic * D + d];
+        Ps[d * ncl + lc] = v;
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * SCD_THREADS + threadIdx.x;
+    if (i >= N2) return;
+    const long long p = p_lo + i;
+    long long q = p % N2;
+    if (q < 0) q += N2;
+    if (p > p_hi) {
+        out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    df ar[B], ai[B];
+    float fr = 0.f, fi = 0.f;
+#pragma unroll
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+    const int lbase = threadIdx.x + ntap - 1;
+    for (int t = 0; t < ntap; ++t) {
+        const int lc = lbase - t;
+        const float2 *ct = coef + t * D;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const float4 pv = Ps[d * ncl + lc];
+            const float2 c2 = ct[d];
+            if (d < B) {
+                const df cd = mk(c2.x, c2.y);
+                acc(ar[d < B ? d : 0], mul_u(cd, mk(pv.x, pv.y)));
+                acc(ai[d < B ? d : 0], mul_u(cd, mk(pv.z, pv.w)));
+            } else {
+                fr = fmaf(c2.x, pv.x, fr);
+                fi = fmaf(c2.x, pv.z, fi);
+            }
+        }
+    }
+    cdf g;
+    g.re = mk(fr);
+    g.im = mk(fi);
+#pragma unroll
+    for (int d = B - 1; d >= 0; --d) {
+        g.re = add(g.re, norm(ar[d]));
+        g.im = add(g.im, norm(ai[d]));
+    }
+    if (scale != nullptr) {
+        const long long si = p + scale_off;
+        const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
+        g = cscale(g, mk(sc.x, sc.y));
+    }
+    st(out + q, g);
+}
+
+// ---------------------------------------------------------------------------------
+// FFT (step 3), four-step N2 = n1 * n2 as in kern_fft.cu, Stockham stages in
+// double-float.  Twiddle tables hold exp(-2 pi i k/n) as float4; sign = +1 conjugates.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ cdf twd(const float4 *tw, int idx, int sign) {
+    return conj_if(ld(tw + idx), sign > 0);
+}
+
+template <int R>
+__device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, int L,
+                                         const float4 *tw, int sign) {
+    const int nr = n / R;
+    const int tstep = n / (L * R);
+    for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+        const int k = j % L;
+        cdf a[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            a[q] = ld(src + j + q * nr);
+            if (q > 0 && k > 0) a[q] = cmul(a[q], twd(tw, q * k * tstep, sign));
+        }
+        cdf b[R];
+        if (R == 2) {
+            b[0] = cadd(a[0], a[1]);
+            b[1] = csub(a[0], a[1]);
+        } else if (R == 4) {
+            const cdf s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+            const cdf s13 = cadd(a[1], a[3]);
+            const cdf d13 = cmul_isign(csub(a[1], a[3]), sign);
+            b[0] = cadd(s02, s13);
+            b[1] = cadd(d02, d13);
+            b[2] = csub(s02, s13);
+            b[3] = csub(d02, d13);
+        } else {
+#pragma unroll
+            for (int p = 0; p < R; ++p) {
+                cdf accv = a[0];
+#pragma unroll
+                for (int q = 1; q < R; ++q)
+                    accv = cadd(accv, cmul(a[q], twd(tw, ((p * q) % R) * nr, sign)));
+                b[p] = accv;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < R; ++p) st(dst + (j - k) * R + k + p * L, b[p]);
+    }
+}
+
+__device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, const int *radices, int nrad,
+                               const float4 *tw, int sign) {
+    int L = 1;
+    float4 *src = A, *dst = Bf;
+    for (int s = 0; s < nrad; ++s) {
+        const int R = radices[s];
+        switch (R) {
+            case 2: stage_df<2>(src, dst, n, L, tw, sign); break;
+            case 3: stage_df<3>(src, dst, n, L, tw, sign); break;
+            case 4: stage_df<4>(src, dst, n, L, tw, sign); break;
+            case 5: stage_df<5>(src, dst, n, L, tw, sign); break;
+            default: break;
+        }
+        __syncthreads();
+        L *= R;
+        float4 *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+__global__ void __launch_bounds__(128)
+k_fft_pass1_df(const float4 *__restrict__ X, float4 *__restrict__ Z, FftDf F, int sign) {
+    extern __shared__ float4 smem4[];
+    const int n = F.n1;
+    float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
+    const int b = blockIdx.x;
+    for (int a = threadIdx.x; a < n; a += blockDim.x) {
+        A[a] = X[(long long)F.n2 * a + b];
+        tw[a] = F.tw1[a];
+    }
+    __syncthreads();
+    const float4 *res = stockham_df(A, Bf, n, F.r1, F.nr1, tw, sign);
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        st(Z + (long long)b * n + c, cmul(ld(res + c), twd(F.twN, b * c, sign)));
+}
+
+__global__ void __launch_bounds__(128)
+k_fft_pass2_df(const float4 *__restrict__ Z, float4 *__restrict__ Y, FftDf F, int sign) {
+    extern __shared__ float4 smem4[];
+    const int n = F.n2;
+    float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
+    const int c = blockIdx.x;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        A[b] = Z[(long long)b * F.n1 + c];
+        tw[b] = F.tw2[b];
+    }
+    __syncthreads();
+    const float4 *res = stockham_df(A, Bf, n, F.r2, F.nr2, tw, sign);
+    for (int d = threadIdx.x; d < n; d += blockDim.x) Y[c + (long long)F.n1 * d] = res[d];
+}
+
+// ---------------------------------------------------------------------------------
+// Gather convolution, one thread per cell:
+//   Q_c[d] = sum_t coef[t][d] * scale(p) * h[p mod N2],  p = c - m + 1 + t,
+// then (x side) the 1/phihat1 fold in the Chebyshev basis.  Output float4 per (c, d).
+// ---------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(32)
+k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
+                 const float2 *__restrict__ scale, long long scale_off, long long scale_len,
+                 int N2, float4 *__restrict__ Q4) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    extern __shared__ float2 coef_s[];
+    const int m = S.m, ntap = 2 * S.m;
+    for (int i = threadIdx.x; i < ntap * D; i += blockDim.x) coef_s[i] = T.coef[i];
+    __syncthreads();
+    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ic >= S.ncell) return;
+    const long long c = S.c_lo + ic;
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < B; ++d) { qr[d] = mk(0.f); qi[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { fr[d] = 0.f; fi[d] = 0.f; }
+    for (int t = 0; t < ntap; ++t) {
+        const long long p = c - m + 1 + t;
+        long long qidx = p % N2;
+        if (qidx < 0) qidx += N2;
+        cdf h = ld(buf + qidx);
+        if (scale != nullptr) {
+            const long long si = p + scale_off;
+            const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
+            h = cscale(h, mk(sc.x, sc.y));
+        }
+        const float2 *ct = coef_s + t * D;
+#pragma unroll
+        for (int d = 0; d < B; ++d) {
+            const df cd = mk(ct[d].x, ct[d].y);
+            acc(qr[d], mul_u(cd, h.re));
+            acc(qi[d], mul_u(cd, h.im));
+        }
+#pragma unroll
+        for (int d = 0; d < F; ++d) {
+            fr[d] = fmaf(ct[B + d].x, h.re.h, fr[d]);
+            fi[d] = fmaf(ct[B + d].x, h.im.h, fi[d]);
+        }
+    }
+    cdf q[D];
+#pragma unroll
+    for (int d = 0; d < B; ++d) {
+        q[d].re = norm(qr[d]);
+        q[d].im = norm(qi[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        q[B + d].re = mk(fr[d]);
+        q[B + d].im = mk(fi[d]);
+    }
+    if (T.rfit != nullptr) {
+        df r[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float2 v = T.rfit[(long long)ic * NR + j];
+            r[j] = mk(v.x, v.y);
+        }
+        df orr[D], oi[D];
+#pragma unroll
+        for (int n = 0; n < D; ++n) { orr[n] = mk(0.f); oi[n] = mk(0.f); }
+#pragma unroll
+        for (int ii = 0; ii < D; ++ii) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const int hi = ii + j, lo = ii > j ? ii - j : j - ii;
+                const df pr = mul_u(r[j], q[ii].re), pi = mul_u(r[j], q[ii].im);
+                if (hi < D) { acc(orr[hi < D ? hi : 0], pr); acc(oi[hi < D ? hi : 0], pi); }
+                if (lo < D) { acc(orr[lo], pr); acc(oi[lo], pi); }
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            q[d].re = norm(orr[d]);
+            q[d].im = norm(oi[d]);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) st(Q4 + (long long)ic * D + d, q[d]);
+}
+
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+#define NNFFT_DISPATCH_DF2(D_, ...)                             \
+    switch (D_) {                                               \
+        case 8: { constexpr int DD = 8; __VA_ARGS__; } break;   \
+        case 10: { constexpr int DD = 10; __VA_ARGS__; } break; \
+        case 12: { constexpr int DD = 12; __VA_ARGS__; } break; \
+        case 14: { constexpr int DD = 14; __VA_ARGS__; } break; \
+        case 16: { constexpr int DD = 16; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;                  \
+    }
+
+cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
+                                void *Pc4, cudaStream_t s) {
+    if (S.ncell <= 0) return cudaSuccess;
+    NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df<DD><<<cdiv(S.ncell, 64), 64, 0, s>>>(
+                                S, T, static_cast<const float4 *>(P4), static_cast<float4 *>(Pc4))));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread_conv_df(const SideK<double> &S, const SideDf &T, const void *Pc4,
+                                  const float2 *scale, long long scale_off, long long scale_len,
+                                  int N2, void *out, cudaStream_t s) {
+    const int ntap = 2 * S.m;
+    const size_t sm = sizeof(float4) * (size_t)S.D * (SCD_THREADS + ntap - 1) +
+                      sizeof(float2) * (size_t)ntap * S.D;
+    NNFFT_DISPATCH_DF2(S.D, (k_spread_conv_df<DD><<<cdiv(N2, SCD_THREADS), SCD_THREADS, sm, s>>>(
+                                S, T, static_cast<const float4 *>(Pc4), scale, scale_off, scale_len,
+                                N2, static_cast<float4 *>(out))));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_df(const FftDf &F, const void *in, void *tmp, void *out, int sign,
+                          cudaStream_t s) {
+    const size_t sm1 = 3 * sizeof(float4) * F.n1;
+    const size_t sm2 = 3 * sizeof(float4) * F.n2;
+    if (sm1 > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_pass1_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    if (sm2 > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_pass2_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    k_fft_pass1_df<<<F.n2, 128, sm1, s>>>(static_cast<const float4 *>(in),
+                                           static_cast<float4 *>(tmp), F, sign);
+    k_fft_pass2_df<<<F.n1, 128, sm2, s>>>(static_cast<const float4 *>(tmp),
+                                           static_cast<float4 *>(out), F, sign);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_conv_df(const SideK<double> &S, const SideDf &T, const void *buf,
+                                  const float2 *scale, long long scale_off, long long scale_len,
+                                  int N2, void *Q4, cudaStream_t s) {
+    if (S.ncell <= 0) return cudaSuccess;
+    const size_t sm = sizeof(float2) * 2 * S.m * S.D;
+    NNFFT_DISPATCH_DF2(S.D, (k_gather_conv_df<DD><<<cdiv(S.ncell, 32), 32, sm, s>>>(
+                                S, T, static_cast<const float4 *>(buf), scale, scale_off, scale_len,
+                                N2, static_cast<float4 *>(Q4))));
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nnfft

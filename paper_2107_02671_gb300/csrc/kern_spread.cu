@@ -245,12 +245,10 @@ k_spread_conv(SideK<Real> S, const C2<Real> *__restrict__ Pc, const Real *__rest
 // truncated at degree D.
 // v side (adjoint): buf = the +sign FFT of the x-side spread, scale = 1/(N1 N2 phihat2(l)).
 // ---------------------------------------------------------------------------------
-template <typename Real, int D, bool OUT_DF>
+template <typename Real, int D>
 __global__ void __launch_bounds__(32)
 k_gather_conv(SideK<Real> S, const C2<Real> *__restrict__ buf, const Real *__restrict__ scale,
-              long long scale_off, long long scale_len, int N2, void *__restrict__ Qout) {
-    C2<Real> *__restrict__ Q = static_cast<C2<Real> *>(Qout);
-    float4 *__restrict__ Q2 = static_cast<float4 *>(Qout);
+              long long scale_off, long long scale_len, int N2, C2<Real> *__restrict__ Q) {
     extern __shared__ unsigned char smem_raw[];
     Real *coef = reinterpret_cast<Real *>(smem_raw);
     const int m = S.m, ntap = 2 * S.m;
@@ -299,18 +297,8 @@ k_gather_conv(SideK<Real> S, const C2<Real> *__restrict__ buf, const Real *__res
 #pragma unroll
         for (int d = 0; d < D; ++d) { qr[d] = orr[d]; qi[d] = oi[d]; }
     }
-    if constexpr (OUT_DF) {
-        // split-precision evaluation: each coefficient as (re.hi, re.lo, im.hi, im.lo) floats
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const float rh = (float)qr[d], ih = (float)qi[d];
-            Q2[(long long)ic * D + d] = make_float4(rh, (float)(qr[d] - (Real)rh), ih,
-                                                    (float)(qi[d] - (Real)ih));
-        }
-    } else {
-#pragma unroll
-        for (int d = 0; d < D; ++d) Q[(long long)ic * D + d] = mk2<Real>(qr[d], qi[d]);
-    }
+    for (int d = 0; d < D; ++d) Q[(long long)ic * D + d] = mk2<Real>(qr[d], qi[d]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -408,17 +396,13 @@ cudaError_t launch_spread_conv(const SideK<Real> &S, const void *Pc, const Real 
 template <typename Real>
 cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *Q,
-                               bool out_df, cudaStream_t s) {
+                               cudaStream_t s) {
     if (S.ncell <= 0) return cudaSuccess;
     const size_t sm = sizeof(Real) * 2 * S.m * S.D;
     const C2<Real> *b = static_cast<const C2<Real> *>(buf);
-    if (out_df && sizeof(Real) == sizeof(double)) {
-        NNFFT_DISPATCH_D(S.D, (k_gather_conv<Real, DD, true><<<cdiv(S.ncell, 32), 32, sm, s>>>(
-                                  S, b, scale, scale_off, scale_len, N2, Q)));
-    } else {
-        NNFFT_DISPATCH_D(S.D, (k_gather_conv<Real, DD, false><<<cdiv(S.ncell, 32), 32, sm, s>>>(
-                                  S, b, scale, scale_off, scale_len, N2, Q)));
-    }
+    C2<Real> *q = static_cast<C2<Real> *>(Q);
+    NNFFT_DISPATCH_D(S.D, (k_gather_conv<Real, DD><<<cdiv(S.ncell, 32), 32, sm, s>>>(
+                              S, b, scale, scale_off, scale_len, N2, q)));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -441,7 +425,7 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
                                                long long, long long, int, void *,         \
                                                cudaStream_t);                              \
     template cudaError_t launch_gather_conv<R>(const SideK<R> &, const void *, const R *,  \
-                                               long long, long long, int, void *, bool,   \
+                                               long long, long long, int, void *,         \
                                                cudaStream_t);                              \
     template cudaError_t launch_cell_fold<R>(const SideK<R> &, const void *, void *,       \
                                              cudaStream_t);                                \

@@ -74,11 +74,16 @@ struct nnfft_plan_s {
     cudaStream_t aux = nullptr;              // second stream: the two node sides sort concurrently
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool dbl = true;
-    bool split = false;          // fp64 plan using the split-precision point kernels
+    bool split = false;          // fp64 plan using the split-precision kernels
+    std::vector<double> rfit_host;   // x-side 1/phihat1 fits (plan construction only)
     bool split_ok = false;       // the window fits allow them (see kern_spread_df.cu)
     Side side[2];   // 0: v (frequency) side, 1: x (spatial) side
     void *dec2 = nullptr;
     FftPlanDev fft{};
+    // split-precision tables (fp64 plans)
+    void *coef_df[2] = {nullptr, nullptr};
+    void *rfit_df = nullptr, *dec2_df = nullptr;
+    FftDf fftdf{};
     void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;
     void *P = nullptr;   // per-item moments
     void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
@@ -133,6 +138,22 @@ int upload_real(nnfft_plan_s *p, void **dst, const std::vector<double> &src, con
         NN_CUDA(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice),
                 what);
     }
+    return NNFFT_OK;
+}
+
+// Upload doubles as (hi, lo) float pairs: hi = fl(x), lo = fl(x - hi); scale multiplies x.
+int upload_df2(nnfft_plan_s *p, void **dst, const std::vector<double> &src, double scale,
+               const char *what) {
+    std::vector<float> f(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        const double x = src[i] * scale;
+        const float h = (float)x;
+        f[2 * i] = h;
+        f[2 * i + 1] = (float)(x - (double)h);
+    }
+    int rc = dalloc(p, dst, f.size() * sizeof(float), what);
+    if (rc) return rc;
+    NN_CUDA(cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice), what);
     return NNFFT_OK;
 }
 
@@ -243,6 +264,7 @@ int setup_side(nnfft_plan_s *p, int s, const hm::Derived &d, const std::vector<d
         }
         rc = upload_real(p, &S.rfit, r, "phihat1 fit");
         if (rc) return rc;
+        p->rfit_host = r;
     }
     const size_t M = (size_t)S.M;
     const size_t rs = real_size(p->dbl);
@@ -358,6 +380,81 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     return NNFFT_OK;
 }
 
+int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
+    const Side &V = p->side[0], &X = p->side[1];
+    cudaStream_t st = p->stream;
+    if (X.M == 0) return NNFFT_OK;
+    const SideK<double> sv = side_args<double>(V, false);
+    const SideK<double> sx = side_args<double>(X, true);
+    const SideDf tv{static_cast<const float2 *>(p->coef_df[0]), nullptr};
+    const SideDf tx{static_cast<const float2 *>(p->coef_df[1]), static_cast<const float2 *>(p->rfit_df)};
+    const long long K1 = p->info.K1;
+    const int N2 = (int)p->info.N2;
+    {
+        StageTimer t(p, 2);
+        NN_CUDA(launch_moments_df(sv, f, p->P, st), "spread moments");
+        NN_CUDA(launch_cell_fold_df(sv, tv, p->P, p->Q, st), "cell fold");
+    }
+    {
+        StageTimer t(p, 3);
+        NN_CUDA(launch_spread_conv_df(sv, tv, p->Q, static_cast<const float2 *>(p->dec2_df), K1 / 2,
+                                      K1, N2, p->bufA, st),
+                "spread convolution");
+    }
+    {
+        StageTimer t(p, 4);
+        NN_CUDA(launch_fft_df(p->fftdf, p->bufA, p->bufB, p->bufC, -1, st), "fft");
+    }
+    {
+        StageTimer t(p, 5);
+        NN_CUDA(launch_gather_conv_df(sx, tx, p->bufC, nullptr, 0, 0, N2, p->Q, st),
+                "gather convolution");
+    }
+    {
+        StageTimer t(p, 6);
+        NN_CUDA(launch_eval_df(sx, p->Q, y, st), "gather evaluation");
+    }
+    return NNFFT_OK;
+}
+
+int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
+    const Side &V = p->side[0], &X = p->side[1];
+    cudaStream_t st = p->stream;
+    if (V.M == 0) return NNFFT_OK;
+    const SideK<double> sv = side_args<double>(V, false);
+    const SideK<double> sx = side_args<double>(X, true);
+    const SideDf tv{static_cast<const float2 *>(p->coef_df[0]), nullptr};
+    const SideDf tx{static_cast<const float2 *>(p->coef_df[1]), static_cast<const float2 *>(p->rfit_df)};
+    const SideDf tx_nofold{static_cast<const float2 *>(p->coef_df[1]), nullptr};
+    const long long K1 = p->info.K1;
+    const int N2 = (int)p->info.N2;
+    {
+        StageTimer t(p, 7);
+        NN_CUDA(launch_moments_df(sx, g, p->P, st), "adjoint spread moments");
+        NN_CUDA(launch_cell_fold_df(sx, tx, p->P, p->Q, st), "adjoint cell fold");
+    }
+    {
+        StageTimer t(p, 8);
+        NN_CUDA(launch_spread_conv_df(sx, tx_nofold, p->Q, nullptr, 0, 0, N2, p->bufA, st),
+                "adjoint spread convolution");
+    }
+    {
+        StageTimer t(p, 9);
+        NN_CUDA(launch_fft_df(p->fftdf, p->bufA, p->bufB, p->bufC, +1, st), "adjoint fft");
+    }
+    {
+        StageTimer t(p, 10);
+        NN_CUDA(launch_gather_conv_df(sv, tv, p->bufC, static_cast<const float2 *>(p->dec2_df),
+                                      K1 / 2, K1, N2, p->Q, st),
+                "adjoint gather convolution");
+    }
+    {
+        StageTimer t(p, 11);
+        NN_CUDA(launch_eval_df(sv, p->Q, z, st), "adjoint gather evaluation");
+    }
+    return NNFFT_OK;
+}
+
 template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y) {
     const Side &V = p->side[0], &X = p->side[1];
     cudaStream_t st = p->stream;
@@ -366,14 +463,9 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     const SideK<Real> sx = side_args<Real>(X, true);
     const long long K1 = p->info.K1;
     const int N2 = (int)p->info.N2;
-    const bool split = p->split && sizeof(Real) == sizeof(double);
     {
         StageTimer t(p, 2);
-        if (split)
-            NN_CUDA(launch_moments_df(reinterpret_cast<const SideK<double> &>(sv), f, p->P, p->Q, st),
-                    "spread moments");
-        else
-            NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
+        NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
     }
     {
         StageTimer t(p, 3);
@@ -387,16 +479,12 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     }
     {
         StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv<Real>(sx, p->bufC, nullptr, 0, 0, N2, p->Q, split, st),
+        NN_CUDA(launch_gather_conv<Real>(sx, p->bufC, nullptr, 0, 0, N2, p->Q, st),
                 "gather convolution");
     }
     {
         StageTimer t(p, 6);
-        if (split)
-            NN_CUDA(launch_eval_df(reinterpret_cast<const SideK<double> &>(sx), p->Q, y, st),
-                    "gather evaluation");
-        else
-            NN_CUDA(launch_eval<Real>(sx, p->Q, y, st), "gather evaluation");
+        NN_CUDA(launch_eval<Real>(sx, p->Q, y, st), "gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -409,14 +497,9 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     const SideK<Real> sx = side_args<Real>(X, true);
     const long long K1 = p->info.K1;
     const int N2 = (int)p->info.N2;
-    const bool split = p->split && sizeof(Real) == sizeof(double);
     {
         StageTimer t(p, 7);
-        if (split)
-            NN_CUDA(launch_moments_df(reinterpret_cast<const SideK<double> &>(sx), g, p->P, p->Q, st),
-                    "adjoint spread moments");
-        else
-            NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
+        NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
     }
     {
         StageTimer t(p, 8);
@@ -430,16 +513,12 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     {
         StageTimer t(p, 10);
         NN_CUDA(launch_gather_conv<Real>(sv, p->bufC, static_cast<const Real *>(p->dec2), K1 / 2,
-                                         K1, N2, p->Q, split, st),
+                                         K1, N2, p->Q, st),
                 "adjoint gather convolution");
     }
     {
         StageTimer t(p, 11);
-        if (split)
-            NN_CUDA(launch_eval_df(reinterpret_cast<const SideK<double> &>(sv), p->Q, z, st),
-                    "adjoint gather evaluation");
-        else
-            NN_CUDA(launch_eval<Real>(sv, p->Q, z, st), "adjoint gather evaluation");
+        NN_CUDA(launch_eval<Real>(sv, p->Q, z, st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -543,6 +622,11 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
                   split_weights_ok(coef1, 2 * d.m1, I.D1) && split_weights_ok(coef2, 2 * d.m2, I.D2);
     p->split = p->split_ok;
     p->info.arith = !p->dbl ? NNFFT_ARITH_FP32 : (p->split ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64);
+    if (p->split_ok) {
+        if ((rc = upload_df2(p, &p->coef_df[0], coef1, 1.0, "window coefficients (df)")) ||
+            (rc = upload_df2(p, &p->coef_df[1], coef2, 1.0, "window coefficients (df)")))
+            return bail(rc);
+    }
 
     // dec2[l] = 1 / (N1 N2 phihat2(l)), l in I_{K1}: the 1/N1 of eq. (gell), the division
     // of step 2 and the 1/N2 of step 3, with phihat2(l) = (m2/N2) omegahat2(m2 l / N2).
@@ -554,6 +638,10 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
                                     hm::omega_sinh_hat((double)d.m2 * l / (double)I.N2, d.beta2));
         }
         if ((rc = upload_real(p, &p->dec2, dec, "deconvolution table"))) return bail(rc);
+        if (p->split_ok && (rc = upload_df2(p, &p->dec2_df, dec, 1.0, "deconvolution table (df)")))
+            return bail(rc);
+        if (p->split_ok && (rc = upload_df2(p, &p->rfit_df, p->rfit_host, 0.5, "phihat1 fit (df)")))
+            return bail(rc);
     }
     // FFT tables
     {
@@ -572,6 +660,26 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
         F.tw1 = t1;
         F.tw2 = t2;
         F.twN = tN;
+        if (p->split_ok) {
+            FftDf &G = p->fftdf;
+            G.N2 = F.N2;
+            G.n1 = F.n1;
+            G.n2 = F.n2;
+            G.nr1 = F.nr1;
+            G.nr2 = F.nr2;
+            for (int i = 0; i < FFT_MAX_STAGES; ++i) {
+                G.r1[i] = F.r1[i];
+                G.r2[i] = F.r2[i];
+            }
+            void *u1 = nullptr, *u2 = nullptr, *uN = nullptr;
+            if ((rc = upload_df2(p, &u1, twiddles(F.n1), 1.0, "twiddles (df)")) ||
+                (rc = upload_df2(p, &u2, twiddles(F.n2), 1.0, "twiddles (df)")) ||
+                (rc = upload_df2(p, &uN, twiddles(F.N2), 1.0, "twiddles (df)")))
+                return bail(rc);
+            G.tw1 = static_cast<const float4 *>(u1);
+            G.tw2 = static_cast<const float4 *>(u2);
+            G.twN = static_cast<const float4 *>(uN);
+        }
     }
     // work buffers
     {
@@ -624,6 +732,7 @@ int nnfft_exec(nnfft_plan_t p, const void *f_dev, void *y_dev) {
     if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
     if ((p->info.M1 > 0 && !f_dev) || (p->info.M2 > 0 && !y_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
+    if (p->dbl && p->split) return run_forward_split(p, f_dev, y_dev);
     return p->dbl ? run_forward<double>(p, f_dev, y_dev) : run_forward<float>(p, f_dev, y_dev);
 }
 
@@ -632,6 +741,7 @@ int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev) {
     if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
     if ((p->info.M2 > 0 && !g_dev) || (p->info.M1 > 0 && !z_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
+    if (p->dbl && p->split) return run_adjoint_split(p, g_dev, z_dev);
     return p->dbl ? run_adjoint<double>(p, g_dev, z_dev) : run_adjoint<float>(p, g_dev, z_dev);
 }
 
