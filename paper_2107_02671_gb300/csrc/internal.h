@@ -97,6 +97,21 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
 size_t radix_sort_hist_len(int n);
 cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
                                 cudaStream_t s);
+// Fused step 0: keys, local coordinates (caller order, format yfmt: 0 float, 1 double,
+// 2 float pair) and the first radix pass's histogram in hist (radix_sort_hist_len ints).
+cudaError_t launch_node_keys_y(const double *nodes, int n, double uscale, long long c_lo,
+                               int ncell, uint32_t *keys, void *y_user, int yfmt, int *hist,
+                               int *status, cudaStream_t s);
+// Stable LSD radix sort of the keys from launch_node_keys_y (values: the identity
+// permutation, generated in pass 0); the last pass also moves the ybytes-byte
+// coordinates: ys[sorted position] = y_user[original index].
+cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                             int *hist, int n, int key_bits, const void *y_user, void *ys,
+                             int ybytes, cudaStream_t s, uint32_t **keys_sorted,
+                             int **vals_sorted);
+cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
+                                     int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                                     cudaStream_t s);
 cudaError_t launch_build_items(const int *cell_off, int ncell, int *item_cnt, int *item_off,
                                int *item_cell, int *item_pb, int *item_pe, int *nitems,
                                cudaStream_t s);

@@ -22,44 +22,48 @@ using namespace dfa;
 // rh holds r_j / 2 as (hi, lo) floats.
 // ---------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(64)
+__device__ __forceinline__ cdf item_sum(const float4 *__restrict__ P4, int i0, int i1, int e) {
+    cdf m = ld(P4 + (long long)i0 * D + e);
+    for (int it = i0 + 1; it < i1; ++it) m = cadd(m, ld(P4 + (long long)it * D + e));
+    return m;
+}
+
+// one thread per (cell, degree d)
+template <int D>
+__global__ void __launch_bounds__(128)
 k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
                float4 *__restrict__ Pc4) {
-    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ic = (int)(idx / D), d = (int)(idx - (long long)ic * D);
     if (ic >= S.ncell) return;
-    cdf m[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) m[d] = czero();
     const int i0 = S.item_off[ic], i1 = S.item_off[ic + 1];
-    for (int it = i0; it < i1; ++it) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) m[d] = cadd(m[d], ld(P4 + (long long)it * D + d));
-    }
-    if (T.rfit != nullptr) {
-        df r[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const float2 v = T.rfit[(long long)ic * NR + j];
-            r[j] = mk(v.x, v.y);
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
+    cdf o = czero();
+    if (i1 > i0) {
+        if (T.rfit == nullptr) {
+            o = item_sum<D>(P4, i0, i1, d);
+        } else {
             df ar = mk(0.f), ai = mk(0.f);
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
+                const float2 rv = T.rfit[(long long)ic * NR + j];
+                const df r = mk(rv.x, rv.y);
                 const int hi = d + j, lo = d > j ? d - j : j - d;
-                if (hi < D) { acc(ar, mul_u(r[j], m[hi < D ? hi : 0].re)); acc(ai, mul_u(r[j], m[hi < D ? hi : 0].im)); }
-                if (lo < D) { acc(ar, mul_u(r[j], m[lo].re)); acc(ai, mul_u(r[j], m[lo].im)); }
+                if (hi < D) {
+                    const cdf m = item_sum<D>(P4, i0, i1, hi);
+                    acc(ar, mul_u(r, m.re));
+                    acc(ai, mul_u(r, m.im));
+                }
+                if (lo < D) {
+                    const cdf m = item_sum<D>(P4, i0, i1, lo);
+                    acc(ar, mul_u(r, m.re));
+                    acc(ai, mul_u(r, m.im));
+                }
             }
-            cdf o;
             o.re = norm(ar);
             o.im = norm(ai);
-            st(Pc4 + (long long)ic * D + d, o);
         }
-    } else {
-#pragma unroll
-        for (int d = 0; d < D; ++d) st(Pc4 + (long long)ic * D + d, m[d]);
     }
+    st(Pc4 + (long long)ic * D + d, o);
 }
 
 // ---------------------------------------------------------------------------------
@@ -345,7 +349,7 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
                                 void *Pc4, cudaStream_t s) {
     if (S.ncell <= 0) return cudaSuccess;
-    NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df<DD><<<cdiv(S.ncell, 64), 64, 0, s>>>(
+    NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df<DD><<<cdiv((long long)S.ncell * S.D, 128), 128, 0, s>>>(
                                 S, T, static_cast<const float4 *>(P4), static_cast<float4 *>(Pc4))));
     count_launches(1);
     return cudaGetLastError();

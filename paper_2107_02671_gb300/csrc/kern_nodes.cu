@@ -2,6 +2,8 @@
 // the grid cell it falls in, sort the nodes by cell (stable LSD radix sort with
 // 8-bit digits), and build the per-cell offsets and the work items that the
 // spread / gather kernels walk.  Deterministic: no order depends on timing.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace nnfft {
@@ -37,6 +39,69 @@ __global__ void k_node_keys(const double *__restrict__ nodes, int n, double usca
     }
     keys[i] = (uint32_t)ic;
     vals[i] = i;
+}
+
+// Coordinate storage formats of the sorted local coordinate y = 2(u - floor u) - 1.
+//   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans)
+__device__ __forceinline__ void store_y(void *yout, int fmt, long long i, double y) {
+    if (fmt == 0) {
+        static_cast<float *>(yout)[i] = (float)y;
+    } else if (fmt == 1) {
+        static_cast<double *>(yout)[i] = y;
+    } else {
+        // (hi, lo) by integer operations: hi = y truncated to 24 bits, lo = rounded rest
+        const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+        const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+        const unsigned sign = hi & 0x80000000u;
+        const int ex = (int)((hi >> 20) & 0x7ffu);
+        const unsigned mh = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const bool ok = ex > 1023 - 100;
+        const float h = ok ? __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | mh) : 0.0f;
+        const float rem = __uint2float_rn(lo & 0x1fffffffu);
+        const int se = ex - 1075 + 127;
+        const float lv = se > 0 ? rem * __uint_as_float((unsigned)se << 23) : 0.0f;
+        static_cast<float2 *>(yout)[i] = make_float2(h, ok ? (sign ? -lv : lv) : 0.0f);
+    }
+}
+
+// Step 0 for one node side in a single pass over the nodes: validate each node,
+// compute its cell key c - c_lo and local coordinate y in FP64 (u = node * uscale,
+// c = floor(u), y = 2 (u - c) - 1), store y (caller order) in the plan's format, and
+// count the digits of the first radix pass for this block's tile (the tiles match
+// k_sort_scatter's: SORT_TILE keys per block).
+__global__ void __launch_bounds__(SORT_THREADS)
+k_node_keys_y(const double *__restrict__ nodes, int n, double uscale, long long c_lo, int ncell,
+              uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int nblocks,
+              int *__restrict__ hist, int *__restrict__ digit_tot, int *status) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * SORT_TILE;
+    for (int k = threadIdx.x; k < SORT_TILE; k += SORT_THREADS) {
+        const long long i = base + k;
+        if (i >= n) break;
+        const double x = nodes[i];
+        long long ic = 0;
+        double y = 0.0;
+        if (!(x >= -0.5 && x <= 0.5)) {
+            atomicOr(status, STATUS_RANGE);
+        } else {
+            const double u = node_u(x, uscale);
+            const double c = floor(u);
+            ic = (long long)c - c_lo;
+            y = 2.0 * (u - c) - 1.0;
+            if (ic < 0 || ic >= ncell) {
+                atomicOr(status, STATUS_INTERNAL);
+                ic = ic < 0 ? 0 : ncell - 1;
+            }
+        }
+        keys[i] = (uint32_t)ic;
+        store_y(yout, yfmt, i, y);
+        atomicAdd(&h[ic & 255], 1);
+    }
+    __syncthreads();
+    hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    if (h[threadIdx.x]) atomicAdd(&digit_tot[threadIdx.x], h[threadIdx.x]);
 }
 
 // ---- radix sort ------------------------------------------------------------------
@@ -106,10 +171,14 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // same digit are ranked by lane (match_any), across rounds by a per-warp digit
 // counter, and across warps by an exclusive scan of those counters.  So keys
 // with equal digits keep their input order.
+// FIRST: the values are the identity (vin unused).  Y: payload moved along in the last
+// pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.
+template <bool FIRST, typename Y>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
-               int nblocks, const int *__restrict__ hist_scanned) {
+               int nblocks, const int *__restrict__ hist_scanned, const Y *__restrict__ yin,
+               Y *__restrict__ yout) {
     constexpr int WARPS = SORT_THREADS / 32;
     constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 8
     __shared__ int cnt[WARPS][256];
@@ -120,15 +189,30 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     uint32_t key[ROUNDS];
     int val[ROUNDS], rank[ROUNDS];
     const unsigned lt = lanemask_lt();
+    // issue every load of the warp's keys (and values) before the ranking rounds
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
-        long long idx = base + r * 32 + lane;
-        bool valid = idx < n;
+        const long long idx = base + r * 32 + lane;
+        const bool valid = idx < n;
         key[r] = valid ? kin[idx] : 0u;
-        val[r] = valid ? vin[idx] : 0;
-        unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int before = valid ? cnt[w][d] : 0;
+        if (FIRST) val[r] = (int)idx;
+        else val[r] = valid ? vin[idx] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < ROUNDS; ++r) {
+        const long long idx = base + r * 32 + lane;
+        const bool valid = idx < n;
+        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
+        // lanes with the same 9-bit value d (256 marks an invalid lane): intersect the
+        // ballots of the bits of d
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const unsigned bit = (d >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        const int before = valid ? cnt[w][d] : 0;
         __syncwarp();
         if (valid && (peers & lt) == 0) cnt[w][d] += __popc(peers);
         __syncwarp();
@@ -154,6 +238,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
             int pos = cnt[w][d] + rank[r];
             kout[pos] = key[r];
             vout[pos] = val[r];
+            if constexpr (!std::is_void<Y>::value) yout[pos] = yin[val[r]];
         }
     }
 }
@@ -205,6 +290,67 @@ __global__ void k_cell_offsets(const uint32_t *__restrict__ keys, int n, int nce
     int prev = i == 0 ? -1 : (int)keys[i - 1];
     int cur = i == n ? ncell : (int)keys[i];
     for (int c = prev + 1; c <= cur; ++c) off[c] = i;
+}
+
+// Work items in one block: for every cell, ceil(count / ITEM_CAP) items of at most
+// ITEM_CAP consecutive sorted points; item_off[c] = first item of cell c, nitems = total.
+// Coalesced tiles of 1024 cells (one per thread), exclusive scan with a running carry;
+// the next tile's offsets are loaded before the current tile is scanned.
+__global__ void __launch_bounds__(1024)
+k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off,
+              int *__restrict__ item_cell, int *__restrict__ item_pb, int *__restrict__ item_pe,
+              int *__restrict__ nitems) {
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) carry = 0;
+    int c = tid;
+    int p0 = c < ncell ? off[c] : 0, p1 = c < ncell ? off[c + 1] : 0;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += 1024) {
+        const int cn = c + 1024;
+        const int q0 = cn < ncell ? off[cn] : 0, q1 = cn < ncell ? off[cn + 1] : 0;   // prefetch
+        const int v = c < ncell ? (p1 - p0 + ITEM_CAP - 1) / ITEM_CAP : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int x = wsum[lane];
+            int xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
+            }
+            wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        const int first = carry + wsum[w] + incl - v;
+        if (c < ncell) {
+            item_off[c] = first;
+            for (int j = 0; j < v; ++j) {
+                const int pb = p0 + j * ITEM_CAP;
+                item_cell[first + j] = c;
+                item_pb[first + j] = pb;
+                item_pe[first + j] = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
+            }
+        }
+        __syncthreads();
+        if (tid == 1023) carry = first + v;
+        __syncthreads();
+        c = cn;
+        p0 = q0;
+        p1 = q1;
+    }
+    if (tid == 0) {
+        item_off[ncell] = carry;
+        *nitems = carry;
+    }
 }
 
 __global__ void k_item_counts(const int *__restrict__ off, int ncell, int *__restrict__ cnt) {
@@ -313,8 +459,8 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
             if (e0 != cudaSuccess) return e0;
             k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist, digit_tot);
             k_sort_scan_rows<<<256, 256, 0, s>>>(hist, nblocks, digit_tot);
-            k_sort_scatter<<<nblocks, SORT_THREADS, 0, s>>>(ka, va, kb, vb, n, shift, nblocks,
-                                                            hist);
+            k_sort_scatter<false, void><<<nblocks, SORT_THREADS, 0, s>>>(
+                ka, va, kb, vb, n, shift, nblocks, hist, nullptr, nullptr);
             count_launches(3);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
@@ -325,6 +471,96 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     *keys_sorted = ka;
     *vals_sorted = va;
     return cudaSuccess;
+}
+
+cudaError_t launch_node_keys_y(const double *nodes, int n, double uscale, long long c_lo,
+                               int ncell, uint32_t *keys, void *y_user, int yfmt, int *hist,
+                               int *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nblocks = cdiv(n, SORT_TILE);
+    int *digit_tot = hist + 256LL * nblocks + 1;
+    cudaError_t e = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_node_keys_y<<<nblocks, SORT_THREADS, 0, s>>>(nodes, n, uscale, c_lo, ncell, keys, y_user,
+                                                   yfmt, nblocks, hist, digit_tot, status);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+template <bool FIRST, typename Y>
+void scatter_launch(int nblocks, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
+                    int *vb, int n, int shift, const int *hist, const void *yin, void *yout) {
+    k_sort_scatter<FIRST, Y><<<nblocks, SORT_THREADS, 0, s>>>(
+        ka, va, kb, vb, n, shift, nblocks, hist, static_cast<const Y *>(yin),
+        static_cast<Y *>(yout));
+}
+template <bool FIRST>
+void scatter_dispatch(int ybytes, int nblocks, cudaStream_t s, const uint32_t *ka, const int *va,
+                      uint32_t *kb, int *vb, int n, int shift, const int *hist, const void *yin,
+                      void *yout) {
+    if (ybytes == 4)
+        scatter_launch<FIRST, unsigned>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin, yout);
+    else if (ybytes == 8)
+        scatter_launch<FIRST, unsigned long long>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin,
+                                                  yout);
+    else
+        scatter_launch<FIRST, void>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin, yout);
+}
+}  // namespace
+
+cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                             int *hist, int n, int key_bits, const void *y_user, void *ys,
+                             int ybytes, cudaStream_t s, uint32_t **keys_sorted,
+                             int **vals_sorted) {
+    uint32_t *ka = keys, *kb = keys_alt;
+    int *va = vals, *vb = vals_alt;
+    if (n <= 1) {
+        if (n == 1) {
+            cudaError_t e = cudaMemsetAsync(vals, 0, sizeof(int), s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ys, y_user, ybytes, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return e;
+        }
+        *keys_sorted = ka;
+        *vals_sorted = va;
+        return cudaSuccess;
+    }
+    const int nblocks = cdiv(n, SORT_TILE);
+    int *digit_tot = hist + 256LL * nblocks + 1;
+    const int passes = (key_bits + 7) / 8;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        const bool last = pass == passes - 1;
+        if (pass > 0) {
+            cudaError_t e0 = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
+            if (e0 != cudaSuccess) return e0;
+            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist, digit_tot);
+            count_launches(1);
+        }   // pass 0: histogram and digit totals come from k_node_keys_y
+        k_sort_scan_rows<<<256, 256, 0, s>>>(hist, nblocks, digit_tot);
+        const int yb = last ? ybytes : 0;
+        if (pass == 0)
+            scatter_dispatch<true>(yb, nblocks, s, ka, va, kb, vb, n, shift, hist, y_user, ys);
+        else
+            scatter_dispatch<false>(yb, nblocks, s, ka, va, kb, vb, n, shift, hist, y_user, ys);
+        count_launches(2);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint32_t *tk = ka; ka = kb; kb = tk;
+        int *tv = va; va = vb; vb = tv;
+    }
+    *keys_sorted = ka;
+    *vals_sorted = va;
+    return cudaSuccess;
+}
+
+cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
+                                     int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                                     cudaStream_t s) {
+    k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
+                                     nitems);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,

@@ -61,6 +61,7 @@ struct Side {
     int *perm = nullptr;
     uint32_t *keys_sorted = nullptr;
     void *ys = nullptr;
+    void *y_user = nullptr;        // coordinates in caller order (step-0 scratch)
     int *cell_off = nullptr, *item_cnt = nullptr, *item_off = nullptr;
     int *item_cell = nullptr, *item_pb = nullptr, *item_pe = nullptr, *nitems = nullptr;
     bool set = false;
@@ -272,6 +273,7 @@ int setup_side(nnfft_plan_s *p, int s, const hm::Derived &d, const std::vector<d
         (rc = dalloc_n(p, &S.vals, M, "perm")) || (rc = dalloc_n(p, &S.vals_alt, M, "perm")) ||
         (rc = dalloc_n(p, &S.hist, radix_sort_hist_len(S.M), "sort histogram")) ||
         (rc = dalloc(p, &S.ys, M * rs, "sorted coordinates")) ||
+        (rc = dalloc(p, &S.y_user, M * rs, "coordinates")) ||
         (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
         (rc = dalloc_n(p, &S.item_cnt, (size_t)S.ncell + 1, "item counts")) ||
         (rc = dalloc_n(p, &S.item_off, (size_t)S.ncell + 1, "item offsets")) ||
@@ -350,32 +352,22 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
         S.set = true;
         return NNFFT_OK;
     }
-    NN_CUDA(launch_node_keys(nodes, S.M, S.uscale, S.c_lo, S.ncell, S.keys, S.vals, p->status, st),
+    const int yfmt = !p->dbl ? 0 : (p->split ? 2 : 1);
+    const int ybytes = p->dbl ? 8 : 4;
+    NN_CUDA(launch_node_keys_y(nodes, S.M, S.uscale, S.c_lo, S.ncell, S.keys, S.y_user, yfmt,
+                               S.hist, p->status, st),
             "node keys");
     uint32_t *ks = nullptr;
     int *vs = nullptr;
-    NN_CUDA(radix_sort_pairs(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, S.M, S.key_bits, st,
-                             &ks, &vs),
+    NN_CUDA(radix_sort_cells(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, S.M, S.key_bits,
+                             S.y_user, S.ys, ybytes, st, &ks, &vs),
             "radix sort");
     S.perm = vs;
     S.keys_sorted = ks;
     NN_CUDA(launch_cell_offsets(ks, S.M, S.ncell, S.cell_off, st), "cell offsets");
-    NN_CUDA(launch_build_items(S.cell_off, S.ncell, S.item_cnt, S.item_off, S.item_cell,
-                               S.item_pb, S.item_pe, S.nitems, st),
+    NN_CUDA(launch_build_items_fused(S.cell_off, S.ncell, S.item_off, S.item_cell, S.item_pb,
+                                     S.item_pe, S.nitems, st),
             "work items");
-    if (p->dbl && p->split) {
-        NN_CUDA(launch_sorted_coords_split(nodes, vs, ks, S.M, S.uscale, S.c_lo,
-                                           static_cast<float2 *>(S.ys), p->status, st),
-                "sorted coordinates");
-    } else if (p->dbl) {
-        NN_CUDA(launch_sorted_coords<double>(nodes, vs, ks, S.M, S.uscale, S.c_lo,
-                                             static_cast<double *>(S.ys), p->status, st),
-                "sorted coordinates");
-    } else {
-        NN_CUDA(launch_sorted_coords<float>(nodes, vs, ks, S.M, S.uscale, S.c_lo,
-                                            static_cast<float *>(S.ys), p->status, st),
-                "sorted coordinates");
-    }
     S.set = true;
     return NNFFT_OK;
 }
