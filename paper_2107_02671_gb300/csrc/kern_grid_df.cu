@@ -67,10 +67,14 @@ k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
 }
 
 // ---------------------------------------------------------------------------------
-// Spread convolution (thread i -> grid position p = p_lo + i, buffer index p mod N2):
+// Spread convolution.  Grid position p = p_lo + i (centered; the taps of all cells
+// cover [p_lo, p_hi], never wider than N2) goes to buffer index p mod N2:
 //   g_p = scale(p) * sum_t sum_d coef[t][d] * Pc_{p+m-1-t}[d],  0 beyond p_hi.
+// A block handles PPB consecutive positions with one thread per (position, degree d):
+// the d-th partial sum over the taps, then the D partials of a position are added in
+// shared memory.  The block's cells are staged in shared memory.
 // ---------------------------------------------------------------------------------
-constexpr int SCD_THREADS = 32;
+constexpr int SCD_THREADS = 128;
 
 template <int D>
 __global__ void __launch_bounds__(SCD_THREADS)
@@ -78,13 +82,27 @@ k_spread_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ Pc4,
                  const float2 *__restrict__ scale, long long scale_off, long long scale_len,
                  int N2, float4 *__restrict__ out) {
     constexpr int B = D / 2;
+    constexpr int PPB = SCD_THREADS / D;                       // positions per block
     extern __shared__ float4 smem4[];
     const int m = S.m, ntap = 2 * S.m;
-    const int ncl = SCD_THREADS + ntap - 1;
-    float4 *Ps = smem4;                                           // [D][ncl]
-    float2 *coef = reinterpret_cast<float2 *>(smem4 + D * ncl);  // [ntap][D]
+    const int ncl = PPB + ntap - 1;
+    float4 *Ps = smem4;                                           // [D][ncl] staged cells
+    float4 *part = smem4 + D * ncl;                               // [PPB][D] partial sums
+    float2 *coef = reinterpret_cast<float2 *>(part + PPB * D);   // [ntap][D]
     const long long p_lo = S.c_lo - m + 1, p_hi = S.c_lo + S.ncell - 1 + m;
-    const long long p0 = p_lo + (long long)blockIdx.x * SCD_THREADS;
+    const long long i0 = (long long)blockIdx.x * PPB;
+    const long long p0 = p_lo + i0;
+    if (p0 > p_hi) {                                              // zero padding only
+        for (int k = threadIdx.x; k < PPB; k += SCD_THREADS) {
+            const long long i = i0 + k;
+            if (i < N2) {
+                long long q = (p_lo + i) % N2;
+                if (q < 0) q += N2;
+                out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        return;
+    }
     const long long cbase = p0 - m;
     for (int i = threadIdx.x; i < ntap * D; i += SCD_THREADS) coef[i] = T.coef[i];
     for (int i = threadIdx.x; i < ncl * D; i += SCD_THREADS) {
@@ -95,51 +113,56 @@ k_spread_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ Pc4,
         Ps[d * ncl + lc] = v;
     }
     __syncthreads();
-    const long long i = (long long)blockIdx.x * SCD_THREADS + threadIdx.x;
-    if (i >= N2) return;
-    const long long p = p_lo + i;
-    long long q = p % N2;
-    if (q < 0) q += N2;
-    if (p > p_hi) {
-        out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    df ar[B], ai[B];
-    float fr = 0.f, fi = 0.f;
-#pragma unroll
-    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
-    const int lbase = threadIdx.x + ntap - 1;
-    for (int t = 0; t < ntap; ++t) {
-        const int lc = lbase - t;
-        const float2 *ct = coef + t * D;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const float4 pv = Ps[d * ncl + lc];
-            const float2 c2 = ct[d];
-            if (d < B) {
+    const int k = threadIdx.x / D, d = threadIdx.x - k * D;      // position, degree
+    if (k < PPB) {
+        const int lbase = k + ntap - 1;
+        cdf g = czero();
+        if (d < B) {
+            df ar = mk(0.f), ai = mk(0.f);
+            for (int t = 0; t < ntap; ++t) {
+                const float4 pv = Ps[d * ncl + lbase - t];
+                const float2 c2 = coef[t * D + d];
                 const df cd = mk(c2.x, c2.y);
-                acc(ar[d < B ? d : 0], mul_u(cd, mk(pv.x, pv.y)));
-                acc(ai[d < B ? d : 0], mul_u(cd, mk(pv.z, pv.w)));
+                acc(ar, mul_u(cd, mk(pv.x, pv.y)));
+                acc(ai, mul_u(cd, mk(pv.z, pv.w)));
+            }
+            g.re = norm(ar);
+            g.im = norm(ai);
+        } else {
+            float fr = 0.f, fi = 0.f;
+            for (int t = 0; t < ntap; ++t) {
+                const float4 pv = Ps[d * ncl + lbase - t];
+                const float c = coef[t * D + d].x;
+                fr = fmaf(c, pv.x, fr);
+                fi = fmaf(c, pv.z, fi);
+            }
+            g.re = mk(fr);
+            g.im = mk(fi);
+        }
+        st(part + k * D + d, g);
+    }
+    __syncthreads();
+    if (k < PPB && d == 0) {
+        const long long i = i0 + k;
+        if (i < N2) {
+            const long long p = p_lo + i;
+            long long q = p % N2;
+            if (q < 0) q += N2;
+            if (p > p_hi) {
+                out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
-                fr = fmaf(c2.x, pv.x, fr);
-                fi = fmaf(c2.x, pv.z, fi);
+                cdf g = ld(part + k * D + D - 1);
+#pragma unroll
+                for (int e = D - 2; e >= 0; --e) g = cadd(g, ld(part + k * D + e));
+                if (scale != nullptr) {
+                    const long long si = p + scale_off;
+                    const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
+                    g = cscale(g, mk(sc.x, sc.y));
+                }
+                st(out + q, g);
             }
         }
     }
-    cdf g;
-    g.re = mk(fr);
-    g.im = mk(fi);
-#pragma unroll
-    for (int d = B - 1; d >= 0; --d) {
-        g.re = add(g.re, norm(ar[d]));
-        g.im = add(g.im, norm(ai[d]));
-    }
-    if (scale != nullptr) {
-        const long long si = p + scale_off;
-        const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
-        g = cscale(g, mk(sc.x, sc.y));
-    }
-    st(out + q, g);
 }
 
 // ---------------------------------------------------------------------------------
@@ -244,92 +267,106 @@ k_fft_pass2_df(const float4 *__restrict__ Z, float4 *__restrict__ Y, FftDf F, in
 }
 
 // ---------------------------------------------------------------------------------
-// Gather convolution, one thread per cell:
+// Gather convolution:
 //   Q_c[d] = sum_t coef[t][d] * scale(p) * h[p mod N2],  p = c - m + 1 + t,
-// then (x side) the 1/phihat1 fold in the Chebyshev basis.  Output float4 per (c, d).
+// then (x side) the 1/phihat1 fold in the Chebyshev basis: the coefficients of
+// R(y) sum_i Q_c[i] T_i(y) with R(y) = sum_j r_j T_j(y), truncated at degree D.
+// One thread per (cell, degree); a block holds GCB = GC_THREADS / D cells, whose D
+// sums meet in shared memory for the fold.  Output float4 per (cell, degree).
 // ---------------------------------------------------------------------------------
+constexpr int GC_THREADS = 128;
+
 template <int D>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(GC_THREADS)
 k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
                  const float2 *__restrict__ scale, long long scale_off, long long scale_len,
                  int N2, float4 *__restrict__ Q4) {
     constexpr int B = D / 2;
-    constexpr int F = D - B;
-    extern __shared__ float2 coef_s[];
+    constexpr int GCB = GC_THREADS / D;
+    __shared__ float4 qs[GCB * D];
     const int m = S.m, ntap = 2 * S.m;
-    for (int i = threadIdx.x; i < ntap * D; i += blockDim.x) coef_s[i] = T.coef[i];
-    __syncthreads();
-    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= S.ncell) return;
-    const long long c = S.c_lo + ic;
-    df qr[B], qi[B];
-    float fr[F], fi[F];
-#pragma unroll
-    for (int d = 0; d < B; ++d) { qr[d] = mk(0.f); qi[d] = mk(0.f); }
-#pragma unroll
-    for (int d = 0; d < F; ++d) { fr[d] = 0.f; fi[d] = 0.f; }
-    for (int t = 0; t < ntap; ++t) {
-        const long long p = c - m + 1 + t;
-        long long qidx = p % N2;
-        if (qidx < 0) qidx += N2;
-        cdf h = ld(buf + qidx);
-        if (scale != nullptr) {
-            const long long si = p + scale_off;
-            const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
-            h = cscale(h, mk(sc.x, sc.y));
-        }
-        const float2 *ct = coef_s + t * D;
-#pragma unroll
-        for (int d = 0; d < B; ++d) {
-            const df cd = mk(ct[d].x, ct[d].y);
-            acc(qr[d], mul_u(cd, h.re));
-            acc(qi[d], mul_u(cd, h.im));
-        }
-#pragma unroll
-        for (int d = 0; d < F; ++d) {
-            fr[d] = fmaf(ct[B + d].x, h.re.h, fr[d]);
-            fi[d] = fmaf(ct[B + d].x, h.im.h, fi[d]);
-        }
-    }
-    cdf q[D];
-#pragma unroll
-    for (int d = 0; d < B; ++d) {
-        q[d].re = norm(qr[d]);
-        q[d].im = norm(qi[d]);
-    }
-#pragma unroll
-    for (int d = 0; d < F; ++d) {
-        q[B + d].re = mk(fr[d]);
-        q[B + d].im = mk(fi[d]);
-    }
-    if (T.rfit != nullptr) {
-        df r[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const float2 v = T.rfit[(long long)ic * NR + j];
-            r[j] = mk(v.x, v.y);
-        }
-        df orr[D], oi[D];
-#pragma unroll
-        for (int n = 0; n < D; ++n) { orr[n] = mk(0.f); oi[n] = mk(0.f); }
-#pragma unroll
-        for (int ii = 0; ii < D; ++ii) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const int hi = ii + j, lo = ii > j ? ii - j : j - ii;
-                const df pr = mul_u(r[j], q[ii].re), pi = mul_u(r[j], q[ii].im);
-                if (hi < D) { acc(orr[hi < D ? hi : 0], pr); acc(oi[hi < D ? hi : 0], pi); }
-                if (lo < D) { acc(orr[lo], pr); acc(oi[lo], pi); }
+    const int k = threadIdx.x / D, d = threadIdx.x - k * D;
+    const int ic = blockIdx.x * GCB + k;
+    const bool active = k < GCB && ic < S.ncell;
+    if (active) {
+        const long long c = S.c_lo + ic;
+        cdf q = czero();
+        if (d < B) {
+            df qr = mk(0.f), qi = mk(0.f);
+            for (int t = 0; t < ntap; ++t) {
+                const long long p = c - m + 1 + t;
+                long long qidx = p % N2;
+                if (qidx < 0) qidx += N2;
+                cdf h = ld(buf + qidx);
+                if (scale != nullptr) {
+                    const long long si = p + scale_off;
+                    const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
+                    h = cscale(h, mk(sc.x, sc.y));
+                }
+                const float2 c2 = T.coef[t * D + d];
+                const df cd = mk(c2.x, c2.y);
+                acc(qr, mul_u(cd, h.re));
+                acc(qi, mul_u(cd, h.im));
             }
+            q.re = norm(qr);
+            q.im = norm(qi);
+        } else {
+            float fr = 0.f, fi = 0.f;
+            for (int t = 0; t < ntap; ++t) {
+                const long long p = c - m + 1 + t;
+                long long qidx = p % N2;
+                if (qidx < 0) qidx += N2;
+                const float4 hv = buf[qidx];
+                float hr = hv.x, hi = hv.z;
+                if (scale != nullptr) {
+                    const long long si = p + scale_off;
+                    const float sc = (si >= 0 && si < scale_len) ? scale[si].x : 0.f;
+                    hr *= sc;
+                    hi *= sc;
+                }
+                const float cc = T.coef[t * D + d].x;
+                fr = fmaf(cc, hr, fr);
+                fi = fmaf(cc, hi, fi);
+            }
+            q.re = mk(fr);
+            q.im = mk(fi);
         }
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            q[d].re = norm(orr[d]);
-            q[d].im = norm(oi[d]);
+        if (T.rfit == nullptr) {
+            st(Q4 + (long long)ic * D + d, q);
+        } else {
+            st(qs + k * D + d, q);
         }
     }
+    if (T.rfit == nullptr) return;
+    __syncthreads();
+    if (!active) return;
+    // coefficient n = d of R(y) S(y) = sum_{i,j} (r_j/2) Q_i (T_{i+j} + T_{|i-j|}):
+    //   i = n - j (j <= n),  i = n + j,  and i = j - n (j >= n, n > 0)
+    df ar = mk(0.f), ai = mk(0.f);
 #pragma unroll
-    for (int d = 0; d < D; ++d) st(Q4 + (long long)ic * D + d, q[d]);
+    for (int j = 0; j < NR; ++j) {
+        const float2 rv = T.rfit[(long long)ic * NR + j];
+        const df r = mk(rv.x, rv.y);
+        if (j <= d) {
+            const cdf v = ld(qs + k * D + d - j);
+            acc(ar, mul_u(r, v.re));
+            acc(ai, mul_u(r, v.im));
+        }
+        if (d + j < D) {
+            const cdf v = ld(qs + k * D + d + j);
+            acc(ar, mul_u(r, v.re));
+            acc(ai, mul_u(r, v.im));
+        }
+        if (d > 0 && j >= d && j - d < D) {
+            const cdf v = ld(qs + k * D + j - d);
+            acc(ar, mul_u(r, v.re));
+            acc(ai, mul_u(r, v.im));
+        }
+    }
+    cdf o;
+    o.re = norm(ar);
+    o.im = norm(ai);
+    st(Q4 + (long long)ic * D + d, o);
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -359,9 +396,10 @@ cudaError_t launch_spread_conv_df(const SideK<double> &S, const SideDf &T, const
                                   const float2 *scale, long long scale_off, long long scale_len,
                                   int N2, void *out, cudaStream_t s) {
     const int ntap = 2 * S.m;
-    const size_t sm = sizeof(float4) * (size_t)S.D * (SCD_THREADS + ntap - 1) +
-                      sizeof(float2) * (size_t)ntap * S.D;
-    NNFFT_DISPATCH_DF2(S.D, (k_spread_conv_df<DD><<<cdiv(N2, SCD_THREADS), SCD_THREADS, sm, s>>>(
+    const int ppb = SCD_THREADS / S.D;
+    const size_t sm = sizeof(float4) * (size_t)S.D * (ppb + ntap - 1) +
+                      sizeof(float4) * (size_t)ppb * S.D + sizeof(float2) * (size_t)ntap * S.D;
+    NNFFT_DISPATCH_DF2(S.D, (k_spread_conv_df<DD><<<cdiv(N2, ppb), SCD_THREADS, sm, s>>>(
                                 S, T, static_cast<const float4 *>(Pc4), scale, scale_off, scale_len,
                                 N2, static_cast<float4 *>(out))));
     count_launches(1);
@@ -388,8 +426,8 @@ cudaError_t launch_gather_conv_df(const SideK<double> &S, const SideDf &T, const
                                   const float2 *scale, long long scale_off, long long scale_len,
                                   int N2, void *Q4, cudaStream_t s) {
     if (S.ncell <= 0) return cudaSuccess;
-    const size_t sm = sizeof(float2) * 2 * S.m * S.D;
-    NNFFT_DISPATCH_DF2(S.D, (k_gather_conv_df<DD><<<cdiv(S.ncell, 32), 32, sm, s>>>(
+    const int gcb = GC_THREADS / S.D;
+    NNFFT_DISPATCH_DF2(S.D, (k_gather_conv_df<DD><<<cdiv(S.ncell, gcb), GC_THREADS, 0, s>>>(
                                 S, T, static_cast<const float4 *>(buf), scale, scale_off, scale_len,
                                 N2, static_cast<float4 *>(Q4))));
     count_launches(1);

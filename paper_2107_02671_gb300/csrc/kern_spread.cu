@@ -32,6 +32,9 @@ __device__ __forceinline__ C2<Real> mk2(Real a, Real b) {
 __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
 
+// points per lane of a work item (ITEM_CAP points, 32 lanes)
+constexpr int PPL = ITEM_CAP / 32;
+
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real v) {
 #pragma unroll
@@ -79,15 +82,27 @@ k_moments(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict
     Real ar[D], ai[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
-    for (int p = pb + lane; p < pe; p += 32) {
-        const Real y = S.ys[p];
-        const C2<Real> v = vals[S.perm[p]];
+    // issue every load of the item first (coordinates and indices, then the gathers)
+    Real yv[PPL];
+    int jv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int p = pb + lane + 32 * k;
+        yv[k] = p < pe ? S.ys[p] : Real(0);
+        jv[k] = p < pe ? S.perm[p] : -1;
+    }
+    C2<Real> fv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) fv[k] = jv[k] >= 0 ? vals[jv[k]] : mk2<Real>(Real(0), Real(0));
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (pb + 32 * k >= pe) break;                 // warp-uniform: no point in this round
         Real T[D];
-        cheb<Real, D>(y, T);
+        cheb<Real, D>(yv[k], T);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            ar[d] = fma(v.x, T[d], ar[d]);
-            ai[d] = fma(v.y, T[d], ai[d]);
+            ar[d] = fma(fv[k].x, T[d], ar[d]);
+            ai[d] = fma(fv[k].y, T[d], ai[d]);
         }
     }
     if constexpr (2 * D <= 32) {
@@ -321,17 +336,26 @@ k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out
         qr[d] = q.x;
         qi[d] = q.y;
     }
-    for (int p = pb + lane; p < pe; p += 32) {
-        const Real y = S.ys[p];
+    Real yv[PPL];
+    int jv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int p = pb + lane + 32 * k;
+        yv[k] = p < pe ? S.ys[p] : Real(0);
+        jv[k] = p < pe ? S.perm[p] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (pb + 32 * k >= pe) break;
         Real T[D];
-        cheb<Real, D>(y, T);
+        cheb<Real, D>(yv[k], T);
         Real sr = Real(0), si = Real(0);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
             sr = fma(qr[d], T[d], sr);
             si = fma(qi[d], T[d], si);
         }
-        out[S.perm[p]] = mk2<Real>(sr, si);
+        if (jv[k] >= 0) out[jv[k]] = mk2<Real>(sr, si);
     }
 }
 

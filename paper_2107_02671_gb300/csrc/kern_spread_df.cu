@@ -23,6 +23,8 @@ namespace {
 
 using namespace dfa;
 
+constexpr int PPL = ITEM_CAP / 32;   // points per lane of a work item
+
 // Chebyshev recurrence T_{d+1} = (2y) T_d - T_{d-1} in double-float
 __device__ __forceinline__ df df_rec(df y2, df t1, df t0) {
     const df p = mul_u(y2, t1);
@@ -69,9 +71,23 @@ k_moments_df(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__r
     for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
 #pragma unroll
     for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
-    for (int p = pb + lane; p < pe; p += 32) {
-        const float2 yy = ys2[p];
-        const double2 v = vals[S.perm[p]];
+    // issue every load of the item first (coordinates and indices, then the gathers)
+    float2 yv[PPL];
+    int jv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int p = pb + lane + 32 * k;
+        yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+        jv[k] = p < pe ? S.perm[p] : -1;
+    }
+    double2 vv2[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) vv2[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (pb + 32 * k >= pe) break;                 // warp-uniform: no point in this round
+        const float2 yy = yv[k];
+        const double2 v = vv2[k];
         const df fr = split_double(v.x), fi = split_double(v.y);
         const df y = mk(yy.x, yy.y);
         const df y2 = mk(2.f * yy.x, 2.f * yy.y);
@@ -129,7 +145,7 @@ k_moments_df(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__r
 // the rest in FP32, and the pair is assembled into a double.
 // ---------------------------------------------------------------------------------
 template <int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restrict__ Q4,
           double2 *__restrict__ out) {
     constexpr int B = D / 2;
@@ -151,8 +167,18 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
             fi[d >= B ? d - B : 0] = q.z;
         }
     }
-    for (int p = pb + lane; p < pe; p += 32) {
-        const float2 yy = ys2[p];
+    float2 yv[PPL];
+    int jv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        const int p = pb + lane + 32 * k;
+        yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+        jv[k] = p < pe ? S.perm[p] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (pb + 32 * k >= pe) break;
+        const float2 yy = yv[k];
         const df y = mk(yy.x, yy.y);
         const df y2 = mk(2.f * yy.x, 2.f * yy.y);
         df sr = qr[0], si = qi[0];
@@ -182,7 +208,7 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
         double2 o;
         o.x = to_double(norm(sr));
         o.y = to_double(norm(si));
-        out[S.perm[p]] = o;
+        if (jv[k] >= 0) out[jv[k]] = o;
     }
 }
 
