@@ -224,6 +224,45 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------------------------------
 # our arm
 # -------------------------------------------------------------------------------------------
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the point
+# kernels, from one ncu capture of `python bench.py --steps 5 --warmup 3 --no-cpu-baseline`
+# (profiles/k_*_nnfft_fp64_N4096_M2e20.md).  Each entry names the sources the kernel is
+# built from and their hash at capture time; a changed source reports null.
+NCU_TRAFFIC = {
+    "moments": {"kernel": "k_moments_df<14>", "bytes": 29.48e6,
+                "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "1c23e1fd1c5a151e"},
+    "eval": {"kernel": "k_eval_df<14>", "bytes": 16.35e6 + 1.69e6,
+             "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "1c23e1fd1c5a151e"},
+}
+
+
+def ncu_traffic(stage):
+    import hashlib
+    key = "moments" if stage.endswith("_moments") else "eval" if stage.endswith("_eval") else None
+    if key is None:
+        return None, None
+    ent = NCU_TRAFFIC[key]
+    h = hashlib.sha256()
+    for f in ent["sources"]:
+        with open(os.path.join(ROOT, "paper_2107_02671_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != ent["hash"]:
+        return None, ent["kernel"] + ": source changed since the ncu capture"
+    return ent["bytes"], ent["kernel"]
+
+
+def whole_job_value(total_ms, steps, pts_step, world, device="cpu"):
+    """Replicas: every rank times its own copy of the workload; the job's time is the
+    maximum over ranks and its throughput counts the points of all ranks."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * pts_step / (total_ms / 1e3)
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -296,13 +335,8 @@ def run_ours(args, rank, world):
     with ClockSampler(local) as clk:
         ms, launches, stages = timed(step, args.steps, plan)
     plan.sync()
-    total_ms = float(np.sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     pts_step = 2 * (M_PTS + M_PTS)
-    value = world * args.steps * pts_step / (total_ms / 1e3)
+    total_ms, value = whole_job_value(float(np.sum(ms)), args.steps, pts_step, world, dev)
 
     # ---- accuracy on sampled rows (rank 0) --------------------------------------------------
     acc = None
@@ -344,8 +378,10 @@ def run_ours(args, rank, world):
         # point kernels: split precision (double-float + FP32), memory/latency bound;
         # algorithmic bytes = 8 B node + 16 B value per point
         gbs = 24 * M_PTS / (avg_ms / 1e3) / 1e9
+        traffic, tnote = ncu_traffic(dom)
         roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": traffic,
+                "traffic_source": tnote,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})",
                 "algorithmic_bytes_per_launch": 24 * M_PTS}
     roof["stage_ms_per_launch"] = avg_ms
@@ -402,13 +438,16 @@ def run_ours(args, rank, world):
     hd = torch.empty(SINC_L, dtype=torch.float64, device=dev)
     cd32 = cd.to(torch.float32)
     hd32 = torch.empty(SINC_L, dtype=torch.float32, device=dev)
-    for name, cc, hh, m in (("sinc_fp64_m8", cd, hd, 8), ("sinc_fp32_m4", cd32, hd32, 4)):
-        fn = lambda cc=cc, hh=hh, m=m: B.sinc(SINC_N, ad, cc, bd, m=m, out=hh)   # noqa: E731
+    for name, cc, hh, m, rule in (("sinc_fp64_m8", cd, hd, 8, "gl"), ("sinc_fp32_m4", cd32, hd32, 4, "gl"),
+                                  ("sinc_cc_fp64_m8", cd, hd, 8, "cc"),
+                                  ("sinc_cc_fp32_m4", cd32, hd32, 4, "cc")):
+        fn = lambda cc=cc, hh=hh, m=m, rule=rule: B.sinc(SINC_N, ad, cc, bd, m=m, out=hh, rule=rule)  # noqa: E731
         fn(); fn(); B.sinc_sync()
         ms_s, _, _ = timed(fn, max(3, args.steps // 2))
         B.sinc_sync()
         extra[name] = {"value": 2 * SINC_L / (np.mean(ms_s) / 1e3), "unit": "pts/s (L1+L2)/s",
-                       "ms_per_call": float(np.mean(ms_s))}
+                       "ms_per_call": float(np.mean(ms_s)),
+                       "rule": "Gauss-Legendre, 2N nodes" if rule == "gl" else "Clenshaw-Curtis, n = 4N"}
     B.sinc_release()
 
     # ---- end to end through the host-buffer C ABI calls -----------------------------------------

@@ -200,6 +200,44 @@ int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype,
               const double *a_dev, const void *c_dev, const double *b_dev, void *h_dev,
               int is_complex, void *stream);
 
+/*
+ * Quadrature rules for sinc(N pi x) = int_{-1/2}^{1/2} exp(-2 pi i N t x) dt
+ * (Section 5; equivalently (1/2) int_{-1}^{1} exp(-pi i N z x) dz with z = 2t):
+ *   SINC_RULE_GL  n-point Gauss-Legendre rule on [-1/2, 1/2] (n = 0 selects 2N);
+ *   SINC_RULE_CC  Clenshaw-Curtis: nodes t_j = cos(j pi / n) / 2, j = 0..n, and the
+ *                 weights of eq. (wk=) computed on the GPU by Algorithm 5.4 (a DCT-I,
+ *                 done as one FFT of length 2n).  n = 0 selects 4N (Algorithm 6.1:
+ *                 n >= 4N); n is rounded up to the next 5-smooth integer (the paper's
+ *                 n = 2^t is one) and 2n may not exceed 2^20.  Theorem 5.3 bounds the
+ *                 quadrature error by 36(1 + e^{-2CN})/(35(e^2 - 1)) e^{-N(n/N - C)},
+ *                 C = pi (e^2 - 1)/(2e) ~ 3.69.
+ */
+enum { SINC_RULE_GL = 0, SINC_RULE_CC = 1 };
+
+/*
+ * sinc_exec_rule: Algorithm 6.1 with the given rule (t_j, w_j):
+ *   step 1  g_j     = sum_k c_k exp(-2 pi i N a_k x1_j)   (NNFFT #1, nodes a -> x1)
+ *   step 2  alpha_j = w_j g_j
+ *   step 3  h_l     = sum_j alpha_j exp(-2 pi i N v2_j b_l) (NNFFT #2, nodes v2 -> b)
+ * with x1 = t, v2 = -t for CC (the signs of Algorithm 6.1) and x1 = -t, v2 = t for GL
+ * (the same sums, since the GL rule is symmetric).  Arguments, caching, streams and
+ * errors as in sinc_exec; the cache key includes rule and n.  EINVAL for an unknown
+ * rule or n < 0.
+ */
+int sinc_exec_rule(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, int rule,
+                   int64_t n, const double *a_dev, const void *c_dev, const double *b_dev,
+                   void *h_dev, int is_complex, void *stream);
+
+/*
+ * sinc_quadrature: the rule sinc_exec_rule uses for (rule, N, n): *nodes_out = its
+ * number of nodes (n for GL, n + 1 for CC after rounding); if t_host and w_host are
+ * non-null they receive the nodes t_j (in [-1/2, 1/2]) and weights w_j (host arrays
+ * of *nodes_out doubles).  GL needs no GPU; CC weights come from the device
+ * (NNFFT_ECUDA without one).  Synchronous.
+ */
+int sinc_quadrature(int rule, int64_t N, int64_t n, double *t_host, double *w_host,
+                    int64_t *nodes_out);
+
 /* sinc_sync: wait for `stream` and return/clear the status of the cached sinc plans on it. */
 int sinc_sync(void *stream);
 
@@ -224,8 +262,9 @@ int nnfft_gauss_legendre(int64_t n, double *tau_host, double *w_host);
  *   6 forward point evaluation (x)   7 adjoint cell moments (x)
  *   8 adjoint spread convolution     9 adjoint FFT
  *  10 adjoint gather convolution    11 adjoint point evaluation (v)
+ *  12 forward per-cell fold (v)      13 adjoint per-cell fold (x, with 1/phihat1)
  */
-#define NNFFT_NSTAGES 12
+#define NNFFT_NSTAGES 14
 typedef struct {
     double ms[16];      /* accumulated milliseconds per stage */
     int64_t count[16];  /* number of timed executions per stage */

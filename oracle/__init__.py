@@ -79,6 +79,8 @@ def _load():
         lib.orc_gauss_legendre.argtypes = [i64, dptr, dptr]
         lib.orc_sinc_gl.argtypes = [i64, i64, i64, dptr, dptr, i64, dptr, lptr, i64, dptr,
                                     ctypes.c_int]
+        lib.orc_sinc_cc.argtypes = [i64, i64, i64, dptr, dptr, i64, dptr, lptr, i64, dptr,
+                                    ctypes.c_int]
         lib.orc_omega_sinh.argtypes = [ctypes.c_double, ctypes.c_double]
         lib.orc_omega_sinh.restype = ctypes.c_double
         lib.orc_omega_sinh_hat.argtypes = [ctypes.c_double, ctypes.c_double]
@@ -195,6 +197,22 @@ def sinc_gl(N, a, c, b, n=None, rows=None, nthreads=0):
     nout = nr if r is not None else b.size
     out = np.zeros(nout, dtype=np.complex128)
     rc = lib.orc_sinc_gl(int(N), n, a.size, _d(a), _d(cc), b.size, _d(b),
+                         r.ctypes.data_as(lptr) if r is not None else None, nr,
+                         _d(out.view(np.float64)), int(nthreads))
+    assert rc == 0
+    return out
+
+
+def sinc_cc(N, a, c, b, n=None, rows=None, nthreads=0):
+    """Algorithm 6.1 with the Clenshaw-Curtis rule (z_j = cos(j pi/n), eq. (wk=) weights,
+    n = 4N default), each step a direct sum."""
+    lib = _load()
+    n = 4 * int(N) if n is None else int(n)
+    a = _real(a); b = _real(b); cc = _cplx(c)
+    r, nr = _rows(rows)
+    nout = nr if r is not None else b.size
+    out = np.zeros(nout, dtype=np.complex128)
+    rc = lib.orc_sinc_cc(int(N), n, a.size, _d(a), _d(cc), b.size, _d(b),
                          r.ctypes.data_as(lptr) if r is not None else None, nr,
                          _d(out.view(np.float64)), int(nthreads))
     assert rc == 0

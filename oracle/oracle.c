@@ -22,9 +22,9 @@
  *                       the sinh-type window of Example 2.1 and its Fourier
  *                       transform, eq. (hatomegasinh), with the I1 power series.
  *   - orc_make_params   N*, N1, N2, a, beta_j of Section 2 (eq. (consta), the
- *                       rescaling after eq. (condvk)) and Section 4, under the
- *                       readings listed in the design doc (N1 rounded up to even,
- *                       N2 rounded up to an even 5-smooth length).
+ *                       rescaling after eq. (condvk)) and Section 4, with two
+ *                       choices the paper leaves open: N1 rounded up to even and
+ *                       N2 rounded up to an even 5-smooth length.
  *   - orc_nnfft_alg22 / orc_nnfft_alg22_adjoint
  *                       Algorithm 2.2 step by step (a naive DFT for step 3) and
  *                       its exact transpose.
@@ -32,6 +32,8 @@
  *   - orc_cc_weights, orc_cc_bound
  *                       Clenshaw-Curtis weights, eq. (wk=), and the bound of
  *                       Theorem 5.3.
+ *   - orc_sinc_cc       Algorithm 6.1 with the Clenshaw-Curtis rule, steps 1-3
+ *                       as direct sums.
  *
  * Equations are cited by their LaTeX labels, e.g. eq. (gell).
  * Complex arrays are interleaved (re, im) doubles.  A centered index set
@@ -343,7 +345,8 @@ int orc_make_params(i64 N, double sigma1, double sigma2, int m1, int m2, orc_par
 /* Algorithm 2.2 (NNFFT), step by step, for v_k, x_j in [-1/2,1/2]:           */
 /*   rescale v*_k = (N/N*) v_k so that N v_k = N* v*_k (after eq. (condvk));      */
 /*   step 1: g_l = (1/N1) sum_k f_k phi1(l/N1 - v*_k), l in I_{K1} (eq. (gell)) */
-/*   step 2: ghat_l = g_l / phi2hat(l)  (phi2hat at the integer l; see DESIGN) */
+/*   step 2: ghat_l = g_l / phi2hat(l)  (phi2hat at the integer l, as step 2 and  */
+/*           the proof of Theorem 3.5 use it; step 0 lists phi2hat(l/a))         */
 /*   step 3: h_s = (1/N2) sum_l ghat_l exp(-2 pi i l s / N2), s in I_{N2}      */
 /*           (a naive DFT with the index product reduced mod N2 in integers)   */
 /*   step 4: s1_j = sum_{s in I''(x_j)} h_s phi2(x_j/sigma1 - s/N2)            */
@@ -531,4 +534,32 @@ double orc_cc_constant(void) {
 double orc_cc_bound(double N, double nu) {
     double e = exp(1.0), C = orc_cc_constant();
     return 36.0 * (1.0 + exp(-2.0 * C * N)) / (35.0 * (e * e - 1.0)) * exp(-N * (nu - C));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 6.1 with the Clenshaw-Curtis rule, every sum taken directly:    */
+/*   z_j = cos(j pi/n), w_j of eq. (wk=), j = 0..n;                          */
+/*   step 1: g_j     = sum_k c_k exp(-pi i N z_j a_k)                         */
+/*   step 2: alpha_j = w_j g_j                                                */
+/*   step 3: h_l     = sum_j alpha_j exp(+pi i N z_j b_l)                     */
+/* The exponents are written as exp(-+2 pi i N (z_j/2) .), the form of       */
+/* orc_expsum.                                                                */
+/* ------------------------------------------------------------------------ */
+int orc_sinc_cc(i64 N, i64 n, i64 L1, const double *a, const double *c,
+                i64 L2, const double *b, const i64 *rows, i64 nrows,
+                double *h, int nthreads) {
+    if (n < 1) return 1;
+    double *z = (double *)malloc(sizeof(double) * (n + 1));
+    double *w = (double *)malloc(sizeof(double) * (n + 1));
+    double *g = (double *)malloc(sizeof(double) * 2 * (n + 1));
+    if (!z || !w || !g) { free(z); free(w); free(g); return 2; }
+    orc_cc_weights(n, z, w);
+    for (i64 j = 0; j <= n; ++j) z[j] *= 0.5;
+    /* g_j = sum_k c_k exp(-2 pi i N a_k (z_j/2)) */
+    orc_expsum(N, L1, a, c, n + 1, z, -1, NULL, 0, g, nthreads);
+    for (i64 j = 0; j <= n; ++j) { g[2 * j] *= w[j]; g[2 * j + 1] *= w[j]; }
+    /* h_l = sum_j alpha_j exp(+2 pi i N (z_j/2) b_l) */
+    orc_expsum(N, n + 1, z, g, L2, b, +1, rows, nrows, h, nthreads);
+    free(z); free(w); free(g);
+    return 0;
 }

@@ -36,7 +36,7 @@ double omega_sinh_hat(double v, double beta) {
     return pref * ::j1(r) / r;
 }
 
-static bool smooth5(int64_t n) {
+bool smooth5(int64_t n) {
     if (n <= 0) return false;
     const int64_t p[3] = {2, 3, 5};
     for (int i = 0; i < 3; ++i)

@@ -55,6 +55,8 @@ int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
 // n-point Gauss-Legendre rule on [-1/2, 1/2] (Newton on the Legendre recurrence).
 void gauss_legendre(int64_t n, double *tau, double *w);
 
+// n has no prime factor above 5.
+bool smooth5(int64_t n);
 // N2 = n1 * n2 with n1, n2 <= maxf and 5-smooth, as square as possible; radix lists.
 bool split_fft(int64_t N2, int maxf, int *n1, int *n2);
 int radices(int n, int *r, int maxr);

@@ -126,11 +126,11 @@ cudaError_t launch_sorted_coords_split(const double *nodes, const int *perm,
 cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
 
 // ---- kern_spread.cu ---------------------------------------------------------------
-// Cell moments of vals over the sorted points (per work item into P), then the
-// per-cell fold (item sum and, with S.rfit, the 1/phihat1 factor) into Pc.
+// Cell moments of vals over the sorted points, one set per work item, into P; the
+// per-cell fold (launch_cell_fold: item sum and, with S.rfit, the 1/phihat1 factor)
+// follows as its own launch.
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, void *Pc,
-                           cudaStream_t s);
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *scale,
                                long long scale_off, long long scale_len, int N2, void *out,
@@ -174,6 +174,11 @@ template <typename Real>
 cudaError_t launch_scale_by_weights(void *vals, const double *w, int n, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_t s);
+// Clenshaw-Curtis weights (Algorithm 5.4): even extension of length 2n into x (double2),
+// then, after a length-2n FFT of x into X, the weights w[0..n] and nodes +-cos(k pi/n)/2.
+cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s);
+cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half_z,
+                             double *neg_half_z, cudaStream_t s);
 cudaError_t launch_negate(const double *in, int n, double *out, cudaStream_t s);
 
 }  // namespace nnfft

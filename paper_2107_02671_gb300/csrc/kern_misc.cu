@@ -1,6 +1,7 @@
 // kern_misc.cu -- small elementwise kernels of the fast sinc transform
 // (Algorithm 6.1): real <-> complex packing, the step-2 product alpha_j = w_j g_j,
-// and the node reflection tau -> -tau of NNFFT #1.
+// the node reflection tau -> -tau, and the two ends of the Clenshaw-Curtis weight
+// computation (Algorithm 5.4) around a length-2n FFT.
 #include "internal.h"
 
 namespace nnfft {
@@ -41,6 +42,43 @@ __global__ void k_negate(const double *__restrict__ in, int n, double *__restric
     out[i] = -in[i];
 }
 
+// Clenshaw-Curtis weights, eq. (wk=), through Algorithm 5.4's DCT-I: with
+//   x_j = eps(j)^2 * 2/(1 - j^2)  for even j <= n,  x_j = 0 for odd j
+// (eps(0)^2 = eps(n)^2 = 1/2, else 1), w_k = eps(k)^2/n * sum_{j=0}^{n} x_j cos(j k pi/n).
+// The sum is the DCT-I of x; it is read off the FFT of the even extension of
+// length 2n, X_k = x_0 + (-1)^k x_n + 2 sum_{0<j<n} x_j cos(pi j k / n).
+__device__ __forceinline__ double cc_x(long long j, long long n) {
+    if (j & 1) return 0.0;
+    const double h = (double)(j / 2);
+    const double e2 = (j == 0 || j == n) ? 0.5 : 1.0;
+    return e2 * 2.0 / (1.0 - 4.0 * h * h);
+}
+
+__global__ void k_cc_extend(long long n, double2 *__restrict__ x) {
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= 2 * n) return;
+    const long long jj = j <= n ? j : 2 * n - j;
+    x[j] = make_double2(cc_x(jj, n), 0.0);
+}
+
+// w_k, k = 0..n, and the nodes z_k / 2 = cos(k pi / n) / 2 (exactly antisymmetric)
+__global__ void k_cc_finish(long long n, const double2 *__restrict__ X, double *__restrict__ w,
+                            double *__restrict__ half_z, double *__restrict__ neg_half_z) {
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k > n) return;
+    const double ek2 = (k == 0 || k == n) ? 0.5 : 1.0;
+    const double xn = cc_x(n, n);
+    const double dct = 0.5 * (X[k].x + cc_x(0, n) + ((k & 1) ? -xn : xn));
+    w[k] = ek2 * dct / (double)n;
+    // cos(k pi / n) from the half of the range nearer to zero, mirrored for k > n/2
+    const long long kk = 2 * k <= n ? k : n - k;
+    double z = 0.5 * cospi((double)kk / (double)n);
+    if (2 * k == n) z = 0.0;
+    if (kk != k) z = -z;
+    half_z[k] = z;
+    neg_half_z[k] = -z;
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 std::atomic<long long> g_launches{0};
@@ -75,6 +113,19 @@ cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_
 cudaError_t launch_negate(const double *in, int n, double *out, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     k_negate<<<cdiv(n, 256), 256, 0, s>>>(in, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s) {
+    k_cc_extend<<<cdiv(2 * n, 256), 256, 0, s>>>(n, static_cast<double2 *>(x));
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half_z,
+                             double *neg_half_z, cudaStream_t s) {
+    k_cc_finish<<<cdiv(n + 1, 256), 256, 0, s>>>(n, static_cast<const double2 *>(X), w, half_z,
+                                                  neg_half_z);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -390,16 +390,14 @@ cudaError_t launch_cell_fold(const SideK<Real> &S, const void *P, void *Pc, cuda
 }
 
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, void *Pc,
-                           cudaStream_t s) {
-    if (S.max_items > 0) {
-        const int blocks = cdiv((long long)S.max_items * 32, 256);
-        const C2<Real> *v = static_cast<const C2<Real> *>(vals);
-        C2<Real> *Pp = static_cast<C2<Real> *>(P);
-        NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
-        count_launches(1);
-    }
-    return launch_cell_fold<Real>(S, P, Pc, s);
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s) {
+    if (S.max_items <= 0) return cudaSuccess;
+    const int blocks = cdiv((long long)S.max_items * 32, 256);
+    const C2<Real> *v = static_cast<const C2<Real> *>(vals);
+    C2<Real> *Pp = static_cast<C2<Real> *>(P);
+    NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <typename Real>
@@ -443,7 +441,7 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
 }
 
 #define NNFFT_INST(R)                                                                      \
-    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *, void *, \
+    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *,         \
                                            cudaStream_t);                                  \
     template cudaError_t launch_spread_conv<R>(const SideK<R> &, const void *, const R *,  \
                                                long long, long long, int, void *,         \

@@ -385,6 +385,9 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
     {
         StageTimer t(p, 2);
         NN_CUDA(launch_moments_df(sv, f, p->P, st), "spread moments");
+    }
+    {
+        StageTimer t(p, 12);
         NN_CUDA(launch_cell_fold_df(sv, tv, p->P, p->Q, st), "cell fold");
     }
     {
@@ -423,6 +426,9 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
     {
         StageTimer t(p, 7);
         NN_CUDA(launch_moments_df(sx, g, p->P, st), "adjoint spread moments");
+    }
+    {
+        StageTimer t(p, 13);
         NN_CUDA(launch_cell_fold_df(sx, tx, p->P, p->Q, st), "adjoint cell fold");
     }
     {
@@ -457,7 +463,11 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 2);
-        NN_CUDA(launch_moments<Real>(sv, f, p->P, p->Q, st), "spread moments");
+        NN_CUDA(launch_moments<Real>(sv, f, p->P, st), "spread moments");
+    }
+    {
+        StageTimer t(p, 12);
+        NN_CUDA(launch_cell_fold<Real>(sv, p->P, p->Q, st), "cell fold");
     }
     {
         StageTimer t(p, 3);
@@ -491,7 +501,11 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 7);
-        NN_CUDA(launch_moments<Real>(sx, g, p->P, p->Q, st), "adjoint spread moments");
+        NN_CUDA(launch_moments<Real>(sx, g, p->P, st), "adjoint spread moments");
+    }
+    {
+        StageTimer t(p, 13);
+        NN_CUDA(launch_cell_fold<Real>(sx, p->P, p->Q, st), "adjoint cell fold");
     }
     {
         StageTimer t(p, 8);
@@ -864,19 +878,26 @@ int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host) {
 }  // extern "C"
 
 // =====================================================================================
-// Fast sinc transform (Algorithm 6.1 with a Gauss-Legendre rule)
+// Fast sinc transform (Algorithm 6.1) with a Gauss-Legendre or a Clenshaw-Curtis rule
 // =====================================================================================
 namespace {
 
+// One quadrature rule (t_j, w_j) with sum_j w_j exp(-2 pi i N t_j x) ~ sinc(N pi x):
+//   GL: the n-point Gauss-Legendre rule on [-1/2, 1/2];
+//   CC: t_j = cos(j pi / n) / 2, j = 0..n, with the weights of eq. (wk=) (Section 5).
+// NNFFT #1 evaluates g_j at the nodes x1 (= -t for GL, +t for CC) and NNFFT #2 sums
+// alpha_j = w_j g_j from the nodes v2 (= +t for GL, -t for CC); for CC this is the
+// sign convention of Algorithm 6.1, for the symmetric GL rule both conventions agree.
 struct SincPlan {
-    nnfft_plan_t p1 = nullptr, p2 = nullptr;   // #1: a -> -tau,  #2: tau -> b
-    double *tau = nullptr, *negtau = nullptr, *w = nullptr;
+    nnfft_plan_t p1 = nullptr, p2 = nullptr;
+    int64_t nq = 0;                           // number of quadrature nodes
+    double *x1 = nullptr, *v2 = nullptr, *w = nullptr;
     void *cbuf = nullptr, *gbuf = nullptr, *hbuf = nullptr;
     bool nodes_fixed = false;
     cudaStream_t stream = nullptr;
 };
 
-using SincKey = std::tuple<int64_t, int64_t, int64_t, int, int, uintptr_t>;
+using SincKey = std::tuple<int64_t, int64_t, int64_t, int, int, int, int64_t, uintptr_t>;
 std::mutex g_sinc_mu;
 std::map<SincKey, SincPlan *> g_sinc;
 
@@ -885,8 +906,8 @@ void sinc_free(SincPlan *s) {
     cudaStreamSynchronize(s->stream);
     nnfft_destroy(s->p1);
     nnfft_destroy(s->p2);
-    cudaFree(s->tau);
-    cudaFree(s->negtau);
+    cudaFree(s->x1);
+    cudaFree(s->v2);
     cudaFree(s->w);
     cudaFree(s->cbuf);
     cudaFree(s->gbuf);
@@ -894,46 +915,121 @@ void sinc_free(SincPlan *s) {
     delete s;
 }
 
-int sinc_make(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, cudaStream_t st,
-              SincPlan **out) {
+// Number of quadrature intervals / nodes of a rule: GL n nodes (default 2N); CC n
+// intervals (default 4N, Algorithm 6.1's n >= 4N) rounded up to a 5-smooth n so that
+// the DCT-I runs as one FFT of length 2n; n + 1 nodes.
+int sinc_rule_size(int rule, int64_t N, int64_t n_req, int64_t *n_out, int64_t *nodes_out) {
+    if (rule == SINC_RULE_GL) {
+        const int64_t n = n_req > 0 ? n_req : 2 * N;
+        *n_out = n;
+        *nodes_out = n;
+        return NNFFT_OK;
+    }
+    if (rule != SINC_RULE_CC) return fail(NNFFT_EINVAL, "unknown quadrature rule");
+    int64_t n = n_req > 0 ? n_req : 4 * N;
+    if (n < 2) n = 2;
+    while (!hm::smooth5(n)) ++n;
+    if (2 * n > (int64_t)FFT_MAX_FACTOR * FFT_MAX_FACTOR)
+        return fail(NNFFT_EINVAL, "Clenshaw-Curtis rule too long (2n > 2^20)");
+    *n_out = n;
+    *nodes_out = n + 1;
+    return NNFFT_OK;
+}
+
+// Clenshaw-Curtis weights and nodes on the device (Algorithm 5.4 with the DCT-I taken
+// from a length-2n FFT of the even extension).  w, half_z, neg_half_z: n + 1 doubles.
+int cc_rule_device(int64_t n, double *w, double *half_z, double *neg_half_z, cudaStream_t st) {
+    const int64_t L = 2 * n;
+    FftPlanDev F{};
+    int n1 = 0, n2 = 0;
+    if (!hm::split_fft(L, FFT_MAX_FACTOR, &n1, &n2))
+        return fail(NNFFT_EINVAL, "Clenshaw-Curtis FFT length not factorable");
+    F.N2 = (int)L;
+    F.n1 = n1;
+    F.n2 = n2;
+    F.nr1 = hm::radices(n1, F.r1, FFT_MAX_STAGES);
+    F.nr2 = hm::radices(n2, F.r2, FFT_MAX_STAGES);
+    if (F.nr1 < 0 || F.nr2 < 0) return fail(NNFFT_EINVAL, "FFT factorisation failed");
+    void *t1 = nullptr, *t2 = nullptr, *tN = nullptr, *x = nullptr, *y = nullptr, *X = nullptr;
+    auto release = [&]() {
+        cudaFree(t1); cudaFree(t2); cudaFree(tN); cudaFree(x); cudaFree(y); cudaFree(X);
+    };
+    cudaError_t e = cudaSuccess;
+    const std::vector<double> w1 = twiddles(n1), w2 = twiddles(n2), wN = twiddles(L);
+    if (e == cudaSuccess) e = cudaMalloc(&t1, w1.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&t2, w2.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&tN, wN.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&x, (size_t)L * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)L * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMalloc(&X, (size_t)L * sizeof(double2));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t1, w1.data(), w1.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t2, w2.data(), w2.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tN, wN.data(), wN.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+    F.tw1 = t1;
+    F.tw2 = t2;
+    F.twN = tN;
+    if (e == cudaSuccess) e = launch_cc_extend(n, x, st);
+    if (e == cudaSuccess) e = launch_fft<double>(F, x, y, X, -1, st);
+    if (e == cudaSuccess) e = launch_cc_finish(n, X, w, half_z, neg_half_z, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    release();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? NNFFT_ENOMEM : NNFFT_ECUDA,
+                    std::string("Clenshaw-Curtis weights: ") + cudaGetErrorString(e));
+    }
+    return NNFFT_OK;
+}
+
+int sinc_make(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, int rule, int64_t n_req,
+              cudaStream_t st, SincPlan **out) {
+    int64_t n = 0, nq = 0;
+    int rc = sinc_rule_size(rule, N, n_req, &n, &nq);
+    if (rc) return rc;
     SincPlan *s = new SincPlan();
     s->stream = st;
-    const int64_t n = 2 * N;
-    int rc = nnfft_plan(&s->p1, N, L1, n, 2.0, 2.0, m, m, dtype, st);
-    if (!rc) rc = nnfft_plan(&s->p2, N, n, L2, 2.0, 2.0, m, m, dtype, st);
+    s->nq = nq;
+    rc = nnfft_plan(&s->p1, N, L1, nq, 2.0, 2.0, m, m, dtype, st);
+    if (!rc) rc = nnfft_plan(&s->p2, N, nq, L2, 2.0, 2.0, m, m, dtype, st);
     if (rc) { sinc_free(s); return rc; }
-    std::vector<double> tau((size_t)n), w((size_t)n), neg((size_t)n);
-    hm::gauss_legendre(n, tau.data(), w.data());
-    for (int64_t j = 0; j < n; ++j) neg[(size_t)j] = -tau[(size_t)j];
     const size_t cs = 2 * (dtype == NNFFT_C128 ? sizeof(double) : sizeof(float));
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&s->tau, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&s->negtau, sizeof(double) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&s->w, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->x1, sizeof(double) * nq);
+    if (e == cudaSuccess) e = cudaMalloc(&s->v2, sizeof(double) * nq);
+    if (e == cudaSuccess) e = cudaMalloc(&s->w, sizeof(double) * nq);
     if (e == cudaSuccess) e = cudaMalloc(&s->cbuf, cs * (size_t)std::max<int64_t>(L1, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&s->gbuf, cs * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gbuf, cs * (size_t)nq);
     if (e == cudaSuccess) e = cudaMalloc(&s->hbuf, cs * (size_t)std::max<int64_t>(L2, 1));
-    if (e == cudaSuccess) e = cudaMemcpy(s->tau, tau.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->negtau, neg.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(s->w, w.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && rule == SINC_RULE_GL) {
+        std::vector<double> tau((size_t)nq), w((size_t)nq), neg((size_t)nq);
+        hm::gauss_legendre(nq, tau.data(), w.data());
+        for (int64_t j = 0; j < nq; ++j) neg[(size_t)j] = -tau[(size_t)j];
+        e = cudaMemcpy(s->x1, neg.data(), sizeof(double) * nq, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->v2, tau.data(), sizeof(double) * nq, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->w, w.data(), sizeof(double) * nq, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         sinc_free(s);
         return fail(e == cudaErrorMemoryAllocation ? NNFFT_ENOMEM : NNFFT_ECUDA,
                     std::string("sinc plan: ") + cudaGetErrorString(e));
     }
+    if (rule == SINC_RULE_CC && (rc = cc_rule_device(n, s->w, s->x1, s->v2, st))) {
+        sinc_free(s);
+        return rc;
+    }
     *out = s;
     return NNFFT_OK;
 }
 
 template <typename Real>
-int sinc_run(SincPlan *s, int64_t N, int64_t L1, int64_t L2, const double *a, const void *c,
-             const double *b, void *h, int is_complex) {
+int sinc_run(SincPlan *s, int64_t L1, int64_t L2, const double *a, const void *c, const double *b,
+             void *h, int is_complex) {
     cudaStream_t st = s->stream;
-    const int n = (int)(2 * N);
+    const int nq = (int)s->nq;
     int rc;
-    // NNFFT #1: g_j = sum_k c_k e^{-2 pi i N a_k (-tau_j)} = sum_k c_k e^{+2 pi i N tau_j a_k}
-    if ((rc = nnfft_set_nodes(s->p1, a, s->nodes_fixed ? nullptr : s->negtau))) return rc;
+    // step 1, NNFFT #1: g_j = sum_k c_k e^{-2 pi i N a_k x1_j}
+    if ((rc = nnfft_set_nodes(s->p1, a, s->nodes_fixed ? nullptr : s->x1))) return rc;
     const void *cin = c;
     if (!is_complex) {
         NN_CUDA(launch_real_to_complex<Real>(static_cast<const Real *>(c), (int)L1, s->cbuf, st),
@@ -942,9 +1038,9 @@ int sinc_run(SincPlan *s, int64_t N, int64_t L1, int64_t L2, const double *a, co
     }
     if ((rc = nnfft_exec(s->p1, cin, s->gbuf))) return rc;
     // step 2: alpha_j = w_j g_j
-    NN_CUDA(launch_scale_by_weights<Real>(s->gbuf, s->w, n, st), "sinc weights");
-    // NNFFT #2: h_l = sum_j alpha_j e^{-2 pi i N tau_j b_l}
-    if ((rc = nnfft_set_nodes(s->p2, s->nodes_fixed ? nullptr : s->tau, b))) return rc;
+    NN_CUDA(launch_scale_by_weights<Real>(s->gbuf, s->w, nq, st), "sinc weights");
+    // step 3, NNFFT #2: h_l = sum_j alpha_j e^{-2 pi i N v2_j b_l}
+    if ((rc = nnfft_set_nodes(s->p2, s->nodes_fixed ? nullptr : s->v2, b))) return rc;
     s->nodes_fixed = true;
     if (is_complex) {
         if ((rc = nnfft_exec(s->p2, s->gbuf, h))) return rc;
@@ -956,33 +1052,80 @@ int sinc_run(SincPlan *s, int64_t N, int64_t L1, int64_t L2, const double *a, co
     return NNFFT_OK;
 }
 
+int sinc_get(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, int rule, int64_t n,
+             cudaStream_t st, SincPlan **out) {
+    std::lock_guard<std::mutex> lk(g_sinc_mu);
+    SincKey key{N, L1, L2, m, (int)dtype, rule, n, reinterpret_cast<uintptr_t>(st)};
+    auto it = g_sinc.find(key);
+    if (it != g_sinc.end()) {
+        *out = it->second;
+        return NNFFT_OK;
+    }
+    SincPlan *s = nullptr;
+    const int rc = sinc_make(N, L1, L2, m, dtype, rule, n, st, &s);
+    if (rc) return rc;
+    g_sinc[key] = s;
+    *out = s;
+    return NNFFT_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
-int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, const double *a_dev,
-              const void *c_dev, const double *b_dev, void *h_dev, int is_complex, void *stream) {
-    if (N < 1 || L1 < 0 || L2 < 0) return fail(NNFFT_EINVAL, "invalid sinc sizes");
+int sinc_exec_rule(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, int rule,
+                   int64_t n, const double *a_dev, const void *c_dev, const double *b_dev,
+                   void *h_dev, int is_complex, void *stream) {
+    if (N < 1 || L1 < 0 || L2 < 0 || n < 0) return fail(NNFFT_EINVAL, "invalid sinc sizes");
     if ((L1 > 0 && (!a_dev || !c_dev)) || (L2 > 0 && (!b_dev || !h_dev)))
         return fail(NNFFT_EINVAL, "null data pointer");
     if (dtype != NNFFT_C64 && dtype != NNFFT_C128) return fail(NNFFT_EINVAL, "unknown dtype");
+    if (rule != SINC_RULE_GL && rule != SINC_RULE_CC) return fail(NNFFT_EINVAL, "unknown quadrature rule");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     SincPlan *s = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_sinc_mu);
-        SincKey key{N, L1, L2, m, (int)dtype, reinterpret_cast<uintptr_t>(st)};
-        auto it = g_sinc.find(key);
-        if (it == g_sinc.end()) {
-            int rc = sinc_make(N, L1, L2, m, dtype, st, &s);
-            if (rc) return rc;
-            g_sinc[key] = s;
-        } else {
-            s = it->second;
-        }
-    }
+    int rc = sinc_get(N, L1, L2, m, dtype, rule, n, st, &s);
+    if (rc) return rc;
     if (L2 == 0) return NNFFT_OK;
-    return dtype == NNFFT_C128 ? sinc_run<double>(s, N, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex)
-                               : sinc_run<float>(s, N, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex);
+    return dtype == NNFFT_C128 ? sinc_run<double>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex)
+                               : sinc_run<float>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex);
+}
+
+int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, const double *a_dev,
+              const void *c_dev, const double *b_dev, void *h_dev, int is_complex, void *stream) {
+    return sinc_exec_rule(N, L1, L2, m, dtype, SINC_RULE_GL, 0, a_dev, c_dev, b_dev, h_dev,
+                          is_complex, stream);
+}
+
+int sinc_quadrature(int rule, int64_t N, int64_t n, double *t_host, double *w_host,
+                    int64_t *nodes_out) {
+    if (N < 1 || n < 0) return fail(NNFFT_EINVAL, "invalid sizes");
+    int64_t nn = 0, nq = 0;
+    int rc = sinc_rule_size(rule, N, n, &nn, &nq);
+    if (rc) return rc;
+    if (nodes_out) *nodes_out = nq;
+    if (!t_host || !w_host) return NNFFT_OK;
+    if (rule == SINC_RULE_GL) {
+        hm::gauss_legendre(nq, t_host, w_host);
+        return NNFFT_OK;
+    }
+    int dev = 0;
+    if (cudaGetDeviceCount(&dev) != cudaSuccess || dev == 0) {
+        cudaGetLastError();
+        return fail(NNFFT_ECUDA, "no CUDA device (the Clenshaw-Curtis weights are computed on the GPU)");
+    }
+    double *d = nullptr;
+    NN_CUDA(cudaMalloc(&d, sizeof(double) * 3 * (size_t)nq), "quadrature buffers");
+    rc = cc_rule_device(nn, d, d + nq, d + 2 * nq, nullptr);
+    cudaError_t e = cudaSuccess;
+    if (!rc) e = cudaMemcpy(t_host, d + nq, sizeof(double) * nq, cudaMemcpyDeviceToHost);
+    if (!rc && e == cudaSuccess) e = cudaMemcpy(w_host, d, sizeof(double) * nq, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NNFFT_ECUDA, std::string("quadrature copy: ") + cudaGetErrorString(e));
+    }
+    return NNFFT_OK;
 }
 
 int sinc_sync(void *stream) {

@@ -24,7 +24,8 @@ _CODES = {0: "OK", 1: "EINVAL", 2: "ERANGE", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEO
 
 
 STAGES = ("nodes_v", "nodes_x", "fwd_moments", "fwd_spread_conv", "fwd_fft", "fwd_gather_conv",
-          "fwd_eval", "adj_moments", "adj_spread_conv", "adj_fft", "adj_gather_conv", "adj_eval")
+          "fwd_eval", "adj_moments", "adj_spread_conv", "adj_fft", "adj_gather_conv", "adj_eval",
+          "fwd_cell_fold", "adj_cell_fold")
 
 
 class Timing(ctypes.Structure):
@@ -86,6 +87,9 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_sync.argtypes = [vp]
         lib.nnfft_destroy.argtypes = [vp]
         lib.sinc_exec.argtypes = [i64, i64, i64, cint, cint, vp, vp, vp, vp, cint, vp]
+        lib.sinc_exec_rule.argtypes = [i64, i64, i64, cint, cint, cint, i64, vp, vp, vp, vp, cint,
+                                       vp]
+        lib.sinc_quadrature.argtypes = [cint, i64, i64, vp, vp, P(i64)]
         lib.sinc_sync.argtypes = [vp]
         lib.sinc_release.argtypes = []
         lib.nnfft_gauss_legendre.argtypes = [i64, vp, vp]
@@ -268,12 +272,36 @@ class Plan:
             pass
 
 
-def sinc(N, a, c, b, m=8, out=None, stream=None):
-    """Fast sinc transform (Algorithm 6.1, Gauss-Legendre rule with 2N nodes).
+SINC_RULES = {"gl": 0, "cc": 1}
+
+
+def _rule_code(rule):
+    try:
+        return SINC_RULES[rule]
+    except KeyError:
+        raise ValueError(f"unknown quadrature rule {rule!r} (use 'gl' or 'cc')") from None
+
+
+def sinc_quadrature(rule, N, n=0):
+    """The quadrature rule (t, w) that sinc() uses: 'gl' (n nodes, default 2N) or 'cc'
+    (nodes cos(j pi/n)/2, j = 0..n, default n = 4N, weights from the GPU)."""
+    lib = load_library()
+    cnt = ctypes.c_int64(0)
+    _check(lib.sinc_quadrature(_rule_code(rule), int(N), int(n), None, None, ctypes.byref(cnt)))
+    t = np.zeros(cnt.value); w = np.zeros(cnt.value)
+    _check(lib.sinc_quadrature(_rule_code(rule), int(N), int(n), t.ctypes.data, w.ctypes.data,
+                               ctypes.byref(cnt)))
+    return t, w
+
+
+def sinc(N, a, c, b, m=8, out=None, stream=None, rule="gl", n=0):
+    """Fast sinc transform (Algorithm 6.1).
 
     a: L1 float64 CUDA nodes, c: L1 coefficients (float64/float32 real or
     complex128/complex64), b: L2 float64 CUDA targets.  Returns h (L2) of c's type.
-    fp64 types use the fp64 path, fp32 types the fp32 path.
+    fp64 types use the fp64 path, fp32 types the fp32 path.  rule 'gl': n-point
+    Gauss-Legendre (n = 0: 2N); rule 'cc': Clenshaw-Curtis with n + 1 Chebyshev
+    nodes (n = 0: 4N, rounded up to 5-smooth).
     """
     import torch
     lib = load_library()
@@ -287,8 +315,8 @@ def sinc(N, a, c, b, m=8, out=None, stream=None):
     if out is None:
         out = torch.empty(L2, dtype=c.dtype, device=b.device)
     po = _dev_tensor(out, c.dtype, L2, "out")
-    _check(lib.sinc_exec(int(N), int(L1), int(L2), int(m), code, pa, pc, pb, po, int(is_complex),
-                         _stream_ptr(stream)))
+    _check(lib.sinc_exec_rule(int(N), int(L1), int(L2), int(m), code, _rule_code(rule), int(n),
+                              pa, pc, pb, po, int(is_complex), _stream_ptr(stream)))
     return out
 
 

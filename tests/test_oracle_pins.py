@@ -310,3 +310,55 @@ def test_cc_sinc_error_below_theorem_5_3(N, nu):
     approx = (w[None, :] * np.exp(-1j * np.pi * N * z[None, :] * x[:, None])).sum(1)
     exact = np.array([oracle.sinc_Npi(N, t, 0.0) for t in x])
     assert np.max(np.abs(approx - exact)) <= oracle.cc_bound(N, nu) + 1e-14
+
+
+# --------------------------------------------------------------------------------------
+# Algorithm 6.1 with the Clenshaw-Curtis rule (steps 1-3 as direct sums)
+# --------------------------------------------------------------------------------------
+def test_cc_weights_n4_textbook():
+    """n = 4: the Clenshaw-Curtis weights on [-1,1] are 1/15, 8/15, 12/15, 8/15, 1/15;
+    the rule of eq. (wk=) carries the factor 1/2 of (1/2) int_{-1}^{1}."""
+    z, w = oracle.cc_weights(4)
+    assert np.max(np.abs(w - np.array([1, 8, 12, 8, 1]) / 30)) < 1e-15
+    assert np.max(np.abs(z - np.array([1, np.sqrt(0.5), 0, -np.sqrt(0.5), -1]))) < 1e-15
+
+
+@pytest.mark.parametrize("N,nu", [(16, 4), (32, 4), (64, 4), (32, 6)])
+def test_sinc_cc_within_theorem_5_3(N, nu):
+    """|h_CC - h| <= (Theorem 5.3 bound) * sum |c_k| + rounding, with b_l = l/N and
+    L1 = N/2 as in the Fig. 6.1 experiment."""
+    rng = np.random.default_rng(N + nu)
+    a = rng.uniform(-0.5, 0.5, N // 2)
+    b = np.arange(-(N // 2), N - N // 2) / N
+    c = rng.standard_normal(N // 2) + 1j * rng.standard_normal(N // 2)
+    h = oracle.sinc_cc(N, a, c, b, n=nu * N)
+    d = oracle.sinc_direct(N, a, c, b)
+    err = np.max(np.abs(h - d)) / np.sum(np.abs(c))
+    assert err <= oracle.cc_bound(N, nu) + 1e-14
+
+
+def test_sinc_cc_single_coefficient_and_real_output():
+    """c = e_0: h(b) = sinc(N pi (b - a_0)) up to the quadrature error; real c gives a
+    real h because z_j = -z_{n-j} and w_j = w_{n-j}."""
+    N = 64
+    a = np.array([0.1234])
+    b = np.linspace(-0.5, 0.5, 101)
+    h = oracle.sinc_cc(N, a, np.array([1.0]), b)
+    exact = np.array([oracle.sinc_Npi(N, bb, a[0]) for bb in b])
+    assert np.max(np.abs(h - exact)) <= oracle.cc_bound(N, 4) + 1e-14
+    assert np.max(np.abs(h.imag)) <= 1e-14
+
+
+def test_sinc_cc_needs_both_steps():
+    """A rule with too few nodes (n = N, below Theorem 5.3's nu > C) misses the sinc by
+    far more than the n = 4N rule: the test above would catch a dropped weight or a
+    node scaled by 2 instead of 1/2."""
+    N = 64
+    rng = np.random.default_rng(5)
+    a = rng.uniform(-0.5, 0.5, 32)
+    b = rng.uniform(-0.5, 0.5, 40)
+    c = rng.standard_normal(32)
+    d = oracle.sinc_direct(N, a, c, b)
+    bad = np.max(np.abs(oracle.sinc_cc(N, a, c, b, n=N) - d)) / np.sum(np.abs(c))
+    good = np.max(np.abs(oracle.sinc_cc(N, a, c, b, n=4 * N) - d)) / np.sum(np.abs(c))
+    assert bad > 1e-3 and good < 1e-14
