@@ -109,7 +109,36 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2,
                double sigma1, double sigma2, int m1, int m2, nnfft_dtype dtype,
                void *stream);
 
-/* nnfft_plan_info: copy the derived parameters of a plan. */
+/*
+ * nnfft_batch_plan: one plan holding `count` independent NNFFT instances (the paper has no
+ * batched form; each instance is Algorithm 2.2 with its own N[i], M1[i], M2[i] and the
+ * shared sigma1, sigma2, m1, m2, dtype).  Every later call (set_nodes, exec, adjoint, the
+ * host-buffer forms, sync, timing) treats the instances' data as concatenated: v holds
+ * the M1[0] nodes of instance 0, then the M1[1] nodes of instance 1, ...; likewise x
+ * (M2), f and z (M1), y and g (M2).  Each call does all instances at once: one launch
+ * per stage, the node sort of all instances in one pass.  The window series of a side
+ * use one Chebyshev length for all instances (the largest any instance needs), so a
+ * batch result can differ from the single-instance plan's in the last bits.
+ * count >= 1; the totals sum(M1), sum(M2) must be <= 2^30.  Errors as nnfft_plan; an
+ * invalid instance gives EINVAL with its index in the message.
+ * nnfft_plan(N, M1, M2, ...) is nnfft_batch_plan with count = 1.
+ */
+int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
+                     const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
+                     nnfft_dtype dtype, void *stream);
+
+/* nnfft_batch_count: number of instances in the plan (1 for nnfft_plan). */
+int nnfft_batch_count(nnfft_plan_t p, int64_t *count);
+
+/* nnfft_batch_info: derived parameters of instance i (0 <= i < count; EINVAL otherwise). */
+int nnfft_batch_info(nnfft_plan_t p, int64_t i, nnfft_info *out);
+
+/*
+ * nnfft_plan_info: copy the derived parameters of a plan.  For a batch: M1, M2, K1, N1,
+ * N2, ncell1, ncell2 are sums over the instances (N2: total grid length), N, Nstar,
+ * fit_err1/2 and fft_n1/n2 maxima, D1/D2 the common degrees, the other fields those of
+ * instance 0.
+ */
 int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
 
 /*

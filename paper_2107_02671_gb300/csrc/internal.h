@@ -64,11 +64,14 @@ struct SideDf {
     const float2 *rfit;   // [ncell][NR] (hi, lo) of r_j / 2 (x side) or nullptr
 };
 
+// One instance's FFT of length N2 = n1 * n2 (four-step, radix lists r1, r2), on the
+// grid buffer elements [grid_base, grid_base + N2).
 struct FftDf {
     int N2, n1, n2;
     int nr1, nr2;
     int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
     const float4 *tw1, *tw2, *twN;   // exp(-2 pi i k / n) as (re.h, re.l, im.h, im.l)
+    long long grid_base;
 };
 
 struct FftPlanDev {
@@ -76,7 +79,60 @@ struct FftPlanDev {
     int nr1, nr2;
     int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
     const void *tw1, *tw2, *twN;   // C2<Real>: exp(-2 pi i k / n) for n = n1, n2, N2
+    long long grid_base;
 };
+
+// ---- instances -----------------------------------------------------------------
+// A plan holds one or more independent NNFFT instances (a batch).  On each node side
+// their points and cells are concatenated: instance i owns points [pt_off[i],
+// pt_off[i+1]) and cells [cell_base, cell_base + ncell); the point kernels, the sort
+// and the cell fold see one side with all cells.  The grid stage runs per instance,
+// one launch for all instances: block b belongs to the instance i with
+// blk[i] <= b < blk[i+1] and works on that instance's grid of length N2 at
+// grid_base in the concatenated grid buffers.
+
+// Node binning of one instance: u = node * uscale, cell key cell_base + floor(u) - c_lo.
+struct NodeInst {
+    double uscale;
+    long long c_lo;
+    int ncell, cell_base;
+};
+
+// Grid-stage geometry of one instance on one side.  CoefT: Real, or float2 (hi, lo)
+// pairs for split precision.
+template <typename CoefT> struct GridInst {
+    long long c_lo;                   // centered index of the instance's first cell
+    long long grid_base;              // first element of its grid buffer
+    long long scale_off, scale_len;   // scale index p + scale_off, valid below scale_len
+    const CoefT *coef;                // [2m][D] tap coefficients
+    const CoefT *scale;               // deconvolution factors (v side) or nullptr
+    const CoefT *rfit;                // [ncell][NR] 1/phihat1 fits (x side) or nullptr
+    int ncell, cell_base, N2, pad;
+};
+
+// One grid-stage launch over all instances.
+template <typename CoefT> struct GridLaunch {
+    const GridInst<CoefT> *inst;   // [ninst] device
+    const int *blk;                // [ninst + 1] device: first block of each instance
+    int ninst, nblocks, m, D;
+    bool fold;                     // gather: apply the instance's rfit (1/phihat1)
+};
+
+template <typename F> struct FftLaunch {
+    const F *inst;                 // [ninst] device
+    const int *blk1, *blk2;        // [ninst + 1] device: pass-1 blocks (n2 each), pass-2 (n1)
+    int ninst, nblk1, nblk2, max_n1, max_n2;
+};
+
+// Instance of block b: the largest i with blk[i] <= b (blk[0] = 0, increasing).
+__device__ __forceinline__ int block_instance(const int *blk, int ninst, int b) {
+    int lo = 0, hi = ninst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(blk + mid) <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 // ---- nnfft_host.cu (for the other translation units) -------------------------------
 // Record a status code and message for nnfft_last_error; returns code.
@@ -85,23 +141,17 @@ int report_error(int code, const std::string &msg);
 cudaStream_t plan_stream(nnfft_plan_t p);
 
 // ---- kern_nodes.cu ----------------------------------------------------------------
-cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,
-                             int ncell, uint32_t *keys, int *vals, int *status,
-                             cudaStream_t s);
-// Stable LSD radix sort of (keys, vals) by the low key_bits bits.  Uses the
-// *_alt buffers and hist (radix_sort_hist_len(n) ints) as scratch.
-// On return *keys_sorted / *vals_sorted point at whichever buffers hold the result.
-cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
-                             int *hist, int n, int key_bits, cudaStream_t s,
-                             uint32_t **keys_sorted, int **vals_sorted);
 size_t radix_sort_hist_len(int n);
 cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
                                 cudaStream_t s);
 // Fused step 0: keys, local coordinates (caller order, format yfmt: 0 float, 1 double,
 // 2 float pair) and the first radix pass's histogram in hist (radix_sort_hist_len ints).
-cudaError_t launch_node_keys_y(const double *nodes, int n, double uscale, long long c_lo,
-                               int ncell, uint32_t *keys, void *y_user, int yfmt, int *hist,
-                               int *status, cudaStream_t s);
+// With ninst > 1, pt_off [ninst + 1] (device) splits the points into instances and
+// tab [ninst] (device) gives each instance's binning; otherwise `one` applies to all.
+cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
+                               const long long *pt_off, const NodeInst *tab, int ninst,
+                               uint32_t *keys, void *y_user, int yfmt, int *hist, int *status,
+                               cudaStream_t s);
 // Stable LSD radix sort of the keys from launch_node_keys_y (values: the identity
 // permutation, generated in pass 0); the last pass also moves the ybytes-byte
 // coordinates: ys[sorted position] = y_user[original index].
@@ -109,21 +159,14 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
                              int *hist, int n, int key_bits, const void *y_user, void *ys,
                              int ybytes, cudaStream_t s, uint32_t **keys_sorted,
                              int **vals_sorted);
+// Work items (at most ITEM_CAP sorted points of one cell each) from the cell offsets:
+// one block for up to ITEMS_ONE_BLOCK_MAX cells, else three launches using scratch
+// (build_items_scratch_len(ncell) ints).
+constexpr int ITEMS_ONE_BLOCK_MAX = 65536;
 cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
                                      int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                                     cudaStream_t s);
-cudaError_t launch_build_items(const int *cell_off, int ncell, int *item_cnt, int *item_off,
-                               int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                               cudaStream_t s);
-template <typename Real>
-cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
-                                 const uint32_t *keys_sorted, int n, double uscale,
-                                 long long c_lo, Real *ys, int *status, cudaStream_t s);
-// same, but each coordinate stored as a float pair (hi, lo) with hi + lo = y to 2^-48
-cudaError_t launch_sorted_coords_split(const double *nodes, const int *perm,
-                                       const uint32_t *keys_sorted, int n, double uscale,
-                                       long long c_lo, float2 *ys, int *status, cudaStream_t s);
-cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
+                                     int *scratch, cudaStream_t s);
+size_t build_items_scratch_len(int ncell);
 
 // ---- kern_spread.cu ---------------------------------------------------------------
 // Cell moments of vals over the sorted points, one set per work item, into P; the
@@ -131,16 +174,22 @@ cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s
 // follows as its own launch.
 template <typename Real>
 cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s);
+// Spread convolution of every instance: cell sums Pc (all cells of the side) -> grid
+// buffers out (concatenated).  Gather convolution: grid buffers buf -> per-cell window
+// sums Q.  Block counts per instance: spread_blocks / gather_blocks.
 template <typename Real>
-cudaError_t launch_spread_conv(const SideK<Real> &S, const void *P, const Real *scale,
-                               long long scale_off, long long scale_len, int N2, void *out,
+cudaError_t launch_spread_conv(const GridLaunch<Real> &L, const void *Pc, void *out,
                                cudaStream_t s);
 template <typename Real>
 cudaError_t launch_cell_fold(const SideK<Real> &S, const void *P, void *Pc, cudaStream_t s);
 template <typename Real>
-cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
-                               long long scale_off, long long scale_len, int N2, void *Q,
+cudaError_t launch_gather_conv(const GridLaunch<Real> &L, const void *buf, void *Q,
                                cudaStream_t s);
+// blocks of one instance's spread / gather convolution (all-real and split kernels)
+int spread_blocks_native(int N2, int D);
+int gather_blocks_native(int ncell, int D);
+int spread_blocks_df(int N2, int D);
+int gather_blocks_df(int ncell, int D);
 template <typename Real>
 cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s);
 bool supported_degree(int D);
@@ -153,19 +202,17 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
 cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, cudaStream_t s);
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
                                 void *Pc4, cudaStream_t s);
-cudaError_t launch_spread_conv_df(const SideK<double> &S, const SideDf &T, const void *Pc4,
-                                  const float2 *scale, long long scale_off, long long scale_len,
-                                  int N2, void *out, cudaStream_t s);
-cudaError_t launch_fft_df(const FftDf &F, const void *in, void *tmp, void *out, int sign,
-                          cudaStream_t s);
-cudaError_t launch_gather_conv_df(const SideK<double> &S, const SideDf &T, const void *buf,
-                                  const float2 *scale, long long scale_off, long long scale_len,
-                                  int N2, void *Q4, cudaStream_t s);
+cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,
+                                  cudaStream_t s);
+cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, void *out,
+                          int sign, cudaStream_t s);
+cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, void *Q4,
+                                  cudaStream_t s);
 
 // ---- kern_fft.cu ------------------------------------------------------------------
 template <typename Real>
-cudaError_t launch_fft(const FftPlanDev &F, const void *in, void *tmp, void *out, int sign,
-                       cudaStream_t s);
+cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,
+                       int sign, cudaStream_t s);
 
 // ---- kern_misc.cu -----------------------------------------------------------------
 template <typename Real>
@@ -179,6 +226,5 @@ cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_
 cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s);
 cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half_z,
                              double *neg_half_z, cudaStream_t s);
-cudaError_t launch_negate(const double *in, int n, double *out, cudaStream_t s);
 
 }  // namespace nnfft

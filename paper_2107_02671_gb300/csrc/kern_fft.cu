@@ -114,17 +114,24 @@ __device__ C2<Real> *stockham(C2<Real> *A, C2<Real> *B, int n, const int *radice
     return src;
 }
 
+// Block b of pass 1 is column b - blk1[i] of instance i (n2 columns each), block c of
+// pass 2 row c - blk2[i] (n1 rows each); each instance works on its own grid_base.
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_fft_pass1(const C2<Real> *__restrict__ X, C2<Real> *__restrict__ Z, FftPlanDev F, int sign) {
+k_fft_pass1(const C2<Real> *__restrict__ X_all, C2<Real> *__restrict__ Z_all,
+            FftLaunch<FftPlanDev> L, int sign) {
     extern __shared__ unsigned char smem_raw[];
+    const int inst = block_instance(L.blk1, L.ninst, blockIdx.x);
+    const FftPlanDev &F = L.inst[inst];
+    const C2<Real> *__restrict__ X = X_all + F.grid_base;
+    C2<Real> *__restrict__ Z = Z_all + F.grid_base;
     const int n = F.n1;
     C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
     C2<Real> *B = A + n;
     C2<Real> *tw = B + n;
     const C2<Real> *tw1 = static_cast<const C2<Real> *>(F.tw1);
     const C2<Real> *twN = static_cast<const C2<Real> *>(F.twN);
-    const int b = blockIdx.x;
+    const int b = blockIdx.x - L.blk1[inst];
     for (int a = threadIdx.x; a < n; a += blockDim.x) {
         A[a] = X[(long long)F.n2 * a + b];
         tw[a] = tw1[a];
@@ -137,14 +144,19 @@ k_fft_pass1(const C2<Real> *__restrict__ X, C2<Real> *__restrict__ Z, FftPlanDev
 
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_fft_pass2(const C2<Real> *__restrict__ Z, C2<Real> *__restrict__ Y, FftPlanDev F, int sign) {
+k_fft_pass2(const C2<Real> *__restrict__ Z_all, C2<Real> *__restrict__ Y_all,
+            FftLaunch<FftPlanDev> L, int sign) {
     extern __shared__ unsigned char smem_raw[];
+    const int inst = block_instance(L.blk2, L.ninst, blockIdx.x);
+    const FftPlanDev &F = L.inst[inst];
+    const C2<Real> *__restrict__ Z = Z_all + F.grid_base;
+    C2<Real> *__restrict__ Y = Y_all + F.grid_base;
     const int n = F.n2;
     C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
     C2<Real> *B = A + n;
     C2<Real> *tw = B + n;
     const C2<Real> *tw2 = static_cast<const C2<Real> *>(F.tw2);
-    const int c = blockIdx.x;
+    const int c = blockIdx.x - L.blk2[inst];
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         A[b] = Z[(long long)b * F.n1 + c];
         tw[b] = tw2[b];
@@ -157,27 +169,28 @@ k_fft_pass2(const C2<Real> *__restrict__ Z, C2<Real> *__restrict__ Y, FftPlanDev
 }  // namespace
 
 template <typename Real>
-cudaError_t launch_fft(const FftPlanDev &F, const void *in, void *tmp, void *out, int sign,
-                       cudaStream_t s) {
-    const size_t sm1 = 3 * sizeof(C2<Real>) * F.n1;
-    const size_t sm2 = 3 * sizeof(C2<Real>) * F.n2;
+cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,
+                       int sign, cudaStream_t s) {
+    if (F.nblk1 <= 0) return cudaSuccess;
+    const size_t sm1 = 3 * sizeof(C2<Real>) * F.max_n1;
+    const size_t sm2 = 3 * sizeof(C2<Real>) * F.max_n2;
     if (sm1 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass1<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm1);
     if (sm2 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass2<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm2);
-    k_fft_pass1<Real><<<F.n2, 256, sm1, s>>>(static_cast<const C2<Real> *>(in),
-                                             static_cast<C2<Real> *>(tmp), F, sign);
-    k_fft_pass2<Real><<<F.n1, 256, sm2, s>>>(static_cast<const C2<Real> *>(tmp),
-                                             static_cast<C2<Real> *>(out), F, sign);
+    k_fft_pass1<Real><<<F.nblk1, 256, sm1, s>>>(static_cast<const C2<Real> *>(in),
+                                                static_cast<C2<Real> *>(tmp), F, sign);
+    k_fft_pass2<Real><<<F.nblk2, 256, sm2, s>>>(static_cast<const C2<Real> *>(tmp),
+                                                static_cast<C2<Real> *>(out), F, sign);
     count_launches(2);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fft<double>(const FftPlanDev &, const void *, void *, void *, int,
-                                        cudaStream_t);
-template cudaError_t launch_fft<float>(const FftPlanDev &, const void *, void *, void *, int,
-                                       cudaStream_t);
+template cudaError_t launch_fft<double>(const FftLaunch<FftPlanDev> &, const void *, void *,
+                                        void *, int, cudaStream_t);
+template cudaError_t launch_fft<float>(const FftLaunch<FftPlanDev> &, const void *, void *,
+                                       void *, int, cudaStream_t);
 
 }  // namespace nnfft

@@ -70,27 +70,33 @@ k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
 // Spread convolution.  Grid position p = p_lo + i (centered; the taps of all cells
 // cover [p_lo, p_hi], never wider than N2) goes to buffer index p mod N2:
 //   g_p = scale(p) * sum_t sum_d coef[t][d] * Pc_{p+m-1-t}[d],  0 beyond p_hi.
-// A block handles PPB consecutive positions with one thread per (position, degree d):
-// the d-th partial sum over the taps, then the D partials of a position are added in
-// shared memory.  The block's cells are staged in shared memory.
+// A block handles PPB consecutive positions of one instance with one thread per
+// (position, degree d): the d-th partial sum over the taps, then the D partials of a
+// position are added in shared memory.  The block's cells are staged in shared memory.
 // ---------------------------------------------------------------------------------
 constexpr int SCD_THREADS = 128;
 
 template <int D>
 __global__ void __launch_bounds__(SCD_THREADS)
-k_spread_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ Pc4,
-                 const float2 *__restrict__ scale, long long scale_off, long long scale_len,
-                 int N2, float4 *__restrict__ out) {
+k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
+                 float4 *__restrict__ out_all) {
     constexpr int B = D / 2;
     constexpr int PPB = SCD_THREADS / D;                       // positions per block
     extern __shared__ float4 smem4[];
-    const int m = S.m, ntap = 2 * S.m;
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<float2> G = L.inst[inst];
+    const float4 *__restrict__ Pc4 = Pc_all + (long long)G.cell_base * D;
+    float4 *__restrict__ out = out_all + G.grid_base;
+    const float2 *__restrict__ scale = G.scale;
+    const long long scale_off = G.scale_off, scale_len = G.scale_len;
+    const int N2 = G.N2;
+    const int m = L.m, ntap = 2 * L.m;
     const int ncl = PPB + ntap - 1;
     float4 *Ps = smem4;                                           // [D][ncl] staged cells
     float4 *part = smem4 + D * ncl;                               // [PPB][D] partial sums
     float2 *coef = reinterpret_cast<float2 *>(part + PPB * D);   // [ntap][D]
-    const long long p_lo = S.c_lo - m + 1, p_hi = S.c_lo + S.ncell - 1 + m;
-    const long long i0 = (long long)blockIdx.x * PPB;
+    const long long p_lo = G.c_lo - m + 1, p_hi = G.c_lo + G.ncell - 1 + m;
+    const long long i0 = (long long)(blockIdx.x - L.blk[inst]) * PPB;
     const long long p0 = p_lo + i0;
     if (p0 > p_hi) {                                              // zero padding only
         for (int k = threadIdx.x; k < PPB; k += SCD_THREADS) {
@@ -104,12 +110,12 @@ k_spread_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ Pc4,
         return;
     }
     const long long cbase = p0 - m;
-    for (int i = threadIdx.x; i < ntap * D; i += SCD_THREADS) coef[i] = T.coef[i];
+    for (int i = threadIdx.x; i < ntap * D; i += SCD_THREADS) coef[i] = G.coef[i];
     for (int i = threadIdx.x; i < ncl * D; i += SCD_THREADS) {
         const int lc = i / D, d = i - lc * D;
-        const long long ic = cbase + lc - S.c_lo;
+        const long long ic = cbase + lc - G.c_lo;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ic >= 0 && ic < S.ncell) v = Pc4[ic * D + d];
+        if (ic >= 0 && ic < G.ncell) v = Pc4[ic * D + d];
         Ps[d * ncl + lc] = v;
     }
     __syncthreads();
@@ -235,12 +241,19 @@ __device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, const int *radices,
     return src;
 }
 
+// Block b of pass 1 is column b - blk1[i] of instance i (n2 columns each), block c of
+// pass 2 row c - blk2[i] (n1 rows each).
 __global__ void __launch_bounds__(128)
-k_fft_pass1_df(const float4 *__restrict__ X, float4 *__restrict__ Z, FftDf F, int sign) {
+k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, FftLaunch<FftDf> L,
+               int sign) {
     extern __shared__ float4 smem4[];
+    const int inst = block_instance(L.blk1, L.ninst, blockIdx.x);
+    const FftDf &F = L.inst[inst];
+    const float4 *__restrict__ X = X_all + F.grid_base;
+    float4 *__restrict__ Z = Z_all + F.grid_base;
     const int n = F.n1;
     float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
-    const int b = blockIdx.x;
+    const int b = blockIdx.x - L.blk1[inst];
     for (int a = threadIdx.x; a < n; a += blockDim.x) {
         A[a] = X[(long long)F.n2 * a + b];
         tw[a] = F.tw1[a];
@@ -252,11 +265,16 @@ k_fft_pass1_df(const float4 *__restrict__ X, float4 *__restrict__ Z, FftDf F, in
 }
 
 __global__ void __launch_bounds__(128)
-k_fft_pass2_df(const float4 *__restrict__ Z, float4 *__restrict__ Y, FftDf F, int sign) {
+k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, FftLaunch<FftDf> L,
+               int sign) {
     extern __shared__ float4 smem4[];
+    const int inst = block_instance(L.blk2, L.ninst, blockIdx.x);
+    const FftDf &F = L.inst[inst];
+    const float4 *__restrict__ Z = Z_all + F.grid_base;
+    float4 *__restrict__ Y = Y_all + F.grid_base;
     const int n = F.n2;
     float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
-    const int c = blockIdx.x;
+    const int c = blockIdx.x - L.blk2[inst];
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         A[b] = Z[(long long)b * F.n1 + c];
         tw[b] = F.tw2[b];
@@ -278,18 +296,25 @@ constexpr int GC_THREADS = 128;
 
 template <int D>
 __global__ void __launch_bounds__(GC_THREADS)
-k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
-                 const float2 *__restrict__ scale, long long scale_off, long long scale_len,
-                 int N2, float4 *__restrict__ Q4) {
+k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
+                 float4 *__restrict__ Q_all) {
     constexpr int B = D / 2;
     constexpr int GCB = GC_THREADS / D;
     __shared__ float4 qs[GCB * D];
-    const int m = S.m, ntap = 2 * S.m;
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<float2> G = L.inst[inst];
+    const float4 *__restrict__ buf = buf_all + G.grid_base;
+    float4 *__restrict__ Q4 = Q_all + (long long)G.cell_base * D;
+    const float2 *__restrict__ scale = G.scale;
+    const float2 *__restrict__ rfit = L.fold ? G.rfit : nullptr;
+    const long long scale_off = G.scale_off, scale_len = G.scale_len;
+    const int N2 = G.N2;
+    const int m = L.m, ntap = 2 * L.m;
     const int k = threadIdx.x / D, d = threadIdx.x - k * D;
-    const int ic = blockIdx.x * GCB + k;
-    const bool active = k < GCB && ic < S.ncell;
+    const int ic = (blockIdx.x - L.blk[inst]) * GCB + k;
+    const bool active = k < GCB && ic < G.ncell;
     if (active) {
-        const long long c = S.c_lo + ic;
+        const long long c = G.c_lo + ic;
         cdf q = czero();
         if (d < B) {
             df qr = mk(0.f), qi = mk(0.f);
@@ -303,7 +328,7 @@ k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
                     const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
                     h = cscale(h, mk(sc.x, sc.y));
                 }
-                const float2 c2 = T.coef[t * D + d];
+                const float2 c2 = G.coef[t * D + d];
                 const df cd = mk(c2.x, c2.y);
                 acc(qr, mul_u(cd, h.re));
                 acc(qi, mul_u(cd, h.im));
@@ -324,20 +349,20 @@ k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
                     hr *= sc;
                     hi *= sc;
                 }
-                const float cc = T.coef[t * D + d].x;
+                const float cc = G.coef[t * D + d].x;
                 fr = fmaf(cc, hr, fr);
                 fi = fmaf(cc, hi, fi);
             }
             q.re = mk(fr);
             q.im = mk(fi);
         }
-        if (T.rfit == nullptr) {
+        if (rfit == nullptr) {
             st(Q4 + (long long)ic * D + d, q);
         } else {
             st(qs + k * D + d, q);
         }
     }
-    if (T.rfit == nullptr) return;
+    if (rfit == nullptr) return;
     __syncthreads();
     if (!active) return;
     // coefficient n = d of R(y) S(y) = sum_{i,j} (r_j/2) Q_i (T_{i+j} + T_{|i-j|}):
@@ -345,7 +370,7 @@ k_gather_conv_df(SideK<double> S, SideDf T, const float4 *__restrict__ buf,
     df ar = mk(0.f), ai = mk(0.f);
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        const float2 rv = T.rfit[(long long)ic * NR + j];
+        const float2 rv = rfit[(long long)ic * NR + j];
         const df r = mk(rv.x, rv.y);
         if (j <= d) {
             const cdf v = ld(qs + k * D + d - j);
@@ -392,44 +417,44 @@ cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const v
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread_conv_df(const SideK<double> &S, const SideDf &T, const void *Pc4,
-                                  const float2 *scale, long long scale_off, long long scale_len,
-                                  int N2, void *out, cudaStream_t s) {
-    const int ntap = 2 * S.m;
-    const int ppb = SCD_THREADS / S.D;
-    const size_t sm = sizeof(float4) * (size_t)S.D * (ppb + ntap - 1) +
-                      sizeof(float4) * (size_t)ppb * S.D + sizeof(float2) * (size_t)ntap * S.D;
-    NNFFT_DISPATCH_DF2(S.D, (k_spread_conv_df<DD><<<cdiv(N2, ppb), SCD_THREADS, sm, s>>>(
-                                S, T, static_cast<const float4 *>(Pc4), scale, scale_off, scale_len,
-                                N2, static_cast<float4 *>(out))));
+int spread_blocks_df(int N2, int D) { return cdiv(N2, SCD_THREADS / D); }
+int gather_blocks_df(int ncell, int D) { return cdiv(ncell, GC_THREADS / D); }
+
+cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,
+                                  cudaStream_t s) {
+    if (L.nblocks <= 0) return cudaSuccess;
+    const int ntap = 2 * L.m;
+    const int ppb = SCD_THREADS / L.D;
+    const size_t sm = sizeof(float4) * (size_t)L.D * (ppb + ntap - 1) +
+                      sizeof(float4) * (size_t)ppb * L.D + sizeof(float2) * (size_t)ntap * L.D;
+    NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df<DD><<<L.nblocks, SCD_THREADS, sm, s>>>(
+                                L, static_cast<const float4 *>(Pc4), static_cast<float4 *>(out))));
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_df(const FftDf &F, const void *in, void *tmp, void *out, int sign,
-                          cudaStream_t s) {
-    const size_t sm1 = 3 * sizeof(float4) * F.n1;
-    const size_t sm2 = 3 * sizeof(float4) * F.n2;
+cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, void *out,
+                          int sign, cudaStream_t s) {
+    if (F.nblk1 <= 0) return cudaSuccess;
+    const size_t sm1 = 3 * sizeof(float4) * F.max_n1;
+    const size_t sm2 = 3 * sizeof(float4) * F.max_n2;
     if (sm1 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass1_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (sm2 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass2_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-    k_fft_pass1_df<<<F.n2, 128, sm1, s>>>(static_cast<const float4 *>(in),
-                                           static_cast<float4 *>(tmp), F, sign);
-    k_fft_pass2_df<<<F.n1, 128, sm2, s>>>(static_cast<const float4 *>(tmp),
-                                           static_cast<float4 *>(out), F, sign);
+    k_fft_pass1_df<<<F.nblk1, 128, sm1, s>>>(static_cast<const float4 *>(in),
+                                              static_cast<float4 *>(tmp), F, sign);
+    k_fft_pass2_df<<<F.nblk2, 128, sm2, s>>>(static_cast<const float4 *>(tmp),
+                                              static_cast<float4 *>(out), F, sign);
     count_launches(2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_conv_df(const SideK<double> &S, const SideDf &T, const void *buf,
-                                  const float2 *scale, long long scale_off, long long scale_len,
-                                  int N2, void *Q4, cudaStream_t s) {
-    if (S.ncell <= 0) return cudaSuccess;
-    const int gcb = GC_THREADS / S.D;
-    NNFFT_DISPATCH_DF2(S.D, (k_gather_conv_df<DD><<<cdiv(S.ncell, gcb), GC_THREADS, 0, s>>>(
-                                S, T, static_cast<const float4 *>(buf), scale, scale_off, scale_len,
-                                N2, static_cast<float4 *>(Q4))));
+cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, void *Q4,
+                                  cudaStream_t s) {
+    if (L.nblocks <= 0) return cudaSuccess;
+    NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df<DD><<<L.nblocks, GC_THREADS, 0, s>>>(
+                                L, static_cast<const float4 *>(buf), static_cast<float4 *>(Q4))));
     count_launches(1);
     return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
 // kern_misc.cu -- small elementwise kernels of the fast sinc transform
 // (Algorithm 6.1): real <-> complex packing, the step-2 product alpha_j = w_j g_j,
-// the node reflection tau -> -tau, and the two ends of the Clenshaw-Curtis weight
+// and the two ends of the Clenshaw-Curtis weight
 // computation (Algorithm 5.4) around a length-2n FFT.
 #include "internal.h"
 
@@ -34,12 +34,6 @@ __global__ void k_complex_to_real(const C2<Real> *__restrict__ in, int n, Real *
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     out[i] = in[i].x;
-}
-
-__global__ void k_negate(const double *__restrict__ in, int n, double *__restrict__ out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    out[i] = -in[i];
 }
 
 // Clenshaw-Curtis weights, eq. (wk=), through Algorithm 5.4's DCT-I: with
@@ -110,13 +104,6 @@ cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_
     count_launches(1);
     return cudaGetLastError();
 }
-cudaError_t launch_negate(const double *in, int n, double *out, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_negate<<<cdiv(n, 256), 256, 0, s>>>(in, n, out);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s) {
     k_cc_extend<<<cdiv(2 * n, 256), 256, 0, s>>>(n, static_cast<double2 *>(x));
     count_launches(1);

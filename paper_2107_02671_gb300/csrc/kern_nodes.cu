@@ -16,30 +16,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Cell index of a node: c = floor(node * uscale) - c_lo.  The same expression is
-// used by k_sorted_coords so both kernels agree on every cell boundary.
+// Cell of a node: c = floor(node * uscale), key c - c_lo (+ the instance's first cell).
 __device__ __forceinline__ double node_u(double x, double uscale) { return x * uscale; }
-
-__global__ void k_node_keys(const double *__restrict__ nodes, int n, double uscale,
-                            long long c_lo, int ncell, uint32_t *__restrict__ keys,
-                            int *__restrict__ vals, int *status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = nodes[i];
-    long long ic = 0;
-    if (!(x >= -0.5 && x <= 0.5)) {          // also catches NaN
-        atomicOr(status, STATUS_RANGE);
-    } else {
-        double u = node_u(x, uscale);
-        ic = (long long)floor(u) - c_lo;
-        if (ic < 0 || ic >= ncell) {
-            atomicOr(status, STATUS_INTERNAL);
-            ic = ic < 0 ? 0 : ncell - 1;
-        }
-    }
-    keys[i] = (uint32_t)ic;
-    vals[i] = i;
-}
 
 // Coordinate storage formats of the sorted local coordinate y = 2(u - floor u) - 1.
 //   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans)
@@ -68,9 +46,11 @@ __device__ __forceinline__ void store_y(void *yout, int fmt, long long i, double
 // compute its cell key c - c_lo and local coordinate y in FP64 (u = node * uscale,
 // c = floor(u), y = 2 (u - c) - 1), store y (caller order) in the plan's format, and
 // count the digits of the first radix pass for this block's tile (the tiles match
-// k_sort_scatter's: SORT_TILE keys per block).
+// k_sort_scatter's: SORT_TILE keys per block).  In a batch each point takes the
+// binning of its instance and the key is offset by the instance's first cell.
 __global__ void __launch_bounds__(SORT_THREADS)
-k_node_keys_y(const double *__restrict__ nodes, int n, double uscale, long long c_lo, int ncell,
+k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
+              const long long *__restrict__ pt_off, const NodeInst *__restrict__ tab, int ninst,
               uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int nblocks,
               int *__restrict__ hist, int *__restrict__ digit_tot, int *status) {
     __shared__ int h[256];
@@ -80,21 +60,31 @@ k_node_keys_y(const double *__restrict__ nodes, int n, double uscale, long long 
     for (int k = threadIdx.x; k < SORT_TILE; k += SORT_THREADS) {
         const long long i = base + k;
         if (i >= n) break;
+        NodeInst I = one;
+        if (ninst > 1) {                     // instance of point i: pt_off[j] <= i < pt_off[j+1]
+            int lo = 0, hi = ninst;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(pt_off + mid) <= i) lo = mid; else hi = mid;
+            }
+            I = tab[lo];
+        }
         const double x = nodes[i];
         long long ic = 0;
         double y = 0.0;
         if (!(x >= -0.5 && x <= 0.5)) {
             atomicOr(status, STATUS_RANGE);
         } else {
-            const double u = node_u(x, uscale);
+            const double u = node_u(x, I.uscale);
             const double c = floor(u);
-            ic = (long long)c - c_lo;
+            ic = (long long)c - I.c_lo;
             y = 2.0 * (u - c) - 1.0;
-            if (ic < 0 || ic >= ncell) {
+            if (ic < 0 || ic >= I.ncell) {
                 atomicOr(status, STATUS_INTERNAL);
-                ic = ic < 0 ? 0 : ncell - 1;
+                ic = ic < 0 ? 0 : I.ncell - 1;
             }
         }
+        ic += I.cell_base;
         keys[i] = (uint32_t)ic;
         store_y(yout, yfmt, i, y);
         atomicAdd(&h[ic & 255], 1);
@@ -353,136 +343,96 @@ k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off
     }
 }
 
-__global__ void k_item_counts(const int *__restrict__ off, int ncell, int *__restrict__ cnt) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    int np = off[c + 1] - off[c];
-    cnt[c] = (np + ITEM_CAP - 1) / ITEM_CAP;
+// Work items for many cells (a batch), in three launches: per block of 1024 cells the
+// number of items, a single-block scan of those block sums, then per block the local
+// scan, the items and item_off.  Same items as k_build_items.
+__device__ __forceinline__ int cell_items(const int *off, int c, int ncell) {
+    return c < ncell ? (off[c + 1] - off[c] + ITEM_CAP - 1) / ITEM_CAP : 0;
 }
 
-__global__ void k_item_fill(const int *__restrict__ off, const int *__restrict__ item_off,
-                            int ncell, int *__restrict__ item_cell, int *__restrict__ item_pb,
-                            int *__restrict__ item_pe, int *__restrict__ nitems) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) *nitems = item_off[ncell];
-    if (c >= ncell) return;
-    int i0 = item_off[c], i1 = item_off[c + 1];
-    int p0 = off[c], p1 = off[c + 1];
-    for (int j = 0; j < i1 - i0; ++j) {
-        int pb = p0 + j * ITEM_CAP;
-        int pe = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
-        item_cell[i0 + j] = c;
-        item_pb[i0 + j] = pb;
-        item_pe[i0 + j] = pe;
+__global__ void __launch_bounds__(1024)
+k_item_block_sums(const int *__restrict__ off, int ncell, int *__restrict__ bsum) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int v = cell_items(off, blockIdx.x * 1024 + tid, ncell);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int t = wsum[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) bsum[blockIdx.x] = t;
     }
 }
 
-template <typename Real>
-__global__ void k_sorted_coords(const double *__restrict__ nodes, const int *__restrict__ perm,
-                                const uint32_t *__restrict__ keys, int n, double uscale,
-                                long long c_lo, Real *__restrict__ ys, int *status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = nodes[perm[i]];
-    double y = 0.0;
-    if (x >= -0.5 && x <= 0.5) {
-        double u = node_u(x, uscale);
-        double c = floor(u);
-        y = 2.0 * (u - c) - 1.0;
-        if ((long long)c - c_lo != (long long)keys[i]) atomicOr(status, STATUS_INTERNAL);
+__global__ void __launch_bounds__(1024)
+k_item_fill_blocks(const int *__restrict__ off, int ncell, const int *__restrict__ bbase,
+                   int nblocks, int *__restrict__ item_off, int *__restrict__ item_cell,
+                   int *__restrict__ item_pb, int *__restrict__ item_pe,
+                   int *__restrict__ nitems) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int c = blockIdx.x * 1024 + tid;
+    const int v = cell_items(off, c, ncell);
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
     }
-    ys[i] = (Real)y;
-}
-
-__global__ void k_sorted_coords_split(const double *__restrict__ nodes,
-                                      const int *__restrict__ perm,
-                                      const uint32_t *__restrict__ keys, int n, double uscale,
-                                      long long c_lo, float2 *__restrict__ ys, int *status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double x = nodes[perm[i]];
-    double y = 0.0;
-    if (x >= -0.5 && x <= 0.5) {
-        double u = node_u(x, uscale);
-        double c = floor(u);
-        y = 2.0 * (u - c) - 1.0;
-        if ((long long)c - c_lo != (long long)keys[i]) atomicOr(status, STATUS_INTERNAL);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int x = wsum[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += u;
+        }
+        wsum[lane] = xi - x;
     }
-    const float h = (float)y;
-    ys[i] = make_float2(h, (float)(y - (double)h));
+    __syncthreads();
+    const int first = bbase[blockIdx.x] + wsum[w] + incl - v;
+    if (c < ncell) {
+        item_off[c] = first;
+        const int p0 = off[c], p1 = off[c + 1];
+        for (int j = 0; j < v; ++j) {
+            const int pb = p0 + j * ITEM_CAP;
+            item_cell[first + j] = c;
+            item_pb[first + j] = pb;
+            item_pe[first + j] = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
+        }
+    }
+    if (blockIdx.x == nblocks - 1 && tid == 0) {
+        item_off[ncell] = bbase[nblocks];
+        *nitems = bbase[nblocks];
+    }
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
 
-cudaError_t launch_sorted_coords_split(const double *nodes, const int *perm,
-                                       const uint32_t *keys_sorted, int n, double uscale,
-                                       long long c_lo, float2 *ys, int *status, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_sorted_coords_split<<<cdiv(n, 256), 256, 0, s>>>(nodes, perm, keys_sorted, n, uscale, c_lo,
-                                                       ys, status);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_node_keys(const double *nodes, int n, double uscale, long long c_lo,
-                             int ncell, uint32_t *keys, int *vals, int *status,
-                             cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_node_keys<<<cdiv(n, 256), 256, 0, s>>>(nodes, n, uscale, c_lo, ncell, keys, vals, status);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 size_t radix_sort_hist_len(int n) {
     long long nb = n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1;
     return (size_t)(256 * nb + 1 + 256);   // histogram, total, digit totals
 }
 
-cudaError_t launch_scan_exclusive(const int *in, int *out, int n, cudaStream_t s) {
-    k_scan_exclusive<<<1, 1024, 0, s>>>(in, out, n);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t radix_sort_pairs(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
-                             int *hist, int n, int key_bits, cudaStream_t s,
-                             uint32_t **keys_sorted, int **vals_sorted) {
-    uint32_t *ka = keys, *kb = keys_alt;
-    int *va = vals, *vb = vals_alt;
-    if (n > 1) {
-        int nblocks = cdiv(n, SORT_TILE);
-        int *digit_tot = hist + 256LL * nblocks + 1;
-        for (int shift = 0; shift < key_bits; shift += 8) {
-            cudaError_t e0 = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
-            if (e0 != cudaSuccess) return e0;
-            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist, digit_tot);
-            k_sort_scan_rows<<<256, 256, 0, s>>>(hist, nblocks, digit_tot);
-            k_sort_scatter<false, void><<<nblocks, SORT_THREADS, 0, s>>>(
-                ka, va, kb, vb, n, shift, nblocks, hist, nullptr, nullptr);
-            count_launches(3);
-            cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-            uint32_t *tk = ka; ka = kb; kb = tk;
-            int *tv = va; va = vb; vb = tv;
-        }
-    }
-    *keys_sorted = ka;
-    *vals_sorted = va;
-    return cudaSuccess;
-}
-
-cudaError_t launch_node_keys_y(const double *nodes, int n, double uscale, long long c_lo,
-                               int ncell, uint32_t *keys, void *y_user, int yfmt, int *hist,
-                               int *status, cudaStream_t s) {
+cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
+                               const long long *pt_off, const NodeInst *tab, int ninst,
+                               uint32_t *keys, void *y_user, int yfmt, int *hist, int *status,
+                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int nblocks = cdiv(n, SORT_TILE);
     int *digit_tot = hist + 256LL * nblocks + 1;
     cudaError_t e = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_node_keys_y<<<nblocks, SORT_THREADS, 0, s>>>(nodes, n, uscale, c_lo, ncell, keys, y_user,
-                                                   yfmt, nblocks, hist, digit_tot, status);
+    k_node_keys_y<<<nblocks, SORT_THREADS, 0, s>>>(nodes, n, one, pt_off, tab, ninst, keys,
+                                                   y_user, yfmt, nblocks, hist, digit_tot,
+                                                   status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -556,12 +506,23 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
 
 cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
                                      int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                                     cudaStream_t s) {
-    k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
-                                     nitems);
-    count_launches(1);
+                                     int *scratch, cudaStream_t s) {
+    if (ncell <= ITEMS_ONE_BLOCK_MAX) {
+        k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
+                                         nitems);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    const int nb = cdiv(ncell, 1024);
+    k_item_block_sums<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(scratch, scratch, nb);
+    k_item_fill_blocks<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch, nb, item_off, item_cell,
+                                           item_pb, item_pe, nitems);
+    count_launches(3);
     return cudaGetLastError();
 }
+
+size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 1; }
 
 cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
                                 cudaStream_t s) {
@@ -569,34 +530,5 @@ cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, i
     count_launches(1);
     return cudaGetLastError();
 }
-
-cudaError_t launch_build_items(const int *cell_off, int ncell, int *item_cnt, int *item_off,
-                               int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                               cudaStream_t s) {
-    k_item_counts<<<cdiv(ncell, 256), 256, 0, s>>>(cell_off, ncell, item_cnt);
-    k_scan_exclusive<<<1, 1024, 0, s>>>(item_cnt, item_off, ncell);
-    k_item_fill<<<cdiv(ncell, 256), 256, 0, s>>>(cell_off, item_off, ncell, item_cell, item_pb,
-                                                  item_pe, nitems);
-    count_launches(3);
-    return cudaGetLastError();
-}
-
-template <typename Real>
-cudaError_t launch_sorted_coords(const double *nodes, const int *perm,
-                                 const uint32_t *keys_sorted, int n, double uscale,
-                                 long long c_lo, Real *ys, int *status, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_sorted_coords<Real><<<cdiv(n, 256), 256, 0, s>>>(nodes, perm, keys_sorted, n, uscale,
-                                                       c_lo, ys, status);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-template cudaError_t launch_sorted_coords<double>(const double *, const int *,
-                                                  const uint32_t *, int, double, long long,
-                                                  double *, int *, cudaStream_t);
-template cudaError_t launch_sorted_coords<float>(const double *, const int *, const uint32_t *,
-                                                 int, double, long long, float *, int *,
-                                                 cudaStream_t);
 
 }  // namespace nnfft

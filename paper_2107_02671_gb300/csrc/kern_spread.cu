@@ -194,29 +194,38 @@ k_cell_fold(SideK<Real> S, const C2<Real> *__restrict__ P, C2<Real> *__restrict_
 // v side (forward): scale = 1/(N1 N2 phihat2(l)); x side (adjoint): scale = 1.
 // ---------------------------------------------------------------------------------
 constexpr int SC_THREADS = 32;
+constexpr int GCN_THREADS = 32;
 
 template <typename Real, int D>
 __global__ void __launch_bounds__(SC_THREADS)
-k_spread_conv(SideK<Real> S, const C2<Real> *__restrict__ Pc, const Real *__restrict__ scale,
-              long long scale_off, long long scale_len, int N2, C2<Real> *__restrict__ out) {
+k_spread_conv(GridLaunch<Real> L, const C2<Real> *__restrict__ Pc_all,
+              C2<Real> *__restrict__ out_all) {
     extern __shared__ unsigned char smem_raw[];
-    const int m = S.m, ntap = 2 * S.m;
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<Real> G = L.inst[inst];
+    const C2<Real> *__restrict__ Pc = Pc_all + (long long)G.cell_base * D;
+    C2<Real> *__restrict__ out = out_all + G.grid_base;
+    const Real *__restrict__ scale = G.scale;
+    const long long scale_off = G.scale_off, scale_len = G.scale_len;
+    const int N2 = G.N2;
+    const int lb = blockIdx.x - L.blk[inst];
+    const int m = L.m, ntap = 2 * L.m;
     const int ncl = SC_THREADS + ntap - 1;                    // staged cells
     Real *coef = reinterpret_cast<Real *>(smem_raw);
     C2<Real> *Ps = reinterpret_cast<C2<Real> *>(coef + ((ntap * D + 1) & ~1));   // [D][ncl]
-    const long long p_lo = S.c_lo - m + 1, p_hi = S.c_lo + S.ncell - 1 + m;
-    const long long p0 = p_lo + (long long)blockIdx.x * SC_THREADS;
+    const long long p_lo = G.c_lo - m + 1, p_hi = G.c_lo + G.ncell - 1 + m;
+    const long long p0 = p_lo + (long long)lb * SC_THREADS;
     const long long cbase = p0 - m;                           // cell of local index 0
-    for (int i = threadIdx.x; i < ntap * D; i += SC_THREADS) coef[i] = S.coef[i];
+    for (int i = threadIdx.x; i < ntap * D; i += SC_THREADS) coef[i] = G.coef[i];
     for (int i = threadIdx.x; i < ncl * D; i += SC_THREADS) {
         const int lc = i / D, d = i - lc * D;
-        const long long ic = cbase + lc - S.c_lo;
+        const long long ic = cbase + lc - G.c_lo;
         C2<Real> v = mk2<Real>(Real(0), Real(0));
-        if (ic >= 0 && ic < S.ncell) v = Pc[ic * D + d];
+        if (ic >= 0 && ic < G.ncell) v = Pc[ic * D + d];
         Ps[d * ncl + lc] = v;
     }
     __syncthreads();
-    const long long i = (long long)blockIdx.x * SC_THREADS + threadIdx.x;
+    const long long i = (long long)lb * SC_THREADS + threadIdx.x;
     if (i >= N2) return;
     const long long p = p_lo + i;
     long long q = p % N2;
@@ -261,17 +270,25 @@ k_spread_conv(SideK<Real> S, const C2<Real> *__restrict__ Pc, const Real *__rest
 // v side (adjoint): buf = the +sign FFT of the x-side spread, scale = 1/(N1 N2 phihat2(l)).
 // ---------------------------------------------------------------------------------
 template <typename Real, int D>
-__global__ void __launch_bounds__(32)
-k_gather_conv(SideK<Real> S, const C2<Real> *__restrict__ buf, const Real *__restrict__ scale,
-              long long scale_off, long long scale_len, int N2, C2<Real> *__restrict__ Q) {
+__global__ void __launch_bounds__(GCN_THREADS)
+k_gather_conv(GridLaunch<Real> L, const C2<Real> *__restrict__ buf_all,
+              C2<Real> *__restrict__ Q_all) {
     extern __shared__ unsigned char smem_raw[];
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<Real> G = L.inst[inst];
+    const C2<Real> *__restrict__ buf = buf_all + G.grid_base;
+    C2<Real> *__restrict__ Q = Q_all + (long long)G.cell_base * D;
+    const Real *__restrict__ scale = G.scale;
+    const Real *__restrict__ rfit = L.fold ? G.rfit : nullptr;
+    const long long scale_off = G.scale_off, scale_len = G.scale_len;
+    const int N2 = G.N2;
     Real *coef = reinterpret_cast<Real *>(smem_raw);
-    const int m = S.m, ntap = 2 * S.m;
-    for (int i = threadIdx.x; i < ntap * D; i += blockDim.x) coef[i] = S.coef[i];
+    const int m = L.m, ntap = 2 * L.m;
+    for (int i = threadIdx.x; i < ntap * D; i += blockDim.x) coef[i] = G.coef[i];
     __syncthreads();
-    const int ic = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ic >= S.ncell) return;
-    const long long c = S.c_lo + ic;
+    const int ic = (blockIdx.x - L.blk[inst]) * GCN_THREADS + threadIdx.x;
+    if (ic >= G.ncell) return;
+    const long long c = G.c_lo + ic;
     Real qr[D], qi[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) { qr[d] = Real(0); qi[d] = Real(0); }
@@ -293,10 +310,10 @@ k_gather_conv(SideK<Real> S, const C2<Real> *__restrict__ buf, const Real *__res
             qi[d] = fma(ct[d], h.y, qi[d]);
         }
     }
-    if (S.rfit != nullptr) {
+    if (rfit != nullptr) {
         Real r[NR];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) r[j] = Real(0.5) * S.rfit[(long long)ic * NR + j];
+        for (int j = 0; j < NR; ++j) r[j] = Real(0.5) * rfit[(long long)ic * NR + j];
         Real orr[D], oi[D];
 #pragma unroll
         for (int n = 0; n < D; ++n) { orr[n] = Real(0); oi[n] = Real(0); }
@@ -400,31 +417,31 @@ cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cuda
     return cudaGetLastError();
 }
 
+int spread_blocks_native(int N2, int D) { return cdiv(N2, SC_THREADS); }
+int gather_blocks_native(int ncell, int D) { return cdiv(ncell, GCN_THREADS); }
+
 template <typename Real>
-cudaError_t launch_spread_conv(const SideK<Real> &S, const void *Pc, const Real *scale,
-                               long long scale_off, long long scale_len, int N2, void *out,
+cudaError_t launch_spread_conv(const GridLaunch<Real> &L, const void *Pc, void *out,
                                cudaStream_t s) {
-    const int ntap = 2 * S.m;
-    const size_t sm = sizeof(Real) * (size_t)((ntap * S.D + 1) & ~1) +
-                      sizeof(C2<Real>) * (size_t)S.D * (SC_THREADS + ntap - 1);
+    if (L.nblocks <= 0) return cudaSuccess;
+    const int ntap = 2 * L.m;
+    const size_t sm = sizeof(Real) * (size_t)((ntap * L.D + 1) & ~1) +
+                      sizeof(C2<Real>) * (size_t)L.D * (SC_THREADS + ntap - 1);
     const C2<Real> *pc = static_cast<const C2<Real> *>(Pc);
     C2<Real> *o = static_cast<C2<Real> *>(out);
-    NNFFT_DISPATCH_D(S.D, (k_spread_conv<Real, DD><<<cdiv(N2, SC_THREADS), SC_THREADS, sm, s>>>(
-                              S, pc, scale, scale_off, scale_len, N2, o)));
+    NNFFT_DISPATCH_D(L.D, (k_spread_conv<Real, DD><<<L.nblocks, SC_THREADS, sm, s>>>(L, pc, o)));
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_gather_conv(const SideK<Real> &S, const void *buf, const Real *scale,
-                               long long scale_off, long long scale_len, int N2, void *Q,
+cudaError_t launch_gather_conv(const GridLaunch<Real> &L, const void *buf, void *Q,
                                cudaStream_t s) {
-    if (S.ncell <= 0) return cudaSuccess;
-    const size_t sm = sizeof(Real) * 2 * S.m * S.D;
+    if (L.nblocks <= 0) return cudaSuccess;
+    const size_t sm = sizeof(Real) * 2 * L.m * L.D;
     const C2<Real> *b = static_cast<const C2<Real> *>(buf);
     C2<Real> *q = static_cast<C2<Real> *>(Q);
-    NNFFT_DISPATCH_D(S.D, (k_gather_conv<Real, DD><<<cdiv(S.ncell, 32), 32, sm, s>>>(
-                              S, b, scale, scale_off, scale_len, N2, q)));
+    NNFFT_DISPATCH_D(L.D, (k_gather_conv<Real, DD><<<L.nblocks, GCN_THREADS, sm, s>>>(L, b, q)));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -443,11 +460,9 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
 #define NNFFT_INST(R)                                                                      \
     template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *,         \
                                            cudaStream_t);                                  \
-    template cudaError_t launch_spread_conv<R>(const SideK<R> &, const void *, const R *,  \
-                                               long long, long long, int, void *,         \
+    template cudaError_t launch_spread_conv<R>(const GridLaunch<R> &, const void *, void *, \
                                                cudaStream_t);                              \
-    template cudaError_t launch_gather_conv<R>(const SideK<R> &, const void *, const R *,  \
-                                               long long, long long, int, void *,         \
+    template cudaError_t launch_gather_conv<R>(const GridLaunch<R> &, const void *, void *, \
                                                cudaStream_t);                              \
     template cudaError_t launch_cell_fold<R>(const SideK<R> &, const void *, void *,       \
                                              cudaStream_t);                                \

@@ -48,13 +48,21 @@ int cuda_fail(cudaError_t e, const char *where) {
     } while (0)
 
 struct Side {
-    // plan-time
+    // plan-time (all instances of the plan concatenated)
     int m = 0, D = 0;
-    double beta = 0, sigma = 0, uscale = 0, fit_err = 0;
-    long long c_lo = 0;
     int ncell = 0, M = 0, max_items = 0, key_bits = 8;
     bool has_r = false;
-    void *coef = nullptr, *rfit = nullptr;
+    NodeInst one{};                        // binning of a single-instance plan
+    long long *pt_off = nullptr;           // [ninst + 1] device, batches only
+    NodeInst *node_tab = nullptr;          // [ninst] device, batches only
+    void *coef = nullptr;                  // [ninst][2m][D] real tap coefficients
+    void *coef_df = nullptr;               // same as (hi, lo) float pairs
+    void *rfit = nullptr;                  // x side: [ncell][NR] real 1/phihat1 fits
+    void *rfit_df = nullptr;               // x side: (hi, lo) of r_j / 2
+    void *grid_real = nullptr;             // [ninst] GridInst<Real>
+    void *grid_df = nullptr;               // [ninst] GridInst<float2>
+    int *blk_sn = nullptr, *blk_gn = nullptr, *blk_sd = nullptr, *blk_gd = nullptr;
+    int nb_sn = 0, nb_gn = 0, nb_sd = 0, nb_gd = 0;   // spread/gather x native/df blocks
     // node-time
     uint32_t *keys = nullptr, *keys_alt = nullptr;
     int *vals = nullptr, *vals_alt = nullptr, *hist = nullptr;
@@ -62,7 +70,7 @@ struct Side {
     uint32_t *keys_sorted = nullptr;
     void *ys = nullptr;
     void *y_user = nullptr;        // coordinates in caller order (step-0 scratch)
-    int *cell_off = nullptr, *item_cnt = nullptr, *item_off = nullptr;
+    int *cell_off = nullptr, *item_off = nullptr, *items_scratch = nullptr;
     int *item_cell = nullptr, *item_pb = nullptr, *item_pe = nullptr, *nitems = nullptr;
     bool set = false;
 };
@@ -70,21 +78,20 @@ struct Side {
 }  // namespace
 
 struct nnfft_plan_s {
-    nnfft_info info{};
+    nnfft_info info{};                       // the instance (or, for batches, totals)
+    int64_t ninst = 1;
+    std::vector<nnfft_info> inst_info;       // per instance
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;              // second stream: the two node sides sort concurrently
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool dbl = true;
     bool split = false;          // fp64 plan using the split-precision kernels
-    std::vector<double> rfit_host;   // x-side 1/phihat1 fits (plan construction only)
     bool split_ok = false;       // the window fits allow them (see kern_spread_df.cu)
     Side side[2];   // 0: v (frequency) side, 1: x (spatial) side
-    void *dec2 = nullptr;
-    FftPlanDev fft{};
-    // split-precision tables (fp64 plans)
-    void *coef_df[2] = {nullptr, nullptr};
-    void *rfit_df = nullptr, *dec2_df = nullptr;
-    FftDf fftdf{};
+    // FFT of every instance (four-step tables), all-real and double-float forms
+    FftLaunch<FftPlanDev> fft{};
+    FftLaunch<FftDf> fftdf{};
+    long long grid_total = 0;    // sum of the instances' N2
     void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;
     void *P = nullptr;   // per-item moments
     void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
@@ -231,59 +238,353 @@ int key_bits_for(int ncell) {
     return ((b + 7) / 8) * 8;
 }
 
-int setup_side(nnfft_plan_s *p, int s, const hm::Derived &d, const std::vector<double> &coef) {
-    Side &S = p->side[s];
-    const nnfft_info &I = p->info;
-    S.m = s == 0 ? d.m1 : d.m2;
-    S.D = s == 0 ? I.D1 : I.D2;
-    S.beta = s == 0 ? d.beta1 : d.beta2;
-    S.sigma = s == 0 ? d.sigma1 : d.sigma2;
-    S.fit_err = s == 0 ? I.fit_err1 : I.fit_err2;
-    S.uscale = s == 0 ? (double)d.N1 * (double)d.N / (double)d.Nstar
-                      : (double)d.N2 * (double)d.Nstar / (double)d.N1;
-    S.c_lo = (long long)std::floor(-0.5 * S.uscale);
-    S.ncell = (int)(s == 0 ? I.ncell1 : I.ncell2);
-    S.M = (int)(s == 0 ? I.M1 : I.M2);
-    S.max_items = S.ncell + (S.M + ITEM_CAP - 1) / ITEM_CAP;
-    S.key_bits = key_bits_for(S.ncell);
-    S.has_r = s == 1;
-    if (!supported_degree(S.D)) return fail(NNFFT_EINVAL, "unsupported window degree");
-    int rc = upload_real(p, &S.coef, coef, "window coefficients");
+template <class T>
+int upload_vec(nnfft_plan_s *p, T **dst, const std::vector<T> &v, const char *what) {
+    int rc = dalloc_n(p, dst, v.size(), what);
     if (rc) return rc;
-    if (S.has_r) {
-        // Per x cell c: Chebyshev fit in y of 1/phihat1(N* x), x = (c + (y+1)/2)/uscale,
-        // phihat1(v) = (m1/N1) omegahat1(m1 v / N1) (scaling in the proof of Theorem 3.4).
-        std::vector<double> r((size_t)S.ncell * NR);
-        for (int ic = 0; ic < S.ncell; ++ic) {
-            const double c = (double)(S.c_lo + ic);
-            auto f = [&](double y) {
-                const double x = (c + 0.5 * (y + 1.0)) / S.uscale;
-                const double w = (double)d.m1 * (double)d.Nstar * x / (double)d.N1;
-                return (double)d.N1 / ((double)d.m1 * hm::omega_sinh_hat(w, d.beta1));
-            };
-            hm::cheb_interp(f, NR, r.data() + (size_t)ic * NR);
+    if (!v.empty())
+        NN_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    return NNFFT_OK;
+}
+
+// Prefix sums of per-instance block counts: blk[i] = first block of instance i.
+std::vector<int> prefix(const std::vector<int> &cnt, int *total) {
+    std::vector<int> off(cnt.size() + 1, 0);
+    for (size_t i = 0; i < cnt.size(); ++i) off[i + 1] = off[i] + cnt[i];
+    *total = off.back();
+    return off;
+}
+
+// Per-instance host data gathered while the plan is built.
+struct InstHost {
+    hm::Derived d;
+    std::vector<double> coef[2];
+};
+
+// Grid-stage descriptor tables of one side for one real/coefficient type.
+template <typename CoefT>
+int upload_grid_tables(nnfft_plan_s *p, Side &S, int s, const void *coef_base, const void *dec_base,
+                       const std::vector<long long> &dec_off, const void *rfit_base,
+                       const std::vector<long long> &cell_base, const std::vector<long long> &grid_base,
+                       void **dst) {
+    const int64_t n = p->ninst;
+    std::vector<GridInst<CoefT>> tab((size_t)n);
+    const size_t per = (size_t)2 * S.m * S.D;
+    for (int64_t i = 0; i < n; ++i) {
+        const nnfft_info &I = p->inst_info[(size_t)i];
+        GridInst<CoefT> &G = tab[(size_t)i];
+        memset(&G, 0, sizeof(G));
+        const double us = s == 0 ? (double)I.N1 * (double)I.N / (double)I.Nstar
+                                 : (double)I.N2 * (double)I.Nstar / (double)I.N1;
+        G.c_lo = (long long)std::floor(-0.5 * us);
+        G.ncell = (int)(s == 0 ? I.ncell1 : I.ncell2);
+        G.cell_base = (int)cell_base[(size_t)i];
+        G.N2 = (int)I.N2;
+        G.grid_base = grid_base[(size_t)i];
+        G.coef = static_cast<const CoefT *>(coef_base) + per * (size_t)i;
+        if (s == 0) {
+            G.scale = static_cast<const CoefT *>(dec_base) + dec_off[(size_t)i];
+            G.scale_off = I.K1 / 2;
+            G.scale_len = I.K1;
         }
-        rc = upload_real(p, &S.rfit, r, "phihat1 fit");
-        if (rc) return rc;
-        p->rfit_host = r;
+        if (s == 1 && rfit_base)
+            G.rfit = static_cast<const CoefT *>(rfit_base) + (size_t)cell_base[(size_t)i] * NR;
     }
-    const size_t M = (size_t)S.M;
+    GridInst<CoefT> *d = nullptr;
+    int rc = upload_vec(p, &d, tab, "grid tables");
+    *dst = d;
+    return rc;
+}
+
+// Step 0 (i) for every instance and both sides: window fits at a common degree per side,
+// binning tables, 1/phihat1 fits, deconvolution tables, FFT tables, the grid-stage
+// descriptors and block maps, and all device buffers.
+int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t *M1s,
+               const int64_t *M2s, double sigma1, double sigma2, int m1, int m2,
+               nnfft_dtype dtype) {
+    int rc;
+    p->ninst = count;
+    p->dbl = dtype == NNFFT_C128;
+    p->inst_info.assign((size_t)count, nnfft_info{});
+    std::vector<InstHost> H((size_t)count);
+    int D[2] = {0, 0};
+    long long Mtot[2] = {0, 0};
+    for (int64_t i = 0; i < count; ++i) {
+        rc = fill_info(Ns[i], M1s[i], M2s[i], sigma1, sigma2, m1, m2, dtype, &p->inst_info[(size_t)i],
+                       &H[(size_t)i].d, &H[(size_t)i].coef[0], &H[(size_t)i].coef[1]);
+        if (rc) return count > 1 ? fail(rc, "instance " + std::to_string(i) + ": " + g_last_error) : rc;
+        D[0] = std::max(D[0], (int)p->inst_info[(size_t)i].D1);
+        D[1] = std::max(D[1], (int)p->inst_info[(size_t)i].D2);
+        Mtot[0] += M1s[i];
+        Mtot[1] += M2s[i];
+    }
+    if (Mtot[0] > (1LL << 30) || Mtot[1] > (1LL << 30))
+        return fail(NNFFT_EINVAL, "total M1 and M2 of a plan must be <= 2^30");
+    // one degree per side for all instances: refit the instances that chose fewer terms
+    for (int64_t i = 0; i < count; ++i) {
+        nnfft_info &I = p->inst_info[(size_t)i];
+        if (I.D1 != D[0]) { I.fit_err1 = hm::fit_taps(m1, I.beta1, D[0], H[(size_t)i].coef[0]); I.D1 = D[0]; }
+        if (I.D2 != D[1]) { I.fit_err2 = hm::fit_taps(m2, I.beta2, D[1], H[(size_t)i].coef[1]); I.D2 = D[1]; }
+    }
+    if (!supported_degree(D[0]) || !supported_degree(D[1]))
+        return fail(NNFFT_EINVAL, "unsupported window degree");
+    // Split precision (fp64 plans): degrees >= D/2 run in FP32, so their weights
+    // kappa_d = max_t |coef[t][d]| must be small enough that an FP32 error there stays
+    // near 1e-13 of ||f||_1 in the worst case.
+    p->split_ok = p->dbl && df_supported_degree(D[0]) && df_supported_degree(D[1]);
+    for (int64_t i = 0; i < count && p->split_ok; ++i)
+        p->split_ok = split_weights_ok(H[(size_t)i].coef[0], 2 * m1, D[0]) &&
+                      split_weights_ok(H[(size_t)i].coef[1], 2 * m2, D[1]);
+    p->split = p->split_ok;
+
+    // grid layout: instance i's grid buffer [grid_base, grid_base + N2)
+    std::vector<long long> grid_base((size_t)count);
+    long long gtot = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        grid_base[(size_t)i] = gtot;
+        gtot += p->inst_info[(size_t)i].N2;
+    }
+    p->grid_total = gtot;
+
+    // aggregate info: the instance itself, or totals / maxima for a batch
+    p->info = p->inst_info[0];
+    if (count > 1) {
+        nnfft_info &A = p->info;
+        A.M1 = Mtot[0];
+        A.M2 = Mtot[1];
+        A.N = A.Nstar = A.N1 = A.K1 = 0;
+        A.N2 = gtot;
+        A.ncell1 = A.ncell2 = 0;
+        A.fit_err1 = A.fit_err2 = 0;
+        A.fft_n1 = A.fft_n2 = 0;
+        for (const nnfft_info &I : p->inst_info) {
+            A.N = std::max(A.N, I.N);
+            A.Nstar = std::max(A.Nstar, I.Nstar);
+            A.N1 += I.N1;
+            A.K1 += I.K1;
+            A.ncell1 += I.ncell1;
+            A.ncell2 += I.ncell2;
+            A.fit_err1 = std::max(A.fit_err1, I.fit_err1);
+            A.fit_err2 = std::max(A.fit_err2, I.fit_err2);
+            A.fft_n1 = std::max(A.fft_n1, I.fft_n1);
+            A.fft_n2 = std::max(A.fft_n2, I.fft_n2);
+        }
+    }
+    const int arith = !p->dbl ? NNFFT_ARITH_FP32 : (p->split ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64);
+    p->info.arith = arith;
+    for (nnfft_info &I : p->inst_info) I.arith = arith;
+
+    // deconvolution tables dec2[l] = 1 / (N1 N2 phihat2(l)), l in I_{K1}: the 1/N1 of
+    // eq. (gell), the division of step 2 and the 1/N2 of step 3, with
+    // phihat2(l) = (m2/N2) omegahat2(m2 l / N2); concatenated over instances.
+    std::vector<double> dec;
+    std::vector<long long> dec_off((size_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        const nnfft_info &I = p->inst_info[(size_t)i];
+        dec_off[(size_t)i] = (long long)dec.size();
+        for (int64_t k = 0; k < I.K1; ++k) {
+            const double l = (double)(k - I.K1 / 2);
+            dec.push_back(1.0 / ((double)I.N1 * (double)m2 *
+                                 hm::omega_sinh_hat((double)m2 * l / (double)I.N2, I.beta2)));
+        }
+    }
+    void *dec_real = nullptr, *dec_df = nullptr;
+    if ((rc = upload_real(p, &dec_real, dec, "deconvolution table"))) return rc;
+    if (p->split_ok && (rc = upload_df2(p, &dec_df, dec, 1.0, "deconvolution table (df)"))) return rc;
+
     const size_t rs = real_size(p->dbl);
-    if ((rc = dalloc_n(p, &S.keys, M, "keys")) || (rc = dalloc_n(p, &S.keys_alt, M, "keys")) ||
-        (rc = dalloc_n(p, &S.vals, M, "perm")) || (rc = dalloc_n(p, &S.vals_alt, M, "perm")) ||
-        (rc = dalloc_n(p, &S.hist, radix_sort_hist_len(S.M), "sort histogram")) ||
-        (rc = dalloc(p, &S.ys, M * rs, "sorted coordinates")) ||
-        (rc = dalloc(p, &S.y_user, M * rs, "coordinates")) ||
-        (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
-        (rc = dalloc_n(p, &S.item_cnt, (size_t)S.ncell + 1, "item counts")) ||
-        (rc = dalloc_n(p, &S.item_off, (size_t)S.ncell + 1, "item offsets")) ||
-        (rc = dalloc_n(p, &S.item_cell, (size_t)S.max_items, "items")) ||
-        (rc = dalloc_n(p, &S.item_pb, (size_t)S.max_items, "items")) ||
-        (rc = dalloc_n(p, &S.item_pe, (size_t)S.max_items, "items")) ||
-        (rc = dalloc_n(p, &S.nitems, 1, "item count")))
-        return rc;
-    NN_CUDA(cudaMemset(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1)), "memset");
-    NN_CUDA(cudaMemset(S.nitems, 0, sizeof(int)), "memset");
+    for (int s = 0; s < 2; ++s) {
+        Side &S = p->side[s];
+        S.m = s == 0 ? m1 : m2;
+        S.D = D[s];
+        S.has_r = s == 1;
+        std::vector<NodeInst> tab((size_t)count);
+        std::vector<long long> pt_off((size_t)count + 1, 0), cell_base((size_t)count);
+        std::vector<double> coef_all, rfit_all;
+        long long cells = 0;
+        for (int64_t i = 0; i < count; ++i) {
+            const nnfft_info &I = p->inst_info[(size_t)i];
+            const hm::Derived &d = H[(size_t)i].d;
+            NodeInst &T = tab[(size_t)i];
+            T.uscale = s == 0 ? (double)d.N1 * (double)d.N / (double)d.Nstar
+                              : (double)d.N2 * (double)d.Nstar / (double)d.N1;
+            T.c_lo = (long long)std::floor(-0.5 * T.uscale);
+            T.ncell = (int)(s == 0 ? I.ncell1 : I.ncell2);
+            T.cell_base = (int)cells;
+            cell_base[(size_t)i] = cells;
+            cells += T.ncell;
+            pt_off[(size_t)i + 1] = pt_off[(size_t)i] + (s == 0 ? I.M1 : I.M2);
+            const std::vector<double> &c = H[(size_t)i].coef[s];
+            coef_all.insert(coef_all.end(), c.begin(), c.end());
+            if (S.has_r) {
+                // Per x cell c: Chebyshev fit in y of 1/phihat1(N* x), x = (c + (y+1)/2)/uscale,
+                // phihat1(v) = (m1/N1) omegahat1(m1 v / N1) (scaling in the proof of Theorem 3.4).
+                const size_t r0 = rfit_all.size();
+                rfit_all.resize(r0 + (size_t)T.ncell * NR);
+                for (int ic = 0; ic < T.ncell; ++ic) {
+                    const double cc = (double)(T.c_lo + ic);
+                    auto f = [&](double y) {
+                        const double x = (cc + 0.5 * (y + 1.0)) / T.uscale;
+                        const double w = (double)d.m1 * (double)d.Nstar * x / (double)d.N1;
+                        return (double)d.N1 / ((double)d.m1 * hm::omega_sinh_hat(w, d.beta1));
+                    };
+                    hm::cheb_interp(f, NR, rfit_all.data() + r0 + (size_t)ic * NR);
+                }
+            }
+        }
+        if (cells > (1LL << 30)) return fail(NNFFT_EINVAL, "too many grid cells in one plan");
+        S.ncell = (int)cells;
+        S.M = (int)pt_off.back();
+        S.max_items = S.ncell + (S.M + ITEM_CAP - 1) / ITEM_CAP + (int)count;
+        S.key_bits = key_bits_for(S.ncell);
+        S.one = tab[0];
+        if (count > 1) {
+            if ((rc = upload_vec(p, &S.node_tab, tab, "binning tables")) ||
+                (rc = upload_vec(p, &S.pt_off, pt_off, "instance offsets")))
+                return rc;
+        }
+        if ((rc = upload_real(p, &S.coef, coef_all, "window coefficients"))) return rc;
+        if (p->split_ok && (rc = upload_df2(p, &S.coef_df, coef_all, 1.0, "window coefficients (df)")))
+            return rc;
+        if (S.has_r) {
+            if ((rc = upload_real(p, &S.rfit, rfit_all, "phihat1 fit"))) return rc;
+            if (p->split_ok && (rc = upload_df2(p, &S.rfit_df, rfit_all, 0.5, "phihat1 fit (df)")))
+                return rc;
+        }
+        // grid-stage descriptors and block maps
+        rc = p->dbl ? upload_grid_tables<double>(p, S, s, S.coef, dec_real, dec_off, S.rfit,
+                                                 cell_base, grid_base, &S.grid_real)
+                    : upload_grid_tables<float>(p, S, s, S.coef, dec_real, dec_off, S.rfit,
+                                                cell_base, grid_base, &S.grid_real);
+        if (rc) return rc;
+        if (p->split_ok &&
+            (rc = upload_grid_tables<float2>(p, S, s, S.coef_df, dec_df, dec_off, S.rfit_df,
+                                             cell_base, grid_base, &S.grid_df)))
+            return rc;
+        std::vector<int> sn((size_t)count), gn((size_t)count), sd((size_t)count), gd((size_t)count);
+        for (int64_t i = 0; i < count; ++i) {
+            const int N2 = (int)p->inst_info[(size_t)i].N2, nc = tab[(size_t)i].ncell;
+            sn[(size_t)i] = spread_blocks_native(N2, S.D);
+            gn[(size_t)i] = gather_blocks_native(nc, S.D);
+            sd[(size_t)i] = p->split_ok ? spread_blocks_df(N2, S.D) : 0;
+            gd[(size_t)i] = p->split_ok ? gather_blocks_df(nc, S.D) : 0;
+        }
+        if ((rc = upload_vec(p, &S.blk_sn, prefix(sn, &S.nb_sn), "block map")) ||
+            (rc = upload_vec(p, &S.blk_gn, prefix(gn, &S.nb_gn), "block map")) ||
+            (rc = upload_vec(p, &S.blk_sd, prefix(sd, &S.nb_sd), "block map")) ||
+            (rc = upload_vec(p, &S.blk_gd, prefix(gd, &S.nb_gd), "block map")))
+            return rc;
+        // node-time buffers
+        const size_t M = (size_t)S.M;
+        if ((rc = dalloc_n(p, &S.keys, M, "keys")) || (rc = dalloc_n(p, &S.keys_alt, M, "keys")) ||
+            (rc = dalloc_n(p, &S.vals, M, "perm")) || (rc = dalloc_n(p, &S.vals_alt, M, "perm")) ||
+            (rc = dalloc_n(p, &S.hist, radix_sort_hist_len(S.M), "sort histogram")) ||
+            (rc = dalloc(p, &S.ys, M * rs, "sorted coordinates")) ||
+            (rc = dalloc(p, &S.y_user, M * rs, "coordinates")) ||
+            (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
+            (rc = dalloc_n(p, &S.item_off, (size_t)S.ncell + 1, "item offsets")) ||
+            (rc = dalloc_n(p, &S.items_scratch, build_items_scratch_len(S.ncell), "item scratch")) ||
+            (rc = dalloc_n(p, &S.item_cell, (size_t)S.max_items, "items")) ||
+            (rc = dalloc_n(p, &S.item_pb, (size_t)S.max_items, "items")) ||
+            (rc = dalloc_n(p, &S.item_pe, (size_t)S.max_items, "items")) ||
+            (rc = dalloc_n(p, &S.nitems, 1, "item count")))
+            return rc;
+        NN_CUDA(cudaMemset(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1)), "memset");
+        NN_CUDA(cudaMemset(S.nitems, 0, sizeof(int)), "memset");
+    }
+
+    // FFT tables: twiddles exp(-2 pi i k/n) for every distinct length, concatenated
+    {
+        std::map<int64_t, size_t> at;          // length -> first complex entry
+        std::vector<double> tw;
+        auto twid_of = [&](int64_t n) {
+            auto it = at.find(n);
+            if (it != at.end()) return it->second;
+            const size_t off = tw.size() / 2;
+            const std::vector<double> t = twiddles(n);
+            tw.insert(tw.end(), t.begin(), t.end());
+            at[n] = off;
+            return off;
+        };
+        std::vector<FftPlanDev> F((size_t)count);
+        std::vector<FftDf> G((size_t)count);
+        std::vector<int> c1((size_t)count), c2((size_t)count);
+        std::vector<size_t> o1((size_t)count), o2((size_t)count), oN((size_t)count);
+        int max1 = 0, max2 = 0;
+        for (int64_t i = 0; i < count; ++i) {
+            const nnfft_info &I = p->inst_info[(size_t)i];
+            FftPlanDev &f = F[(size_t)i];
+            memset(&f, 0, sizeof(f));
+            f.N2 = (int)I.N2;
+            f.n1 = (int)I.fft_n1;
+            f.n2 = (int)I.fft_n2;
+            f.nr1 = hm::radices(f.n1, f.r1, FFT_MAX_STAGES);
+            f.nr2 = hm::radices(f.n2, f.r2, FFT_MAX_STAGES);
+            if (f.nr1 < 0 || f.nr2 < 0) return fail(NNFFT_EINVAL, "FFT factorisation failed");
+            f.grid_base = grid_base[(size_t)i];
+            o1[(size_t)i] = twid_of(f.n1);
+            o2[(size_t)i] = twid_of(f.n2);
+            oN[(size_t)i] = twid_of(f.N2);
+            c1[(size_t)i] = f.n2;               // pass 1: one block per column
+            c2[(size_t)i] = f.n1;               // pass 2: one block per row
+            max1 = std::max(max1, f.n1);
+            max2 = std::max(max2, f.n2);
+        }
+        void *tw_real = nullptr, *tw_df = nullptr;
+        if ((rc = upload_real(p, &tw_real, tw, "twiddles"))) return rc;
+        if (p->split_ok && (rc = upload_df2(p, &tw_df, tw, 1.0, "twiddles (df)"))) return rc;
+        const size_t cs = 2 * rs;
+        for (int64_t i = 0; i < count; ++i) {
+            FftPlanDev &f = F[(size_t)i];
+            f.tw1 = static_cast<const char *>(tw_real) + cs * o1[(size_t)i];
+            f.tw2 = static_cast<const char *>(tw_real) + cs * o2[(size_t)i];
+            f.twN = static_cast<const char *>(tw_real) + cs * oN[(size_t)i];
+            FftDf &g = G[(size_t)i];
+            memset(&g, 0, sizeof(g));
+            g.N2 = f.N2;
+            g.n1 = f.n1;
+            g.n2 = f.n2;
+            g.nr1 = f.nr1;
+            g.nr2 = f.nr2;
+            for (int k = 0; k < FFT_MAX_STAGES; ++k) {
+                g.r1[k] = f.r1[k];
+                g.r2[k] = f.r2[k];
+            }
+            g.grid_base = f.grid_base;
+            if (tw_df) {
+                g.tw1 = static_cast<const float4 *>(tw_df) + o1[(size_t)i];
+                g.tw2 = static_cast<const float4 *>(tw_df) + o2[(size_t)i];
+                g.twN = static_cast<const float4 *>(tw_df) + oN[(size_t)i];
+            }
+        }
+        int n1tot = 0, n2tot = 0;
+        int *b1 = nullptr, *b2 = nullptr;
+        FftPlanDev *fd = nullptr;
+        if ((rc = upload_vec(p, &b1, prefix(c1, &n1tot), "FFT block map")) ||
+            (rc = upload_vec(p, &b2, prefix(c2, &n2tot), "FFT block map")) ||
+            (rc = upload_vec(p, &fd, F, "FFT tables")))
+            return rc;
+        p->fft = FftLaunch<FftPlanDev>{fd, b1, b2, (int)count, n1tot, n2tot, max1, max2};
+        if (p->split_ok) {
+            FftDf *gd = nullptr;
+            if ((rc = upload_vec(p, &gd, G, "FFT tables (df)"))) return rc;
+            p->fftdf = FftLaunch<FftDf>{gd, b1, b2, (int)count, n1tot, n2tot, max1, max2};
+        }
+    }
+    // work buffers
+    {
+        const size_t cs = 2 * rs;
+        size_t pmax = 0, qmax = 0;
+        for (int s = 0; s < 2; ++s) {
+            pmax = std::max(pmax, (size_t)p->side[s].max_items * p->side[s].D);
+            qmax = std::max(qmax, (size_t)p->side[s].ncell * p->side[s].D);
+        }
+        const size_t G2 = (size_t)gtot;
+        if ((rc = dalloc(p, &p->bufA, G2 * cs, "grid")) || (rc = dalloc(p, &p->bufB, G2 * cs, "grid")) ||
+            (rc = dalloc(p, &p->bufC, G2 * cs, "grid")) || (rc = dalloc(p, &p->P, pmax * cs, "moments")) ||
+            (rc = dalloc(p, &p->Q, qmax * cs, "cell windows")))
+            return rc;
+    }
     return NNFFT_OK;
 }
 
@@ -328,8 +629,8 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     k.m = S.m;
     k.D = S.D;
     k.ncell = S.ncell;
-    k.c_lo = S.c_lo;
-    k.coef = static_cast<const Real *>(S.coef);
+    k.c_lo = 0;
+    k.coef = nullptr;
     k.rfit = with_r ? static_cast<const Real *>(S.rfit) : nullptr;
     k.perm = S.perm;
     k.ys = static_cast<const Real *>(S.ys);
@@ -340,6 +641,22 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     k.nitems = S.nitems;
     k.max_items = S.max_items;
     return k;
+}
+
+// Grid-stage launch over all instances of one side.
+template <typename CoefT>
+GridLaunch<CoefT> grid_launch(const nnfft_plan_s *p, int s, bool spread, bool fold) {
+    const Side &S = p->side[s];
+    constexpr bool df = std::is_same<CoefT, float2>::value;
+    GridLaunch<CoefT> L;
+    L.inst = static_cast<const GridInst<CoefT> *>(df ? S.grid_df : S.grid_real);
+    L.blk = spread ? (df ? S.blk_sd : S.blk_sn) : (df ? S.blk_gd : S.blk_gn);
+    L.nblocks = spread ? (df ? S.nb_sd : S.nb_sn) : (df ? S.nb_gd : S.nb_gn);
+    L.ninst = (int)p->ninst;
+    L.m = S.m;
+    L.D = S.D;
+    L.fold = fold;
+    return L;
 }
 
 int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st) {
@@ -354,8 +671,8 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     }
     const int yfmt = !p->dbl ? 0 : (p->split ? 2 : 1);
     const int ybytes = p->dbl ? 8 : 4;
-    NN_CUDA(launch_node_keys_y(nodes, S.M, S.uscale, S.c_lo, S.ncell, S.keys, S.y_user, yfmt,
-                               S.hist, p->status, st),
+    NN_CUDA(launch_node_keys_y(nodes, S.M, S.one, S.pt_off, S.node_tab, (int)p->ninst, S.keys,
+                               S.y_user, yfmt, S.hist, p->status, st),
             "node keys");
     uint32_t *ks = nullptr;
     int *vs = nullptr;
@@ -366,7 +683,7 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     S.keys_sorted = ks;
     NN_CUDA(launch_cell_offsets(ks, S.M, S.ncell, S.cell_off, st), "cell offsets");
     NN_CUDA(launch_build_items_fused(S.cell_off, S.ncell, S.item_off, S.item_cell, S.item_pb,
-                                     S.item_pe, S.nitems, st),
+                                     S.item_pe, S.nitems, S.items_scratch, st),
             "work items");
     S.set = true;
     return NNFFT_OK;
@@ -378,10 +695,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
     if (X.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
-    const SideDf tv{static_cast<const float2 *>(p->coef_df[0]), nullptr};
-    const SideDf tx{static_cast<const float2 *>(p->coef_df[1]), static_cast<const float2 *>(p->rfit_df)};
-    const long long K1 = p->info.K1;
-    const int N2 = (int)p->info.N2;
+    const SideDf tv{nullptr, nullptr};
     {
         StageTimer t(p, 2);
         NN_CUDA(launch_moments_df(sv, f, p->P, st), "spread moments");
@@ -392,8 +706,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
     }
     {
         StageTimer t(p, 3);
-        NN_CUDA(launch_spread_conv_df(sv, tv, p->Q, static_cast<const float2 *>(p->dec2_df), K1 / 2,
-                                      K1, N2, p->bufA, st),
+        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), p->Q, p->bufA, st),
                 "spread convolution");
     }
     {
@@ -402,7 +715,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
     }
     {
         StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv_df(sx, tx, p->bufC, nullptr, 0, 0, N2, p->Q, st),
+        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), p->bufC, p->Q, st),
                 "gather convolution");
     }
     {
@@ -418,11 +731,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
     if (V.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
-    const SideDf tv{static_cast<const float2 *>(p->coef_df[0]), nullptr};
-    const SideDf tx{static_cast<const float2 *>(p->coef_df[1]), static_cast<const float2 *>(p->rfit_df)};
-    const SideDf tx_nofold{static_cast<const float2 *>(p->coef_df[1]), nullptr};
-    const long long K1 = p->info.K1;
-    const int N2 = (int)p->info.N2;
+    const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
     {
         StageTimer t(p, 7);
         NN_CUDA(launch_moments_df(sx, g, p->P, st), "adjoint spread moments");
@@ -433,7 +742,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
     }
     {
         StageTimer t(p, 8);
-        NN_CUDA(launch_spread_conv_df(sx, tx_nofold, p->Q, nullptr, 0, 0, N2, p->bufA, st),
+        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), p->Q, p->bufA, st),
                 "adjoint spread convolution");
     }
     {
@@ -442,8 +751,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
     }
     {
         StageTimer t(p, 10);
-        NN_CUDA(launch_gather_conv_df(sv, tv, p->bufC, static_cast<const float2 *>(p->dec2_df),
-                                      K1 / 2, K1, N2, p->Q, st),
+        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), p->bufC, p->Q, st),
                 "adjoint gather convolution");
     }
     {
@@ -459,8 +767,6 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     if (X.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
-    const long long K1 = p->info.K1;
-    const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 2);
         NN_CUDA(launch_moments<Real>(sv, f, p->P, st), "spread moments");
@@ -471,8 +777,7 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     }
     {
         StageTimer t(p, 3);
-        NN_CUDA(launch_spread_conv<Real>(sv, p->Q, static_cast<const Real *>(p->dec2), K1 / 2, K1,
-                                         N2, p->bufA, st),
+        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 0, true, false), p->Q, p->bufA, st),
                 "spread convolution");
     }
     {
@@ -481,7 +786,7 @@ template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y
     }
     {
         StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv<Real>(sx, p->bufC, nullptr, 0, 0, N2, p->Q, st),
+        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), p->bufC, p->Q, st),
                 "gather convolution");
     }
     {
@@ -497,8 +802,6 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     if (V.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
-    const long long K1 = p->info.K1;
-    const int N2 = (int)p->info.N2;
     {
         StageTimer t(p, 7);
         NN_CUDA(launch_moments<Real>(sx, g, p->P, st), "adjoint spread moments");
@@ -509,7 +812,7 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     }
     {
         StageTimer t(p, 8);
-        NN_CUDA(launch_spread_conv<Real>(sx, p->Q, nullptr, 0, 0, N2, p->bufA, st),
+        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 1, true, false), p->Q, p->bufA, st),
                 "adjoint spread convolution");
     }
     {
@@ -518,8 +821,7 @@ template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z
     }
     {
         StageTimer t(p, 10);
-        NN_CUDA(launch_gather_conv<Real>(sv, p->bufC, static_cast<const Real *>(p->dec2), K1 / 2,
-                                         K1, N2, p->Q, st),
+        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), p->bufC, p->Q, st),
                 "adjoint gather convolution");
     }
     {
@@ -587,10 +889,13 @@ int nnfft_gauss_legendre(int64_t n, double *tau_host, double *w_host) {
     return NNFFT_OK;
 }
 
-int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigma1,
-               double sigma2, int m1, int m2, nnfft_dtype dtype, void *stream) {
+int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
+                     const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
+                     nnfft_dtype dtype, void *stream) {
     if (!out) return fail(NNFFT_EINVAL, "null plan pointer");
     *out = nullptr;
+    if (count < 1 || !N || !M1 || !M2) return fail(NNFFT_EINVAL, "a plan needs >= 1 instance");
+    if (count > (1 << 20)) return fail(NNFFT_EINVAL, "too many instances in one plan");
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -599,19 +904,12 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
     }
     nnfft_plan_s *p = new nnfft_plan_s();
     p->stream = static_cast<cudaStream_t>(stream);
-    p->dbl = dtype == NNFFT_C128;
-    hm::Derived d;
-    std::vector<double> coef1, coef2;
-    int rc = fill_info(N, M1, M2, sigma1, sigma2, m1, m2, dtype, &p->info, &d, &coef1, &coef2);
-    if (rc) { delete p; return rc; }
-    const nnfft_info &I = p->info;
-    const size_t rs = real_size(p->dbl), cs = 2 * rs;
     auto bail = [&](int code) { free_plan(p); return code; };
-
     if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return bail(cuda_fail(cudaGetLastError(), "stream/event creation"));
+    int rc;
     if ((rc = dalloc_n(p, &p->status, 1, "status"))) return bail(rc);
     if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     if (cudaMallocHost(&p->status_host, sizeof(int)) != cudaSuccess) {
@@ -619,88 +917,26 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
         cudaGetLastError();
         return bail(fail(NNFFT_ENOMEM, "cudaMallocHost(status)"));
     }
-    if ((rc = setup_side(p, 0, d, coef1))) return bail(rc);
-    if ((rc = setup_side(p, 1, d, coef2))) return bail(rc);
-    // Split precision (fp64 plans): degrees >= D/2 run in FP32, so their weights
-    // kappa_d = max_t |coef[t][d]| must be small enough that an FP32 error there stays
-    // near 1e-13 of ||f||_1 in the worst case.
-    p->split_ok = p->dbl && df_supported_degree(I.D1) && df_supported_degree(I.D2) &&
-                  split_weights_ok(coef1, 2 * d.m1, I.D1) && split_weights_ok(coef2, 2 * d.m2, I.D2);
-    p->split = p->split_ok;
-    p->info.arith = !p->dbl ? NNFFT_ARITH_FP32 : (p->split ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64);
-    if (p->split_ok) {
-        if ((rc = upload_df2(p, &p->coef_df[0], coef1, 1.0, "window coefficients (df)")) ||
-            (rc = upload_df2(p, &p->coef_df[1], coef2, 1.0, "window coefficients (df)")))
-            return bail(rc);
-    }
-
-    // dec2[l] = 1 / (N1 N2 phihat2(l)), l in I_{K1}: the 1/N1 of eq. (gell), the division
-    // of step 2 and the 1/N2 of step 3, with phihat2(l) = (m2/N2) omegahat2(m2 l / N2).
-    {
-        std::vector<double> dec((size_t)I.K1);
-        for (int64_t i = 0; i < I.K1; ++i) {
-            const double l = (double)(i - I.K1 / 2);
-            dec[(size_t)i] = 1.0 / ((double)I.N1 * (double)d.m2 *
-                                    hm::omega_sinh_hat((double)d.m2 * l / (double)I.N2, d.beta2));
-        }
-        if ((rc = upload_real(p, &p->dec2, dec, "deconvolution table"))) return bail(rc);
-        if (p->split_ok && (rc = upload_df2(p, &p->dec2_df, dec, 1.0, "deconvolution table (df)")))
-            return bail(rc);
-        if (p->split_ok && (rc = upload_df2(p, &p->rfit_df, p->rfit_host, 0.5, "phihat1 fit (df)")))
-            return bail(rc);
-    }
-    // FFT tables
-    {
-        FftPlanDev &F = p->fft;
-        F.N2 = (int)I.N2;
-        F.n1 = (int)I.fft_n1;
-        F.n2 = (int)I.fft_n2;
-        F.nr1 = hm::radices(F.n1, F.r1, FFT_MAX_STAGES);
-        F.nr2 = hm::radices(F.n2, F.r2, FFT_MAX_STAGES);
-        if (F.nr1 < 0 || F.nr2 < 0) return bail(fail(NNFFT_EINVAL, "FFT factorisation failed"));
-        void *t1 = nullptr, *t2 = nullptr, *tN = nullptr;
-        if ((rc = upload_real(p, &t1, twiddles(F.n1), "twiddles")) ||
-            (rc = upload_real(p, &t2, twiddles(F.n2), "twiddles")) ||
-            (rc = upload_real(p, &tN, twiddles(F.N2), "twiddles")))
-            return bail(rc);
-        F.tw1 = t1;
-        F.tw2 = t2;
-        F.twN = tN;
-        if (p->split_ok) {
-            FftDf &G = p->fftdf;
-            G.N2 = F.N2;
-            G.n1 = F.n1;
-            G.n2 = F.n2;
-            G.nr1 = F.nr1;
-            G.nr2 = F.nr2;
-            for (int i = 0; i < FFT_MAX_STAGES; ++i) {
-                G.r1[i] = F.r1[i];
-                G.r2[i] = F.r2[i];
-            }
-            void *u1 = nullptr, *u2 = nullptr, *uN = nullptr;
-            if ((rc = upload_df2(p, &u1, twiddles(F.n1), 1.0, "twiddles (df)")) ||
-                (rc = upload_df2(p, &u2, twiddles(F.n2), 1.0, "twiddles (df)")) ||
-                (rc = upload_df2(p, &uN, twiddles(F.N2), 1.0, "twiddles (df)")))
-                return bail(rc);
-            G.tw1 = static_cast<const float4 *>(u1);
-            G.tw2 = static_cast<const float4 *>(u2);
-            G.twN = static_cast<const float4 *>(uN);
-        }
-    }
-    // work buffers
-    {
-        const size_t N2 = (size_t)I.N2;
-        size_t pmax = 0, qmax = 0;
-        for (int s = 0; s < 2; ++s) {
-            pmax = std::max(pmax, (size_t)p->side[s].max_items * p->side[s].D);
-            qmax = std::max(qmax, (size_t)p->side[s].ncell * p->side[s].D);
-        }
-        if ((rc = dalloc(p, &p->bufA, N2 * cs, "grid")) || (rc = dalloc(p, &p->bufB, N2 * cs, "grid")) ||
-            (rc = dalloc(p, &p->bufC, N2 * cs, "grid")) || (rc = dalloc(p, &p->P, pmax * cs, "moments")) ||
-            (rc = dalloc(p, &p->Q, qmax * cs, "cell windows")))
-            return bail(rc);
-    }
+    if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype))) return bail(rc);
     *out = p;
+    return NNFFT_OK;
+}
+
+int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigma1,
+               double sigma2, int m1, int m2, nnfft_dtype dtype, void *stream) {
+    return nnfft_batch_plan(out, 1, &N, &M1, &M2, sigma1, sigma2, m1, m2, dtype, stream);
+}
+
+int nnfft_batch_count(nnfft_plan_t p, int64_t *count) {
+    if (!p || !count) return fail(NNFFT_EINVAL, "null argument");
+    *count = p->ninst;
+    return NNFFT_OK;
+}
+
+int nnfft_batch_info(nnfft_plan_t p, int64_t i, nnfft_info *out) {
+    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
+    if (i < 0 || i >= p->ninst) return fail(NNFFT_EINVAL, "instance index out of range");
+    *out = p->inst_info[(size_t)i];
     return NNFFT_OK;
 }
 
@@ -768,6 +1004,7 @@ int nnfft_set_arith(nnfft_plan_t p, int arith) {
         p->side[0].set = p->side[1].set = false;     // coordinates are stored per mode
     }
     p->info.arith = want ? NNFFT_ARITH_FP64_SPLIT : NNFFT_ARITH_FP64;
+    for (nnfft_info &I : p->inst_info) I.arith = p->info.arith;
     return NNFFT_OK;
 }
 
@@ -951,8 +1188,10 @@ int cc_rule_device(int64_t n, double *w, double *half_z, double *neg_half_z, cud
     F.nr2 = hm::radices(n2, F.r2, FFT_MAX_STAGES);
     if (F.nr1 < 0 || F.nr2 < 0) return fail(NNFFT_EINVAL, "FFT factorisation failed");
     void *t1 = nullptr, *t2 = nullptr, *tN = nullptr, *x = nullptr, *y = nullptr, *X = nullptr;
+    void *tab = nullptr;     // the FftPlanDev, then the two block maps {0, n2} and {0, n1}
     auto release = [&]() {
         cudaFree(t1); cudaFree(t2); cudaFree(tN); cudaFree(x); cudaFree(y); cudaFree(X);
+        cudaFree(tab);
     };
     cudaError_t e = cudaSuccess;
     const std::vector<double> w1 = twiddles(n1), w2 = twiddles(n2), wN = twiddles(L);
@@ -968,8 +1207,18 @@ int cc_rule_device(int64_t n, double *w, double *half_z, double *neg_half_z, cud
     F.tw1 = t1;
     F.tw2 = t2;
     F.twN = tN;
+    F.grid_base = 0;
+    const size_t fb = (sizeof(FftPlanDev) + 15) / 16 * 16;
+    const int blk[4] = {0, n2, 0, n1};
+    if (e == cudaSuccess) e = cudaMalloc(&tab, fb + sizeof(blk));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tab, &F, sizeof(F), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char *>(tab) + fb, blk, sizeof(blk), cudaMemcpyHostToDevice, st);
+    const int *blk_dev = reinterpret_cast<const int *>(static_cast<char *>(tab) + fb);
+    const FftLaunch<FftPlanDev> FL{static_cast<const FftPlanDev *>(tab), blk_dev, blk_dev + 2, 1,
+                                   n2, n1, n1, n2};
     if (e == cudaSuccess) e = launch_cc_extend(n, x, st);
-    if (e == cudaSuccess) e = launch_fft<double>(F, x, y, X, -1, st);
+    if (e == cudaSuccess) e = launch_fft<double>(FL, x, y, X, -1, st);
     if (e == cudaSuccess) e = launch_cc_finish(n, X, w, half_z, neg_half_z, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     release();

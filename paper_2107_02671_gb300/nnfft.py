@@ -78,6 +78,10 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_params.argtypes = [i64, i64, i64, dbl, dbl, cint, cint, cint, P(Info)]
         lib.nnfft_plan.argtypes = [P(vp), i64, i64, i64, dbl, dbl, cint, cint, cint, vp]
         lib.nnfft_plan_info.argtypes = [vp, P(Info)]
+        lib.nnfft_batch_plan.argtypes = [P(vp), i64, P(i64), P(i64), P(i64), dbl, dbl, cint, cint,
+                                         cint, vp]
+        lib.nnfft_batch_count.argtypes = [vp, P(i64)]
+        lib.nnfft_batch_info.argtypes = [vp, i64, P(Info)]
         lib.nnfft_set_nodes.argtypes = [vp, vp, vp]
         lib.nnfft_exec.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint.argtypes = [vp, vp, vp]
@@ -270,6 +274,46 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class BatchPlan(Plan):
+    """Many independent NNFFT instances in one plan (one launch per stage for all of them).
+
+    N, M1, M2: sequences of equal length (one entry per instance); sigma, m and dtype are
+    shared.  Node, coefficient and output tensors are the instances' arrays concatenated
+    in instance order (offsets in `off1` / `off2`); every method of Plan applies.
+    """
+
+    def __init__(self, N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype=None,
+                 stream=None):
+        import torch
+        lib = load_library()
+        N, M1, M2 = (np.ascontiguousarray(a, dtype=np.int64).ravel() for a in (N, M1, M2))
+        if not (N.size == M1.size == M2.size) or N.size == 0:
+            raise ValueError("N, M1 and M2 need one entry per instance (at least one)")
+        dtype = torch.complex128 if dtype is None else dtype
+        self.dtype = dtype
+        self.cdtype = torch.complex128 if _dtype_code(dtype) == NNFFT_C128 else torch.complex64
+        self.np_cdtype = np.complex128 if self.cdtype == torch.complex128 else np.complex64
+        self.count = int(N.size)
+        self.Ns, self.M1s, self.M2s = N.copy(), M1.copy(), M2.copy()
+        self.off1 = np.concatenate([[0], np.cumsum(M1)]).astype(np.int64)
+        self.off2 = np.concatenate([[0], np.cumsum(M2)]).astype(np.int64)
+        self.M1, self.M2, self.N = int(self.off1[-1]), int(self.off2[-1]), int(N.max())
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._h = ctypes.c_void_p()
+        m2 = m1 if m2 is None else m2
+        pi = ctypes.POINTER(ctypes.c_int64)
+        _check(lib.nnfft_batch_plan(ctypes.byref(self._h), self.count,
+                                    N.ctypes.data_as(pi), M1.ctypes.data_as(pi),
+                                    M2.ctypes.data_as(pi), float(sigma1), float(sigma2), int(m1),
+                                    int(m2), _dtype_code(dtype), _stream_ptr(self.stream)))
+        self._lib = lib
+
+    def instance_info(self, i) -> dict:
+        info = Info()
+        _check(self._lib.nnfft_batch_info(self._h, int(i), ctypes.byref(info)))
+        return info.as_dict()
 
 
 SINC_RULES = {"gl": 0, "cc": 1}

@@ -64,3 +64,27 @@ def sample_rows(M, count, seed=0, extremes=None):
     if extremes is not None:
         rows = np.concatenate([rows, np.asarray(extremes, dtype=np.int64)])
     return np.unique(rows.astype(np.int64))
+
+
+def batch_sizes(count, seed=0, M_range=(1e3, 1e6), N_range=(64, 8192)):
+    """Instance sizes of a batch: M1, M2 drawn separately and N, each log-uniform in its
+    range (rounded to integers), from stream seed + 3*10**6."""
+    rng = np.random.default_rng(seed + 3_000_000)
+    lm = np.log(np.asarray(M_range, dtype=np.float64))
+    ln = np.log(np.asarray(N_range, dtype=np.float64))
+    M1 = np.rint(np.exp(rng.uniform(lm[0], lm[1], size=count))).astype(np.int64)
+    M2 = np.rint(np.exp(rng.uniform(lm[0], lm[1], size=count))).astype(np.int64)
+    N = np.rint(np.exp(rng.uniform(ln[0], ln[1], size=count))).astype(np.int64)
+    return N, M1, M2
+
+
+def batch_inputs(M1, M2, seed=0, nodes="uniform", dtype=np.complex128):
+    """(v, x, f) of a batch: the instances' nnfft_inputs concatenated; instance i uses
+    seed + i."""
+    vs, xs, fs = [], [], []
+    for i, (m1, m2) in enumerate(zip(M1, M2)):
+        v, x, f = nnfft_inputs(int(m1), int(m2), seed + i, nodes, dtype)
+        vs.append(v)
+        xs.append(x)
+        fs.append(f)
+    return np.concatenate(vs), np.concatenate(xs), np.concatenate(fs)
