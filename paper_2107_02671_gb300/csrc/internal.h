@@ -66,12 +66,15 @@ struct SideDf {
 
 // One instance's FFT of length N2 = n1 * n2 (four-step, radix lists r1, r2), on the
 // grid buffer elements [grid_base, grid_base + N2).
+// A pass-1 block transforms cols1 columns (of length n1), a pass-2 block cols2 rows
+// (of length n2), so short transforms share a block.
 struct FftDf {
     int N2, n1, n2;
     int nr1, nr2;
     int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
     const float4 *tw1, *tw2, *twN;   // exp(-2 pi i k / n) as (re.h, re.l, im.h, im.l)
     long long grid_base;
+    int cols1, cols2;
 };
 
 struct FftPlanDev {
@@ -80,7 +83,10 @@ struct FftPlanDev {
     int r1[FFT_MAX_STAGES], r2[FFT_MAX_STAGES];
     const void *tw1, *tw2, *twN;   // C2<Real>: exp(-2 pi i k / n) for n = n1, n2, N2
     long long grid_base;
+    int cols1, cols2;
 };
+// Elements per FFT block when short columns are packed together.
+constexpr int FFT_TILE = 1024;
 
 // ---- instances -----------------------------------------------------------------
 // A plan holds one or more independent NNFFT instances (a batch).  On each node side
@@ -120,9 +126,17 @@ template <typename CoefT> struct GridLaunch {
 
 template <typename F> struct FftLaunch {
     const F *inst;                 // [ninst] device
-    const int *blk1, *blk2;        // [ninst + 1] device: pass-1 blocks (n2 each), pass-2 (n1)
-    int ninst, nblk1, nblk2, max_n1, max_n2;
+    const int *blk1, *blk2;        // [ninst + 1] device: first pass-1 / pass-2 block
+    int ninst, nblk1, nblk2;
+    int smem1, smem2;              // elements of shared memory per pass-1 / pass-2 block
 };
+
+// p mod n in [0, n) for a grid position p with |p| < 2^31 and 0 < n < 2^31 (one 32-bit
+// remainder; the grids are far shorter than 2^31).
+__device__ __forceinline__ int wrap_index(long long p, int n) {
+    const int r = (int)p % n;
+    return r < 0 ? r + n : r;
+}
 
 // Instance of block b: the largest i with blk[i] <= b (blk[0] = 0, increasing).
 __device__ __forceinline__ int block_instance(const int *blk, int ninst, int b) {

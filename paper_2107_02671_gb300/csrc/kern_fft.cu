@@ -44,22 +44,25 @@ __device__ __forceinline__ C2<Real> mul_isign(C2<Real> a, int sign) {
     return r;
 }
 
-// One Stockham stage of radix R over a length-n sequence held in shared memory:
-// butterfly j (0 <= j < n/R), k = j mod L,
+// One Stockham stage of radix R over `cols` length-n sequences held back to back in
+// shared memory: butterfly j (0 <= j < n/R) of each sequence, k = j mod L,
 //   a_q = src[j + q n/R] * w_{L R}^{q k},  b_p = sum_q a_q w_R^{p q},
 //   dst[(j - k) R + k + p L] = b_p,
 // where L is the product of the radices of the earlier stages.
 template <typename Real, int R>
-__device__ __forceinline__ void stage(const C2<Real> *src, C2<Real> *dst, int n, int L,
+__device__ __forceinline__ void stage(const C2<Real> *src, C2<Real> *dst, int n, int cols, int L,
                                       const C2<Real> *tw, int sign) {
     const int nr = n / R;
     const int tstep = n / (L * R);
-    for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+    for (int jj = threadIdx.x; jj < cols * nr; jj += blockDim.x) {
+        const int col = jj / nr, j = jj - col * nr;
+        const C2<Real> *s0 = src + col * n;
+        C2<Real> *d0 = dst + col * n;
         const int k = j % L;
         C2<Real> a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            a[q] = src[j + q * nr];
+            a[q] = s0[j + q * nr];
             if (q > 0 && k > 0) a[q] = cmul<Real>(a[q], twid<Real>(tw, q * k * tstep, sign));
         }
         C2<Real> b[R];
@@ -85,26 +88,24 @@ __device__ __forceinline__ void stage(const C2<Real> *src, C2<Real> *dst, int n,
             }
         }
 #pragma unroll
-        for (int p = 0; p < R; ++p) dst[(j - k) * R + k + p * L] = b[p];
+        for (int p = 0; p < R; ++p) d0[(j - k) * R + k + p * L] = b[p];
     }
 }
 
-// Stockham FFT of length n (= product of radices) in shared memory; returns the
-// buffer that holds the natural-order result (A or B).
+// Stockham FFTs of `cols` sequences of length n (= product of radices) in shared
+// memory; returns the buffer that holds the natural-order results (A or B).
 template <typename Real>
-__device__ C2<Real> *stockham(C2<Real> *A, C2<Real> *B, int n, const int *radices, int nr,
-                              const C2<Real> *tw, int sign) {
+__device__ C2<Real> *stockham(C2<Real> *A, C2<Real> *B, int n, int cols, const int *radices,
+                              int nr, const C2<Real> *tw, int sign) {
     int L = 1;
     C2<Real> *src = A, *dst = B;
     for (int s = 0; s < nr; ++s) {
         const int R = radices[s];
         switch (R) {
-            case 2: stage<Real, 2>(src, dst, n, L, tw, sign); break;
-            case 3: stage<Real, 3>(src, dst, n, L, tw, sign); break;
-            case 4: stage<Real, 4>(src, dst, n, L, tw, sign); break;
-            case 5: stage<Real, 5>(src, dst, n, L, tw, sign); break;
-            case 7: stage<Real, 7>(src, dst, n, L, tw, sign); break;
-            case 8: stage<Real, 8>(src, dst, n, L, tw, sign); break;
+            case 2: stage<Real, 2>(src, dst, n, cols, L, tw, sign); break;
+            case 3: stage<Real, 3>(src, dst, n, cols, L, tw, sign); break;
+            case 4: stage<Real, 4>(src, dst, n, cols, L, tw, sign); break;
+            case 5: stage<Real, 5>(src, dst, n, cols, L, tw, sign); break;
             default: break;
         }
         __syncthreads();
@@ -114,8 +115,9 @@ __device__ C2<Real> *stockham(C2<Real> *A, C2<Real> *B, int n, const int *radice
     return src;
 }
 
-// Block b of pass 1 is column b - blk1[i] of instance i (n2 columns each), block c of
-// pass 2 row c - blk2[i] (n1 rows each); each instance works on its own grid_base.
+// Block b of pass 1 holds columns [b0, b0 + cols1) of instance i (b0 = (b - blk1[i]) cols1),
+// block c of pass 2 rows [c0, c0 + cols2); each instance works on its own grid_base.
+// Shared memory: A and B (cols x n each), then the length-n twiddles.
 template <typename Real>
 __global__ void __launch_bounds__(256)
 k_fft_pass1(const C2<Real> *__restrict__ X_all, C2<Real> *__restrict__ Z_all,
@@ -125,21 +127,25 @@ k_fft_pass1(const C2<Real> *__restrict__ X_all, C2<Real> *__restrict__ Z_all,
     const FftPlanDev &F = L.inst[inst];
     const C2<Real> *__restrict__ X = X_all + F.grid_base;
     C2<Real> *__restrict__ Z = Z_all + F.grid_base;
-    const int n = F.n1;
+    const int n = F.n1, n2 = F.n2;
+    const int b0 = (blockIdx.x - L.blk1[inst]) * F.cols1;
+    const int cols = min(F.cols1, n2 - b0);
     C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
-    C2<Real> *B = A + n;
-    C2<Real> *tw = B + n;
+    C2<Real> *B = A + cols * n;
+    C2<Real> *tw = B + cols * n;
     const C2<Real> *tw1 = static_cast<const C2<Real> *>(F.tw1);
     const C2<Real> *twN = static_cast<const C2<Real> *>(F.twN);
-    const int b = blockIdx.x - L.blk1[inst];
-    for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        A[a] = X[(long long)F.n2 * a + b];
-        tw[a] = tw1[a];
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {   // element (a, b0 + bb)
+        const int a = e / cols, bb = e - a * cols;
+        A[bb * n + a] = X[(long long)n2 * a + b0 + bb];
     }
+    for (int a = threadIdx.x; a < n; a += blockDim.x) tw[a] = tw1[a];
     __syncthreads();
-    const C2<Real> *res = stockham<Real>(A, B, n, F.r1, F.nr1, tw, sign);
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        Z[(long long)b * n + c] = cmul<Real>(res[c], twid<Real>(twN, b * c, sign));
+    const C2<Real> *res = stockham<Real>(A, B, n, cols, F.r1, F.nr1, tw, sign);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int bb = e / n, c = e - bb * n, b = b0 + bb;
+        Z[(long long)b * n + c] = cmul<Real>(res[e], twid<Real>(twN, b * c, sign));
+    }
 }
 
 template <typename Real>
@@ -151,19 +157,24 @@ k_fft_pass2(const C2<Real> *__restrict__ Z_all, C2<Real> *__restrict__ Y_all,
     const FftPlanDev &F = L.inst[inst];
     const C2<Real> *__restrict__ Z = Z_all + F.grid_base;
     C2<Real> *__restrict__ Y = Y_all + F.grid_base;
-    const int n = F.n2;
+    const int n = F.n2, n1 = F.n1;
+    const int c0 = (blockIdx.x - L.blk2[inst]) * F.cols2;
+    const int cols = min(F.cols2, n1 - c0);
     C2<Real> *A = reinterpret_cast<C2<Real> *>(smem_raw);
-    C2<Real> *B = A + n;
-    C2<Real> *tw = B + n;
+    C2<Real> *B = A + cols * n;
+    C2<Real> *tw = B + cols * n;
     const C2<Real> *tw2 = static_cast<const C2<Real> *>(F.tw2);
-    const int c = blockIdx.x - L.blk2[inst];
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        A[b] = Z[(long long)b * F.n1 + c];
-        tw[b] = tw2[b];
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {   // element (b, c0 + cc)
+        const int b = e / cols, cc = e - b * cols;
+        A[cc * n + b] = Z[(long long)b * n1 + c0 + cc];
     }
+    for (int b = threadIdx.x; b < n; b += blockDim.x) tw[b] = tw2[b];
     __syncthreads();
-    const C2<Real> *res = stockham<Real>(A, B, n, F.r2, F.nr2, tw, sign);
-    for (int d = threadIdx.x; d < n; d += blockDim.x) Y[c + (long long)F.n1 * d] = res[d];
+    const C2<Real> *res = stockham<Real>(A, B, n, cols, F.r2, F.nr2, tw, sign);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {   // element (d, c0 + cc)
+        const int d = e / cols, cc = e - d * cols;
+        Y[c0 + cc + (long long)n1 * d] = res[cc * n + d];
+    }
 }
 
 }  // namespace
@@ -172,8 +183,8 @@ template <typename Real>
 cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,
                        int sign, cudaStream_t s) {
     if (F.nblk1 <= 0) return cudaSuccess;
-    const size_t sm1 = 3 * sizeof(C2<Real>) * F.max_n1;
-    const size_t sm2 = 3 * sizeof(C2<Real>) * F.max_n2;
+    const size_t sm1 = sizeof(C2<Real>) * F.smem1;
+    const size_t sm2 = sizeof(C2<Real>) * F.smem2;
     if (sm1 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass1<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sm1);

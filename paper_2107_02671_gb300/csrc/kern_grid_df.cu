@@ -102,9 +102,7 @@ k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
         for (int k = threadIdx.x; k < PPB; k += SCD_THREADS) {
             const long long i = i0 + k;
             if (i < N2) {
-                long long q = (p_lo + i) % N2;
-                if (q < 0) q += N2;
-                out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                out[wrap_index(p_lo + i, N2)] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         return;
@@ -152,8 +150,7 @@ k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
         const long long i = i0 + k;
         if (i < N2) {
             const long long p = p_lo + i;
-            long long q = p % N2;
-            if (q < 0) q += N2;
+            const int q = wrap_index(p, N2);
             if (p > p_hi) {
                 out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
             } else {
@@ -180,16 +177,19 @@ __device__ __forceinline__ cdf twd(const float4 *tw, int idx, int sign) {
 }
 
 template <int R>
-__device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, int L,
+__device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, int cols, int L,
                                          const float4 *tw, int sign) {
     const int nr = n / R;
     const int tstep = n / (L * R);
-    for (int j = threadIdx.x; j < nr; j += blockDim.x) {
+    for (int jj = threadIdx.x; jj < cols * nr; jj += blockDim.x) {
+        const int col = jj / nr, j = jj - col * nr;
+        const float4 *s0 = src + col * n;
+        float4 *d0 = dst + col * n;
         const int k = j % L;
         cdf a[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) {
-            a[q] = ld(src + j + q * nr);
+            a[q] = ld(s0 + j + q * nr);
             if (q > 0 && k > 0) a[q] = cmul(a[q], twd(tw, q * k * tstep, sign));
         }
         cdf b[R];
@@ -215,21 +215,21 @@ __device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, 
             }
         }
 #pragma unroll
-        for (int p = 0; p < R; ++p) st(dst + (j - k) * R + k + p * L, b[p]);
+        for (int p = 0; p < R; ++p) st(d0 + (j - k) * R + k + p * L, b[p]);
     }
 }
 
-__device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, const int *radices, int nrad,
-                               const float4 *tw, int sign) {
+__device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, int cols, const int *radices,
+                               int nrad, const float4 *tw, int sign) {
     int L = 1;
     float4 *src = A, *dst = Bf;
     for (int s = 0; s < nrad; ++s) {
         const int R = radices[s];
         switch (R) {
-            case 2: stage_df<2>(src, dst, n, L, tw, sign); break;
-            case 3: stage_df<3>(src, dst, n, L, tw, sign); break;
-            case 4: stage_df<4>(src, dst, n, L, tw, sign); break;
-            case 5: stage_df<5>(src, dst, n, L, tw, sign); break;
+            case 2: stage_df<2>(src, dst, n, cols, L, tw, sign); break;
+            case 3: stage_df<3>(src, dst, n, cols, L, tw, sign); break;
+            case 4: stage_df<4>(src, dst, n, cols, L, tw, sign); break;
+            case 5: stage_df<5>(src, dst, n, cols, L, tw, sign); break;
             default: break;
         }
         __syncthreads();
@@ -241,8 +241,8 @@ __device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, const int *radices,
     return src;
 }
 
-// Block b of pass 1 is column b - blk1[i] of instance i (n2 columns each), block c of
-// pass 2 row c - blk2[i] (n1 rows each).
+// Block b of pass 1 holds columns [b0, b0 + cols1) of instance i (b0 = (b - blk1[i]) cols1),
+// block c of pass 2 rows [c0, c0 + cols2); shared memory A, B (cols x n) and twiddles (n).
 __global__ void __launch_bounds__(128)
 k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, FftLaunch<FftDf> L,
                int sign) {
@@ -251,17 +251,21 @@ k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, Fft
     const FftDf &F = L.inst[inst];
     const float4 *__restrict__ X = X_all + F.grid_base;
     float4 *__restrict__ Z = Z_all + F.grid_base;
-    const int n = F.n1;
-    float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
-    const int b = blockIdx.x - L.blk1[inst];
-    for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        A[a] = X[(long long)F.n2 * a + b];
-        tw[a] = F.tw1[a];
+    const int n = F.n1, n2 = F.n2;
+    const int b0 = (blockIdx.x - L.blk1[inst]) * F.cols1;
+    const int cols = min(F.cols1, n2 - b0);
+    float4 *A = smem4, *Bf = smem4 + cols * n, *tw = smem4 + 2 * cols * n;
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int a = e / cols, bb = e - a * cols;
+        A[bb * n + a] = X[(long long)n2 * a + b0 + bb];
     }
+    for (int a = threadIdx.x; a < n; a += blockDim.x) tw[a] = F.tw1[a];
     __syncthreads();
-    const float4 *res = stockham_df(A, Bf, n, F.r1, F.nr1, tw, sign);
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        st(Z + (long long)b * n + c, cmul(ld(res + c), twd(F.twN, b * c, sign)));
+    const float4 *res = stockham_df(A, Bf, n, cols, F.r1, F.nr1, tw, sign);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int bb = e / n, c = e - bb * n, b = b0 + bb;
+        st(Z + (long long)b * n + c, cmul(ld(res + e), twd(F.twN, b * c, sign)));
+    }
 }
 
 __global__ void __launch_bounds__(128)
@@ -272,16 +276,21 @@ k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, Fft
     const FftDf &F = L.inst[inst];
     const float4 *__restrict__ Z = Z_all + F.grid_base;
     float4 *__restrict__ Y = Y_all + F.grid_base;
-    const int n = F.n2;
-    float4 *A = smem4, *Bf = smem4 + n, *tw = smem4 + 2 * n;
-    const int c = blockIdx.x - L.blk2[inst];
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
-        A[b] = Z[(long long)b * F.n1 + c];
-        tw[b] = F.tw2[b];
+    const int n = F.n2, n1 = F.n1;
+    const int c0 = (blockIdx.x - L.blk2[inst]) * F.cols2;
+    const int cols = min(F.cols2, n1 - c0);
+    float4 *A = smem4, *Bf = smem4 + cols * n, *tw = smem4 + 2 * cols * n;
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int b = e / cols, cc = e - b * cols;
+        A[cc * n + b] = Z[(long long)b * n1 + c0 + cc];
     }
+    for (int b = threadIdx.x; b < n; b += blockDim.x) tw[b] = F.tw2[b];
     __syncthreads();
-    const float4 *res = stockham_df(A, Bf, n, F.r2, F.nr2, tw, sign);
-    for (int d = threadIdx.x; d < n; d += blockDim.x) Y[c + (long long)F.n1 * d] = res[d];
+    const float4 *res = stockham_df(A, Bf, n, cols, F.r2, F.nr2, tw, sign);
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+        const int d = e / cols, cc = e - d * cols;
+        Y[c0 + cc + (long long)n1 * d] = res[cc * n + d];
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -318,10 +327,9 @@ k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
         cdf q = czero();
         if (d < B) {
             df qr = mk(0.f), qi = mk(0.f);
-            for (int t = 0; t < ntap; ++t) {
+            int qidx = wrap_index(c - m + 1, N2);             // buffer index of tap 0
+            for (int t = 0; t < ntap; ++t, qidx = qidx + 1 == N2 ? 0 : qidx + 1) {
                 const long long p = c - m + 1 + t;
-                long long qidx = p % N2;
-                if (qidx < 0) qidx += N2;
                 cdf h = ld(buf + qidx);
                 if (scale != nullptr) {
                     const long long si = p + scale_off;
@@ -337,10 +345,9 @@ k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
             q.im = norm(qi);
         } else {
             float fr = 0.f, fi = 0.f;
-            for (int t = 0; t < ntap; ++t) {
+            int qidx = wrap_index(c - m + 1, N2);
+            for (int t = 0; t < ntap; ++t, qidx = qidx + 1 == N2 ? 0 : qidx + 1) {
                 const long long p = c - m + 1 + t;
-                long long qidx = p % N2;
-                if (qidx < 0) qidx += N2;
                 const float4 hv = buf[qidx];
                 float hr = hv.x, hi = hv.z;
                 if (scale != nullptr) {
@@ -436,8 +443,8 @@ cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, 
 cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, void *out,
                           int sign, cudaStream_t s) {
     if (F.nblk1 <= 0) return cudaSuccess;
-    const size_t sm1 = 3 * sizeof(float4) * F.max_n1;
-    const size_t sm2 = 3 * sizeof(float4) * F.max_n2;
+    const size_t sm1 = sizeof(float4) * F.smem1;
+    const size_t sm2 = sizeof(float4) * F.smem2;
     if (sm1 > 48 * 1024)
         cudaFuncSetAttribute(k_fft_pass1_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (sm2 > 48 * 1024)

@@ -228,8 +228,7 @@ k_spread_conv(GridLaunch<Real> L, const C2<Real> *__restrict__ Pc_all,
     const long long i = (long long)lb * SC_THREADS + threadIdx.x;
     if (i >= N2) return;
     const long long p = p_lo + i;
-    long long q = p % N2;
-    if (q < 0) q += N2;
+    const int q = wrap_index(p, N2);
     if (p > p_hi) {
         out[q] = mk2<Real>(Real(0), Real(0));
         return;
@@ -292,10 +291,9 @@ k_gather_conv(GridLaunch<Real> L, const C2<Real> *__restrict__ buf_all,
     Real qr[D], qi[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) { qr[d] = Real(0); qi[d] = Real(0); }
-    for (int t = 0; t < ntap; ++t) {
+    int qidx = wrap_index(c - m + 1, N2);                     // buffer index of tap 0
+    for (int t = 0; t < ntap; ++t, qidx = qidx + 1 == N2 ? 0 : qidx + 1) {
         const long long p = c - m + 1 + t;
-        long long qidx = p % N2;
-        if (qidx < 0) qidx += N2;
         C2<Real> h = buf[qidx];
         if (scale != nullptr) {
             const long long si = p + scale_off;

@@ -510,7 +510,13 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         std::vector<FftDf> G((size_t)count);
         std::vector<int> c1((size_t)count), c2((size_t)count);
         std::vector<size_t> o1((size_t)count), o2((size_t)count), oN((size_t)count);
-        int max1 = 0, max2 = 0;
+        int sm1 = 0, sm2 = 0;
+        // Short columns share a block when the plan's grids are large enough to fill the
+        // GPU anyway: about 4 blocks per SM of FFT_TILE elements each.
+        auto cols_for = [&](int n) {
+            const long long c = gtot / (4LL * 152 * n);
+            return (int)std::max(1LL, std::min(c, (long long)std::max(1, FFT_TILE / n)));
+        };
         for (int64_t i = 0; i < count; ++i) {
             const nnfft_info &I = p->inst_info[(size_t)i];
             FftPlanDev &f = F[(size_t)i];
@@ -525,10 +531,12 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             o1[(size_t)i] = twid_of(f.n1);
             o2[(size_t)i] = twid_of(f.n2);
             oN[(size_t)i] = twid_of(f.N2);
-            c1[(size_t)i] = f.n2;               // pass 1: one block per column
-            c2[(size_t)i] = f.n1;               // pass 2: one block per row
-            max1 = std::max(max1, f.n1);
-            max2 = std::max(max2, f.n2);
+            f.cols1 = cols_for(f.n1);
+            f.cols2 = cols_for(f.n2);
+            c1[(size_t)i] = (f.n2 + f.cols1 - 1) / f.cols1;    // pass 1: columns of length n1
+            c2[(size_t)i] = (f.n1 + f.cols2 - 1) / f.cols2;    // pass 2: rows of length n2
+            sm1 = std::max(sm1, (2 * f.cols1 + 1) * f.n1);
+            sm2 = std::max(sm2, (2 * f.cols2 + 1) * f.n2);
         }
         void *tw_real = nullptr, *tw_df = nullptr;
         if ((rc = upload_real(p, &tw_real, tw, "twiddles"))) return rc;
@@ -551,6 +559,8 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
                 g.r2[k] = f.r2[k];
             }
             g.grid_base = f.grid_base;
+            g.cols1 = f.cols1;
+            g.cols2 = f.cols2;
             if (tw_df) {
                 g.tw1 = static_cast<const float4 *>(tw_df) + o1[(size_t)i];
                 g.tw2 = static_cast<const float4 *>(tw_df) + o2[(size_t)i];
@@ -564,11 +574,11 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             (rc = upload_vec(p, &b2, prefix(c2, &n2tot), "FFT block map")) ||
             (rc = upload_vec(p, &fd, F, "FFT tables")))
             return rc;
-        p->fft = FftLaunch<FftPlanDev>{fd, b1, b2, (int)count, n1tot, n2tot, max1, max2};
+        p->fft = FftLaunch<FftPlanDev>{fd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
         if (p->split_ok) {
             FftDf *gd = nullptr;
             if ((rc = upload_vec(p, &gd, G, "FFT tables (df)"))) return rc;
-            p->fftdf = FftLaunch<FftDf>{gd, b1, b2, (int)count, n1tot, n2tot, max1, max2};
+            p->fftdf = FftLaunch<FftDf>{gd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
         }
     }
     // work buffers
@@ -1208,6 +1218,7 @@ int cc_rule_device(int64_t n, double *w, double *half_z, double *neg_half_z, cud
     F.tw2 = t2;
     F.twN = tN;
     F.grid_base = 0;
+    F.cols1 = F.cols2 = 1;
     const size_t fb = (sizeof(FftPlanDev) + 15) / 16 * 16;
     const int blk[4] = {0, n2, 0, n1};
     if (e == cudaSuccess) e = cudaMalloc(&tab, fb + sizeof(blk));
@@ -1216,7 +1227,7 @@ int cc_rule_device(int64_t n, double *w, double *half_z, double *neg_half_z, cud
         e = cudaMemcpyAsync(static_cast<char *>(tab) + fb, blk, sizeof(blk), cudaMemcpyHostToDevice, st);
     const int *blk_dev = reinterpret_cast<const int *>(static_cast<char *>(tab) + fb);
     const FftLaunch<FftPlanDev> FL{static_cast<const FftPlanDev *>(tab), blk_dev, blk_dev + 2, 1,
-                                   n2, n1, n1, n2};
+                                   n2, n1, 3 * n1, 3 * n2};
     if (e == cudaSuccess) e = launch_cc_extend(n, x, st);
     if (e == cudaSuccess) e = launch_fft<double>(FL, x, y, X, -1, st);
     if (e == cudaSuccess) e = launch_cc_finish(n, X, w, half_z, neg_half_z, st);
