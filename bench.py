@@ -406,6 +406,13 @@ def run_ours(args, rank, world):
             pl.timing(False)
         return ms, launches, stages
 
+    if args.only_batched:      # the batched workload alone (profiling runs)
+        pk, _ = peaks()
+        res = run_batched(args, rank, dev, flush, timed, pk)
+        if rank == 0:
+            print(json.dumps({"section": "batched", **res}))
+        return 0
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -602,6 +609,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="run only the batched workload and print its numbers (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

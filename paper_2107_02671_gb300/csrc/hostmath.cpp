@@ -164,6 +164,20 @@ void gauss_legendre(int64_t n, double *tau, double *w) {
     if (n % 2 == 1) tau[n / 2] = 0.0;
 }
 
+bool cell_map(int64_t num, int64_t den, CellMap *out) {
+    if (num <= 0 || den <= 0) return false;
+    const unsigned __int128 q = ((unsigned __int128)(uint64_t)num << FX_SB) + (uint64_t)den / 2;
+    const unsigned __int128 S = q / (uint64_t)den;
+    if (S >> 63) return false;
+    out->S = (uint64_t)S;
+    const uint64_t half = (uint64_t)1 << (FX_SB + 1);
+    const int64_t c_hi = (int64_t)(out->S >> (FX_SB + 1));
+    out->c_lo = -(int64_t)((out->S + half - 1) >> (FX_SB + 1));
+    out->ncell = c_hi - out->c_lo + 1;
+    out->scale = (double)num / (double)den;
+    return true;
+}
+
 bool split_fft(int64_t N2, int maxf, int *n1, int *n2) {
     int best1 = 0;
     for (int64_t a = 1; a <= maxf; ++a) {

@@ -55,6 +55,20 @@ int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
 // n-point Gauss-Legendre rule on [-1/2, 1/2] (Newton on the Legendre recurrence).
 void gauss_legendre(int64_t n, double *tau, double *w);
 
+// Cells of one node side.  A node t in [-1/2, 1/2] has u = t * num / den (the rational
+// scale N1 N / N* on the v side, N2 N* / N1 on the x side); the kernels compute u in
+// fixed point with the scale rounded to S = round(num / den * 2^FX_SB).  Cell c = floor(u)
+// runs from c_lo = floor(-S / 2^(FX_SB+1)) to floor(S / 2^(FX_SB+1)), exactly as the
+// kernels' fixed-point floor does at t = -1/2 and t = 1/2.
+constexpr int FX_SB = 44;
+struct CellMap {
+    uint64_t S;        // scale in units of 2^-FX_SB (< 2^63: scale < 2^19)
+    int64_t c_lo;
+    int64_t ncell;
+    double scale;      // num / den as a double (host-side fits only)
+};
+bool cell_map(int64_t num, int64_t den, CellMap *out);
+
 // n has no prime factor above 5.
 bool smooth5(int64_t n);
 // N2 = n1 * n2 with n1, n2 <= maxf and 5-smooth, as square as possible; radix lists.

@@ -97,9 +97,10 @@ constexpr int FFT_TILE = 1024;
 // blk[i] <= b < blk[i+1] and works on that instance's grid of length N2 at
 // grid_base in the concatenated grid buffers.
 
-// Node binning of one instance: u = node * uscale, cell key cell_base + floor(u) - c_lo.
+// Node binning of one instance: u = node * scale with the scale in fixed point,
+// S = scale * 2^44 (see kern_nodes.cu); cell key cell_base + floor(u) - c_lo.
 struct NodeInst {
-    double uscale;
+    unsigned long long S;
     long long c_lo;
     int ncell, cell_base;
 };

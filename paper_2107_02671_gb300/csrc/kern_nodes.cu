@@ -16,35 +16,64 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// Cell of a node: c = floor(node * uscale), key c - c_lo (+ the instance's first cell).
-__device__ __forceinline__ double node_u(double x, double uscale) { return x * uscale; }
-
-// Coordinate storage formats of the sorted local coordinate y = 2(u - floor u) - 1.
-//   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans)
-__device__ __forceinline__ void store_y(void *yout, int fmt, long long i, double y) {
-    if (fmt == 0) {
-        static_cast<float *>(yout)[i] = (float)y;
-    } else if (fmt == 1) {
-        static_cast<double *>(yout)[i] = y;
+// Cell and local coordinate of a node t in fixed point, with integer operations only.
+// |t| is truncated to X = |t| 2^62 (exact for |t| >= 2^-10, absolute error < 2^-62), the
+// scale is S = scale 2^FX_SB, so A = X S = |u| 2^(62 + FX_SB) exactly in 128 bits
+// (|u| < 2^19).  Its integer part gives floor |u|, its top 63 fraction bits the local
+// coordinate; for t < 0 the cell is -floor|u| - 1 (or -|u| when u is an integer).
+// The error in u is below 2^-46 + 2^-62 |scale| (an FP64 product would round u to 2^-40).
+// Returns false for |t| > 1/2 and NaN / Inf.  On success c = floor(u) and
+// Y = (2 (u - c) - 1) 2^63 as a signed 64-bit integer.
+constexpr int FX_SB = 44;   // matches the host's cell map
+__device__ __forceinline__ bool node_fixed(double t, unsigned long long S, long long &c,
+                                           long long &Y) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    const unsigned long long mant = (b & 0xfffffffffffffULL) | (e ? (1ULL << 52) : 0ULL);
+    const bool ok = e < 1022u || (e == 1022u && mant == (1ULL << 52));
+    unsigned long long X = 0;                              // |t| 2^62 = mant 2^(e - 1013)
+    if (e >= 1013u && e <= 1022u) X = mant << (e - 1013u);
+    else if (e > 949u && e < 1013u) X = mant >> (1013u - e);
+    const unsigned long long lo = X * S, hi = __umul64hi(X, S);
+    constexpr int SH = 62 + FX_SB - 64;                    // integer part = hi >> SH
+    const unsigned long long ip = hi >> SH;
+    const unsigned long long fm = hi & ((1ULL << SH) - 1);
+    const unsigned long long f63 = (fm << (63 - SH)) | (lo >> (SH + 1));   // top 63 bits
+    unsigned long long frac;
+    if ((b >> 63) == 0) {
+        c = (long long)ip;
+        frac = f63;
+    } else if ((fm | lo) == 0) {
+        c = -(long long)ip;
+        frac = 0;
     } else {
-        // (hi, lo) by integer operations: hi = y truncated to 24 bits, lo = rounded rest
-        const unsigned long long b = (unsigned long long)__double_as_longlong(y);
-        const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-        const unsigned sign = hi & 0x80000000u;
-        const int ex = (int)((hi >> 20) & 0x7ffu);
-        const unsigned mh = ((hi & 0xfffffu) << 3) | (lo >> 29);
-        const bool ok = ex > 1023 - 100;
-        const float h = ok ? __uint_as_float(sign | ((unsigned)(ex - 896) << 23) | mh) : 0.0f;
-        const float rem = __uint2float_rn(lo & 0x1fffffffu);
-        const int se = ex - 1075 + 127;
-        const float lv = se > 0 ? rem * __uint_as_float((unsigned)se << 23) : 0.0f;
-        static_cast<float2 *>(yout)[i] = make_float2(h, ok ? (sign ? -lv : lv) : 0.0f);
+        c = -(long long)ip - 1;
+        frac = (~f63) & 0x7fffffffffffffffULL;             // 1 - f, to 2^-63
+    }
+    Y = (long long)((frac << 1) ^ 0x8000000000000000ULL);  // 2 frac - 1, times 2^63
+    return ok;
+}
+
+// Store the local coordinate y = Y 2^-63 in the plan's format:
+//   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans),
+// the pair from integer arithmetic: hi = Y rounded toward zero to 24 bits, lo = the rest.
+__device__ __forceinline__ void store_y(void *yout, int fmt, long long i, long long Y) {
+    if (fmt == 0) {
+        static_cast<float *>(yout)[i] = __ll2float_rn(Y) * 0x1p-63f;
+    } else if (fmt == 1) {
+        static_cast<double *>(yout)[i] = __ll2double_rn(Y) * 0x1p-63;
+    } else {
+        const float h = __ll2float_rz(Y);
+        const float l = __ll2float_rn(Y - __float2ll_rz(h));
+        const float sh = h + l;                            // Fast2Sum: |h| >= |l|
+        const float sl = l - (sh - h);
+        static_cast<float2 *>(yout)[i] = make_float2(sh * 0x1p-63f, sl * 0x1p-63f);
     }
 }
 
 // Step 0 for one node side in a single pass over the nodes: validate each node,
-// compute its cell key c - c_lo and local coordinate y in FP64 (u = node * uscale,
-// c = floor(u), y = 2 (u - c) - 1), store y (caller order) in the plan's format, and
+// compute its cell key c - c_lo and local coordinate y = 2 (u - c) - 1 (c = floor(u),
+// u = node * scale, node_fixed), store y (caller order) in the plan's format, and
 // count the digits of the first radix pass for this block's tile (the tiles match
 // k_sort_scatter's: SORT_TILE keys per block).  In a batch each point takes the
 // binning of its instance and the key is offset by the instance's first cell.
@@ -54,31 +83,34 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
               uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int nblocks,
               int *__restrict__ hist, int *__restrict__ digit_tot, int *status) {
     __shared__ int h[256];
+    __shared__ int first_inst;
     h[threadIdx.x] = 0;
-    __syncthreads();
     const long long base = (long long)blockIdx.x * SORT_TILE;
+    if (threadIdx.x == 0) {       // instance of the tile's first point: pt_off[j] <= base < pt_off[j+1]
+        int lo = 0, hi = ninst > 1 ? ninst : 1;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pt_off[mid] <= base) lo = mid; else hi = mid;
+        }
+        first_inst = lo;
+    }
+    __syncthreads();
     for (int k = threadIdx.x; k < SORT_TILE; k += SORT_THREADS) {
         const long long i = base + k;
         if (i >= n) break;
         NodeInst I = one;
-        if (ninst > 1) {                     // instance of point i: pt_off[j] <= i < pt_off[j+1]
-            int lo = 0, hi = ninst;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(pt_off + mid) <= i) lo = mid; else hi = mid;
-            }
-            I = tab[lo];
+        if (ninst > 1) {              // a tile meets few instances: step forward from the first
+            int j = first_inst;
+            while (j + 1 < ninst && __ldg(pt_off + j + 1) <= i) ++j;
+            I = tab[j];
         }
-        const double x = nodes[i];
+        long long c = 0, Y = -0x7fffffffffffffffLL - 1;
         long long ic = 0;
-        double y = 0.0;
-        if (!(x >= -0.5 && x <= 0.5)) {
+        if (!node_fixed(nodes[i], I.S, c, Y)) {
             atomicOr(status, STATUS_RANGE);
+            Y = -0x7fffffffffffffffLL - 1;
         } else {
-            const double u = node_u(x, I.uscale);
-            const double c = floor(u);
-            ic = (long long)c - I.c_lo;
-            y = 2.0 * (u - c) - 1.0;
+            ic = c - I.c_lo;
             if (ic < 0 || ic >= I.ncell) {
                 atomicOr(status, STATUS_INTERNAL);
                 ic = ic < 0 ? 0 : I.ncell - 1;
@@ -86,7 +118,7 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
         }
         ic += I.cell_base;
         keys[i] = (uint32_t)ic;
-        store_y(yout, yfmt, i, y);
+        store_y(yout, yfmt, i, Y);
         atomicAdd(&h[ic & 255], 1);
     }
     __syncthreads();
@@ -158,9 +190,11 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 
 // Stable scatter.  Warp w of a block owns 32 * ROUNDS consecutive keys of the
 // tile and visits them in ROUNDS rounds of 32 in index order; within a round lanes with the
-// same digit are ranked by lane (match_any), across rounds by a per-warp digit
-// counter, and across warps by an exclusive scan of those counters.  So keys
-// with equal digits keep their input order.
+// same digit are ranked by lane (ballots of the digit bits), across rounds by a per-warp
+// digit counter, and across warps by an exclusive scan of those counters.  So keys
+// with equal digits keep their input order.  The tile is first reordered by digit in
+// shared memory and then written out in that order, so each digit's run of the tile
+// leaves as consecutive addresses (coalesced) instead of one scattered store per key.
 // FIRST: the values are the identity (vin unused).  Y: payload moved along in the last
 // pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.
 template <bool FIRST, typename Y>
@@ -171,11 +205,18 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                Y *__restrict__ yout) {
     constexpr int WARPS = SORT_THREADS / 32;
     constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 8
+    static_assert(SORT_THREADS == 256, "one thread per digit in the digit scans");
     __shared__ int cnt[WARPS][256];
+    __shared__ int lstart[256];          // first tile-local slot of each digit
+    __shared__ int delta[256];           // global position - tile-local slot, per digit
+    __shared__ int wtot[WARPS];
+    __shared__ uint32_t skey[SORT_TILE];
+    __shared__ int sval[SORT_TILE];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
     __syncwarp();
-    const long long base = (long long)blockIdx.x * SORT_TILE + (long long)w * (32 * ROUNDS);
+    const long long tile0 = (long long)blockIdx.x * SORT_TILE;
+    const long long base = tile0 + (long long)w * (32 * ROUNDS);
     uint32_t key[ROUNDS];
     int val[ROUNDS], rank[ROUNDS];
     const unsigned lt = lanemask_lt();
@@ -209,27 +250,50 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         rank[r] = before + __popc(peers & lt);
     }
     __syncthreads();
-    {   // digit threadIdx.x: exclusive scan over warps plus the block's global base
-        int d = threadIdx.x;
-        int run = hist_scanned[(long long)d * nblocks + blockIdx.x];
+    {   // digit d = threadIdx.x: exclusive scan over warps, then over digits (tile-local)
+        const int d = threadIdx.x;
+        int run = 0;
 #pragma unroll
         for (int ww = 0; ww < WARPS; ++ww) {
-            int t = cnt[ww][d];
+            const int t = cnt[ww][d];
             cnt[ww][d] = run;
             run += t;
         }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wtot[w] = incl;
+        __syncthreads();
+        int wpre = 0;
+#pragma unroll
+        for (int ww = 0; ww < WARPS; ++ww) wpre += ww < w ? wtot[ww] : 0;
+        const int start = wpre + incl - run;
+        lstart[d] = start;
+        delta[d] = hist_scanned[(long long)d * nblocks + blockIdx.x] - start;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
-        long long idx = base + r * 32 + lane;
+        const long long idx = base + r * 32 + lane;
         if (idx < n) {
-            unsigned d = (key[r] >> shift) & 255u;
-            int pos = cnt[w][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
-            if constexpr (!std::is_void<Y>::value) yout[pos] = yin[val[r]];
+            const unsigned d = (key[r] >> shift) & 255u;
+            const int loc = lstart[d] + cnt[w][d] + rank[r];
+            skey[loc] = key[r];
+            sval[loc] = val[r];
         }
+    }
+    __syncthreads();
+    const int tn = (int)min((long long)SORT_TILE, (long long)n - tile0);
+    for (int i = threadIdx.x; i < tn; i += SORT_THREADS) {
+        const uint32_t k = skey[i];
+        const int v = sval[i];
+        const int pos = delta[(k >> shift) & 255u] + i;
+        kout[pos] = k;
+        vout[pos] = v;
+        if constexpr (!std::is_void<Y>::value) yout[pos] = yin[v];
     }
 }
 

@@ -211,10 +211,11 @@ int fill_info(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, i
     info->D2 = hm::choose_degree(m2, d->sigma2, d->beta2, fp64, &info->fit_err2,
                                  coef2 ? *coef2 : tmp2);
     // cells: v side u = v * N1 N / N*, x side u = x * N2 N* / N1; |node| <= 1/2
-    const double us1 = (double)d->N1 * (double)d->N / (double)d->Nstar;
-    const double us2 = (double)d->N2 * (double)d->Nstar / (double)d->N1;
-    info->ncell1 = (int64_t)std::floor(0.5 * us1) - (int64_t)std::floor(-0.5 * us1) + 1;
-    info->ncell2 = (int64_t)std::floor(0.5 * us2) - (int64_t)std::floor(-0.5 * us2) + 1;
+    hm::CellMap c1, c2;
+    if (!hm::cell_map(d->N1 * d->N, d->Nstar, &c1) || !hm::cell_map(d->N2 * d->Nstar, d->N1, &c2))
+        return fail(NNFFT_EINVAL, "grid too large for the node binning (scale >= 2^19)");
+    info->ncell1 = c1.ncell;
+    info->ncell2 = c2.ncell;
     int n1 = 0, n2 = 0;
     if (!hm::split_fft(d->N2, FFT_MAX_FACTOR, &n1, &n2))
         return fail(NNFFT_EINVAL, "N2 has no factorisation n1*n2 with n1, n2 <= 1024");
@@ -247,6 +248,14 @@ int upload_vec(nnfft_plan_s *p, T **dst, const std::vector<T> &v, const char *wh
     return NNFFT_OK;
 }
 
+// Cell map of side s of an instance: v side u = v N1 N / N*, x side u = x N2 N* / N1.
+hm::CellMap side_map(const nnfft_info &I, int s) {
+    hm::CellMap c{};
+    if (s == 0) hm::cell_map(I.N1 * I.N, I.Nstar, &c);
+    else hm::cell_map(I.N2 * I.Nstar, I.N1, &c);
+    return c;
+}
+
 // Prefix sums of per-instance block counts: blk[i] = first block of instance i.
 std::vector<int> prefix(const std::vector<int> &cnt, int *total) {
     std::vector<int> off(cnt.size() + 1, 0);
@@ -274,9 +283,7 @@ int upload_grid_tables(nnfft_plan_s *p, Side &S, int s, const void *coef_base, c
         const nnfft_info &I = p->inst_info[(size_t)i];
         GridInst<CoefT> &G = tab[(size_t)i];
         memset(&G, 0, sizeof(G));
-        const double us = s == 0 ? (double)I.N1 * (double)I.N / (double)I.Nstar
-                                 : (double)I.N2 * (double)I.Nstar / (double)I.N1;
-        G.c_lo = (long long)std::floor(-0.5 * us);
+        G.c_lo = side_map(I, s).c_lo;
         G.ncell = (int)(s == 0 ? I.ncell1 : I.ncell2);
         G.cell_base = (int)cell_base[(size_t)i];
         G.N2 = (int)I.N2;
@@ -406,10 +413,10 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             const nnfft_info &I = p->inst_info[(size_t)i];
             const hm::Derived &d = H[(size_t)i].d;
             NodeInst &T = tab[(size_t)i];
-            T.uscale = s == 0 ? (double)d.N1 * (double)d.N / (double)d.Nstar
-                              : (double)d.N2 * (double)d.Nstar / (double)d.N1;
-            T.c_lo = (long long)std::floor(-0.5 * T.uscale);
-            T.ncell = (int)(s == 0 ? I.ncell1 : I.ncell2);
+            const hm::CellMap cm = side_map(I, s);
+            T.S = cm.S;
+            T.c_lo = cm.c_lo;
+            T.ncell = (int)cm.ncell;
             T.cell_base = (int)cells;
             cell_base[(size_t)i] = cells;
             cells += T.ncell;
@@ -424,7 +431,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
                 for (int ic = 0; ic < T.ncell; ++ic) {
                     const double cc = (double)(T.c_lo + ic);
                     auto f = [&](double y) {
-                        const double x = (cc + 0.5 * (y + 1.0)) / T.uscale;
+                        const double x = (cc + 0.5 * (y + 1.0)) / cm.scale;
                         const double w = (double)d.m1 * (double)d.Nstar * x / (double)d.N1;
                         return (double)d.N1 / ((double)d.m1 * hm::omega_sinh_hat(w, d.beta1));
                     };

@@ -4,6 +4,7 @@ Gauss-Legendre rule, error paths) agrees with the oracle.  No compute call is
 made on a device."""
 import ctypes
 import math
+from fractions import Fraction
 import os
 import re
 
@@ -48,9 +49,11 @@ def test_plan_parameters_match_oracle(N, s1, s2, m1, m2):
             assert abs(info[k] - getattr(P, k)) < 1e-12 * abs(getattr(P, k)), k
         assert info["fft_n1"] * info["fft_n2"] == info["N2"]
         assert max(info["fft_n1"], info["fft_n2"]) <= 1024
-        # cell counts cover every node in [-1/2, 1/2]
-        us1 = P.N1 * N / P.Nstar
+        # cell counts cover every node in [-1/2, 1/2]: u = v N1 N / N* (exact rational)
+        us1 = Fraction(P.N1 * N, P.Nstar)
         assert info["ncell1"] == math.floor(us1 / 2) - math.floor(-us1 / 2) + 1
+        us2 = Fraction(P.N2 * P.Nstar, P.N1)
+        assert info["ncell2"] == math.floor(us2 / 2) - math.floor(-us2 / 2) + 1
 
 
 def test_window_fit_is_accurate_against_oracle_window():

@@ -180,6 +180,34 @@ def test_boundary_nodes_and_one_cell():
     assert oracle.relative_error(y, exact, f) <= 1e-12
 
 
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+def test_node_edge_values(dtype, m, tol):
+    """Nodes on cell boundaries (k / scale and their neighbours one ulp away), +-0,
+    subnormal and tiny nodes, +-1/2: the fixed-point binning puts each in a valid cell
+    with its local coordinate, so the sums match the direct sum."""
+    N = 96
+    info = B.params(N, 10, 10, 2.0, 2.0, m, m, "complex128")
+    us1 = info["N1"] * N / info["Nstar"]
+    us2 = info["N2"] * info["Nstar"] / info["N1"]
+    edges1 = np.arange(-40, 41) / us1
+    edges2 = np.arange(-40, 41) / us2
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 1e-300, -1e-300, 1e-17, -1e-17, 0.5, -0.5,
+                        np.nextafter(0.5, 0), np.nextafter(-0.5, 0)])
+    v = np.concatenate([edges1, np.nextafter(edges1, 1), np.nextafter(edges1, -1), special])
+    x = np.concatenate([edges2, np.nextafter(edges2, 1), np.nextafter(edges2, -1), special])
+    v, x = np.clip(v, -0.5, 0.5), np.clip(x, -0.5, 0.5)
+    rng = np.random.default_rng(12)
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    f = W.draw_complex(rng, len(v), npd)
+    y, _ = run_forward(N, v, x, f, m, dtype)
+    exact = oracle.nnfft_direct(N, v, f.astype(np.complex128), x)
+    assert oracle.relative_error(y.astype(np.complex128), exact, f.astype(np.complex128)) <= tol
+    g = W.draw_complex(rng, len(x), npd)
+    z, _ = run_adjoint(N, v, x, g, m, dtype)
+    exact = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128))
+    assert oracle.relative_error(z.astype(np.complex128), exact, g.astype(np.complex128)) <= tol
+
+
 def test_heavy_cells_split_into_items():
     """Chebyshev nodes at small N put thousands of points in the edge cells (> ITEM_CAP)."""
     N, M1, M2 = 32, 60000, 50000
