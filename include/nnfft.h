@@ -127,6 +127,31 @@ int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const i
                      const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
                      nnfft_dtype dtype, void *stream);
 
+/*
+ * nnfft_set_sizes: use a single-instance plan for M1 <= (M1 at creation) frequency nodes
+ * and M2 <= (M2 at creation) spatial nodes from now on (a plan made for the largest size
+ * serves smaller requests; the results are those of a plan made for the exact sizes).
+ * Discards the node preprocessing: call nnfft_set_nodes next.  EINVAL for batches or
+ * sizes above the capacity.  Host-side only; work already queued is unaffected.
+ */
+int nnfft_set_sizes(nnfft_plan_t p, int64_t M1, int64_t M2);
+
+/*
+ * nnfft_set_bandwidth: use a single-instance plan made for bandwidth N' for the
+ * transform with bandwidth N <= N' (exp(-2 pi i N v x)): the frequency nodes are binned
+ * with u = v N1 N / N* instead of v N1 N' / N*, which is the plan's transform at the
+ * nodes v N / N' (in [-1/2, 1/2]).  The window parameters stay those of N' (oversampling
+ * relative to N grows).  Discards the node preprocessing of the v side.  EINVAL for
+ * batches or N outside [1, N'].
+ */
+int nnfft_set_bandwidth(nnfft_plan_t p, int64_t N);
+
+/*
+ * nnfft_set_stream: issue the plan's later work on `stream` (cudaStream_t or NULL).
+ * The caller orders it after the plan's earlier work (e.g. by waiting for it).
+ */
+int nnfft_set_stream(nnfft_plan_t p, void *stream);
+
 /* nnfft_batch_count: number of instances in the plan (1 for nnfft_plan). */
 int nnfft_batch_count(nnfft_plan_t p, int64_t *count);
 
@@ -303,6 +328,71 @@ int nnfft_timing_read(nnfft_plan_t p, nnfft_timing *out, int reset);
 
 /* nnfft_launch_count: number of kernels this library has launched in the process. */
 int64_t nnfft_launch_count(void);
+
+/*
+ * Request loop (serving).  The paper has no counterpart: this serves many NNFFT and fast
+ * sinc transform requests of different N, M1, M2 and tolerances on one GPU.
+ *
+ * nnfft_tolerance_params: the arithmetic a tolerance (max error / sum |f|) is served
+ * with: *dtype = NNFFT_C64 for tol >= 1e-6, else NNFFT_C128; *m = the smallest window
+ * half-width in [2, 12] with (24 m^{3/2} + 10) exp(-2 pi m sqrt(1/2)) <= tol (the first
+ * term of Theorem 4.1 at sigma = 2).  Host only.
+ */
+int nnfft_tolerance_params(double tol, int *dtype, int *m);
+
+enum { NNFFT_REQ_NNFFT = 0, NNFFT_REQ_SINC = 1 };
+
+/*
+ * One request.  NNFFT: y_j = sum_k f_k exp(-2 pi i N v_k x_j), M1 nodes v and values f,
+ * M2 nodes x and outputs y.  Sinc (Algorithm 6.1): h_l = sum_k c_k sinc(N pi (b_l - a_k)),
+ * with v = a and f = c (M1 = L1 of them), x = b and y = h (M2 = L2), `rule` a
+ * SINC_RULE_* (2N Gauss-Legendre or 4N Clenshaw-Curtis for the request's bandwidth
+ * bucket), `is_complex` selecting complex c / h (else real).  All pointers are HOST
+ * memory (pinned memory gives asynchronous copies), owned by the caller and kept alive
+ * until nnfft_server_wait returns for the request.  Values are in the tolerance's type
+ * (nnfft_tolerance_params): complex64 / float for NNFFT_C64, complex128 / double else.
+ */
+typedef struct {
+    int kind;              /* NNFFT_REQ_NNFFT or NNFFT_REQ_SINC */
+    int rule;              /* sinc only */
+    int is_complex;        /* sinc only */
+    int reserved;
+    int64_t N, M1, M2;     /* 1 <= N <= 65536 (sinc: <= 16384); M1, M2 <= max_points */
+    double tol;            /* > 0 */
+    const double *v, *x;
+    const void *f;
+    void *y;
+} nnfft_request;
+
+typedef struct {
+    int64_t completed, failed, pending, in_flight;
+    double p50_ms, p99_ms, mean_ms, max_ms;   /* latency submit -> completion */
+    double points;                            /* sum of M1 + M2 of completed requests */
+    double seconds;                           /* first submit -> last completion */
+    int64_t plans_cached, plans_made, plans_evicted, device_bytes;
+} nnfft_server_report;
+
+/*
+ * nnfft_server_create: start a request loop on the current device with `slots` request
+ * slots (streams; 1..64), device buffers for requests of up to max_points nodes per side,
+ * and a device-memory budget (bytes) for buffers plus cached plans.  Requests queue in
+ * arrival order; a request starts when a slot is free and its plans fit in the budget
+ * (idle cached plans are evicted least recently used first).  Plans are cached per
+ * (bandwidth rounded up to a power of two >= 64, tolerance class) with capacities
+ * rounded up to powers of two; a result equals that of the library's own plan for the
+ * bucket's parameters (the same result alone and in any mix of requests).
+ */
+typedef struct nnfft_server_s *nnfft_server_t;
+int nnfft_server_create(nnfft_server_t *out, int64_t mem_budget_bytes, int slots,
+                        int64_t max_points);
+/* Queue a request (copied); *id identifies it.  EINVAL for sizes outside the limits. */
+int nnfft_server_submit(nnfft_server_t s, const nnfft_request *r, int64_t *id);
+/* Block until request id is done; returns its status (the id is then released). */
+int nnfft_server_wait(nnfft_server_t s, int64_t id, double *latency_ms);
+/* Latency percentiles and throughput of the requests completed so far (reset: restart). */
+int nnfft_server_stats(nnfft_server_t s, nnfft_server_report *out, int reset);
+/* Finish the queued requests, stop the loop and free everything. */
+int nnfft_server_destroy(nnfft_server_t s);
 
 /* nnfft_last_error: thread-local message describing the last non-OK status. */
 const char *nnfft_last_error(void);

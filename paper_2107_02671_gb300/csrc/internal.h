@@ -154,6 +154,15 @@ __device__ __forceinline__ int block_instance(const int *blk, int ninst, int b) 
 int report_error(int code, const std::string &msg);
 // The stream a plan was created with.
 cudaStream_t plan_stream(nnfft_plan_t p);
+// Device bytes a plan holds.
+size_t plan_bytes(nnfft_plan_t p);
+// Fast sinc transform through plans cached per (sizes rounded up to capacities, stream);
+// *plan_bytes receives the device bytes of the plans used.
+int sinc_exec_capacity(int64_t N, int64_t L1, int64_t L2, int64_t L1cap, int64_t L2cap, int m,
+                       nnfft_dtype dtype, int rule, int64_t n, const double *a_dev,
+                       const void *c_dev, const double *b_dev, void *h_dev, int is_complex,
+                       cudaStream_t stream, size_t *plan_bytes);
+size_t sinc_release_stream(cudaStream_t stream);
 
 // ---- kern_nodes.cu ----------------------------------------------------------------
 size_t radix_sort_hist_len(int n);

@@ -51,6 +51,7 @@ struct Side {
     // plan-time (all instances of the plan concatenated)
     int m = 0, D = 0;
     int ncell = 0, M = 0, max_items = 0, key_bits = 8;
+    int M_cap = 0;                         // points the buffers hold (M <= M_cap)
     bool has_r = false;
     NodeInst one{};                        // binning of a single-instance plan
     long long *pt_off = nullptr;           // [ninst + 1] device, batches only
@@ -80,6 +81,7 @@ struct Side {
 struct nnfft_plan_s {
     nnfft_info info{};                       // the instance (or, for batches, totals)
     int64_t ninst = 1;
+    int64_t N_built = 0;                     // N the plan was made for (single instance)
     std::vector<nnfft_info> inst_info;       // per instance
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;              // second stream: the two node sides sort concurrently
@@ -101,6 +103,7 @@ struct nnfft_plan_s {
     double *st_v = nullptr, *st_x = nullptr;
     void *st_f = nullptr, *st_y = nullptr;
     std::vector<void *> allocs;
+    size_t bytes = 0;            // device bytes the plan holds
     // per-stage timing (nnfft_timing_enable)
     bool timing = false;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -124,6 +127,7 @@ int dalloc(nnfft_plan_s *p, void **ptr, size_t bytes, const char *what) {
                     std::string("cudaMalloc(") + what + "): " + cudaGetErrorString(e));
     }
     p->allocs.push_back(*ptr);
+    p->bytes += bytes;
     return NNFFT_OK;
 }
 
@@ -355,6 +359,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
 
     // aggregate info: the instance itself, or totals / maxima for a batch
     p->info = p->inst_info[0];
+    p->N_built = p->inst_info[0].N;
     if (count > 1) {
         nnfft_info &A = p->info;
         A.M1 = Mtot[0];
@@ -442,6 +447,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         if (cells > (1LL << 30)) return fail(NNFFT_EINVAL, "too many grid cells in one plan");
         S.ncell = (int)cells;
         S.M = (int)pt_off.back();
+        S.M_cap = S.M;
         S.max_items = S.ncell + (S.M + ITEM_CAP - 1) / ITEM_CAP + (int)count;
         S.key_bits = key_bits_for(S.ncell);
         S.one = tab[0];
@@ -944,6 +950,39 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigm
     return nnfft_batch_plan(out, 1, &N, &M1, &M2, sigma1, sigma2, m1, m2, dtype, stream);
 }
 
+int nnfft_set_sizes(nnfft_plan_t p, int64_t M1, int64_t M2) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (p->ninst != 1) return fail(NNFFT_EINVAL, "nnfft_set_sizes applies to single-instance plans");
+    if (M1 < 0 || M2 < 0 || M1 > p->side[0].M_cap || M2 > p->side[1].M_cap)
+        return fail(NNFFT_EINVAL, "sizes exceed the plan's capacity");
+    p->side[0].M = (int)M1;
+    p->side[1].M = (int)M2;
+    p->side[0].set = p->side[1].set = false;
+    p->info.M1 = p->inst_info[0].M1 = M1;
+    p->info.M2 = p->inst_info[0].M2 = M2;
+    return NNFFT_OK;
+}
+
+int nnfft_set_bandwidth(nnfft_plan_t p, int64_t N) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (p->ninst != 1) return fail(NNFFT_EINVAL, "nnfft_set_bandwidth applies to single-instance plans");
+    nnfft_info &I = p->inst_info[0];
+    if (N < 1 || N > p->N_built) return fail(NNFFT_EINVAL, "bandwidth above the plan's N");
+    hm::CellMap cm{};
+    if (!hm::cell_map(I.N1 * N, I.Nstar, &cm)) return fail(NNFFT_EINVAL, "invalid bandwidth");
+    p->side[0].one.S = cm.S;      // u = v N1 N / N*: the cells of the plan's N cover it
+    p->side[0].set = false;
+    I.N = N;
+    p->info.N = N;
+    return NNFFT_OK;
+}
+
+int nnfft_set_stream(nnfft_plan_t p, void *stream) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    p->stream = static_cast<cudaStream_t>(stream);
+    return NNFFT_OK;
+}
+
 int nnfft_batch_count(nnfft_plan_t p, int64_t *count) {
     if (!p || !count) return fail(NNFFT_EINVAL, "null argument");
     *count = p->ninst;
@@ -1077,10 +1116,11 @@ int nnfft_destroy(nnfft_plan_t p) {
 static int ensure_staging(nnfft_plan_s *p) {
     const size_t cs = 2 * real_size(p->dbl);
     int rc;
-    if (!p->st_v && (rc = dalloc_n(p, &p->st_v, (size_t)p->info.M1, "staging"))) return rc;
-    if (!p->st_x && (rc = dalloc_n(p, &p->st_x, (size_t)p->info.M2, "staging"))) return rc;
-    if (!p->st_f && (rc = dalloc(p, &p->st_f, (size_t)p->info.M1 * cs, "staging"))) return rc;
-    if (!p->st_y && (rc = dalloc(p, &p->st_y, (size_t)p->info.M2 * cs, "staging"))) return rc;
+    const size_t c1 = (size_t)p->side[0].M_cap, c2 = (size_t)p->side[1].M_cap;
+    if (!p->st_v && (rc = dalloc_n(p, &p->st_v, c1, "staging"))) return rc;
+    if (!p->st_x && (rc = dalloc_n(p, &p->st_x, c2, "staging"))) return rc;
+    if (!p->st_f && (rc = dalloc(p, &p->st_f, c1 * cs, "staging"))) return rc;
+    if (!p->st_y && (rc = dalloc(p, &p->st_y, c2 * cs, "staging"))) return rc;
     return NNFFT_OK;
 }
 
@@ -1145,6 +1185,7 @@ namespace {
 struct SincPlan {
     nnfft_plan_t p1 = nullptr, p2 = nullptr;
     int64_t nq = 0;                           // number of quadrature nodes
+    int64_t L1 = 0, L2 = 0;                   // current sizes (<= the plans' capacities)
     double *x1 = nullptr, *v2 = nullptr, *w = nullptr;
     void *cbuf = nullptr, *gbuf = nullptr, *hbuf = nullptr;
     bool nodes_fixed = false;
@@ -1256,6 +1297,8 @@ int sinc_make(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, int r
     SincPlan *s = new SincPlan();
     s->stream = st;
     s->nq = nq;
+    s->L1 = L1;
+    s->L2 = L2;
     rc = nnfft_plan(&s->p1, N, L1, nq, 2.0, 2.0, m, m, dtype, st);
     if (!rc) rc = nnfft_plan(&s->p2, N, nq, L2, 2.0, 2.0, m, m, dtype, st);
     if (rc) { sinc_free(s); return rc; }
@@ -1295,6 +1338,12 @@ int sinc_run(SincPlan *s, int64_t L1, int64_t L2, const double *a, const void *c
     cudaStream_t st = s->stream;
     const int nq = (int)s->nq;
     int rc;
+    if (L1 != s->L1 || L2 != s->L2) {         // a plan made for larger sizes serves this call
+        if ((rc = nnfft_set_sizes(s->p1, L1, nq)) || (rc = nnfft_set_sizes(s->p2, nq, L2))) return rc;
+        s->L1 = L1;
+        s->L2 = L2;
+        s->nodes_fixed = false;
+    }
     // step 1, NNFFT #1: g_j = sum_k c_k e^{-2 pi i N a_k x1_j}
     if ((rc = nnfft_set_nodes(s->p1, a, s->nodes_fixed ? nullptr : s->x1))) return rc;
     const void *cin = c;
@@ -1356,6 +1405,44 @@ int sinc_exec_rule(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, 
     return dtype == NNFFT_C128 ? sinc_run<double>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex)
                                : sinc_run<float>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex);
 }
+
+}  // extern "C"
+
+namespace nnfft {
+// Algorithm 6.1 through plans cached for capacities (L1cap, L2cap) >= (L1, L2) on `stream`
+// (the request loop's slots): the cache key holds the capacities, the call the sizes.
+int sinc_exec_capacity(int64_t N, int64_t L1, int64_t L2, int64_t L1cap, int64_t L2cap, int m,
+                       nnfft_dtype dtype, int rule, int64_t n, const double *a_dev,
+                       const void *c_dev, const double *b_dev, void *h_dev, int is_complex,
+                       cudaStream_t stream, size_t *plan_bytes) {
+    if (L1 > L1cap || L2 > L2cap) return fail(NNFFT_EINVAL, "sizes above the capacity");
+    SincPlan *s = nullptr;
+    int rc = sinc_get(N, L1cap, L2cap, m, dtype, rule, n, stream, &s);
+    if (rc) return rc;
+    if (plan_bytes) *plan_bytes = s->p1->bytes + s->p2->bytes;
+    if (L2 == 0) return NNFFT_OK;
+    return dtype == NNFFT_C128 ? sinc_run<double>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex)
+                               : sinc_run<float>(s, L1, L2, a_dev, c_dev, b_dev, h_dev, is_complex);
+}
+// Free the cached sinc plans of one stream; returns the device bytes released.
+size_t sinc_release_stream(cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g_sinc_mu);
+    size_t freed = 0;
+    for (auto it = g_sinc.begin(); it != g_sinc.end();) {
+        if (it->second->stream == stream) {
+            freed += it->second->p1->bytes + it->second->p2->bytes;
+            sinc_free(it->second);
+            it = g_sinc.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return freed;
+}
+size_t plan_bytes(nnfft_plan_t p) { return p ? p->bytes : 0; }
+}  // namespace nnfft
+
+extern "C" {
 
 int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype, const double *a_dev,
               const void *c_dev, const double *b_dev, void *h_dev, int is_complex, void *stream) {

@@ -28,6 +28,26 @@ STAGES = ("nodes_v", "nodes_x", "fwd_moments", "fwd_spread_conv", "fwd_fft", "fw
           "fwd_cell_fold", "adj_cell_fold")
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("rule", ctypes.c_int), ("is_complex", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("N", ctypes.c_int64), ("M1", ctypes.c_int64),
+                ("M2", ctypes.c_int64), ("tol", ctypes.c_double), ("v", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("f", ctypes.c_void_p), ("y", ctypes.c_void_p)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("points", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("plans_cached", ctypes.c_int64), ("plans_made", ctypes.c_int64),
+                ("plans_evicted", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("count", ctypes.c_int64 * 16)]
 
@@ -81,6 +101,15 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_batch_plan.argtypes = [P(vp), i64, P(i64), P(i64), P(i64), dbl, dbl, cint, cint,
                                          cint, vp]
         lib.nnfft_batch_count.argtypes = [vp, P(i64)]
+        lib.nnfft_set_sizes.argtypes = [vp, i64, i64]
+        lib.nnfft_set_bandwidth.argtypes = [vp, i64]
+        lib.nnfft_tolerance_params.argtypes = [dbl, P(cint), P(cint)]
+        lib.nnfft_server_create.argtypes = [P(vp), i64, cint, i64]
+        lib.nnfft_server_submit.argtypes = [vp, P(Request), P(i64)]
+        lib.nnfft_server_wait.argtypes = [vp, i64, P(dbl)]
+        lib.nnfft_server_stats.argtypes = [vp, P(ServerReport), cint]
+        lib.nnfft_server_destroy.argtypes = [vp]
+        lib.nnfft_set_stream.argtypes = [vp, vp]
         lib.nnfft_batch_info.argtypes = [vp, i64, P(Info)]
         lib.nnfft_set_nodes.argtypes = [vp, vp, vp]
         lib.nnfft_exec.argtypes = [vp, vp, vp]
@@ -188,6 +217,18 @@ class Plan:
         info = Info()
         _check(self._lib.nnfft_plan_info(self._h, ctypes.byref(info)))
         return info.as_dict()
+
+    def set_sizes(self, M1, M2):
+        """Serve M1 <= capacity frequency and M2 <= capacity spatial nodes (set_nodes next)."""
+        _check(self._lib.nnfft_set_sizes(self._h, int(M1), int(M2)))
+        self.M1, self.M2 = int(M1), int(M2)
+        return self
+
+    def set_bandwidth(self, N):
+        """Use the plan (made for bandwidth N') for bandwidth N <= N' (set_nodes next)."""
+        _check(self._lib.nnfft_set_bandwidth(self._h, int(N)))
+        self.N = int(N)
+        return self
 
     def set_arith(self, arith):
         """ARITH_FP64 or ARITH_FP64_SPLIT for complex128 plans; call set_nodes afterwards."""
@@ -314,6 +355,85 @@ class BatchPlan(Plan):
         info = Info()
         _check(self._lib.nnfft_batch_info(self._h, int(i), ctypes.byref(info)))
         return info.as_dict()
+
+
+def tolerance_params(tol):
+    """(dtype code, m) that the request loop serves a tolerance with."""
+    lib = load_library()
+    dt, m = ctypes.c_int(), ctypes.c_int()
+    _check(lib.nnfft_tolerance_params(float(tol), ctypes.byref(dt), ctypes.byref(m)))
+    return dt.value, m.value
+
+
+class Server:
+    """Request loop (continuous batching) for NNFFT and sinc requests on the current GPU.
+
+    Arrays are host numpy arrays (pinned ones copy asynchronously) of the tolerance's type
+    (tolerance_params: complex64/float32 for tol >= 1e-6, complex128/float64 otherwise);
+    they must stay alive until wait() returns for the request.
+    """
+
+    def __init__(self, mem_budget_bytes=64 << 30, slots=4, max_points=1 << 22):
+        lib = load_library()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        _check(lib.nnfft_server_create(ctypes.byref(self._h), int(mem_budget_bytes), int(slots),
+                                       int(max_points)))
+
+    @staticmethod
+    def _ptr(a, dtypes, n, name):
+        if not (isinstance(a, np.ndarray) and a.dtype in dtypes and a.size == n and a.flags.c_contiguous):
+            raise TypeError(f"{name} must be a contiguous {'/'.join(map(str, dtypes))} array of {n}")
+        return a.ctypes.data if n else None
+
+    def _submit(self, kind, N, v, x, f, y, tol, rule=0, is_complex=1):
+        dt, _ = tolerance_params(tol)
+        c = np.complex128 if dt == NNFFT_C128 else np.complex64
+        r = np.float64 if dt == NNFFT_C128 else np.float32
+        vals = (np.dtype(c),) if is_complex else (np.dtype(r),)
+        req = Request(kind, int(rule), int(is_complex), 0, int(N), int(v.size), int(x.size), float(tol),
+                      self._ptr(v, (np.dtype(np.float64),), v.size, "v"),
+                      self._ptr(x, (np.dtype(np.float64),), x.size, "x"),
+                      self._ptr(f, vals, v.size, "f"), self._ptr(y, vals, x.size, "y"))
+        rid = ctypes.c_int64()
+        _check(self._lib.nnfft_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)))
+        self._keep[rid.value] = (v, x, f, y)
+        return rid.value
+
+    def submit_nnfft(self, N, v, x, f, y, tol):
+        """y = sum_k f_k exp(-2 pi i N v_k x); returns the request id."""
+        return self._submit(0, N, v, x, f, y, tol)
+
+    def submit_sinc(self, N, a, c, b, h, tol, rule="gl"):
+        """h = sum_k c_k sinc(N pi (b - a_k)) (Algorithm 6.1); returns the request id."""
+        return self._submit(1, N, a, b, c, h, tol, _rule_code(rule), int(np.iscomplexobj(c)))
+
+    def wait(self, rid):
+        """Block until the request is done; returns its latency in ms."""
+        lat = ctypes.c_double()
+        try:
+            _check(self._lib.nnfft_server_wait(self._h, int(rid), ctypes.byref(lat)))
+        finally:
+            self._keep.pop(rid, None)
+        return lat.value
+
+    def stats(self, reset=False) -> dict:
+        rep = ServerReport()
+        _check(self._lib.nnfft_server_stats(self._h, ctypes.byref(rep), int(bool(reset))))
+        return rep.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.nnfft_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 SINC_RULES = {"gl": 0, "cc": 1}

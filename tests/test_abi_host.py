@@ -96,3 +96,15 @@ def test_plan_without_gpu_fails_loudly():
     rc = lib.nnfft_plan(ctypes.byref(h), 64, 10, 10, 2.0, 2.0, 4, 4, 1, None)
     assert rc == 4 and not h.value
     assert b"CUDA" in lib.nnfft_last_error() or len(lib.nnfft_last_error()) > 0
+
+
+def test_tolerance_classes():
+    """The request loop serves tol >= 1e-6 in fp32 and smaller tolerances in fp64, with the
+    smallest m whose Theorem 4.1 first term (sigma = 2) is below tol."""
+    assert B.tolerance_params(1e-5) == (B.NNFFT_C64, 4)
+    assert B.tolerance_params(1e-9) == (B.NNFFT_C128, 6)
+    assert B.tolerance_params(1e-12) == (B.NNFFT_C128, 8)
+    for tol in (1e-3, 1e-5, 1e-7, 1e-9, 1e-11, 1e-13):
+        _, m = B.tolerance_params(tol)
+        term = lambda mm: (24 * mm ** 1.5 + 10) * math.exp(-2 * math.pi * mm * math.sqrt(0.5))  # noqa: E731
+        assert term(m) <= tol and (m == 2 or term(m - 1) > tol)
