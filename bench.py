@@ -329,6 +329,98 @@ def run_batched(args, rank, dev, flush, timed, pk):
     return out
 
 
+SERVE_RATE, SERVE_WARM, SERVE_TIMED = 2000.0, 1500, 12000
+SERVE_MAXP = 1 << 22
+
+
+def run_served(args, rank):
+    """The served mixed stream: Poisson arrivals at 2000 requests/s, 70% NNFFT and 30% sinc
+    transform, N log-uniform in [64, 16384], M1 and M2 log-uniform in [1e3, 4e6], tolerance
+    drawn from {1e-5, 1e-9, 1e-12}, 64 GB device budget, 4 slots.  Host inputs are slices
+    of pinned pools (synthetic uniform nodes, N(0,1) values).  The first SERVE_WARM
+    requests fill the plan cache and are not counted; latency is submit -> completion."""
+    import threading
+    import torch
+    from paper_2107_02671_gb300 import nnfft as B
+    rng = np.random.default_rng(42 + rank)
+    n = SERVE_WARM + min(SERVE_TIMED, max(2000, 100 * args.steps))
+    gaps = rng.exponential(1.0 / SERVE_RATE, n)
+    kind = rng.random(n) < 0.7                       # True: NNFFT
+    lN, lM = np.log([64, 16384]), np.log([1e3, 4e6])
+    Ns = np.rint(np.exp(rng.uniform(*lN, n))).astype(np.int64)
+    M1 = np.rint(np.exp(rng.uniform(*lM, n))).astype(np.int64)
+    M2 = np.rint(np.exp(rng.uniform(*lM, n))).astype(np.int64)
+    tols = rng.choice([1e-5, 1e-9, 1e-12], n)
+    P = SERVE_MAXP
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()      # noqa: E731
+    nodes = pin(rng.uniform(-0.5, 0.5, P))
+    c128 = pin((rng.standard_normal(P) + 1j * rng.standard_normal(P)).astype(np.complex128))
+    c64 = pin(c128.astype(np.complex64))
+    r64 = pin(rng.standard_normal(P))
+    r32 = pin(r64.astype(np.float32))
+    ring = 16
+    out128 = [torch.empty(P, dtype=torch.complex128).pin_memory().numpy() for _ in range(ring)]
+    S = B.Server(mem_budget_bytes=64 << 30, slots=4, max_points=P)
+    ids = []
+    done = threading.Event()
+    lat = []
+
+    def waiter():
+        k = 0
+        while k < n:
+            if k < len(ids):
+                lat.append(S.wait(ids[k]))
+                k += 1
+            elif done.is_set() and k >= len(ids):
+                break
+            else:
+                time.sleep(0.0002)
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    warm_done_at = None
+    for i in range(n):
+        if i == SERVE_WARM:
+            while len(lat) < SERVE_WARM:               # drain the warm-up, then restart the clock
+                time.sleep(0.001)
+            S.stats(reset=True)
+            t_next = time.perf_counter()
+            warm_done_at = t_next
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            pass
+        m1, m2, N = int(M1[i]), int(M2[i]), int(Ns[i])
+        o1, o2 = int(rng.integers(0, P - m1 + 1)), int(rng.integers(0, P - m2 + 1))
+        v, x = nodes[o1:o1 + m1], nodes[o2:o2 + m2]
+        dt, _ = B.tolerance_params(tols[i])
+        buf = out128[i % ring]
+        if kind[i]:
+            f = (c128 if dt == B.NNFFT_C128 else c64)[o1:o1 + m1]
+            y = buf.view(f.dtype)[:m2]
+            ids.append(S.submit_nnfft(N, v, x, f, y, tols[i]))
+        else:
+            N = min(N, 16384)
+            c = (r64 if dt == B.NNFFT_C128 else r32)[o1:o1 + m1]
+            h = buf.view(c.dtype)[:m2]
+            ids.append(S.submit_sinc(N, v, c, x, h, tols[i], "gl"))
+    done.set()
+    th.join()
+    st = S.stats()
+    S.close()
+    timed = n - SERVE_WARM
+    offered = float(np.sum((M1 + M2)[SERVE_WARM:]))
+    return {"requests_timed": timed, "requests_warmup": SERVE_WARM, "arrival_rate_per_s": SERVE_RATE,
+            "mix": "70% NNFFT / 30% sinc (GL), N in [64, 16384], M in [1e3, 4e6], tol {1e-5, 1e-9, 1e-12}",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "pts_per_s": st["points"] / st["seconds"] if st["seconds"] > 0 else None,
+            "offered_pts_per_s": offered / (time.perf_counter() - warm_done_at),
+            "completed": st["completed"], "failed": st["failed"], "plans_cached": st["plans_cached"],
+            "plans_made": st["plans_made"], "plans_evicted": st["plans_evicted"],
+            "device_gb": st["device_bytes"] / 2**30, "slots": 4, "budget_gb": 64}
+
+
 def whole_job_value(total_ms, steps, pts_step, world, device="cpu"):
     """Replicas: every rank times its own copy of the workload; the job's time is the
     maximum over ranks and its throughput counts the points of all ranks."""
@@ -406,6 +498,11 @@ def run_ours(args, rank, world):
             pl.timing(False)
         return ms, launches, stages
 
+    if args.only_served:
+        res = run_served(args, rank)
+        if rank == 0:
+            print(json.dumps({"section": "served", **res}))
+        return 0
     if args.only_batched:      # the batched workload alone (profiling runs)
         pk, _ = peaks()
         res = run_batched(args, rank, dev, flush, timed, pk)
@@ -521,6 +618,13 @@ def run_ours(args, rank, world):
     if not args.no_batch:
         extra["batched"] = run_batched(args, rank, dev, flush, timed, pk)
 
+    # ---- served mixed stream (request loop) --------------------------------------------------
+    if not args.no_serve and rank == 0:
+        try:
+            extra["served"] = run_served(args, rank)
+        except Exception as e:   # reported, the tests enforce correctness
+            extra["served"] = {"error": f"{type(e).__name__}: {e}"}
+
     # ---- fast sinc transform (config N=1024, L1=L2=2^18) ----------------------------------------
     a, c, bb = W.sinc_inputs(SINC_L, SINC_L, rank)
     ad, cd, bd = to_dev(a), to_dev(c), to_dev(bb)
@@ -609,6 +713,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served mixed stream")
+    ap.add_argument("--only-served", action="store_true",
+                    help="run only the served mixed stream and print its numbers")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched workload and print its numbers (profiling)")
     args = ap.parse_args()

@@ -1,4 +1,7 @@
 // hostmath.cpp -- see hostmath.h.
+#include <algorithm>
+#include <thread>
+
 #include "hostmath.h"
 
 #include <cmath>
@@ -128,24 +131,13 @@ int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
     return 20;
 }
 
-void gauss_legendre(int64_t n, double *tau, double *w) {
-    for (int64_t i = 0; i < (n + 1) / 2; ++i) {
-        double t = std::cos(PI * ((double)i + 0.75) / ((double)n + 0.5));
-        double pn = 0.0, pm = 0.0;
-        for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = t;
-            for (int64_t k = 2; k <= n; ++k) {
-                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
-                p0 = p1;
-                p1 = p2;
-            }
-            pn = n == 1 ? t : p1;
-            pm = n == 1 ? 1.0 : p0;
-            const double dp = (double)n * (t * pn - pm) / (t * t - 1.0);
-            const double dt = pn / dp;
-            t -= dt;
-            if (std::fabs(dt) < 1e-17) break;
-        }
+// One node pair of the n-point rule: Newton on P_n (three-term recurrence) from the
+// Chebyshev-like initial guess of node i (from the top), then the weight 2/((1-t^2) P_n'(t)^2),
+// halved for [-1/2, 1/2].
+static void gl_node(int64_t n, int64_t i, double *tau, double *w) {
+    double t = std::cos(PI * ((double)i + 0.75) / ((double)n + 0.5));
+    double pn = 0.0, pm = 0.0;
+    for (int it = 0; it < 100; ++it) {
         double p0 = 1.0, p1 = t;
         for (int64_t k = 2; k <= n; ++k) {
             const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
@@ -155,12 +147,36 @@ void gauss_legendre(int64_t n, double *tau, double *w) {
         pn = n == 1 ? t : p1;
         pm = n == 1 ? 1.0 : p0;
         const double dp = (double)n * (t * pn - pm) / (t * t - 1.0);
-        const double wt = 1.0 / ((1.0 - t * t) * dp * dp);   // 2/(...) halved for [-1/2,1/2]
-        tau[n - 1 - i] = 0.5 * t;
-        tau[i] = -0.5 * t;
-        w[n - 1 - i] = wt;
-        w[i] = wt;
+        const double dt = pn / dp;
+        t -= dt;
+        if (std::fabs(dt) < 1e-15) break;      // quadratic convergence: t is at ulp level
     }
+    double p0 = 1.0, p1 = t;
+    for (int64_t k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / (double)k;
+        p0 = p1;
+        p1 = p2;
+    }
+    pn = n == 1 ? t : p1;
+    pm = n == 1 ? 1.0 : p0;
+    const double dp = (double)n * (t * pn - pm) / (t * t - 1.0);
+    const double wt = 1.0 / ((1.0 - t * t) * dp * dp);
+    tau[n - 1 - i] = 0.5 * t;
+    tau[i] = -0.5 * t;
+    w[n - 1 - i] = wt;
+    w[i] = wt;
+}
+
+void gauss_legendre(int64_t n, double *tau, double *w) {
+    const int64_t half = (n + 1) / 2;
+    // O(n) work per node: large rules are spread over the host's cores
+    const int64_t nt = n < 512 ? 1 : std::min<int64_t>(16, std::max<unsigned>(1u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int64_t r = 0; r < nt; ++r)
+        th.emplace_back([=] {
+            for (int64_t i = r; i < half; i += nt) gl_node(n, i, tau, w);
+        });
+    for (auto &x : th) x.join();
     if (n % 2 == 1) tau[n / 2] = 0.0;
 }
 

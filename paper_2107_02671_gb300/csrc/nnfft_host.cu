@@ -169,16 +169,24 @@ int upload_df2(nnfft_plan_s *p, void **dst, const std::vector<double> &src, doub
     return NNFFT_OK;
 }
 
-// Complex table exp(-2 pi i k / n), k < n, computed in long double and rounded.
+// Complex table exp(-2 pi i k / n), k < n.  k/n is split exactly into a quarter turn q
+// and a remainder, so the library sin / cos calls see angles in [0, pi/2) (error about one
+// ulp), and exp(-2 pi i k/n) = (-i)^q exp(-i theta).
 std::vector<double> twiddles(int64_t n) {
     std::vector<double> t(2 * (size_t)n);
-    const long double twopi = 6.283185307179586476925286766559005768L;
+    const double half_pi = 1.57079632679489661923;
     for (int64_t k = 0; k < n; ++k) {
-        // reduce k/n to [-1/2, 1/2] before the trig calls
-        int64_t kk = k <= n / 2 ? k : k - n;
-        long double a = -twopi * (long double)kk / (long double)n;
-        t[2 * k] = (double)cosl(a);
-        t[2 * k + 1] = (double)sinl(a);
+        const int64_t q = (4 * k) / n, rem = 4 * k - q * n;
+        const double th = half_pi * ((double)rem / (double)n);
+        const double c = std::cos(th), sn = std::sin(th);
+        double re = c, im = -sn;                       // exp(-i theta)
+        for (int64_t j = 0; j < q; ++j) {              // times -i per quarter turn
+            const double r2 = im, i2 = -re;
+            re = r2;
+            im = i2;
+        }
+        t[2 * k] = re;
+        t[2 * k + 1] = im;
     }
     return t;
 }

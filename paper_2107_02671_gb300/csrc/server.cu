@@ -14,7 +14,8 @@
 // keyed by (bandwidth bucket, dtype, m): a plan made for bandwidth N' and capacities
 // (M1', M2') serves any request with N <= N', M1 <= M1', M2 <= M2' through
 // nnfft_set_bandwidth / nnfft_set_sizes, with the results of a plan made for the exact
-// sizes.  A sinc request (Algorithm 6.1) takes two such plans (nodes a -> quadrature
+// sizes.  Plans are made with the server's full capacity (max_points) on their data
+// sides, so one plan per bucket serves every request size.  A sinc request (Algorithm 6.1) takes two such plans (nodes a -> quadrature
 // nodes, quadrature nodes -> b) and the quadrature rule of its bandwidth bucket.  Idle
 // plans are evicted least recently used first when a new plan would exceed the budget.
 //
@@ -24,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -102,12 +104,13 @@ struct nnfft_server_s {
     int64_t next_id = 1;
     uint64_t tick = 0;
     int64_t budget = 0, max_points = 0;
-    size_t fixed_bytes = 0;          // slot buffers and rules
-    size_t plan_bytes = 0;
+    std::atomic<size_t> fixed_bytes{0};   // slot buffers and rules (worker writes)
+    std::atomic<size_t> plan_bytes{0};    // cached plans (worker writes)
+    std::atomic<int64_t> plans_cached{0}, plans_made{0}, plans_evicted{0};
     // statistics
     std::vector<double> lat_ms;
     double points = 0;
-    int64_t completed = 0, failed = 0, plans_made = 0, plans_evicted = 0;
+    int64_t completed = 0, failed = 0;
     Clock::time_point t_first{}, t_last{};
     bool any = false;
     int device = 0;
@@ -126,10 +129,18 @@ void tolerance_class(double tol, int *dtype, int *m) {
     *m = mm;
 }
 
+// An idle plan's last work has completed (its slot's event was seen): detach it from the
+// slot stream it last ran on (which may be destroyed before the plan) and free it.
+void destroy_idle_plan(nnfft_plan_t p) {
+    nnfft_set_stream(p, nullptr);
+    nnfft_destroy(p);
+}
+
 // An idle cached plan for (Ncap, dtype, m) with capacities >= (M1, M2), or a new one
-// within the budget (evicting idle plans, least recently used first).  nullptr: not now.
+// within the budget (evicting idle plans, least recently used first).  nullptr with
+// *err == OK: not now (plans in use will free up); *err != OK: the request fails.
 PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64_t M1,
-                        int64_t M2, int *err) {
+                        int64_t M2, int64_t c1, int64_t c2, int *err) {
     *err = NNFFT_OK;
     PlanEntry *best = nullptr;
     for (PlanEntry *e : S->plans)
@@ -141,7 +152,7 @@ PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64
         best->last = ++S->tick;
         return best;
     }
-    const int64_t c1 = pow2_at_least(M1, 4096), c2 = pow2_at_least(M2, 4096);
+    // a new plan gets the capacities (c1, c2) >= (M1, M2) the caller asks for
     // rough size for admission: sort and coordinate buffers, moments, cells, grids
     const size_t est = (size_t)(c1 + c2) * 64 + (size_t)Ncap * 2048 + (64u << 20);
     auto over = [&](size_t extra) {
@@ -151,12 +162,21 @@ PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64
         PlanEntry *victim = nullptr;
         for (PlanEntry *e : S->plans)
             if (!e->busy && (!victim || e->last < victim->last)) victim = e;
-        if (!victim) return nullptr;            // everything in use: wait for a slot
+        if (!victim) {
+            bool any_busy = false;
+            for (PlanEntry *e : S->plans) any_busy = any_busy || e->busy;
+            if (!any_busy) {                    // nothing will ever free up: cannot serve
+                *err = sfail(NNFFT_ENOMEM, "request does not fit the server's device budget");
+                return nullptr;
+            }
+            return nullptr;                     // everything in use: wait for a slot
+        }
         S->plan_bytes -= victim->bytes;
-        nnfft_destroy(victim->p);
+        destroy_idle_plan(victim->p);
         S->plans.erase(std::find(S->plans.begin(), S->plans.end(), victim));
         delete victim;
         ++S->plans_evicted;
+        --S->plans_cached;
     }
     PlanEntry *e = new PlanEntry();
     int rc = nnfft_plan(&e->p, Ncap, c1, c2, 2.0, 2.0, m, m, (nnfft_dtype)dtype, nullptr);
@@ -176,6 +196,7 @@ PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64
     S->plan_bytes += e->bytes;
     S->plans.push_back(e);
     ++S->plans_made;
+    ++S->plans_cached;
     return e;
 }
 
@@ -280,16 +301,24 @@ int launch_sinc(nnfft_server_s *S, Slot &sl, Req *q, Rule *R) {
     return NNFFT_OK;
 }
 
-void finish(nnfft_server_s *S, Slot &sl, int status) {
+// The slot's request is over (its event has completed, or it failed to start): collect
+// device-side status, release the plans and the slot.  No lock: slots and plans belong to
+// the worker thread.  Returns the request and its status.
+Req *retire(Slot &sl, int &status) {
     Req *q = sl.req;
     if (status == NNFFT_OK && sl.pa) status = nnfft_sync(sl.pa->p);
     if (status == NNFFT_OK && sl.pb) status = nnfft_sync(sl.pb->p);
     release_plan(sl.pa);
     release_plan(sl.pb);
+    sl.req = nullptr;
+    return q;
+}
+
+// Publish a finished request (caller holds the lock).
+void record_done(nnfft_server_s *S, Req *q, int status) {
     q->status = status;
     q->t_done = Clock::now();
     q->done = true;
-    sl.req = nullptr;
     if (status == NNFFT_OK) {
         ++S->completed;
         S->lat_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
@@ -300,20 +329,32 @@ void finish(nnfft_server_s *S, Slot &sl, int status) {
     S->t_last = q->t_done;
 }
 
-// Try to start the head request on slot sl; false: it has to wait (plans or memory).
-bool admit(nnfft_server_s *S, Slot &sl, Req *q) {
+enum Admit { ADMITTED, WAIT, FAILED };
+
+// Try to start request q on the free slot sl (no lock held).  WAIT: plans or memory will
+// free up when other slots finish; FAILED: *status says why.
+Admit admit(nnfft_server_s *S, Slot &sl, Req *q, int *status) {
     int err = NNFFT_OK;
     Rule *R = nullptr;
     if (q->r.kind == NNFFT_REQ_SINC) {
         if ((err = get_rule(S, q->Ncap, q->r.rule, &R)) == NNFFT_OK) {
-            sl.pa = acquire_plan(S, q->Ncap, q->dtype, q->m, q->r.M1, R->nq, &err);
-            if (sl.pa) sl.pb = acquire_plan(S, q->Ncap, q->dtype, q->m, R->nq, q->r.M2, &err);
+            // data sides get the server's full capacity, the quadrature side its rule size
+            const int64_t cq = pow2_at_least(R->nq, 64);
+            sl.pa = acquire_plan(S, q->Ncap, q->dtype, q->m, q->r.M1, R->nq, S->max_points, cq, &err);
+            if (sl.pa)
+                sl.pb = acquire_plan(S, q->Ncap, q->dtype, q->m, R->nq, q->r.M2, cq, S->max_points, &err);
             if (sl.pa && !sl.pb) release_plan(sl.pa);
         }
     } else {
-        sl.pa = acquire_plan(S, q->Ncap, q->dtype, q->m, q->r.M1, q->r.M2, &err);
+        sl.pa = acquire_plan(S, q->Ncap, q->dtype, q->m, q->r.M1, q->r.M2, S->max_points,
+                             S->max_points, &err);
     }
-    if (err == NNFFT_OK && !sl.pa) return false;
+    if (err == NNFFT_OK && !sl.pa) {
+        // waiting helps only if another slot will release plans or memory
+        for (const Slot &o : S->slots)
+            if (&o != &sl && o.req) return WAIT;
+        err = sfail(NNFFT_ENOMEM, "request does not fit the server's device budget");
+    }
     sl.req = q;
     int rc = err;
     if (rc == NNFFT_OK)
@@ -322,19 +363,17 @@ bool admit(nnfft_server_s *S, Slot &sl, Req *q) {
         cudaGetLastError();
         rc = NNFFT_ECUDA;
     }
-    if (rc != NNFFT_OK) {
-        if (sl.pa) cudaStreamSynchronize(sl.st);
-        finish(S, sl, rc);
-        S->cv_done.notify_all();
-    }
-    return true;
+    if (rc == NNFFT_OK) return ADMITTED;
+    if (sl.pa) cudaStreamSynchronize(sl.st);
+    retire(sl, rc);
+    *status = rc;
+    return FAILED;
 }
 
 void worker_loop(nnfft_server_s *S) {
     cudaSetDevice(S->device);
-    std::unique_lock<std::mutex> lk(S->mu);
     for (;;) {
-        bool progress = false, busy = false;
+        bool busy = false;
         for (Slot &sl : S->slots) {                 // retire finished requests
             if (!sl.req) continue;
             const cudaError_t e = cudaEventQuery(sl.ev);
@@ -343,25 +382,51 @@ void worker_loop(nnfft_server_s *S) {
                 continue;
             }
             if (e != cudaSuccess) cudaGetLastError();
-            finish(S, sl, e == cudaSuccess ? NNFFT_OK : NNFFT_ECUDA);
-            progress = true;
+            int st = e == cudaSuccess ? NNFFT_OK : NNFFT_ECUDA;
+            Req *q = retire(sl, st);
+            {
+                std::lock_guard<std::mutex> g(S->mu);
+                record_done(S, q, st);
+            }
+            S->cv_done.notify_all();
         }
-        if (progress) S->cv_done.notify_all();
         for (Slot &sl : S->slots) {                 // admit in arrival order
-            if (sl.req || S->pending.empty()) continue;
-            Req *q = S->pending.front();
-            if (!admit(S, sl, q)) break;
-            S->pending.pop_front();
-            busy = busy || sl.req != nullptr;
+            if (sl.req) {
+                busy = true;
+                continue;
+            }
+            Req *q = nullptr;
+            {
+                std::lock_guard<std::mutex> g(S->mu);
+                if (S->pending.empty()) break;
+                q = S->pending.front();
+                S->pending.pop_front();
+            }
+            int st = NNFFT_OK;
+            const Admit a = admit(S, sl, q, &st);
+            if (a == WAIT) {
+                std::lock_guard<std::mutex> g(S->mu);
+                S->pending.push_front(q);
+                break;
+            }
+            if (a == FAILED) {
+                {
+                    std::lock_guard<std::mutex> g(S->mu);
+                    record_done(S, q, st);
+                }
+                S->cv_done.notify_all();
+                continue;
+            }
+            busy = true;
         }
-        if (S->stop && S->pending.empty() && !busy) break;
-        if (!busy && S->pending.empty()) {
-            S->cv_work.wait(lk);
-        } else {
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (busy || !S->pending.empty()) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
-            lk.lock();
+            continue;
         }
+        if (S->stop) break;
+        S->cv_work.wait(lk);
     }
 }
 
@@ -423,6 +488,7 @@ int nnfft_server_submit(nnfft_server_t S, const nnfft_request *r, int64_t *id) {
         return sfail(NNFFT_EINVAL, "null data pointer");
     if (r->kind == NNFFT_REQ_SINC && r->rule != SINC_RULE_GL && r->rule != SINC_RULE_CC)
         return sfail(NNFFT_EINVAL, "unknown quadrature rule");
+    const Clock::time_point t0 = Clock::now();
     Req *q = new Req();
     q->r = *r;
     if (!(r->tol > 0)) {
@@ -438,7 +504,7 @@ int nnfft_server_submit(nnfft_server_t S, const nnfft_request *r, int64_t *id) {
     {
         std::lock_guard<std::mutex> lk(S->mu);
         q->id = S->next_id++;
-        q->t_submit = Clock::now();
+        q->t_submit = t0;
         if (!S->any) {
             S->t_first = q->t_submit;
             S->any = true;
@@ -479,7 +545,8 @@ int nnfft_server_stats(nnfft_server_t S, nnfft_server_report *out, int reset) {
     out->completed = S->completed;
     out->failed = S->failed;
     out->pending = (int64_t)S->pending.size();
-    for (const Slot &sl : S->slots) out->in_flight += sl.req ? 1 : 0;
+    out->in_flight = (int64_t)S->reqs.size() - (int64_t)S->pending.size();
+    for (const auto &kv : S->reqs) out->in_flight -= kv.second->done ? 1 : 0;
     out->p50_ms = pct(0.50);
     out->p99_ms = pct(0.99);
     out->max_ms = l.empty() ? 0.0 : l.back();
@@ -488,7 +555,7 @@ int nnfft_server_stats(nnfft_server_t S, nnfft_server_report *out, int reset) {
     out->mean_ms = l.empty() ? 0.0 : sum / (double)l.size();
     out->points = S->points;
     out->seconds = S->any ? std::chrono::duration<double>(S->t_last - S->t_first).count() : 0.0;
-    out->plans_cached = (int64_t)S->plans.size();
+    out->plans_cached = S->plans_cached.load();
     out->plans_made = S->plans_made;
     out->plans_evicted = S->plans_evicted;
     out->device_bytes = (int64_t)(S->fixed_bytes + S->plan_bytes);
@@ -509,8 +576,15 @@ int nnfft_server_destroy(nnfft_server_t S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
-    for (Slot &sl : S->slots) {
+    for (Slot &sl : S->slots)
         if (sl.st) cudaStreamSynchronize(sl.st);
+    // plans first: they may still name a slot stream
+    for (PlanEntry *e : S->plans) {
+        destroy_idle_plan(e->p);
+        delete e;
+    }
+    S->plans.clear();
+    for (Slot &sl : S->slots) {
         cudaFree(sl.d1);
         cudaFree(sl.d2);
         cudaFree(sl.c1);
@@ -518,10 +592,6 @@ int nnfft_server_destroy(nnfft_server_t S) {
         cudaFree(sl.g);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.st) cudaStreamDestroy(sl.st);
-    }
-    for (PlanEntry *e : S->plans) {
-        nnfft_destroy(e->p);
-        delete e;
     }
     for (auto &kv : S->rules) cudaFree(kv.second.x1);
     for (auto &kv : S->reqs) delete kv.second;

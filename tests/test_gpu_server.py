@@ -84,19 +84,33 @@ def test_results_alone_equal_results_in_the_mix_and_meet_tolerance():
 
 
 def test_budget_forces_eviction_and_results_stay_correct():
-    # room for the slot buffers (about 2.5 MB) and one plan's admission estimate (about
-    # 66 MB for these sizes): every new bucket evicts the previous plan
-    budget = 70 << 20
-    S = B.Server(mem_budget_bytes=budget, slots=1, max_points=1 << 13)
-    specs = [("nnfft", 64, 500, 400, 1e-12, None, True), ("nnfft", 200, 500, 400, 1e-12, None, True),
-             ("nnfft", 700, 500, 400, 1e-12, None, True), ("nnfft", 64, 500, 400, 1e-12, None, True)]
-    for i, spec in enumerate(specs):
-        v, x, f, y = make_inputs(50 + i, spec)
-        S.wait(submit(S, spec, v, x, f, y))
-        assert np.max(np.abs(y - exact(spec, v, x, f))) / np.sum(np.abs(f)) <= 1e-12
+    """Plans for 600k-point requests hold about 70 MB each; the budget (300 MB with about
+    50 MB of slot buffers) admits one such plan next to its admission estimate, so each new
+    bandwidth bucket evicts the previous plan.  Sampled rows against the oracle."""
+    budget = 300 << 20
+    S = B.Server(mem_budget_bytes=budget, slots=1, max_points=1 << 20)
+    M = 600_000
+    for i, N in enumerate([64, 200, 700, 64]):
+        rng = np.random.default_rng(50 + i)
+        v, x = rng.uniform(-0.5, 0.5, M), rng.uniform(-0.5, 0.5, M)
+        f, y = W.draw_complex(rng, M), np.zeros(M, np.complex128)
+        S.wait(S.submit_nnfft(N, v, x, f, y, 1e-12))
+        rows = W.sample_rows(M, 64, i)
+        want = oracle.nnfft_direct(N, v, f, x, rows=rows)
+        assert np.max(np.abs(y[rows] - want)) / np.sum(np.abs(f)) <= 1e-12
     st = S.stats()
     S.close()
     assert st["plans_evicted"] >= 2 and st["device_bytes"] <= budget
+
+
+def test_request_larger_than_the_budget_fails():
+    S = B.Server(mem_budget_bytes=40 << 20, slots=1, max_points=4096)
+    spec = ("nnfft", 64, 100, 100, 1e-12, None, True)
+    v, x, f, y = make_inputs(8, spec)
+    with pytest.raises(B.NNFFTError) as e:
+        S.wait(S.submit_nnfft(64, v, x, f, y, 1e-12))
+    S.close()
+    assert e.value.code == 3                                 # NNFFT_ENOMEM
 
 
 def test_request_errors_do_not_stop_the_loop():
