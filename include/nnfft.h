@@ -199,6 +199,15 @@ int nnfft_exec(nnfft_plan_t p, const void *f_dev, void *y_dev);
 int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev);
 
 /*
+ * nnfft_exec_adjoint: y = A f and z = A^H g for the same nodes in one call, the two
+ * directions running concurrently (the adjoint on the plan's second stream with its own
+ * work buffers, allocated on the first call).  Same results, arguments and errors as
+ * nnfft_exec followed by nnfft_adjoint; ordered on the plan stream like them.
+ */
+int nnfft_exec_adjoint(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
+                       void *z_dev);
+
+/*
  * Host-buffer variants of set_nodes / exec / adjoint.  Same arguments as above
  * but host pointers: the call copies the inputs into plan-owned device
  * staging buffers, runs the transform, copies the result back and waits for

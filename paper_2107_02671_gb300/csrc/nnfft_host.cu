@@ -76,6 +76,13 @@ struct Side {
     bool set = false;
 };
 
+// Work buffers of one transform direction.
+struct Work {
+    void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;   // grids (all instances)
+    void *P = nullptr;   // per-item moments
+    void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
+};
+
 }  // namespace
 
 struct nnfft_plan_s {
@@ -94,9 +101,10 @@ struct nnfft_plan_s {
     FftLaunch<FftPlanDev> fft{};
     FftLaunch<FftDf> fftdf{};
     long long grid_total = 0;    // sum of the instances' N2
-    void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;
-    void *P = nullptr;   // per-item moments
-    void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
+    // work buffers of a transform: [0] for exec / adjoint, [1] (allocated on first use) for
+    // the adjoint when nnfft_exec_adjoint runs both directions concurrently
+    Work work[2];
+    size_t work_bytes[3] = {0, 0, 0};   // grid, moments, cell buffer sizes
     int *status = nullptr;
     int *status_host = nullptr;   // pinned
     // host-API staging (allocated on first use)
@@ -274,6 +282,17 @@ std::vector<int> prefix(const std::vector<int> &cnt, int *total) {
     for (size_t i = 0; i < cnt.size(); ++i) off[i + 1] = off[i] + cnt[i];
     *total = off.back();
     return off;
+}
+
+int alloc_work(nnfft_plan_s *p, Work &W) {
+    int rc;
+    if ((rc = dalloc(p, &W.bufA, p->work_bytes[0], "grid")) ||
+        (rc = dalloc(p, &W.bufB, p->work_bytes[0], "grid")) ||
+        (rc = dalloc(p, &W.bufC, p->work_bytes[0], "grid")) ||
+        (rc = dalloc(p, &W.P, p->work_bytes[1], "moments")) ||
+        (rc = dalloc(p, &W.Q, p->work_bytes[2], "cell windows")))
+        return rc;
+    return NNFFT_OK;
 }
 
 // Per-instance host data gathered while the plan is built.
@@ -610,11 +629,10 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             pmax = std::max(pmax, (size_t)p->side[s].max_items * p->side[s].D);
             qmax = std::max(qmax, (size_t)p->side[s].ncell * p->side[s].D);
         }
-        const size_t G2 = (size_t)gtot;
-        if ((rc = dalloc(p, &p->bufA, G2 * cs, "grid")) || (rc = dalloc(p, &p->bufB, G2 * cs, "grid")) ||
-            (rc = dalloc(p, &p->bufC, G2 * cs, "grid")) || (rc = dalloc(p, &p->P, pmax * cs, "moments")) ||
-            (rc = dalloc(p, &p->Q, qmax * cs, "cell windows")))
-            return rc;
+        p->work_bytes[0] = (size_t)gtot * cs;
+        p->work_bytes[1] = pmax * cs;
+        p->work_bytes[2] = qmax * cs;
+        if ((rc = alloc_work(p, p->work[0]))) return rc;
     }
     return NNFFT_OK;
 }
@@ -720,146 +738,154 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     return NNFFT_OK;
 }
 
-int run_forward_split(nnfft_plan_s *p, const void *f, void *y) {
+int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
     const Side &V = p->side[0], &X = p->side[1];
-    cudaStream_t st = p->stream;
     if (X.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
     const SideDf tv{nullptr, nullptr};
     {
-        StageTimer t(p, 2);
-        NN_CUDA(launch_moments_df(sv, f, p->P, st), "spread moments");
+        StageTimer t(p, 2, st);
+        NN_CUDA(launch_moments_df(sv, f, W.P, st), "spread moments");
     }
     {
-        StageTimer t(p, 12);
-        NN_CUDA(launch_cell_fold_df(sv, tv, p->P, p->Q, st), "cell fold");
+        StageTimer t(p, 12, st);
+        NN_CUDA(launch_cell_fold_df(sv, tv, W.P, W.Q, st), "cell fold");
     }
     {
-        StageTimer t(p, 3);
-        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), p->Q, p->bufA, st),
+        StageTimer t(p, 3, st);
+        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), W.Q, W.bufA, st),
                 "spread convolution");
     }
     {
-        StageTimer t(p, 4);
-        NN_CUDA(launch_fft_df(p->fftdf, p->bufA, p->bufB, p->bufC, -1, st), "fft");
+        StageTimer t(p, 4, st);
+        NN_CUDA(launch_fft_df(p->fftdf, W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
     {
-        StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), p->bufC, p->Q, st),
+        StageTimer t(p, 5, st);
+        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
                 "gather convolution");
     }
     {
-        StageTimer t(p, 6);
-        NN_CUDA(launch_eval_df(sx, p->Q, y, st), "gather evaluation");
+        StageTimer t(p, 6, st);
+        NN_CUDA(launch_eval_df(sx, W.Q, y, st), "gather evaluation");
     }
     return NNFFT_OK;
 }
 
-int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z) {
+int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
     const Side &V = p->side[0], &X = p->side[1];
-    cudaStream_t st = p->stream;
     if (V.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
     const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
     {
-        StageTimer t(p, 7);
-        NN_CUDA(launch_moments_df(sx, g, p->P, st), "adjoint spread moments");
+        StageTimer t(p, 7, st);
+        NN_CUDA(launch_moments_df(sx, g, W.P, st), "adjoint spread moments");
     }
     {
-        StageTimer t(p, 13);
-        NN_CUDA(launch_cell_fold_df(sx, tx, p->P, p->Q, st), "adjoint cell fold");
+        StageTimer t(p, 13, st);
+        NN_CUDA(launch_cell_fold_df(sx, tx, W.P, W.Q, st), "adjoint cell fold");
     }
     {
-        StageTimer t(p, 8);
-        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), p->Q, p->bufA, st),
+        StageTimer t(p, 8, st);
+        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), W.Q, W.bufA, st),
                 "adjoint spread convolution");
     }
     {
-        StageTimer t(p, 9);
-        NN_CUDA(launch_fft_df(p->fftdf, p->bufA, p->bufB, p->bufC, +1, st), "adjoint fft");
+        StageTimer t(p, 9, st);
+        NN_CUDA(launch_fft_df(p->fftdf, W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
     {
-        StageTimer t(p, 10);
-        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), p->bufC, p->Q, st),
+        StageTimer t(p, 10, st);
+        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
                 "adjoint gather convolution");
     }
     {
-        StageTimer t(p, 11);
-        NN_CUDA(launch_eval_df(sv, p->Q, z, st), "adjoint gather evaluation");
+        StageTimer t(p, 11, st);
+        NN_CUDA(launch_eval_df(sv, W.Q, z, st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
 }
 
-template <typename Real> int run_forward(nnfft_plan_s *p, const void *f, void *y) {
+template <typename Real>
+int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
     const Side &V = p->side[0], &X = p->side[1];
-    cudaStream_t st = p->stream;
     if (X.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
     {
-        StageTimer t(p, 2);
-        NN_CUDA(launch_moments<Real>(sv, f, p->P, st), "spread moments");
+        StageTimer t(p, 2, st);
+        NN_CUDA(launch_moments<Real>(sv, f, W.P, st), "spread moments");
     }
     {
-        StageTimer t(p, 12);
-        NN_CUDA(launch_cell_fold<Real>(sv, p->P, p->Q, st), "cell fold");
+        StageTimer t(p, 12, st);
+        NN_CUDA(launch_cell_fold<Real>(sv, W.P, W.Q, st), "cell fold");
     }
     {
-        StageTimer t(p, 3);
-        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 0, true, false), p->Q, p->bufA, st),
+        StageTimer t(p, 3, st);
+        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 0, true, false), W.Q, W.bufA, st),
                 "spread convolution");
     }
     {
-        StageTimer t(p, 4);
-        NN_CUDA(launch_fft<Real>(p->fft, p->bufA, p->bufB, p->bufC, -1, st), "fft");
+        StageTimer t(p, 4, st);
+        NN_CUDA(launch_fft<Real>(p->fft, W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
     {
-        StageTimer t(p, 5);
-        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), p->bufC, p->Q, st),
+        StageTimer t(p, 5, st);
+        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), W.bufC, W.Q, st),
                 "gather convolution");
     }
     {
-        StageTimer t(p, 6);
-        NN_CUDA(launch_eval<Real>(sx, p->Q, y, st), "gather evaluation");
+        StageTimer t(p, 6, st);
+        NN_CUDA(launch_eval<Real>(sx, W.Q, y, st), "gather evaluation");
     }
     return NNFFT_OK;
 }
 
-template <typename Real> int run_adjoint(nnfft_plan_s *p, const void *g, void *z) {
+template <typename Real>
+int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
     const Side &V = p->side[0], &X = p->side[1];
-    cudaStream_t st = p->stream;
     if (V.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
     {
-        StageTimer t(p, 7);
-        NN_CUDA(launch_moments<Real>(sx, g, p->P, st), "adjoint spread moments");
+        StageTimer t(p, 7, st);
+        NN_CUDA(launch_moments<Real>(sx, g, W.P, st), "adjoint spread moments");
     }
     {
-        StageTimer t(p, 13);
-        NN_CUDA(launch_cell_fold<Real>(sx, p->P, p->Q, st), "adjoint cell fold");
+        StageTimer t(p, 13, st);
+        NN_CUDA(launch_cell_fold<Real>(sx, W.P, W.Q, st), "adjoint cell fold");
     }
     {
-        StageTimer t(p, 8);
-        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 1, true, false), p->Q, p->bufA, st),
+        StageTimer t(p, 8, st);
+        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 1, true, false), W.Q, W.bufA, st),
                 "adjoint spread convolution");
     }
     {
-        StageTimer t(p, 9);
-        NN_CUDA(launch_fft<Real>(p->fft, p->bufA, p->bufB, p->bufC, +1, st), "adjoint fft");
+        StageTimer t(p, 9, st);
+        NN_CUDA(launch_fft<Real>(p->fft, W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
     {
-        StageTimer t(p, 10);
-        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), p->bufC, p->Q, st),
+        StageTimer t(p, 10, st);
+        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), W.bufC, W.Q, st),
                 "adjoint gather convolution");
     }
     {
-        StageTimer t(p, 11);
-        NN_CUDA(launch_eval<Real>(sv, p->Q, z, st), "adjoint gather evaluation");
+        StageTimer t(p, 11, st);
+        NN_CUDA(launch_eval<Real>(sv, W.Q, z, st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
+}
+
+int forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
+    if (p->dbl && p->split) return run_forward_split(p, f, y, st, W);
+    return p->dbl ? run_forward<double>(p, f, y, st, W) : run_forward<float>(p, f, y, st, W);
+}
+
+int adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
+    if (p->dbl && p->split) return run_adjoint_split(p, g, z, st, W);
+    return p->dbl ? run_adjoint<double>(p, g, z, st, W) : run_adjoint<float>(p, g, z, st, W);
 }
 
 int collect_status(nnfft_plan_s *p) {
@@ -1038,8 +1064,7 @@ int nnfft_exec(nnfft_plan_t p, const void *f_dev, void *y_dev) {
     if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
     if ((p->info.M1 > 0 && !f_dev) || (p->info.M2 > 0 && !y_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
-    if (p->dbl && p->split) return run_forward_split(p, f_dev, y_dev);
-    return p->dbl ? run_forward<double>(p, f_dev, y_dev) : run_forward<float>(p, f_dev, y_dev);
+    return forward(p, f_dev, y_dev, p->stream, p->work[0]);
 }
 
 int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev) {
@@ -1047,8 +1072,25 @@ int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev) {
     if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
     if ((p->info.M2 > 0 && !g_dev) || (p->info.M1 > 0 && !z_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
-    if (p->dbl && p->split) return run_adjoint_split(p, g_dev, z_dev);
-    return p->dbl ? run_adjoint<double>(p, g_dev, z_dev) : run_adjoint<float>(p, g_dev, z_dev);
+    return adjoint(p, g_dev, z_dev, p->stream, p->work[0]);
+}
+
+int nnfft_exec_adjoint(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
+                       void *z_dev) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
+    if ((p->info.M1 > 0 && (!f_dev || !z_dev)) || (p->info.M2 > 0 && (!y_dev || !g_dev)))
+        return fail(NNFFT_EINVAL, "null data pointer");
+    int rc;
+    if (!p->work[1].P && (rc = alloc_work(p, p->work[1]))) return rc;
+    // fork: the adjoint runs on the auxiliary stream with its own work buffers
+    NN_CUDA(cudaEventRecord(p->ev_fork, p->stream), "fork");
+    NN_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork");
+    const int ra = adjoint(p, g_dev, z_dev, p->aux, p->work[1]);
+    const int rf = forward(p, f_dev, y_dev, p->stream, p->work[0]);
+    NN_CUDA(cudaEventRecord(p->ev_join, p->aux), "join");
+    NN_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "join");
+    return ra ? ra : rf;
 }
 
 int nnfft_set_arith(nnfft_plan_t p, int arith) {

@@ -114,6 +114,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_set_nodes.argtypes = [vp, vp, vp]
         lib.nnfft_exec.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint.argtypes = [vp, vp, vp]
+        lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
         lib.nnfft_set_nodes_host.argtypes = [vp, vp, vp]
         lib.nnfft_exec_host.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint_host.argtypes = [vp, vp, vp]
@@ -259,6 +260,20 @@ class Plan:
         po = _dev_tensor(out, self.cdtype, self.M1, "out")
         _check(self._lib.nnfft_adjoint(self._h, pg, po))
         return out
+
+    def exec_adjoint(self, f, g, y=None, z=None):
+        """(A f, A^H g) for the same nodes, both directions running concurrently."""
+        import torch
+        pf = _dev_tensor(f, self.cdtype, self.M1, "f")
+        pg = _dev_tensor(g, self.cdtype, self.M2, "g")
+        if y is None:
+            y = torch.empty(self.M2, dtype=self.cdtype, device=f.device)
+        if z is None:
+            z = torch.empty(self.M1, dtype=self.cdtype, device=f.device)
+        py = _dev_tensor(y, self.cdtype, self.M2, "y")
+        pz = _dev_tensor(z, self.cdtype, self.M1, "z")
+        _check(self._lib.nnfft_exec_adjoint(self._h, pf, py, pg, pz))
+        return y, z
 
     # host-buffer variants (numpy in, numpy out; copies inside the call)
     def set_nodes_host(self, v=None, x=None):

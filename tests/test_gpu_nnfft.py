@@ -376,3 +376,29 @@ def test_set_arith_requires_new_nodes_and_rejects_fp32():
     assert p32.info["arith"] == B.ARITH_FP32
     with pytest.raises(B.NNFFTError):
         p32.set_arith(B.ARITH_FP64_SPLIT)
+
+
+@pytest.mark.parametrize("dtype,m", [(torch.complex128, 8), (torch.complex64, 4)])
+def test_exec_adjoint_concurrent_equals_separate(dtype, m):
+    """nnfft_exec_adjoint (both directions on two streams) gives bit for bit the results of
+    nnfft_exec and nnfft_adjoint, for a single plan and a batch."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 300, 20000, 15000
+    v, x, f = W.nnfft_inputs(M1, M2, 31, dtype=npd)
+    g = W.adjoint_inputs(M2, 31, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    y1 = plan.exec(dev(f, dtype)).cpu().numpy()
+    z1 = plan.adjoint(dev(g, dtype)).cpu().numpy()
+    y2, z2 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+    plan.sync()
+    assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
+    Nb, M1b, M2b = np.array([64, 500, 33]), np.array([1000, 3000, 10]), np.array([2000, 5, 700])
+    vb, xb, fb = W.batch_inputs(M1b, M2b, 32, dtype=npd)
+    gb = W.draw_complex(np.random.default_rng(3), int(M2b.sum()), npd)
+    P = B.BatchPlan(Nb, M1b, M2b, 2.0, 2.0, m, dtype=dtype)
+    P.set_nodes(dev(vb), dev(xb))
+    y1, z1 = P.exec(dev(fb, dtype)).cpu().numpy(), P.adjoint(dev(gb, dtype)).cpu().numpy()
+    y2, z2 = P.exec_adjoint(dev(fb, dtype), dev(gb, dtype))
+    P.sync()
+    assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
