@@ -167,6 +167,30 @@ int nnfft_batch_info(nnfft_plan_t p, int64_t i, nnfft_info *out);
 int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
 
 /*
+ * Autotuning (the paper has no counterpart).  nnfft_autotune times the plan's kernel
+ * variants on its current nodes (nnfft_set_nodes first) with the caller's buffers, `reps`
+ * runs of nnfft_exec_adjoint per configuration (CUDA events on the plan stream), and keeps
+ * the fastest: threads per work item of the split-precision moments kernel on each side
+ * (32: one warp per item, 16: two items per warp) and the FFT's packing of short columns
+ * into blocks (variant 0 by the plan-size rule, variant 1 the other extreme).  y and z
+ * receive the transforms.  Synchronous.  A different moments variant sums each cell's
+ * points in another order, so later results may change in the last bits.
+ */
+typedef struct {
+    int moments_lanes_v, moments_lanes_x;   /* 32 or 16 */
+    int fft_variant;                        /* 0 or 1 */
+    int tuned;                              /* 1 after nnfft_autotune */
+    double default_ms, best_ms;             /* per exec_adjoint: default and chosen config */
+} nnfft_tuning;
+int nnfft_autotune(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
+                   void *z_dev, int reps);
+int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
+/* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
+ * moments_lanes_v / _x in {16, 32}, fft_variant in {0, 1}; the other fields are ignored.
+ * EINVAL otherwise.  Takes effect for the work queued next. */
+int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t);
+
+/*
  * nnfft_set_arith: choose NNFFT_ARITH_FP64 or NNFFT_ARITH_FP64_SPLIT for a complex128 plan
  * (EINVAL if unavailable).  Changing the mode discards the plan's node preprocessing:
  * call nnfft_set_nodes again before the next exec/adjoint.

@@ -51,13 +51,16 @@ __device__ __forceinline__ void rs_step_df(df (&v)[32], int lane) {
 }
 
 // ---------------------------------------------------------------------------------
-// Cell moments, split precision.  One warp per work item, lanes stride over the
-// item's points, reduce-scatter; P4[item*D + d] = moment d as (re.h, re.l, im.h, im.l).
-// ys2 holds each sorted local coordinate y as a float pair (hi, lo).
+// Cell moments, split precision, one warp per work item: lanes stride over the item's
+// points (up to 8 each, all loads issued first), then a 32-lane reduce-scatter of the 2D
+// double-float moments.  Fewer serial points per lane than the half-warp form below
+// (shorter accumulation chains), more exchange work per point; which is faster depends on
+// the cell sizes and occupancy, so the plan's autotuner picks.
+// P4[item*D + d] = moment d as (re.h, re.l, im.h, im.l).
 // ---------------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(256)
-k_moments_df(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
+k_moments_df_warp(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
              float4 *__restrict__ P4) {
     constexpr int B = D / 2;
     constexpr int F = D - B;
@@ -137,6 +140,128 @@ k_moments_df(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__r
     float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
     if (lane < D) P2[2 * lane] = make_float2(vv[0].h, vv[0].l);
     else if (lane < 2 * D) P2[2 * (lane - D) + 1] = make_float2(vv[0].h, vv[0].l);
+}
+
+// ---------------------------------------------------------------------------------
+// Cell moments, split precision.  Half a warp (16 lanes) per work item, lanes stride over
+// the item's points (up to 16 each, loaded 8 at a time), then a reduce-scatter over the
+// 16 lanes.  The 2D moments sit in 16 double-float slots (re of degree d < B at j = d, im
+// at j = 8 + d) and 16 FP32 slots (re of degree B + d at j = d, im at 8 + d); each
+// exchange step pairs slots that differ in one bit of j, so double-float meets
+// double-float and FP32 meets FP32, and after four steps lane s of the half holds slot
+// j = s of each kind.  P4[item*D + d] = moment d as (re.h, re.l, im.h, im.l).
+// ys2 holds each sorted local coordinate y as a float pair (hi, lo).
+// ---------------------------------------------------------------------------------
+template <int O>
+__device__ __forceinline__ void rs_step_mixed(df (&vd)[16], float (&vf)[16], int sub) {
+    const bool up = (sub & O) != 0;
+#pragma unroll
+    for (int i = 0; i < O; ++i) {
+        const df send = up ? vd[i] : vd[O + i];
+        const df keep = up ? vd[O + i] : vd[i];
+        df other;
+        other.h = __shfl_xor_sync(0xffffffffu, send.h, O);
+        other.l = __shfl_xor_sync(0xffffffffu, send.l, O);
+        vd[i] = add(keep, other);
+        const float fs = up ? vf[i] : vf[O + i];
+        const float fk = up ? vf[O + i] : vf[i];
+        vf[i] = fk + __shfl_xor_sync(0xffffffffu, fs, O);
+    }
+}
+
+constexpr int MOM_LANES = 16;                       // lanes per work item
+constexpr int MOM_CHUNK = 8;                        // points per lane loaded at a time
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_moments_df_half(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
+                  float4 *__restrict__ P4) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    static_assert(B <= 8 && F <= 8, "the slot layout holds at most 8 degrees of each kind");
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = gt / MOM_LANES;
+    const int sub = threadIdx.x & (MOM_LANES - 1);
+    const bool live = item < *S.nitems;             // both halves of a warp stay for the shuffles
+    int pb = 0, pe = 0;
+    if (live) {
+        pb = S.item_pb[item];
+        pe = S.item_pe[item];
+    }
+    df ar[B], ai[B];
+    float br[F], bi[F];
+#pragma unroll
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
+    for (int c0 = pb; c0 < pe; c0 += MOM_LANES * MOM_CHUNK) {
+        float2 yv[MOM_CHUNK];
+        int jv[MOM_CHUNK];
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) {
+            const int p = c0 + sub + MOM_LANES * k;
+            yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+        double2 vv2[MOM_CHUNK];
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) vv2[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) {
+            if (jv[k] < 0) continue;
+            const float2 yy = yv[k];
+            const double2 v = vv2[k];
+            const df fr = split_double(v.x), fi = split_double(v.y);
+            const df y = mk(yy.x, yy.y);
+            const df y2 = mk(2.f * yy.x, 2.f * yy.y);
+            acc(ar[0], fr);
+            acc(ai[0], fi);
+            acc(ar[1], mul_u(fr, y));
+            acc(ai[1], mul_u(fi, y));
+            df t0 = mk(1.f), t1 = y;
+#pragma unroll
+            for (int d = 2; d < B; ++d) {
+                const df t = df_rec(y2, t1, t0);
+                acc(ar[d], mul_u(fr, t));
+                acc(ai[d], mul_u(fi, t));
+                t0 = t1;
+                t1 = t;
+            }
+            float g0 = t0.h, g1 = t1.h;
+            const float yf2 = y2.h;
+#pragma unroll
+            for (int d = 0; d < F; ++d) {
+                const float t = fmaf(yf2, g1, -g0);
+                br[d] = fmaf(fr.h, t, br[d]);
+                bi[d] = fmaf(fi.h, t, bi[d]);
+                g0 = g1;
+                g1 = t;
+            }
+        }
+    }
+    df vd[16];
+    float vf[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
+#pragma unroll
+    for (int d = 0; d < B; ++d) {
+        vd[d] = norm(ar[d]);
+        vd[8 + d] = norm(ai[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        vf[d] = br[d];
+        vf[8 + d] = bi[d];
+    }
+    rs_step_mixed<8>(vd, vf, sub);
+    rs_step_mixed<4>(vd, vf, sub);
+    rs_step_mixed<2>(vd, vf, sub);
+    rs_step_mixed<1>(vd, vf, sub);
+    if (!live) return;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
+    const int j = sub & 7, part = sub >> 3;          // part 0: real, 1: imaginary
+    if (j < B) P2[2 * j + part] = make_float2(vd[0].h, vd[0].l);
+    if (j < F) P2[2 * (B + j) + part] = make_float2(vf[0], 0.f);
 }
 
 // ---------------------------------------------------------------------------------
@@ -228,12 +353,19 @@ bool df_supported_degree(int D) { return D == 8 || D == 10 || D == 12 || D == 14
         default: return cudaErrorInvalidValue;                  \
     }
 
-cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4, cudaStream_t s) {
+cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4, int lanes,
+                              cudaStream_t s) {
     if (S.max_items <= 0) return cudaSuccess;
-    const int blocks = cdiv((long long)S.max_items * 32, 256);
-    NNFFT_DISPATCH_DF(S.D, (k_moments_df<DD><<<blocks, 256, 0, s>>>(
-                               S, reinterpret_cast<const float2 *>(S.ys),
-                               static_cast<const double2 *>(vals), static_cast<float4 *>(P4))));
+    const float2 *y2 = reinterpret_cast<const float2 *>(S.ys);
+    const double2 *v = static_cast<const double2 *>(vals);
+    float4 *o = static_cast<float4 *>(P4);
+    if (lanes == MOM_LANES) {
+        const int blocks = cdiv((long long)S.max_items * MOM_LANES, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_half<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+    } else {
+        const int blocks = cdiv((long long)S.max_items * 32, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+    }
     count_launches(1);
     return cudaGetLastError();
 }

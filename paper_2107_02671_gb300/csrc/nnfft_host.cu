@@ -98,8 +98,12 @@ struct nnfft_plan_s {
     bool split_ok = false;       // the window fits allow them (see kern_spread_df.cu)
     Side side[2];   // 0: v (frequency) side, 1: x (spatial) side
     // FFT of every instance (four-step tables), all-real and double-float forms
-    FftLaunch<FftPlanDev> fft{};
-    FftLaunch<FftDf> fftdf{};
+    FftLaunch<FftPlanDev> fft[2]{};   // two column packings (see build_plan)
+    FftLaunch<FftDf> fftdf[2]{};
+    // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
+    int mom_lanes[2] = {32, 32};
+    int fft_variant = 0;
+    nnfft_tuning tuning{};
     long long grid_total = 0;    // sum of the instances' N2
     // work buffers of a transform: [0] for exec / adjoint, [1] (allocated on first use) for
     // the adjoint when nnfft_exec_adjoint runs both directions concurrently
@@ -547,16 +551,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             return off;
         };
         std::vector<FftPlanDev> F((size_t)count);
-        std::vector<FftDf> G((size_t)count);
-        std::vector<int> c1((size_t)count), c2((size_t)count);
         std::vector<size_t> o1((size_t)count), o2((size_t)count), oN((size_t)count);
-        int sm1 = 0, sm2 = 0;
-        // Short columns share a block when the plan's grids are large enough to fill the
-        // GPU anyway: about 4 blocks per SM of FFT_TILE elements each.
-        auto cols_for = [&](int n) {
-            const long long c = gtot / (4LL * 152 * n);
-            return (int)std::max(1LL, std::min(c, (long long)std::max(1, FFT_TILE / n)));
-        };
         for (int64_t i = 0; i < count; ++i) {
             const nnfft_info &I = p->inst_info[(size_t)i];
             FftPlanDev &f = F[(size_t)i];
@@ -571,12 +566,6 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             o1[(size_t)i] = twid_of(f.n1);
             o2[(size_t)i] = twid_of(f.n2);
             oN[(size_t)i] = twid_of(f.N2);
-            f.cols1 = cols_for(f.n1);
-            f.cols2 = cols_for(f.n2);
-            c1[(size_t)i] = (f.n2 + f.cols1 - 1) / f.cols1;    // pass 1: columns of length n1
-            c2[(size_t)i] = (f.n1 + f.cols2 - 1) / f.cols2;    // pass 2: rows of length n2
-            sm1 = std::max(sm1, (2 * f.cols1 + 1) * f.n1);
-            sm2 = std::max(sm2, (2 * f.cols2 + 1) * f.n2);
         }
         void *tw_real = nullptr, *tw_df = nullptr;
         if ((rc = upload_real(p, &tw_real, tw, "twiddles"))) return rc;
@@ -587,38 +576,66 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             f.tw1 = static_cast<const char *>(tw_real) + cs * o1[(size_t)i];
             f.tw2 = static_cast<const char *>(tw_real) + cs * o2[(size_t)i];
             f.twN = static_cast<const char *>(tw_real) + cs * oN[(size_t)i];
-            FftDf &g = G[(size_t)i];
-            memset(&g, 0, sizeof(g));
-            g.N2 = f.N2;
-            g.n1 = f.n1;
-            g.n2 = f.n2;
-            g.nr1 = f.nr1;
-            g.nr2 = f.nr2;
-            for (int k = 0; k < FFT_MAX_STAGES; ++k) {
-                g.r1[k] = f.r1[k];
-                g.r2[k] = f.r2[k];
-            }
-            g.grid_base = f.grid_base;
-            g.cols1 = f.cols1;
-            g.cols2 = f.cols2;
-            if (tw_df) {
-                g.tw1 = static_cast<const float4 *>(tw_df) + o1[(size_t)i];
-                g.tw2 = static_cast<const float4 *>(tw_df) + o2[(size_t)i];
-                g.twN = static_cast<const float4 *>(tw_df) + oN[(size_t)i];
-            }
         }
-        int n1tot = 0, n2tot = 0;
-        int *b1 = nullptr, *b2 = nullptr;
-        FftPlanDev *fd = nullptr;
-        if ((rc = upload_vec(p, &b1, prefix(c1, &n1tot), "FFT block map")) ||
-            (rc = upload_vec(p, &b2, prefix(c2, &n2tot), "FFT block map")) ||
-            (rc = upload_vec(p, &fd, F, "FFT tables")))
-            return rc;
-        p->fft = FftLaunch<FftPlanDev>{fd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
-        if (p->split_ok) {
-            FftDf *gd = nullptr;
-            if ((rc = upload_vec(p, &gd, G, "FFT tables (df)"))) return rc;
-            p->fftdf = FftLaunch<FftDf>{gd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
+        // Two packings of short columns into blocks: variant 0 by rule (packed when the
+        // plan's grids fill the GPU anyway, about 4 blocks of FFT_TILE elements per SM),
+        // variant 1 the other extreme (one column per block, or as many as fit FFT_TILE);
+        // the autotuner may switch.
+        auto rule = [&](int n) {
+            const long long c = gtot / (4LL * 152 * n);
+            return (int)std::max(1LL, std::min(c, (long long)std::max(1, FFT_TILE / n)));
+        };
+        bool rule_packs = false;
+        for (const FftPlanDev &f : F) rule_packs = rule_packs || rule(f.n1) > 1 || rule(f.n2) > 1;
+        for (int variant = 0; variant < 2; ++variant) {
+            std::vector<int> c1((size_t)count), c2((size_t)count);
+            std::vector<FftDf> G((size_t)count);
+            int sm1 = 0, sm2 = 0;
+            for (int64_t i = 0; i < count; ++i) {
+                FftPlanDev &f = F[(size_t)i];
+                auto cols = [&](int n) {
+                    if (variant == 0) return rule(n);
+                    return rule_packs ? 1 : std::max(1, FFT_TILE / n);
+                };
+                f.cols1 = cols(f.n1);
+                f.cols2 = cols(f.n2);
+                c1[(size_t)i] = (f.n2 + f.cols1 - 1) / f.cols1;    // pass 1: columns of length n1
+                c2[(size_t)i] = (f.n1 + f.cols2 - 1) / f.cols2;    // pass 2: rows of length n2
+                sm1 = std::max(sm1, (2 * f.cols1 + 1) * f.n1);
+                sm2 = std::max(sm2, (2 * f.cols2 + 1) * f.n2);
+                FftDf &g = G[(size_t)i];
+                memset(&g, 0, sizeof(g));
+                g.N2 = f.N2;
+                g.n1 = f.n1;
+                g.n2 = f.n2;
+                g.nr1 = f.nr1;
+                g.nr2 = f.nr2;
+                for (int k = 0; k < FFT_MAX_STAGES; ++k) {
+                    g.r1[k] = f.r1[k];
+                    g.r2[k] = f.r2[k];
+                }
+                g.grid_base = f.grid_base;
+                g.cols1 = f.cols1;
+                g.cols2 = f.cols2;
+                if (tw_df) {
+                    g.tw1 = static_cast<const float4 *>(tw_df) + o1[(size_t)i];
+                    g.tw2 = static_cast<const float4 *>(tw_df) + o2[(size_t)i];
+                    g.twN = static_cast<const float4 *>(tw_df) + oN[(size_t)i];
+                }
+            }
+            int n1tot = 0, n2tot = 0;
+            int *b1 = nullptr, *b2 = nullptr;
+            FftPlanDev *fd = nullptr;
+            if ((rc = upload_vec(p, &b1, prefix(c1, &n1tot), "FFT block map")) ||
+                (rc = upload_vec(p, &b2, prefix(c2, &n2tot), "FFT block map")) ||
+                (rc = upload_vec(p, &fd, F, "FFT tables")))
+                return rc;
+            p->fft[variant] = FftLaunch<FftPlanDev>{fd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
+            if (p->split_ok) {
+                FftDf *gd = nullptr;
+                if ((rc = upload_vec(p, &gd, G, "FFT tables (df)"))) return rc;
+                p->fftdf[variant] = FftLaunch<FftDf>{gd, b1, b2, (int)count, n1tot, n2tot, sm1, sm2};
+            }
         }
     }
     // work buffers
@@ -746,7 +763,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     const SideDf tv{nullptr, nullptr};
     {
         StageTimer t(p, 2, st);
-        NN_CUDA(launch_moments_df(sv, f, W.P, st), "spread moments");
+        NN_CUDA(launch_moments_df(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
     }
     {
         StageTimer t(p, 12, st);
@@ -759,7 +776,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     }
     {
         StageTimer t(p, 4, st);
-        NN_CUDA(launch_fft_df(p->fftdf, W.bufA, W.bufB, W.bufC, -1, st), "fft");
+        NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
     {
         StageTimer t(p, 5, st);
@@ -781,7 +798,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
     {
         StageTimer t(p, 7, st);
-        NN_CUDA(launch_moments_df(sx, g, W.P, st), "adjoint spread moments");
+        NN_CUDA(launch_moments_df(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
     }
     {
         StageTimer t(p, 13, st);
@@ -794,7 +811,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     }
     {
         StageTimer t(p, 9, st);
-        NN_CUDA(launch_fft_df(p->fftdf, W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+        NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
     {
         StageTimer t(p, 10, st);
@@ -829,7 +846,7 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
     }
     {
         StageTimer t(p, 4, st);
-        NN_CUDA(launch_fft<Real>(p->fft, W.bufA, W.bufB, W.bufC, -1, st), "fft");
+        NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
     {
         StageTimer t(p, 5, st);
@@ -864,7 +881,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     }
     {
         StageTimer t(p, 9, st);
-        NN_CUDA(launch_fft<Real>(p->fft, W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+        NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
     {
         StageTimer t(p, 10, st);
@@ -1091,6 +1108,79 @@ int nnfft_exec_adjoint(nnfft_plan_t p, const void *f_dev, void *y_dev, const voi
     NN_CUDA(cudaEventRecord(p->ev_join, p->aux), "join");
     NN_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "join");
     return ra ? ra : rf;
+}
+
+int nnfft_autotune(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
+                   void *z_dev, int reps) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
+    if (reps < 1) reps = 1;
+    const bool lanes_matter = p->dbl && p->split;
+    std::vector<int> lanes = lanes_matter ? std::vector<int>{32, 16} : std::vector<int>{32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NN_CUDA(cudaEventCreate(&e0), "event");
+    NN_CUDA(cudaEventCreate(&e1), "event");
+    double best = 1e300, dflt = 0;
+    int best_v = 32, best_x = 32, best_f = 0, rc = NNFFT_OK;
+    const bool timing = p->timing;
+    p->timing = false;
+    for (int fv = 0; fv < 2 && !rc; ++fv)
+        for (size_t iv = 0; iv < lanes.size() && !rc; ++iv)
+            for (size_t ix = 0; ix < lanes.size() && !rc; ++ix) {
+                const int lv = lanes[iv], lx = lanes[ix];
+                p->fft_variant = fv;
+                p->mom_lanes[0] = lv;
+                p->mom_lanes[1] = lx;
+                if ((rc = nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev))) break;   // warm-up
+                cudaEventRecord(e0, p->stream);
+                for (int r = 0; r < reps && !rc; ++r) rc = nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev);
+                cudaEventRecord(e1, p->stream);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = cuda_fail(cudaGetLastError(), "autotune timing");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / reps;
+                if (fv == 0 && lv == 32 && lx == 32) dflt = per;
+                if (per < best) {
+                    best = per;
+                    best_v = lv;
+                    best_x = lx;
+                    best_f = fv;
+                }
+            }
+    p->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->fft_variant = best_f;
+    p->mom_lanes[0] = best_v;
+    p->mom_lanes[1] = best_x;
+    if (rc) return rc;
+    p->tuning = nnfft_tuning{best_v, best_x, best_f, 1, dflt, best};
+    return collect_status(p);
+}
+
+int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
+    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
+    *out = p->tuning;
+    out->moments_lanes_v = p->mom_lanes[0];
+    out->moments_lanes_x = p->mom_lanes[1];
+    out->fft_variant = p->fft_variant;
+    return NNFFT_OK;
+}
+
+int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
+    if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
+    auto ok_lanes = [](int l) { return l == 16 || l == 32; };
+    if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
+        (t->fft_variant != 0 && t->fft_variant != 1))
+        return fail(NNFFT_EINVAL, "invalid tuning values");
+    p->mom_lanes[0] = t->moments_lanes_v;
+    p->mom_lanes[1] = t->moments_lanes_x;
+    p->fft_variant = t->fft_variant;
+    return NNFFT_OK;
 }
 
 int nnfft_set_arith(nnfft_plan_t p, int arith) {

@@ -48,6 +48,15 @@ class ServerReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("moments_lanes_v", ctypes.c_int), ("moments_lanes_x", ctypes.c_int),
+                ("fft_variant", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 16), ("count", ctypes.c_int64 * 16)]
 
@@ -115,6 +124,9 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_exec.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint.argtypes = [vp, vp, vp]
         lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
+        lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, cint]
+        lib.nnfft_get_tuning.argtypes = [vp, P(Tuning)]
+        lib.nnfft_set_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_nodes_host.argtypes = [vp, vp, vp]
         lib.nnfft_exec_host.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint_host.argtypes = [vp, vp, vp]
@@ -274,6 +286,30 @@ class Plan:
         pz = _dev_tensor(z, self.cdtype, self.M1, "z")
         _check(self._lib.nnfft_exec_adjoint(self._h, pf, py, pg, pz))
         return y, z
+
+    def autotune(self, f, g, y=None, z=None, reps=3) -> dict:
+        """Time the kernel variants on the current nodes and keep the fastest."""
+        import torch
+        if y is None:
+            y = torch.empty(self.M2, dtype=self.cdtype, device=f.device)
+        if z is None:
+            z = torch.empty(self.M1, dtype=self.cdtype, device=f.device)
+        _check(self._lib.nnfft_autotune(self._h, _dev_tensor(f, self.cdtype, self.M1, "f"),
+                                        _dev_tensor(y, self.cdtype, self.M2, "y"),
+                                        _dev_tensor(g, self.cdtype, self.M2, "g"),
+                                        _dev_tensor(z, self.cdtype, self.M1, "z"), int(reps)))
+        return self.tuning()
+
+    def set_tuning(self, moments_lanes_v=32, moments_lanes_x=32, fft_variant=0):
+        """Apply a kernel-variant configuration (see autotune)."""
+        t = Tuning(int(moments_lanes_v), int(moments_lanes_x), int(fft_variant), 0, 0.0, 0.0)
+        _check(self._lib.nnfft_set_tuning(self._h, ctypes.byref(t)))
+        return self
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(self._lib.nnfft_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
 
     # host-buffer variants (numpy in, numpy out; copies inside the call)
     def set_nodes_host(self, v=None, x=None):

@@ -402,3 +402,50 @@ def test_exec_adjoint_concurrent_equals_separate(dtype, m):
     y2, z2 = P.exec_adjoint(dev(fb, dtype), dev(gb, dtype))
     P.sync()
     assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
+    """nnfft_autotune picks among the kernel variants; every variant is a correct transform
+    (within tolerance of the direct sum, deterministic), and the choice is reported."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 500, 30000, 20000
+    v, x, f = W.nnfft_inputs(M1, M2, 41, dtype=npd)
+    g = W.adjoint_inputs(M2, 41, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
+    assert t["tuned"] == 1 and t["moments_lanes_v"] in (16, 32) and t["moments_lanes_x"] in (16, 32)
+    assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= t["default_ms"]
+    y1, z1 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+    y2, z2 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+    plan.sync()
+    y1, z1 = y1.cpu().numpy(), z1.cpu().numpy()
+    assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
+    rows = W.sample_rows(M2, 64, 3)
+    want = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
+    assert np.max(np.abs(y1[rows] - want)) / np.sum(np.abs(f)) <= tol
+    rows = W.sample_rows(M1, 64, 4)
+    want = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows)
+    assert np.max(np.abs(z1[rows] - want)) / np.sum(np.abs(g)) <= tol
+
+
+def test_every_moments_and_fft_variant_is_correct():
+    """Both split-precision moments kernels (16 and 32 lanes per item) and both FFT
+    packings give the transform within 1e-12, forward and adjoint."""
+    N, M1, M2 = 700, 40000, 30000
+    v, x, f = W.nnfft_inputs(M1, M2, 43)
+    g = W.adjoint_inputs(M2, 43)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, 8, 8)
+    plan.set_nodes(dev(v), dev(x))
+    rows2, rows1 = W.sample_rows(M2, 48, 5), W.sample_rows(M1, 48, 6)
+    want_y = oracle.nnfft_direct(N, v, f, x, rows=rows2)
+    want_z = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows1)
+    for lanes in (16, 32):
+        for fv in (0, 1):
+            plan.set_tuning(lanes, lanes, fv)
+            y, z = plan.exec_adjoint(dev(f), dev(g))
+            plan.sync()
+            y, z = y.cpu().numpy(), z.cpu().numpy()
+            assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= 1e-12, (lanes, fv)
+            assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= 1e-12, (lanes, fv)
