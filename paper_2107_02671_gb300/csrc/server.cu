@@ -57,9 +57,16 @@ struct PlanEntry {
     nnfft_plan_t p = nullptr;
     int64_t Ncap = 0, cap1 = 0, cap2 = 0;
     int dtype = 0, m = 0;
-    size_t bytes = 0;
+    size_t bytes = 0;          // device bytes (the admission estimate while building)
     bool busy = false;
+    bool ready = false;        // false while the builder thread makes the plan
     uint64_t last = 0;
+};
+
+struct BuildDone {             // a plan the builder thread finished (or failed to make)
+    PlanEntry *e;
+    nnfft_plan_t p;
+    int rc;
 };
 
 struct Rule {                       // quadrature rule of a sinc bandwidth bucket (device)
@@ -99,8 +106,16 @@ struct nnfft_server_s {
     std::vector<Slot> slots;
     std::vector<PlanEntry *> plans;
     std::map<std::tuple<int64_t, int, int>, Rule> rules;   // (Ncap, rule, dtype)
-    std::thread worker;
+    std::thread worker, builder;
     bool stop = false;
+    // plan builds run on the builder thread so that admission never waits for one
+    std::mutex mu_build;
+    std::condition_variable cv_build;
+    std::deque<PlanEntry *> build_jobs;
+    std::vector<BuildDone> built;
+    bool stop_build = false;
+    int builds_in_flight = 0;                 // worker only
+    std::map<std::tuple<int64_t, int, int>, int> build_error;   // (Ncap, dtype, m) -> status
     int64_t next_id = 1;
     uint64_t tick = 0;
     int64_t budget = 0, max_points = 0;
@@ -136,23 +151,36 @@ void destroy_idle_plan(nnfft_plan_t p) {
     nnfft_destroy(p);
 }
 
-// An idle cached plan for (Ncap, dtype, m) with capacities >= (M1, M2), or a new one
-// within the budget (evicting idle plans, least recently used first).  nullptr with
-// *err == OK: not now (plans in use will free up); *err != OK: the request fails.
+// An idle cached plan for (Ncap, dtype, m) with capacities >= (M1, M2).  Without one, a
+// build of a new plan with capacities (c1, c2) is queued for the builder thread (one at a
+// time per key; idle plans are evicted least recently used first to fit the budget) and
+// nullptr is returned with *err == OK: not now.  *err != OK: the request fails.
 PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64_t M1,
                         int64_t M2, int64_t c1, int64_t c2, int *err) {
     *err = NNFFT_OK;
     PlanEntry *best = nullptr;
-    for (PlanEntry *e : S->plans)
-        if (!e->busy && e->Ncap == Ncap && e->dtype == dtype && e->m == m && e->cap1 >= M1 &&
-            e->cap2 >= M2 && (!best || e->cap1 + e->cap2 < best->cap1 + best->cap2))
+    bool building = false;
+    for (PlanEntry *e : S->plans) {
+        if (e->Ncap != Ncap || e->dtype != dtype || e->m != m) continue;
+        if (!e->ready) {
+            building = building || (e->cap1 >= M1 && e->cap2 >= M2);
+            continue;
+        }
+        if (!e->busy && e->cap1 >= M1 && e->cap2 >= M2 &&
+            (!best || e->cap1 + e->cap2 < best->cap1 + best->cap2))
             best = e;
+    }
     if (best) {
         best->busy = true;
         best->last = ++S->tick;
         return best;
     }
-    // a new plan gets the capacities (c1, c2) >= (M1, M2) the caller asks for
+    if (building) return nullptr;               // one build per key at a time
+    auto berr = S->build_error.find(std::make_tuple(Ncap, dtype, m));
+    if (berr != S->build_error.end()) {
+        *err = berr->second;
+        return nullptr;
+    }
     // rough size for admission: sort and coordinate buffers, moments, cells, grids
     const size_t est = (size_t)(c1 + c2) * 64 + (size_t)Ncap * 2048 + (64u << 20);
     auto over = [&](size_t extra) {
@@ -161,15 +189,15 @@ PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64
     while (over(est)) {
         PlanEntry *victim = nullptr;
         for (PlanEntry *e : S->plans)
-            if (!e->busy && (!victim || e->last < victim->last)) victim = e;
+            if (e->ready && !e->busy && (!victim || e->last < victim->last)) victim = e;
         if (!victim) {
-            bool any_busy = false;
+            bool any_busy = S->builds_in_flight > 0;
             for (PlanEntry *e : S->plans) any_busy = any_busy || e->busy;
             if (!any_busy) {                    // nothing will ever free up: cannot serve
                 *err = sfail(NNFFT_ENOMEM, "request does not fit the server's device budget");
                 return nullptr;
             }
-            return nullptr;                     // everything in use: wait for a slot
+            return nullptr;                     // everything in use: wait
         }
         S->plan_bytes -= victim->bytes;
         destroy_idle_plan(victim->p);
@@ -179,25 +207,70 @@ PlanEntry *acquire_plan(nnfft_server_s *S, int64_t Ncap, int dtype, int m, int64
         --S->plans_cached;
     }
     PlanEntry *e = new PlanEntry();
-    int rc = nnfft_plan(&e->p, Ncap, c1, c2, 2.0, 2.0, m, m, (nnfft_dtype)dtype, nullptr);
-    if (rc) {
-        delete e;
-        *err = rc;
-        return nullptr;
-    }
     e->Ncap = Ncap;
     e->cap1 = c1;
     e->cap2 = c2;
     e->dtype = dtype;
     e->m = m;
-    e->bytes = plan_bytes(e->p);
+    e->bytes = est;                             // reserved until the plan exists
     e->busy = true;
+    e->ready = false;
     e->last = ++S->tick;
-    S->plan_bytes += e->bytes;
+    S->plan_bytes += est;
     S->plans.push_back(e);
-    ++S->plans_made;
-    ++S->plans_cached;
-    return e;
+    ++S->builds_in_flight;
+    {
+        std::lock_guard<std::mutex> g(S->mu_build);
+        S->build_jobs.push_back(e);
+    }
+    S->cv_build.notify_one();
+    return nullptr;
+}
+
+// Take in the plans the builder thread finished (worker thread).
+void integrate_builds(nnfft_server_s *S) {
+    std::vector<BuildDone> done;
+    {
+        std::lock_guard<std::mutex> g(S->mu_build);
+        done.swap(S->built);
+    }
+    for (BuildDone &d : done) {
+        PlanEntry *e = d.e;
+        --S->builds_in_flight;
+        S->plan_bytes -= e->bytes;
+        if (d.rc) {
+            S->build_error[std::make_tuple(e->Ncap, e->dtype, e->m)] = d.rc;
+            S->plans.erase(std::find(S->plans.begin(), S->plans.end(), e));
+            delete e;
+            continue;
+        }
+        e->p = d.p;
+        e->bytes = plan_bytes(d.p);
+        S->plan_bytes += e->bytes;
+        e->ready = true;
+        e->busy = false;
+        ++S->plans_made;
+        ++S->plans_cached;
+    }
+}
+
+void builder_loop(nnfft_server_s *S) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        PlanEntry *e = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu_build);
+            S->cv_build.wait(lk, [&] { return S->stop_build || !S->build_jobs.empty(); });
+            if (S->build_jobs.empty()) return;
+            e = S->build_jobs.front();
+            S->build_jobs.pop_front();
+        }
+        nnfft_plan_t p = nullptr;
+        const int rc = nnfft_plan(&p, e->Ncap, e->cap1, e->cap2, 2.0, 2.0, e->m, e->m,
+                                  (nnfft_dtype)e->dtype, nullptr);
+        std::lock_guard<std::mutex> g(S->mu_build);
+        S->built.push_back(BuildDone{e, rc ? nullptr : p, rc});
+    }
 }
 
 void release_plan(PlanEntry *&e) {
@@ -350,7 +423,9 @@ Admit admit(nnfft_server_s *S, Slot &sl, Req *q, int *status) {
                              S->max_points, &err);
     }
     if (err == NNFFT_OK && !sl.pa) {
-        // waiting helps only if another slot will release plans or memory
+        // waiting helps only if a plan is being built or another slot will release
+        // plans or memory
+        if (S->builds_in_flight > 0) return WAIT;
         for (const Slot &o : S->slots)
             if (&o != &sl && o.req) return WAIT;
         err = sfail(NNFFT_ENOMEM, "request does not fit the server's device budget");
@@ -370,10 +445,14 @@ Admit admit(nnfft_server_s *S, Slot &sl, Req *q, int *status) {
     return FAILED;
 }
 
+// Requests the worker looks at past a waiting one (whose plan is being built).
+constexpr size_t LOOKAHEAD = 64;
+
 void worker_loop(nnfft_server_s *S) {
     cudaSetDevice(S->device);
     for (;;) {
-        bool busy = false;
+        integrate_builds(S);
+        bool busy = S->builds_in_flight > 0;
         for (Slot &sl : S->slots) {                 // retire finished requests
             if (!sl.req) continue;
             const cudaError_t e = cudaEventQuery(sl.ev);
@@ -390,34 +469,35 @@ void worker_loop(nnfft_server_s *S) {
             }
             S->cv_done.notify_all();
         }
-        for (Slot &sl : S->slots) {                 // admit in arrival order
+        // admit in arrival order; a request whose plan is not ready yet keeps its place
+        // while later ones (up to LOOKAHEAD) may start
+        for (Slot &sl : S->slots) {
             if (sl.req) {
                 busy = true;
                 continue;
             }
-            Req *q = nullptr;
-            {
-                std::lock_guard<std::mutex> g(S->mu);
-                if (S->pending.empty()) break;
-                q = S->pending.front();
-                S->pending.pop_front();
-            }
-            int st = NNFFT_OK;
-            const Admit a = admit(S, sl, q, &st);
-            if (a == WAIT) {
-                std::lock_guard<std::mutex> g(S->mu);
-                S->pending.push_front(q);
-                break;
-            }
-            if (a == FAILED) {
+            size_t i = 0;
+            while (!sl.req) {
+                Req *q = nullptr;
                 {
                     std::lock_guard<std::mutex> g(S->mu);
-                    record_done(S, q, st);
+                    if (i >= S->pending.size() || i >= LOOKAHEAD) break;
+                    q = S->pending[i];
                 }
-                S->cv_done.notify_all();
-                continue;
+                int st = NNFFT_OK;
+                const Admit a = admit(S, sl, q, &st);
+                if (a == WAIT) {
+                    ++i;
+                    continue;
+                }
+                {
+                    std::lock_guard<std::mutex> g(S->mu);
+                    S->pending.erase(S->pending.begin() + (std::ptrdiff_t)i);
+                    if (a == FAILED) record_done(S, q, st);
+                }
+                if (a == FAILED) S->cv_done.notify_all();
+                else busy = true;
             }
-            busy = true;
         }
         std::unique_lock<std::mutex> lk(S->mu);
         if (busy || !S->pending.empty()) {
@@ -472,6 +552,7 @@ int nnfft_server_create(nnfft_server_t *out, int64_t mem_budget_bytes, int nslot
         }
         S->fixed_bytes += 48 * mp + 16 * (8 * 16384 + 1);
     }
+    S->builder = std::thread(builder_loop, S);
     S->worker = std::thread(worker_loop, S);
     *out = S;
     return NNFFT_OK;
@@ -576,11 +657,23 @@ int nnfft_server_destroy(nnfft_server_t S) {
     }
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    {
+        std::lock_guard<std::mutex> g(S->mu_build);
+        S->stop_build = true;
+        for (PlanEntry *e : S->build_jobs) {   // queued, never started
+            S->plans.erase(std::find(S->plans.begin(), S->plans.end(), e));
+            delete e;
+        }
+        S->build_jobs.clear();
+    }
+    S->cv_build.notify_all();
+    if (S->builder.joinable()) S->builder.join();
+    integrate_builds(S);
     for (Slot &sl : S->slots)
         if (sl.st) cudaStreamSynchronize(sl.st);
     // plans first: they may still name a slot stream
     for (PlanEntry *e : S->plans) {
-        destroy_idle_plan(e->p);
+        if (e->p) destroy_idle_plan(e->p);
         delete e;
     }
     S->plans.clear();
