@@ -666,9 +666,7 @@ def run_ours(args, rank, world):
     zh = _t.empty(M_PTS, dtype=_t.complex128).pin_memory().numpy()
 
     def e2e_step():
-        plan.set_nodes_host(vh, xh)
-        plan.exec_host(fh, yh)
-        plan.adjoint_host(gh, zh)
+        plan.transform_host(vh, xh, fh, gh, yh, zh)
     e2e_step()
     k_e2e = max(3, min(args.steps, 10))
     barrier()
@@ -683,8 +681,8 @@ def run_ours(args, rank, world):
     e2e = {"value": world * pts_step / t_e2e, "unit": "pts/s",
            "h2d_bytes_per_step": int(vh.nbytes + xh.nbytes + fh.nbytes + gh.nbytes),
            "d2h_bytes_per_step": int(yh.nbytes + zh.nbytes),
-           "what": "nnfft_set_nodes_host + nnfft_exec_host + nnfft_adjoint_host from pinned host "
-                   "buffers, results copied back, wall clock"}
+           "what": "nnfft_transform_host (new nodes, forward and adjoint) from pinned host "
+                   "buffers, uploads overlapped with the node sort, results copied back, wall clock"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

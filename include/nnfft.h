@@ -261,6 +261,19 @@ int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host);
  */
 int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void *y_host);
 
+/*
+ * nnfft_transform_host: new nodes and both directions from host memory in one call:
+ * y = A f and z = A^H g for the nodes v, x (all host arrays of the plan's sizes; pinned
+ * memory copies asynchronously).  The nodes are uploaded first and sorted (one side per
+ * stream) while f and g go up on a third stream; the forward and the adjoint then run
+ * concurrently and their results come back on their own streams.  Pass f = y = NULL or
+ * g = z = NULL to skip a direction.  Synchronous; returns any kernel status (ERANGE for a
+ * node outside [-1/2, 1/2]).  Results equal nnfft_set_nodes_host + nnfft_exec_host +
+ * nnfft_adjoint_host.
+ */
+int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_host,
+                         const void *f_host, void *y_host, const void *g_host, void *z_host);
+
 /* nnfft_sync: wait for the plan's stream; return and clear the kernel status. */
 int nnfft_sync(nnfft_plan_t p);
 

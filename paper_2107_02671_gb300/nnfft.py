@@ -124,6 +124,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_exec.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint.argtypes = [vp, vp, vp]
         lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
+        lib.nnfft_transform_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, cint]
         lib.nnfft_get_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_tuning.argtypes = [vp, P(Tuning)]
@@ -330,6 +331,25 @@ class Plan:
                 and arr.flags.c_contiguous):
             raise TypeError(f"{name} must be a contiguous {np.dtype(self.np_cdtype)} numpy array of {n}")
         return ctypes.c_void_p(arr.ctypes.data)
+
+    def transform_host(self, v, x, f=None, g=None, y=None, z=None):
+        """New nodes and both directions from host arrays in one call (overlapped copies):
+        returns (A f, A^H g); a direction is skipped when its input is None."""
+        for arr, n, name in ((v, self.M1, "v"), (x, self.M2, "x")):
+            if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.size == n
+                    and arr.flags.c_contiguous):
+                raise TypeError(f"{name} must be a contiguous float64 numpy array of {n}")
+        if f is not None and y is None:
+            y = np.empty(self.M2, dtype=self.np_cdtype)
+        if g is not None and z is None:
+            z = np.empty(self.M1, dtype=self.np_cdtype)
+        pf = self._host_arr(f, self.M1, "f") if f is not None else None
+        py = self._host_arr(y, self.M2, "y") if f is not None else None
+        pg = self._host_arr(g, self.M2, "g") if g is not None else None
+        pz = self._host_arr(z, self.M1, "z") if g is not None else None
+        _check(self._lib.nnfft_transform_host(self._h, ctypes.c_void_p(v.ctypes.data),
+                                              ctypes.c_void_p(x.ctypes.data), pf, py, pg, pz))
+        return y, z
 
     def exec_host(self, f, out=None):
         out = np.empty(self.M2, dtype=self.np_cdtype) if out is None else out

@@ -449,3 +449,29 @@ def test_every_moments_and_fft_variant_is_correct():
             y, z = y.cpu().numpy(), z.cpu().numpy()
             assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= 1e-12, (lanes, fv)
             assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= 1e-12, (lanes, fv)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_transform_host_equals_separate_host_calls(dtype):
+    """nnfft_transform_host (overlapped uploads, both directions concurrently) returns
+    bit for bit what set_nodes_host + exec_host + adjoint_host return; either direction
+    can be skipped; a node out of range reports ERANGE."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    m = 8 if dtype == torch.complex128 else 4
+    N, M1, M2 = 800, 50000, 40000
+    v, x, f = W.nnfft_inputs(M1, M2, 51, dtype=npd)
+    g = W.adjoint_inputs(M2, 51, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    plan.set_nodes_host(v, x)
+    y1, z1 = plan.exec_host(f), plan.adjoint_host(g)
+    y2, z2 = plan.transform_host(v, x, f, g)
+    assert np.array_equal(y1, y2) and np.array_equal(z1, z2)
+    y3, z3 = plan.transform_host(v, x, f=f)
+    assert np.array_equal(y1, y3) and z3 is None
+    y4, z4 = plan.transform_host(v, x, g=g)
+    assert y4 is None and np.array_equal(z1, z4)
+    vb = v.copy()
+    vb[7] = 0.6
+    with pytest.raises(B.NNFFTError) as e:
+        plan.transform_host(vb, x, f, g)
+    assert e.value.code == 2
