@@ -277,8 +277,7 @@ def run_batched(args, rank, dev, flush, timed, pk):
         z = torch.empty(int(M1.sum()), dtype=dt, device=dev)
 
         def step(P=P, vd=vd, xd=xd, fd=fd, gd=gd, y=y, z=z):
-            P.set_nodes(vd, xd)
-            P.exec_adjoint(fd, gd, y, z)
+            P.transform(vd, xd, fd, gd, y, z)
 
         def fwd_adj(P=P, fd=fd, gd=gd, y=y, z=z):
             P.exec_adjoint(fd, gd, y, z)
@@ -466,8 +465,9 @@ def run_ours(args, rank, world):
     info = plan.info
 
     def step(p=plan, vv=vd, xx=xd, ff=fd, gg=gd, yy=y, zz=z):
-        p.set_nodes(vv, xx)
-        p.exec_adjoint(ff, gg, yy, zz)      # forward and adjoint run concurrently
+        # new nodes, forward and adjoint in one call: the two sorts and the two directions
+        # overlap (each direction waits for the other side's sort only before its gather)
+        p.transform(vv, xx, ff, gg, yy, zz)
 
     def timed(stepfn, k, pl=None, flush_l2=True):
         """Per-step CUDA-event timing on the plan stream, L2 flushed between steps."""

@@ -262,6 +262,18 @@ int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host);
 int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void *y_host);
 
 /*
+ * nnfft_transform: new nodes and both directions in one call, device buffers:
+ * y = A f and z = A^H g for the nodes v, x (sizes as nnfft_set_nodes / nnfft_exec).  The
+ * two node sides are sorted concurrently; the forward starts as soon as v is sorted and
+ * waits for x only before its gather half, the adjoint the other way round, so the
+ * directions overlap each other and the sort.  f = y = NULL or g = z = NULL skips a
+ * direction.  Asynchronous on the plan stream; results equal nnfft_set_nodes +
+ * nnfft_exec + nnfft_adjoint.
+ */
+int nnfft_transform(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
+                    void *y_dev, const void *g_dev, void *z_dev);
+
+/*
  * nnfft_transform_host: new nodes and both directions from host memory in one call:
  * y = A f and z = A^H g for the nodes v, x (all host arrays of the plan's sizes; pinned
  * memory copies asynchronously).  The nodes are uploaded first and sorted (one side per

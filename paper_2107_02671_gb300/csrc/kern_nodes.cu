@@ -95,8 +95,16 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
         first_inst = lo;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < SORT_TILE; k += SORT_THREADS) {
-        const long long i = base + k;
+    constexpr int PER = SORT_TILE / SORT_THREADS;
+    double xv[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {            // all loads of the thread first
+        const long long i = base + threadIdx.x + (long long)r * SORT_THREADS;
+        xv[r] = i < n ? nodes[i] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const long long i = base + threadIdx.x + (long long)r * SORT_THREADS;
         if (i >= n) break;
         NodeInst I = one;
         if (ninst > 1) {              // a tile meets few instances: step forward from the first
@@ -106,7 +114,7 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
         }
         long long c = 0, Y = -0x7fffffffffffffffLL - 1;
         long long ic = 0;
-        if (!node_fixed(nodes[i], I.S, c, Y)) {
+        if (!node_fixed(xv[r], I.S, c, Y)) {
             atomicOr(status, STATUS_RANGE);
             Y = -0x7fffffffffffffffLL - 1;
         } else {

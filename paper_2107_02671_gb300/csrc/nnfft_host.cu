@@ -758,7 +758,8 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     return NNFFT_OK;
 }
 
-int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
+int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
+                      cudaEvent_t mid = nullptr) {
     const Side &V = p->side[0], &X = p->side[1];
     if (X.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
@@ -781,6 +782,8 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
         StageTimer t(p, 4, st);
         NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
+    // the gather side's nodes (sorted on another stream) are needed from here on
+    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
     {
         StageTimer t(p, 5, st);
         NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
@@ -793,7 +796,8 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     return NNFFT_OK;
 }
 
-int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
+int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
+                      cudaEvent_t mid = nullptr) {
     const Side &V = p->side[0], &X = p->side[1];
     if (V.M == 0) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
@@ -816,6 +820,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
         StageTimer t(p, 9, st);
         NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
+    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
     {
         StageTimer t(p, 10, st);
         NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
@@ -829,7 +834,8 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
 }
 
 template <typename Real>
-int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
+int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
+                cudaEvent_t mid = nullptr) {
     const Side &V = p->side[0], &X = p->side[1];
     if (X.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
@@ -851,6 +857,8 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
         StageTimer t(p, 4, st);
         NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
     }
+    // the gather side's nodes (sorted on another stream) are needed from here on
+    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
     {
         StageTimer t(p, 5, st);
         NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), W.bufC, W.Q, st),
@@ -864,7 +872,8 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
 }
 
 template <typename Real>
-int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
+int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
+                cudaEvent_t mid = nullptr) {
     const Side &V = p->side[0], &X = p->side[1];
     if (V.M == 0) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
@@ -886,6 +895,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
         StageTimer t(p, 9, st);
         NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
     }
+    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
     {
         StageTimer t(p, 10, st);
         NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), W.bufC, W.Q, st),
@@ -898,14 +908,17 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     return NNFFT_OK;
 }
 
-int forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W) {
-    if (p->dbl && p->split) return run_forward_split(p, f, y, st, W);
-    return p->dbl ? run_forward<double>(p, f, y, st, W) : run_forward<float>(p, f, y, st, W);
+// mid: an event the gather half (gather convolution + evaluation) waits for, or nullptr
+int forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
+            cudaEvent_t mid = nullptr) {
+    if (p->dbl && p->split) return run_forward_split(p, f, y, st, W, mid);
+    return p->dbl ? run_forward<double>(p, f, y, st, W, mid) : run_forward<float>(p, f, y, st, W, mid);
 }
 
-int adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W) {
-    if (p->dbl && p->split) return run_adjoint_split(p, g, z, st, W);
-    return p->dbl ? run_adjoint<double>(p, g, z, st, W) : run_adjoint<float>(p, g, z, st, W);
+int adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
+            cudaEvent_t mid = nullptr) {
+    if (p->dbl && p->split) return run_adjoint_split(p, g, z, st, W, mid);
+    return p->dbl ? run_adjoint<double>(p, g, z, st, W, mid) : run_adjoint<float>(p, g, z, st, W, mid);
 }
 
 int collect_status(nnfft_plan_s *p) {
@@ -1280,6 +1293,57 @@ static int ensure_staging(nnfft_plan_s *p) {
     return NNFFT_OK;
 }
 
+// Both node sides sorted concurrently (v on the plan stream, x on the second stream); each
+// direction starts on the stream of the side its spread needs and waits for the other side
+// only before its gather half.  Nodes are in st_v / st_x style device arrays v, x.
+static int transform_dag(nnfft_plan_s *p, const double *v, const double *x, const void *f,
+                         void *y, const void *g, void *z, cudaEvent_t values_ready) {
+    cudaStream_t A = p->stream, Bs = p->aux;
+    int rc;
+    if ((rc = set_side_nodes(p, 1, x, Bs))) return rc;
+    NN_CUDA(cudaEventRecord(p->ev_x, Bs), "event");
+    if ((rc = set_side_nodes(p, 0, v, A))) return rc;
+    NN_CUDA(cudaEventRecord(p->ev_v, A), "event");
+    if (values_ready) {
+        NN_CUDA(cudaStreamWaitEvent(A, values_ready, 0), "wait for uploads");
+        NN_CUDA(cudaStreamWaitEvent(Bs, values_ready, 0), "wait for uploads");
+    }
+    // adjoint: spread from x (on Bs), gather to v; forward: spread from v (on A), gather to x
+    if (g && (rc = adjoint(p, g, z, Bs, p->work[1], p->ev_v))) return rc;
+    if (f && (rc = forward(p, f, y, A, p->work[0], p->ev_x))) return rc;
+    return NNFFT_OK;
+}
+
+static int ensure_dag(nnfft_plan_s *p, bool adj) {
+    int rc;
+    if (adj && !p->work[1].P && (rc = alloc_work(p, p->work[1]))) return rc;
+    if (!p->copy) {
+        NN_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking), "stream");
+        NN_CUDA(cudaEventCreateWithFlags(&p->ev_v, cudaEventDisableTiming), "event");
+        NN_CUDA(cudaEventCreateWithFlags(&p->ev_x, cudaEventDisableTiming), "event");
+        NN_CUDA(cudaEventCreateWithFlags(&p->ev_up, cudaEventDisableTiming), "event");
+    }
+    return NNFFT_OK;
+}
+
+int nnfft_transform(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
+                    void *y_dev, const void *g_dev, void *z_dev) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    const int64_t M1 = p->info.M1, M2 = p->info.M2;
+    if ((M1 > 0 && !v_dev) || (M2 > 0 && !x_dev)) return fail(NNFFT_EINVAL, "null node pointer");
+    const bool fwd = f_dev && y_dev, adj = g_dev && z_dev;
+    int rc = ensure_dag(p, adj);
+    if (rc) return rc;
+    NN_CUDA(cudaEventRecord(p->ev_fork, p->stream), "fork");
+    NN_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0), "fork");
+    if ((rc = transform_dag(p, v_dev, x_dev, fwd ? f_dev : nullptr, y_dev, adj ? g_dev : nullptr,
+                            z_dev, nullptr)))
+        return rc;
+    NN_CUDA(cudaEventRecord(p->ev_join, p->aux), "join");
+    NN_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "join");
+    return NNFFT_OK;
+}
+
 int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_host,
                          const void *f_host, void *y_host, const void *g_host, void *z_host) {
     if (!p) return fail(NNFFT_EINVAL, "null plan");
@@ -1292,13 +1356,7 @@ int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_h
     const size_t cs = 2 * real_size(p->dbl);
     if (adj && !p->st_g && (rc = dalloc(p, &p->st_g, (size_t)p->side[1].M_cap * cs, "staging"))) return rc;
     if (adj && !p->st_z && (rc = dalloc(p, &p->st_z, (size_t)p->side[0].M_cap * cs, "staging"))) return rc;
-    if (adj && !p->work[1].P && (rc = alloc_work(p, p->work[1]))) return rc;
-    if (!p->copy) {
-        NN_CUDA(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking), "stream");
-        NN_CUDA(cudaEventCreateWithFlags(&p->ev_v, cudaEventDisableTiming), "event");
-        NN_CUDA(cudaEventCreateWithFlags(&p->ev_x, cudaEventDisableTiming), "event");
-        NN_CUDA(cudaEventCreateWithFlags(&p->ev_up, cudaEventDisableTiming), "event");
-    }
+    if ((rc = ensure_dag(p, adj))) return rc;
     cudaStream_t A = p->stream, Bs = p->aux, C = p->copy;
     // nodes first, one side per stream; the values go up on the copy stream while the
     // nodes are sorted
@@ -1310,17 +1368,9 @@ int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_h
     if (fwd && M1) NN_CUDA(cudaMemcpyAsync(p->st_f, f_host, cs * (size_t)M1, cudaMemcpyHostToDevice, C), "copy f");
     if (adj && M2) NN_CUDA(cudaMemcpyAsync(p->st_g, g_host, cs * (size_t)M2, cudaMemcpyHostToDevice, C), "copy g");
     NN_CUDA(cudaEventRecord(p->ev_up, C), "event");
-    if ((rc = set_side_nodes(p, 1, p->st_x, Bs))) return rc;
-    if ((rc = set_side_nodes(p, 0, p->st_v, A))) return rc;
-    NN_CUDA(cudaEventRecord(p->ev_v, A), "event");
-    NN_CUDA(cudaEventRecord(p->ev_x, Bs), "event");
-    NN_CUDA(cudaStreamWaitEvent(A, p->ev_x, 0), "join");
-    NN_CUDA(cudaStreamWaitEvent(A, p->ev_up, 0), "join");
-    NN_CUDA(cudaStreamWaitEvent(Bs, p->ev_v, 0), "join");
-    NN_CUDA(cudaStreamWaitEvent(Bs, p->ev_up, 0), "join");
-    // forward on the plan stream, adjoint on the second stream, results back on each
-    if (adj && (rc = adjoint(p, p->st_g, p->st_z, Bs, p->work[1]))) return rc;
-    if (fwd && (rc = forward(p, p->st_f, p->st_y, A, p->work[0]))) return rc;
+    if ((rc = transform_dag(p, p->st_v, p->st_x, fwd ? p->st_f : nullptr, p->st_y,
+                            adj ? p->st_g : nullptr, p->st_z, p->ev_up)))
+        return rc;
     if (adj && M1) NN_CUDA(cudaMemcpyAsync(z_host, p->st_z, cs * (size_t)M1, cudaMemcpyDeviceToHost, Bs), "copy z");
     if (fwd && M2) NN_CUDA(cudaMemcpyAsync(y_host, p->st_y, cs * (size_t)M2, cudaMemcpyDeviceToHost, A), "copy y");
     NN_CUDA(cudaEventRecord(p->ev_join, Bs), "join");

@@ -125,6 +125,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_adjoint.argtypes = [vp, vp, vp]
         lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
         lib.nnfft_transform_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.nnfft_transform.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, cint]
         lib.nnfft_get_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_tuning.argtypes = [vp, P(Tuning)]
@@ -331,6 +332,24 @@ class Plan:
                 and arr.flags.c_contiguous):
             raise TypeError(f"{name} must be a contiguous {np.dtype(self.np_cdtype)} numpy array of {n}")
         return ctypes.c_void_p(arr.ctypes.data)
+
+    def transform(self, v, x, f=None, g=None, y=None, z=None):
+        """New nodes and both directions in one call (device tensors): returns (A f, A^H g);
+        a direction is skipped when its input is None."""
+        import torch
+        pv = _dev_tensor(v, torch.float64, self.M1, "v")
+        px = _dev_tensor(x, torch.float64, self.M2, "x")
+        pf = py = pg = pz = None
+        if f is not None:
+            pf = _dev_tensor(f, self.cdtype, self.M1, "f")
+            y = torch.empty(self.M2, dtype=self.cdtype, device=f.device) if y is None else y
+            py = _dev_tensor(y, self.cdtype, self.M2, "y")
+        if g is not None:
+            pg = _dev_tensor(g, self.cdtype, self.M2, "g")
+            z = torch.empty(self.M1, dtype=self.cdtype, device=g.device) if z is None else z
+            pz = _dev_tensor(z, self.cdtype, self.M1, "z")
+        _check(self._lib.nnfft_transform(self._h, pv, px, pf, py, pg, pz))
+        return (y if f is not None else None), (z if g is not None else None)
 
     def transform_host(self, v, x, f=None, g=None, y=None, z=None):
         """New nodes and both directions from host arrays in one call (overlapped copies):

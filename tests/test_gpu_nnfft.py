@@ -475,3 +475,34 @@ def test_transform_host_equals_separate_host_calls(dtype):
     with pytest.raises(B.NNFFTError) as e:
         plan.transform_host(vb, x, f, g)
     assert e.value.code == 2
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_transform_device_equals_separate_calls(dtype):
+    """nnfft_transform (sorts and both directions overlapped, device buffers) returns bit
+    for bit set_nodes + exec + adjoint, for a single plan and a batch; directions can be
+    skipped."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    m = 8 if dtype == torch.complex128 else 4
+    N, M1, M2 = 900, 60000, 30000
+    v, x, f = W.nnfft_inputs(M1, M2, 61, dtype=npd)
+    g = W.adjoint_inputs(M2, 61, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    y1 = plan.exec(dev(f, dtype)).cpu().numpy()
+    z1 = plan.adjoint(dev(g, dtype)).cpu().numpy()
+    y2, z2 = plan.transform(dev(v), dev(x), dev(f, dtype), dev(g, dtype))
+    y3, _ = plan.transform(dev(v), dev(x), f=dev(f, dtype))
+    _, z4 = plan.transform(dev(v), dev(x), g=dev(g, dtype))
+    plan.sync()
+    assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
+    assert np.array_equal(y1, y3.cpu().numpy()) and np.array_equal(z1, z4.cpu().numpy())
+    Nb, M1b, M2b = np.array([100, 2000, 50]), np.array([4000, 100, 900]), np.array([300, 5000, 1])
+    vb, xb, fb = W.batch_inputs(M1b, M2b, 62, dtype=npd)
+    gb = W.draw_complex(np.random.default_rng(9), int(M2b.sum()), npd)
+    P = B.BatchPlan(Nb, M1b, M2b, 2.0, 2.0, m, dtype=dtype)
+    P.set_nodes(dev(vb), dev(xb))
+    y1, z1 = P.exec(dev(fb, dtype)).cpu().numpy(), P.adjoint(dev(gb, dtype)).cpu().numpy()
+    y2, z2 = P.transform(dev(vb), dev(xb), dev(fb, dtype), dev(gb, dtype))
+    P.sync()
+    assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
