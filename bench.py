@@ -225,14 +225,15 @@ def run_reference(args, rank, world):
 # our arm
 # -------------------------------------------------------------------------------------------
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the point
-# kernels, from one ncu capture of `python bench.py --steps 5 --warmup 3 --no-cpu-baseline`
+# kernels, from one ncu capture of
+# `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve`
 # (profiles/k_*_nnfft_fp64_N4096_M2e20.md).  Each entry names the sources the kernel is
 # built from and their hash at capture time; a changed source reports null.
 NCU_TRAFFIC = {
-    "moments": {"kernel": "k_moments_df<14>", "bytes": 29.48e6,
-                "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "1c23e1fd1c5a151e"},
-    "eval": {"kernel": "k_eval_df<14>", "bytes": 16.35e6 + 1.69e6,
-             "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "1c23e1fd1c5a151e"},
+    "moments": {"kernel": "k_moments_df_warp<14>", "bytes": 29.48e6,
+                "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "188812269663e2e0"},
+    "eval": {"kernel": "k_eval_df<14>", "bytes": 16.21e6 + 1.65e6,
+             "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "188812269663e2e0"},
 }
 
 
