@@ -262,12 +262,16 @@ def run_batched(args, rank, dev, flush, timed, pk):
     import torch
     from paper_2107_02671_gb300 import nnfft as B
     from paper_2107_02671_gb300 import workloads as W
-    N, M1, M2 = W.batch_sizes(BATCH_COUNT, rank)
-    out = {"instances": BATCH_COUNT, "sum_M1": int(M1.sum()), "sum_M2": int(M2.sum()),
+    count = args.batch_count
+    N, M1, M2 = W.batch_sizes(count, rank)
+    out = {"instances": count, "sum_M1": int(M1.sum()), "sum_M2": int(M2.sum()),
            "sizes": "M1, M2 log-uniform in [1e3, 1e6], N log-uniform in [64, 8192], uniform nodes"}
     pts = int(M1.sum() + M2.sum())
-    for name, dt, npd, m, bpp in (("fp32_m4", torch.complex64, np.complex64, 4, 16),
-                                  ("fp64_m8", torch.complex128, np.complex128, 8, 24)):
+    variants = (("fp32_m4", torch.complex64, np.complex64, 4, 16),
+                ("fp64_m8", torch.complex128, np.complex128, 8, 24))
+    if args.only_fp32_batch:
+        variants = variants[:1]
+    for name, dt, npd, m, bpp in variants:
         v, x, f = W.batch_inputs(M1, M2, 1000 * rank, dtype=npd)
         g = W.draw_complex(np.random.default_rng(7 + rank), int(M2.sum()), npd)
         t0 = time.time()
@@ -283,8 +287,7 @@ def run_batched(args, rank, dev, flush, timed, pk):
         def fwd_adj(P=P, fd=fd, gd=gd, y=y, z=z):
             P.exec_adjoint(fd, gd, y, z)
 
-        P.set_nodes(vd, xd)
-        tune = P.autotune(fd, gd, y, z, reps=2)
+        tune = P.autotune(fd, gd, y, z, reps=2, v=vd, x=xd, flush_l2=True)
         for _ in range(3):
             step()
         P.sync()
@@ -307,7 +310,7 @@ def run_batched(args, rank, dev, flush, timed, pk):
                 import oracle
                 yh = y.cpu().numpy()
                 worst = 0.0
-                for i in range(0, BATCH_COUNT, 97):
+                for i in range(0, count, 97):
                     a1, b1, a2, b2 = P.off1[i], P.off1[i + 1], P.off2[i], P.off2[i + 1]
                     rows = W.sample_rows(int(M2[i]), 4, i)
                     fi = f[a1:b1].astype(np.complex128)
@@ -511,8 +514,7 @@ def run_ours(args, rank, world):
         return 0
 
     # kernel variants picked by the library's autotuner on this node set (outside timing)
-    plan.set_nodes(vd, xd)
-    tuning = plan.autotune(fd, gd, y, z, reps=3)
+    tuning = plan.autotune(fd, gd, y, z, reps=3, v=vd, x=xd, flush_l2=True)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -732,6 +734,10 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the served mixed stream")
     ap.add_argument("--only-served", action="store_true",
                     help="run only the served mixed stream and print its numbers")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="instances of the batched workload (512; fewer for profiling runs)")
+    ap.add_argument("--only-fp32-batch", action="store_true",
+                    help="batched workload at fp32 only (profiling runs)")
     ap.add_argument("--only-batched", action="store_true",
                     help="run only the batched workload and print its numbers (profiling)")
     args = ap.parse_args()

@@ -168,26 +168,35 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
 
 /*
  * Autotuning (the paper has no counterpart).  nnfft_autotune times the plan's kernel
- * variants on its current nodes (nnfft_set_nodes first) with the caller's buffers, `reps`
- * runs of nnfft_exec_adjoint per configuration (CUDA events on the plan stream), and keeps
- * the fastest: threads per work item of the split-precision moments kernel on each side
- * (32: one warp per item, 16: two items per warp) and the FFT's packing of short columns
- * into blocks (variant 0 by the plan-size rule, variant 1 the other extreme).  y and z
- * receive the transforms.  Synchronous.  A different moments variant sums each cell's
- * points in another order, so later results may change in the last bits.
+ * variants with the caller's buffers and keeps the fastest: threads per work item of the
+ * split-precision moments kernel on each side (32: one warp per item, 16: two items per
+ * warp), the FFT's packing of short columns into blocks (variant 0 by the plan-size rule,
+ * variant 1 the other extreme) and, when the nodes are given, whether work items of at
+ * most 16 points run one thread per item (item_split; only tried where some instance has
+ * few points per cell).  With v and x (device) every run is a full nnfft_transform; with
+ * v = x = NULL it is nnfft_exec_adjoint on the current nodes.  Every configuration is
+ * timed in three interleaved sweeps of `reps` runs (best kept); the default stays unless
+ * another is more than 3 % faster.  flags: NNFFT_TUNE_FLUSH_L2 writes a 192 MB buffer
+ * before every timed run (cold L2, as in a stream of new problems).  y and z receive the
+ * transforms.  Synchronous.  Other variants sum in another order, so later results may
+ * change in the last bits.
  */
+enum { NNFFT_TUNE_FLUSH_L2 = 1 };
 typedef struct {
     int moments_lanes_v, moments_lanes_x;   /* 32 or 16 */
     int fft_variant;                        /* 0 or 1 */
     int tuned;                              /* 1 after nnfft_autotune */
-    double default_ms, best_ms;             /* per exec_adjoint: default and chosen config */
+    double default_ms, best_ms;             /* per run: default and chosen config */
+    int item_split;                         /* 1: small work items one thread each (default 0) */
+    int timed_transform;                    /* 1: runs were full transforms */
 } nnfft_tuning;
-int nnfft_autotune(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
-                   void *z_dev, int reps);
+int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
+                   void *y_dev, const void *g_dev, void *z_dev, int reps, int flags);
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
- * moments_lanes_v / _x in {16, 32}, fft_variant in {0, 1}; the other fields are ignored.
- * EINVAL otherwise.  Takes effect for the work queued next. */
+ * moments_lanes_v / _x in {16, 32}, fft_variant in {0, 1}, item_split in {0, 1}; the other
+ * fields are ignored.  EINVAL otherwise.  Takes effect for the work queued next; a changed
+ * item_split needs nnfft_set_nodes again. */
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t);
 
 /*

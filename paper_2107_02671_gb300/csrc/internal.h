@@ -56,7 +56,13 @@ template <typename Real> struct SideK {
     const int *item_pe;    // [max_items] one past its last point
     const int *nitems;     // device scalar: number of items
     int max_items;
+    // with small-item splitting: items of at most SMALL_ITEM points (list_small, count
+    // *n_small) run one thread per item, the others (list_big, *n_big) one warp per item;
+    // nullptr lists: every item runs one warp per item
+    const int *list_small, *list_big, *n_small, *n_big;
 };
+// Largest work item handled by one thread (no reduction) when a plan splits items.
+constexpr int SMALL_ITEM = 16;
 
 // Double-float tables of one side for the split-precision grid kernels.
 struct SideDf {
@@ -191,6 +197,11 @@ cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_o
                                      int *item_cell, int *item_pb, int *item_pe, int *nitems,
                                      int *scratch, cudaStream_t s);
 size_t build_items_scratch_len(int ncell);
+// Split the work items into those of at most SMALL_ITEM points and the rest (lists of
+// item ids in no particular order, counts in n2[0], n2[1]; n2 zeroed by the caller).
+cudaError_t launch_split_items(const int *nitems, const int *item_pb, const int *item_pe,
+                               int max_items, int *list_small, int *list_big, int *n2,
+                               cudaStream_t s);
 
 // ---- kern_spread.cu ---------------------------------------------------------------
 // Cell moments of vals over the sorted points, one set per work item, into P; the

@@ -484,9 +484,43 @@ k_item_fill_blocks(const int *__restrict__ off, int ncell, const int *__restrict
     }
 }
 
+// Work items of at most SMALL_ITEM points to list_small, the rest to list_big; one
+// warp-aggregated atomic per warp and list (the order within a list does not matter:
+// every item is computed independently).
+__global__ void k_split_items(const int *__restrict__ nitems, const int *__restrict__ item_pb,
+                              const int *__restrict__ item_pe, int *__restrict__ list_small,
+                              int *__restrict__ list_big, int *__restrict__ n2) {
+    const int it = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = it < *nitems;
+    const bool small = valid && item_pe[it] - item_pb[it] <= SMALL_ITEM;
+    const unsigned ms = __ballot_sync(0xffffffffu, small);
+    const unsigned mb = __ballot_sync(0xffffffffu, valid && !small);
+    int bs = 0, bb = 0;
+    if (lane == 0) {
+        if (ms) bs = atomicAdd(&n2[0], __popc(ms));
+        if (mb) bb = atomicAdd(&n2[1], __popc(mb));
+    }
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    const unsigned lt = lanemask_lt();
+    if (small) list_small[bs + __popc(ms & lt)] = it;
+    else if (valid) list_big[bb + __popc(mb & lt)] = it;
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
+
+cudaError_t launch_split_items(const int *nitems, const int *item_pb, const int *item_pe,
+                               int max_items, int *list_small, int *list_big, int *n2,
+                               cudaStream_t s) {
+    if (max_items <= 0) return cudaSuccess;
+    k_split_items<<<cdiv(max_items, 256), 256, 0, s>>>(nitems, item_pb, item_pe, list_small,
+                                                       list_big, n2);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 size_t radix_sort_hist_len(int n) {
     long long nb = n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1;

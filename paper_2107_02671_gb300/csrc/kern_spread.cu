@@ -34,6 +34,8 @@ __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a,
 
 // points per lane of a work item (ITEM_CAP points, 32 lanes)
 constexpr int PPL = ITEM_CAP / 32;
+// points a small-item thread loads at a time
+constexpr int SMALL_BATCH = 4;
 
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real v) {
@@ -72,12 +74,19 @@ __device__ __forceinline__ void rs_step(Real (&v)[32], int lane) {
 // points of one cell): lanes stride over the points and accumulate
 // sum_k val_k T_d(y_k) in registers; the warp then reduces the D complex sums.
 // ---------------------------------------------------------------------------------
+// Work item of warp w: w itself, or the w-th entry of the big-item list; -1 past the end.
+template <typename Real>
+__device__ __forceinline__ int warp_item(const SideK<Real> &S, int w) {
+    if (S.list_big) return w < *S.n_big ? S.list_big[w] : -1;
+    return w < *S.nitems ? w : -1;
+}
+
 template <typename Real, int D>
 __global__ void __launch_bounds__(256)
 k_moments(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict__ P) {
-    const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int item = warp_item(S, (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5));
     const int lane = threadIdx.x & 31;
-    if (item >= *S.nitems) return;
+    if (item < 0) return;
     const int pb = S.item_pb[item], pe = S.item_pe[item];
     Real ar[D], ai[D];
 #pragma unroll
@@ -132,6 +141,48 @@ k_moments(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict
         for (int d = 0; d < D; ++d)
             if (lane == d) P[(long long)item * D + d] = mk2<Real>(ar[d], ai[d]);
     }
+}
+
+// ---------------------------------------------------------------------------------
+// Cell moments of small work items (<= SMALL_ITEM points): one thread per item walks
+// its points in order, no reduction.
+// ---------------------------------------------------------------------------------
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_moments_small(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict__ P) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= *S.n_small) return;
+    const int item = S.list_small[idx];
+    const int pb = S.item_pb[item], pe = S.item_pe[item];
+    Real ar[D], ai[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
+    for (int p0 = pb; p0 < pe; p0 += SMALL_BATCH) {   // loads of SMALL_BATCH points first
+        Real yv[SMALL_BATCH];
+        int jv[SMALL_BATCH];
+#pragma unroll
+        for (int k = 0; k < SMALL_BATCH; ++k) {
+            const int p = p0 + k;
+            yv[k] = p < pe ? S.ys[p] : Real(0);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+        C2<Real> fv[SMALL_BATCH];
+#pragma unroll
+        for (int k = 0; k < SMALL_BATCH; ++k) fv[k] = jv[k] >= 0 ? vals[jv[k]] : mk2<Real>(Real(0), Real(0));
+#pragma unroll
+        for (int k = 0; k < SMALL_BATCH; ++k) {
+            if (jv[k] < 0) break;
+            Real T[D];
+            cheb<Real, D>(yv[k], T);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                ar[d] = fma(fv[k].x, T[d], ar[d]);
+                ai[d] = fma(fv[k].y, T[d], ai[d]);
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) P[(long long)item * D + d] = mk2<Real>(ar[d], ai[d]);
 }
 
 // ---------------------------------------------------------------------------------
@@ -340,9 +391,9 @@ k_gather_conv(GridLaunch<Real> L, const C2<Real> *__restrict__ buf_all,
 template <typename Real, int D>
 __global__ void __launch_bounds__(256)
 k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
-    const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int item = warp_item(S, (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5));
     const int lane = threadIdx.x & 31;
-    if (item >= *S.nitems) return;
+    if (item < 0) return;
     const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
     Real qr[D], qi[D];
 #pragma unroll
@@ -371,6 +422,46 @@ k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out
             si = fma(qi[d], T[d], si);
         }
         if (jv[k] >= 0) out[jv[k]] = mk2<Real>(sr, si);
+    }
+}
+
+// Point evaluation of small work items: one thread per item.
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_eval_small(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= *S.n_small) return;
+    const int item = S.list_small[idx];
+    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
+    Real qr[D], qi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const C2<Real> q = Q[(long long)c * D + d];
+        qr[d] = q.x;
+        qi[d] = q.y;
+    }
+    for (int p0 = pb; p0 < pe; p0 += SMALL_BATCH) {
+        Real yv[SMALL_BATCH];
+        int jv[SMALL_BATCH];
+#pragma unroll
+        for (int k = 0; k < SMALL_BATCH; ++k) {
+            const int p = p0 + k;
+            yv[k] = p < pe ? S.ys[p] : Real(0);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < SMALL_BATCH; ++k) {
+            if (jv[k] < 0) break;
+            Real T[D];
+            cheb<Real, D>(yv[k], T);
+            Real sr = Real(0), si = Real(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                sr = fma(qr[d], T[d], sr);
+                si = fma(qi[d], T[d], si);
+            }
+            out[jv[k]] = mk2<Real>(sr, si);
+        }
     }
 }
 
@@ -412,6 +503,10 @@ cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cuda
     C2<Real> *Pp = static_cast<C2<Real> *>(P);
     NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
     count_launches(1);
+    if (S.list_small) {
+        NNFFT_DISPATCH_D(S.D, (k_moments_small<Real, DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(S, v, Pp)));
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -452,6 +547,10 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
     C2<Real> *o = static_cast<C2<Real> *>(out);
     NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));
     count_launches(1);
+    if (S.list_small) {
+        NNFFT_DISPATCH_D(S.D, (k_eval_small<Real, DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(S, q, o)));
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

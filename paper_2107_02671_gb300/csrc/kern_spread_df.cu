@@ -50,6 +50,81 @@ __device__ __forceinline__ void rs_step_df(df (&v)[32], int lane) {
     }
 }
 
+// One point's contribution to the moments: degrees d < B in double-float, the rest in
+// FP32 from the high parts (the arithmetic of every moments kernel below).
+template <int B, int F>
+__device__ __forceinline__ void moments_point(float2 yy, double2 v, df (&ar)[B], df (&ai)[B],
+                                              float (&br)[F], float (&bi)[F]) {
+    const df fr = split_double(v.x), fi = split_double(v.y);
+    const df y = mk(yy.x, yy.y);
+    const df y2 = mk(2.f * yy.x, 2.f * yy.y);
+    acc(ar[0], fr);
+    acc(ai[0], fi);
+    acc(ar[1], mul_u(fr, y));
+    acc(ai[1], mul_u(fi, y));
+    df t0 = mk(1.f), t1 = y;
+#pragma unroll
+    for (int d = 2; d < B; ++d) {
+        const df t = df_rec(y2, t1, t0);
+        acc(ar[d], mul_u(fr, t));
+        acc(ai[d], mul_u(fi, t));
+        t0 = t1;
+        t1 = t;
+    }
+    float g0 = t0.h, g1 = t1.h;
+    const float yf2 = y2.h;
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        const float t = fmaf(yf2, g1, -g0);
+        br[d] = fmaf(fr.h, t, br[d]);
+        bi[d] = fmaf(fi.h, t, bi[d]);
+        g0 = g1;
+        g1 = t;
+    }
+}
+
+// One point's value sum_d Q[d] T_d(y) (double-float for d < B, FP32 above), as a double pair.
+template <int B, int F>
+__device__ __forceinline__ double2 eval_point(float2 yy, const df (&qr)[B], const df (&qi)[B],
+                                              const float (&fr)[F], const float (&fi)[F]) {
+    const df y = mk(yy.x, yy.y);
+    const df y2 = mk(2.f * yy.x, 2.f * yy.y);
+    df sr = qr[0], si = qi[0];
+    acc(sr, mul_u(qr[1], y));
+    acc(si, mul_u(qi[1], y));
+    df t0 = mk(1.f), t1 = y;
+#pragma unroll
+    for (int d = 2; d < B; ++d) {
+        const df t = df_rec(y2, t1, t0);
+        acc(sr, mul_u(qr[d], t));
+        acc(si, mul_u(qi[d], t));
+        t0 = t1;
+        t1 = t;
+    }
+    float g0 = t0.h, g1 = t1.h, ur = 0.f, ui = 0.f;
+    const float yf2 = y2.h;
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        const float t = fmaf(yf2, g1, -g0);
+        ur = fmaf(fr[d], t, ur);
+        ui = fmaf(fi[d], t, ui);
+        g0 = g1;
+        g1 = t;
+    }
+    acc(sr, mk(ur));
+    acc(si, mk(ui));
+    double2 o;
+    o.x = to_double(norm(sr));
+    o.y = to_double(norm(si));
+    return o;
+}
+
+// Work item of warp w (or of half-warp w): w itself, or the w-th big item; -1 past the end.
+__device__ __forceinline__ int big_item(const SideK<double> &S, int w) {
+    if (S.list_big) return w < *S.n_big ? S.list_big[w] : -1;
+    return w < *S.nitems ? w : -1;
+}
+
 // ---------------------------------------------------------------------------------
 // Cell moments, split precision, one warp per work item: lanes stride over the item's
 // points (up to 8 each, all loads issued first), then a 32-lane reduce-scatter of the 2D
@@ -64,9 +139,9 @@ k_moments_df_warp(SideK<double> S, const float2 *__restrict__ ys2, const double2
              float4 *__restrict__ P4) {
     constexpr int B = D / 2;
     constexpr int F = D - B;
-    const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int item = big_item(S, (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5));
     const int lane = threadIdx.x & 31;
-    if (item >= *S.nitems) return;
+    if (item < 0) return;
     const int pb = S.item_pb[item], pe = S.item_pe[item];
     df ar[B], ai[B];
     float br[F], bi[F];
@@ -89,34 +164,7 @@ k_moments_df_warp(SideK<double> S, const float2 *__restrict__ ys2, const double2
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
         if (pb + 32 * k >= pe) break;                 // warp-uniform: no point in this round
-        const float2 yy = yv[k];
-        const double2 v = vv2[k];
-        const df fr = split_double(v.x), fi = split_double(v.y);
-        const df y = mk(yy.x, yy.y);
-        const df y2 = mk(2.f * yy.x, 2.f * yy.y);
-        acc(ar[0], fr);
-        acc(ai[0], fi);
-        acc(ar[1], mul_u(fr, y));
-        acc(ai[1], mul_u(fi, y));
-        df t0 = mk(1.f), t1 = y;
-#pragma unroll
-        for (int d = 2; d < B; ++d) {
-            const df t = df_rec(y2, t1, t0);
-            acc(ar[d], mul_u(fr, t));
-            acc(ai[d], mul_u(fi, t));
-            t0 = t1;
-            t1 = t;
-        }
-        float g0 = t0.h, g1 = t1.h;
-        const float yf2 = y2.h;
-#pragma unroll
-        for (int d = 0; d < F; ++d) {
-            const float t = fmaf(yf2, g1, -g0);
-            br[d] = fmaf(fr.h, t, br[d]);
-            bi[d] = fmaf(fi.h, t, bi[d]);
-            g0 = g1;
-            g1 = t;
-        }
+        moments_point<B, F>(yv[k], vv2[k], ar, ai, br, bi);
     }
     static_assert(2 * D <= 32, "split-precision moments need 2D <= 32");
     df vv[32];
@@ -180,9 +228,9 @@ k_moments_df_half(SideK<double> S, const float2 *__restrict__ ys2, const double2
     constexpr int F = D - B;
     static_assert(B <= 8 && F <= 8, "the slot layout holds at most 8 degrees of each kind");
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int item = gt / MOM_LANES;
+    const int item = big_item(S, gt / MOM_LANES);
     const int sub = threadIdx.x & (MOM_LANES - 1);
-    const bool live = item < *S.nitems;             // both halves of a warp stay for the shuffles
+    const bool live = item >= 0;                    // both halves of a warp stay for the shuffles
     int pb = 0, pe = 0;
     if (live) {
         pb = S.item_pb[item];
@@ -209,34 +257,7 @@ k_moments_df_half(SideK<double> S, const float2 *__restrict__ ys2, const double2
 #pragma unroll
         for (int k = 0; k < MOM_CHUNK; ++k) {
             if (jv[k] < 0) continue;
-            const float2 yy = yv[k];
-            const double2 v = vv2[k];
-            const df fr = split_double(v.x), fi = split_double(v.y);
-            const df y = mk(yy.x, yy.y);
-            const df y2 = mk(2.f * yy.x, 2.f * yy.y);
-            acc(ar[0], fr);
-            acc(ai[0], fi);
-            acc(ar[1], mul_u(fr, y));
-            acc(ai[1], mul_u(fi, y));
-            df t0 = mk(1.f), t1 = y;
-#pragma unroll
-            for (int d = 2; d < B; ++d) {
-                const df t = df_rec(y2, t1, t0);
-                acc(ar[d], mul_u(fr, t));
-                acc(ai[d], mul_u(fi, t));
-                t0 = t1;
-                t1 = t;
-            }
-            float g0 = t0.h, g1 = t1.h;
-            const float yf2 = y2.h;
-#pragma unroll
-            for (int d = 0; d < F; ++d) {
-                const float t = fmaf(yf2, g1, -g0);
-                br[d] = fmaf(fr.h, t, br[d]);
-                bi[d] = fmaf(fi.h, t, bi[d]);
-                g0 = g1;
-                g1 = t;
-            }
+            moments_point<B, F>(yv[k], vv2[k], ar, ai, br, bi);
         }
     }
     df vd[16];
@@ -275,9 +296,9 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
           double2 *__restrict__ out) {
     constexpr int B = D / 2;
     constexpr int F = D - B;
-    const int item = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int item = big_item(S, (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5));
     const int lane = threadIdx.x & 31;
-    if (item >= *S.nitems) return;
+    if (item < 0) return;
     const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
     df qr[B], qi[B];
     float fr[F], fi[F];
@@ -303,37 +324,90 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
 #pragma unroll
     for (int k = 0; k < PPL; ++k) {
         if (pb + 32 * k >= pe) break;
-        const float2 yy = yv[k];
-        const df y = mk(yy.x, yy.y);
-        const df y2 = mk(2.f * yy.x, 2.f * yy.y);
-        df sr = qr[0], si = qi[0];
-        acc(sr, mul_u(qr[1], y));
-        acc(si, mul_u(qi[1], y));
-        df t0 = mk(1.f), t1 = y;
-#pragma unroll
-        for (int d = 2; d < B; ++d) {
-            const df t = df_rec(y2, t1, t0);
-            acc(sr, mul_u(qr[d], t));
-            acc(si, mul_u(qi[d], t));
-            t0 = t1;
-            t1 = t;
-        }
-        float g0 = t0.h, g1 = t1.h, ur = 0.f, ui = 0.f;
-        const float yf2 = y2.h;
-#pragma unroll
-        for (int d = 0; d < F; ++d) {
-            const float t = fmaf(yf2, g1, -g0);
-            ur = fmaf(fr[d], t, ur);
-            ui = fmaf(fi[d], t, ui);
-            g0 = g1;
-            g1 = t;
-        }
-        acc(sr, mk(ur));
-        acc(si, mk(ui));
-        double2 o;
-        o.x = to_double(norm(sr));
-        o.y = to_double(norm(si));
+        const double2 o = eval_point<B, F>(yv[k], qr, qi, fr, fi);
         if (jv[k] >= 0) out[jv[k]] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Small work items (<= SMALL_ITEM points): one thread per item walks its points in
+// order; moments go out without any reduction, values straight to the caller's order.
+// ---------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256)
+k_moments_df_small(SideK<double> S, const float2 *__restrict__ ys2,
+                   const double2 *__restrict__ vals, float4 *__restrict__ P4) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= *S.n_small) return;
+    const int item = S.list_small[idx];
+    const int pb = S.item_pb[item], pe = S.item_pe[item];
+    df ar[B], ai[B];
+    float br[F], bi[F];
+#pragma unroll
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
+    for (int p0 = pb; p0 < pe; p0 += 4) {             // loads of 4 points first
+        float2 yv[4];
+        int jv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yv[k] = p0 + k < pe ? ys2[p0 + k] : make_float2(0.f, 0.f);
+            jv[k] = p0 + k < pe ? S.perm[p0 + k] : -1;
+        }
+        double2 vv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) vv[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (jv[k] >= 0) moments_point<B, F>(yv[k], vv[k], ar, ai, br, bi);
+    }
+    float4 *o = P4 + (long long)item * D;
+#pragma unroll
+    for (int d = 0; d < B; ++d) {
+        const df r = norm(ar[d]), i = norm(ai[d]);
+        o[d] = make_float4(r.h, r.l, i.h, i.l);
+    }
+#pragma unroll
+    for (int d = 0; d < F; ++d) o[B + d] = make_float4(br[d], 0.f, bi[d], 0.f);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_eval_df_small(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restrict__ Q4,
+                double2 *__restrict__ out) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= *S.n_small) return;
+    const int item = S.list_small[idx];
+    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float4 q = Q4[(long long)c * D + d];
+        if (d < B) {
+            qr[d < B ? d : 0] = mk(q.x, q.y);
+            qi[d < B ? d : 0] = mk(q.z, q.w);
+        } else {
+            fr[d >= B ? d - B : 0] = q.x;
+            fi[d >= B ? d - B : 0] = q.z;
+        }
+    }
+    for (int p0 = pb; p0 < pe; p0 += 4) {
+        float2 yv[4];
+        int jv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yv[k] = p0 + k < pe ? ys2[p0 + k] : make_float2(0.f, 0.f);
+            jv[k] = p0 + k < pe ? S.perm[p0 + k] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (jv[k] >= 0) out[jv[k]] = eval_point<B, F>(yv[k], qr, qi, fr, fi);
     }
 }
 
@@ -367,6 +441,10 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     }
     count_launches(1);
+    if (S.list_small) {
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_small<DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(S, y2, v, o)));
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 
@@ -377,6 +455,12 @@ cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, cu
                                S, reinterpret_cast<const float2 *>(S.ys),
                                static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
     count_launches(1);
+    if (S.list_small) {
+        NNFFT_DISPATCH_DF(S.D, (k_eval_df_small<DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(
+                                   S, reinterpret_cast<const float2 *>(S.ys),
+                                   static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -73,6 +73,10 @@ struct Side {
     void *y_user = nullptr;        // coordinates in caller order (step-0 scratch)
     int *cell_off = nullptr, *item_off = nullptr, *items_scratch = nullptr;
     int *item_cell = nullptr, *item_pb = nullptr, *item_pe = nullptr, *nitems = nullptr;
+    // small-item split (sides where some instance has few points per cell)
+    bool split_items = false;     // for the current node set
+    bool split_rule = false;      // batches: some instance has few points per cell
+    int *list_small = nullptr, *list_big = nullptr, *n2 = nullptr;
     bool set = false;
 };
 
@@ -103,6 +107,9 @@ struct nnfft_plan_s {
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
     int mom_lanes[2] = {32, 32};
     int fft_variant = 0;
+    int item_split = 0;          // 1: split small work items where the size rule says so
+                                 // (off by default: the warp-per-item kernels measured faster
+                                 // on the batched workload; the autotuner may turn it on)
     nnfft_tuning tuning{};
     long long grid_total = 0;    // sum of the instances' N2
     // work buffers of a transform: [0] for exec / adjoint, [1] (allocated on first use) for
@@ -538,6 +545,18 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             return rc;
         NN_CUDA(cudaMemset(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1)), "memset");
         NN_CUDA(cudaMemset(S.nitems, 0, sizeof(int)), "memset");
+        // Small-item split when some instance expects few points per cell (a warp per item
+        // would idle most of its lanes and pay a full reduction per item); single plans
+        // decide again at every node set from their current size (nnfft_set_sizes).
+        for (int64_t i = 0; i < count && !S.split_rule; ++i) {
+            const int64_t Mi = pt_off[(size_t)i + 1] - pt_off[(size_t)i];
+            S.split_rule = Mi > 0 && Mi < 4LL * SMALL_ITEM * tab[(size_t)i].ncell;
+        }
+        if ((rc = dalloc_n(p, &S.list_small, (size_t)S.max_items, "item lists")) ||
+            (rc = dalloc_n(p, &S.list_big, (size_t)S.max_items, "item lists")) ||
+            (rc = dalloc_n(p, &S.n2, 2, "item lists")))
+            return rc;
+        NN_CUDA(cudaMemset(S.n2, 0, 2 * sizeof(int)), "memset");
     }
 
     // FFT tables: twiddles exp(-2 pi i k/n) for every distinct length, concatenated
@@ -709,6 +728,10 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     k.item_pe = S.item_pe;
     k.nitems = S.nitems;
     k.max_items = S.max_items;
+    k.list_small = S.split_items ? S.list_small : nullptr;
+    k.list_big = S.split_items ? S.list_big : nullptr;
+    k.n_small = S.split_items ? S.n2 : nullptr;
+    k.n_big = S.split_items ? S.n2 + 1 : nullptr;
     return k;
 }
 
@@ -731,9 +754,13 @@ GridLaunch<CoefT> grid_launch(const nnfft_plan_s *p, int s, bool spread, bool fo
 int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st) {
     Side &S = p->side[s];
     StageTimer timer(p, s, st);
+    if (p->ninst == 1) S.split_items = S.M > 0 && (int64_t)S.M < 4LL * SMALL_ITEM * S.ncell;
+    else S.split_items = S.split_rule;
+    S.split_items = S.split_items && p->item_split;
     if (S.M == 0) {
         NN_CUDA(cudaMemsetAsync(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1), st), "memset");
         NN_CUDA(cudaMemsetAsync(S.nitems, 0, sizeof(int), st), "memset");
+        NN_CUDA(cudaMemsetAsync(S.n2, 0, 2 * sizeof(int), st), "memset");
         S.perm = S.vals;
         S.set = true;
         return NNFFT_OK;
@@ -754,6 +781,12 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     NN_CUDA(launch_build_items_fused(S.cell_off, S.ncell, S.item_off, S.item_cell, S.item_pb,
                                      S.item_pe, S.nitems, S.items_scratch, st),
             "work items");
+    if (S.split_items) {
+        NN_CUDA(cudaMemsetAsync(S.n2, 0, 2 * sizeof(int), st), "memset");
+        NN_CUDA(launch_split_items(S.nitems, S.item_pb, S.item_pe, S.max_items, S.list_small,
+                                   S.list_big, S.n2, st),
+                "item split");
+    }
     S.set = true;
     return NNFFT_OK;
 }
@@ -1133,25 +1166,49 @@ int nnfft_exec_adjoint(nnfft_plan_t p, const void *f_dev, void *y_dev, const voi
     return ra ? ra : rf;
 }
 
-int nnfft_autotune(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,
-                   void *z_dev, int reps) {
+int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
+                   void *y_dev, const void *g_dev, void *z_dev, int reps, int flags) {
     if (!p) return fail(NNFFT_EINVAL, "null plan");
-    if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
+    const bool with_nodes = v_dev || x_dev;
+    if (with_nodes && ((p->info.M1 > 0 && !v_dev) || (p->info.M2 > 0 && !x_dev)))
+        return fail(NNFFT_EINVAL, "give both node arrays or neither");
+    if (!with_nodes && (!p->side[0].set || !p->side[1].set))
+        return fail(NNFFT_ESTATE, "nnfft_set_nodes first (or pass the nodes)");
     if (reps < 1) reps = 1;
     const bool lanes_matter = p->dbl && p->split;
     std::vector<int> lanes = lanes_matter ? std::vector<int>{32, 16} : std::vector<int>{32};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    NN_CUDA(cudaEventCreate(&e0), "event");
-    NN_CUDA(cudaEventCreate(&e1), "event");
-    // every configuration is timed in ROUNDS interleaved sweeps and keeps its best time;
-    // the default stays unless another configuration is more than 3 % faster
-    struct Cfg { int lv, lx, fv; double t; };
-    std::vector<Cfg> cfgs;
-    for (int fv = 0; fv < 2; ++fv)
-        for (int lv : lanes)
-            for (int lx : lanes) cfgs.push_back(Cfg{lv, lx, fv, 1e300});
-    constexpr int ROUNDS = 3;
+    // splitting small items changes the node-time work lists: only with the nodes given,
+    // and only where the size rule would split somewhere
+    bool split_possible = false;
+    for (int s = 0; s < 2; ++s) {
+        const Side &S = p->side[s];
+        split_possible = split_possible || S.split_rule ||
+                         (p->ninst == 1 && S.M > 0 && (int64_t)S.M < 4LL * SMALL_ITEM * S.ncell);
+    }
+    std::vector<int> splits = with_nodes && split_possible ? std::vector<int>{0, 1} : std::vector<int>{p->item_split};
+    void *flush = nullptr;
+    const size_t flush_bytes = (size_t)192 << 20;         // larger than GB300's L2
+    if ((flags & NNFFT_TUNE_FLUSH_L2) && cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;
+    }
+    std::vector<cudaEvent_t> ev(2 * (size_t)reps, nullptr);
     int rc = NNFFT_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) rc = cuda_fail(cudaGetLastError(), "event");
+    auto run = [&]() {
+        return with_nodes ? nnfft_transform(p, v_dev, x_dev, f_dev, y_dev, g_dev, z_dev)
+                          : nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev);
+    };
+    // every configuration is timed in ROUNDS interleaved sweeps and keeps its best time;
+    // the default (first entry) stays unless another configuration is more than 3 % faster
+    struct Cfg { int lv, lx, fv, sp; double t; };
+    std::vector<Cfg> cfgs;
+    for (int sp : splits)
+        for (int fv = 0; fv < 2; ++fv)
+            for (int lv : lanes)
+                for (int lx : lanes) cfgs.push_back(Cfg{lv, lx, fv, sp, 1e300});
+    constexpr int ROUNDS = 3;
     const bool timing = p->timing;
     p->timing = false;
     for (int round = 0; round < ROUNDS && !rc; ++round)
@@ -1160,34 +1217,47 @@ int nnfft_autotune(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g
             p->fft_variant = c.fv;
             p->mom_lanes[0] = c.lv;
             p->mom_lanes[1] = c.lx;
-            if ((rc = nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev))) break;   // warm-up
-            cudaEventRecord(e0, p->stream);
-            for (int r = 0; r < reps && !rc; ++r) rc = nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev);
-            cudaEventRecord(e1, p->stream);
+            p->item_split = c.sp;
+            if ((rc = run())) break;                        // warm-up (and work lists)
+            for (int r = 0; r < reps && !rc; ++r) {
+                if (flush) cudaMemsetAsync(flush, r & 1, flush_bytes, p->stream);
+                cudaEventRecord(ev[2 * r], p->stream);
+                rc = run();
+                cudaEventRecord(ev[2 * r + 1], p->stream);
+            }
             if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
+            if (cudaEventSynchronize(ev.back()) != cudaSuccess) {
                 rc = cuda_fail(cudaGetLastError(), "autotune timing");
                 break;
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            c.t = std::min(c.t, (double)ms / reps);
+            double tot = 0;
+            for (int r = 0; r < reps; ++r) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+                tot += ms;
+            }
+            c.t = std::min(c.t, tot / reps);
         }
-    const Cfg *best = &cfgs[0];                    // cfgs[0] is the default (32, 32, 0)
+    p->timing = timing;
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    if (flush) {
+        cudaStreamSynchronize(p->stream);
+        cudaFree(flush);
+    }
+    const Cfg *best = &cfgs[0];
     for (const Cfg &c : cfgs)
         if (c.t < best->t) best = &c;
     if (best->t > 0.97 * cfgs[0].t) best = &cfgs[0];
-    const double dflt = cfgs[0].t;
-    const int best_v = best->lv, best_x = best->lx, best_f = best->fv;
-    const double best_t = best->t;
-    p->timing = timing;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->fft_variant = best_f;
-    p->mom_lanes[0] = best_v;
-    p->mom_lanes[1] = best_x;
+    p->fft_variant = best->fv;
+    p->mom_lanes[0] = best->lv;
+    p->mom_lanes[1] = best->lx;
+    p->item_split = best->sp;
     if (rc) return rc;
-    p->tuning = nnfft_tuning{best_v, best_x, best_f, 1, dflt, best_t};
+    p->tuning = nnfft_tuning{best->lv, best->lx, best->fv, 1, cfgs[0].t, best->t, best->sp,
+                             with_nodes ? 1 : 0};
+    // the work lists of the current node set follow the chosen split
+    if (with_nodes && (rc = run())) return rc;
     return collect_status(p);
 }
 
@@ -1197,6 +1267,7 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
     out->moments_lanes_v = p->mom_lanes[0];
     out->moments_lanes_x = p->mom_lanes[1];
     out->fft_variant = p->fft_variant;
+    out->item_split = p->item_split;
     return NNFFT_OK;
 }
 
@@ -1204,11 +1275,15 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
     auto ok_lanes = [](int l) { return l == 16 || l == 32; };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
-        (t->fft_variant != 0 && t->fft_variant != 1))
+        (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1))
         return fail(NNFFT_EINVAL, "invalid tuning values");
     p->mom_lanes[0] = t->moments_lanes_v;
     p->mom_lanes[1] = t->moments_lanes_x;
     p->fft_variant = t->fft_variant;
+    if (t->item_split != p->item_split) {         // work lists are built with the nodes
+        p->item_split = t->item_split;
+        p->side[0].set = p->side[1].set = false;
+    }
     return NNFFT_OK;
 }
 

@@ -51,7 +51,8 @@ class ServerReport(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("moments_lanes_v", ctypes.c_int), ("moments_lanes_x", ctypes.c_int),
                 ("fft_variant", ctypes.c_int), ("tuned", ctypes.c_int),
-                ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
+                ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
+                ("item_split", ctypes.c_int), ("timed_transform", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,7 +127,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
         lib.nnfft_transform_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_transform.argtypes = [vp, vp, vp, vp, vp, vp, vp]
-        lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, cint]
+        lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, cint, cint]
         lib.nnfft_get_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_nodes_host.argtypes = [vp, vp, vp]
@@ -289,22 +290,29 @@ class Plan:
         _check(self._lib.nnfft_exec_adjoint(self._h, pf, py, pg, pz))
         return y, z
 
-    def autotune(self, f, g, y=None, z=None, reps=3) -> dict:
-        """Time the kernel variants on the current nodes and keep the fastest."""
+    def autotune(self, f, g, y=None, z=None, reps=3, v=None, x=None, flush_l2=False) -> dict:
+        """Time the kernel variants and keep the fastest: full transforms when the nodes
+        v, x are given (else exec + adjoint on the current nodes); flush_l2 writes a buffer
+        larger than L2 before every timed run."""
         import torch
         if y is None:
             y = torch.empty(self.M2, dtype=self.cdtype, device=f.device)
         if z is None:
             z = torch.empty(self.M1, dtype=self.cdtype, device=f.device)
-        _check(self._lib.nnfft_autotune(self._h, _dev_tensor(f, self.cdtype, self.M1, "f"),
+        pv = _dev_tensor(v, torch.float64, self.M1, "v") if v is not None else None
+        px = _dev_tensor(x, torch.float64, self.M2, "x") if x is not None else None
+        _check(self._lib.nnfft_autotune(self._h, pv, px, _dev_tensor(f, self.cdtype, self.M1, "f"),
                                         _dev_tensor(y, self.cdtype, self.M2, "y"),
                                         _dev_tensor(g, self.cdtype, self.M2, "g"),
-                                        _dev_tensor(z, self.cdtype, self.M1, "z"), int(reps)))
+                                        _dev_tensor(z, self.cdtype, self.M1, "z"), int(reps),
+                                        1 if flush_l2 else 0))
         return self.tuning()
 
-    def set_tuning(self, moments_lanes_v=32, moments_lanes_x=32, fft_variant=0):
-        """Apply a kernel-variant configuration (see autotune)."""
-        t = Tuning(int(moments_lanes_v), int(moments_lanes_x), int(fft_variant), 0, 0.0, 0.0)
+    def set_tuning(self, moments_lanes_v=32, moments_lanes_x=32, fft_variant=0, item_split=0):
+        """Apply a kernel-variant configuration (see autotune); a changed item_split needs
+        set_nodes again."""
+        t = Tuning(int(moments_lanes_v), int(moments_lanes_x), int(fft_variant), 0, 0.0, 0.0,
+                   int(item_split), 0)
         _check(self._lib.nnfft_set_tuning(self._h, ctypes.byref(t)))
         return self
 

@@ -417,6 +417,9 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
     assert t["tuned"] == 1 and t["moments_lanes_v"] in (16, 32) and t["moments_lanes_x"] in (16, 32)
     assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= t["default_ms"]
+    assert t["timed_transform"] == 0
+    t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
+    assert t["timed_transform"] == 1 and t["item_split"] in (0, 1)
     y1, z1 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
     y2, z2 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
     plan.sync()
@@ -441,14 +444,34 @@ def test_every_moments_and_fft_variant_is_correct():
     rows2, rows1 = W.sample_rows(M2, 48, 5), W.sample_rows(M1, 48, 6)
     want_y = oracle.nnfft_direct(N, v, f, x, rows=rows2)
     want_z = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows1)
-    for lanes in (16, 32):
-        for fv in (0, 1):
-            plan.set_tuning(lanes, lanes, fv)
-            y, z = plan.exec_adjoint(dev(f), dev(g))
-            plan.sync()
-            y, z = y.cpu().numpy(), z.cpu().numpy()
-            assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= 1e-12, (lanes, fv)
-            assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= 1e-12, (lanes, fv)
+    for lanes, fv, split in ((16, 0, 1), (16, 1, 0), (32, 0, 0), (32, 1, 1)):
+        plan.set_tuning(lanes, lanes, fv, split)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f), dev(g))
+        plan.sync()
+        y, z = y.cpu().numpy(), z.cpu().numpy()
+        assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= 1e-12, (lanes, fv)
+        assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= 1e-12, (lanes, fv)
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+def test_small_item_split_on_and_off(dtype, m, tol):
+    """Sparse nodes (few points per cell) take the one-thread-per-item kernels when
+    item_split is on; both settings give the transform within tolerance."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 4000, 3000, 5000                 # about 0.4-0.6 points per cell
+    v, x, f = W.nnfft_inputs(M1, M2, 71, dtype=npd)
+    g = W.adjoint_inputs(M2, 71, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    want_y = oracle.nnfft_direct(N, v, f.astype(np.complex128), x)
+    want_z = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128))
+    for split in (1, 0):
+        plan.set_tuning(32, 32, 0, split)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+        plan.sync()
+        assert oracle.relative_error(y.cpu().numpy().astype(np.complex128), want_y, f) <= tol
+        assert oracle.relative_error(z.cpu().numpy().astype(np.complex128), want_z, g) <= tol
 
 
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
