@@ -529,3 +529,29 @@ def test_transform_device_equals_separate_calls(dtype):
     y2, z2 = P.transform(dev(vb), dev(xb), dev(fb, dtype), dev(gb, dtype))
     P.sync()
     assert np.array_equal(y1, y2.cpu().numpy()) and np.array_equal(z1, z2.cpu().numpy())
+
+
+@pytest.mark.parametrize("sigma", [1.25, 1.5, 2.0])
+def test_figure_4_1b_protocol(sigma):
+    """The Fig. 4.1(b) experiment with the sinh window itself: N = 1200, m1 = m2 = m in
+    2..8, sigma1 = sigma2, M1 = 2400, M2 = 1600, x uniform in [-1/2, 1/2], v uniform in
+    [-1/(2a), 1/(2a)] with a = 1 + 2m/N1, complex N(0,1) coefficients; the maximum over
+    repetitions of the error eq. (relative_nnfft_error) lies below the bound E(phi_sinh)
+    of Theorem 4.1 and falls with m."""
+    N, M1, M2, reps = 1200, 2400, 1600, 4
+    worst = {}
+    for m in range(2, 9):
+        P = oracle.make_params(N, sigma, sigma, m, m)
+        a = 1.0 + 2.0 * m / P.N1
+        E, _, _ = oracle.bound_sinh(P.N1, m, m, P.sigma1, P.sigma2)
+        err = 0.0
+        for rep in range(reps):
+            rng = np.random.default_rng(1000 * m + rep)
+            x = rng.uniform(-0.5, 0.5, M2)
+            v = rng.uniform(-0.5 / a, 0.5 / a, M1)
+            f = rng.standard_normal(M1) + 1j * rng.standard_normal(M1)
+            y, _ = run_forward(N, v, x, f, m, torch.complex128, sigma=sigma)
+            err = max(err, oracle.relative_error(y, oracle.nnfft_direct(N, v, f, x), f))
+        worst[m] = err
+        assert err <= E, (sigma, m, err, E)
+    assert worst[8] < 1e-3 * worst[2]
