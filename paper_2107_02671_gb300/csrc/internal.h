@@ -207,8 +207,10 @@ cudaError_t launch_split_items(const int *nitems, const int *item_pb, const int 
 // Cell moments of vals over the sorted points, one set per work item, into P; the
 // per-cell fold (launch_cell_fold: item sum and, with S.rfit, the 1/phihat1 factor)
 // follows as its own launch.
+// lanes: 32 (one warp per work item) or 8 (four items per warp, D <= 16)
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s);
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, int lanes,
+                           cudaStream_t s);
 // Spread convolution of every instance: cell sums Pc (all cells of the side) -> grid
 // buffers out (concatenated).  Gather convolution: grid buffers buf -> per-cell window
 // sums Q.  Block counts per instance: spread_blocks / gather_blocks.
@@ -226,7 +228,8 @@ int gather_blocks_native(int ncell, int D);
 int spread_blocks_df(int N2, int D);
 int gather_blocks_df(int ncell, int D);
 template <typename Real>
-cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s);
+cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, int lanes,
+                        cudaStream_t s);
 bool supported_degree(int D);
 
 // ---- kern_spread_df.cu / kern_grid_df.cu (fp64 plans, split precision) ------------

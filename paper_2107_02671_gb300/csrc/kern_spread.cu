@@ -425,6 +425,126 @@ k_eval(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Team variants: TEAM = 8 lanes per work item, four items per warp.  For sparse cells
+// (a few dozen points per item) a whole warp per item leaves most lanes idle and pays a
+// 32-lane reduction per item; a team of 8 reduces in 3 exchange steps and every lane has
+// points.  Moments: the 2D sums (padded to 32) are reduce-scattered over the team, after
+// which lane s of the team holds sums 4s .. 4s+3 (real parts first, then imaginary).
+// ---------------------------------------------------------------------------------
+constexpr int TEAM = 8;
+
+template <typename Real, int O, int LB>
+__device__ __forceinline__ void rs_team(Real (&v)[32], int sub) {
+    const bool up = (sub & LB) != 0;
+#pragma unroll
+    for (int i = 0; i < O; ++i) {
+        const Real send = up ? v[i] : v[O + i];
+        const Real keep = up ? v[O + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, LB);
+    }
+}
+
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_moments_team(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict__ P) {
+    static_assert(2 * D <= 32, "team moments hold at most 16 degrees");
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = threadIdx.x & (TEAM - 1);
+    const int item = warp_item(S, gt / TEAM);
+    int pb = 0, pe = 0;
+    if (item >= 0) {                                 // every lane stays for the exchanges
+        pb = S.item_pb[item];
+        pe = S.item_pe[item];
+    }
+    Real ar[D], ai[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
+    for (int c0 = pb; c0 < pe; c0 += TEAM * PPL) {
+        Real yv[PPL];
+        int jv[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const int p = c0 + sub + TEAM * k;
+            yv[k] = p < pe ? S.ys[p] : Real(0);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+        C2<Real> fv[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) fv[k] = jv[k] >= 0 ? vals[jv[k]] : mk2<Real>(Real(0), Real(0));
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            if (jv[k] < 0) continue;
+            Real T[D];
+            cheb<Real, D>(yv[k], T);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                ar[d] = fma(fv[k].x, T[d], ar[d]);
+                ai[d] = fma(fv[k].y, T[d], ai[d]);
+            }
+        }
+    }
+    Real vv[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) vv[i] = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        vv[d] = ar[d];
+        vv[D + d] = ai[d];
+    }
+    rs_team<Real, 16, 4>(vv, sub);
+    rs_team<Real, 8, 2>(vv, sub);
+    rs_team<Real, 4, 1>(vv, sub);
+    if (item < 0) return;
+    Real *Pr = reinterpret_cast<Real *>(P + (long long)item * D);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int idx = 4 * sub + t;
+        if (idx < D) Pr[2 * idx] = vv[t];
+        else if (idx < 2 * D) Pr[2 * (idx - D) + 1] = vv[t];
+    }
+}
+
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_eval_team(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = threadIdx.x & (TEAM - 1);
+    const int item = warp_item(S, gt / TEAM);
+    if (item < 0) return;
+    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
+    Real qr[D], qi[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const C2<Real> q = Q[(long long)c * D + d];
+        qr[d] = q.x;
+        qi[d] = q.y;
+    }
+    for (int c0 = pb; c0 < pe; c0 += TEAM * PPL) {
+        Real yv[PPL];
+        int jv[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const int p = c0 + sub + TEAM * k;
+            yv[k] = p < pe ? S.ys[p] : Real(0);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            if (jv[k] < 0) continue;
+            Real T[D];
+            cheb<Real, D>(yv[k], T);
+            Real sr = Real(0), si = Real(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                sr = fma(qr[d], T[d], sr);
+                si = fma(qi[d], T[d], si);
+            }
+            out[jv[k]] = mk2<Real>(sr, si);
+        }
+    }
+}
+
 // Point evaluation of small work items: one thread per item.
 template <typename Real, int D>
 __global__ void __launch_bounds__(256)
@@ -496,12 +616,18 @@ cudaError_t launch_cell_fold(const SideK<Real> &S, const void *P, void *Pc, cuda
 }
 
 template <typename Real>
-cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, cudaStream_t s) {
+cudaError_t launch_moments(const SideK<Real> &S, const void *vals, void *P, int lanes,
+                           cudaStream_t s) {
     if (S.max_items <= 0) return cudaSuccess;
-    const int blocks = cdiv((long long)S.max_items * 32, 256);
     const C2<Real> *v = static_cast<const C2<Real> *>(vals);
     C2<Real> *Pp = static_cast<C2<Real> *>(P);
-    NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
+    if (lanes == TEAM && S.D <= 16) {
+        const int blocks = cdiv((long long)S.max_items * TEAM, 256);
+        NNFFT_DISPATCH_D(S.D, (k_moments_team<Real, (DD <= 16 ? DD : 16)><<<blocks, 256, 0, s>>>(S, v, Pp)));
+    } else {
+        const int blocks = cdiv((long long)S.max_items * 32, 256);
+        NNFFT_DISPATCH_D(S.D, (k_moments<Real, DD><<<blocks, 256, 0, s>>>(S, v, Pp)));
+    }
     count_launches(1);
     if (S.list_small) {
         NNFFT_DISPATCH_D(S.D, (k_moments_small<Real, DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(S, v, Pp)));
@@ -540,12 +666,18 @@ cudaError_t launch_gather_conv(const GridLaunch<Real> &L, const void *buf, void 
 }
 
 template <typename Real>
-cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStream_t s) {
+cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, int lanes,
+                        cudaStream_t s) {
     if (S.max_items <= 0) return cudaSuccess;
-    const int blocks = cdiv((long long)S.max_items * 32, 256);
     const C2<Real> *q = static_cast<const C2<Real> *>(Q);
     C2<Real> *o = static_cast<C2<Real> *>(out);
-    NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));
+    if (lanes == TEAM) {
+        const int blocks = cdiv((long long)S.max_items * TEAM, 256);
+        NNFFT_DISPATCH_D(S.D, (k_eval_team<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));
+    } else {
+        const int blocks = cdiv((long long)S.max_items * 32, 256);
+        NNFFT_DISPATCH_D(S.D, (k_eval<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));
+    }
     count_launches(1);
     if (S.list_small) {
         NNFFT_DISPATCH_D(S.D, (k_eval_small<Real, DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(S, q, o)));
@@ -555,7 +687,7 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
 }
 
 #define NNFFT_INST(R)                                                                      \
-    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *,         \
+    template cudaError_t launch_moments<R>(const SideK<R> &, const void *, void *, int,    \
                                            cudaStream_t);                                  \
     template cudaError_t launch_spread_conv<R>(const GridLaunch<R> &, const void *, void *, \
                                                cudaStream_t);                              \
@@ -563,7 +695,8 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, cudaStre
                                                cudaStream_t);                              \
     template cudaError_t launch_cell_fold<R>(const SideK<R> &, const void *, void *,       \
                                              cudaStream_t);                                \
-    template cudaError_t launch_eval<R>(const SideK<R> &, const void *, void *, cudaStream_t);
+    template cudaError_t launch_eval<R>(const SideK<R> &, const void *, void *, int,       \
+                                        cudaStream_t);
 
 NNFFT_INST(double)
 NNFFT_INST(float)

@@ -105,7 +105,8 @@ struct nnfft_plan_s {
     FftLaunch<FftPlanDev> fft[2]{};   // two column packings (see build_plan)
     FftLaunch<FftDf> fftdf[2]{};
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
-    int mom_lanes[2] = {32, 32};
+    int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision) or 8 (all-real)
+    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 (all-real kernels)
     int fft_variant = 0;
     int item_split = 0;          // 1: split small work items where the size rule says so
                                  // (off by default: the warp-per-item kernels measured faster
@@ -875,7 +876,7 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
     const SideK<Real> sx = side_args<Real>(X, true);
     {
         StageTimer t(p, 2, st);
-        NN_CUDA(launch_moments<Real>(sv, f, W.P, st), "spread moments");
+        NN_CUDA(launch_moments<Real>(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
     }
     {
         StageTimer t(p, 12, st);
@@ -899,7 +900,7 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
     }
     {
         StageTimer t(p, 6, st);
-        NN_CUDA(launch_eval<Real>(sx, W.Q, y, st), "gather evaluation");
+        NN_CUDA(launch_eval<Real>(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -913,7 +914,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     const SideK<Real> sx = side_args<Real>(X, true);
     {
         StageTimer t(p, 7, st);
-        NN_CUDA(launch_moments<Real>(sx, g, W.P, st), "adjoint spread moments");
+        NN_CUDA(launch_moments<Real>(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
     }
     {
         StageTimer t(p, 13, st);
@@ -936,7 +937,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     }
     {
         StageTimer t(p, 11, st);
-        NN_CUDA(launch_eval<Real>(sv, W.Q, z, st), "adjoint gather evaluation");
+        NN_CUDA(launch_eval<Real>(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -1175,8 +1176,12 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     if (!with_nodes && (!p->side[0].set || !p->side[1].set))
         return fail(NNFFT_ESTATE, "nnfft_set_nodes first (or pass the nodes)");
     if (reps < 1) reps = 1;
-    const bool lanes_matter = p->dbl && p->split;
-    std::vector<int> lanes = lanes_matter ? std::vector<int>{32, 16} : std::vector<int>{32};
+    // moments lanes per item: 32/16 for the split-precision kernels, 32/8 for the all-real
+    // ones (D <= 16); evaluation lanes 32/8 for the all-real kernels
+    const bool dfk = p->dbl && p->split;
+    const bool small_d = p->side[0].D <= 16 && p->side[1].D <= 16;
+    std::vector<int> lanes = dfk ? std::vector<int>{32, 16} : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
+    std::vector<int> elanes = dfk ? std::vector<int>{32} : std::vector<int>{32, 8};
     // splitting small items changes the node-time work lists: only with the nodes given,
     // and only where the size rule would split somewhere
     bool split_possible = false;
@@ -1202,12 +1207,13 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     };
     // every configuration is timed in ROUNDS interleaved sweeps and keeps its best time;
     // the default (first entry) stays unless another configuration is more than 3 % faster
-    struct Cfg { int lv, lx, fv, sp; double t; };
+    struct Cfg { int lv, lx, el, fv, sp; double t; };
     std::vector<Cfg> cfgs;
     for (int sp : splits)
         for (int fv = 0; fv < 2; ++fv)
-            for (int lv : lanes)
-                for (int lx : lanes) cfgs.push_back(Cfg{lv, lx, fv, sp, 1e300});
+            for (int el : elanes)
+                for (int lv : lanes)
+                    for (int lx : lanes) cfgs.push_back(Cfg{lv, lx, el, fv, sp, 1e300});
     constexpr int ROUNDS = 3;
     const bool timing = p->timing;
     p->timing = false;
@@ -1217,6 +1223,7 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
             p->fft_variant = c.fv;
             p->mom_lanes[0] = c.lv;
             p->mom_lanes[1] = c.lx;
+            p->eval_lanes[0] = p->eval_lanes[1] = c.el;
             p->item_split = c.sp;
             if ((rc = run())) break;                        // warm-up (and work lists)
             for (int r = 0; r < reps && !rc; ++r) {
@@ -1252,10 +1259,11 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     p->fft_variant = best->fv;
     p->mom_lanes[0] = best->lv;
     p->mom_lanes[1] = best->lx;
+    p->eval_lanes[0] = p->eval_lanes[1] = best->el;
     p->item_split = best->sp;
     if (rc) return rc;
     p->tuning = nnfft_tuning{best->lv, best->lx, best->fv, 1, cfgs[0].t, best->t, best->sp,
-                             with_nodes ? 1 : 0};
+                             with_nodes ? 1 : 0, best->el, best->el};
     // the work lists of the current node set follow the chosen split
     if (with_nodes && (rc = run())) return rc;
     return collect_status(p);
@@ -1268,17 +1276,23 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
     out->moments_lanes_x = p->mom_lanes[1];
     out->fft_variant = p->fft_variant;
     out->item_split = p->item_split;
+    out->eval_lanes_v = p->eval_lanes[0];
+    out->eval_lanes_x = p->eval_lanes[1];
     return NNFFT_OK;
 }
 
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
-    auto ok_lanes = [](int l) { return l == 16 || l == 32; };
+    auto ok_lanes = [](int l) { return l == 8 || l == 16 || l == 32; };
+    auto ok_elanes = [](int l) { return l == 0 || l == 8 || l == 32; };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
+        !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
         (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1))
         return fail(NNFFT_EINVAL, "invalid tuning values");
     p->mom_lanes[0] = t->moments_lanes_v;
     p->mom_lanes[1] = t->moments_lanes_x;
+    p->eval_lanes[0] = t->eval_lanes_v ? t->eval_lanes_v : 32;
+    p->eval_lanes[1] = t->eval_lanes_x ? t->eval_lanes_x : 32;
     p->fft_variant = t->fft_variant;
     if (t->item_split != p->item_split) {         // work lists are built with the nodes
         p->item_split = t->item_split;

@@ -555,3 +555,28 @@ def test_figure_4_1b_protocol(sigma):
         worst[m] = err
         assert err <= E, (sigma, m, err, E)
     assert worst[8] < 1e-3 * worst[2]
+
+
+@pytest.mark.parametrize("dtype,arith,m,tol", [(torch.complex64, None, 4, 2e-5),
+                                               (torch.complex128, "fp64", 8, 1e-12)])
+@pytest.mark.parametrize("N,M1,M2", [(300, 40000, 30000), (3000, 2500, 3500)])
+def test_team_kernels_eight_lanes_per_item(dtype, arith, m, tol, N, M1, M2):
+    """The all-real moments and evaluation kernels with 8 lanes per work item (four items
+    per warp) against the direct sums, dense (~60 points per cell) and sparse (< 1)."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, f = W.nnfft_inputs(M1, M2, 81, dtype=npd)
+    g = W.adjoint_inputs(M2, 81, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    if arith == "fp64":
+        plan.set_arith(B.ARITH_FP64)
+    rows2, rows1 = W.sample_rows(M2, 64, 7), W.sample_rows(M1, 64, 8)
+    want_y = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows2)
+    want_z = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows1)
+    for ml, el in ((8, 8), (8, 32), (32, 8)):
+        plan.set_tuning(ml, ml, 0, 0, el, el)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+        plan.sync()
+        y, z = y.cpu().numpy().astype(np.complex128), z.cpu().numpy().astype(np.complex128)
+        assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= tol, (ml, el)
+        assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= tol, (ml, el)
