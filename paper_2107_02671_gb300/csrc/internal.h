@@ -236,10 +236,12 @@ bool supported_degree(int D);
 // S.ys holds float2 (hi, lo) coordinates; degrees < D/2 in double-float, the rest FP32;
 // all intermediate complex arrays are float4 (re.h, re.l, im.h, im.l).
 bool df_supported_degree(int D);
-// lanes: 32 (one warp per work item) or 16 (two items per warp); the plan's autotuner picks.
+// lanes: 32 (one warp per work item), 16 (two items per warp) or 8 (four items per warp);
+// the plan's autotuner picks.  Evaluation: 32 or 8.
 cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4, int lanes,
                               cudaStream_t s);
-cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, cudaStream_t s);
+cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, int lanes,
+                           cudaStream_t s);
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
                                 void *Pc4, cudaStream_t s);
 cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,

@@ -330,6 +330,133 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
 }
 
 // ---------------------------------------------------------------------------------
+// Team kernels: DTEAM = 8 lanes per work item, four items per warp (sparse cells).
+// Moments use the slot layout of the half-warp kernel; three exchange steps over slot
+// bits 3..1 leave lane s with slots j = 2s and 2s+1 of each kind.
+// ---------------------------------------------------------------------------------
+constexpr int DTEAM = 8;
+
+template <int O, int LB>
+__device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int sub) {
+    const bool up = (sub & LB) != 0;
+#pragma unroll
+    for (int i = 0; i < O; ++i) {
+        const df send = up ? vd[i] : vd[O + i];
+        const df keep = up ? vd[O + i] : vd[i];
+        df other;
+        other.h = __shfl_xor_sync(0xffffffffu, send.h, LB);
+        other.l = __shfl_xor_sync(0xffffffffu, send.l, LB);
+        vd[i] = add(keep, other);
+        const float fs = up ? vf[i] : vf[O + i];
+        const float fk = up ? vf[O + i] : vf[i];
+        vf[i] = fk + __shfl_xor_sync(0xffffffffu, fs, LB);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
+                  float4 *__restrict__ P4) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    static_assert(B <= 8 && F <= 8, "the slot layout holds at most 8 degrees of each kind");
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = big_item(S, gt / DTEAM);
+    const int sub = threadIdx.x & (DTEAM - 1);
+    int pb = 0, pe = 0;
+    if (item >= 0) {                                 // every lane stays for the exchanges
+        pb = S.item_pb[item];
+        pe = S.item_pe[item];
+    }
+    df ar[B], ai[B];
+    float br[F], bi[F];
+#pragma unroll
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
+    for (int c0 = pb; c0 < pe; c0 += DTEAM * MOM_CHUNK) {
+        float2 yv[MOM_CHUNK];
+        int jv[MOM_CHUNK];
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) {
+            const int p = c0 + sub + DTEAM * k;
+            yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+        double2 vv2[MOM_CHUNK];
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) vv2[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k)
+            if (jv[k] >= 0) moments_point<B, F>(yv[k], vv2[k], ar, ai, br, bi);
+    }
+    df vd[16];
+    float vf[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
+#pragma unroll
+    for (int d = 0; d < B; ++d) {
+        vd[d] = norm(ar[d]);
+        vd[8 + d] = norm(ai[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        vf[d] = br[d];
+        vf[8 + d] = bi[d];
+    }
+    rs_mixed_team<8, 4>(vd, vf, sub);
+    rs_mixed_team<4, 2>(vd, vf, sub);
+    rs_mixed_team<2, 1>(vd, vf, sub);
+    if (item < 0) return;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int j = 2 * sub + t, deg = j & 7, part = j >> 3;   // part 0: real, 1: imaginary
+        if (deg < B) P2[2 * deg + part] = make_float2(vd[t].h, vd[t].l);
+        if (deg < F) P2[2 * (B + deg) + part] = make_float2(vf[t], 0.f);
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256)
+k_eval_df_team(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restrict__ Q4,
+               double2 *__restrict__ out) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = big_item(S, gt / DTEAM);
+    const int sub = threadIdx.x & (DTEAM - 1);
+    if (item < 0) return;
+    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float4 q = Q4[(long long)c * D + d];
+        if (d < B) {
+            qr[d < B ? d : 0] = mk(q.x, q.y);
+            qi[d < B ? d : 0] = mk(q.z, q.w);
+        } else {
+            fr[d >= B ? d - B : 0] = q.x;
+            fi[d >= B ? d - B : 0] = q.z;
+        }
+    }
+    for (int c0 = pb; c0 < pe; c0 += DTEAM * MOM_CHUNK) {
+        float2 yv[MOM_CHUNK];
+        int jv[MOM_CHUNK];
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k) {
+            const int p = c0 + sub + DTEAM * k;
+            yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+            jv[k] = p < pe ? S.perm[p] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < MOM_CHUNK; ++k)
+            if (jv[k] >= 0) out[jv[k]] = eval_point<B, F>(yv[k], qr, qi, fr, fi);
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Small work items (<= SMALL_ITEM points): one thread per item walks its points in
 // order; moments go out without any reduction, values straight to the caller's order.
 // ---------------------------------------------------------------------------------
@@ -436,6 +563,9 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
     if (lanes == MOM_LANES) {
         const int blocks = cdiv((long long)S.max_items * MOM_LANES, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_half<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+    } else if (lanes == DTEAM) {
+        const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     } else {
         const int blocks = cdiv((long long)S.max_items * 32, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
@@ -448,12 +578,20 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, cudaStream_t s) {
+cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, int lanes,
+                           cudaStream_t s) {
     if (S.max_items <= 0) return cudaSuccess;
-    const int blocks = cdiv((long long)S.max_items * 32, 256);
-    NNFFT_DISPATCH_DF(S.D, (k_eval_df<DD><<<blocks, 256, 0, s>>>(
-                               S, reinterpret_cast<const float2 *>(S.ys),
-                               static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+    if (lanes == DTEAM) {
+        const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_eval_df_team<DD><<<blocks, 256, 0, s>>>(
+                                   S, reinterpret_cast<const float2 *>(S.ys),
+                                   static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+    } else {
+        const int blocks = cdiv((long long)S.max_items * 32, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_eval_df<DD><<<blocks, 256, 0, s>>>(
+                                   S, reinterpret_cast<const float2 *>(S.ys),
+                                   static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+    }
     count_launches(1);
     if (S.list_small) {
         NNFFT_DISPATCH_DF(S.D, (k_eval_df_small<DD><<<cdiv(S.max_items, 256), 256, 0, s>>>(

@@ -105,8 +105,8 @@ struct nnfft_plan_s {
     FftLaunch<FftPlanDev> fft[2]{};   // two column packings (see build_plan)
     FftLaunch<FftDf> fftdf[2]{};
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
-    int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision) or 8 (all-real)
-    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 (all-real kernels)
+    int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
+    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8
     int fft_variant = 0;
     int item_split = 0;          // 1: split small work items where the size rule says so
                                  // (off by default: the warp-per-item kernels measured faster
@@ -825,7 +825,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     }
     {
         StageTimer t(p, 6, st);
-        NN_CUDA(launch_eval_df(sx, W.Q, y, st), "gather evaluation");
+        NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -862,7 +862,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     }
     {
         StageTimer t(p, 11, st);
-        NN_CUDA(launch_eval_df(sv, W.Q, z, st), "adjoint gather evaluation");
+        NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
     }
     return NNFFT_OK;
 }
@@ -1180,8 +1180,8 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // ones (D <= 16); evaluation lanes 32/8 for the all-real kernels
     const bool dfk = p->dbl && p->split;
     const bool small_d = p->side[0].D <= 16 && p->side[1].D <= 16;
-    std::vector<int> lanes = dfk ? std::vector<int>{32, 16} : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
-    std::vector<int> elanes = dfk ? std::vector<int>{32} : std::vector<int>{32, 8};
+    std::vector<int> lanes = dfk ? std::vector<int>{32, 16, 8} : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
+    std::vector<int> elanes{32, 8};
     // splitting small items changes the node-time work lists: only with the nodes given,
     // and only where the size rule would split somewhere
     bool split_possible = false;
@@ -1209,11 +1209,10 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // the default (first entry) stays unless another configuration is more than 3 % faster
     struct Cfg { int lv, lx, el, fv, sp; double t; };
     std::vector<Cfg> cfgs;
-    for (int sp : splits)
-        for (int fv = 0; fv < 2; ++fv)
+    for (int sp : splits)            // lanes tuned jointly for both sides (nnfft_set_tuning
+        for (int fv = 0; fv < 2; ++fv)  // can still set them per side)
             for (int el : elanes)
-                for (int lv : lanes)
-                    for (int lx : lanes) cfgs.push_back(Cfg{lv, lx, el, fv, sp, 1e300});
+                for (int l : lanes) cfgs.push_back(Cfg{l, l, el, fv, sp, 1e300});
     constexpr int ROUNDS = 3;
     const bool timing = p->timing;
     p->timing = false;

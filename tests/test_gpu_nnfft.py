@@ -444,8 +444,9 @@ def test_every_moments_and_fft_variant_is_correct():
     rows2, rows1 = W.sample_rows(M2, 48, 5), W.sample_rows(M1, 48, 6)
     want_y = oracle.nnfft_direct(N, v, f, x, rows=rows2)
     want_z = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows1)
-    for lanes, fv, split in ((16, 0, 1), (16, 1, 0), (32, 0, 0), (32, 1, 1)):
-        plan.set_tuning(lanes, lanes, fv, split)
+    for lanes, fv, split, el in ((16, 0, 1, 32), (16, 1, 0, 8), (32, 0, 0, 32), (32, 1, 1, 8),
+                                 (8, 0, 0, 8), (8, 1, 1, 32)):
+        plan.set_tuning(lanes, lanes, fv, split, el, el)
         plan.set_nodes(dev(v), dev(x))
         y, z = plan.exec_adjoint(dev(f), dev(g))
         plan.sync()
