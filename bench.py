@@ -39,6 +39,23 @@ WORKLOAD = ("nnfft_fp64 N=4096 M1=M2=2^20 uniform nodes sigma=2 m=8: "
             "set_nodes + forward + adjoint per step")
 
 
+def nvtx_push(name):
+    """Open an NVTX range (profilers filter launches on it); a no-op without NVTX."""
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -292,9 +309,9 @@ def run_batched(args, rank, dev, flush, timed, pk):
             step()
         P.sync()
         k = max(3, min(20, args.steps // 10))
-        ms_full, l_full, _ = timed(step, k)
+        ms_full, l_full, _ = timed(step, k, label="batched_step")
         P.sync()
-        ms_exec, _, _ = timed(fwd_adj, k)
+        ms_exec, _, _ = timed(fwd_adj, k, label="batched_exec")
         P.sync()
 
         def step_seq(P=P, vd=vd, xd=xd, fd=fd, gd=gd, y=y, z=z):
@@ -303,7 +320,7 @@ def run_batched(args, rank, dev, flush, timed, pk):
             P.adjoint(gd, z)
         # per-stage times (and kernel HBM fractions) from a pass with the two directions
         # one after the other: in the timed step they share the GPU
-        _, _, st = timed(step_seq, k, P)
+        _, _, st = timed(step_seq, k, P, label="batched_seq")
         P.sync()
         stage = {kk: round(1e3 * tot / n, 1) for kk, (tot, n) in st.items() if n}
         hbm = {}
@@ -484,8 +501,9 @@ def run_ours(args, rank, world):
         # overlap (each direction waits for the other side's sort only before its gather)
         p.transform(vv, xx, ff, gg, yy, zz)
 
-    def timed(stepfn, k, pl=None, flush_l2=True):
-        """Per-step CUDA-event timing on the plan stream, L2 flushed between steps."""
+    def timed(stepfn, k, pl=None, flush_l2=True, label="timed"):
+        """Per-step CUDA-event timing on the plan stream, L2 flushed between steps.  The
+        region is an NVTX range named `label`, so a profiler can filter on it."""
         evs = []
         torch.cuda.synchronize()
         barrier()
@@ -493,6 +511,7 @@ def run_ours(args, rank, world):
             pl.timing(True)
             pl.timing_read(reset=True)
         l0 = B.launch_count()
+        nvtx_push(label)
         for _ in range(k):
             if flush_l2:
                 flush.zero_()
@@ -502,6 +521,7 @@ def run_ours(args, rank, world):
             stepfn()
             b.record(stream)
             evs.append((a, b))
+        nvtx_pop()
         torch.cuda.synchronize()
         launches = B.launch_count() - l0
         barrier()
@@ -525,13 +545,17 @@ def run_ours(args, rank, world):
         return 0
 
     # kernel variants picked by the library's autotuner on this node set (outside timing)
-    tuning = plan.autotune(fd, gd, y, z, reps=3, v=vd, x=xd, flush_l2=True)
+    if args.tuning:              # a configuration kept from an earlier run (profiling runs)
+        plan.set_tuning(*args.tuning)
+        tuning = plan.tuning()
+    else:
+        tuning = plan.autotune(fd, gd, y, z, reps=3, v=vd, x=xd, flush_l2=True)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     plan.sync()
     with ClockSampler(local) as clk:
-        ms, launches, stages = timed(step, args.steps, plan)
+        ms, launches, stages = timed(step, args.steps, plan, label="headline")
     plan.sync()
     pts_step = 2 * (M_PTS + M_PTS)
     total_ms, value = whole_job_value(float(np.sum(ms)), args.steps, pts_step, world, dev)
@@ -557,7 +581,7 @@ def run_ours(args, rank, world):
         p.set_nodes(vv, xx)
         p.exec(ff, yy)
         p.adjoint(gg, zz)
-    ms_seq, _, stages_seq = timed(step_seq, max(3, args.steps // 2), plan)
+    ms_seq, _, stages_seq = timed(step_seq, max(3, args.steps // 2), plan, label="headline_seq")
     plan.sync()
     stage_ms = {k: (tot / max(n, 1), n) for k, (tot, n) in stages_seq.items() if n}
     # dominant single kernel: the node stages (binning + radix sort) and the FFT are several
@@ -742,6 +766,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--tuning", type=lambda t: [int(u) for u in t.split(",")], default=None,
+                    help="headline kernel variants instead of autotuning: moments lanes v,x, "
+                         "fft variant, item split, evaluation lanes v,x (e.g. 8,8,0,0,1,1)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served mixed stream")
     ap.add_argument("--only-served", action="store_true",
                     help="run only the served mixed stream and print its numbers")

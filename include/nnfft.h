@@ -170,8 +170,8 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
  * Autotuning (the paper has no counterpart).  nnfft_autotune times the plan's kernel
  * variants with the caller's buffers and keeps the fastest: threads per work item of the
  * moments kernel on each side (32: one warp per item; 16: two items per warp in the
- * split-precision kernel; 8: four items per warp in the all-real kernels) and of the
- * all-real evaluation kernel (32 or 8), the FFT's packing of short columns into blocks (variant 0 by the plan-size rule,
+ * split-precision kernel; 8: four items per warp) and of the evaluation kernel (32 or 8
+ * per item, or 1: one thread per sorted point with no work items), the FFT's packing of short columns into blocks (variant 0 by the plan-size rule,
  * variant 1 the other extreme) and, when the nodes are given, whether work items of at
  * most 16 points run one thread per item (item_split; only tried where some instance has
  * few points per cell).  With v and x (device) every run is a full nnfft_transform; with
@@ -184,19 +184,19 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
  */
 enum { NNFFT_TUNE_FLUSH_L2 = 1 };
 typedef struct {
-    int moments_lanes_v, moments_lanes_x;   /* 32 or 16 */
+    int moments_lanes_v, moments_lanes_x;   /* 32, 16 or 8 */
     int fft_variant;                        /* 0 or 1 */
     int tuned;                              /* 1 after nnfft_autotune */
     double default_ms, best_ms;             /* per run: default and chosen config */
     int item_split;                         /* 1: small work items one thread each (default 0) */
     int timed_transform;                    /* 1: runs were full transforms */
-    int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8 */
+    int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8; 1 = flat */
 } nnfft_tuning;
 int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
                    void *y_dev, const void *g_dev, void *z_dev, int reps, int flags);
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
- * moments_lanes_v / _x in {8, 16, 32}, eval_lanes_v / _x in {8, 32} (0: 32), fft_variant in
+ * moments_lanes_v / _x in {8, 16, 32}, eval_lanes_v / _x in {1, 8, 32} (0: 32), fft_variant in
  * {0, 1}, item_split in {0, 1}; the other fields are ignored (a lane count a kernel does not
  * have runs as one warp per item).  EINVAL otherwise.  Takes effect for the work queued next; a changed
  * item_split needs nnfft_set_nodes again. */

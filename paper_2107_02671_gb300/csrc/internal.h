@@ -60,7 +60,13 @@ template <typename Real> struct SideK {
     // *n_small) run one thread per item, the others (list_big, *n_big) one warp per item;
     // nullptr lists: every item runs one warp per item
     const int *list_small, *list_big, *n_small, *n_big;
+    // sorted cell index of every point ([M], ascending) and the active point count, for
+    // the flat (one thread per point) evaluation kernels
+    const uint32_t *keys;
+    int M;
 };
+// Evaluation lanes value that selects the flat kernels: one thread per sorted point.
+constexpr int EVAL_FLAT = 1;
 // Largest work item handled by one thread (no reduction) when a plan splits items.
 constexpr int SMALL_ITEM = 16;
 
@@ -156,6 +162,12 @@ __device__ __forceinline__ int block_instance(const int *blk, int ninst, int b) 
 }
 
 // ---- nnfft_host.cu (for the other translation units) -------------------------------
+// Streaming multiprocessors of the current device (cached per device).
+int device_sm_count();
+// Grid-stage kernels with two thread layouts (degree-major: one warp per degree, many
+// warps for small grids; position-major: one thread per position, fewer instructions)
+// take the position-major one from this many blocks per SM on.
+constexpr int POS_MAJOR_BLOCKS_PER_SM = 16;
 // Record a status code and message for nnfft_last_error; returns code.
 int report_error(int code, const std::string &msg);
 // The stream a plan was created with.

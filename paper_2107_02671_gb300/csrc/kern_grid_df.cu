@@ -70,102 +70,186 @@ k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
 // Spread convolution.  Grid position p = p_lo + i (centered; the taps of all cells
 // cover [p_lo, p_hi], never wider than N2) goes to buffer index p mod N2:
 //   g_p = scale(p) * sum_t sum_d coef[t][d] * Pc_{p+m-1-t}[d],  0 beyond p_hi.
-// A block handles PPB consecutive positions of one instance with one thread per
-// (position, degree d): the d-th partial sum over the taps, then the D partials of a
-// position are added in shared memory.  The block's cells are staged in shared memory.
+// A block handles SCP = 32 consecutive positions of one instance with one warp per
+// Chebyshev degree d (lane = position): every warp takes one arithmetic path
+// (double-float for d < D/2, FP32 above), reads its tap coefficients as broadcasts and
+// consecutive staged cells ([D][SCP + 2m - 1] in shared memory), and there are D warps
+// per 32 positions to hide the latency of the accumulation chains.  Warp 0 then adds
+// the D partial sums of its position in the order d = D-1, ..., 0 and applies the
+// deconvolution factor.
 // ---------------------------------------------------------------------------------
-constexpr int SCD_THREADS = 128;
+constexpr int SCP = 32;
 
 template <int D>
-__global__ void __launch_bounds__(SCD_THREADS)
+__global__ void __launch_bounds__(512)
 k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
                  float4 *__restrict__ out_all) {
     constexpr int B = D / 2;
-    constexpr int PPB = SCD_THREADS / D;                       // positions per block
+    constexpr int NT = D * SCP;
     extern __shared__ float4 smem4[];
     const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
     const GridInst<float2> G = L.inst[inst];
     const float4 *__restrict__ Pc4 = Pc_all + (long long)G.cell_base * D;
     float4 *__restrict__ out = out_all + G.grid_base;
-    const float2 *__restrict__ scale = G.scale;
-    const long long scale_off = G.scale_off, scale_len = G.scale_len;
     const int N2 = G.N2;
     const int m = L.m, ntap = 2 * L.m;
-    const int ncl = PPB + ntap - 1;
-    float4 *Ps = smem4;                                           // [D][ncl] staged cells
-    float4 *part = smem4 + D * ncl;                               // [PPB][D] partial sums
-    float2 *coef = reinterpret_cast<float2 *>(part + PPB * D);   // [ntap][D]
+    const int ncl = SCP + ntap - 1;
+    float4 *Ps = smem4;                                          // [D][ncl] staged cells
+    float4 *part = Ps + D * ncl;                                 // [D][SCP] partial sums
+    float2 *coef = reinterpret_cast<float2 *>(part + D * SCP);  // [ntap][D]
     const long long p_lo = G.c_lo - m + 1, p_hi = G.c_lo + G.ncell - 1 + m;
-    const long long i0 = (long long)(blockIdx.x - L.blk[inst]) * PPB;
+    const long long i0 = (long long)(blockIdx.x - L.blk[inst]) * SCP;
     const long long p0 = p_lo + i0;
-    if (p0 > p_hi) {                                              // zero padding only
-        for (int k = threadIdx.x; k < PPB; k += SCD_THREADS) {
-            const long long i = i0 + k;
-            if (i < N2) {
-                out[wrap_index(p_lo + i, N2)] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
+    const int k = threadIdx.x & (SCP - 1), d = threadIdx.x / SCP;   // position, degree
+    const long long i = i0 + k;
+    if (p0 > p_hi) {                                             // zero padding only
+        if (d == 0 && i < N2) out[wrap_index(p_lo + i, N2)] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     const long long cbase = p0 - m;
-    for (int i = threadIdx.x; i < ntap * D; i += SCD_THREADS) coef[i] = G.coef[i];
-    for (int i = threadIdx.x; i < ncl * D; i += SCD_THREADS) {
-        const int lc = i / D, d = i - lc * D;
+    for (int e = threadIdx.x; e < ntap * D; e += NT) coef[e] = G.coef[e];
+    for (int e = threadIdx.x; e < ncl * D; e += NT) {
+        const int lc = e / D, dd = e - lc * D;
+        const long long ic = cbase + lc - G.c_lo;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ic >= 0 && ic < G.ncell) v = Pc4[ic * D + dd];
+        Ps[dd * ncl + lc] = v;
+    }
+    __syncthreads();
+    const int lbase = k + ntap - 1;
+    const float4 *Pd = Ps + d * ncl + lbase;
+    cdf g;
+    if (d < B) {                                                 // warp-uniform branch
+        df ar = mk(0.f), ai = mk(0.f);
+        for (int t = 0; t < ntap; ++t) {
+            const float4 pv = Pd[-t];
+            const float2 c2 = coef[t * D + d];
+            const df cd = mk(c2.x, c2.y);
+            acc(ar, mul_u(cd, mk(pv.x, pv.y)));
+            acc(ai, mul_u(cd, mk(pv.z, pv.w)));
+        }
+        g.re = norm(ar);
+        g.im = norm(ai);
+    } else {
+        float fr = 0.f, fi = 0.f;
+        for (int t = 0; t < ntap; ++t) {
+            const float4 pv = Pd[-t];
+            const float c = coef[t * D + d].x;
+            fr = fmaf(c, pv.x, fr);
+            fi = fmaf(c, pv.z, fi);
+        }
+        g.re = mk(fr);
+        g.im = mk(fi);
+    }
+    st(part + d * SCP + k, g);
+    __syncthreads();
+    if (d != 0 || i >= N2) return;
+    const long long p = p_lo + i;
+    const int q = wrap_index(p, N2);
+    if (p > p_hi) {
+        out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    g = ld(part + (D - 1) * SCP + k);
+#pragma unroll
+    for (int e = D - 2; e >= 0; --e) g = cadd(g, ld(part + e * SCP + k));
+    if (G.scale != nullptr) {
+        const long long si = p + G.scale_off;
+        const float2 sc = (si >= 0 && si < G.scale_len) ? G.scale[si] : make_float2(0.f, 0.f);
+        g = cscale(g, mk(sc.x, sc.y));
+    }
+    st(out + q, g);
+}
+
+// Position-major form of the same sum for launches with many blocks (batches): one
+// thread per position with all D degrees in registers (fewer instructions per position,
+// one warp per block); the degree partials meet in the same order.
+template <int D>
+__global__ void __launch_bounds__(SCP)
+k_spread_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
+                     float4 *__restrict__ out_all) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    extern __shared__ float4 smem4[];
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<float2> G = L.inst[inst];
+    const float4 *__restrict__ Pc4 = Pc_all + (long long)G.cell_base * D;
+    float4 *__restrict__ out = out_all + G.grid_base;
+    const int N2 = G.N2;
+    const int m = L.m, ntap = 2 * L.m;
+    const int ncl = SCP + ntap - 1;
+    float4 *Ps = smem4;                                          // [D][ncl] staged cells
+    float2 *coef = reinterpret_cast<float2 *>(Ps + D * ncl);    // [ntap][D]
+    const long long p_lo = G.c_lo - m + 1, p_hi = G.c_lo + G.ncell - 1 + m;
+    const long long i0 = (long long)(blockIdx.x - L.blk[inst]) * SCP;
+    const long long p0 = p_lo + i0;
+    const int k = threadIdx.x;
+    const long long i = i0 + k;
+    if (p0 > p_hi) {                                             // zero padding only
+        if (i < N2) out[wrap_index(p_lo + i, N2)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const long long cbase = p0 - m;
+    for (int e = k; e < ntap * D; e += SCP) coef[e] = G.coef[e];
+    for (int e = k; e < ncl * D; e += SCP) {
+        const int lc = e / D, d = e - lc * D;
         const long long ic = cbase + lc - G.c_lo;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (ic >= 0 && ic < G.ncell) v = Pc4[ic * D + d];
         Ps[d * ncl + lc] = v;
     }
     __syncthreads();
-    const int k = threadIdx.x / D, d = threadIdx.x - k * D;      // position, degree
-    if (k < PPB) {
-        const int lbase = k + ntap - 1;
-        cdf g = czero();
-        if (d < B) {
-            df ar = mk(0.f), ai = mk(0.f);
-            for (int t = 0; t < ntap; ++t) {
-                const float4 pv = Ps[d * ncl + lbase - t];
-                const float2 c2 = coef[t * D + d];
-                const df cd = mk(c2.x, c2.y);
-                acc(ar, mul_u(cd, mk(pv.x, pv.y)));
-                acc(ai, mul_u(cd, mk(pv.z, pv.w)));
-            }
-            g.re = norm(ar);
-            g.im = norm(ai);
-        } else {
-            float fr = 0.f, fi = 0.f;
-            for (int t = 0; t < ntap; ++t) {
-                const float4 pv = Ps[d * ncl + lbase - t];
-                const float c = coef[t * D + d].x;
-                fr = fmaf(c, pv.x, fr);
-                fi = fmaf(c, pv.z, fi);
-            }
-            g.re = mk(fr);
-            g.im = mk(fi);
-        }
-        st(part + k * D + d, g);
+    if (i >= N2) return;
+    const long long p = p_lo + i;
+    const int q = wrap_index(p, N2);
+    if (p > p_hi) {
+        out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
     }
-    __syncthreads();
-    if (k < PPB && d == 0) {
-        const long long i = i0 + k;
-        if (i < N2) {
-            const long long p = p_lo + i;
-            const int q = wrap_index(p, N2);
-            if (p > p_hi) {
-                out[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                cdf g = ld(part + k * D + D - 1);
+    df ar[B], ai[B];
+    float fr[F], fi[F];
 #pragma unroll
-                for (int e = D - 2; e >= 0; --e) g = cadd(g, ld(part + k * D + e));
-                if (scale != nullptr) {
-                    const long long si = p + scale_off;
-                    const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
-                    g = cscale(g, mk(sc.x, sc.y));
-                }
-                st(out + q, g);
-            }
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { fr[d] = 0.f; fi[d] = 0.f; }
+    const int lbase = k + ntap - 1;
+    for (int t = 0; t < ntap; ++t) {
+        const int lc = lbase - t;
+#pragma unroll
+        for (int d = 0; d < B; ++d) {
+            const float4 pv = Ps[d * ncl + lc];
+            const float2 c2 = coef[t * D + d];
+            const df cd = mk(c2.x, c2.y);
+            acc(ar[d], mul_u(cd, mk(pv.x, pv.y)));
+            acc(ai[d], mul_u(cd, mk(pv.z, pv.w)));
+        }
+#pragma unroll
+        for (int d = 0; d < F; ++d) {
+            const float4 pv = Ps[(B + d) * ncl + lc];
+            const float c = coef[t * D + B + d].x;
+            fr[d] = fmaf(c, pv.x, fr[d]);
+            fi[d] = fmaf(c, pv.z, fi[d]);
         }
     }
+    cdf g;
+    g.re = mk(fr[F - 1]);
+    g.im = mk(fi[F - 1]);
+#pragma unroll
+    for (int d = F - 2; d >= 0; --d) {
+        g.re = add(g.re, mk(fr[d]));
+        g.im = add(g.im, mk(fi[d]));
+    }
+#pragma unroll
+    for (int d = B - 1; d >= 0; --d) {
+        g.re = add(g.re, norm(ar[d]));
+        g.im = add(g.im, norm(ai[d]));
+    }
+    if (G.scale != nullptr) {
+        const long long si = p + G.scale_off;
+        const float2 sc = (si >= 0 && si < G.scale_len) ? G.scale[si] : make_float2(0.f, 0.f);
+        g = cscale(g, mk(sc.x, sc.y));
+    }
+    st(out + q, g);
 }
 
 // ---------------------------------------------------------------------------------
@@ -298,107 +382,227 @@ k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, Fft
 //   Q_c[d] = sum_t coef[t][d] * scale(p) * h[p mod N2],  p = c - m + 1 + t,
 // then (x side) the 1/phihat1 fold in the Chebyshev basis: the coefficients of
 // R(y) sum_i Q_c[i] T_i(y) with R(y) = sum_j r_j T_j(y), truncated at degree D.
-// One thread per (cell, degree); a block holds GCB = GC_THREADS / D cells, whose D
-// sums meet in shared memory for the fold.  Output float4 per (cell, degree).
+// A block handles GCP = 32 consecutive cells of one instance with one warp per degree
+// (lane = cell): the block's 32 + 2m - 1 grid values are loaded and scaled once into
+// shared memory, each warp takes one arithmetic path and reads its tap coefficients as
+// broadcasts; the fold runs with one warp per output degree on the [D][GCP] sums, and
+// the outputs leave through shared memory as coalesced rows.
 // ---------------------------------------------------------------------------------
-constexpr int GC_THREADS = 128;
+constexpr int GCP = 32;
 
 template <int D>
-__global__ void __launch_bounds__(GC_THREADS)
+__global__ void __launch_bounds__(512)
 k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
                  float4 *__restrict__ Q_all) {
     constexpr int B = D / 2;
-    constexpr int GCB = GC_THREADS / D;
-    __shared__ float4 qs[GCB * D];
+    constexpr int NT = D * GCP;
+    extern __shared__ float4 smem4[];
     const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
     const GridInst<float2> G = L.inst[inst];
     const float4 *__restrict__ buf = buf_all + G.grid_base;
     float4 *__restrict__ Q4 = Q_all + (long long)G.cell_base * D;
-    const float2 *__restrict__ scale = G.scale;
     const float2 *__restrict__ rfit = L.fold ? G.rfit : nullptr;
-    const long long scale_off = G.scale_off, scale_len = G.scale_len;
     const int N2 = G.N2;
     const int m = L.m, ntap = 2 * L.m;
-    const int k = threadIdx.x / D, d = threadIdx.x - k * D;
-    const int ic = (blockIdx.x - L.blk[inst]) * GCB + k;
-    const bool active = k < GCB && ic < G.ncell;
-    if (active) {
-        const long long c = G.c_lo + ic;
-        cdf q = czero();
-        if (d < B) {
-            df qr = mk(0.f), qi = mk(0.f);
-            int qidx = wrap_index(c - m + 1, N2);             // buffer index of tap 0
-            for (int t = 0; t < ntap; ++t, qidx = qidx + 1 == N2 ? 0 : qidx + 1) {
-                const long long p = c - m + 1 + t;
-                cdf h = ld(buf + qidx);
-                if (scale != nullptr) {
-                    const long long si = p + scale_off;
-                    const float2 sc = (si >= 0 && si < scale_len) ? scale[si] : make_float2(0.f, 0.f);
-                    h = cscale(h, mk(sc.x, sc.y));
-                }
-                const float2 c2 = G.coef[t * D + d];
-                const df cd = mk(c2.x, c2.y);
-                acc(qr, mul_u(cd, h.re));
-                acc(qi, mul_u(cd, h.im));
-            }
-            q.re = norm(qr);
-            q.im = norm(qi);
-        } else {
-            float fr = 0.f, fi = 0.f;
-            int qidx = wrap_index(c - m + 1, N2);
-            for (int t = 0; t < ntap; ++t, qidx = qidx + 1 == N2 ? 0 : qidx + 1) {
-                const long long p = c - m + 1 + t;
-                const float4 hv = buf[qidx];
-                float hr = hv.x, hi = hv.z;
-                if (scale != nullptr) {
-                    const long long si = p + scale_off;
-                    const float sc = (si >= 0 && si < scale_len) ? scale[si].x : 0.f;
-                    hr *= sc;
-                    hi *= sc;
-                }
-                const float cc = G.coef[t * D + d].x;
-                fr = fmaf(cc, hr, fr);
-                fi = fmaf(cc, hi, fi);
-            }
-            q.re = mk(fr);
-            q.im = mk(fi);
+    const int nh = GCP + ntap - 1;
+    float4 *hs = smem4;                                          // [nh] scaled grid values
+    float4 *qs = hs + nh;                                        // [GCP][D] outputs
+    float4 *qa = qs + GCP * D;                                   // [D][GCP] tap sums (fold only)
+    float2 *coef = reinterpret_cast<float2 *>(qs + (L.fold ? 2 : 1) * GCP * D);   // [ntap][D]
+    const int k = threadIdx.x & (GCP - 1), d = threadIdx.x / GCP;   // cell, degree
+    const int ic0 = (blockIdx.x - L.blk[inst]) * GCP;
+    const int ncb = min(GCP, G.ncell - ic0);                     // cells of this block
+    const long long pb = G.c_lo + ic0 - m + 1;                   // position of hs[0]
+    for (int e = threadIdx.x; e < ntap * D; e += NT) coef[e] = G.coef[e];
+    for (int e = threadIdx.x; e < ncb + ntap - 1; e += NT) {
+        const long long p = pb + e;
+        cdf h = ld(buf + wrap_index(p, N2));
+        if (G.scale != nullptr) {
+            const long long si = p + G.scale_off;
+            const float2 sc = (si >= 0 && si < G.scale_len) ? G.scale[si] : make_float2(0.f, 0.f);
+            h = cscale(h, mk(sc.x, sc.y));
         }
-        if (rfit == nullptr) {
-            st(Q4 + (long long)ic * D + d, q);
-        } else {
-            st(qs + k * D + d, q);
-        }
+        st(hs + e, h);
     }
-    if (rfit == nullptr) return;
     __syncthreads();
-    if (!active) return;
-    // coefficient n = d of R(y) S(y) = sum_{i,j} (r_j/2) Q_i (T_{i+j} + T_{|i-j|}):
-    //   i = n - j (j <= n),  i = n + j,  and i = j - n (j >= n, n > 0)
-    df ar = mk(0.f), ai = mk(0.f);
+    cdf q;
+    if (d < B) {                                                 // warp-uniform branch
+        df qr = mk(0.f), qi = mk(0.f);
+        for (int t = 0; t < ntap; ++t) {
+            const cdf h = ld(hs + k + t);
+            const float2 c2 = coef[t * D + d];
+            const df cd = mk(c2.x, c2.y);
+            acc(qr, mul_u(cd, h.re));
+            acc(qi, mul_u(cd, h.im));
+        }
+        q.re = norm(qr);
+        q.im = norm(qi);
+    } else {
+        float fr = 0.f, fi = 0.f;
+        for (int t = 0; t < ntap; ++t) {
+            const float4 hv = hs[k + t];
+            const float cc = coef[t * D + d].x;
+            fr = fmaf(cc, hv.x, fr);
+            fi = fmaf(cc, hv.z, fi);
+        }
+        q.re = mk(fr);
+        q.im = mk(fi);
+    }
+    if (rfit == nullptr) {
+        st(qs + k * D + d, q);
+    } else {
+        st(qa + d * GCP + k, q);
+        __syncthreads();
+        // coefficient n = d of R(y) S(y) = sum_{i,j} (r_j/2) Q_i (T_{i+j} + T_{|i-j|}):
+        //   i = n - j (j <= n),  i = n + j,  and i = j - n (j >= n, n > 0)
+        if (k < ncb) {
+            const int n = d;
+            df ar = mk(0.f), ai = mk(0.f);
 #pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        const float2 rv = rfit[(long long)ic * NR + j];
-        const df r = mk(rv.x, rv.y);
-        if (j <= d) {
-            const cdf v = ld(qs + k * D + d - j);
-            acc(ar, mul_u(r, v.re));
-            acc(ai, mul_u(r, v.im));
-        }
-        if (d + j < D) {
-            const cdf v = ld(qs + k * D + d + j);
-            acc(ar, mul_u(r, v.re));
-            acc(ai, mul_u(r, v.im));
-        }
-        if (d > 0 && j >= d && j - d < D) {
-            const cdf v = ld(qs + k * D + j - d);
-            acc(ar, mul_u(r, v.re));
-            acc(ai, mul_u(r, v.im));
+            for (int j = 0; j < NR; ++j) {
+                const float2 rv = rfit[(long long)(ic0 + k) * NR + j];
+                const df r = mk(rv.x, rv.y);
+                if (j <= n) {
+                    const cdf v = ld(qa + (n - j) * GCP + k);
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+                if (n + j < D) {
+                    const cdf v = ld(qa + (n + j) * GCP + k);
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+                if (n > 0 && j >= n && j - n < D) {
+                    const cdf v = ld(qa + (j - n) * GCP + k);
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+            }
+            cdf o;
+            o.re = norm(ar);
+            o.im = norm(ai);
+            st(qs + k * D + n, o);
         }
     }
-    cdf o;
-    o.re = norm(ar);
-    o.im = norm(ai);
-    st(Q4 + (long long)ic * D + d, o);
+    __syncthreads();
+    float4 *dst = Q4 + (long long)ic0 * D;
+    for (int e = threadIdx.x; e < ncb * D; e += NT) dst[e] = qs[e];
+}
+
+// Position-major form for launches with many blocks: one thread per cell with all D
+// degrees in registers; the fold reads the thread's own row of sums from shared memory.
+template <int D>
+__global__ void __launch_bounds__(GCP)
+k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
+                     float4 *__restrict__ Q_all) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    extern __shared__ float4 smem4[];
+    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const GridInst<float2> G = L.inst[inst];
+    const float4 *__restrict__ buf = buf_all + G.grid_base;
+    float4 *__restrict__ Q4 = Q_all + (long long)G.cell_base * D;
+    const float2 *__restrict__ rfit = L.fold ? G.rfit : nullptr;
+    const int N2 = G.N2;
+    const int m = L.m, ntap = 2 * L.m;
+    const int nh = GCP + ntap - 1;
+    float4 *hs = smem4;                                          // [nh] scaled grid values
+    float4 *qa = hs + nh;                                        // [GCP][D] tap sums
+    float4 *qs = qa + GCP * D;                                   // [GCP][D] outputs (fold only)
+    float2 *coef = reinterpret_cast<float2 *>(qa + (L.fold ? 2 : 1) * GCP * D);   // [ntap][D]
+    const int k = threadIdx.x;
+    const int ic0 = (blockIdx.x - L.blk[inst]) * GCP;
+    const int ncb = min(GCP, G.ncell - ic0);
+    const long long pb = G.c_lo + ic0 - m + 1;
+    for (int e = k; e < ntap * D; e += GCP) coef[e] = G.coef[e];
+    for (int e = k; e < ncb + ntap - 1; e += GCP) {
+        const long long p = pb + e;
+        cdf h = ld(buf + wrap_index(p, N2));
+        if (G.scale != nullptr) {
+            const long long si = p + G.scale_off;
+            const float2 sc = (si >= 0 && si < G.scale_len) ? G.scale[si] : make_float2(0.f, 0.f);
+            h = cscale(h, mk(sc.x, sc.y));
+        }
+        st(hs + e, h);
+    }
+    __syncthreads();
+    if (k < ncb) {
+        df qr[B], qi[B];
+        float fr[F], fi[F];
+#pragma unroll
+        for (int d = 0; d < B; ++d) { qr[d] = mk(0.f); qi[d] = mk(0.f); }
+#pragma unroll
+        for (int d = 0; d < F; ++d) { fr[d] = 0.f; fi[d] = 0.f; }
+        for (int t = 0; t < ntap; ++t) {
+            const cdf h = ld(hs + k + t);
+#pragma unroll
+            for (int d = 0; d < B; ++d) {
+                const float2 c2 = coef[t * D + d];
+                const df cd = mk(c2.x, c2.y);
+                acc(qr[d], mul_u(cd, h.re));
+                acc(qi[d], mul_u(cd, h.im));
+            }
+#pragma unroll
+            for (int d = 0; d < F; ++d) {
+                const float cc = coef[t * D + B + d].x;
+                fr[d] = fmaf(cc, h.re.h, fr[d]);
+                fi[d] = fmaf(cc, h.im.h, fi[d]);
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < B; ++d) {
+            cdf q;
+            q.re = norm(qr[d]);
+            q.im = norm(qi[d]);
+            st(qa + k * D + d, q);
+        }
+#pragma unroll
+        for (int d = 0; d < F; ++d) {
+            cdf q;
+            q.re = mk(fr[d]);
+            q.im = mk(fi[d]);
+            st(qa + k * D + B + d, q);
+        }
+        if (rfit != nullptr) {
+            const float4 *qk = qa + k * D;
+            df r[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const float2 rv = rfit[(long long)(ic0 + k) * NR + j];
+                r[j] = mk(rv.x, rv.y);
+            }
+#pragma unroll
+            for (int n = 0; n < D; ++n) {
+                df ar = mk(0.f), ai = mk(0.f);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    if (j <= n) {
+                        const cdf v = ld(qk + n - j);
+                        acc(ar, mul_u(r[j], v.re));
+                        acc(ai, mul_u(r[j], v.im));
+                    }
+                    if (n + j < D) {
+                        const cdf v = ld(qk + n + j);
+                        acc(ar, mul_u(r[j], v.re));
+                        acc(ai, mul_u(r[j], v.im));
+                    }
+                    if (n > 0 && j >= n && j - n < D) {
+                        const cdf v = ld(qk + j - n);
+                        acc(ar, mul_u(r[j], v.re));
+                        acc(ai, mul_u(r[j], v.im));
+                    }
+                }
+                cdf o;
+                o.re = norm(ar);
+                o.im = norm(ai);
+                st(qs + k * D + n, o);
+            }
+        }
+    }
+    __syncthreads();
+    const float4 *src = rfit != nullptr ? qs : qa;
+    float4 *dst = Q4 + (long long)ic0 * D;
+    for (int e = k; e < ncb * D; e += GCP) dst[e] = src[e];
 }
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -424,18 +628,24 @@ cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const v
     return cudaGetLastError();
 }
 
-int spread_blocks_df(int N2, int D) { return cdiv(N2, SCD_THREADS / D); }
-int gather_blocks_df(int ncell, int D) { return cdiv(ncell, GC_THREADS / D); }
+int spread_blocks_df(int N2, int D) { return cdiv(N2, SCP); }
+int gather_blocks_df(int ncell, int D) { return cdiv(ncell, GCP); }
 
 cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,
                                   cudaStream_t s) {
     if (L.nblocks <= 0) return cudaSuccess;
     const int ntap = 2 * L.m;
-    const int ppb = SCD_THREADS / L.D;
-    const size_t sm = sizeof(float4) * (size_t)L.D * (ppb + ntap - 1) +
-                      sizeof(float4) * (size_t)ppb * L.D + sizeof(float2) * (size_t)ntap * L.D;
-    NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df<DD><<<L.nblocks, SCD_THREADS, sm, s>>>(
-                                L, static_cast<const float4 *>(Pc4), static_cast<float4 *>(out))));
+    const float4 *in = static_cast<const float4 *>(Pc4);
+    float4 *o = static_cast<float4 *>(out);
+    if (L.nblocks >= POS_MAJOR_BLOCKS_PER_SM * device_sm_count()) {
+        const size_t sm = sizeof(float4) * (size_t)L.D * (SCP + ntap - 1) +
+                          sizeof(float2) * (size_t)ntap * L.D;
+        NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df_pos<DD><<<L.nblocks, SCP, sm, s>>>(L, in, o)));
+    } else {
+        const size_t sm = sizeof(float4) * (size_t)L.D * (SCP + ntap - 1 + SCP) +
+                          sizeof(float2) * (size_t)ntap * L.D;
+        NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df<DD><<<L.nblocks, DD * SCP, sm, s>>>(L, in, o)));
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -460,8 +670,16 @@ cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, 
 cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, void *Q4,
                                   cudaStream_t s) {
     if (L.nblocks <= 0) return cudaSuccess;
-    NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df<DD><<<L.nblocks, GC_THREADS, 0, s>>>(
-                                L, static_cast<const float4 *>(buf), static_cast<float4 *>(Q4))));
+    const int ntap = 2 * L.m;
+    const size_t sm = sizeof(float4) * (size_t)(GCP + ntap - 1 + (L.fold ? 2 : 1) * GCP * L.D) +
+                      sizeof(float2) * (size_t)ntap * L.D;
+    const float4 *in = static_cast<const float4 *>(buf);
+    float4 *o = static_cast<float4 *>(Q4);
+    if (L.nblocks >= POS_MAJOR_BLOCKS_PER_SM * device_sm_count()) {
+        NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df_pos<DD><<<L.nblocks, GCP, sm, s>>>(L, in, o)));
+    } else {
+        NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df<DD><<<L.nblocks, DD * GCP, sm, s>>>(L, in, o)));
+    }
     count_launches(1);
     return cudaGetLastError();
 }

@@ -152,47 +152,44 @@ k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
 }
 
 // Exclusive scan of the digit-major histogram: block d scans row d (the counts of
-// digit d in every tile, coalesced tiles of 256) starting from the number of keys
-// with a smaller digit, sum_{d' < d} digit_tot[d'].
+// digit d in every tile) starting from the number of keys with a smaller digit,
+// sum_{d' < d} digit_tot[d'].  Warp w owns a contiguous eighth of the row: a first pass
+// sums it (independent coalesced loads), a block scan of the eight warp totals gives each
+// warp its start, and a second pass scans the warp's segment in chunks of 32 with a
+// running carry (a few dozen serial steps per warp for a row of tens of thousands).
 __global__ void __launch_bounds__(256)
 k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ digit_tot) {
     __shared__ int wsum[8];
-    __shared__ int carry;
+    __shared__ int dbase[8];
     const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int t = tid < d ? digit_tot[tid] : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) wsum[w] = t;
-    __syncthreads();
-    if (tid == 0) {
-        int b = 0;
-        for (int i = 0; i < 8; ++i) b += wsum[i];
-        carry = b;
-    }
-    __syncthreads();
+    if (lane == 0) dbase[w] = t;
     int *row = hist + (long long)d * nblocks;
-    for (int base = 0; base < nblocks; base += 256) {
-        const int i = base + tid;
-        const int v = i < nblocks ? row[i] : 0;
+    const int seg = (((nblocks + 7) / 8) + 31) & ~31;
+    const int a = min(w * seg, nblocks), b = min(a + seg, nblocks);
+    int s = 0;
+#pragma unroll 4
+    for (int i = a + lane; i < b; i += 32) s += row[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[w] = s;
+    __syncthreads();
+    int pre = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pre += dbase[k] + (k < w ? wsum[k] : 0);
+    for (int i0 = a; i0 < b; i0 += 32) {
+        const int i = i0 + lane;
+        const int v = i < b ? row[i] : 0;
         int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += u;
         }
-        __syncthreads();
-        if (lane == 31) wsum[w] = incl;
-        __syncthreads();
-        int wpre = 0, tot = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            wpre += k < w ? wsum[k] : 0;
-            tot += wsum[k];
-        }
-        const int c0 = carry;
-        if (i < nblocks) row[i] = c0 + wpre + incl - v;
-        __syncthreads();
-        if (tid == 0) carry = c0 + tot;
+        if (i < b) row[i] = pre + incl - v;
+        pre += __shfl_sync(0xffffffffu, incl, 31);
     }
 }
 

@@ -545,6 +545,31 @@ k_eval_team(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict_
     }
 }
 
+// Flat point evaluation: one thread per sorted point, its cell read from the sorted cell
+// keys.  There is no work-item indirection, the point loads are coalesced, and threads of
+// the same cell share the cell's coefficients through L1; for sparse cells this hides
+// far more latency than item teams, at 4 extra bytes (the key) per point.
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_eval_flat(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.M) return;
+    const int c = (int)S.keys[p];
+    const Real y = S.ys[p];
+    const int j = S.perm[p];
+    const C2<Real> *q = Q + (long long)c * D;
+    Real T[D];
+    cheb<Real, D>(y, T);
+    Real sr = Real(0), si = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const C2<Real> qd = q[d];
+        sr = fma(qd.x, T[d], sr);
+        si = fma(qd.y, T[d], si);
+    }
+    out[j] = mk2<Real>(sr, si);
+}
+
 // Point evaluation of small work items: one thread per item.
 template <typename Real, int D>
 __global__ void __launch_bounds__(256)
@@ -671,6 +696,12 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, int lane
     if (S.max_items <= 0) return cudaSuccess;
     const C2<Real> *q = static_cast<const C2<Real> *>(Q);
     C2<Real> *o = static_cast<C2<Real> *>(out);
+    if (lanes == EVAL_FLAT) {                       // covers every point: no small-item pass
+        if (S.M <= 0) return cudaSuccess;
+        NNFFT_DISPATCH_D(S.D, (k_eval_flat<Real, DD><<<cdiv(S.M, 256), 256, 0, s>>>(S, q, o)));
+        count_launches(1);
+        return cudaGetLastError();
+    }
     if (lanes == TEAM) {
         const int blocks = cdiv((long long)S.max_items * TEAM, 256);
         NNFFT_DISPATCH_D(S.D, (k_eval_team<Real, DD><<<blocks, 256, 0, s>>>(S, q, o)));

@@ -329,6 +329,36 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
     }
 }
 
+// Flat split-precision evaluation: one thread per sorted point, its cell from the sorted
+// cell keys (no work-item indirection; threads of one cell share Q4 through L1).
+template <int D>
+__global__ void __launch_bounds__(256)
+k_eval_df_flat(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restrict__ Q4,
+               double2 *__restrict__ out) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= S.M) return;
+    const int c = (int)S.keys[p];
+    const float2 yv = ys2[p];
+    const int j = S.perm[p];
+    const float4 *q4 = Q4 + (long long)c * D;
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float4 q = q4[d];
+        if (d < B) {
+            qr[d < B ? d : 0] = mk(q.x, q.y);
+            qi[d < B ? d : 0] = mk(q.z, q.w);
+        } else {
+            fr[d >= B ? d - B : 0] = q.x;
+            fi[d >= B ? d - B : 0] = q.z;
+        }
+    }
+    out[j] = eval_point<B, F>(yv, qr, qi, fr, fi);
+}
+
 // ---------------------------------------------------------------------------------
 // Team kernels: DTEAM = 8 lanes per work item, four items per warp (sparse cells).
 // Moments use the slot layout of the half-warp kernel; three exchange steps over slot
@@ -581,6 +611,14 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
 cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, int lanes,
                            cudaStream_t s) {
     if (S.max_items <= 0) return cudaSuccess;
+    if (lanes == EVAL_FLAT) {                       // covers every point: no small-item pass
+        if (S.M <= 0) return cudaSuccess;
+        NNFFT_DISPATCH_DF(S.D, (k_eval_df_flat<DD><<<cdiv(S.M, 256), 256, 0, s>>>(
+                                   S, reinterpret_cast<const float2 *>(S.ys),
+                                   static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+        count_launches(1);
+        return cudaGetLastError();
+    }
     if (lanes == DTEAM) {
         const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
         NNFFT_DISPATCH_DF(S.D, (k_eval_df_team<DD><<<blocks, 256, 0, s>>>(

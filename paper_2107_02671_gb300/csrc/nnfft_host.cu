@@ -106,7 +106,7 @@ struct nnfft_plan_s {
     FftLaunch<FftDf> fftdf[2]{};
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
-    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8
+    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point
     int fft_variant = 0;
     int item_split = 0;          // 1: split small work items where the size rule says so
                                  // (off by default: the warp-per-item kernels measured faster
@@ -713,6 +713,30 @@ struct StageTimer {
     }
 };
 
+}  // namespace
+
+namespace nnfft {
+int device_sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    int n = cache[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cache[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+}  // namespace nnfft
+
+namespace {
+
 template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     SideK<Real> k;
     k.m = S.m;
@@ -733,6 +757,8 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     k.list_big = S.split_items ? S.list_big : nullptr;
     k.n_small = S.split_items ? S.n2 : nullptr;
     k.n_big = S.split_items ? S.n2 + 1 : nullptr;
+    k.keys = S.keys_sorted;
+    k.M = (int)S.M;
     return k;
 }
 
@@ -1176,12 +1202,12 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     if (!with_nodes && (!p->side[0].set || !p->side[1].set))
         return fail(NNFFT_ESTATE, "nnfft_set_nodes first (or pass the nodes)");
     if (reps < 1) reps = 1;
-    // moments lanes per item: 32/16 for the split-precision kernels, 32/8 for the all-real
-    // ones (D <= 16); evaluation lanes 32/8 for the all-real kernels
+    // moments lanes per item: 32/16/8 for the split-precision kernels, 32/8 for the all-real
+    // ones (D <= 16); evaluation: 32 or 8 lanes per item, or flat (one thread per point)
     const bool dfk = p->dbl && p->split;
     const bool small_d = p->side[0].D <= 16 && p->side[1].D <= 16;
     std::vector<int> lanes = dfk ? std::vector<int>{32, 16, 8} : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
-    std::vector<int> elanes{32, 8};
+    std::vector<int> elanes{32, 8, EVAL_FLAT};
     // splitting small items changes the node-time work lists: only with the nodes given,
     // and only where the size rule would split somewhere
     bool split_possible = false;
@@ -1283,7 +1309,7 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
     auto ok_lanes = [](int l) { return l == 8 || l == 16 || l == 32; };
-    auto ok_elanes = [](int l) { return l == 0 || l == 8 || l == 32; };
+    auto ok_elanes = [](int l) { return l == 0 || l == EVAL_FLAT || l == 8 || l == 32; };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
         (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1))

@@ -136,3 +136,22 @@ def test_batch_errors():
     with pytest.raises(B.NNFFTError) as e:
         P.sync()
     assert e.value.code == 2                            # NNFFT_ERANGE
+
+
+@pytest.mark.parametrize("dtype,m", [(torch.complex128, 8), (torch.complex64, 4)])
+def test_batch_flat_evaluation_bitwise(dtype, m):
+    """Flat evaluation over a batch (cell keys carry each instance's cell base): bitwise
+    the per-item evaluation's result, both directions, empty instances included."""
+    N, M1, M2 = (np.array(SMALL[k]) for k in ("N", "M1", "M2"))
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, f = W.batch_inputs(M1, M2, 51, dtype=npd)
+    g = W.draw_complex(np.random.default_rng(6), int(M2.sum()), npd)
+    P = B.BatchPlan(N, M1, M2, 2.0, 2.0, m, dtype=dtype)
+    res = []
+    for el in (32, 1):
+        P.set_tuning(32, 32, 0, 0, el, el)
+        P.set_nodes(dev(v), dev(x))
+        y, z = P.exec_adjoint(dev(f), dev(g))
+        P.sync()
+        res.append((y.cpu().numpy(), z.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])

@@ -415,7 +415,8 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
     plan.set_nodes(dev(v), dev(x))
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
-    assert t["tuned"] == 1 and t["moments_lanes_v"] in (16, 32) and t["moments_lanes_x"] in (16, 32)
+    assert t["tuned"] == 1 and t["moments_lanes_v"] in (8, 16, 32) and t["moments_lanes_x"] in (8, 16, 32)
+    assert t["eval_lanes_v"] in (1, 8, 32) and t["eval_lanes_x"] in (1, 8, 32)
     assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= t["default_ms"]
     assert t["timed_transform"] == 0
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
@@ -581,3 +582,47 @@ def test_team_kernels_eight_lanes_per_item(dtype, arith, m, tol, N, M1, M2):
         y, z = y.cpu().numpy().astype(np.complex128), z.cpu().numpy().astype(np.complex128)
         assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= tol, (ml, el)
         assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= tol, (ml, el)
+
+
+@pytest.mark.parametrize("dtype,arith,m,tol", [(torch.complex64, None, 4, 2e-5),
+                                               (torch.complex128, "fp64", 8, 1e-12),
+                                               (torch.complex128, None, 8, 1e-12)])
+@pytest.mark.parametrize("N,M1,M2", [(300, 40000, 30000), (3000, 2500, 3500)])
+def test_flat_evaluation_equals_item_evaluation(dtype, arith, m, tol, N, M1, M2):
+    """The flat evaluation kernels (one thread per sorted point, cell from the sorted keys)
+    compute each point exactly as the per-item kernels do: bitwise equal outputs for every
+    arithmetic path, dense and sparse cells, and within tolerance of the direct sums; with
+    a reduced active size (set_sizes) only the active points are written."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, f = W.nnfft_inputs(M1, M2, 91, dtype=npd)
+    g = W.adjoint_inputs(M2, 91, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    if arith == "fp64":
+        plan.set_arith(B.ARITH_FP64)
+    outs = {}
+    for el in (32, 8, 1):
+        plan.set_tuning(32, 32, 0, 0, el, el)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+        plan.sync()
+        outs[el] = (y.cpu().numpy(), z.cpu().numpy())
+    for el in (8, 1):
+        assert np.array_equal(outs[el][0], outs[32][0]) and np.array_equal(outs[el][1], outs[32][1]), el
+    rows2, rows1 = W.sample_rows(M2, 64, 9), W.sample_rows(M1, 64, 10)
+    y, z = (a.astype(np.complex128) for a in outs[1])
+    want_y = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows2)
+    want_z = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows1)
+    assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= tol
+    assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= tol
+    # reduced active sizes: the flat kernel covers exactly the active points
+    m1, m2 = M1 // 3, M2 // 2
+    plan.set_sizes(m1, m2)
+    plan.set_nodes(dev(v[:m1]), dev(x[:m2]))
+    sentinel = torch.full((M2,), 7.0 + 7.0j, dtype=dtype, device="cuda")
+    plan.exec(dev(f[:m1], dtype), out=sentinel[:m2])
+    plan.sync()
+    ys = sentinel.cpu().numpy()
+    assert np.all(ys[m2:] == 7.0 + 7.0j)
+    rows = W.sample_rows(m2, 32, 11)
+    want = oracle.nnfft_direct(N, v[:m1], f[:m1].astype(np.complex128), x[:m2], rows=rows)
+    assert np.max(np.abs(ys[:m2][rows].astype(np.complex128) - want)) / np.sum(np.abs(f[:m1])) <= tol
