@@ -550,14 +550,28 @@ def run_ours(args, rank, world):
         tuning = plan.tuning()
     else:
         tuning = plan.autotune(fd, gd, y, z, reps=3, v=vd, x=xd, flush_l2=True)
+    # the step as one CUDA graph launch: nnfft_transform captured once over these buffers
+    # (both node sorts, forward and adjoint on two streams), replayed every step
+    graph = None if args.no_graph else plan.transform_graph(vd, xd, fd, gd, y, z)
+
+    def step_graph(gr=graph):
+        gr.launch()
+
+    main_step = step if graph is None else step_graph
     for _ in range(args.warmup):
-        step()
+        main_step()
     torch.cuda.synchronize()
     plan.sync()
     with ClockSampler(local) as clk:
-        ms, launches, stages = timed(step, args.steps, plan, label="headline")
+        ms, launches, _ = timed(main_step, args.steps, None, label="headline")
     plan.sync()
     pts_step = 2 * (M_PTS + M_PTS)
+    # the same step launched kernel by kernel on the plan's two streams (and its
+    # per-stage times with the directions overlapping)
+    for _ in range(3):
+        step()
+    ms_str, _, stages = timed(step, max(3, args.steps // 2), plan, label="headline_streams")
+    plan.sync()
     total_ms, value = whole_job_value(float(np.sum(ms)), args.steps, pts_step, world, dev)
 
     # ---- accuracy on sampled rows (rank 0) --------------------------------------------------
@@ -621,6 +635,10 @@ def run_ours(args, rank, world):
                            f"{float(np.mean(ms_seq)):.4f} ms per step")
 
     extra = {}
+    extra["stream_launched"] = {"value": pts_step / (np.mean(ms_str) / 1e3), "unit": "pts/s",
+                                "ms_per_step": float(np.mean(ms_str)),
+                                "what": "the headline step launched kernel by kernel (nnfft_transform "
+                                        "on the plan's two streams) instead of one graph launch"}
     # ---- exec-only with a resident plan (fp64) ------------------------------------------------
     def fwd_adj():
         plan.exec_adjoint(fd, gd, y, z)
@@ -735,6 +753,8 @@ def run_ours(args, rank, world):
             "config": {"workload": WORKLOAD, "N": N_BW, "M1": M_PTS, "M2": M_PTS, "m": 8,
                        "sigma": 2.0, "nodes": "uniform", "points_per_step": pts_step,
                        "l2": "flushed between timed steps (512 MB device write, outside the events)",
+                       "launch": ("kernel by kernel on two streams" if graph is None else
+                                  f"one CUDA graph launch per step ({graph.kernels} kernels)"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "plan": {k: info[k] for k in ("N1", "K1", "N2", "D1", "D2", "fft_n1",
                                                      "fft_n2")}},
@@ -766,6 +786,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="headline step launched kernel by kernel instead of as one CUDA graph")
     ap.add_argument("--tuning", type=lambda t: [int(u) for u in t.split(",")], default=None,
                     help="headline kernel variants instead of autotuning: moments lanes v,x, "
                          "fft variant, item split, evaluation lanes v,x (e.g. 8,8,0,0,1,1)")

@@ -286,6 +286,27 @@ int nnfft_transform(nnfft_plan_t p, const double *v_dev, const double *x_dev, co
                     void *y_dev, const void *g_dev, void *z_dev);
 
 /*
+ * CUDA graph of one nnfft_transform over fixed device buffers.  nnfft_transform_graph
+ * records the whole call (both node sorts, forward and adjoint, both streams) into a
+ * graph; each nnfft_graph_launch replays it on the plan stream with the buffers' contents
+ * at that time (write new nodes or values into the same buffers between launches), with
+ * one launch instead of a few dozen.  The kernel variants (nnfft_set_tuning /
+ * nnfft_autotune) and sizes are those at capture time: capture again after changing
+ * them.  The capture queues no work, but the plan then holds the captured nodes as its
+ * node set: launch the graph before nnfft_exec / nnfft_adjoint on them.  The graph must
+ * not outlive the plan or the buffers.
+ * nnfft_graph_kernels: library kernels one replay runs (counted by nnfft_launch_count at
+ * every launch).  Errors: EINVAL (null argument), ENOMEM, ECUDA.
+ */
+typedef struct nnfft_graph_s *nnfft_graph_t;
+int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_dev,
+                          const void *f_dev, void *y_dev, const void *g_dev, void *z_dev,
+                          nnfft_graph_t *out);
+int nnfft_graph_launch(nnfft_graph_t g);
+int64_t nnfft_graph_kernels(nnfft_graph_t g);
+int nnfft_graph_destroy(nnfft_graph_t g);
+
+/*
  * nnfft_transform_host: new nodes and both directions from host memory in one call:
  * y = A f and z = A^H g for the nodes v, x (all host arrays of the plan's sizes; pinned
  * memory copies asynchronously).  The nodes are uploaded first and sorted (one side per

@@ -66,6 +66,57 @@ k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
     st(Pc4 + (long long)ic * D + d, o);
 }
 
+// With the fit (x side, adjoint): a block of CFP = 32 cells and one warp per degree
+// (lane = cell).  The item sums M_d are formed once per (cell, degree) into shared memory,
+// the fold reads them there (the per-thread form above re-sums up to 2 NR of them), and
+// the outputs leave as coalesced rows.  Same sums in the same order.
+constexpr int CFP = 32;
+
+template <int D>
+__global__ void __launch_bounds__(512)
+k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
+                   float4 *__restrict__ Pc4) {
+    __shared__ float4 ms[D][CFP];
+    __shared__ float4 os[CFP * D];
+    const int k = threadIdx.x & (CFP - 1), d = threadIdx.x / CFP;
+    const int c0 = blockIdx.x * CFP;
+    const int ic = c0 + k;
+    int i0 = 0, i1 = 0;
+    if (ic < S.ncell) {
+        i0 = S.item_off[ic];
+        i1 = S.item_off[ic + 1];
+    }
+    st(&ms[d][k], i1 > i0 ? item_sum<D>(P4, i0, i1, d) : czero());
+    __syncthreads();
+    cdf o = czero();
+    if (i1 > i0) {
+        df ar = mk(0.f), ai = mk(0.f);
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            const float2 rv = T.rfit[(long long)ic * NR + j];
+            const df r = mk(rv.x, rv.y);
+            const int hi = d + j, lo = d > j ? d - j : j - d;
+            if (hi < D) {
+                const cdf m = ld(&ms[hi][k]);
+                acc(ar, mul_u(r, m.re));
+                acc(ai, mul_u(r, m.im));
+            }
+            if (lo < D) {
+                const cdf m = ld(&ms[lo][k]);
+                acc(ar, mul_u(r, m.re));
+                acc(ai, mul_u(r, m.im));
+            }
+        }
+        o.re = norm(ar);
+        o.im = norm(ai);
+    }
+    st(os + k * D + d, o);
+    __syncthreads();
+    const int nc = min(CFP, S.ncell - c0);
+    float4 *dst = Pc4 + (long long)c0 * D;
+    for (int e = threadIdx.x; e < nc * D; e += D * CFP) dst[e] = os[e];
+}
+
 // ---------------------------------------------------------------------------------
 // Spread convolution.  Grid position p = p_lo + i (centered; the taps of all cells
 // cover [p_lo, p_hi], never wider than N2) goes to buffer index p mod N2:
@@ -491,7 +542,7 @@ k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
 
 // Position-major form for launches with many blocks: one thread per cell with all D
 // degrees in registers; the fold reads the thread's own row of sums from shared memory.
-template <int D>
+template <int D, bool FOLD>
 __global__ void __launch_bounds__(GCP)
 k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
                      float4 *__restrict__ Q_all) {
@@ -502,14 +553,14 @@ k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
     const GridInst<float2> G = L.inst[inst];
     const float4 *__restrict__ buf = buf_all + G.grid_base;
     float4 *__restrict__ Q4 = Q_all + (long long)G.cell_base * D;
-    const float2 *__restrict__ rfit = L.fold ? G.rfit : nullptr;
+    const float2 *__restrict__ rfit = FOLD ? G.rfit : nullptr;
     const int N2 = G.N2;
     const int m = L.m, ntap = 2 * L.m;
     const int nh = GCP + ntap - 1;
     float4 *hs = smem4;                                          // [nh] scaled grid values
     float4 *qa = hs + nh;                                        // [GCP][D] tap sums
     float4 *qs = qa + GCP * D;                                   // [GCP][D] outputs (fold only)
-    float2 *coef = reinterpret_cast<float2 *>(qa + (L.fold ? 2 : 1) * GCP * D);   // [ntap][D]
+    float2 *coef = reinterpret_cast<float2 *>(qa + (FOLD ? 2 : 1) * GCP * D);   // [ntap][D]
     const int k = threadIdx.x;
     const int ic0 = (blockIdx.x - L.blk[inst]) * GCP;
     const int ncb = min(GCP, G.ncell - ic0);
@@ -563,7 +614,7 @@ k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
             q.im = mk(fi[d]);
             st(qa + k * D + B + d, q);
         }
-        if (rfit != nullptr) {
+        if (FOLD && rfit != nullptr) {
             const float4 *qk = qa + k * D;
             df r[NR];
 #pragma unroll
@@ -571,7 +622,7 @@ k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
                 const float2 rv = rfit[(long long)(ic0 + k) * NR + j];
                 r[j] = mk(rv.x, rv.y);
             }
-#pragma unroll
+#pragma unroll 1
             for (int n = 0; n < D; ++n) {
                 df ar = mk(0.f), ai = mk(0.f);
 #pragma unroll
@@ -600,7 +651,7 @@ k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
         }
     }
     __syncthreads();
-    const float4 *src = rfit != nullptr ? qs : qa;
+    const float4 *src = FOLD && rfit != nullptr ? qs : qa;
     float4 *dst = Q4 + (long long)ic0 * D;
     for (int e = k; e < ncb * D; e += GCP) dst[e] = src[e];
 }
@@ -622,8 +673,13 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
                                 void *Pc4, cudaStream_t s) {
     if (S.ncell <= 0) return cudaSuccess;
-    NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df<DD><<<cdiv((long long)S.ncell * S.D, 128), 128, 0, s>>>(
-                                S, T, static_cast<const float4 *>(P4), static_cast<float4 *>(Pc4))));
+    const float4 *in = static_cast<const float4 *>(P4);
+    float4 *o = static_cast<float4 *>(Pc4);
+    if (T.rfit != nullptr) {
+        NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df_fit<DD><<<cdiv(S.ncell, CFP), DD * CFP, 0, s>>>(S, T, in, o)));
+    } else {
+        NNFFT_DISPATCH_DF2(S.D, (k_cell_fold_df<DD><<<cdiv((long long)S.ncell * S.D, 128), 128, 0, s>>>(S, T, in, o)));
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -676,7 +732,11 @@ cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, 
     const float4 *in = static_cast<const float4 *>(buf);
     float4 *o = static_cast<float4 *>(Q4);
     if (L.nblocks >= POS_MAJOR_BLOCKS_PER_SM * device_sm_count()) {
-        NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df_pos<DD><<<L.nblocks, GCP, sm, s>>>(L, in, o)));
+        if (L.fold) {
+            NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df_pos<DD, true><<<L.nblocks, GCP, sm, s>>>(L, in, o)));
+        } else {
+            NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df_pos<DD, false><<<L.nblocks, GCP, sm, s>>>(L, in, o)));
+        }
     } else {
         NNFFT_DISPATCH_DF2(L.D, (k_gather_conv_df<DD><<<L.nblocks, DD * GCP, sm, s>>>(L, in, o)));
     }

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -1455,6 +1456,85 @@ int nnfft_transform(nnfft_plan_t p, const double *v_dev, const double *x_dev, co
         return rc;
     NN_CUDA(cudaEventRecord(p->ev_join, p->aux), "join");
     NN_CUDA(cudaStreamWaitEvent(p->stream, p->ev_join, 0), "join");
+    return NNFFT_OK;
+}
+
+struct nnfft_graph_s {
+    nnfft_plan_t plan = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;       // library kernels one replay runs
+};
+
+int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_dev,
+                          const void *f_dev, void *y_dev, const void *g_dev, void *z_dev,
+                          nnfft_graph_t *out) {
+    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
+    *out = nullptr;
+    const int64_t M1 = p->info.M1, M2 = p->info.M2;
+    if ((M1 > 0 && !v_dev) || (M2 > 0 && !x_dev)) return fail(NNFFT_EINVAL, "null node pointer");
+    const bool adj = g_dev && z_dev;
+    int rc = ensure_dag(p, adj);        // every buffer and stream exists before the capture
+    if (rc) return rc;
+    // the capture runs on a stream of its own (the plan stream may be the legacy default
+    // stream, which cannot be captured); replays go to the plan stream
+    cudaStream_t cs = nullptr;
+    NN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t saved = p->stream;
+    const bool timing = p->timing;
+    p->stream = cs;
+    p->timing = false;
+    const long long l0 = launches_so_far();
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) {
+        rc = nnfft_transform(p, v_dev, x_dev, f_dev, y_dev, g_dev, z_dev);
+        const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+        if (!rc && ee != cudaSuccess) rc = cuda_fail(ee, "end capture");
+    } else {
+        rc = cuda_fail(ce, "begin capture");
+    }
+    const int64_t kernels = launches_so_far() - l0;
+    p->stream = saved;
+    p->timing = timing;
+    cudaGetLastError();
+    cudaStreamDestroy(cs);
+    count_launches(-(int)kernels);          // captured, not run
+    cudaGraphExec_t exec = nullptr;
+    if (!rc && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        rc = cuda_fail(cudaGetLastError(), "graph instantiate");
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    nnfft_graph_s *gr = new (std::nothrow) nnfft_graph_s;
+    if (!gr) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(NNFFT_ENOMEM, "graph handle");
+    }
+    gr->plan = p;
+    gr->graph = graph;
+    gr->exec = exec;
+    gr->kernels = kernels;
+    *out = gr;
+    return NNFFT_OK;
+}
+
+int nnfft_graph_launch(nnfft_graph_t gr) {
+    if (!gr) return fail(NNFFT_EINVAL, "null graph");
+    NN_CUDA(cudaGraphLaunch(gr->exec, gr->plan->stream), "graph launch");
+    count_launches((int)gr->kernels);
+    return NNFFT_OK;
+}
+
+int64_t nnfft_graph_kernels(nnfft_graph_t gr) { return gr ? gr->kernels : -1; }
+
+int nnfft_graph_destroy(nnfft_graph_t gr) {
+    if (!gr) return NNFFT_OK;
+    if (gr->exec) cudaGraphExecDestroy(gr->exec);
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
     return NNFFT_OK;
 }
 

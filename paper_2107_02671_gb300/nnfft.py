@@ -8,6 +8,7 @@ library is missing or no GPU is present, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import weakref
 import os
 import threading
 
@@ -128,6 +129,11 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_exec_adjoint.argtypes = [vp, vp, vp, vp, vp]
         lib.nnfft_transform_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_transform.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        lib.nnfft_transform_graph.argtypes = [vp, vp, vp, vp, vp, vp, vp, P(vp)]
+        lib.nnfft_graph_launch.argtypes = [vp]
+        lib.nnfft_graph_kernels.argtypes = [vp]
+        lib.nnfft_graph_kernels.restype = i64
+        lib.nnfft_graph_destroy.argtypes = [vp]
         lib.nnfft_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, cint, cint]
         lib.nnfft_get_tuning.argtypes = [vp, P(Tuning)]
         lib.nnfft_set_tuning.argtypes = [vp, P(Tuning)]
@@ -361,6 +367,26 @@ class Plan:
         _check(self._lib.nnfft_transform(self._h, pv, px, pf, py, pg, pz))
         return (y if f is not None else None), (z if g is not None else None)
 
+    def transform_graph(self, v, x, f=None, g=None, y=None, z=None):
+        """Capture one transform over these device buffers as a CUDA graph (nothing runs
+        yet): returns a TransformGraph whose launch() replays set_nodes + forward + adjoint
+        on the buffers' current contents; y and z receive the results."""
+        import torch
+        pv = _dev_tensor(v, torch.float64, self.M1, "v")
+        px = _dev_tensor(x, torch.float64, self.M2, "x")
+        pf = py = pg = pz = None
+        if f is not None:
+            pf = _dev_tensor(f, self.cdtype, self.M1, "f")
+            y = torch.empty(self.M2, dtype=self.cdtype, device=f.device) if y is None else y
+            py = _dev_tensor(y, self.cdtype, self.M2, "y")
+        if g is not None:
+            pg = _dev_tensor(g, self.cdtype, self.M2, "g")
+            z = torch.empty(self.M1, dtype=self.cdtype, device=g.device) if z is None else z
+            pz = _dev_tensor(z, self.cdtype, self.M1, "z")
+        h = ctypes.c_void_p()
+        _check(self._lib.nnfft_transform_graph(self._h, pv, px, pf, py, pg, pz, ctypes.byref(h)))
+        return TransformGraph(self, h, (v, x, f, g, y, z))
+
     def transform_host(self, v, x, f=None, g=None, y=None, z=None):
         """New nodes and both directions from host arrays in one call (overlapped copies):
         returns (A f, A^H g); a direction is skipped when its input is None."""
@@ -406,9 +432,42 @@ class Plan:
         return {name: (t.ms[i], int(t.count[i])) for i, name in enumerate(STAGES)}
 
     def close(self):
+        for gr in list(getattr(self, "_graphs", ())):     # graphs first: they use the plan
+            gr.close()
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.nnfft_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TransformGraph:
+    """A captured nnfft_transform (see Plan.transform_graph).  launch() replays it on the
+    plan stream; y and z hold the results."""
+
+    def __init__(self, plan, handle, tensors):
+        self._plan, self._h = plan, handle
+        self._keep = tensors                    # the buffers the graph reads and writes
+        self.y, self.z = tensors[4], tensors[5]
+        self.kernels = int(plan._lib.nnfft_graph_kernels(handle))
+        if not hasattr(plan, "_graphs"):
+            plan._graphs = weakref.WeakSet()
+        plan._graphs.add(self)
+
+    def launch(self):
+        if self._h is None:
+            raise NNFFTError(1, "graph closed")
+        _check(self._plan._lib.nnfft_graph_launch(self._h))
+        return self.y, self.z
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            self._plan._lib.nnfft_graph_destroy(self._h)
+        self._h = None
 
     def __del__(self):
         try:

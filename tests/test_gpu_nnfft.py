@@ -626,3 +626,60 @@ def test_flat_evaluation_equals_item_evaluation(dtype, arith, m, tol, N, M1, M2)
     rows = W.sample_rows(m2, 32, 11)
     want = oracle.nnfft_direct(N, v[:m1], f[:m1].astype(np.complex128), x[:m2], rows=rows)
     assert np.max(np.abs(ys[:m2][rows].astype(np.complex128) - want)) / np.sum(np.abs(f[:m1])) <= tol
+
+
+@pytest.mark.parametrize("dtype,m", [(torch.complex128, 8), (torch.complex64, 4)])
+def test_transform_graph_replays_the_transform(dtype, m):
+    """A captured transform (CUDA graph) replays set_nodes + forward + adjoint: bitwise the
+    result of nnfft_transform on the same buffers; new contents written into the buffers
+    are used by the next replay; every replay counts its kernels."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 600, 30000, 20000
+    v, x, f = W.nnfft_inputs(M1, M2, 95, dtype=npd)
+    g = W.adjoint_inputs(M2, 95, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    vd, xd, fd, gd = dev(v), dev(x), dev(f, dtype), dev(g, dtype)
+    y0, z0 = plan.transform(vd, xd, fd, gd)
+    plan.sync()
+    y0, z0 = y0.cpu().numpy(), z0.cpu().numpy()
+    gr = plan.transform_graph(vd, xd, fd, gd)
+    assert gr.kernels > 10
+    l0 = B.launch_count()
+    y, z = gr.launch()
+    plan.sync()
+    assert B.launch_count() - l0 == gr.kernels
+    assert np.array_equal(y.cpu().numpy(), y0) and np.array_equal(z.cpu().numpy(), z0)
+    # new nodes and values in the same buffers
+    v2, x2, f2 = W.nnfft_inputs(M1, M2, 96, dtype=npd)
+    g2 = W.adjoint_inputs(M2, 96, dtype=npd)
+    vd.copy_(dev(v2)); xd.copy_(dev(x2)); fd.copy_(dev(f2, dtype)); gd.copy_(dev(g2, dtype))
+    gr.launch()
+    plan.sync()
+    y2, z2 = y.cpu().numpy().astype(np.complex128), z.cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if dtype == torch.complex128 else 2e-5
+    rows2, rows1 = W.sample_rows(M2, 32, 12), W.sample_rows(M1, 32, 13)
+    want_y = oracle.nnfft_direct(N, v2, f2.astype(np.complex128), x2, rows=rows2)
+    want_z = oracle.nnfft_adjoint_direct(N, v2, x2, g2.astype(np.complex128), rows=rows1)
+    assert np.max(np.abs(y2[rows2] - want_y)) / np.sum(np.abs(f2)) <= tol
+    assert np.max(np.abs(z2[rows1] - want_z)) / np.sum(np.abs(g2)) <= tol
+    gr.close()
+    with pytest.raises(B.NNFFTError):
+        gr.launch()
+    plan.close()
+
+
+def test_transform_graph_batch_plan():
+    N, M1, M2 = np.array([64, 300, 7]), np.array([500, 2000, 1]), np.array([400, 0, 90])
+    v, x, f = W.batch_inputs(M1, M2, 97)
+    g = W.draw_complex(np.random.default_rng(98), int(M2.sum()), np.complex128)
+    P = B.BatchPlan(N, M1, M2, 2.0, 2.0, 8)
+    vd, xd, fd, gd = dev(v), dev(x), dev(f), dev(g)
+    y0, z0 = P.transform(vd, xd, fd, gd)
+    P.sync()
+    y0, z0 = y0.cpu().numpy(), z0.cpu().numpy()
+    gr = P.transform_graph(vd, xd, fd, gd)
+    y, z = gr.launch()
+    gr.launch()
+    P.sync()
+    assert np.array_equal(y.cpu().numpy(), y0) and np.array_equal(z.cpu().numpy(), z0)
+    P.close()
