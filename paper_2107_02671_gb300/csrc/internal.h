@@ -161,6 +161,10 @@ __device__ __forceinline__ int block_instance(const int *blk, int ninst, int b) 
     return lo;
 }
 
+// Self-test of the integer-built fixed-point conversions of the node kernel: per input
+// four floats (truncated, rounded, and CUDA's conversions of the same value).
+cudaError_t selftest_fixed63(const long long *in, float *out, int n, cudaStream_t s);
+
 // ---- nnfft_host.cu (for the other translation units) -------------------------------
 // Streaming multiprocessors of the current device (cached per device).
 int device_sm_count();

@@ -54,20 +54,62 @@ __device__ __forceinline__ bool node_fixed(double t, unsigned long long S, long 
     return ok;
 }
 
+// v 2^-63 as a float, truncated toward zero (rn = false) or rounded to nearest, ties to
+// even (rn = true), built from the bits of v with integer operations: conversions from
+// 64-bit integers run on the FP64 pipe, of which GB300 has 1/64 of the FP32 rate.  Any v
+// (v = -2^63 gives -1).  The truncated part of v is returned in *kept (rn = false).
+__device__ __forceinline__ float fixed63_to_float(long long v, bool rn, long long *kept = nullptr) {
+    if (v == 0) {
+        if (kept) *kept = 0;
+        return 0.f;
+    }
+    const bool neg = v < 0;
+    const unsigned long long a = neg ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+    int p = 63 - __clzll((long long)a);                 // most significant bit, 0..63
+    unsigned long long m;
+    if (p > 23) {
+        const int sh = p - 23;
+        m = a >> sh;                                     // 24 bits with the leading one
+        if (kept) {
+            const unsigned long long t = m << sh;
+            *kept = neg ? (long long)(0ULL - t) : (long long)t;
+        }
+        if (rn) {
+            const unsigned long long rem = a & ((1ULL << sh) - 1);
+            const unsigned long long half = 1ULL << (sh - 1);
+            if (rem > half || (rem == half && (m & 1ULL))) {
+                ++m;
+                if (m >> 24) {
+                    m >>= 1;
+                    ++p;
+                }
+            }
+        }
+    } else {
+        m = a << (23 - p);
+        if (kept) *kept = v;
+    }
+    // m 2^(p - 23) 2^-63 = 1.f x 2^(p - 63): biased exponent p + 64
+    return __uint_as_float((neg ? 0x80000000u : 0u) | ((unsigned)(p + 64) << 23) |
+                           ((unsigned)m & 0x7fffffu));
+}
+
 // Store the local coordinate y = Y 2^-63 in the plan's format:
 //   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans),
-// the pair from integer arithmetic: hi = Y rounded toward zero to 24 bits, lo = the rest.
+// the pair from integer arithmetic: hi = Y rounded toward zero to 24 bits, lo = the rest
+// rounded to nearest, then renormalised.
 __device__ __forceinline__ void store_y(void *yout, int fmt, long long i, long long Y) {
     if (fmt == 0) {
-        static_cast<float *>(yout)[i] = __ll2float_rn(Y) * 0x1p-63f;
+        static_cast<float *>(yout)[i] = fixed63_to_float(Y, true);
     } else if (fmt == 1) {
         static_cast<double *>(yout)[i] = __ll2double_rn(Y) * 0x1p-63;
     } else {
-        const float h = __ll2float_rz(Y);
-        const float l = __ll2float_rn(Y - __float2ll_rz(h));
+        long long kept = 0;
+        const float h = fixed63_to_float(Y, false, &kept);
+        const float l = fixed63_to_float(Y - kept, true);
         const float sh = h + l;                            // Fast2Sum: |h| >= |l|
         const float sl = l - (sh - h);
-        static_cast<float2 *>(yout)[i] = make_float2(sh * 0x1p-63f, sl * 0x1p-63f);
+        static_cast<float2 *>(yout)[i] = make_float2(sh, sl);
     }
 }
 
@@ -630,6 +672,27 @@ size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 1
 cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
                                 cudaStream_t s) {
     k_cell_offsets<<<cdiv((long long)n + 1, 256), 256, 0, s>>>(keys_sorted, n, ncell, off);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
+// four floats per input: the integer-built truncated and rounded values, then CUDA's
+// own conversions of the same integer (the self-test compares them)
+__global__ void k_selftest_fixed63(const long long *__restrict__ in, float *__restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long v = in[i];
+    out[4 * i + 0] = fixed63_to_float(v, false);
+    out[4 * i + 1] = fixed63_to_float(v, true);
+    out[4 * i + 2] = __ll2float_rz(v) * 0x1p-63f;
+    out[4 * i + 3] = __ll2float_rn(v) * 0x1p-63f;
+}
+}  // namespace
+
+cudaError_t selftest_fixed63(const long long *in, float *out, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_selftest_fixed63<<<cdiv(n, 256), 256, 0, s>>>(in, out, n);
     count_launches(1);
     return cudaGetLastError();
 }

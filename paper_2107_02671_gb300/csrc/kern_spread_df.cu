@@ -365,6 +365,10 @@ k_eval_df_flat(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__
 // bits 3..1 leave lane s with slots j = 2s and 2s+1 of each kind.
 // ---------------------------------------------------------------------------------
 constexpr int DTEAM = 8;
+// team moments: points per lane loaded at a time and blocks per SM the registers allow
+// (4 and 3: 80 registers without spills, three 256-thread blocks per SM)
+constexpr int TEAM_CH = 4;
+constexpr int TEAM_MINB = 3;
 
 template <int O, int LB>
 __device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int sub) {
@@ -383,8 +387,8 @@ __device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256)
+template <int D, int CH, int MINB>
+__global__ void __launch_bounds__(256, MINB)
 k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
                   float4 *__restrict__ P4) {
     constexpr int B = D / 2;
@@ -404,20 +408,20 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
     for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
 #pragma unroll
     for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
-    for (int c0 = pb; c0 < pe; c0 += DTEAM * MOM_CHUNK) {
-        float2 yv[MOM_CHUNK];
-        int jv[MOM_CHUNK];
+    for (int c0 = pb; c0 < pe; c0 += DTEAM * CH) {
+        float2 yv[CH];
+        int jv[CH];
 #pragma unroll
-        for (int k = 0; k < MOM_CHUNK; ++k) {
+        for (int k = 0; k < CH; ++k) {
             const int p = c0 + sub + DTEAM * k;
             yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
             jv[k] = p < pe ? S.perm[p] : -1;
         }
-        double2 vv2[MOM_CHUNK];
+        double2 vv2[CH];
 #pragma unroll
-        for (int k = 0; k < MOM_CHUNK; ++k) vv2[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
+        for (int k = 0; k < CH; ++k) vv2[k] = jv[k] >= 0 ? vals[jv[k]] : make_double2(0.0, 0.0);
 #pragma unroll
-        for (int k = 0; k < MOM_CHUNK; ++k)
+        for (int k = 0; k < CH; ++k)
             if (jv[k] >= 0) moments_point<B, F>(yv[k], vv2[k], ar, ai, br, bi);
     }
     df vd[16];
@@ -595,7 +599,7 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_half<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     } else if (lanes == DTEAM) {
         const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
-        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD, TEAM_CH, TEAM_MINB><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     } else {
         const int blocks = cdiv((long long)S.max_items * 32, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));

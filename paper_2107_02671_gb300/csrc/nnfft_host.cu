@@ -1385,6 +1385,15 @@ int nnfft_timing_read(nnfft_plan_t p, nnfft_timing *out, int reset) {
     return NNFFT_OK;
 }
 
+int nnfft_selftest_fixed63(const int64_t *in_dev, float *out_dev, int64_t n) {
+    if (n < 0 || n > (1LL << 28) || (n > 0 && (!in_dev || !out_dev)))
+        return fail(NNFFT_EINVAL, "invalid self-test arguments");
+    NN_CUDA(selftest_fixed63(reinterpret_cast<const long long *>(in_dev), out_dev, (int)n, nullptr),
+            "self-test launch");
+    NN_CUDA(cudaStreamSynchronize(nullptr), "self-test");
+    return NNFFT_OK;
+}
+
 int64_t nnfft_launch_count(void) { return launches_so_far(); }
 
 int nnfft_sync(nnfft_plan_t p) {

@@ -152,6 +152,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_set_arith.argtypes = [vp, cint]
         lib.nnfft_timing_enable.argtypes = [vp, cint]
         lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
+        lib.nnfft_selftest_fixed63.argtypes = [vp, vp, i64]
         lib.nnfft_launch_count.argtypes = []
         lib.nnfft_launch_count.restype = i64
         lib.nnfft_last_error.restype = ctypes.c_char_p
@@ -640,6 +641,19 @@ def sinc(N, a, c, b, m=8, out=None, stream=None, rule="gl", n=0):
     po = _dev_tensor(out, c.dtype, L2, "out")
     _check(lib.sinc_exec_rule(int(N), int(L1), int(L2), int(m), code, _rule_code(rule), int(n),
                               pa, pc, pb, po, int(is_complex), _stream_ptr(stream)))
+    return out
+
+
+def selftest_fixed63(y):
+    """Node-kernel conversion check: for an int64 device tensor of fixed-point coordinates
+    (value y 2^-63) returns an (n, 4) float32 tensor: integer-built truncated and rounded
+    floats, then CUDA's truncating and rounding conversions."""
+    import torch
+    if y.dtype != torch.int64 or not y.is_cuda or not y.is_contiguous():
+        raise TypeError("y must be a contiguous int64 CUDA tensor")
+    out = torch.empty((y.numel(), 4), dtype=torch.float32, device=y.device)
+    _check(load_library().nnfft_selftest_fixed63(ctypes.c_void_p(y.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr()), y.numel()))
     return out
 
 

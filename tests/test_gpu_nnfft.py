@@ -683,3 +683,34 @@ def test_transform_graph_batch_plan():
     P.sync()
     assert np.array_equal(y.cpu().numpy(), y0) and np.array_equal(z.cpu().numpy(), z0)
     P.close()
+
+
+def test_fixed_point_coordinate_conversion_matches_cuda():
+    """The node kernel builds the float (and float pair) coordinates from the fixed-point
+    value with integer operations; they equal CUDA's truncating and rounding conversions
+    bit for bit, for edge values (0, +-1, -2^63, powers of two +- 1, rounding ties) and
+    random values of every magnitude."""
+    rng = np.random.default_rng(123)
+    edge = [0, 1, -1, 2**63 - 1, -2**63, -2**63 + 1, 2**62, -2**62]
+    for k in range(0, 63):
+        for d in (-1, 0, 1):
+            edge += [2**k + d, -(2**k + d)]
+    for k in range(25, 63):                      # exact ties and neighbours at 24 bits
+        base = (2**23 + 1) << (k - 23)
+        half = 1 << (k - 24)
+        edge += [base + half, base + half - 1, base + half + 1, -(base + half), base - half]
+    edge = [e for e in edge if -2**63 <= e < 2**63]
+    mags = rng.integers(0, 63, 200000)
+    rand = (rng.integers(0, 2**62, 200000, dtype=np.int64) >> (62 - mags).astype(np.int64))
+    rand *= np.where(rng.random(200000) < 0.5, -1, 1)
+    y = np.concatenate([np.array(edge, dtype=np.int64), rand.astype(np.int64)])
+    out = B.selftest_fixed63(torch.from_numpy(y).cuda()).cpu().numpy()
+    assert np.array_equal(out[:, 0].view(np.uint32), out[:, 2].view(np.uint32))
+    assert np.array_equal(out[:, 1].view(np.uint32), out[:, 3].view(np.uint32))
+    # and against the exact value: truncation never increases |v|, rounding is nearest
+    from fractions import Fraction
+    for v, t, r in zip(y[:len(edge)], out[:len(edge), 0], out[:len(edge), 1]):
+        exact = Fraction(int(v), 2**63)
+        ft, fr = Fraction(float(t)), Fraction(float(r))
+        assert abs(ft) <= abs(exact) and abs(exact) - abs(ft) < Fraction(float(np.spacing(np.abs(t))))
+        assert abs(fr - exact) <= Fraction(float(np.spacing(np.abs(r)))) / 2
