@@ -241,32 +241,46 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------------------------------
 # our arm
 # -------------------------------------------------------------------------------------------
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the point
-# kernels, from one ncu capture of
-# `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve`
-# (profiles/k_*_nnfft_fp64_N4096_M2e20.md).  Each entry names the sources the kernel is
-# built from and their hash at capture time; a changed source reports null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of every
+# split-precision point-kernel variant at the headline size, from ncu captures of
+# `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
+# with T = 8,8,0,0,1,1 / 32,32,0,0,32,32 / 16,16,0,0,8,8 (profiles/k_*_nnfft_fp64_N4096_M2e20.md).
+# The sources the kernels are built from were hashed at capture time; a changed source
+# reports null.
+NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "internal.h"]
+NCU_HASH = "904f7d23ef350aa3"
 NCU_TRAFFIC = {
-    "moments": {"kernel": "k_moments_df_warp<14>", "bytes": 29.48e6,
-                "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "188812269663e2e0"},
-    "eval": {"kernel": "k_eval_df<14>", "bytes": 16.21e6 + 1.65e6,
-             "sources": ["kern_spread_df.cu", "df.cuh", "internal.h"], "hash": "188812269663e2e0"},
+    "k_moments_df_team<14>": 29463808,          # 8 lanes per work item
+    "k_moments_df_half<14>": 29482752,          # 16
+    "k_moments_df_warp<14>": 29486080,          # 32
+    "k_eval_df_flat<14>": 20417024 + 1797632,   # one thread per point
+    "k_eval_df_team<14>": 14562048 + 768,       # 8 lanes per work item
+    "k_eval_df<14>": 16181248 + 1621504,        # 32
 }
 
 
-def ncu_traffic(stage):
+def point_kernel(stage, tuning):
+    """Name of the split-precision kernel a point stage ran with the plan's tuning."""
+    side = "v" if stage in ("fwd_moments", "adj_eval") else "x"
+    if stage.endswith("_moments"):
+        lanes = tuning.get(f"moments_lanes_{side}", 32)
+        return {8: "k_moments_df_team<14>", 16: "k_moments_df_half<14>"}.get(lanes, "k_moments_df_warp<14>")
+    lanes = tuning.get(f"eval_lanes_{side}", 32)
+    return {1: "k_eval_df_flat<14>", 8: "k_eval_df_team<14>"}.get(lanes, "k_eval_df<14>")
+
+
+def ncu_traffic(stage, tuning):
     import hashlib
-    key = "moments" if stage.endswith("_moments") else "eval" if stage.endswith("_eval") else None
-    if key is None:
+    if not (stage.endswith("_moments") or stage.endswith("_eval")):
         return None, None
-    ent = NCU_TRAFFIC[key]
+    kern = point_kernel(stage, tuning)
     h = hashlib.sha256()
-    for f in ent["sources"]:
+    for f in NCU_SOURCES:
         with open(os.path.join(ROOT, "paper_2107_02671_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != ent["hash"]:
-        return None, ent["kernel"] + ": source changed since the ncu capture"
-    return ent["bytes"], ent["kernel"]
+    if h.hexdigest()[:16] != NCU_HASH:
+        return None, kern + ": source changed since the ncu capture"
+    return NCU_TRAFFIC.get(kern), kern
 
 
 BATCH_COUNT = 512
@@ -624,7 +638,7 @@ def run_ours(args, rank, world):
         # point kernels: split precision (double-float + FP32), memory/latency bound;
         # algorithmic bytes = 8 B node + 16 B value per point
         gbs = 24 * M_PTS / (avg_ms / 1e3) / 1e9
-        traffic, tnote = ncu_traffic(dom)
+        traffic, tnote = ncu_traffic(dom, tuning)
         roof = {"bound": "hbm", "kernel": dom, "achieved": gbs, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": gbs / pk["hbm_gbs"], "traffic": traffic,
                 "traffic_source": tnote,
