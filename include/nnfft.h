@@ -169,18 +169,21 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
 /*
  * Autotuning (the paper has no counterpart).  nnfft_autotune times the plan's kernel
  * variants with the caller's buffers and keeps the fastest: threads per work item of the
- * moments kernel on each side (32: one warp per item; 16: two items per warp in the
- * split-precision kernel; 8: four items per warp) and of the evaluation kernel (32 or 8
- * per item, or 1: one thread per sorted point with no work items), the FFT's packing of short columns into blocks (variant 0 by the plan-size rule,
- * variant 1 the other extreme) and, when the nodes are given, whether work items of at
- * most 16 points run one thread per item (item_split; only tried where some instance has
- * few points per cell).  With v and x (device) every run is a full nnfft_transform; with
- * v = x = NULL it is nnfft_exec_adjoint on the current nodes.  Every configuration is
- * timed in three interleaved sweeps of `reps` runs (best kept); the default stays unless
- * another is more than 3 % faster.  flags: NNFFT_TUNE_FLUSH_L2 writes a 192 MB buffer
- * before every timed run (cold L2, as in a stream of new problems).  y and z receive the
- * transforms.  Synchronous.  Other variants sum in another order, so later results may
- * change in the last bits.
+ * moments kernel (32: one warp per item; 16: two items per warp, split-precision kernel
+ * only; 8: four items per warp; the same for both sides), the evaluation kernel (32 or 8
+ * per item, or 1: one thread per sorted point with no work items), the FFT's packing of
+ * short columns into blocks (variant 0 by the plan-size rule, variant 1 the other
+ * extreme) and, when the nodes are given, the largest work item (item_cap: 256, 128, 64
+ * or 32 points; smaller items give dense cells more parallel work) and whether work items
+ * of at most 16 points run one thread per item (item_split; only tried where some
+ * instance has few points per cell).  With v and x (device) every run is a full
+ * nnfft_transform; with v = x = NULL it is nnfft_exec_adjoint on the current nodes.  The
+ * settings are searched one at a time from the defaults with the others at their current
+ * best (two sweeps); each value is timed in three interleaved rounds of `reps` runs (best
+ * kept) and the current value stays unless another is more than 3 % faster.  flags:
+ * NNFFT_TUNE_FLUSH_L2 writes a 192 MB buffer before every timed run (cold L2, as in a
+ * stream of new problems).  y and z receive the transforms.  Synchronous.  Other variants
+ * sum in another order, so later results may change in the last bits.
  */
 enum { NNFFT_TUNE_FLUSH_L2 = 1 };
 typedef struct {
@@ -191,15 +194,17 @@ typedef struct {
     int item_split;                         /* 1: small work items one thread each (default 0) */
     int timed_transform;                    /* 1: runs were full transforms */
     int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8; 1 = flat */
+    int item_cap;                           /* points per work item at most: 256, 128, 64, 32 */
 } nnfft_tuning;
 int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
                    void *y_dev, const void *g_dev, void *z_dev, int reps, int flags);
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
  * moments_lanes_v / _x in {8, 16, 32}, eval_lanes_v / _x in {1, 8, 32} (0: 32), fft_variant in
- * {0, 1}, item_split in {0, 1}; the other fields are ignored (a lane count a kernel does not
- * have runs as one warp per item).  EINVAL otherwise.  Takes effect for the work queued next; a changed
- * item_split needs nnfft_set_nodes again. */
+ * {0, 1}, item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256); the other fields are
+ * ignored (a lane count a kernel does not have runs as one warp per item).  EINVAL otherwise.
+ * Takes effect for the work queued next; a changed item_split or item_cap needs
+ * nnfft_set_nodes again. */
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t);
 
 /*

@@ -14,8 +14,10 @@ namespace nnfft {
 
 // Coefficients of the per-cell Chebyshev fit of 1/phihat1(N* x) on the x side.
 constexpr int NR = 8;
-// A work item is a run of at most ITEM_CAP sorted points of one cell.
+// A work item is a run of at most `cap` sorted points of one cell, ITEM_CAP_MIN <= cap <=
+// ITEM_CAP (a plan setting; the point kernels are written for items of up to ITEM_CAP).
 constexpr int ITEM_CAP = 256;
+constexpr int ITEM_CAP_MIN = 32;
 // Radix sort: 8-bit digits, tiles of SORT_TILE keys per block (8 warps x 256).
 constexpr int SORT_TILE = 2048;
 constexpr int SORT_THREADS = 256;
@@ -188,8 +190,6 @@ size_t sinc_release_stream(cudaStream_t stream);
 
 // ---- kern_nodes.cu ----------------------------------------------------------------
 size_t radix_sort_hist_len(int n);
-cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
-                                cudaStream_t s);
 // Fused step 0: keys, local coordinates (caller order, format yfmt: 0 float, 1 double,
 // 2 float pair) and the first radix pass's histogram in hist (radix_sort_hist_len ints).
 // With ninst > 1, pt_off [ninst + 1] (device) splits the points into instances and
@@ -205,13 +205,19 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
                              int *hist, int n, int key_bits, const void *y_user, void *ys,
                              int ybytes, cudaStream_t s, uint32_t **keys_sorted,
                              int **vals_sorted);
-// Work items (at most ITEM_CAP sorted points of one cell each) from the cell offsets:
-// one block for up to ITEMS_ONE_BLOCK_MAX cells, else three launches using scratch
-// (build_items_scratch_len(ncell) ints).
+// Cell offsets (cell_off[c] = first sorted point of cell c, cell_off[ncell] = n) and work
+// items (at most cap sorted points of one cell each, ITEM_CAP_MIN <= cap <= ITEM_CAP;
+// item_off[c] = first item of cell c, *nitems = total) from the sorted keys.  With
+// per_cell_first (dense plans) the offsets pass also makes one item per cell (empty cells
+// included) and the scan of ceil(count / cap) over the cells runs only if some cell holds
+// more than cap points; otherwise the scan always runs (it skips empty cells).  The scan
+// is one block up to ITEMS_ONE_BLOCK_MAX cells, else three launches.  scratch:
+// build_items_scratch_len(ncell) ints.
 constexpr int ITEMS_ONE_BLOCK_MAX = 65536;
-cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
-                                     int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                                     int *scratch, cudaStream_t s);
+cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell, int cap,
+                                   bool per_cell_first, int *cell_off, int *item_off,
+                                   int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                                   int *scratch, cudaStream_t s);
 size_t build_items_scratch_len(int ncell);
 // Split the work items into those of at most SMALL_ITEM points and the rest (lists of
 // item ids in no particular order, counts in n2[0], n2[1]; n2 zeroed by the caller).

@@ -347,9 +347,11 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
 // Single-block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total.
 // Coalesced tiles of 1024 (one element per thread) with a running carry.
 // in and out may alias.
-__global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out, int n) {
+__global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out, int n,
+                                                         const int *run_if = nullptr) {
     __shared__ int wsum[32];
     __shared__ int carry;
+    if (run_if && *run_if == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) carry = 0;
     __syncthreads();
@@ -384,23 +386,49 @@ __global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out
     if (tid == 0) out[n] = carry;
 }
 
-__global__ void k_cell_offsets(const uint32_t *__restrict__ keys, int n, int ncell,
-                               int *__restrict__ off) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Cell offsets from the sorted keys and, in the same pass, one work item per cell (empty
+// cells included: pb = pe) for the common case that no cell holds more than cap points.
+// The first point i of a cell with more (keys[i + cap] still in the cell) sets *overflow;
+// the scan-based builders launched next then rebuild the items (they return at once
+// otherwise), so the decision stays on the device.
+__global__ void k_cell_offsets_items(const uint32_t *__restrict__ keys, int n, int ncell, int cap,
+                                     int *__restrict__ off, int *__restrict__ item_off,
+                                     int *__restrict__ item_cell, int *__restrict__ item_pb,
+                                     int *__restrict__ item_pe, int *__restrict__ nitems,
+                                     int *__restrict__ overflow) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > n) return;
-    int prev = i == 0 ? -1 : (int)keys[i - 1];
-    int cur = i == n ? ncell : (int)keys[i];
-    for (int c = prev + 1; c <= cur; ++c) off[c] = i;
+    const int prev = i == 0 ? -1 : (int)keys[i - 1];
+    const int cur = i == n ? ncell : (int)keys[i];
+    if (overflow == nullptr) {                            // offsets only
+        for (int c = prev + 1; c <= cur; ++c) off[c] = i;
+        return;
+    }
+    if (cur > prev && i + cap < n && (int)keys[i + cap] == cur) *overflow = 1;
+    for (int c = prev + 1; c <= cur; ++c) {
+        off[c] = i;
+        if (c < ncell) {
+            item_off[c] = c;
+            item_cell[c] = c;
+            item_pb[c] = i;
+        }
+        if (c > 0) item_pe[c - 1] = i;
+    }
+    if (i == n) {
+        item_off[ncell] = ncell;
+        *nitems = ncell;
+    }
 }
 
-// Work items in one block: for every cell, ceil(count / ITEM_CAP) items of at most
-// ITEM_CAP consecutive sorted points; item_off[c] = first item of cell c, nitems = total.
+// Work items in one block: for every cell, ceil(count / cap) items of at most cap
+// (<= ITEM_CAP) consecutive sorted points; item_off[c] = first item of cell c, nitems = total.
 // Coalesced tiles of 1024 cells (one per thread), exclusive scan with a running carry;
 // the next tile's offsets are loaded before the current tile is scanned.
 __global__ void __launch_bounds__(1024)
 k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off,
               int *__restrict__ item_cell, int *__restrict__ item_pb, int *__restrict__ item_pe,
-              int *__restrict__ nitems) {
+              int *__restrict__ nitems, int cap, const int *__restrict__ run_if) {
+    if (run_if && *run_if == 0) return;                 // items already one per cell
     __shared__ int wsum[32];
     __shared__ int carry;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -411,7 +439,7 @@ k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off
     for (int base = 0; base < ncell; base += 1024) {
         const int cn = c + 1024;
         const int q0 = cn < ncell ? off[cn] : 0, q1 = cn < ncell ? off[cn + 1] : 0;   // prefetch
-        const int v = c < ncell ? (p1 - p0 + ITEM_CAP - 1) / ITEM_CAP : 0;
+        const int v = c < ncell ? (p1 - p0 + cap - 1) / cap : 0;
         int incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -435,10 +463,10 @@ k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off
         if (c < ncell) {
             item_off[c] = first;
             for (int j = 0; j < v; ++j) {
-                const int pb = p0 + j * ITEM_CAP;
+                const int pb = p0 + j * cap;
                 item_cell[first + j] = c;
                 item_pb[first + j] = pb;
-                item_pe[first + j] = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
+                item_pe[first + j] = pb + cap < p1 ? pb + cap : p1;
             }
         }
         __syncthreads();
@@ -457,15 +485,17 @@ k_build_items(const int *__restrict__ off, int ncell, int *__restrict__ item_off
 // Work items for many cells (a batch), in three launches: per block of 1024 cells the
 // number of items, a single-block scan of those block sums, then per block the local
 // scan, the items and item_off.  Same items as k_build_items.
-__device__ __forceinline__ int cell_items(const int *off, int c, int ncell) {
-    return c < ncell ? (off[c + 1] - off[c] + ITEM_CAP - 1) / ITEM_CAP : 0;
+__device__ __forceinline__ int cell_items(const int *off, int c, int ncell, int cap) {
+    return c < ncell ? (off[c + 1] - off[c] + cap - 1) / cap : 0;
 }
 
 __global__ void __launch_bounds__(1024)
-k_item_block_sums(const int *__restrict__ off, int ncell, int *__restrict__ bsum) {
+k_item_block_sums(const int *__restrict__ off, int ncell, int *__restrict__ bsum, int cap,
+                  const int *__restrict__ run_if) {
     __shared__ int wsum[32];
+    if (run_if && *run_if == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    int v = cell_items(off, blockIdx.x * 1024 + tid, ncell);
+    int v = cell_items(off, blockIdx.x * 1024 + tid, ncell, cap);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) wsum[w] = v;
@@ -482,11 +512,12 @@ __global__ void __launch_bounds__(1024)
 k_item_fill_blocks(const int *__restrict__ off, int ncell, const int *__restrict__ bbase,
                    int nblocks, int *__restrict__ item_off, int *__restrict__ item_cell,
                    int *__restrict__ item_pb, int *__restrict__ item_pe,
-                   int *__restrict__ nitems) {
+                   int *__restrict__ nitems, int cap, const int *__restrict__ run_if) {
     __shared__ int wsum[32];
+    if (run_if && *run_if == 0) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int c = blockIdx.x * 1024 + tid;
-    const int v = cell_items(off, c, ncell);
+    const int v = cell_items(off, c, ncell, cap);
     int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -511,10 +542,10 @@ k_item_fill_blocks(const int *__restrict__ off, int ncell, const int *__restrict
         item_off[c] = first;
         const int p0 = off[c], p1 = off[c + 1];
         for (int j = 0; j < v; ++j) {
-            const int pb = p0 + j * ITEM_CAP;
+            const int pb = p0 + j * cap;
             item_cell[first + j] = c;
             item_pb[first + j] = pb;
-            item_pe[first + j] = pb + ITEM_CAP < p1 ? pb + ITEM_CAP : p1;
+            item_pe[first + j] = pb + cap < p1 ? pb + cap : p1;
         }
     }
     if (blockIdx.x == nblocks - 1 && tid == 0) {
@@ -649,32 +680,36 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     return cudaSuccess;
 }
 
-cudaError_t launch_build_items_fused(const int *cell_off, int ncell, int *item_off,
-                                     int *item_cell, int *item_pb, int *item_pe, int *nitems,
-                                     int *scratch, cudaStream_t s) {
+cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell, int cap,
+                                   bool per_cell_first, int *cell_off, int *item_off,
+                                   int *item_cell, int *item_pb, int *item_pe, int *nitems,
+                                   int *scratch, cudaStream_t s) {
+    if (cap < ITEM_CAP_MIN || cap > ITEM_CAP) return cudaErrorInvalidValue;
+    const int nb = cdiv(ncell, 1024);
+    int *overflow = nullptr;                              // nullptr: the scan always runs
+    if (per_cell_first) {
+        overflow = scratch + nb + 1;
+        cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_cell_offsets_items<<<cdiv((long long)n + 1, 256), 256, 0, s>>>(
+        keys_sorted, n, ncell, cap, cell_off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
+    // cells above cap: items by a scan of ceil(count / cap) over the cells
     if (ncell <= ITEMS_ONE_BLOCK_MAX) {
         k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
-                                         nitems);
-        count_launches(1);
+                                         nitems, cap, overflow);
+        count_launches(2);
         return cudaGetLastError();
     }
-    const int nb = cdiv(ncell, 1024);
-    k_item_block_sums<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch);
-    k_scan_exclusive<<<1, 1024, 0, s>>>(scratch, scratch, nb);
+    k_item_block_sums<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch, cap, overflow);
+    k_scan_exclusive<<<1, 1024, 0, s>>>(scratch, scratch, nb, overflow);
     k_item_fill_blocks<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch, nb, item_off, item_cell,
-                                           item_pb, item_pe, nitems);
-    count_launches(3);
+                                           item_pb, item_pe, nitems, cap, overflow);
+    count_launches(4);
     return cudaGetLastError();
 }
 
-size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 1; }
-
-cudaError_t launch_cell_offsets(const uint32_t *keys_sorted, int n, int ncell, int *off,
-                                cudaStream_t s) {
-    k_cell_offsets<<<cdiv((long long)n + 1, 256), 256, 0, s>>>(keys_sorted, n, ncell, off);
-    count_launches(1);
-    return cudaGetLastError();
-}
+size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 2; }
 
 namespace {
 // four floats per input: the integer-built truncated and rounded values, then CUDA's

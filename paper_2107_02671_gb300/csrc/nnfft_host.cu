@@ -52,6 +52,7 @@ struct Side {
     // plan-time (all instances of the plan concatenated)
     int m = 0, D = 0;
     int ncell = 0, M = 0, max_items = 0, key_bits = 8;
+    int max_items_alloc = 0;               // item buffers: enough for the smallest item cap
     int M_cap = 0;                         // points the buffers hold (M <= M_cap)
     bool has_r = false;
     NodeInst one{};                        // binning of a single-instance plan
@@ -109,6 +110,7 @@ struct nnfft_plan_s {
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
     int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point
     int fft_variant = 0;
+    int item_cap = ITEM_CAP;     // points per work item at most (ITEM_CAP_MIN .. ITEM_CAP)
     int item_split = 0;          // 1: split small work items where the size rule says so
                                  // (off by default: the warp-per-item kernels measured faster
                                  // on the batched workload; the autotuner may turn it on)
@@ -492,6 +494,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         S.M = (int)pt_off.back();
         S.M_cap = S.M;
         S.max_items = S.ncell + (S.M + ITEM_CAP - 1) / ITEM_CAP + (int)count;
+        S.max_items_alloc = S.ncell + (S.M + ITEM_CAP_MIN - 1) / ITEM_CAP_MIN + (int)count;
         S.key_bits = key_bits_for(S.ncell);
         S.one = tab[0];
         if (count > 1) {
@@ -540,9 +543,9 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
             (rc = dalloc_n(p, &S.item_off, (size_t)S.ncell + 1, "item offsets")) ||
             (rc = dalloc_n(p, &S.items_scratch, build_items_scratch_len(S.ncell), "item scratch")) ||
-            (rc = dalloc_n(p, &S.item_cell, (size_t)S.max_items, "items")) ||
-            (rc = dalloc_n(p, &S.item_pb, (size_t)S.max_items, "items")) ||
-            (rc = dalloc_n(p, &S.item_pe, (size_t)S.max_items, "items")) ||
+            (rc = dalloc_n(p, &S.item_cell, (size_t)S.max_items_alloc, "items")) ||
+            (rc = dalloc_n(p, &S.item_pb, (size_t)S.max_items_alloc, "items")) ||
+            (rc = dalloc_n(p, &S.item_pe, (size_t)S.max_items_alloc, "items")) ||
             (rc = dalloc_n(p, &S.nitems, 1, "item count")))
             return rc;
         NN_CUDA(cudaMemset(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1)), "memset");
@@ -554,8 +557,8 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             const int64_t Mi = pt_off[(size_t)i + 1] - pt_off[(size_t)i];
             S.split_rule = Mi > 0 && Mi < 4LL * SMALL_ITEM * tab[(size_t)i].ncell;
         }
-        if ((rc = dalloc_n(p, &S.list_small, (size_t)S.max_items, "item lists")) ||
-            (rc = dalloc_n(p, &S.list_big, (size_t)S.max_items, "item lists")) ||
+        if ((rc = dalloc_n(p, &S.list_small, (size_t)S.max_items_alloc, "item lists")) ||
+            (rc = dalloc_n(p, &S.list_big, (size_t)S.max_items_alloc, "item lists")) ||
             (rc = dalloc_n(p, &S.n2, 2, "item lists")))
             return rc;
         NN_CUDA(cudaMemset(S.n2, 0, 2 * sizeof(int)), "memset");
@@ -667,7 +670,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         const size_t cs = 2 * rs;
         size_t pmax = 0, qmax = 0;
         for (int s = 0; s < 2; ++s) {
-            pmax = std::max(pmax, (size_t)p->side[s].max_items * p->side[s].D);
+            pmax = std::max(pmax, (size_t)p->side[s].max_items_alloc * p->side[s].D);
             qmax = std::max(qmax, (size_t)p->side[s].ncell * p->side[s].D);
         }
         p->work_bytes[0] = (size_t)gtot * cs;
@@ -785,6 +788,7 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     if (p->ninst == 1) S.split_items = S.M > 0 && (int64_t)S.M < 4LL * SMALL_ITEM * S.ncell;
     else S.split_items = S.split_rule;
     S.split_items = S.split_items && p->item_split;
+    S.max_items = S.ncell + (S.M + p->item_cap - 1) / p->item_cap + (int)p->ninst;
     if (S.M == 0) {
         NN_CUDA(cudaMemsetAsync(S.item_off, 0, sizeof(int) * ((size_t)S.ncell + 1), st), "memset");
         NN_CUDA(cudaMemsetAsync(S.nitems, 0, sizeof(int), st), "memset");
@@ -805,10 +809,12 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
             "radix sort");
     S.perm = vs;
     S.keys_sorted = ks;
-    NN_CUDA(launch_cell_offsets(ks, S.M, S.ncell, S.cell_off, st), "cell offsets");
-    NN_CUDA(launch_build_items_fused(S.cell_off, S.ncell, S.item_off, S.item_cell, S.item_pb,
-                                     S.item_pe, S.nitems, S.items_scratch, st),
-            "work items");
+    // one item per cell first where cells are dense (a single instance with at least two
+    // points per cell on average): empty items would cost a reduction and a zero row each
+    const bool per_cell = p->ninst == 1 && (int64_t)S.M >= 2LL * S.ncell;
+    NN_CUDA(launch_cells_and_items(ks, S.M, S.ncell, p->item_cap, per_cell, S.cell_off, S.item_off,
+                                   S.item_cell, S.item_pb, S.item_pe, S.nitems, S.items_scratch, st),
+            "cell offsets and work items");
     if (S.split_items) {
         NN_CUDA(cudaMemsetAsync(S.n2, 0, 2 * sizeof(int), st), "memset");
         NN_CUDA(launch_split_items(S.nitems, S.item_pb, S.item_pe, S.max_items, S.list_small,
@@ -1232,44 +1238,86 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
         return with_nodes ? nnfft_transform(p, v_dev, x_dev, f_dev, y_dev, g_dev, z_dev)
                           : nnfft_exec_adjoint(p, f_dev, y_dev, g_dev, z_dev);
     };
-    // every configuration is timed in ROUNDS interleaved sweeps and keeps its best time;
-    // the default (first entry) stays unless another configuration is more than 3 % faster
-    struct Cfg { int lv, lx, el, fv, sp; double t; };
-    std::vector<Cfg> cfgs;
-    for (int sp : splits)            // lanes tuned jointly for both sides (nnfft_set_tuning
-        for (int fv = 0; fv < 2; ++fv)  // can still set them per side)
-            for (int el : elanes)
-                for (int l : lanes) cfgs.push_back(Cfg{l, l, el, fv, sp, 1e300});
+    // Coordinate descent from the defaults: the dimensions (moments lanes, evaluation form,
+    // FFT packing, item split, item cap) are searched one at a time with the others held at
+    // their current best, in two sweeps.  Within a dimension every value is timed in ROUNDS
+    // interleaved rounds (best time kept) and the incumbent stays unless another value is
+    // more than 3 % faster.  The item split and cap change the node-time work lists, so they
+    // are searched only with the nodes given (every run is then a full transform).
+    struct Cfg { int lv, lx, el, fv, sp, cap; };
+    const std::vector<int> caps = with_nodes ? std::vector<int>{ITEM_CAP, 128, 64, ITEM_CAP_MIN}
+                                             : std::vector<int>{p->item_cap};
+    const std::vector<std::vector<int>> dims{lanes, elanes, {0, 1}, splits, caps};
+    auto set_dim = [](Cfg c, size_t d, int v) {
+        switch (d) {
+            case 0: c.lv = c.lx = v; break;
+            case 1: c.el = v; break;
+            case 2: c.fv = v; break;
+            case 3: c.sp = v; break;
+            default: c.cap = v; break;
+        }
+        return c;
+    };
+    auto apply = [&](const Cfg &c) {
+        p->fft_variant = c.fv;
+        p->mom_lanes[0] = c.lv;
+        p->mom_lanes[1] = c.lx;
+        p->eval_lanes[0] = p->eval_lanes[1] = c.el;
+        p->item_split = c.sp;
+        p->item_cap = c.cap;
+    };
+    auto time_cfg = [&](const Cfg &c, double &ms) -> int {
+        apply(c);
+        int r = run();                                  // warm-up (and work lists)
+        for (int k = 0; k < reps && !r; ++k) {
+            if (flush) cudaMemsetAsync(flush, k & 1, flush_bytes, p->stream);
+            cudaEventRecord(ev[2 * k], p->stream);
+            r = run();
+            cudaEventRecord(ev[2 * k + 1], p->stream);
+        }
+        if (r) return r;
+        if (cudaEventSynchronize(ev.back()) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune timing");
+        double tot = 0;
+        for (int k = 0; k < reps; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]);
+            tot += t;
+        }
+        ms = tot / reps;
+        return NNFFT_OK;
+    };
     constexpr int ROUNDS = 3;
     const bool timing = p->timing;
     p->timing = false;
-    for (int round = 0; round < ROUNDS && !rc; ++round)
-        for (size_t ci = 0; ci < cfgs.size() && !rc; ++ci) {
-            Cfg &c = cfgs[round % 2 ? cfgs.size() - 1 - ci : ci];
-            p->fft_variant = c.fv;
-            p->mom_lanes[0] = c.lv;
-            p->mom_lanes[1] = c.lx;
-            p->eval_lanes[0] = p->eval_lanes[1] = c.el;
-            p->item_split = c.sp;
-            if ((rc = run())) break;                        // warm-up (and work lists)
-            for (int r = 0; r < reps && !rc; ++r) {
-                if (flush) cudaMemsetAsync(flush, r & 1, flush_bytes, p->stream);
-                cudaEventRecord(ev[2 * r], p->stream);
-                rc = run();
-                cudaEventRecord(ev[2 * r + 1], p->stream);
-            }
+    Cfg cur{lanes[0], lanes[0], elanes[0], 0, splits[0], with_nodes ? ITEM_CAP : p->item_cap};
+    double cur_ms = 1e300, default_ms = -1.0;
+    for (int sweep = 0; sweep < 2 && !rc; ++sweep)
+        for (size_t d = 0; d < dims.size() && !rc; ++d) {
+            const std::vector<int> &vals = dims[d];
+            if (vals.size() < 2) continue;
+            std::vector<double> best(vals.size(), 1e300);
+            for (int round = 0; round < ROUNDS && !rc; ++round)
+                for (size_t i = 0; i < vals.size() && !rc; ++i) {
+                    const size_t vi = round % 2 ? vals.size() - 1 - i : i;
+                    double ms = 0;
+                    if ((rc = time_cfg(set_dim(cur, d, vals[vi]), ms))) break;
+                    best[vi] = std::min(best[vi], ms);
+                }
             if (rc) break;
-            if (cudaEventSynchronize(ev.back()) != cudaSuccess) {
-                rc = cuda_fail(cudaGetLastError(), "autotune timing");
-                break;
+            int inc = 0;                                   // the incumbent's value index
+            int curv = d == 0 ? cur.lv : d == 1 ? cur.el : d == 2 ? cur.fv : d == 3 ? cur.sp : cur.cap;
+            for (size_t i = 0; i < vals.size(); ++i)
+                if (vals[i] == curv) inc = (int)i;
+            if (default_ms < 0) default_ms = best[inc];
+            size_t bi = inc;
+            for (size_t i = 0; i < vals.size(); ++i)
+                if (best[i] < best[bi]) bi = i;
+            if (best[bi] < 0.97 * best[inc]) {
+                cur = set_dim(cur, d, vals[bi]);
+                cur_ms = best[bi];
+            } else {
+                cur_ms = best[inc];
             }
-            double tot = 0;
-            for (int r = 0; r < reps; ++r) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
-                tot += ms;
-            }
-            c.t = std::min(c.t, tot / reps);
         }
     p->timing = timing;
     for (auto &e : ev)
@@ -1278,19 +1326,16 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
         cudaStreamSynchronize(p->stream);
         cudaFree(flush);
     }
-    const Cfg *best = &cfgs[0];
-    for (const Cfg &c : cfgs)
-        if (c.t < best->t) best = &c;
-    if (best->t > 0.97 * cfgs[0].t) best = &cfgs[0];
-    p->fft_variant = best->fv;
-    p->mom_lanes[0] = best->lv;
-    p->mom_lanes[1] = best->lx;
-    p->eval_lanes[0] = p->eval_lanes[1] = best->el;
-    p->item_split = best->sp;
+    apply(cur);
     if (rc) return rc;
-    p->tuning = nnfft_tuning{best->lv, best->lx, best->fv, 1, cfgs[0].t, best->t, best->sp,
-                             with_nodes ? 1 : 0, best->el, best->el};
-    // the work lists of the current node set follow the chosen split
+    if (default_ms < 0) {                      // nothing to choose between: time the one config
+        double ms = 0;
+        if ((rc = time_cfg(cur, ms))) return rc;
+        default_ms = cur_ms = ms;
+    }
+    p->tuning = nnfft_tuning{cur.lv, cur.lx, cur.fv, 1, default_ms, cur_ms, cur.sp,
+                             with_nodes ? 1 : 0, cur.el, cur.el, cur.cap};
+    // the work lists of the current node set follow the chosen split and cap
     if (with_nodes && (rc = run())) return rc;
     return collect_status(p);
 }
@@ -1304,6 +1349,7 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
     out->item_split = p->item_split;
     out->eval_lanes_v = p->eval_lanes[0];
     out->eval_lanes_x = p->eval_lanes[1];
+    out->item_cap = p->item_cap;
     return NNFFT_OK;
 }
 
@@ -1313,15 +1359,19 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     auto ok_elanes = [](int l) { return l == 0 || l == EVAL_FLAT || l == 8 || l == 32; };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
-        (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1))
+        (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1) ||
+        (t->item_cap != 0 && t->item_cap != 32 && t->item_cap != 64 && t->item_cap != 128 &&
+         t->item_cap != ITEM_CAP))
         return fail(NNFFT_EINVAL, "invalid tuning values");
     p->mom_lanes[0] = t->moments_lanes_v;
     p->mom_lanes[1] = t->moments_lanes_x;
     p->eval_lanes[0] = t->eval_lanes_v ? t->eval_lanes_v : 32;
     p->eval_lanes[1] = t->eval_lanes_x ? t->eval_lanes_x : 32;
     p->fft_variant = t->fft_variant;
-    if (t->item_split != p->item_split) {         // work lists are built with the nodes
+    const int cap = t->item_cap ? t->item_cap : ITEM_CAP;
+    if (t->item_split != p->item_split || cap != p->item_cap) {   // work lists: built with the nodes
         p->item_split = t->item_split;
+        p->item_cap = cap;
         p->side[0].set = p->side[1].set = false;
     }
     return NNFFT_OK;

@@ -54,7 +54,8 @@ class Tuning(ctypes.Structure):
                 ("fft_variant", ctypes.c_int), ("tuned", ctypes.c_int),
                 ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
                 ("item_split", ctypes.c_int), ("timed_transform", ctypes.c_int),
-                ("eval_lanes_v", ctypes.c_int), ("eval_lanes_x", ctypes.c_int)]
+                ("eval_lanes_v", ctypes.c_int), ("eval_lanes_x", ctypes.c_int),
+                ("item_cap", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -317,11 +318,11 @@ class Plan:
         return self.tuning()
 
     def set_tuning(self, moments_lanes_v=32, moments_lanes_x=32, fft_variant=0, item_split=0,
-                   eval_lanes_v=32, eval_lanes_x=32):
-        """Apply a kernel-variant configuration (see autotune); a changed item_split needs
-        set_nodes again."""
+                   eval_lanes_v=32, eval_lanes_x=32, item_cap=256):
+        """Apply a kernel-variant configuration (see autotune); a changed item_split or
+        item_cap needs set_nodes again."""
         t = Tuning(int(moments_lanes_v), int(moments_lanes_x), int(fft_variant), 0, 0.0, 0.0,
-                   int(item_split), 0, int(eval_lanes_v), int(eval_lanes_x))
+                   int(item_split), 0, int(eval_lanes_v), int(eval_lanes_x), int(item_cap))
         _check(self._lib.nnfft_set_tuning(self._h, ctypes.byref(t)))
         return self
 

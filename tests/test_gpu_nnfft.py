@@ -417,10 +417,11 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
     assert t["tuned"] == 1 and t["moments_lanes_v"] in (8, 16, 32) and t["moments_lanes_x"] in (8, 16, 32)
     assert t["eval_lanes_v"] in (1, 8, 32) and t["eval_lanes_x"] in (1, 8, 32)
-    assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= t["default_ms"]
+    assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
     assert t["timed_transform"] == 0
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
     assert t["timed_transform"] == 1 and t["item_split"] in (0, 1)
+    assert t["item_cap"] in (32, 64, 128, 256) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
     y1, z1 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
     y2, z2 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
     plan.sync()
@@ -714,3 +715,76 @@ def test_fixed_point_coordinate_conversion_matches_cuda():
         ft, fr = Fraction(float(t)), Fraction(float(r))
         assert abs(ft) <= abs(exact) and abs(exact) - abs(ft) < Fraction(float(np.spacing(np.abs(t))))
         assert abs(fr - exact) <= Fraction(float(np.spacing(np.abs(r)))) / 2
+
+
+@pytest.mark.parametrize("dtype,arith,m,tol", [(torch.complex64, None, 4, 2e-5),
+                                               (torch.complex128, "fp64", 8, 1e-12),
+                                               (torch.complex128, None, 8, 1e-12)])
+def test_item_caps(dtype, arith, m, tol):
+    """Work items of at most 256, 128, 64 or 32 points: the transform within tolerance of the
+    direct sums for each cap and moments width, on dense cells (~60 points per cell) and
+    on nodes crowded into a few cells (thousands of points: one cell becomes many items);
+    repeated runs bitwise equal; an invalid cap is rejected."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 300, 40000, 30000
+    v, x, f = W.nnfft_inputs(M1, M2, 101, dtype=npd)
+    g = W.adjoint_inputs(M2, 101, dtype=npd)
+    rng = np.random.default_rng(102)
+    vc = (rng.random(M1) * 2e-3 - 1e-3) + 0.25          # a few cells hold all v nodes
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    if arith == "fp64":
+        plan.set_arith(B.ARITH_FP64)
+    rows2, rows1 = W.sample_rows(M2, 48, 14), W.sample_rows(M1, 48, 15)
+    for nodes_v in (v, vc):
+        want_y = oracle.nnfft_direct(N, nodes_v, f.astype(np.complex128), x, rows=rows2)
+        want_z = oracle.nnfft_adjoint_direct(N, nodes_v, x, g.astype(np.complex128), rows=rows1)
+        for cap in (256, 128, 64, 32):
+            for ml in (32, 8):
+                plan.set_tuning(ml, ml, 0, 0, 1, 1, item_cap=cap)
+                plan.set_nodes(dev(nodes_v), dev(x))
+                y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+                y2, z2 = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+                plan.sync()
+                assert plan.tuning()["item_cap"] == cap
+                y, z = y.cpu().numpy(), z.cpu().numpy()
+                assert np.array_equal(y, y2.cpu().numpy()) and np.array_equal(z, z2.cpu().numpy())
+                y, z = y.astype(np.complex128), z.astype(np.complex128)
+                assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= tol, (cap, ml)
+                assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= tol, (cap, ml)
+    with pytest.raises(B.NNFFTError):
+        plan.set_tuning(32, 32, 0, 0, 32, 32, item_cap=48)
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+def test_equispaced_special_cases(dtype, m, tol):
+    """The NNFFT's equispaced special cases, checked with numpy alone: v_k = k/N gives the
+    NFFT y_j = sum_k f_k e^{-2 pi i k x_j}; x_j = j/N gives its transpose
+    y_j = sum_k f_k e^{-2 pi i j v_k}; both equispaced give a length-N DFT (numpy FFT)."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N = 256
+    k = np.arange(-N // 2, N // 2)
+    grid = k / N
+    rng = np.random.default_rng(103)
+    xr = rng.uniform(-0.5, 0.5, 3000)
+    vr = rng.uniform(-0.5, 0.5, 3000)
+    fN = (rng.standard_normal(N) + 1j * rng.standard_normal(N)).astype(npd)
+    fM = (rng.standard_normal(3000) + 1j * rng.standard_normal(3000)).astype(npd)
+
+    def run(v, x, f):
+        plan = B.Plan(N, len(v), len(x), 2.0, 2.0, m, m, dtype=dtype)
+        plan.set_nodes(dev(v), dev(x))
+        y = plan.exec(dev(f, dtype))
+        plan.sync()
+        return y.cpu().numpy().astype(np.complex128)
+
+    f = fN.astype(np.complex128)
+    want = np.exp(-2j * np.pi * np.outer(xr, k)) @ f                  # NFFT
+    assert np.max(np.abs(run(grid, xr, fN) - want)) / np.sum(np.abs(f)) <= tol
+    f = fM.astype(np.complex128)
+    want = np.exp(-2j * np.pi * np.outer(k, vr)) @ f                  # transposed NFFT
+    assert np.max(np.abs(run(vr, grid, fM) - want)) / np.sum(np.abs(f)) <= tol
+    f = fN.astype(np.complex128)
+    # y_j = sum_k f_k e^{-2 pi i k j / N}, k, j in I_N: a DFT of the coefficients reordered
+    # to k mod N, read back at j mod N
+    want = np.fft.fft(np.fft.ifftshift(f))[np.arange(-N // 2, N // 2) % N]
+    assert np.max(np.abs(run(grid, grid, fN) - want)) / np.sum(np.abs(f)) <= tol
