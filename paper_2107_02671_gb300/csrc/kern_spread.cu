@@ -445,9 +445,19 @@ __device__ __forceinline__ void rs_team(Real (&v)[32], int sub) {
     }
 }
 
+// Points per lane loaded at a time and blocks per SM for the team moments kernel: FP32
+// at 4 points and 6 blocks for D <= 8 (40 registers without spills: 75 % occupancy for
+// the latency of the value gathers), 4 blocks above; FP64 at the work item's 8 per lane.
+template <typename Real, int D> struct TeamCfg {
+    static constexpr bool f32 = std::is_same<Real, float>::value;
+    static constexpr int CH = f32 ? 4 : PPL;
+    static constexpr int MINB = f32 ? (D <= 8 ? 6 : 4) : 1;
+};
+
 template <typename Real, int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, TeamCfg<Real, D>::MINB)
 k_moments_team(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__restrict__ P) {
+    constexpr int CH = TeamCfg<Real, D>::CH;
     static_assert(2 * D <= 32, "team moments hold at most 16 degrees");
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int sub = threadIdx.x & (TEAM - 1);
@@ -460,20 +470,20 @@ k_moments_team(SideK<Real> S, const C2<Real> *__restrict__ vals, C2<Real> *__res
     Real ar[D], ai[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) { ar[d] = Real(0); ai[d] = Real(0); }
-    for (int c0 = pb; c0 < pe; c0 += TEAM * PPL) {
-        Real yv[PPL];
-        int jv[PPL];
+    for (int c0 = pb; c0 < pe; c0 += TEAM * CH) {
+        Real yv[CH];
+        int jv[CH];
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) {
+        for (int k = 0; k < CH; ++k) {
             const int p = c0 + sub + TEAM * k;
             yv[k] = p < pe ? S.ys[p] : Real(0);
             jv[k] = p < pe ? S.perm[p] : -1;
         }
-        C2<Real> fv[PPL];
+        C2<Real> fv[CH];
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) fv[k] = jv[k] >= 0 ? vals[jv[k]] : mk2<Real>(Real(0), Real(0));
+        for (int k = 0; k < CH; ++k) fv[k] = jv[k] >= 0 ? vals[jv[k]] : mk2<Real>(Real(0), Real(0));
 #pragma unroll
-        for (int k = 0; k < PPL; ++k) {
+        for (int k = 0; k < CH; ++k) {
             if (jv[k] < 0) continue;
             Real T[D];
             cheb<Real, D>(yv[k], T);
