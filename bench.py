@@ -263,10 +263,10 @@ def run_reference(args, rank, world):
 # split-precision point-kernel variant at the headline size, from ncu captures of
 # `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
 # with T = 8,8,0,0,1,1 / 32,32,0,0,32,32 / 16,16,0,0,8,8 (profiles/k_*_nnfft_fp64_N4096_M2e20.md).
-# The sources the kernels are built from were hashed at capture time; a changed source
-# reports null.
-NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "internal.h"]
-NCU_HASH = "904f7d23ef350aa3"
+# The files the kernels are built from (their code, the double-float primitives, the side
+# descriptor) are hashed; a change since the capture reports null.
+NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "side.h"]
+NCU_HASH = "6655c79950a54511"
 NCU_TRAFFIC = {
     "k_moments_df_team<14>": 29463808,          # 8 lanes per work item
     "k_moments_df_half<14>": 29482752,          # 16
