@@ -82,6 +82,20 @@ struct NodeInst {
     int ncell, cell_base;
 };
 
+// Radix-sort tiles of a batch side, aligned to the instances: tile t holds the points
+// [start[t], min(start[t] + SORT_TILE, pt_off[inst[t] + 1])) of instance inst[t], and
+// inst_tile0[i] is the first tile of instance i.  A batch sorts each instance by its
+// local cell (key - cell_base), so the passes cover the largest instance's cells, not
+// all cells of the side.  inst == nullptr: one instance, tiles of SORT_TILE points.
+struct SortTiles {
+    const int *inst;
+    const long long *start;
+    const int *inst_tile0;
+    const long long *pt_off;
+    const NodeInst *tab;
+    int ntiles, ninst;
+};
+
 // Grid-stage geometry of one instance on one side.  CoefT: Real, or float2 (hi, lo)
 // pairs for split precision.
 template <typename CoefT> struct GridInst {
@@ -152,22 +166,26 @@ int sinc_exec_capacity(int64_t N, int64_t L1, int64_t L2, int64_t L1cap, int64_t
 size_t sinc_release_stream(cudaStream_t stream);
 
 // ---- kern_nodes.cu ----------------------------------------------------------------
-size_t radix_sort_hist_len(int n);
-// Fused step 0: keys, local coordinates (caller order, format yfmt: 0 float, 1 double,
-// 2 float pair) and the first radix pass's histogram in hist (radix_sort_hist_len ints).
-// With ninst > 1, pt_off [ninst + 1] (device) splits the points into instances and
-// tab [ninst] (device) gives each instance's binning; otherwise `one` applies to all.
+// Sort buffer (ints) for ntiles tiles and ninst instances: per-tile digit counts and
+// per-instance digit totals.
+size_t radix_sort_hist_len(int ntiles, int ninst);
+// Fused step 0: keys (global cell), local coordinates (caller order, format yfmt: 0 float,
+// 1 double, 2 float pair) and the first radix pass's per-tile digit counts and digit
+// totals in hist (radix_sort_hist_len ints).  tiles: a batch's instance-aligned tiles
+// (each point takes its instance's binning, keys offset by the instance's first cell), or
+// nullptr for one instance with binning `one` and ntiles = ceil(n / SORT_TILE).
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
-                               const long long *pt_off, const NodeInst *tab, int ninst,
-                               uint32_t *keys, void *y_user, int yfmt, int *hist, int *status,
-                               cudaStream_t s);
+                               const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
+                               int yfmt, int *hist, int *status, cudaStream_t s);
 // Stable LSD radix sort of the keys from launch_node_keys_y (values: the identity
-// permutation, generated in pass 0); the last pass also moves the ybytes-byte
-// coordinates: ys[sorted position] = y_user[original index].
+// permutation, generated in pass 0) by the low key_bits bits of key - cell_base (the
+// whole key for one instance; within each instance for a batch, whose points are
+// grouped by instance in cell_base order, so the result is sorted by key); the last pass
+// also moves the ybytes-byte coordinates: ys[sorted position] = y_user[original index].
 cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
-                             int *hist, int n, int key_bits, const void *y_user, void *ys,
-                             int ybytes, cudaStream_t s, uint32_t **keys_sorted,
-                             int **vals_sorted);
+                             int *hist, const SortTiles *tiles, int ntiles, int n, int key_bits,
+                             const void *y_user, void *ys, int ybytes, cudaStream_t s,
+                             uint32_t **keys_sorted, int **vals_sorted);
 // Cell offsets (cell_off[c] = first sorted point of cell c, cell_off[ncell] = n) and work
 // items (at most cap sorted points of one cell each, ITEM_CAP_MIN <= cap <= ITEM_CAP;
 // item_off[c] = first item of cell c, *nitems = total) from the sorted keys.  With

@@ -113,47 +113,52 @@ __device__ __forceinline__ void store_y(void *yout, int fmt, long long i, long l
     }
 }
 
-// Step 0 for one node side in a single pass over the nodes: validate each node,
-// compute its cell key c - c_lo and local coordinate y = 2 (u - c) - 1 (c = floor(u),
-// u = node * scale, node_fixed), store y (caller order) in the plan's format, and
-// count the digits of the first radix pass for this block's tile (the tiles match
-// k_sort_scatter's: SORT_TILE keys per block).  In a batch each point takes the
-// binning of its instance and the key is offset by the instance's first cell.
-__global__ void __launch_bounds__(SORT_THREADS)
-k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
-              const long long *__restrict__ pt_off, const NodeInst *__restrict__ tab, int ninst,
-              uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int nblocks,
-              int *__restrict__ hist, int *__restrict__ digit_tot, int *status) {
-    __shared__ int h[256];
-    __shared__ int first_inst;
-    h[threadIdx.x] = 0;
-    const long long base = (long long)blockIdx.x * SORT_TILE;
-    if (threadIdx.x == 0) {       // instance of the tile's first point: pt_off[j] <= base < pt_off[j+1]
-        int lo = 0, hi = ninst > 1 ? ninst : 1;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (pt_off[mid] <= base) lo = mid; else hi = mid;
-        }
-        first_inst = lo;
+// Points of sort tile t and their instance: instance-aligned tiles of a batch, or tiles of
+// SORT_TILE consecutive points of a single instance.
+struct TileSpan {
+    long long begin, end;
+    int inst;
+};
+__device__ __forceinline__ TileSpan tile_span(const SortTiles &st, int t, int n) {
+    TileSpan r;
+    if (st.inst == nullptr) {
+        r.inst = 0;
+        r.begin = (long long)t * SORT_TILE;
+        r.end = min(r.begin + SORT_TILE, (long long)n);
+    } else {
+        r.inst = st.inst[t];
+        r.begin = st.start[t];
+        r.end = min(r.begin + SORT_TILE, st.pt_off[r.inst + 1]);
     }
+    return r;
+}
+
+// Step 0 for one node side in a single pass over the nodes: validate each node,
+// compute its cell key (cell_base + c - c_lo) and local coordinate y = 2 (u - c) - 1
+// (c = floor(u), u = node * scale, node_fixed), store y (caller order) in the plan's
+// format, and count the digits of the first radix pass (of c - c_lo, the local cell) for
+// this block's tile (the tiles of the sort passes), into the per-tile counts and the
+// digit totals of the tile's instance.
+__global__ void __launch_bounds__(SORT_THREADS)
+k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles st,
+              uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int ntiles,
+              int *__restrict__ hist, int *__restrict__ tot, int *status) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    const TileSpan sp = tile_span(st, blockIdx.x, n);
+    const NodeInst I = st.inst == nullptr ? one : st.tab[sp.inst];
     __syncthreads();
     constexpr int PER = SORT_TILE / SORT_THREADS;
     double xv[PER];
 #pragma unroll
     for (int r = 0; r < PER; ++r) {            // all loads of the thread first
-        const long long i = base + threadIdx.x + (long long)r * SORT_THREADS;
-        xv[r] = i < n ? nodes[i] : 0.0;
+        const long long i = sp.begin + threadIdx.x + (long long)r * SORT_THREADS;
+        xv[r] = i < sp.end ? nodes[i] : 0.0;
     }
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const long long i = base + threadIdx.x + (long long)r * SORT_THREADS;
-        if (i >= n) break;
-        NodeInst I = one;
-        if (ninst > 1) {              // a tile meets few instances: step forward from the first
-            int j = first_inst;
-            while (j + 1 < ninst && __ldg(pt_off + j + 1) <= i) ++j;
-            I = tab[j];
-        }
+        const long long i = sp.begin + threadIdx.x + (long long)r * SORT_THREADS;
+        if (i >= sp.end) break;
         long long c = 0, Y = -0x7fffffffffffffffLL - 1;
         long long ic = 0;
         if (!node_fixed(xv[r], I.S, c, Y)) {
@@ -166,31 +171,59 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one,
                 ic = ic < 0 ? 0 : I.ncell - 1;
             }
         }
-        ic += I.cell_base;
-        keys[i] = (uint32_t)ic;
+        keys[i] = (uint32_t)(ic + I.cell_base);
         store_y(yout, yfmt, i, Y);
         atomicAdd(&h[ic & 255], 1);
     }
     __syncthreads();
-    hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
-    if (h[threadIdx.x]) atomicAdd(&digit_tot[threadIdx.x], h[threadIdx.x]);
+    hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    if (h[threadIdx.x]) atomicAdd(&tot[sp.inst * 256 + threadIdx.x], h[threadIdx.x]);
 }
 
 // ---- radix sort ------------------------------------------------------------------
 __global__ void __launch_bounds__(SORT_THREADS)
-k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
-               int *__restrict__ hist, int *__restrict__ digit_tot) {
+k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, SortTiles st, int ntiles,
+               int *__restrict__ hist, int *__restrict__ tot) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
+    const TileSpan sp = tile_span(st, blockIdx.x, n);
+    const uint32_t cb = st.inst == nullptr ? 0u : (uint32_t)st.tab[sp.inst].cell_base;
     __syncthreads();
-    long long base = (long long)blockIdx.x * SORT_TILE;
-    for (int i = threadIdx.x; i < SORT_TILE; i += SORT_THREADS) {
-        long long idx = base + i;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1);
+    for (long long i = sp.begin + threadIdx.x; i < sp.end; i += SORT_THREADS)
+        atomicAdd(&h[((keys[i] - cb) >> shift) & 255u], 1);
+    __syncthreads();
+    hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    if (h[threadIdx.x]) atomicAdd(&tot[sp.inst * 256 + threadIdx.x], h[threadIdx.x]);   // order-free
+}
+
+// Exclusive scan of a batch's digit-major tile counts, one warp per (instance, digit):
+// the digit's first position in the instance's sorted range (the instance's first point
+// plus its keys with a smaller digit), then a scan over the instance's tiles.
+__global__ void __launch_bounds__(256)
+k_seg_scan(int *__restrict__ hist, int ntiles, const int *__restrict__ tot, SortTiles st) {
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const int inst = g >> 8, d = g & 255;
+    if (inst >= st.ninst) return;
+    const int *ti = tot + inst * 256;
+    int part = 0;
+    for (int j = lane; j < d; j += 32) part += ti[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    int carry = (int)st.pt_off[inst] + part;
+    const int t0 = st.inst_tile0[inst], t1 = st.inst_tile0[inst + 1];
+    int *row = hist + (long long)d * ntiles;
+    for (int t = t0; t < t1; t += 32) {
+        const int i = t + lane;
+        const int v = i < t1 ? row[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (i < t1) row[i] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    __syncthreads();
-    hist[(long long)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
-    if (h[threadIdx.x]) atomicAdd(&digit_tot[threadIdx.x], h[threadIdx.x]);   // integer: order-free
 }
 
 // Exclusive scan of the digit-major histogram: block d scans row d (the counts of
@@ -243,13 +276,14 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // shared memory and then written out in that order, so each digit's run of the tile
 // leaves as consecutive addresses (coalesced) instead of one scattered store per key.
 // FIRST: the values are the identity (vin unused).  Y: payload moved along in the last
-// pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.
+// pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.  The
+// digit is taken from key - cell_base of the tile's instance.
 template <bool FIRST, typename Y>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
-               int nblocks, const int *__restrict__ hist_scanned, const Y *__restrict__ yin,
-               Y *__restrict__ yout) {
+               SortTiles st, int ntiles, const int *__restrict__ hist_scanned,
+               const Y *__restrict__ yin, Y *__restrict__ yout) {
     constexpr int WARPS = SORT_THREADS / 32;
     constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 8
     static_assert(SORT_THREADS == 256, "one thread per digit in the digit scans");
@@ -262,7 +296,9 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
     __syncwarp();
-    const long long tile0 = (long long)blockIdx.x * SORT_TILE;
+    const TileSpan sp = tile_span(st, blockIdx.x, n);
+    const uint32_t cb = st.inst == nullptr ? 0u : (uint32_t)st.tab[sp.inst].cell_base;
+    const long long tile0 = sp.begin;
     const long long base = tile0 + (long long)w * (32 * ROUNDS);
     uint32_t key[ROUNDS];
     int val[ROUNDS], rank[ROUNDS];
@@ -271,7 +307,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const long long idx = base + r * 32 + lane;
-        const bool valid = idx < n;
+        const bool valid = idx < sp.end;
         key[r] = valid ? kin[idx] : 0u;
         if (FIRST) val[r] = (int)idx;
         else val[r] = valid ? vin[idx] : 0;
@@ -279,8 +315,8 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const long long idx = base + r * 32 + lane;
-        const bool valid = idx < n;
-        const unsigned d = valid ? ((key[r] >> shift) & 255u) : 256u;
+        const bool valid = idx < sp.end;
+        const unsigned d = valid ? (((key[r] - cb) >> shift) & 255u) : 256u;
         // lanes with the same 9-bit value d (256 marks an invalid lane): intersect the
         // ballots of the bits of d
         unsigned peers = 0xffffffffu;
@@ -319,25 +355,25 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         for (int ww = 0; ww < WARPS; ++ww) wpre += ww < w ? wtot[ww] : 0;
         const int start = wpre + incl - run;
         lstart[d] = start;
-        delta[d] = hist_scanned[(long long)d * nblocks + blockIdx.x] - start;
+        delta[d] = hist_scanned[(long long)d * ntiles + blockIdx.x] - start;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
         const long long idx = base + r * 32 + lane;
-        if (idx < n) {
-            const unsigned d = (key[r] >> shift) & 255u;
+        if (idx < sp.end) {
+            const unsigned d = ((key[r] - cb) >> shift) & 255u;
             const int loc = lstart[d] + cnt[w][d] + rank[r];
             skey[loc] = key[r];
             sval[loc] = val[r];
         }
     }
     __syncthreads();
-    const int tn = (int)min((long long)SORT_TILE, (long long)n - tile0);
+    const int tn = (int)(sp.end - tile0);
     for (int i = threadIdx.x; i < tn; i += SORT_THREADS) {
         const uint32_t k = skey[i];
         const int v = sval[i];
-        const int pos = delta[(k >> shift) & 255u] + i;
+        const int pos = delta[((k - cb) >> shift) & 255u] + i;
         kout[pos] = k;
         vout[pos] = v;
         if constexpr (!std::is_void<Y>::value) yout[pos] = yin[v];
@@ -592,53 +628,67 @@ cudaError_t launch_split_items(const int *nitems, const int *item_pb, const int 
     return cudaGetLastError();
 }
 
-size_t radix_sort_hist_len(int n) {
-    long long nb = n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1;
-    return (size_t)(256 * nb + 1 + 256);   // histogram, total, digit totals
+size_t radix_sort_hist_len(int ntiles, int ninst) {
+    // per-tile digit counts (digit-major), then the digit totals of every instance
+    return (size_t)256 * (size_t)(ntiles > 0 ? ntiles : 1) + (size_t)256 * (size_t)(ninst > 0 ? ninst : 1);
 }
 
+namespace {
+SortTiles single_tiles() {
+    SortTiles t;
+    t.inst = nullptr;
+    t.start = nullptr;
+    t.inst_tile0 = nullptr;
+    t.pt_off = nullptr;
+    t.tab = nullptr;
+    t.ntiles = 0;
+    t.ninst = 1;
+    return t;
+}
+}  // namespace
+
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
-                               const long long *pt_off, const NodeInst *tab, int ninst,
-                               uint32_t *keys, void *y_user, int yfmt, int *hist, int *status,
-                               cudaStream_t s) {
+                               const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
+                               int yfmt, int *hist, int *status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int nblocks = cdiv(n, SORT_TILE);
-    int *digit_tot = hist + 256LL * nblocks + 1;
-    cudaError_t e = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
+    const SortTiles st = tiles ? *tiles : single_tiles();
+    if (!tiles) ntiles = cdiv(n, SORT_TILE);
+    int *tot = hist + 256LL * ntiles;
+    cudaError_t e = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
     if (e != cudaSuccess) return e;
-    k_node_keys_y<<<nblocks, SORT_THREADS, 0, s>>>(nodes, n, one, pt_off, tab, ninst, keys,
-                                                   y_user, yfmt, nblocks, hist, digit_tot,
-                                                   status);
+    k_node_keys_y<<<ntiles, SORT_THREADS, 0, s>>>(nodes, n, one, st, keys, y_user, yfmt, ntiles,
+                                                  hist, tot, status);
     count_launches(1);
     return cudaGetLastError();
 }
 
 namespace {
 template <bool FIRST, typename Y>
-void scatter_launch(int nblocks, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
-                    int *vb, int n, int shift, const int *hist, const void *yin, void *yout) {
-    k_sort_scatter<FIRST, Y><<<nblocks, SORT_THREADS, 0, s>>>(
-        ka, va, kb, vb, n, shift, nblocks, hist, static_cast<const Y *>(yin),
+void scatter_launch(int ntiles, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
+                    int *vb, int n, int shift, const SortTiles &st, const int *hist,
+                    const void *yin, void *yout) {
+    k_sort_scatter<FIRST, Y><<<ntiles, SORT_THREADS, 0, s>>>(
+        ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
         static_cast<Y *>(yout));
 }
 template <bool FIRST>
-void scatter_dispatch(int ybytes, int nblocks, cudaStream_t s, const uint32_t *ka, const int *va,
-                      uint32_t *kb, int *vb, int n, int shift, const int *hist, const void *yin,
-                      void *yout) {
+void scatter_dispatch(int ybytes, int ntiles, cudaStream_t s, const uint32_t *ka, const int *va,
+                      uint32_t *kb, int *vb, int n, int shift, const SortTiles &st,
+                      const int *hist, const void *yin, void *yout) {
     if (ybytes == 4)
-        scatter_launch<FIRST, unsigned>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin, yout);
+        scatter_launch<FIRST, unsigned>(ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
     else if (ybytes == 8)
-        scatter_launch<FIRST, unsigned long long>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin,
-                                                  yout);
+        scatter_launch<FIRST, unsigned long long>(ntiles, s, ka, va, kb, vb, n, shift, st, hist,
+                                                  yin, yout);
     else
-        scatter_launch<FIRST, void>(nblocks, s, ka, va, kb, vb, n, shift, hist, yin, yout);
+        scatter_launch<FIRST, void>(ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
 }
 }  // namespace
 
 cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
-                             int *hist, int n, int key_bits, const void *y_user, void *ys,
-                             int ybytes, cudaStream_t s, uint32_t **keys_sorted,
-                             int **vals_sorted) {
+                             int *hist, const SortTiles *tiles, int ntiles, int n, int key_bits,
+                             const void *y_user, void *ys, int ybytes, cudaStream_t s,
+                             uint32_t **keys_sorted, int **vals_sorted) {
     uint32_t *ka = keys, *kb = keys_alt;
     int *va = vals, *vb = vals_alt;
     if (n <= 1) {
@@ -651,24 +701,28 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
         *vals_sorted = va;
         return cudaSuccess;
     }
-    const int nblocks = cdiv(n, SORT_TILE);
-    int *digit_tot = hist + 256LL * nblocks + 1;
+    const SortTiles st = tiles ? *tiles : single_tiles();
+    if (!tiles) ntiles = cdiv(n, SORT_TILE);
+    int *tot = hist + 256LL * ntiles;
     const int passes = (key_bits + 7) / 8;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
         const bool last = pass == passes - 1;
         if (pass > 0) {
-            cudaError_t e0 = cudaMemsetAsync(digit_tot, 0, 256 * sizeof(int), s);
+            cudaError_t e0 = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
             if (e0 != cudaSuccess) return e0;
-            k_sort_upsweep<<<nblocks, SORT_THREADS, 0, s>>>(ka, n, shift, nblocks, hist, digit_tot);
+            k_sort_upsweep<<<ntiles, SORT_THREADS, 0, s>>>(ka, n, shift, st, ntiles, hist, tot);
             count_launches(1);
-        }   // pass 0: histogram and digit totals come from k_node_keys_y
-        k_sort_scan_rows<<<256, 256, 0, s>>>(hist, nblocks, digit_tot);
+        }   // pass 0: tile counts and digit totals come from k_node_keys_y
+        if (tiles)
+            k_seg_scan<<<cdiv((long long)st.ninst * 256, 8), 256, 0, s>>>(hist, ntiles, tot, st);
+        else
+            k_sort_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, tot);
         const int yb = last ? ybytes : 0;
         if (pass == 0)
-            scatter_dispatch<true>(yb, nblocks, s, ka, va, kb, vb, n, shift, hist, y_user, ys);
+            scatter_dispatch<true>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, y_user, ys);
         else
-            scatter_dispatch<false>(yb, nblocks, s, ka, va, kb, vb, n, shift, hist, y_user, ys);
+            scatter_dispatch<false>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, y_user, ys);
         count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -58,6 +58,10 @@ struct Side {
     NodeInst one{};                        // binning of a single-instance plan
     long long *pt_off = nullptr;           // [ninst + 1] device, batches only
     NodeInst *node_tab = nullptr;          // [ninst] device, batches only
+    // batches: instance-aligned sort tiles; keys are sorted by the local cell within each
+    // instance (sort_bits: the largest instance's cells) instead of over all cells
+    SortTiles tiles{};
+    int sort_bits = 8;
     void *coef = nullptr;                  // [ninst][2m][D] real tap coefficients
     void *coef_df = nullptr;               // same as (hi, lo) float pairs
     void *rfit = nullptr;                  // x side: [ncell][NR] real 1/phihat1 fits
@@ -497,10 +501,37 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         S.max_items_alloc = S.ncell + (S.M + ITEM_CAP_MIN - 1) / ITEM_CAP_MIN + (int)count;
         S.key_bits = key_bits_for(S.ncell);
         S.one = tab[0];
+        S.sort_bits = S.key_bits;
         if (count > 1) {
             if ((rc = upload_vec(p, &S.node_tab, tab, "binning tables")) ||
                 (rc = upload_vec(p, &S.pt_off, pt_off, "instance offsets")))
                 return rc;
+            std::vector<int> tinst, tile0((size_t)count + 1, 0);
+            std::vector<long long> tstart;
+            int max_cells = 1;
+            for (int64_t i = 0; i < count; ++i) {
+                tile0[(size_t)i] = (int)tinst.size();
+                for (long long q = pt_off[(size_t)i]; q < pt_off[(size_t)i + 1]; q += SORT_TILE) {
+                    tinst.push_back((int)i);
+                    tstart.push_back(q);
+                }
+                max_cells = std::max(max_cells, tab[(size_t)i].ncell);
+            }
+            tile0[(size_t)count] = (int)tinst.size();
+            int *d_inst = nullptr, *d_tile0 = nullptr;
+            long long *d_start = nullptr;
+            if (!tinst.empty() && ((rc = upload_vec(p, &d_inst, tinst, "sort tiles")) ||
+                                   (rc = upload_vec(p, &d_start, tstart, "sort tiles"))))
+                return rc;
+            if ((rc = upload_vec(p, &d_tile0, tile0, "sort tiles"))) return rc;
+            S.tiles.inst = d_inst;
+            S.tiles.start = d_start;
+            S.tiles.inst_tile0 = d_tile0;
+            S.tiles.pt_off = S.pt_off;
+            S.tiles.tab = S.node_tab;
+            S.tiles.ntiles = (int)tinst.size();
+            S.tiles.ninst = (int)count;
+            S.sort_bits = key_bits_for(max_cells);
         }
         if ((rc = upload_real(p, &S.coef, coef_all, "window coefficients"))) return rc;
         if (p->split_ok && (rc = upload_df2(p, &S.coef_df, coef_all, 1.0, "window coefficients (df)")))
@@ -537,7 +568,10 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         const size_t M = (size_t)S.M;
         if ((rc = dalloc_n(p, &S.keys, M, "keys")) || (rc = dalloc_n(p, &S.keys_alt, M, "keys")) ||
             (rc = dalloc_n(p, &S.vals, M, "perm")) || (rc = dalloc_n(p, &S.vals_alt, M, "perm")) ||
-            (rc = dalloc_n(p, &S.hist, radix_sort_hist_len(S.M), "sort histogram")) ||
+            (rc = dalloc_n(p, &S.hist,
+                           count > 1 ? radix_sort_hist_len(S.tiles.ntiles, (int)count)
+                                     : radix_sort_hist_len((S.M + SORT_TILE - 1) / SORT_TILE, 1),
+                           "sort histogram")) ||
             (rc = dalloc(p, &S.ys, M * rs, "sorted coordinates")) ||
             (rc = dalloc(p, &S.y_user, M * rs, "coordinates")) ||
             (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
@@ -799,13 +833,14 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     }
     const int yfmt = !p->dbl ? 0 : (p->split ? 2 : 1);
     const int ybytes = p->dbl ? 8 : 4;
-    NN_CUDA(launch_node_keys_y(nodes, S.M, S.one, S.pt_off, S.node_tab, (int)p->ninst, S.keys,
-                               S.y_user, yfmt, S.hist, p->status, st),
+    const SortTiles *tiles = p->ninst > 1 ? &S.tiles : nullptr;
+    NN_CUDA(launch_node_keys_y(nodes, S.M, S.one, tiles, S.tiles.ntiles, S.keys, S.y_user, yfmt,
+                               S.hist, p->status, st),
             "node keys");
     uint32_t *ks = nullptr;
     int *vs = nullptr;
-    NN_CUDA(radix_sort_cells(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, S.M, S.key_bits,
-                             S.y_user, S.ys, ybytes, st, &ks, &vs),
+    NN_CUDA(radix_sort_cells(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, tiles, S.tiles.ntiles,
+                             S.M, S.sort_bits, S.y_user, S.ys, ybytes, st, &ks, &vs),
             "radix sort");
     S.perm = vs;
     S.keys_sorted = ks;
