@@ -277,8 +277,10 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // leaves as consecutive addresses (coalesced) instead of one scattered store per key.
 // FIRST: the values are the identity (vin unused).  Y: payload moved along in the last
 // pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.  The
-// digit is taken from key - cell_base of the tile's instance.
-template <bool FIRST, typename Y>
+// digit is taken from key - cell_base of the tile's instance.  MATCH: the lanes with the
+// same digit from one match instruction instead of nine ballots (measured: fewer issue
+// slots, faster for large sorts; longer latency, slower for small ones).
+template <bool FIRST, typename Y, bool MATCH>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
@@ -317,14 +319,17 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         const long long idx = base + r * 32 + lane;
         const bool valid = idx < sp.end;
         const unsigned d = valid ? (((key[r] - cb) >> shift) & 255u) : 256u;
-        // lanes with the same 9-bit value d (256 marks an invalid lane): intersect the
-        // ballots of the bits of d
+        // lanes with the same 9-bit value d (256 marks an invalid lane)
         unsigned peers = 0xffffffffu;
+        if constexpr (MATCH) {
+            peers = __match_any_sync(0xffffffffu, d);
+        } else {                                  // intersect the ballots of the bits of d
 #pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const unsigned bit = (d >> b) & 1u;
-            const unsigned bal = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? bal : ~bal;
+            for (int b = 0; b < 9; ++b) {
+                const unsigned bit = (d >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
         }
         const int before = valid ? cnt[w][d] : 0;
         __syncwarp();
@@ -427,32 +432,50 @@ __global__ void __launch_bounds__(1024) k_scan_exclusive(const int *in, int *out
 // The first point i of a cell with more (keys[i + cap] still in the cell) sets *overflow;
 // the scan-based builders launched next then rebuild the items (they return at once
 // otherwise), so the decision stays on the device.
-__global__ void k_cell_offsets_items(const uint32_t *__restrict__ keys, int n, int ncell, int cap,
-                                     int *__restrict__ off, int *__restrict__ item_off,
-                                     int *__restrict__ item_cell, int *__restrict__ item_pb,
-                                     int *__restrict__ item_pe, int *__restrict__ nitems,
-                                     int *__restrict__ overflow) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > n) return;
-    const int prev = i == 0 ? -1 : (int)keys[i - 1];
-    const int cur = i == n ? ncell : (int)keys[i];
-    if (overflow == nullptr) {                            // offsets only
-        for (int c = prev + 1; c <= cur; ++c) off[c] = i;
-        return;
+__global__ void __launch_bounds__(256)
+k_cell_offsets_items(const uint32_t *__restrict__ keys, int n, int ncell, int cap,
+                     int *__restrict__ off, int *__restrict__ item_off,
+                     int *__restrict__ item_cell, int *__restrict__ item_pb,
+                     int *__restrict__ item_pe, int *__restrict__ nitems,
+                     int *__restrict__ overflow) {
+    // four consecutive boundaries i = i0 .. i0 + 3 per thread (one 16-byte key load)
+    const long long i0 = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 > n) return;
+    int k[5];                                   // keys i0 - 1 .. i0 + 3 (ncell at n)
+    k[0] = i0 == 0 ? -1 : (int)keys[i0 - 1];
+    if (i0 + 3 < n) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(keys + i0);
+        k[1] = (int)q.x;
+        k[2] = (int)q.y;
+        k[3] = (int)q.z;
+        k[4] = (int)q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[1 + j] = i0 + j < n ? (int)keys[i0 + j] : ncell;
     }
-    if (cur > prev && i + cap < n && (int)keys[i + cap] == cur) *overflow = 1;
-    for (int c = prev + 1; c <= cur; ++c) {
-        off[c] = i;
-        if (c < ncell) {
-            item_off[c] = c;
-            item_cell[c] = c;
-            item_pb[c] = i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = (int)(i0 + j);
+        if (i > n) break;
+        const int prev = k[j], cur = k[j + 1];
+        if (overflow == nullptr) {                        // offsets only
+            for (int c = prev + 1; c <= cur; ++c) off[c] = i;
+            continue;
         }
-        if (c > 0) item_pe[c - 1] = i;
-    }
-    if (i == n) {
-        item_off[ncell] = ncell;
-        *nitems = ncell;
+        if (cur > prev && i + cap < n && (int)keys[i + cap] == cur) *overflow = 1;
+        for (int c = prev + 1; c <= cur; ++c) {
+            off[c] = i;
+            if (c < ncell) {
+                item_off[c] = c;
+                item_cell[c] = c;
+                item_pb[c] = i;
+            }
+            if (c > 0) item_pe[c - 1] = i;
+        }
+        if (i == n) {
+            item_off[ncell] = ncell;
+            *nitems = ncell;
+        }
     }
 }
 
@@ -663,13 +686,21 @@ cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
 }
 
 namespace {
+// keys from which the scatter ranks with match instructions
+constexpr int SORT_MATCH_MIN = 1 << 23;
+
 template <bool FIRST, typename Y>
 void scatter_launch(int ntiles, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
                     int *vb, int n, int shift, const SortTiles &st, const int *hist,
                     const void *yin, void *yout) {
-    k_sort_scatter<FIRST, Y><<<ntiles, SORT_THREADS, 0, s>>>(
-        ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
-        static_cast<Y *>(yout));
+    if (n >= SORT_MATCH_MIN)
+        k_sort_scatter<FIRST, Y, true><<<ntiles, SORT_THREADS, 0, s>>>(
+            ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
+            static_cast<Y *>(yout));
+    else
+        k_sort_scatter<FIRST, Y, false><<<ntiles, SORT_THREADS, 0, s>>>(
+            ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
+            static_cast<Y *>(yout));
 }
 template <bool FIRST>
 void scatter_dispatch(int ybytes, int ntiles, cudaStream_t s, const uint32_t *ka, const int *va,
@@ -746,7 +777,7 @@ cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell
         cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
-    k_cell_offsets_items<<<cdiv((long long)n + 1, 256), 256, 0, s>>>(
+    k_cell_offsets_items<<<cdiv(((long long)n + 4) / 4, 256), 256, 0, s>>>(
         keys_sorted, n, ncell, cap, cell_off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
     // cells above cap: items by a scan of ceil(count / cap) over the cells
     if (ncell <= ITEMS_ONE_BLOCK_MAX) {

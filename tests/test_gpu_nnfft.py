@@ -788,3 +788,25 @@ def test_equispaced_special_cases(dtype, m, tol):
     # to k mod N, read back at j mod N
     want = np.fft.fft(np.fft.ifftshift(f))[np.arange(-N // 2, N // 2) % N]
     assert np.max(np.abs(run(grid, grid, fN) - want)) / np.sum(np.abs(f)) <= tol
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+def test_large_sort_sampled_rows(dtype, m, tol):
+    """More than 2^23 points per side (the size from which the radix scatter ranks digits
+    with match instructions): sampled rows of the forward and adjoint against the direct
+    sums."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M = 1024, (1 << 23) + 12345
+    v, x, f = W.nnfft_inputs(M, M, 105, dtype=npd)
+    g = W.adjoint_inputs(M, 105, dtype=npd)
+    plan = B.Plan(N, M, M, 2.0, 2.0, m, m, dtype=dtype)
+    plan.set_nodes(dev(v), dev(x))
+    y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+    plan.sync()
+    y, z = y.cpu().numpy().astype(np.complex128), z.cpu().numpy().astype(np.complex128)
+    rows = W.sample_rows(M, 16, 16)
+    want = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
+    assert np.max(np.abs(y[rows] - want)) / np.sum(np.abs(f)) <= tol
+    want = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows)
+    assert np.max(np.abs(z[rows] - want)) / np.sum(np.abs(g)) <= tol
+    plan.close()
