@@ -180,11 +180,13 @@ cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
 // Stable LSD radix sort of the keys from launch_node_keys_y (values: the identity
 // permutation, generated in pass 0) by the low key_bits bits of key - cell_base (the
 // whole key for one instance; within each instance for a batch, whose points are
-// grouped by instance in cell_base order, so the result is sorted by key); the last pass
-// also moves the ybytes-byte coordinates: ys[sorted position] = y_user[original index].
+// grouped by instance in cell_base order, so the result is sorted by key).  The
+// ybytes-byte coordinates end as ys[sorted position] = y_user[original index]: 4-byte ones
+// move with their keys in every pass (y_tmp: scratch of the same size), 8-byte ones are
+// gathered by the last pass.
 cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
                              int *hist, const SortTiles *tiles, int ntiles, int n, int key_bits,
-                             const void *y_user, void *ys, int ybytes, cudaStream_t s,
+                             const void *y_user, void *ys, void *y_tmp, int ybytes, cudaStream_t s,
                              uint32_t **keys_sorted, int **vals_sorted);
 // Cell offsets (cell_off[c] = first sorted point of cell c, cell_off[ncell] = n) and work
 // items (at most cap sorted points of one cell each, ITEM_CAP_MIN <= cap <= ITEM_CAP;

@@ -275,9 +275,12 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // with equal digits keep their input order.  The tile is first reordered by digit in
 // shared memory and then written out in that order, so each digit's run of the tile
 // leaves as consecutive addresses (coalesced) instead of one scattered store per key.
-// FIRST: the values are the identity (vin unused).  Y: payload moved along in the last
-// pass, yout[pos] = yin[value] (unsigned / unsigned long long), or void for none.  The
-// digit is taken from key - cell_base of the tile's instance.  MATCH: the lanes with the
+// FIRST: the values are the identity (vin unused).  Y: the local coordinates, or void.
+// A 4-byte Y is carried through every pass with its key (yout[pos] = yin[input position],
+// read coalesced); an 8-byte Y (float pairs) is gathered in the last pass only,
+// yout[pos] = yin[value] (measured: carrying pays for 4 bytes and costs for 8, whose
+// random reads fetch a larger share of each sector).  The digit is taken from
+// key - cell_base of the tile's instance.  MATCH: the lanes with the
 // same digit from one match instruction instead of nine ballots (measured: fewer issue
 // slots, faster for large sorts; longer latency, slower for small ones).
 template <bool FIRST, typename Y, bool MATCH>
@@ -295,6 +298,9 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     __shared__ int wtot[WARPS];
     __shared__ uint32_t skey[SORT_TILE];
     __shared__ int sval[SORT_TILE];
+    using YS = typename std::conditional<std::is_void<Y>::value, char, Y>::type;
+    constexpr bool CARRY = !std::is_void<Y>::value && sizeof(YS) == 4;
+    __shared__ YS sy[CARRY ? SORT_TILE : 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
     __syncwarp();
@@ -304,6 +310,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     const long long base = tile0 + (long long)w * (32 * ROUNDS);
     uint32_t key[ROUNDS];
     int val[ROUNDS], rank[ROUNDS];
+    YS yv[CARRY ? ROUNDS : 1];
     const unsigned lt = lanemask_lt();
     // issue every load of the warp's keys (and values) before the ranking rounds
 #pragma unroll
@@ -313,6 +320,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         key[r] = valid ? kin[idx] : 0u;
         if (FIRST) val[r] = (int)idx;
         else val[r] = valid ? vin[idx] : 0;
+        if constexpr (CARRY) yv[r] = valid ? yin[idx] : YS(0);
     }
 #pragma unroll
     for (int r = 0; r < ROUNDS; ++r) {
@@ -371,6 +379,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
             const int loc = lstart[d] + cnt[w][d] + rank[r];
             skey[loc] = key[r];
             sval[loc] = val[r];
+            if constexpr (CARRY) sy[loc] = yv[r];
         }
     }
     __syncthreads();
@@ -381,7 +390,8 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         const int pos = delta[((k - cb) >> shift) & 255u] + i;
         kout[pos] = k;
         vout[pos] = v;
-        if constexpr (!std::is_void<Y>::value) yout[pos] = yin[v];
+        if constexpr (CARRY) yout[pos] = sy[i];
+        else if constexpr (!std::is_void<Y>::value) yout[pos] = yin[v];
     }
 }
 
@@ -718,7 +728,7 @@ void scatter_dispatch(int ybytes, int ntiles, cudaStream_t s, const uint32_t *ka
 
 cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
                              int *hist, const SortTiles *tiles, int ntiles, int n, int key_bits,
-                             const void *y_user, void *ys, int ybytes, cudaStream_t s,
+                             const void *y_user, void *ys, void *y_tmp, int ybytes, cudaStream_t s,
                              uint32_t **keys_sorted, int **vals_sorted) {
     uint32_t *ka = keys, *kb = keys_alt;
     int *va = vals, *vb = vals_alt;
@@ -738,7 +748,6 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     const int passes = (key_bits + 7) / 8;
     for (int pass = 0; pass < passes; ++pass) {
         const int shift = 8 * pass;
-        const bool last = pass == passes - 1;
         if (pass > 0) {
             cudaError_t e0 = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
             if (e0 != cudaSuccess) return e0;
@@ -749,11 +758,17 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
             k_seg_scan<<<cdiv((long long)st.ninst * 256, 8), 256, 0, s>>>(hist, ntiles, tot, st);
         else
             k_sort_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, tot);
-        const int yb = last ? ybytes : 0;
+        // 4-byte coordinates move with their keys in every pass, alternating between y_tmp
+        // and ys so that the last pass writes ys; 8-byte ones are gathered from y_user by
+        // the last pass
+        const bool carry = ybytes == 4;
+        const void *yin = !carry ? y_user : pass == 0 ? y_user : ((passes - pass) % 2 == 0 ? ys : y_tmp);
+        void *yout = !carry ? ys : (passes - 1 - pass) % 2 == 0 ? ys : y_tmp;
+        const int yb = carry || pass == passes - 1 ? ybytes : 0;
         if (pass == 0)
-            scatter_dispatch<true>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, y_user, ys);
+            scatter_dispatch<true>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
         else
-            scatter_dispatch<false>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, y_user, ys);
+            scatter_dispatch<false>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
         count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

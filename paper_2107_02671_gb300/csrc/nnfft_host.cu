@@ -77,6 +77,7 @@ struct Side {
     uint32_t *keys_sorted = nullptr;
     void *ys = nullptr;
     void *y_user = nullptr;        // coordinates in caller order (step-0 scratch)
+    void *y_tmp = nullptr;         // coordinates between radix passes
     int *cell_off = nullptr, *item_off = nullptr, *items_scratch = nullptr;
     int *item_cell = nullptr, *item_pb = nullptr, *item_pe = nullptr, *nitems = nullptr;
     // small-item split (sides where some instance has few points per cell)
@@ -574,6 +575,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
                            "sort histogram")) ||
             (rc = dalloc(p, &S.ys, M * rs, "sorted coordinates")) ||
             (rc = dalloc(p, &S.y_user, M * rs, "coordinates")) ||
+            (!p->dbl && (rc = dalloc(p, &S.y_tmp, M * rs, "coordinates (sort scratch)"))) ||
             (rc = dalloc_n(p, &S.cell_off, (size_t)S.ncell + 1, "cell offsets")) ||
             (rc = dalloc_n(p, &S.item_off, (size_t)S.ncell + 1, "item offsets")) ||
             (rc = dalloc_n(p, &S.items_scratch, build_items_scratch_len(S.ncell), "item scratch")) ||
@@ -840,7 +842,7 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     uint32_t *ks = nullptr;
     int *vs = nullptr;
     NN_CUDA(radix_sort_cells(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, tiles, S.tiles.ntiles,
-                             S.M, S.sort_bits, S.y_user, S.ys, ybytes, st, &ks, &vs),
+                             S.M, S.sort_bits, S.y_user, S.ys, S.y_tmp, ybytes, st, &ks, &vs),
             "radix sort");
     S.perm = vs;
     S.keys_sorted = ks;
