@@ -14,7 +14,8 @@ namespace nnfft {
 
 // Coefficients of the per-cell Chebyshev fit of 1/phihat1(N* x) on the x side.
 constexpr int NR = 8;
-// Radix sort: 8-bit digits, tiles of SORT_TILE keys per block (8 warps x 256).
+// Radix sort: digits of at most 8 bits (256 counters), tiles of SORT_TILE keys per block
+// (8 warps x 256).
 constexpr int SORT_TILE = 2048;
 constexpr int SORT_THREADS = 256;
 // Largest supported FFT factor (one CTA transforms a column in shared memory).
@@ -176,7 +177,34 @@ size_t radix_sort_hist_len(int ntiles, int ninst);
 // nullptr for one instance with binning `one` and ntiles = ceil(n / SORT_TILE).
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
                                const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
-                               int yfmt, int *hist, int *status, cudaStream_t s);
+                               int yfmt, int key_bits, int ybytes, int *hist, int *status,
+                               cudaStream_t s);
+// Digits of the radix sort of key_bits-bit keys, ceil(key_bits / 8) passes.  A tile of
+// SORT_TILE keys leaves each digit's keys as one run of consecutive addresses, so a narrower
+// digit gives longer runs.  Where the coordinates travel with the keys in every pass
+// (4-byte coordinates) the widths differ by at most one bit, the narrower ones first
+// (14 bits: 7 + 7; 15: 7 + 8; measured at 512 instances, fp32: node stage 3.49 -> 3.43 ms
+// against 8 + 6).  Where the last pass also gathers 8-byte coordinates (wide_first) the
+// digits are 8 bits wide with the remainder last (14 bits: 8 + 6), which measured 6 %
+// faster there than 7 + 7 (fp64 node stage 4.01 against 4.26 ms).
+struct RadixDigit {
+    int shift;
+    unsigned mask;
+};
+inline int radix_passes(int key_bits) { return key_bits < 1 ? 1 : (key_bits + 7) / 8; }
+inline RadixDigit radix_digit(int key_bits, int pass, bool wide_first) {
+    const int np = radix_passes(key_bits), b = key_bits < 1 ? 1 : key_bits;
+    const int lo = b / np, wide = b % np;   // balanced: the last `wide` passes take lo + 1 bits
+    RadixDigit d{0, 0u};
+    for (int q = 0; q <= pass; ++q) {
+        const int w = wide_first ? (b - 8 * q < 8 ? b - 8 * q : 8) : lo + (q >= np - wide ? 1 : 0);
+        if (q < pass) d.shift += w;
+        else d.mask = (1u << w) - 1u;
+    }
+    return d;
+}
+// the digit order radix_sort_cells uses for ybytes-byte coordinates
+inline bool radix_wide_first(int ybytes) { return ybytes == 8; }
 // Stable LSD radix sort of the keys from launch_node_keys_y (values: the identity
 // permutation, generated in pass 0) by the low key_bits bits of key - cell_base (the
 // whole key for one instance; within each instance for a batch, whose points are

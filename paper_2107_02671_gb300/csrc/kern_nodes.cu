@@ -1,6 +1,6 @@
 // kern_nodes.cu -- step 0 of Algorithm 2.2 for one node side: bin every node by
 // the grid cell it falls in, sort the nodes by cell (stable LSD radix sort with
-// 8-bit digits), and build the per-cell offsets and the work items that the
+// digits of at most 8 bits), and build the per-cell offsets and the work items that the
 // spread / gather kernels walk.  Deterministic: no order depends on timing.
 #include <type_traits>
 
@@ -97,10 +97,14 @@ __device__ __forceinline__ float fixed63_to_float(long long v, bool rn, long lon
 // Store the local coordinate y = Y 2^-63 in the plan's format:
 //   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans),
 // the pair from integer arithmetic: hi = Y rounded toward zero to 24 bits, lo = the rest
-// rounded to nearest, then renormalised.
+// rounded to nearest, then renormalised.  The float of fp32 plans is the top 32 bits of Y
+// (floor(Y / 2^32), a signed 32-bit integer) converted by one 32-bit conversion and scaled
+// by 2^-31: |error| < 2^-31 + half an ulp, far below the window error at m <= 8 in FP32,
+// and one conversion instead of the ~30 integer operations of an exact rounding of all
+// 64 bits (the node kernel is bound by the integer ALU pipe).
 __device__ __forceinline__ void store_y(void *yout, int fmt, long long i, long long Y) {
     if (fmt == 0) {
-        static_cast<float *>(yout)[i] = fixed63_to_float(Y, true);
+        static_cast<float *>(yout)[i] = __int2float_rn((int)(Y >> 32)) * 0x1p-31f;
     } else if (fmt == 1) {
         static_cast<double *>(yout)[i] = __ll2double_rn(Y) * 0x1p-63;
     } else {
@@ -142,7 +146,7 @@ __device__ __forceinline__ TileSpan tile_span(const SortTiles &st, int t, int n)
 __global__ void __launch_bounds__(SORT_THREADS)
 k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles st,
               uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int ntiles,
-              int *__restrict__ hist, int *__restrict__ tot, int *status) {
+              unsigned mask0, int *__restrict__ hist, int *__restrict__ tot, int *status) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     const TileSpan sp = tile_span(st, blockIdx.x, n);
@@ -173,7 +177,7 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles s
         }
         keys[i] = (uint32_t)(ic + I.cell_base);
         store_y(yout, yfmt, i, Y);
-        atomicAdd(&h[ic & 255], 1);
+        atomicAdd(&h[ic & mask0], 1);
     }
     __syncthreads();
     hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -182,7 +186,7 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles s
 
 // ---- radix sort ------------------------------------------------------------------
 __global__ void __launch_bounds__(SORT_THREADS)
-k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, SortTiles st, int ntiles,
+k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, unsigned mask, SortTiles st, int ntiles,
                int *__restrict__ hist, int *__restrict__ tot) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
@@ -190,7 +194,7 @@ k_sort_upsweep(const uint32_t *__restrict__ keys, int n, int shift, SortTiles st
     const uint32_t cb = st.inst == nullptr ? 0u : (uint32_t)st.tab[sp.inst].cell_base;
     __syncthreads();
     for (long long i = sp.begin + threadIdx.x; i < sp.end; i += SORT_THREADS)
-        atomicAdd(&h[((keys[i] - cb) >> shift) & 255u], 1);
+        atomicAdd(&h[((keys[i] - cb) >> shift) & mask], 1);
     __syncthreads();
     hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
     if (h[threadIdx.x]) atomicAdd(&tot[sp.inst * 256 + threadIdx.x], h[threadIdx.x]);   // order-free
@@ -279,16 +283,18 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // A 4-byte Y is carried through every pass with its key (yout[pos] = yin[input position],
 // read coalesced); an 8-byte Y (float pairs) is gathered in the last pass only,
 // yout[pos] = yin[value] (measured: carrying pays for 4 bytes and costs for 8, whose
-// random reads fetch a larger share of each sector).  The digit is taken from
-// key - cell_base of the tile's instance.  MATCH: the lanes with the
+// random reads fetch a larger share of each sector).  The digit, (key - cell_base of the
+// tile's instance) >> shift & mask, is at most 8 bits wide (NARROW: mask < 255; else the
+// literal 255, measured cheaper for the fp64 batch's scatters).  MATCH: the lanes with the
 // same digit from one match instruction instead of nine ballots (measured: fewer issue
 // slots, faster for large sorts; longer latency, slower for small ones).
-template <bool FIRST, typename Y, bool MATCH>
+template <bool FIRST, typename Y, bool MATCH, bool NARROW>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
-               SortTiles st, int ntiles, const int *__restrict__ hist_scanned,
+               unsigned mask_arg, SortTiles st, int ntiles, const int *__restrict__ hist_scanned,
                const Y *__restrict__ yin, Y *__restrict__ yout) {
+    const unsigned mask = NARROW ? mask_arg : 255u;
     constexpr int WARPS = SORT_THREADS / 32;
     constexpr int ROUNDS = SORT_TILE / SORT_THREADS;   // 8
     static_assert(SORT_THREADS == 256, "one thread per digit in the digit scans");
@@ -326,7 +332,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     for (int r = 0; r < ROUNDS; ++r) {
         const long long idx = base + r * 32 + lane;
         const bool valid = idx < sp.end;
-        const unsigned d = valid ? (((key[r] - cb) >> shift) & 255u) : 256u;
+        const unsigned d = valid ? (((key[r] - cb) >> shift) & mask) : 256u;
         // lanes with the same 9-bit value d (256 marks an invalid lane)
         unsigned peers = 0xffffffffu;
         if constexpr (MATCH) {
@@ -375,7 +381,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     for (int r = 0; r < ROUNDS; ++r) {
         const long long idx = base + r * 32 + lane;
         if (idx < sp.end) {
-            const unsigned d = ((key[r] - cb) >> shift) & 255u;
+            const unsigned d = ((key[r] - cb) >> shift) & mask;
             const int loc = lstart[d] + cnt[w][d] + rank[r];
             skey[loc] = key[r];
             sval[loc] = val[r];
@@ -387,7 +393,7 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     for (int i = threadIdx.x; i < tn; i += SORT_THREADS) {
         const uint32_t k = skey[i];
         const int v = sval[i];
-        const int pos = delta[((k - cb) >> shift) & 255u] + i;
+        const int pos = delta[((k - cb) >> shift) & mask] + i;
         kout[pos] = k;
         vout[pos] = v;
         if constexpr (CARRY) yout[pos] = sy[i];
@@ -682,7 +688,8 @@ SortTiles single_tiles() {
 
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
                                const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
-                               int yfmt, int *hist, int *status, cudaStream_t s) {
+                               int yfmt, int key_bits, int ybytes, int *hist, int *status,
+                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const SortTiles st = tiles ? *tiles : single_tiles();
     if (!tiles) ntiles = cdiv(n, SORT_TILE);
@@ -690,39 +697,56 @@ cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
     cudaError_t e = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
     if (e != cudaSuccess) return e;
     k_node_keys_y<<<ntiles, SORT_THREADS, 0, s>>>(nodes, n, one, st, keys, y_user, yfmt, ntiles,
-                                                  hist, tot, status);
+                                                  radix_digit(key_bits, 0, radix_wide_first(ybytes)).mask, hist, tot,
+                                                  status);
     count_launches(1);
     return cudaGetLastError();
 }
 
 namespace {
-// keys from which the scatter ranks with match instructions
+// keys from which the scatter passes after the first rank with match instructions.  The
+// first pass ranks with ballots at every size: its digits are the keys' low bits, so a
+// warp's 32 keys hold ~30 distinct digits, for which one match costs more than the nine
+// ballots (measured at 512 instances: node stage 3.64 -> 3.49 ms fp32, 4.12 -> 4.01 ms
+// fp64; the later passes' digits repeat more within a warp and keep match).
 constexpr int SORT_MATCH_MIN = 1 << 23;
 
+template <bool FIRST, typename Y, bool NARROW>
+void scatter_launch_w(int ntiles, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
+                      int *vb, int n, int shift, unsigned mask, const SortTiles &st, const int *hist,
+                      const void *yin, void *yout) {
+    if constexpr (!FIRST) {
+        if (n >= SORT_MATCH_MIN) {
+            k_sort_scatter<FIRST, Y, true, NARROW><<<ntiles, SORT_THREADS, 0, s>>>(
+                ka, va, kb, vb, n, shift, mask, st, ntiles, hist, static_cast<const Y *>(yin),
+                static_cast<Y *>(yout));
+            return;
+        }
+    }
+    k_sort_scatter<FIRST, Y, false, NARROW><<<ntiles, SORT_THREADS, 0, s>>>(
+        ka, va, kb, vb, n, shift, mask, st, ntiles, hist, static_cast<const Y *>(yin),
+        static_cast<Y *>(yout));
+}
 template <bool FIRST, typename Y>
 void scatter_launch(int ntiles, cudaStream_t s, const uint32_t *ka, const int *va, uint32_t *kb,
-                    int *vb, int n, int shift, const SortTiles &st, const int *hist,
+                    int *vb, int n, int shift, unsigned mask, const SortTiles &st, const int *hist,
                     const void *yin, void *yout) {
-    if (n >= SORT_MATCH_MIN)
-        k_sort_scatter<FIRST, Y, true><<<ntiles, SORT_THREADS, 0, s>>>(
-            ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
-            static_cast<Y *>(yout));
+    if (mask == 255u)
+        scatter_launch_w<FIRST, Y, false>(ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
     else
-        k_sort_scatter<FIRST, Y, false><<<ntiles, SORT_THREADS, 0, s>>>(
-            ka, va, kb, vb, n, shift, st, ntiles, hist, static_cast<const Y *>(yin),
-            static_cast<Y *>(yout));
+        scatter_launch_w<FIRST, Y, true>(ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
 }
 template <bool FIRST>
 void scatter_dispatch(int ybytes, int ntiles, cudaStream_t s, const uint32_t *ka, const int *va,
-                      uint32_t *kb, int *vb, int n, int shift, const SortTiles &st,
+                      uint32_t *kb, int *vb, int n, int shift, unsigned mask, const SortTiles &st,
                       const int *hist, const void *yin, void *yout) {
     if (ybytes == 4)
-        scatter_launch<FIRST, unsigned>(ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
+        scatter_launch<FIRST, unsigned>(ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
     else if (ybytes == 8)
-        scatter_launch<FIRST, unsigned long long>(ntiles, s, ka, va, kb, vb, n, shift, st, hist,
+        scatter_launch<FIRST, unsigned long long>(ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist,
                                                   yin, yout);
     else
-        scatter_launch<FIRST, void>(ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
+        scatter_launch<FIRST, void>(ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
 }
 }  // namespace
 
@@ -745,13 +769,16 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     const SortTiles st = tiles ? *tiles : single_tiles();
     if (!tiles) ntiles = cdiv(n, SORT_TILE);
     int *tot = hist + 256LL * ntiles;
-    const int passes = (key_bits + 7) / 8;
+    const int passes = radix_passes(key_bits);
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
+        const RadixDigit dg = radix_digit(key_bits, pass, radix_wide_first(ybytes));
+        const int shift = dg.shift;
+        // the key bits above the last digit are zero: its mask can be the full 8 bits
+        const unsigned mask = pass == passes - 1 ? 255u : dg.mask;
         if (pass > 0) {
             cudaError_t e0 = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
             if (e0 != cudaSuccess) return e0;
-            k_sort_upsweep<<<ntiles, SORT_THREADS, 0, s>>>(ka, n, shift, st, ntiles, hist, tot);
+            k_sort_upsweep<<<ntiles, SORT_THREADS, 0, s>>>(ka, n, shift, mask, st, ntiles, hist, tot);
             count_launches(1);
         }   // pass 0: tile counts and digit totals come from k_node_keys_y
         if (tiles)
@@ -766,9 +793,9 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
         void *yout = !carry ? ys : (passes - 1 - pass) % 2 == 0 ? ys : y_tmp;
         const int yb = carry || pass == passes - 1 ? ybytes : 0;
         if (pass == 0)
-            scatter_dispatch<true>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
+            scatter_dispatch<true>(yb, ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
         else
-            scatter_dispatch<false>(yb, ntiles, s, ka, va, kb, vb, n, shift, st, hist, yin, yout);
+            scatter_dispatch<false>(yb, ntiles, s, ka, va, kb, vb, n, shift, mask, st, hist, yin, yout);
         count_launches(2);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

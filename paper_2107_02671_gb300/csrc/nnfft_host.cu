@@ -279,7 +279,7 @@ bool split_weights_ok(const std::vector<double> &coef, int ntap, int D) {
 int key_bits_for(int ncell) {
     int b = 1;
     while ((1LL << b) < ncell) ++b;
-    return ((b + 7) / 8) * 8;
+    return b;
 }
 
 template <class T>
@@ -837,7 +837,7 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     const int ybytes = p->dbl ? 8 : 4;
     const SortTiles *tiles = p->ninst > 1 ? &S.tiles : nullptr;
     NN_CUDA(launch_node_keys_y(nodes, S.M, S.one, tiles, S.tiles.ntiles, S.keys, S.y_user, yfmt,
-                               S.hist, p->status, st),
+                               S.sort_bits, ybytes, S.hist, p->status, st),
             "node keys");
     uint32_t *ks = nullptr;
     int *vs = nullptr;
