@@ -287,9 +287,15 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // tile's instance) >> shift & mask, is at most 8 bits wide (NARROW: mask < 255; else the
 // literal 255, measured cheaper for the fp64 batch's scatters).  MATCH: the lanes with the
 // same digit from one match instruction instead of nine ballots (measured: fewer issue
-// slots, faster for large sorts; longer latency, slower for small ones).
+// slots, faster for large sorts; longer latency, slower for small ones).  The ballot-ranked
+// passes that move 8-byte coordinates (the sorts below 8M keys) are bounded to four blocks
+// per SM (64 registers, no spills; 73 unbounded, three blocks per SM, so that a 2^20-key
+// sort's 512 tiles took two waves on 152 SMs: node stage 95 -> 93.6 us per side); the others
+// keep the compiler's choice (minimum 0: unspecified; the bound measured 2 % slower on the
+// match-ranked pass of the fp64 batch).
 template <bool FIRST, typename Y, bool MATCH, bool NARROW>
-__global__ void __launch_bounds__(SORT_THREADS)
+__global__ void __launch_bounds__(SORT_THREADS,
+                                  std::is_same<Y, unsigned long long>::value && !MATCH ? 4 : 0)
 k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
                uint32_t *__restrict__ kout, int *__restrict__ vout, int n, int shift,
                unsigned mask_arg, SortTiles st, int ntiles, const int *__restrict__ hist_scanned,

@@ -810,3 +810,26 @@ def test_large_sort_sampled_rows(dtype, m, tol):
     want = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows)
     assert np.max(np.abs(z[rows] - want)) / np.sum(np.abs(g)) <= tol
     plan.close()
+
+
+@pytest.mark.parametrize("dtype,m,tol", [(torch.complex128, 8, 1e-12), (torch.complex64, 4, 2e-5)])
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_three_pass_sort(dtype, m, tol, nodes):
+    """A bandwidth whose cells need 17-bit keys (N = 40000: ~80K cells on the v side,
+    three radix passes: 8 + 8 + 1 bits where the last pass gathers 8-byte coordinates,
+    5 + 6 + 6 where 4-byte ones travel with the keys), forward and adjoint in full against
+    the direct sums."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    N, M1, M2 = 40000, 6000, 5000
+    v, x, f = W.nnfft_inputs(M1, M2, 106, nodes=nodes, dtype=npd)
+    g = W.adjoint_inputs(M2, 106, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    assert plan.info()["K1"] > 1 << 16
+    plan.set_nodes(dev(v), dev(x))
+    y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+    plan.sync()
+    y, z = y.cpu().numpy().astype(np.complex128), z.cpu().numpy().astype(np.complex128)
+    f64, g64 = f.astype(np.complex128), g.astype(np.complex128)
+    assert oracle.relative_error(y, oracle.nnfft_direct(N, v, f64, x), f64) <= tol
+    assert oracle.relative_error(z, oracle.nnfft_adjoint_direct(N, v, x, g64), g64) <= tol
+    plan.close()
