@@ -310,6 +310,17 @@ int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_d
 int nnfft_graph_launch(nnfft_graph_t g);
 int64_t nnfft_graph_kernels(nnfft_graph_t g);
 int nnfft_graph_destroy(nnfft_graph_t g);
+/*
+ * nnfft_transform_host_graph: the same for nnfft_transform_host (below) over fixed
+ * page-locked host buffers (cudaHostAlloc / cudaHostRegister / pinned tensors): one replay
+ * uploads the buffers' current contents, runs the transform and writes y and z back to the
+ * host buffers.  nnfft_graph_launch only queues the work: nnfft_sync(p) waits for it and
+ * returns the node status (ERANGE) that nnfft_transform_host returns directly.  EINVAL if
+ * a given host buffer is not page-locked (a pageable copy cannot be captured).
+ */
+int nnfft_transform_host_graph(nnfft_plan_t p, const double *v_host, const double *x_host,
+                               const void *f_host, void *y_host, const void *g_host,
+                               void *z_host, nnfft_graph_t *out);
 
 /*
  * nnfft_transform_host: new nodes and both directions from host memory in one call:

@@ -1575,18 +1575,13 @@ struct nnfft_graph_s {
     int64_t kernels = 0;       // library kernels one replay runs
 };
 
-int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_dev,
-                          const void *f_dev, void *y_dev, const void *g_dev, void *z_dev,
-                          nnfft_graph_t *out) {
-    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
-    *out = nullptr;
-    const int64_t M1 = p->info.M1, M2 = p->info.M2;
-    if ((M1 > 0 && !v_dev) || (M2 > 0 && !x_dev)) return fail(NNFFT_EINVAL, "null node pointer");
-    const bool adj = g_dev && z_dev;
-    int rc = ensure_dag(p, adj);        // every buffer and stream exists before the capture
-    if (rc) return rc;
-    // the capture runs on a stream of its own (the plan stream may be the legacy default
-    // stream, which cannot be captured); replays go to the plan stream
+}  // extern "C"
+
+// Capture the work enqueue(p) puts on the plan's streams into a CUDA graph.  The capture
+// runs on a stream of its own (the plan stream may be the legacy default stream, which
+// cannot be captured); replays go to the plan stream.
+template <class F>
+static int capture_graph(nnfft_plan_s *p, F &&enqueue, nnfft_graph_t *out) {
     cudaStream_t cs = nullptr;
     NN_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
     cudaStream_t saved = p->stream;
@@ -1595,9 +1590,10 @@ int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_d
     p->timing = false;
     const long long l0 = launches_so_far();
     cudaGraph_t graph = nullptr;
+    int rc = NNFFT_OK;
     cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
-        rc = nnfft_transform(p, v_dev, x_dev, f_dev, y_dev, g_dev, z_dev);
+        rc = enqueue();
         const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
         if (!rc && ee != cudaSuccess) rc = cuda_fail(ee, "end capture");
     } else {
@@ -1630,6 +1626,63 @@ int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_d
     return NNFFT_OK;
 }
 
+static int transform_host_enqueue(nnfft_plan_s *p, const double *v_host, const double *x_host,
+                                  const void *f_host, void *y_host, const void *g_host,
+                                  void *z_host);
+
+// staging buffers, streams and events of the host-buffer transform (allocated once)
+static int transform_host_prepare(nnfft_plan_s *p, bool adj) {
+    int rc = ensure_staging(p);
+    if (rc) return rc;
+    const size_t cs = 2 * real_size(p->dbl);
+    if (adj && !p->st_g && (rc = dalloc(p, &p->st_g, (size_t)p->side[1].M_cap * cs, "staging"))) return rc;
+    if (adj && !p->st_z && (rc = dalloc(p, &p->st_z, (size_t)p->side[0].M_cap * cs, "staging"))) return rc;
+    return ensure_dag(p, adj);
+}
+
+extern "C" {
+
+int nnfft_transform_graph(nnfft_plan_t p, const double *v_dev, const double *x_dev,
+                          const void *f_dev, void *y_dev, const void *g_dev, void *z_dev,
+                          nnfft_graph_t *out) {
+    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
+    *out = nullptr;
+    const int64_t M1 = p->info.M1, M2 = p->info.M2;
+    if ((M1 > 0 && !v_dev) || (M2 > 0 && !x_dev)) return fail(NNFFT_EINVAL, "null node pointer");
+    const bool adj = g_dev && z_dev;
+    int rc = ensure_dag(p, adj);        // every buffer and stream exists before the capture
+    if (rc) return rc;
+    return capture_graph(
+        p, [&]() { return nnfft_transform(p, v_dev, x_dev, f_dev, y_dev, g_dev, z_dev); }, out);
+}
+
+int nnfft_transform_host_graph(nnfft_plan_t p, const double *v_host, const double *x_host,
+                               const void *f_host, void *y_host, const void *g_host,
+                               void *z_host, nnfft_graph_t *out) {
+    if (!p || !out) return fail(NNFFT_EINVAL, "null argument");
+    *out = nullptr;
+    const int64_t M1 = p->info.M1, M2 = p->info.M2;
+    if ((M1 > 0 && !v_host) || (M2 > 0 && !x_host))
+        return fail(NNFFT_EINVAL, "null node pointer");
+    // copies into a graph must come from page-locked memory (a pageable copy cannot be
+    // captured): check every host buffer first
+    const void *bufs[6] = {v_host, x_host, f_host, y_host, g_host, z_host};
+    for (const void *b : bufs) {
+        if (!b) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, b) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return fail(NNFFT_EINVAL, "host buffers of a graph must be page-locked");
+        }
+    }
+    int rc = transform_host_prepare(p, g_host && z_host);   // allocations before the capture
+    if (rc) return rc;
+    return capture_graph(
+        p,
+        [&]() { return transform_host_enqueue(p, v_host, x_host, f_host, y_host, g_host, z_host); },
+        out);
+}
+
 int nnfft_graph_launch(nnfft_graph_t gr) {
     if (!gr) return fail(NNFFT_EINVAL, "null graph");
     NN_CUDA(cudaGraphLaunch(gr->exec, gr->plan->stream), "graph launch");
@@ -1650,16 +1703,24 @@ int nnfft_graph_destroy(nnfft_graph_t gr) {
 int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_host,
                          const void *f_host, void *y_host, const void *g_host, void *z_host) {
     if (!p) return fail(NNFFT_EINVAL, "null plan");
+    const int rc = transform_host_enqueue(p, v_host, x_host, f_host, y_host, g_host, z_host);
+    if (rc) return rc;
+    return collect_status(p);
+}
+
+}  // extern "C"
+
+// the work of nnfft_transform_host, queued (uploads, transform, downloads) without waiting
+static int transform_host_enqueue(nnfft_plan_s *p, const double *v_host, const double *x_host,
+                                  const void *f_host, void *y_host, const void *g_host,
+                                  void *z_host) {
     const int64_t M1 = p->info.M1, M2 = p->info.M2;
     if ((M1 > 0 && !v_host) || (M2 > 0 && !x_host))
         return fail(NNFFT_EINVAL, "null node pointer");
     const bool fwd = f_host && y_host, adj = g_host && z_host;
-    int rc = ensure_staging(p);
+    int rc = transform_host_prepare(p, adj);
     if (rc) return rc;
     const size_t cs = 2 * real_size(p->dbl);
-    if (adj && !p->st_g && (rc = dalloc(p, &p->st_g, (size_t)p->side[1].M_cap * cs, "staging"))) return rc;
-    if (adj && !p->st_z && (rc = dalloc(p, &p->st_z, (size_t)p->side[0].M_cap * cs, "staging"))) return rc;
-    if ((rc = ensure_dag(p, adj))) return rc;
     cudaStream_t A = p->stream, Bs = p->aux, C = p->copy;
     // All uploads in one queue on the copy stream, in the order they are needed: v, x, f,
     // g.  Host-to-device copies share one link (~205 GB/s measured on GB300; two concurrent
@@ -1684,8 +1745,10 @@ int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_h
     if (fwd && M2) NN_CUDA(cudaMemcpyAsync(y_host, p->st_y, cs * (size_t)M2, cudaMemcpyDeviceToHost, A), "copy y");
     NN_CUDA(cudaEventRecord(p->ev_join, Bs), "join");
     NN_CUDA(cudaStreamWaitEvent(A, p->ev_join, 0), "join");
-    return collect_status(p);
+    return NNFFT_OK;
 }
+
+extern "C" {
 
 int nnfft_set_nodes_host(nnfft_plan_t p, const double *v_host, const double *x_host) {
     if (!p) return fail(NNFFT_EINVAL, "null plan");

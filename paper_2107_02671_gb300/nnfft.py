@@ -131,6 +131,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_transform_host.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_transform.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.nnfft_transform_graph.argtypes = [vp, vp, vp, vp, vp, vp, vp, P(vp)]
+        lib.nnfft_transform_host_graph.argtypes = [vp, vp, vp, vp, vp, vp, vp, P(vp)]
         lib.nnfft_graph_launch.argtypes = [vp]
         lib.nnfft_graph_kernels.argtypes = [vp]
         lib.nnfft_graph_kernels.restype = i64
@@ -389,6 +390,30 @@ class Plan:
         _check(self._lib.nnfft_transform_graph(self._h, pv, px, pf, py, pg, pz, ctypes.byref(h)))
         return TransformGraph(self, h, (v, x, f, g, y, z))
 
+    def transform_host_graph(self, v, x, f=None, g=None, y=None, z=None):
+        """Capture one transform_host over these page-locked host arrays as a CUDA graph
+        (nothing runs yet): launch() uploads their current contents, transforms and writes
+        y and z back; sync() waits for it."""
+        for arr, n, name in ((v, self.M1, "v"), (x, self.M2, "x")):
+            if not (isinstance(arr, np.ndarray) and arr.dtype == np.float64 and arr.size == n
+                    and arr.flags.c_contiguous):
+                raise TypeError(f"{name} must be a contiguous float64 numpy array of {n}")
+        import torch
+        if f is not None and y is None:       # page-locked result arrays
+            y = torch.empty(self.M2, dtype=self.cdtype).pin_memory().numpy()
+        if g is not None and z is None:
+            z = torch.empty(self.M1, dtype=self.cdtype).pin_memory().numpy()
+        pf = self._host_arr(f, self.M1, "f") if f is not None else None
+        py = self._host_arr(y, self.M2, "y") if f is not None else None
+        pg = self._host_arr(g, self.M2, "g") if g is not None else None
+        pz = self._host_arr(z, self.M1, "z") if g is not None else None
+        h = ctypes.c_void_p()
+        _check(self._lib.nnfft_transform_host_graph(
+            self._h, ctypes.c_void_p(v.ctypes.data), ctypes.c_void_p(x.ctypes.data), pf, py, pg,
+            pz, ctypes.byref(h)))
+        return TransformGraph(self, h, (v, x, f, g, y if f is not None else None,
+                                        z if g is not None else None))
+
     def transform_host(self, v, x, f=None, g=None, y=None, z=None):
         """New nodes and both directions from host arrays in one call (overlapped copies):
         returns (A f, A^H g); a direction is skipped when its input is None."""
@@ -448,8 +473,9 @@ class Plan:
 
 
 class TransformGraph:
-    """A captured nnfft_transform (see Plan.transform_graph).  launch() replays it on the
-    plan stream; y and z hold the results."""
+    """A captured nnfft_transform or nnfft_transform_host (see Plan.transform_graph and
+    Plan.transform_host_graph).  launch() replays it on the plan stream; y and z hold the
+    results."""
 
     def __init__(self, plan, handle, tensors):
         self._plan, self._h = plan, handle

@@ -504,6 +504,46 @@ def test_transform_host_equals_separate_host_calls(dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_transform_host_graph_replays_the_host_transform(dtype):
+    """nnfft_transform_host_graph over page-locked host arrays: each launch uploads the
+    arrays' current contents and returns bit for bit what nnfft_transform_host returns on
+    them (new nodes and values written in place between launches); one direction alone; a
+    pageable array is rejected with EINVAL; a node out of range reports ERANGE at sync."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    m = 8 if dtype == torch.complex128 else 4
+    N, M1, M2 = 700, 30000, 20000
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+    v, x, f = (pin(a) for a in W.nnfft_inputs(M1, M2, 61, dtype=npd))
+    g = pin(W.adjoint_inputs(M2, 61, dtype=npd))
+    y, z = pin(np.zeros(M2, npd)), pin(np.zeros(M1, npd))
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    graph = plan.transform_host_graph(v, x, f, g, y, z)
+    assert graph.kernels > 0
+    for seed in (61, 62):
+        v2, x2, f2 = W.nnfft_inputs(M1, M2, seed, dtype=npd)
+        v[:], x[:], f[:], g[:] = v2, x2, f2, W.adjoint_inputs(M2, seed, dtype=npd)
+        graph.launch()
+        plan.sync()
+        want_y, want_z = plan.transform_host(v.copy(), x.copy(), f.copy(), g.copy())
+        assert np.array_equal(y, want_y) and np.array_equal(z, want_z)
+    one = plan.transform_host_graph(v, x, f=f)
+    y1 = one.launch()[0]
+    plan.sync()
+    assert np.array_equal(y1, plan.transform_host(v.copy(), x.copy(), f=f.copy())[0])
+    with pytest.raises(B.NNFFTError) as e:
+        plan.transform_host_graph(v.copy(), x, f, g, y, z)       # pageable v
+    assert e.value.code == 1
+    v[5] = 0.75
+    graph.launch()
+    with pytest.raises(B.NNFFTError) as e:
+        plan.sync()
+    assert e.value.code == 2
+    one.close()
+    graph.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_transform_device_equals_separate_calls(dtype):
     """nnfft_transform (sorts and both directions overlapped, device buffers) returns bit
     for bit set_nodes + exec + adjoint, for a single plan and a batch; directions can be
@@ -824,7 +864,7 @@ def test_three_pass_sort(dtype, m, tol, nodes):
     v, x, f = W.nnfft_inputs(M1, M2, 106, nodes=nodes, dtype=npd)
     g = W.adjoint_inputs(M2, 106, dtype=npd)
     plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
-    assert plan.info()["K1"] > 1 << 16
+    assert plan.info["K1"] > 1 << 16
     plan.set_nodes(dev(v), dev(x))
     y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
     plan.sync()
