@@ -434,12 +434,12 @@ int nnfft_timing_enable(nnfft_plan_t p, int enable);
 int nnfft_timing_read(nnfft_plan_t p, nnfft_timing *out, int reset);
 
 /*
- * nnfft_selftest_fixed63: check of the node kernel's integer-built conversion of a signed
- * 64-bit fixed-point coordinate Y (value Y 2^-63) to float.  For each of the n device
- * inputs, out_dev[4i .. 4i+3] = (truncated, rounded to nearest even) from the integer
- * construction, then CUDA's own truncating and rounding conversions of the same Y; the
- * two pairs must agree bitwise.  Synchronous on the legacy default stream.  EINVAL for
- * n < 0, n > 2^28 or null pointers with n > 0.
+ * nnfft_selftest_fixed63: check of the node kernel's conversion of a signed 64-bit
+ * fixed-point coordinate Y (value y = Y 2^-63) to floats.  For each of the n device inputs,
+ * out_dev[4i .. 4i+3] = (the fp32 plans' float, the split plans' float pair h and l, CUDA's
+ * own rounding conversion of Y); the caller checks |float - y| < 2^-31 + half an ulp and
+ * |h + l - y| <= 2^-49 + 2^-56 with |l| <= ulp(h) / 2.  Synchronous on the legacy default
+ * stream.  EINVAL for n < 0, n > 2^28 or null pointers with n > 0.
  */
 int nnfft_selftest_fixed63(const int64_t *in_dev, float *out_dev, int64_t n);
 

@@ -54,66 +54,39 @@ __device__ __forceinline__ bool node_fixed(double t, unsigned long long S, long 
     return ok;
 }
 
-// v 2^-63 as a float, truncated toward zero (rn = false) or rounded to nearest, ties to
-// even (rn = true), built from the bits of v with integer operations: conversions from
-// 64-bit integers run on the FP64 pipe, of which GB300 has 1/64 of the FP32 rate.  Any v
-// (v = -2^63 gives -1).  The truncated part of v is returned in *kept (rn = false).
-__device__ __forceinline__ float fixed63_to_float(long long v, bool rn, long long *kept = nullptr) {
-    if (v == 0) {
-        if (kept) *kept = 0;
-        return 0.f;
-    }
-    const bool neg = v < 0;
-    const unsigned long long a = neg ? 0ULL - (unsigned long long)v : (unsigned long long)v;
-    int p = 63 - __clzll((long long)a);                 // most significant bit, 0..63
-    unsigned long long m;
-    if (p > 23) {
-        const int sh = p - 23;
-        m = a >> sh;                                     // 24 bits with the leading one
-        if (kept) {
-            const unsigned long long t = m << sh;
-            *kept = neg ? (long long)(0ULL - t) : (long long)t;
-        }
-        if (rn) {
-            const unsigned long long rem = a & ((1ULL << sh) - 1);
-            const unsigned long long half = 1ULL << (sh - 1);
-            if (rem > half || (rem == half && (m & 1ULL))) {
-                ++m;
-                if (m >> 24) {
-                    m >>= 1;
-                    ++p;
-                }
-            }
-        }
-    } else {
-        m = a << (23 - p);
-        if (kept) *kept = v;
-    }
-    // m 2^(p - 23) 2^-63 = 1.f x 2^(p - 63): biased exponent p + 64
-    return __uint_as_float((neg ? 0x80000000u : 0u) | ((unsigned)(p + 64) << 23) |
-                           ((unsigned)m & 0x7fffffu));
+// The local coordinate y = Y 2^-63 (Y a signed 64-bit fixed-point value) as floats built
+// from 32-bit conversions.  The node kernel is bound by the integer ALU pipe, and a 64-bit
+// integer -> float conversion runs on the FP64 pipe (1/64 of the FP32 rate on GB300), so
+// both formats start from the top word T = floor(Y / 2^32) (a signed 32-bit integer) and
+// the low word L = Y - T 2^32 in [0, 2^32):
+//   * fp32 plans: y ~ RN(T) 2^-31, |error| < 2^-31 + half an ulp;
+//   * split plans, a float pair h + l: h = RN(T) 2^-31; the exact integer remainder
+//     e = T - RN(T) (|e| <= 64) and L give l = RN(e 2^-31 + RN(L) 2^-63), so
+//     |h + l - y| <= 2^-49 + 2^-56; then renormalised with Fast2Sum (|h| >= |l| or h = 0).
+__device__ __forceinline__ float fixed63_to_float32(long long Y) {
+    return __int2float_rn((int)(Y >> 32)) * 0x1p-31f;
+}
+__device__ __forceinline__ float2 fixed63_to_pair(long long Y) {
+    const int top = (int)(Y >> 32);
+    const unsigned low = (unsigned)(Y & 0xffffffffLL);
+    const float hf = __int2float_rn(top);
+    int e = top - __float2int_rn(hf);
+    if (hf >= 0x1p31f) e -= 1;                    // the conversion saturates at 2^31 - 1
+    const float h = hf * 0x1p-31f;
+    const float l = fmaf(__int2float_rn(e), 0x1p-31f, __uint2float_rn(low) * 0x1p-63f);
+    const float sh = h + l;                       // Fast2Sum
+    return make_float2(sh, l - (sh - h));
 }
 
 // Store the local coordinate y = Y 2^-63 in the plan's format:
-//   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans),
-// the pair from integer arithmetic: hi = Y rounded toward zero to 24 bits, lo = the rest
-// rounded to nearest, then renormalised.  The float of fp32 plans is the top 32 bits of Y
-// (floor(Y / 2^32), a signed 32-bit integer) converted by one 32-bit conversion and scaled
-// by 2^-31: |error| < 2^-31 + half an ulp, far below the window error at m <= 8 in FP32,
-// and one conversion instead of the ~30 integer operations of an exact rounding of all
-// 64 bits (the node kernel is bound by the integer ALU pipe).
+//   0: float (fp32 plans), 1: double (fp64 plans), 2: float pair hi + lo (split plans).
 __device__ __forceinline__ void store_y(void *yout, int fmt, long long i, long long Y) {
     if (fmt == 0) {
-        static_cast<float *>(yout)[i] = __int2float_rn((int)(Y >> 32)) * 0x1p-31f;
+        static_cast<float *>(yout)[i] = fixed63_to_float32(Y);
     } else if (fmt == 1) {
         static_cast<double *>(yout)[i] = __ll2double_rn(Y) * 0x1p-63;
     } else {
-        long long kept = 0;
-        const float h = fixed63_to_float(Y, false, &kept);
-        const float l = fixed63_to_float(Y - kept, true);
-        const float sh = h + l;                            // Fast2Sum: |h| >= |l|
-        const float sl = l - (sh - h);
-        static_cast<float2 *>(yout)[i] = make_float2(sh, sl);
+        static_cast<float2 *>(yout)[i] = fixed63_to_pair(Y);
     }
 }
 
@@ -845,15 +818,16 @@ cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell
 size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 2; }
 
 namespace {
-// four floats per input: the integer-built truncated and rounded values, then CUDA's
-// own conversions of the same integer (the self-test compares them)
+// four floats per input: the node kernel's fp32 coordinate, its float pair (h, l), and
+// CUDA's own rounding conversion of the same integer (the self-test checks the error bounds)
 __global__ void k_selftest_fixed63(const long long *__restrict__ in, float *__restrict__ out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const long long v = in[i];
-    out[4 * i + 0] = fixed63_to_float(v, false);
-    out[4 * i + 1] = fixed63_to_float(v, true);
-    out[4 * i + 2] = __ll2float_rz(v) * 0x1p-63f;
+    const float2 pr = fixed63_to_pair(v);
+    out[4 * i + 0] = fixed63_to_float32(v);
+    out[4 * i + 1] = pr.x;
+    out[4 * i + 2] = pr.y;
     out[4 * i + 3] = __ll2float_rn(v) * 0x1p-63f;
 }
 }  // namespace

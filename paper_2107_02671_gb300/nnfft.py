@@ -673,8 +673,8 @@ def sinc(N, a, c, b, m=8, out=None, stream=None, rule="gl", n=0):
 
 def selftest_fixed63(y):
     """Node-kernel conversion check: for an int64 device tensor of fixed-point coordinates
-    (value y 2^-63) returns an (n, 4) float32 tensor: integer-built truncated and rounded
-    floats, then CUDA's truncating and rounding conversions."""
+    (value y 2^-63) returns an (n, 4) float32 tensor: the fp32 plans' float, the split
+    plans' float pair (h, l), then CUDA's rounding conversion."""
     import torch
     if y.dtype != torch.int64 or not y.is_cuda or not y.is_contiguous():
         raise TypeError("y must be a contiguous int64 CUDA tensor")

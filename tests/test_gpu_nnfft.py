@@ -726,35 +726,39 @@ def test_transform_graph_batch_plan():
     P.close()
 
 
-def test_fixed_point_coordinate_conversion_matches_cuda():
-    """The node kernel builds the float (and float pair) coordinates from the fixed-point
-    value with integer operations; they equal CUDA's truncating and rounding conversions
-    bit for bit, for edge values (0, +-1, -2^63, powers of two +- 1, rounding ties) and
-    random values of every magnitude."""
+def test_fixed_point_coordinate_conversion_error_bounds():
+    """The node kernel builds the fp32 coordinate and the split plans' float pair from the
+    fixed-point value Y (y = Y 2^-63) with 32-bit conversions: the float is within
+    2^-31 + half an ulp of y, the pair within 2^-49 + 2^-56 and normalised (|l| <= ulp(h)/2),
+    for edge values (0, +-1, -2^63, powers of two +- 1, rounding ties at 24 and 32 bits) and
+    random values of every magnitude, checked in exact rational arithmetic."""
+    from fractions import Fraction
     rng = np.random.default_rng(123)
     edge = [0, 1, -1, 2**63 - 1, -2**63, -2**63 + 1, 2**62, -2**62]
     for k in range(0, 63):
         for d in (-1, 0, 1):
             edge += [2**k + d, -(2**k + d)]
-    for k in range(25, 63):                      # exact ties and neighbours at 24 bits
+    for k in range(25, 63):                      # ties and neighbours at 24 bits
         base = (2**23 + 1) << (k - 23)
         half = 1 << (k - 24)
         edge += [base + half, base + half - 1, base + half + 1, -(base + half), base - half]
+    for t in (2**31 - 1, 2**31 - 64, 2**31 - 65, -2**31, -2**31 + 64, 2**24 + 1, -(2**24 + 1)):
+        for low in (0, 1, 2**31, 2**32 - 1):     # top words that round up to 2^31 and others
+            edge.append(t * 2**32 + low)
     edge = [e for e in edge if -2**63 <= e < 2**63]
-    mags = rng.integers(0, 63, 200000)
-    rand = (rng.integers(0, 2**62, 200000, dtype=np.int64) >> (62 - mags).astype(np.int64))
-    rand *= np.where(rng.random(200000) < 0.5, -1, 1)
+    mags = rng.integers(0, 63, 20000)
+    rand = (rng.integers(0, 2**62, 20000, dtype=np.int64) >> (62 - mags).astype(np.int64))
+    rand *= np.where(rng.random(20000) < 0.5, -1, 1)
     y = np.concatenate([np.array(edge, dtype=np.int64), rand.astype(np.int64)])
     out = B.selftest_fixed63(torch.from_numpy(y).cuda()).cpu().numpy()
-    assert np.array_equal(out[:, 0].view(np.uint32), out[:, 2].view(np.uint32))
-    assert np.array_equal(out[:, 1].view(np.uint32), out[:, 3].view(np.uint32))
-    # and against the exact value: truncation never increases |v|, rounding is nearest
-    from fractions import Fraction
-    for v, t, r in zip(y[:len(edge)], out[:len(edge), 0], out[:len(edge), 1]):
+    b_single = Fraction(1, 2**31)
+    b_pair = Fraction(1, 2**49) + Fraction(1, 2**56)
+    for v, (f, h, lo, ref) in zip(y.tolist(), out.tolist()):
         exact = Fraction(int(v), 2**63)
-        ft, fr = Fraction(float(t)), Fraction(float(r))
-        assert abs(ft) <= abs(exact) and abs(exact) - abs(ft) < Fraction(float(np.spacing(np.abs(t))))
-        assert abs(fr - exact) <= Fraction(float(np.spacing(np.abs(r)))) / 2
+        assert abs(Fraction(f) - exact) < b_single + Fraction(float(np.spacing(np.float32(abs(f))))) / 2
+        assert abs(Fraction(h) + Fraction(lo) - exact) <= b_pair
+        assert h == 0 or abs(lo) <= float(np.spacing(np.float32(abs(h)))) / 2
+        assert abs(Fraction(ref) - exact) <= Fraction(float(np.spacing(np.float32(abs(ref))))) / 2
 
 
 @pytest.mark.parametrize("dtype,arith,m,tol", [(torch.complex64, None, 4, 2e-5),
