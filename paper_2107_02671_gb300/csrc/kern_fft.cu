@@ -44,9 +44,24 @@ __device__ __forceinline__ C2<Real> mul_isign(C2<Real> a, int sign) {
     return r;
 }
 
+// cos and sin of 2 pi / 3, 2 pi / 5 and 4 pi / 5 (the radix-3 and radix-5 butterflies)
+constexpr double SB_S3 = 0.866025403784438646763723170753;    // sin(2 pi / 3)
+constexpr double SB_C51 = 0.309016994374947424102293417183;   // cos(2 pi / 5)
+constexpr double SB_C52 = -0.809016994374947424102293417183;  // cos(4 pi / 5)
+constexpr double SB_S51 = 0.951056516295153572116439333379;   // sin(2 pi / 5)
+constexpr double SB_S52 = 0.587785252292473129168705954639;   // sin(4 pi / 5)
+template <typename Real>
+__device__ __forceinline__ C2<Real> cscl(C2<Real> a, Real c) {
+    C2<Real> r;
+    r.x = a.x * c;
+    r.y = a.y * c;
+    return r;
+}
+
 // One Stockham stage of radix R over `cols` length-n sequences held back to back in
 // shared memory: butterfly j (0 <= j < n/R) of each sequence, k = j mod L,
-//   a_q = src[j + q n/R] * w_{L R}^{q k},  b_p = sum_q a_q w_R^{p q},
+//   a_q = src[j + q n/R] * w_{L R}^{q k},  b_p = sum_q a_q w_R^{p q} (radices 3 and 5 through
+//   the symmetric forms above: cosine sums shared by b_p and b_(R-p), sine sums with opposite signs),
 //   dst[(j - k) R + k + p L] = b_p,
 // where L is the product of the radices of the earlier stages.
 template <typename Real, int R>
@@ -77,15 +92,29 @@ __device__ __forceinline__ void stage(const C2<Real> *src, C2<Real> *dst, int n,
             b[1] = cadd<Real>(d02, d13);
             b[2] = csub<Real>(s02, s13);
             b[3] = csub<Real>(d02, d13);
+        } else if (R == 3) {
+            // w = exp(sign 2 pi i / 3): b1, b2 = a0 - (a1 + a2) / 2 +- i sign sin(2 pi / 3) (a1 - a2)
+            const C2<Real> s12 = cadd<Real>(a[1], a[2]);
+            const C2<Real> t = csub<Real>(a[0], cscl<Real>(s12, Real(0.5)));
+            const C2<Real> u = mul_isign<Real>(cscl<Real>(csub<Real>(a[1], a[2]), Real(SB_S3)), sign);
+            b[0] = cadd<Real>(a[0], s12);
+            b[1] = cadd<Real>(t, u);
+            b[2] = csub<Real>(t, u);
         } else {
-#pragma unroll
-            for (int p = 0; p < R; ++p) {
-                C2<Real> acc = a[0];
-#pragma unroll
-                for (int q = 1; q < R; ++q)
-                    acc = cadd<Real>(acc, cmul<Real>(a[q], twid<Real>(tw, ((p * q) % R) * nr, sign)));
-                b[p] = acc;
-            }
+            // R == 5, w = exp(sign 2 pi i / 5): b_p and b_(5-p) share the cosine sums and
+            // differ in the sign of the sine sums
+            const C2<Real> s1 = cadd<Real>(a[1], a[4]), d1 = csub<Real>(a[1], a[4]);
+            const C2<Real> s2 = cadd<Real>(a[2], a[3]), d2 = csub<Real>(a[2], a[3]);
+            const Real c1 = Real(SB_C51), c2 = Real(SB_C52), n1 = Real(SB_S51), n2 = Real(SB_S52);
+            const C2<Real> t1 = cadd<Real>(a[0], cadd<Real>(cscl<Real>(s1, c1), cscl<Real>(s2, c2)));
+            const C2<Real> t2 = cadd<Real>(a[0], cadd<Real>(cscl<Real>(s1, c2), cscl<Real>(s2, c1)));
+            const C2<Real> u1 = mul_isign<Real>(cadd<Real>(cscl<Real>(d1, n1), cscl<Real>(d2, n2)), sign);
+            const C2<Real> u2 = mul_isign<Real>(csub<Real>(cscl<Real>(d1, n2), cscl<Real>(d2, n1)), sign);
+            b[0] = cadd<Real>(a[0], cadd<Real>(s1, s2));
+            b[1] = cadd<Real>(t1, u1);
+            b[4] = csub<Real>(t1, u1);
+            b[2] = cadd<Real>(t2, u2);
+            b[3] = csub<Real>(t2, u2);
         }
 #pragma unroll
         for (int p = 0; p < R; ++p) d0[(j - k) * R + k + p * L] = b[p];

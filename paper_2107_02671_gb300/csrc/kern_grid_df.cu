@@ -311,6 +311,27 @@ __device__ __forceinline__ cdf twd(const float4 *tw, int idx, int sign) {
     return conj_if(ld(tw + idx), sign > 0);
 }
 
+// cos and sin of 2 pi / 3, 2 pi / 5 and 4 pi / 5 as float pairs (the radix-3 and radix-5
+// butterflies below)
+constexpr double BF_S3 = 0.866025403784438646763723170753;    // sin(2 pi / 3)
+constexpr double BF_C51 = 0.309016994374947424102293417183;   // cos(2 pi / 5)
+constexpr double BF_C52 = -0.809016994374947424102293417183;  // cos(4 pi / 5)
+constexpr double BF_S51 = 0.951056516295153572116439333379;   // sin(2 pi / 5)
+constexpr double BF_S52 = 0.587785252292473129168705954639;   // sin(4 pi / 5)
+// float pairs (hi, lo) of those constants, computed at compile time
+constexpr float bf_hi(double c) { return (float)c; }
+constexpr float bf_lo(double c) { return (float)(c - (double)(float)c); }
+constexpr float BF_S3_H = bf_hi(BF_S3), BF_S3_L = bf_lo(BF_S3);
+constexpr float BF_C51_H = bf_hi(BF_C51), BF_C51_L = bf_lo(BF_C51);
+constexpr float BF_C52_H = bf_hi(BF_C52), BF_C52_L = bf_lo(BF_C52);
+constexpr float BF_S51_H = bf_hi(BF_S51), BF_S51_L = bf_lo(BF_S51);
+constexpr float BF_S52_H = bf_hi(BF_S52), BF_S52_L = bf_lo(BF_S52);
+__device__ __forceinline__ cdf chalf(cdf a) {                  // a / 2, exact
+    a.re = mk(0.5f * a.re.h, 0.5f * a.re.l);
+    a.im = mk(0.5f * a.im.h, 0.5f * a.im.l);
+    return a;
+}
+
 template <int R>
 __device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, int cols, int L,
                                          const float4 *tw, int sign) {
@@ -339,15 +360,31 @@ __device__ __forceinline__ void stage_df(const float4 *src, float4 *dst, int n, 
             b[1] = cadd(d02, d13);
             b[2] = csub(s02, s13);
             b[3] = csub(d02, d13);
+        } else if (R == 3) {
+            // with w = exp(sign 2 pi i / 3) = -1/2 + i sign sin(2 pi / 3):
+            // b1, b2 = a0 - (a1 + a2) / 2 +- i sign sin(2 pi / 3) (a1 - a2)
+            const cdf s12 = cadd(a[1], a[2]);
+            const cdf t = csub(a[0], chalf(s12));
+            const cdf u = cmul_isign(cscale(csub(a[1], a[2]), mk(BF_S3_H, BF_S3_L)), sign);
+            b[0] = cadd(a[0], s12);
+            b[1] = cadd(t, u);
+            b[2] = csub(t, u);
         } else {
-#pragma unroll
-            for (int p = 0; p < R; ++p) {
-                cdf accv = a[0];
-#pragma unroll
-                for (int q = 1; q < R; ++q)
-                    accv = cadd(accv, cmul(a[q], twd(tw, ((p * q) % R) * nr, sign)));
-                b[p] = accv;
-            }
+            // R == 5, w = exp(sign 2 pi i / 5): b_p and b_(5-p) share the cosine sums and
+            // differ in the sign of the sine sums (a_q w^(pq) + a_(5-q) w^(-pq))
+            const cdf s1 = cadd(a[1], a[4]), d1 = csub(a[1], a[4]);
+            const cdf s2 = cadd(a[2], a[3]), d2 = csub(a[2], a[3]);
+            const df c1 = mk(BF_C51_H, BF_C51_L), c2 = mk(BF_C52_H, BF_C52_L);
+            const df n1 = mk(BF_S51_H, BF_S51_L), n2 = mk(BF_S52_H, BF_S52_L);
+            const cdf t1 = cadd(a[0], cadd(cscale(s1, c1), cscale(s2, c2)));
+            const cdf t2 = cadd(a[0], cadd(cscale(s1, c2), cscale(s2, c1)));
+            const cdf u1 = cmul_isign(cadd(cscale(d1, n1), cscale(d2, n2)), sign);
+            const cdf u2 = cmul_isign(csub(cscale(d1, n2), cscale(d2, n1)), sign);
+            b[0] = cadd(a[0], cadd(s1, s2));
+            b[1] = cadd(t1, u1);
+            b[4] = csub(t1, u1);
+            b[2] = cadd(t2, u2);
+            b[3] = csub(t2, u2);
         }
 #pragma unroll
         for (int p = 0; p < R; ++p) st(d0 + (j - k) * R + k + p * L, b[p]);
