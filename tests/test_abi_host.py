@@ -38,7 +38,7 @@ def test_library_loads_and_exports_every_declared_symbol():
 
 @pytest.mark.parametrize("N,s1,s2,m1,m2", [(64, 2, 2, 4, 4), (4096, 2, 2, 8, 8), (1024, 2, 2, 8, 8),
                                            (1000, 1.5, 1.25, 6, 3), (77, 1.3, 2.2, 2, 5),
-                                           (16384, 2, 2, 8, 8), (4096, 2, 2, 4, 4)])
+                                           (16384, 2, 2, 8, 8), (4096, 2, 2, 4, 4), (40000, 2, 2, 8, 8)])
 def test_plan_parameters_match_oracle(N, s1, s2, m1, m2):
     for dt in ("complex128", "complex64"):
         info = B.params(N, 1000, 999, s1, s2, m1, m2, dt)
