@@ -214,6 +214,29 @@ def oracle_sample(seconds_target=12.0, seed=0):
             "seconds": t_fwd + t_adj}
 
 
+def oracle_stage_reference(seed=0):
+    """The second CPU baseline: the oracle's Algorithm 2.2 stage reference (the fast method
+    itself, exact sinh windows, naive DFT for step 3) at the full workload, forward and
+    adjoint, on one host core.  Nothing is sampled or extrapolated."""
+    import oracle
+    from paper_2107_02671_gb300 import workloads as W
+    v, x, f = W.nnfft_inputs(M_PTS, M_PTS, seed)
+    g = W.adjoint_inputs(M_PTS, seed)
+    P = oracle.make_params(N_BW, 2.0, 2.0, 8, 8)
+    t0 = time.perf_counter()
+    oracle.nnfft_alg22(P, v, f, x, nthreads=1)
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.nnfft_alg22_adjoint(P, v, x, g, nthreads=1)
+    t_adj = time.perf_counter() - t0
+    return {"value": 4 * M_PTS / (t_fwd + t_adj), "unit": "pts/s", "cores": 1,
+            "kind": "oracle stage reference",
+            "sample": ("Algorithm 2.2 step by step (exact sinh windows, naive DFT of length "
+                       f"N2={P.N2} over K1={P.K1} grid values for step 3) and its transpose at "
+                       "N=4096, M1=M2=2^20, sigma=2, m=8, full size, one thread, no extrapolation"),
+            "seconds": t_fwd + t_adj, "forward_s": t_fwd, "adjoint_s": t_adj}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -237,14 +260,21 @@ def run_reference(args, rank, world):
         oracle.nnfft_adjoint_direct(N_BW, v, x, g, rows=rows)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
-            times.append(dt * M_PTS / len(rows))          # extrapolated full-step seconds
-    full = float(np.mean(times))
-    value = 4 * M_PTS / full
+            times.append(dt)
+    # A step is the bounded sample: J output rows of the forward and J of the adjoint, each
+    # summing all 2^20 terms, i.e. J/M2 of a full forward and of a full adjoint.  In the
+    # metric's unit that is 4 J point-equivalents per step (a full step is 4 M), so
+    # value = 4 J / step time, the full-step throughput.
+    step_s = float(np.mean(times))
+    value = 4 * J / step_s
     sample = (f"per step: direct fp64 forward and adjoint sums for {J} sampled output rows "
-              f"(all 2^20 terms each), extrapolated x{M_PTS / J:.0f} to the full step")
+              f"(all 2^20 terms each) = {J}/{M_PTS} of a full set_nodes + forward + adjoint "
+              f"step; value = 4*{J} point-equivalents / step time (a full step would take "
+              f"{step_s * M_PTS / J:.0f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "points_per_step": 4 * J,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_BW, "M1": M_PTS, "M2": M_PTS,
                                         "m": 8, "sigma": 2.0, "nodes": "uniform"},
@@ -262,7 +292,7 @@ def run_reference(args, rank, world):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of every
 # split-precision point-kernel variant at the headline size, from ncu captures of
 # `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
-# with T = 8,8,0,0,1,1 / 32,32,0,0,32,32 / 16,16,0,0,8,8 (profiles/k_*_nnfft_fp64_N4096_M2e20.md).
+# with T = 8,8,0,0,1,1 / 32,32,0,0,32,32 / 16,16,0,0,8,8 (the moments and evaluation captures).
 # The files the kernels are built from (their code, the double-float primitives, the side
 # descriptor) are hashed; a change since the capture reports null.
 NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "side.h"]
@@ -343,6 +373,14 @@ def run_batched(args, rank, dev, flush, timed, pk):
         k = max(3, min(20, args.steps // 10))
         ms_full, l_full, _ = timed(step, k, label="batched_step")
         P.sync()
+        # the same step captured once as a CUDA graph over these buffers, one launch per step
+        graph = P.transform_graph(vd, xd, fd, gd, y, z)
+        for _ in range(2):
+            graph.launch()
+        P.sync()
+        ms_graph, l_graph, _ = timed(graph.launch, k, label="batched_graph")
+        P.sync()
+        graph.close()
         ms_exec, _, _ = timed(fwd_adj, k, label="batched_exec")
         P.sync()
 
@@ -380,6 +418,11 @@ def run_batched(args, rank, dev, flush, timed, pk):
         out[name] = {"value": 2 * pts / (np.mean(ms_full) / 1e3), "unit": "pts/s",
                      "ms_per_step": float(np.mean(ms_full)),
                      "step": "set_nodes + exec + adjoint over all instances",
+                     "graph_value": 2 * pts / (np.mean(ms_graph) / 1e3),
+                     "graph_ms_per_step": float(np.mean(ms_graph)),
+                     "graph_launches_per_step": l_graph // k,
+                     "graph_what": "the same step as one CUDA graph launch (nnfft_transform "
+                                   "captured once over these buffers)",
                      "exec_adjoint_value": 2 * pts / (np.mean(ms_exec) / 1e3),
                      "exec_adjoint_ms": float(np.mean(ms_exec)),
                      "launches_per_step": l_full // k, "stage_us": stage,
@@ -652,20 +695,29 @@ def run_ours(args, rank, world):
         D_ = D1 if dom in ("fwd_moments", "adj_eval") else D2
         traffic, tnote = ncu_traffic(dom, tuning)
     ops = df_ops(kind, D_) * n_units
-    achieved = ops / (avg_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_LANE_TOPS,
-            "unit": "Tops/s", "frac": achieved / FP32_LANE_TOPS, "traffic": traffic,
-            "traffic_source": tnote,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz: FP32/INT32 lane operations "
-                           "(an FMA counts once); the double-float arithmetic of the split-"
-                           "precision kernels runs there (the FP64 pipe is idle)",
-            "algorithmic_ops_per_launch": ops, "ops_per_unit": df_ops(kind, D_),
-            "hbm": {"achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": gbs / pk["hbm_gbs"], "algorithmic_bytes_per_launch": 24 * M_PTS,
-                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})"}}
+    alu_achieved = ops / (avg_ms / 1e3) / 1e12
+    # The roofline is the HBM one: the dominant kernel's algorithmic bytes (24 B per point for
+    # a point kernel: 8 B node + 16 B complex128 value) over its event-timed duration, against
+    # the measured copy bandwidth.  The split-precision kernels are in fact bound by FP32
+    # instruction issue (ncu: FMA pipe ~40 %, DRAM ~15 %), so the FP32 lane-operation view
+    # is reported beside it under "alu".
+    alg_bytes = 24 * M_PTS if kind != "conv" else None
+    roof = {"bound": "hbm", "kernel": dom, "achieved": gbs if alg_bytes else None,
+            "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": (gbs / pk["hbm_gbs"]) if alg_bytes else None, "traffic": traffic,
+            "traffic_source": tnote, "algorithmic_bytes_per_launch": alg_bytes,
+            "bytes_per_unit": 24, "units_per_launch": M_PTS,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({pk_kind})",
+            "alu": {"achieved": alu_achieved, "peak": FP32_LANE_TOPS, "unit": "Tops/s",
+                    "frac": alu_achieved / FP32_LANE_TOPS, "algorithmic_ops_per_launch": ops,
+                    "ops_per_unit": df_ops(kind, D_),
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz: FP32/INT32 lane "
+                                   "operations (an FMA counts once); the double-float arithmetic "
+                                   "of the split-precision kernels runs there (FP64 pipe idle)"}}
     roof["stage_ms_per_launch"] = avg_ms
     roof["measured_in"] = ("sequential pass of the step (exec, then adjoint), "
-                           f"{float(np.mean(ms_seq)):.4f} ms per step")
+                           f"{float(np.mean(ms_seq)):.4f} ms per step; CUDA events on the plan "
+                           "stream around each stage, averaged over the timed steps")
 
     extra = {}
     extra["stream_launched"] = {"value": pts_step / (np.mean(ms_str) / 1e3), "unit": "pts/s",
@@ -690,6 +742,33 @@ def run_ours(args, rank, world):
     extra["chebyshev_fp64"] = {"value": pts_step / (np.mean(ms_c) / 1e3), "unit": "pts/s",
                                "ms_per_step": float(np.mean(ms_c))}
     del vcd, xcd
+
+    # ---- all-FP64 arithmetic (m = 8): the same plan with every operation in FP64 ----------------
+    plan.set_arith(B.ARITH_FP64)
+    for _ in range(2):
+        step()
+    plan.sync()
+    ms64, _, _ = timed(step, max(3, args.steps // 4))
+    plan.sync()
+    acc64 = None
+    if rank == 0:
+        try:
+            import oracle
+            rows = W.sample_rows(M_PTS, 16, 98)
+            ex = oracle.nnfft_direct(N_BW, v, f, x, rows=rows)
+            acc64 = float(np.max(np.abs(y.cpu().numpy()[rows] - ex)) / np.sum(np.abs(f)))
+        except Exception as e:
+            acc64 = f"unavailable: {e}"
+    extra["fp64_all_fp64_m8"] = {
+        "value": pts_step / (np.mean(ms64) / 1e3), "unit": "pts/s",
+        "ms_per_step": float(np.mean(ms64)), "max_rel_err_sampled": acc64,
+        "what": "the headline step (kernel by kernel) with nnfft_set_arith(NNFFT_ARITH_FP64): "
+                "every point- and grid-kernel operation in FP64 instead of the split "
+                "double-float/FP32 arithmetic"}
+    plan.set_arith(B.ARITH_FP64_SPLIT)
+    plan.set_tuning(**{k: tuning[k] for k in ("moments_lanes_v", "moments_lanes_x", "fft_variant",
+                                              "item_split", "eval_lanes_v", "eval_lanes_x",
+                                              "item_cap") if k in tuning})
 
     # ---- fp32 path (m = 4) -------------------------------------------------------------------
     f32 = fd.to(torch.complex64)
@@ -792,6 +871,10 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample()
+        try:
+            cpu["stage_reference"] = oracle_stage_reference()
+        except Exception as e:   # reported, not fatal
+            cpu["stage_reference"] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {

@@ -4,7 +4,7 @@
  * The library evaluates the NNFFT (nonuniform FFT with nonequispaced spatial
  * and frequency data, "type 3") of Kircheis, Potts and Tasche,
  *
- *     y_j = sum_{k < M1} f_k exp(-2 pi i N v_k x_j),   j < M2,      (eq. (f(xj)))
+ *     y_j = sum_{k < M1} f_k exp(-2 pi i N v_k x_j),   j < M2,      (eq. (1.2))
  *
  * for frequency nodes v_k and spatial nodes x_j in [-1/2, 1/2], by Algorithm 2.2
  * with two sinh-type windows (Example 2.1, Section 4), its adjoint
@@ -13,7 +13,7 @@
  *
  * and the fast sinc transform of Algorithm 6.1 (Section 6),
  *
- *     h_l = sum_{k < L1} c_k sinc(N pi (b_l - a_k)),   l < L2.      (eq. (discretesinctransf))
+ *     h_l = sum_{k < L1} c_k sinc(N pi (b_l - a_k)),   l < L2.      (eq. (6.2))
  *
  * Conventions shared by every entry point:
  *   - Index sets are 0-based arrays; outputs are in the caller's order.
@@ -61,7 +61,7 @@ enum {
 /* Parameters a plan derived from its arguments (Section 2 and Section 4). */
 typedef struct {
     int64_t N, Nstar, N1, K1, N2;   /* N* = N + ceil(2 m1/sigma1); N1 = sigma1 N* rounded up to
-                                       even; K1 = N1 + 2 m1 (= a N1, eq. (consta)); N2 = sigma2 K1
+                                       even; K1 = N1 + 2 m1 (= a N1, eq. (2.6)); N2 = sigma2 K1
                                        rounded up to an even 2^a 3^b 5^c                      */
     int64_t M1, M2;
     int m1, m2;
@@ -218,7 +218,7 @@ int nnfft_set_arith(nnfft_plan_t p, int arith);
  * nnfft_set_nodes: step 0 of Algorithm 2.2 for a new node set.
  * v_dev: M1 doubles, x_dev: M2 doubles, both device pointers, values in
  * [-1/2, 1/2].  Either may be NULL to keep that side's previous nodes.
- * The nodes are rescaled (v* = N v / N*, after eq. (condvk)), binned by grid
+ * The nodes are rescaled (v* = N v / N*, after eq. (2.7)), binned by grid
  * cell and sorted (stable), and the plan keeps the sorted local coordinates
  * and the permutation; the caller's arrays are not referenced afterwards.
  * Out-of-range or NaN nodes set NNFFT_ERANGE in the status word.
@@ -273,6 +273,8 @@ int nnfft_adjoint_host(nnfft_plan_t p, const void *g_host, void *z_host);
  * Same arguments and result as nnfft_exec_host (host pointers; returns after the
  * stream has drained, with any pending kernel status).  All calls on a device
  * share the array; calls whose GPU work overlaps race on it, so serialise them.
+ * The call works on the plan's device (the one current at nnfft_plan), switching
+ * to it for the call if another device is current and back before returning.
  * The first call on each device looks up the array's address (with that device
  * current); make that first call before any stream capture.
  */
@@ -366,7 +368,7 @@ int sinc_exec(int64_t N, int64_t L1, int64_t L2, int m, nnfft_dtype dtype,
  * (Section 5; equivalently (1/2) int_{-1}^{1} exp(-pi i N z x) dz with z = 2t):
  *   SINC_RULE_GL  n-point Gauss-Legendre rule on [-1/2, 1/2] (n = 0 selects 2N);
  *   SINC_RULE_CC  Clenshaw-Curtis: nodes t_j = cos(j pi / n) / 2, j = 0..n, and the
- *                 weights of eq. (wk=) computed on the GPU by Algorithm 5.4 (a DCT-I,
+ *                 weights of eq. (5.4) computed on the GPU by Algorithm 5.4 (a DCT-I,
  *                 done as one FFT of length 2n).  n = 0 selects 4N (Algorithm 6.1:
  *                 n >= 4N); n is rounded up to the next 5-smooth integer (the paper's
  *                 n = 2^t is one) and 2n may not exceed 2^20.  Theorem 5.3 bounds the

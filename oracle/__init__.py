@@ -133,7 +133,7 @@ def num_threads() -> int:
 
 
 def expsum(N, a, c, b, sign=-1, rows=None, nthreads=0):
-    """out_j = sum_k c_k exp(sign 2 pi i N a_k b_j), eq. (f(xj)) -- a direct O(len(a) len(b)) sum.
+    """out_j = sum_k c_k exp(sign 2 pi i N a_k b_j), eq. (1.2) -- a direct O(len(a) len(b)) sum.
 
     sign=-1, a=v, b=x is the NNFFT; sign=+1, a=x, c=g, b=v its adjoint.
     ``rows`` restricts the evaluation to the listed outputs (in that order).
@@ -152,22 +152,22 @@ def expsum(N, a, c, b, sign=-1, rows=None, nthreads=0):
 
 
 def nnfft_direct(N, v, f, x, rows=None, nthreads=0):
-    """f(x_j) = sum_k f_k exp(-2 pi i N v_k x_j), eq. (f(xj)), by definition."""
+    """f(x_j) = sum_k f_k exp(-2 pi i N v_k x_j), eq. (1.2), by definition."""
     return expsum(N, v, f, x, -1, rows, nthreads)
 
 
 def nnfft_adjoint_direct(N, v, x, g, rows=None, nthreads=0):
-    """z_k = sum_j g_j exp(+2 pi i N v_k x_j) (the adjoint of eq. (f(xj))), by definition."""
+    """z_k = sum_j g_j exp(+2 pi i N v_k x_j) (the adjoint of eq. (1.2)), by definition."""
     return expsum(N, x, g, v, +1, rows, nthreads)
 
 
 def sinc_Npi(N, b, a):
-    """sinc(N pi (b - a)) of eq. (sinc), with exact argument reduction."""
+    """sinc(N pi (b - a)) of eq. (5.2), with exact argument reduction."""
     return float(_load().orc_sinc_Npi(int(N), float(b), float(a)))
 
 
 def sinc_direct(N, a, c, b, rows=None, nthreads=0):
-    """h(b_l) = sum_k c_k sinc(N pi (b_l - a_k)), eq. (discretesinctransf), directly."""
+    """h(b_l) = sum_k c_k sinc(N pi (b_l - a_k)), eq. (6.2), directly."""
     lib = _load()
     a = _real(a); b = _real(b); cc = _cplx(c)
     r, nr = _rows(rows)
@@ -189,7 +189,7 @@ def gauss_legendre(n):
 
 
 def sinc_gl(N, a, c, b, n=None, rows=None, nthreads=0):
-    """Eq. (approxsinctrafo) with an n-point Gauss-Legendre rule on [-1/2,1/2] (n = 2N default)."""
+    """Eq. (6.3) with an n-point Gauss-Legendre rule on [-1/2,1/2] (n = 2N default)."""
     lib = _load()
     n = 2 * int(N) if n is None else int(n)
     a = _real(a); b = _real(b); cc = _cplx(c)
@@ -204,7 +204,7 @@ def sinc_gl(N, a, c, b, n=None, rows=None, nthreads=0):
 
 
 def sinc_cc(N, a, c, b, n=None, rows=None, nthreads=0):
-    """Algorithm 6.1 with the Clenshaw-Curtis rule (z_j = cos(j pi/n), eq. (wk=) weights,
+    """Algorithm 6.1 with the Clenshaw-Curtis rule (z_j = cos(j pi/n), eq. (5.4) weights,
     n = 4N default), each step a direct sum."""
     lib = _load()
     n = 4 * int(N) if n is None else int(n)
@@ -226,14 +226,14 @@ def omega_sinh(x, beta):
 
 
 def omega_sinh_hat(v, beta):
-    """Eq. (hatomegasinh), the Fourier transform of omega_sinh (vectorised over v)."""
+    """Eq. (2.1), the Fourier transform of omega_sinh (vectorised over v)."""
     lib = _load()
     return np.vectorize(lambda t: lib.orc_omega_sinh_hat(float(t), float(beta)))(
         np.asarray(v, float))
 
 
 def phi(t, Nj, m, beta):
-    """phi_j(t) = omega(N_j t / m_j), eq. (twowindows)."""
+    """phi_j(t) = omega(N_j t / m_j), eq. (2.5)."""
     lib = _load()
     return np.vectorize(lambda s: lib.orc_phi(float(s), int(Nj), int(m), float(beta)))(
         np.asarray(t, float))
@@ -292,7 +292,7 @@ def bound_sinh(N1, m1, m2, sigma1, sigma2):
 
 
 def cc_weights(n):
-    """Chebyshev points z_k = cos(k pi/n) and Clenshaw-Curtis weights of eq. (wk=), k = 0..n."""
+    """Chebyshev points z_k = cos(k pi/n) and Clenshaw-Curtis weights of eq. (5.4), k = 0..n."""
     lib = _load()
     z = np.zeros(int(n) + 1); w = np.zeros(int(n) + 1)
     assert lib.orc_cc_weights(int(n), _d(z), _d(w)) == 0
@@ -310,6 +310,6 @@ def cc_bound(N, nu):
 
 
 def relative_error(approx, exact, coeffs):
-    """max_j |approx_j - exact_j| / sum_k |coeffs_k|, eq. (relative_nnfft_error)."""
+    """max_j |approx_j - exact_j| / sum_k |coeffs_k|, eq. (4.5)."""
     approx = np.asarray(approx); exact = np.asarray(exact)
     return float(np.max(np.abs(approx - exact)) / np.sum(np.abs(np.asarray(coeffs))))

@@ -9,20 +9,20 @@
  * leg use it.  It shares no code, header, helper or table with the CUDA library.
  *
  * What it computes (each function cites the passage it follows):
- *   - orc_expsum        the exponential sum of eq. (f(xj)) (and, with the sign
+ *   - orc_expsum        the exponential sum of eq. (1.2) (and, with the sign
  *                       flipped and the node roles swapped, its adjoint), by
  *                       its definition: an O(Min*Mout) direct sum.
- *   - orc_sinc_direct   the discrete sinc transform, eq. (discretesinctransf), directly.
+ *   - orc_sinc_direct   the discrete sinc transform, eq. (6.2), directly.
  *   - orc_gauss_legendre, orc_sinc_gl
  *                       Gauss-Legendre nodes/weights on [-1/2,1/2] and the
- *                       quadrature-factorised sinc transform of eq. (approxsinctrafo) with
+ *                       quadrature-factorised sinc transform of eq. (6.3) with
  *                       Gauss-Legendre in place of Clenshaw-Curtis (the variant
  *                       Section 6 attributes to earlier work), by direct sums.
  *   - orc_omega_sinh, orc_omega_sinh_hat
  *                       the sinh-type window of Example 2.1 and its Fourier
- *                       transform, eq. (hatomegasinh), with the I1 power series.
- *   - orc_make_params   N*, N1, N2, a, beta_j of Section 2 (eq. (consta), the
- *                       rescaling after eq. (condvk)) and Section 4, with two
+ *                       transform, eq. (2.1), with the I1 power series.
+ *   - orc_make_params   N*, N1, N2, a, beta_j of Section 2 (eq. (2.6), the
+ *                       rescaling after eq. (2.7)) and Section 4, with two
  *                       choices the paper leaves open: N1 rounded up to even and
  *                       N2 rounded up to an even 5-smooth length.
  *   - orc_nnfft_alg22 / orc_nnfft_alg22_adjoint
@@ -30,12 +30,13 @@
  *                       its exact transpose.
  *   - orc_bound_sinh    the error constant E(phi_sinh) of Theorem 4.1.
  *   - orc_cc_weights, orc_cc_bound
- *                       Clenshaw-Curtis weights, eq. (wk=), and the bound of
+ *                       Clenshaw-Curtis weights, eq. (5.4), and the bound of
  *                       Theorem 5.3.
  *   - orc_sinc_cc       Algorithm 6.1 with the Clenshaw-Curtis rule, steps 1-3
  *                       as direct sums.
  *
- * Equations are cited by their LaTeX labels, e.g. eq. (gell).
+ * Equations are cited by their printed numbers (numbered within each
+ * section), e.g. eq. (2.12) for the grid values g_l of step 1.
  * Complex arrays are interleaved (re, im) doubles.  A centered index set
  * I_M = {-M/2, ..., M/2-1} is stored with array index i = l + M/2.
  *
@@ -96,7 +97,7 @@ int orc_num_threads(void) { return use_threads(0); }
 
 /* ------------------------------------------------------------------------ */
 /* Eq. (1.2): out_j = sum_k c_k exp(sign * 2 pi i N a_k b_j).                */
-/* sign = -1 is the NNFFT of eq. (f(xj)) (a = v frequency nodes, b = x spatial */
+/* sign = -1 is the NNFFT of eq. (1.2) (a = v frequency nodes, b = x spatial */
 /* nodes); sign = +1 with a = x, b = v, c = g is its adjoint                 */
 /* z_k = sum_j g_j exp(+2 pi i N v_k x_j).                                   */
 /* rows == NULL evaluates every output; otherwise only outputs rows[r],      */
@@ -131,7 +132,7 @@ int orc_expsum(i64 N, i64 Min, const double *a, const double *c,
 }
 
 /* ------------------------------------------------------------------------ */
-/* sinc(pi N (b - a)) of eq. (sinc): sin(pi u)/(pi u), value 1 at u = 0.       */
+/* sinc(pi N (b - a)) of eq. (5.2): sin(pi u)/(pi u), value 1 at u = 0.       */
 /* d = b - a is carried as a double-double and u = N d is reduced exactly     */
 /* modulo 2 before the sine, so large N*d loses no accuracy.                 */
 /* ------------------------------------------------------------------------ */
@@ -153,7 +154,7 @@ double orc_sinc_Npi(i64 N, double b, double a) {
     return sin(M_PI * r) / (M_PI * u);
 }
 
-/* Eq. (discretesinctransf): h(b_l) = sum_k c_k sinc(N pi (b_l - a_k)), c complex. */
+/* Eq. (6.2): h(b_l) = sum_k c_k sinc(N pi (b_l - a_k)), c complex. */
 int orc_sinc_direct(i64 N, i64 L1, const double *a, const double *c,
                     i64 L2, const double *b, const i64 *rows, i64 nrows,
                     double *h, int nthreads) {
@@ -224,7 +225,7 @@ int orc_gauss_legendre(i64 n, double *tau, double *w) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Eq. (approxsinctrafo) with a Gauss-Legendre rule (tau_j, w_j), j < n, on [-1/2,1/2]:   */
+/* Eq. (6.3) with a Gauss-Legendre rule (tau_j, w_j), j < n, on [-1/2,1/2]:   */
 /*   g_j   = sum_k c_k exp(+2 pi i N tau_j a_k)                              */
 /*   h_l   = sum_j w_j g_j exp(-2 pi i N tau_j b_l)                          */
 /* which is the quadrature of sinc(N pi (b-a)) = int_{-1/2}^{1/2}             */
@@ -260,14 +261,14 @@ double orc_omega_sinh(double x, double beta) {
     return exp(beta * (s - 1.0)) * (-expm1(-2.0 * beta * s)) / (-expm1(-2.0 * beta));
 }
 
-/* Eq. (hatomegasinh): Fourier transform of omega_sinh.
+/* Eq. (2.1): Fourier transform of omega_sinh.
  *   |v| <  beta/(2 pi): (pi beta / sinh beta) * q^{-1/2} I1(sqrt q), q = beta^2 - 4 pi^2 v^2,
  *                       with q^{-1/2} I1(sqrt q) = (1/2) sum_k q^k / (4^k k! (k+1)!)
- *                       (the power series printed after eq. (hatomegasinh); all terms positive);
+ *                       (the power series printed after eq. (2.1); all terms positive);
  *   |v| == beta/(2 pi): (pi beta / sinh beta) / 2;
  *   |v| >  beta/(2 pi): (pi beta / sinh beta) * q'^{-1/2} J1(sqrt q'), q' = 4 pi^2 v^2 - beta^2
  *                       (libm j1 used as the Bessel primitive).
- * The threshold m(1 - 1/(2 sigma)) of eq. (hatomegasinh) equals beta/(2 pi). */
+ * The threshold m(1 - 1/(2 sigma)) of eq. (2.1) equals beta/(2 pi). */
 double orc_omega_sinh_hat(double v, double beta) {
     double pref = M_PI * beta / sinh(beta);
     double q = beta * beta - 4.0 * M_PI * M_PI * v * v;
@@ -285,7 +286,7 @@ double orc_omega_sinh_hat(double v, double beta) {
     return pref * j1(r) / r;
 }
 
-/* Scaled windows of eq. (twowindows): phi(t) = omega(N t / m), phihat(v) = (m/N) omegahat(m v / N). */
+/* Scaled windows of eq. (2.5): phi(t) = omega(N t / m), phihat(v) = (m/N) omegahat(m v / N). */
 double orc_phi(double t, i64 Nj, int m, double beta) {
     return orc_omega_sinh((double)Nj * t / (double)m, beta);
 }
@@ -295,9 +296,9 @@ double orc_phi_hat(double v, i64 Nj, int m, double beta) {
 
 /* ------------------------------------------------------------------------ */
 /* Parameters of Algorithm 2.2 for v_k, x_j in [-1/2, 1/2] (Section 2):       */
-/*   N*  = N + ceil(2 m1 / sigma1)   (rescaling after eq. (condvk))              */
+/*   N*  = N + ceil(2 m1 / sigma1)   (rescaling after eq. (2.7))              */
 /*   N1  = sigma1 N*, rounded up to an even integer; sigma1,eff = N1/N*       */
-/*   K1  = N1 + 2 m1 = a N1           (eq. (consta))                          */
+/*   K1  = N1 + 2 m1 = a N1           (eq. (2.6))                          */
 /*   N2  = sigma2 K1, rounded up to an even 2^a 3^b 5^c;                      */
 /*         sigma2,eff = N2/K1                                                 */
 /*   beta_j = 2 pi m_j (1 - 1/(2 sigma_j,eff))   (Section 4)                  */
@@ -343,8 +344,8 @@ int orc_make_params(i64 N, double sigma1, double sigma2, int m1, int m2, orc_par
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 2.2 (NNFFT), step by step, for v_k, x_j in [-1/2,1/2]:           */
-/*   rescale v*_k = (N/N*) v_k so that N v_k = N* v*_k (after eq. (condvk));      */
-/*   step 1: g_l = (1/N1) sum_k f_k phi1(l/N1 - v*_k), l in I_{K1} (eq. (gell)) */
+/*   rescale v*_k = (N/N*) v_k so that N v_k = N* v*_k (after eq. (2.7));      */
+/*   step 1: g_l = (1/N1) sum_k f_k phi1(l/N1 - v*_k), l in I_{K1} (eq. (2.12)) */
 /*   step 2: ghat_l = g_l / phi2hat(l)  (phi2hat at the integer l, as step 2 and  */
 /*           the proof of Theorem 3.5 use it; step 0 lists phi2hat(l/a))         */
 /*   step 3: h_s = (1/N2) sum_l ghat_l exp(-2 pi i l s / N2), s in I_{N2}      */
@@ -503,7 +504,7 @@ double orc_bound_sinh(i64 N1, int m1, int m2, double sigma1, double sigma2, doub
 }
 
 /* ------------------------------------------------------------------------ */
-/* Clenshaw-Curtis weights of eq. (wk=) for the rule                         */
+/* Clenshaw-Curtis weights of eq. (5.4) for the rule                         */
 /*   (1/2) int_{-1}^{1} F(t) dt ~ sum_{k=0}^{n} w_k F(z_k), z_k = cos(k pi/n), */
 /* w_k = (1/n) eps(k)^2 sum_{j=0}^{floor(n/2)} eps(2j)^2 2/(1-4j^2) cos(2jk pi/n) */
 /* with eps(0) = eps(n) = sqrt(2)/2 and eps(j) = 1 otherwise (eps(2j) for    */
@@ -538,7 +539,7 @@ double orc_cc_bound(double N, double nu) {
 
 /* ------------------------------------------------------------------------ */
 /* Algorithm 6.1 with the Clenshaw-Curtis rule, every sum taken directly:    */
-/*   z_j = cos(j pi/n), w_j of eq. (wk=), j = 0..n;                          */
+/*   z_j = cos(j pi/n), w_j of eq. (5.4), j = 0..n;                          */
 /*   step 1: g_j     = sum_k c_k exp(-pi i N z_j a_k)                         */
 /*   step 2: alpha_j = w_j g_j                                                */
 /*   step 3: h_l     = sum_j alpha_j exp(+pi i N z_j b_l)                     */

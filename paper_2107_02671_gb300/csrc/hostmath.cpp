@@ -58,12 +58,12 @@ const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Deri
     o->m1 = m1;
     o->m2 = m2;
     // N* = N + ceil(2 m1 / sigma1): frequencies v in [-1/2,1/2] become v* = N v / N*
-    // inside [-1/(2a), 1/(2a)] (rescaling after eq. (condvk)).
+    // inside [-1/(2a), 1/(2a)] (rescaling after eq. (2.7)).
     o->Nstar = N + (int64_t)std::ceil(2.0 * m1 / sigma1 - 1e-12);
     int64_t n1 = (int64_t)std::ceil(sigma1 * (double)o->Nstar - 1e-9);
     if (n1 % 2) ++n1;                                   // N1 in 2N
     o->N1 = n1;
-    o->K1 = n1 + 2 * m1;                                // a N1 = N1 + 2 m1, eq. (consta)
+    o->K1 = n1 + 2 * m1;                                // a N1 = N1 + 2 m1, eq. (2.6)
     int64_t n2 = (int64_t)std::ceil(sigma2 * (double)o->K1 - 1e-9);
     if (n2 % 2) ++n2;
     while (!smooth5(n2)) n2 += 2;                       // even 2^a 3^b 5^c

@@ -14,7 +14,7 @@ constexpr double PI = 3.141592653589793238462643383279502884;
 
 // Sinh-type window of Example 2.1 / Section 4 on [-1, 1] (0 outside).
 double omega_sinh(double x, double beta);
-// Its Fourier transform, eq. (hatomegasinh), for |v| <= beta/(2 pi) via the I1 power
+// Its Fourier transform, eq. (2.1), for |v| <= beta/(2 pi) via the I1 power
 // series (all terms positive); beyond the branch point via J1.
 double omega_sinh_hat(double v, double beta);
 

@@ -156,6 +156,8 @@ constexpr int POS_MAJOR_BLOCKS_PER_SM = 16;
 int report_error(int code, const std::string &msg);
 // The stream a plan was created with.
 cudaStream_t plan_stream(nnfft_plan_t p);
+// The device that was current when the plan was created (its buffers and streams live there).
+int plan_device(nnfft_plan_t p);
 // Device bytes a plan holds.
 size_t plan_bytes(nnfft_plan_t p);
 // Fast sinc transform through plans cached per (sizes rounded up to capacities, stream);

@@ -36,7 +36,7 @@ __global__ void k_complex_to_real(const C2<Real> *__restrict__ in, int n, Real *
     out[i] = in[i].x;
 }
 
-// Clenshaw-Curtis weights, eq. (wk=), through Algorithm 5.4's DCT-I: with
+// Clenshaw-Curtis weights, eq. (5.4), through Algorithm 5.4's DCT-I: with
 //   x_j = eps(j)^2 * 2/(1 - j^2)  for even j <= n,  x_j = 0 for odd j
 // (eps(0)^2 = eps(n)^2 = 1/2, else 1), w_k = eps(k)^2/n * sum_{j=0}^{n} x_j cos(j k pi/n).
 // The sum is the DCT-I of x; it is read off the FFT of the even extension of

@@ -101,6 +101,7 @@ struct nnfft_plan_s {
     int64_t ninst = 1;
     int64_t N_built = 0;                     // N the plan was made for (single instance)
     std::vector<nnfft_info> inst_info;       // per instance
+    int device = 0;                          // the device current when the plan was made
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;              // second stream: the two node sides sort concurrently
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -438,7 +439,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
     for (nnfft_info &I : p->inst_info) I.arith = arith;
 
     // deconvolution tables dec2[l] = 1 / (N1 N2 phihat2(l)), l in I_{K1}: the 1/N1 of
-    // eq. (gell), the division of step 2 and the 1/N2 of step 3, with
+    // eq. (2.12), the division of step 2 and the 1/N2 of step 3, with
     // phihat2(l) = (m2/N2) omegahat2(m2 l / N2); concatenated over instances.
     std::vector<double> dec;
     std::vector<long long> dec_off((size_t)count);
@@ -1073,6 +1074,7 @@ void free_plan(nnfft_plan_s *p) {
 namespace nnfft {
 int report_error(int code, const std::string &msg) { return fail(code, msg); }
 cudaStream_t plan_stream(nnfft_plan_t p) { return p->stream; }
+int plan_device(nnfft_plan_t p) { return p->device; }
 }  // namespace nnfft
 
 // =====================================================================================
@@ -1107,7 +1109,13 @@ int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const i
         cudaGetLastError();
         return fail(NNFFT_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
+    int cur = 0;
+    if ((e = cudaGetDevice(&cur)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NNFFT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
     nnfft_plan_s *p = new nnfft_plan_s();
+    p->device = cur;
     p->stream = static_cast<cudaStream_t>(stream);
     auto bail = [&](int code) { free_plan(p); return code; };
     if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1804,7 +1812,7 @@ namespace {
 
 // One quadrature rule (t_j, w_j) with sum_j w_j exp(-2 pi i N t_j x) ~ sinc(N pi x):
 //   GL: the n-point Gauss-Legendre rule on [-1/2, 1/2];
-//   CC: t_j = cos(j pi / n) / 2, j = 0..n, with the weights of eq. (wk=) (Section 5).
+//   CC: t_j = cos(j pi / n) / 2, j = 0..n, with the weights of eq. (5.4) (Section 5).
 // NNFFT #1 evaluates g_j at the nodes x1 (= -t for GL, +t for CC) and NNFFT #2 sums
 // alpha_j = w_j g_j from the nodes v2 (= +t for GL, -t for CC); for CC this is the
 // sign convention of Algorithm 6.1, for the symmetric GL rule both conventions agree.

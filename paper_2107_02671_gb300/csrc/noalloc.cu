@@ -19,6 +19,10 @@
 //     f and y are fully overwritten by each call, so nothing needs clearing.
 //     Calls whose GPU work overlaps (two host threads, or two plans on different
 //     streams) race on the array: serialise them.
+//   * The call runs on the plan's device (the device that was current when the plan
+//     was made): if another device is current, it switches to the plan's device for
+//     the call and back before returning, so the staging array used is always the
+//     copy on the GPU that holds the plan's buffers and streams.
 //   * The first call on each device looks up the array's device address with
 //     cudaGetSymbolAddress (with that device current) and caches it; make that
 //     first call before any stream capture.
@@ -40,14 +44,10 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of g_noalloc_scratch on the current device (set up once per device).
-int scratch_address(void **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return nnfft::report_error(NNFFT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    }
+// Device address of g_noalloc_scratch on device dev, which must be current (set up
+// once per device).
+int scratch_address(int dev, void **out) {
+    cudaError_t e = cudaSuccess;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES)
         return nnfft::report_error(NNFFT_ECUDA, "device index beyond the no-alloc table");
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
@@ -65,10 +65,36 @@ int scratch_address(void **out) {
     return NNFFT_OK;
 }
 
+// The transform itself, with the plan's device current.
+int exec_noalloc_on_device(nnfft_plan_t p, int dev, const void *f_host, void *y_host);
+
 }  // namespace
 
 extern "C" int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void *y_host) {
     if (!p) return nnfft::report_error(NNFFT_EINVAL, "null plan");
+    const int dev = nnfft::plan_device(p);
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nnfft::report_error(NNFFT_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    if (cur == dev) return exec_noalloc_on_device(p, dev, f_host, y_host);
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) {
+        cudaGetLastError();
+        return nnfft::report_error(NNFFT_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    const int rc = exec_noalloc_on_device(p, dev, f_host, y_host);
+    if ((e = cudaSetDevice(cur)) != cudaSuccess && rc == NNFFT_OK) {
+        cudaGetLastError();
+        return nnfft::report_error(NNFFT_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    }
+    return rc;
+}
+
+namespace {
+
+int exec_noalloc_on_device(nnfft_plan_t p, int dev, const void *f_host, void *y_host) {
     nnfft_info info;
     int rc = nnfft_plan_info(p, &info);
     if (rc) return rc;
@@ -82,7 +108,7 @@ extern "C" int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void 
             NNFFT_EINVAL, "nnfft_exec_host_noalloc: M1 + M2 values exceed the 4 MiB static "
                           "staging array; use nnfft_exec_host");
     void *base = nullptr;
-    if ((rc = scratch_address(&base))) return rc;
+    if ((rc = scratch_address(dev, &base))) return rc;
     unsigned char *f_dev = static_cast<unsigned char *>(base);
     unsigned char *y_dev = f_dev + y_off;
     cudaStream_t st = nnfft::plan_stream(p);
@@ -100,3 +126,5 @@ extern "C" int nnfft_exec_host_noalloc(nnfft_plan_t p, const void *f_host, void 
     }
     return nnfft_sync(p);
 }
+
+}  // namespace

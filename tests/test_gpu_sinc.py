@@ -1,6 +1,6 @@
 """GPU parity of the fast sinc transform (Algorithm 6.1 with a 2N-node
 Gauss-Legendre rule on [-1/2, 1/2]) against the oracle: the direct sum of
-eq. (discretesinctransf) and the Gauss-Legendre definition of eq. (approxsinctrafo)
+eq. (6.2) and the Gauss-Legendre definition of eq. (6.3)
 evaluated by direct sums (which isolates the NNFFT error from the quadrature error)."""
 import numpy as np
 import pytest
@@ -98,7 +98,7 @@ def test_sinc_full_size_sampled_rows():
 # --------------------------------------------------------------------------------------
 @pytest.mark.parametrize("N,n", [(16, 0), (64, 0), (1024, 0), (100, 0), (97, 0), (64, 384)])
 def test_cc_weights_from_gpu(N, n):
-    """Device DCT-I weights against the explicit sum of eq. (wk=); n = 4N by default,
+    """Device DCT-I weights against the explicit sum of eq. (5.4); n = 4N by default,
     rounded up to 5-smooth (N = 97: 388 -> 400)."""
     t, w = B.sinc_quadrature("cc", N, n)
     nn = len(t) - 1
