@@ -240,6 +240,35 @@ int nnfft_exec(nnfft_plan_t p, const void *f_dev, void *y_dev);
 int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev);
 
 /*
+ * Sharded transform: Algorithm 2.2 split at its grid, for node sets divided among P
+ * processes (one GPU each).  Step 1 (eq. (2.12)) is a sum over the frequency nodes k and
+ * step 4 is independent per spatial node j, so each process holds a plan with the same
+ * N, sigma1, sigma2, m1, m2 and dtype for its own share of the v nodes (M1_r of them)
+ * and of the x nodes (M2_r), and a direction becomes
+ *     forward: nnfft_spread_grid (steps 1-2 for its v share) -> sum of the P grids
+ *              (an all-reduce, done by the caller) -> nnfft_exec_grid (steps 3-4 and the
+ *              output division for its x share);
+ *     adjoint: nnfft_adjoint_spread_grid (the transposed steps 4 for its x share) -> sum
+ *              -> nnfft_adjoint_grid (the transposed steps 3-1 for its v share).
+ * The results equal those of one plan over all nodes up to the rounding of the sum.
+ * Grids are device arrays of complex values of the plan's type, centered index l stored
+ * at l + n/2, n even:
+ *     forward: n = K1 = N1 + 2 m1 values ghat_l / N2 = g_l / (N2 phihat2(l)), l in I_K1
+ *              (steps 1-2: the deconvolved grid with the 1/N2 of step 3);
+ *     adjoint: n = N2 values u_s = sum_j g_j phi2(x_j/sigma1 - s/N2) / phihat1(N* x_j),
+ *              s in I_N2 (the window sums taken N2-periodically, N* the rescaled bandwidth of
+ *              eq. (2.7)), the transpose of step 4.
+ * K1 and N2 are in nnfft_plan_info.  Single-instance plans only (NNFFT_EINVAL for a
+ * batch); nnfft_set_nodes first (NNFFT_ESTATE).  Asynchronous on the plan stream like
+ * nnfft_exec; the grid is read or written in stream order.  A share may be empty: its
+ * grid is then zero (spread) or the call does nothing (exec/adjoint from a grid).
+ */
+int nnfft_spread_grid(nnfft_plan_t p, const void *f_dev, void *grid_dev);
+int nnfft_exec_grid(nnfft_plan_t p, const void *grid_dev, void *y_dev);
+int nnfft_adjoint_spread_grid(nnfft_plan_t p, const void *g_dev, void *grid_dev);
+int nnfft_adjoint_grid(nnfft_plan_t p, const void *grid_dev, void *z_dev);
+
+/*
  * nnfft_exec_adjoint: y = A f and z = A^H g for the same nodes in one call, the two
  * directions running concurrently (the adjoint on the plan's second stream with its own
  * work buffers, allocated on the first call).  Same results, arguments and errors as

@@ -303,5 +303,13 @@ cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_
 cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s);
 cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half_z,
                              double *neg_half_z, cudaStream_t s);
+// Sharded transform: copy the n centered positions l in I_n of an N2 grid buffer (element
+// format fmt: 0 float2, 1 double2, 2 double-float float4; p at p mod N2) to out[l + n/2]
+// (complex64 for fmt 0, complex128 otherwise), or back (import writes every buffer
+// element: the n positions and zeros).  n <= N2, both even.
+cudaError_t launch_grid_export(int fmt, const void *buf, int N2, int n, void *out,
+                               cudaStream_t s);
+cudaError_t launch_grid_import(int fmt, const void *in, int N2, int n, void *buf,
+                               cudaStream_t s);
 
 }  // namespace nnfft

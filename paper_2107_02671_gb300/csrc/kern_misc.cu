@@ -1,7 +1,8 @@
 // kern_misc.cu -- small elementwise kernels of the fast sinc transform
 // (Algorithm 6.1): real <-> complex packing, the step-2 product alpha_j = w_j g_j,
 // and the two ends of the Clenshaw-Curtis weight
-// computation (Algorithm 5.4) around a length-2n FFT.
+// computation (Algorithm 5.4) around a length-2n FFT; and the grid export / import
+// of the sharded transform (Algorithm 2.2 split at its grid).
 #include "internal.h"
 
 namespace nnfft {
@@ -73,6 +74,62 @@ __global__ void k_cc_finish(long long n, const double2 *__restrict__ X, double *
     neg_half_z[k] = -z;
 }
 
+// ---------------------------------------------------------------------------------
+// Sharded transform: the grid exchanged between the two halves of a direction.  The
+// plan's N2 grid buffer holds position p (centered) at p mod N2; the exchanged array
+// holds the n positions l in I_n = {-n/2, ..., n/2 - 1} at index l + n/2 as complex
+// values of the plan's type (complex64 for fp32 plans, complex128 for fp64 plans).
+// Buffer element formats: 0 float2, 1 double2, 2 float4 (double-float re.h, re.l, im.h,
+// im.l).  Export reads the n positions; import writes all N2 buffer elements (the n
+// positions, zero elsewhere).
+// ---------------------------------------------------------------------------------
+template <int FMT> struct GridElem;
+template <> struct GridElem<0> {
+    using B = float2;
+    using X = float2;
+    __device__ static X out(B b) { return b; }
+    __device__ static B in(X x) { return x; }
+    __device__ static B zero() { return make_float2(0.f, 0.f); }
+};
+template <> struct GridElem<1> {
+    using B = double2;
+    using X = double2;
+    __device__ static X out(B b) { return b; }
+    __device__ static B in(X x) { return x; }
+    __device__ static B zero() { return make_double2(0.0, 0.0); }
+};
+template <> struct GridElem<2> {
+    using B = float4;
+    using X = double2;
+    __device__ static X out(B b) {
+        return make_double2((double)b.x + (double)b.y, (double)b.z + (double)b.w);
+    }
+    __device__ static B in(X x) {
+        const float rh = (float)x.x, ih = (float)x.y;
+        return make_float4(rh, (float)(x.x - (double)rh), ih, (float)(x.y - (double)ih));
+    }
+    __device__ static B zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+
+template <int FMT>
+__global__ void k_grid_export(const typename GridElem<FMT>::B *__restrict__ buf, int N2, int n,
+                              typename GridElem<FMT>::X *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = i - n / 2;
+    out[i] = GridElem<FMT>::out(buf[l < 0 ? l + N2 : l]);
+}
+
+template <int FMT>
+__global__ void k_grid_import(const typename GridElem<FMT>::X *__restrict__ in, int N2, int n,
+                              typename GridElem<FMT>::B *__restrict__ buf) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N2) return;
+    // the position l in I_n with l = q mod N2, if any (n <= N2, both even)
+    const int l = q < n / 2 ? q : (q >= N2 - n / 2 ? q - N2 : N2);
+    buf[q] = l < N2 ? GridElem<FMT>::in(in[l + n / 2]) : GridElem<FMT>::zero();
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 std::atomic<long long> g_launches{0};
@@ -113,6 +170,41 @@ cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half
                              double *neg_half_z, cudaStream_t s) {
     k_cc_finish<<<cdiv(n + 1, 256), 256, 0, s>>>(n, static_cast<const double2 *>(X), w, half_z,
                                                   neg_half_z);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_export(int fmt, const void *buf, int N2, int n, void *out,
+                               cudaStream_t s) {
+    if (n <= 0 || n > N2 || (n & 1) || (N2 & 1) || fmt < 0 || fmt > 2)
+        return cudaErrorInvalidValue;
+    const int nb = cdiv(n, 256);
+    if (fmt == 0)
+        k_grid_export<0><<<nb, 256, 0, s>>>(static_cast<const float2 *>(buf), N2, n,
+                                            static_cast<float2 *>(out));
+    else if (fmt == 1)
+        k_grid_export<1><<<nb, 256, 0, s>>>(static_cast<const double2 *>(buf), N2, n,
+                                            static_cast<double2 *>(out));
+    else
+        k_grid_export<2><<<nb, 256, 0, s>>>(static_cast<const float4 *>(buf), N2, n,
+                                            static_cast<double2 *>(out));
+    count_launches(1);
+    return cudaGetLastError();
+}
+cudaError_t launch_grid_import(int fmt, const void *in, int N2, int n, void *buf,
+                               cudaStream_t s) {
+    if (n <= 0 || n > N2 || (n & 1) || (N2 & 1) || fmt < 0 || fmt > 2)
+        return cudaErrorInvalidValue;
+    const int nb = cdiv(N2, 256);
+    if (fmt == 0)
+        k_grid_import<0><<<nb, 256, 0, s>>>(static_cast<const float2 *>(in), N2, n,
+                                            static_cast<float2 *>(buf));
+    else if (fmt == 1)
+        k_grid_import<1><<<nb, 256, 0, s>>>(static_cast<const double2 *>(in), N2, n,
+                                            static_cast<double2 *>(buf));
+    else
+        k_grid_import<2><<<nb, 256, 0, s>>>(static_cast<const double2 *>(in), N2, n,
+                                            static_cast<float4 *>(buf));
     count_launches(1);
     return cudaGetLastError();
 }

@@ -865,166 +865,202 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
 }
 
 int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
-                      cudaEvent_t mid = nullptr) {
+                      cudaEvent_t mid = nullptr, int part = 3) {
     const Side &V = p->side[0], &X = p->side[1];
-    if (X.M == 0) return NNFFT_OK;
+    // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
+    if (X.M == 0 && part == 3) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
     const SideDf tv{nullptr, nullptr};
-    {
-        StageTimer t(p, 2, st);
-        NN_CUDA(launch_moments_df(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
+    if (part & 1) {
+        {
+            StageTimer t(p, 2, st);
+            NN_CUDA(launch_moments_df(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
+        }
+        {
+            StageTimer t(p, 12, st);
+            NN_CUDA(launch_cell_fold_df(sv, tv, W.P, W.Q, st), "cell fold");
+        }
+        {
+            StageTimer t(p, 3, st);
+            NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), W.Q, W.bufA, st),
+                    "spread convolution");
+        }
     }
-    {
-        StageTimer t(p, 12, st);
-        NN_CUDA(launch_cell_fold_df(sv, tv, W.P, W.Q, st), "cell fold");
-    }
-    {
-        StageTimer t(p, 3, st);
-        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), W.Q, W.bufA, st),
-                "spread convolution");
-    }
-    {
-        StageTimer t(p, 4, st);
-        NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
-    }
-    // the gather side's nodes (sorted on another stream) are needed from here on
-    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
-    {
-        StageTimer t(p, 5, st);
-        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
-                "gather convolution");
-    }
-    {
-        StageTimer t(p, 6, st);
-        NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+    if ((part & 2) && !(X.M == 0)) {
+        {
+            StageTimer t(p, 4, st);
+            NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
+        }
+        // the gather side's nodes (sorted on another stream) are needed from here on
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 5, st);
+            NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
+                    "gather convolution");
+        }
+        {
+            StageTimer t(p, 6, st);
+            NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+        }
     }
     return NNFFT_OK;
 }
 
 int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
-                      cudaEvent_t mid = nullptr) {
+                      cudaEvent_t mid = nullptr, int part = 3) {
     const Side &V = p->side[0], &X = p->side[1];
-    if (V.M == 0) return NNFFT_OK;
+    // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
+    if (V.M == 0 && part == 3) return NNFFT_OK;
     const SideK<double> sv = side_args<double>(V, false);
     const SideK<double> sx = side_args<double>(X, true);
     const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
-    {
-        StageTimer t(p, 7, st);
-        NN_CUDA(launch_moments_df(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
+    if (part & 1) {
+        {
+            StageTimer t(p, 7, st);
+            NN_CUDA(launch_moments_df(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
+        }
+        {
+            StageTimer t(p, 13, st);
+            NN_CUDA(launch_cell_fold_df(sx, tx, W.P, W.Q, st), "adjoint cell fold");
+        }
+        {
+            StageTimer t(p, 8, st);
+            NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), W.Q, W.bufA, st),
+                    "adjoint spread convolution");
+        }
     }
-    {
-        StageTimer t(p, 13, st);
-        NN_CUDA(launch_cell_fold_df(sx, tx, W.P, W.Q, st), "adjoint cell fold");
-    }
-    {
-        StageTimer t(p, 8, st);
-        NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), W.Q, W.bufA, st),
-                "adjoint spread convolution");
-    }
-    {
-        StageTimer t(p, 9, st);
-        NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
-    }
-    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
-    {
-        StageTimer t(p, 10, st);
-        NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
-                "adjoint gather convolution");
-    }
-    {
-        StageTimer t(p, 11, st);
-        NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+    if ((part & 2) && !(V.M == 0)) {
+        {
+            StageTimer t(p, 9, st);
+            NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+        }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 10, st);
+            NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
+                    "adjoint gather convolution");
+        }
+        {
+            StageTimer t(p, 11, st);
+            NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+        }
     }
     return NNFFT_OK;
 }
 
 template <typename Real>
 int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
-                cudaEvent_t mid = nullptr) {
+                cudaEvent_t mid = nullptr, int part = 3) {
     const Side &V = p->side[0], &X = p->side[1];
-    if (X.M == 0) return NNFFT_OK;
+    // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
+    if (X.M == 0 && part == 3) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
-    {
-        StageTimer t(p, 2, st);
-        NN_CUDA(launch_moments<Real>(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
+    if (part & 1) {
+        {
+            StageTimer t(p, 2, st);
+            NN_CUDA(launch_moments<Real>(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
+        }
+        {
+            StageTimer t(p, 12, st);
+            NN_CUDA(launch_cell_fold<Real>(sv, W.P, W.Q, st), "cell fold");
+        }
+        {
+            StageTimer t(p, 3, st);
+            NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 0, true, false), W.Q, W.bufA, st),
+                    "spread convolution");
+        }
     }
-    {
-        StageTimer t(p, 12, st);
-        NN_CUDA(launch_cell_fold<Real>(sv, W.P, W.Q, st), "cell fold");
-    }
-    {
-        StageTimer t(p, 3, st);
-        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 0, true, false), W.Q, W.bufA, st),
-                "spread convolution");
-    }
-    {
-        StageTimer t(p, 4, st);
-        NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
-    }
-    // the gather side's nodes (sorted on another stream) are needed from here on
-    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
-    {
-        StageTimer t(p, 5, st);
-        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), W.bufC, W.Q, st),
-                "gather convolution");
-    }
-    {
-        StageTimer t(p, 6, st);
-        NN_CUDA(launch_eval<Real>(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+    if ((part & 2) && !(X.M == 0)) {
+        {
+            StageTimer t(p, 4, st);
+            NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
+        }
+        // the gather side's nodes (sorted on another stream) are needed from here on
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 5, st);
+            NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), W.bufC, W.Q, st),
+                    "gather convolution");
+        }
+        {
+            StageTimer t(p, 6, st);
+            NN_CUDA(launch_eval<Real>(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+        }
     }
     return NNFFT_OK;
 }
 
 template <typename Real>
 int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
-                cudaEvent_t mid = nullptr) {
+                cudaEvent_t mid = nullptr, int part = 3) {
     const Side &V = p->side[0], &X = p->side[1];
-    if (V.M == 0) return NNFFT_OK;
+    // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
+    if (V.M == 0 && part == 3) return NNFFT_OK;
     const SideK<Real> sv = side_args<Real>(V, false);
     const SideK<Real> sx = side_args<Real>(X, true);
-    {
-        StageTimer t(p, 7, st);
-        NN_CUDA(launch_moments<Real>(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
+    if (part & 1) {
+        {
+            StageTimer t(p, 7, st);
+            NN_CUDA(launch_moments<Real>(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
+        }
+        {
+            StageTimer t(p, 13, st);
+            NN_CUDA(launch_cell_fold<Real>(sx, W.P, W.Q, st), "adjoint cell fold");
+        }
+        {
+            StageTimer t(p, 8, st);
+            NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 1, true, false), W.Q, W.bufA, st),
+                    "adjoint spread convolution");
+        }
     }
-    {
-        StageTimer t(p, 13, st);
-        NN_CUDA(launch_cell_fold<Real>(sx, W.P, W.Q, st), "adjoint cell fold");
-    }
-    {
-        StageTimer t(p, 8, st);
-        NN_CUDA(launch_spread_conv<Real>(grid_launch<Real>(p, 1, true, false), W.Q, W.bufA, st),
-                "adjoint spread convolution");
-    }
-    {
-        StageTimer t(p, 9, st);
-        NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
-    }
-    if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
-    {
-        StageTimer t(p, 10, st);
-        NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), W.bufC, W.Q, st),
-                "adjoint gather convolution");
-    }
-    {
-        StageTimer t(p, 11, st);
-        NN_CUDA(launch_eval<Real>(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+    if ((part & 2) && !(V.M == 0)) {
+        {
+            StageTimer t(p, 9, st);
+            NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+        }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 10, st);
+            NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), W.bufC, W.Q, st),
+                    "adjoint gather convolution");
+        }
+        {
+            StageTimer t(p, 11, st);
+            NN_CUDA(launch_eval<Real>(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+        }
     }
     return NNFFT_OK;
 }
 
-// mid: an event the gather half (gather convolution + evaluation) waits for, or nullptr
+// mid: an event the gather half (gather convolution + evaluation) waits for, or nullptr.
+// part: 1 the spread half only (into the grid buffer W.bufA), 2 the rest only (from W.bufA:
+// FFT, gather convolution, evaluation), 3 both.
 int forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
-            cudaEvent_t mid = nullptr) {
-    if (p->dbl && p->split) return run_forward_split(p, f, y, st, W, mid);
-    return p->dbl ? run_forward<double>(p, f, y, st, W, mid) : run_forward<float>(p, f, y, st, W, mid);
+            cudaEvent_t mid = nullptr, int part = 3) {
+    if (p->dbl && p->split) return run_forward_split(p, f, y, st, W, mid, part);
+    return p->dbl ? run_forward<double>(p, f, y, st, W, mid, part)
+                  : run_forward<float>(p, f, y, st, W, mid, part);
 }
 
 int adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const Work &W,
-            cudaEvent_t mid = nullptr) {
-    if (p->dbl && p->split) return run_adjoint_split(p, g, z, st, W, mid);
-    return p->dbl ? run_adjoint<double>(p, g, z, st, W, mid) : run_adjoint<float>(p, g, z, st, W, mid);
+            cudaEvent_t mid = nullptr, int part = 3) {
+    if (p->dbl && p->split) return run_adjoint_split(p, g, z, st, W, mid, part);
+    return p->dbl ? run_adjoint<double>(p, g, z, st, W, mid, part)
+                  : run_adjoint<float>(p, g, z, st, W, mid, part);
+}
+
+// Element format of the plan's grid buffers (launch_grid_export / launch_grid_import).
+int grid_format(const nnfft_plan_s *p) { return !p->dbl ? 0 : (p->split ? 2 : 1); }
+
+// Checks shared by the four sharded-transform calls.
+int shard_check(nnfft_plan_s *p, const void *grid) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (p->ninst != 1) return fail(NNFFT_EINVAL, "the sharded calls take single-instance plans");
+    if (!p->side[0].set || !p->side[1].set) return fail(NNFFT_ESTATE, "nnfft_set_nodes first");
+    if (!grid) return fail(NNFFT_EINVAL, "null grid pointer");
+    return NNFFT_OK;
 }
 
 int collect_status(nnfft_plan_s *p) {
@@ -1229,6 +1265,50 @@ int nnfft_adjoint(nnfft_plan_t p, const void *g_dev, void *z_dev) {
     if ((p->info.M2 > 0 && !g_dev) || (p->info.M1 > 0 && !z_dev))
         return fail(NNFFT_EINVAL, "null data pointer");
     return adjoint(p, g_dev, z_dev, p->stream, p->work[0]);
+}
+
+int nnfft_spread_grid(nnfft_plan_t p, const void *f_dev, void *grid_dev) {
+    int rc = shard_check(p, grid_dev);
+    if (rc) return rc;
+    if (p->info.M1 > 0 && !f_dev) return fail(NNFFT_EINVAL, "null data pointer");
+    if ((rc = forward(p, f_dev, nullptr, p->stream, p->work[0], nullptr, 1))) return rc;
+    NN_CUDA(launch_grid_export(grid_format(p), p->work[0].bufA, (int)p->info.N2,
+                               (int)p->info.K1, grid_dev, p->stream),
+            "grid export");
+    return NNFFT_OK;
+}
+
+int nnfft_exec_grid(nnfft_plan_t p, const void *grid_dev, void *y_dev) {
+    int rc = shard_check(p, grid_dev);
+    if (rc) return rc;
+    if (p->info.M2 > 0 && !y_dev) return fail(NNFFT_EINVAL, "null data pointer");
+    if (p->info.M2 == 0) return NNFFT_OK;
+    NN_CUDA(launch_grid_import(grid_format(p), grid_dev, (int)p->info.N2, (int)p->info.K1,
+                               p->work[0].bufA, p->stream),
+            "grid import");
+    return forward(p, nullptr, y_dev, p->stream, p->work[0], nullptr, 2);
+}
+
+int nnfft_adjoint_spread_grid(nnfft_plan_t p, const void *g_dev, void *grid_dev) {
+    int rc = shard_check(p, grid_dev);
+    if (rc) return rc;
+    if (p->info.M2 > 0 && !g_dev) return fail(NNFFT_EINVAL, "null data pointer");
+    if ((rc = adjoint(p, g_dev, nullptr, p->stream, p->work[0], nullptr, 1))) return rc;
+    NN_CUDA(launch_grid_export(grid_format(p), p->work[0].bufA, (int)p->info.N2,
+                               (int)p->info.N2, grid_dev, p->stream),
+            "grid export");
+    return NNFFT_OK;
+}
+
+int nnfft_adjoint_grid(nnfft_plan_t p, const void *grid_dev, void *z_dev) {
+    int rc = shard_check(p, grid_dev);
+    if (rc) return rc;
+    if (p->info.M1 > 0 && !z_dev) return fail(NNFFT_EINVAL, "null data pointer");
+    if (p->info.M1 == 0) return NNFFT_OK;
+    NN_CUDA(launch_grid_import(grid_format(p), grid_dev, (int)p->info.N2, (int)p->info.N2,
+                               p->work[0].bufA, p->stream),
+            "grid import");
+    return adjoint(p, nullptr, z_dev, p->stream, p->work[0], nullptr, 2);
 }
 
 int nnfft_exec_adjoint(nnfft_plan_t p, const void *f_dev, void *y_dev, const void *g_dev,

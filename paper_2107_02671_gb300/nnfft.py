@@ -152,6 +152,10 @@ def load_library(build_if_missing: bool = True):
         lib.sinc_release.argtypes = []
         lib.nnfft_gauss_legendre.argtypes = [i64, vp, vp]
         lib.nnfft_set_arith.argtypes = [vp, cint]
+        lib.nnfft_spread_grid.argtypes = [vp, vp, vp]
+        lib.nnfft_exec_grid.argtypes = [vp, vp, vp]
+        lib.nnfft_adjoint_spread_grid.argtypes = [vp, vp, vp]
+        lib.nnfft_adjoint_grid.argtypes = [vp, vp, vp]
         lib.nnfft_timing_enable.argtypes = [vp, cint]
         lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
         lib.nnfft_selftest_fixed63.argtypes = [vp, vp, i64]
@@ -284,6 +288,49 @@ class Plan:
             out = torch.empty(self.M1, dtype=self.cdtype, device=g.device)
         po = _dev_tensor(out, self.cdtype, self.M1, "out")
         _check(self._lib.nnfft_adjoint(self._h, pg, po))
+        return out
+
+    # sharded transform: Algorithm 2.2 split at its grid (nnfft_spread_grid & co.)
+    def spread_grid(self, f, grid=None):
+        """Steps 1-2 for this plan's v nodes: the K1 grid values ghat_l / N2 (plan dtype)."""
+        import torch
+        pf = _dev_tensor(f, self.cdtype, self.M1, "f")
+        K1 = self.info["K1"]
+        if grid is None:
+            grid = torch.empty(K1, dtype=self.cdtype, device=f.device)
+        pgr = _dev_tensor(grid, self.cdtype, K1, "grid")
+        _check(self._lib.nnfft_spread_grid(self._h, pf, pgr))
+        return grid
+
+    def exec_grid(self, grid, out=None):
+        """Steps 3-4 and the output division for this plan's x nodes from a K1 grid."""
+        import torch
+        pgr = _dev_tensor(grid, self.cdtype, self.info["K1"], "grid")
+        if out is None:
+            out = torch.empty(self.M2, dtype=self.cdtype, device=grid.device)
+        po = _dev_tensor(out, self.cdtype, self.M2, "out")
+        _check(self._lib.nnfft_exec_grid(self._h, pgr, po))
+        return out
+
+    def adjoint_spread_grid(self, g, grid=None):
+        """The adjoint's first half for this plan's x nodes: the N2 grid values u_s."""
+        import torch
+        pg = _dev_tensor(g, self.cdtype, self.M2, "g")
+        N2 = self.info["N2"]
+        if grid is None:
+            grid = torch.empty(N2, dtype=self.cdtype, device=g.device)
+        pgr = _dev_tensor(grid, self.cdtype, N2, "grid")
+        _check(self._lib.nnfft_adjoint_spread_grid(self._h, pg, pgr))
+        return grid
+
+    def adjoint_grid(self, grid, out=None):
+        """The adjoint's second half for this plan's v nodes from an N2 grid."""
+        import torch
+        pgr = _dev_tensor(grid, self.cdtype, self.info["N2"], "grid")
+        if out is None:
+            out = torch.empty(self.M1, dtype=self.cdtype, device=grid.device)
+        po = _dev_tensor(out, self.cdtype, self.M1, "out")
+        _check(self._lib.nnfft_adjoint_grid(self._h, pgr, po))
         return out
 
     def exec_adjoint(self, f, g, y=None, z=None):
