@@ -435,41 +435,42 @@ def run_batched(args, rank, dev, flush, timed, pk):
     return out
 
 
-SERVE_RATE, SERVE_WARM, SERVE_TIMED = 2000.0, 1500, 12000
+SERVE_RATE, SERVE_WARM, SERVE_TIMED = 2000.0, 1500, 100000
 SERVE_MAXP = 1 << 22
+SERVE_SWEEP = (4000.0, 8000.0, 16000.0)      # offered rates of the capacity sweep
+SERVE_SWEEP_N = 4000
 
 
-def run_served(args, rank):
-    """The served mixed stream: Poisson arrivals at 2000 requests/s, 70% NNFFT and 30% sinc
-    transform, N log-uniform in [64, 16384], M1 and M2 log-uniform in [1e3, 4e6], tolerance
-    drawn from {1e-5, 1e-9, 1e-12}, 64 GB device budget, 4 slots.  Host inputs are slices
-    of pinned pools (synthetic uniform nodes, N(0,1) values).  The first SERVE_WARM
-    requests fill the plan cache and are not counted; latency is submit -> completion."""
-    import threading
+def _serve_pools(rng):
+    """Pinned host pools the requests slice: uniform nodes, N(0,1) values."""
     import torch
+    P = SERVE_MAXP
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()      # noqa: E731
+    pools = {"nodes": pin(rng.uniform(-0.5, 0.5, P))}
+    c128 = (rng.standard_normal(P) + 1j * rng.standard_normal(P)).astype(np.complex128)
+    pools["c128"], pools["c64"] = pin(c128), pin(c128.astype(np.complex64))
+    r64 = rng.standard_normal(P)
+    pools["r64"], pools["r32"] = pin(r64), pin(r64.astype(np.float32))
+    pools["out"] = [torch.empty(P, dtype=torch.complex128).pin_memory().numpy() for _ in range(16)]
+    return pools
+
+
+def _serve_stream(S, pools, rng, n, rate, warm):
+    """Submit n requests of the served mix with exponential gaps at `rate` per second; the
+    first `warm` fill the plan cache and are excluded (stats reset after them).  Returns
+    the server's statistics of the rest and the offered points per second."""
+    import threading
     from paper_2107_02671_gb300 import nnfft as B
-    rng = np.random.default_rng(42 + rank)
-    n = SERVE_WARM + min(SERVE_TIMED, max(2000, 100 * args.steps))
-    gaps = rng.exponential(1.0 / SERVE_RATE, n)
+    P = SERVE_MAXP
+    gaps = rng.exponential(1.0 / rate, n)
     kind = rng.random(n) < 0.7                       # True: NNFFT
     lN, lM = np.log([64, 16384]), np.log([1e3, 4e6])
     Ns = np.rint(np.exp(rng.uniform(*lN, n))).astype(np.int64)
     M1 = np.rint(np.exp(rng.uniform(*lM, n))).astype(np.int64)
     M2 = np.rint(np.exp(rng.uniform(*lM, n))).astype(np.int64)
     tols = rng.choice([1e-5, 1e-9, 1e-12], n)
-    P = SERVE_MAXP
-    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()      # noqa: E731
-    nodes = pin(rng.uniform(-0.5, 0.5, P))
-    c128 = pin((rng.standard_normal(P) + 1j * rng.standard_normal(P)).astype(np.complex128))
-    c64 = pin(c128.astype(np.complex64))
-    r64 = pin(rng.standard_normal(P))
-    r32 = pin(r64.astype(np.float32))
-    ring = 16
-    out128 = [torch.empty(P, dtype=torch.complex128).pin_memory().numpy() for _ in range(ring)]
-    S = B.Server(mem_budget_bytes=64 << 30, slots=4, max_points=P)
-    ids = []
+    ids, lat = [], []
     done = threading.Event()
-    lat = []
 
     def waiter():
         k = 0
@@ -484,47 +485,113 @@ def run_served(args, rank):
 
     th = threading.Thread(target=waiter)
     th.start()
-    t0 = time.perf_counter()
-    t_next = t0
-    warm_done_at = None
+    t_next = time.perf_counter()
+    t_start = t_next
+    if warm == 0:
+        S.stats(reset=True)
     for i in range(n):
-        if i == SERVE_WARM:
-            while len(lat) < SERVE_WARM:               # drain the warm-up, then restart the clock
+        if warm and i == warm:
+            while len(lat) < warm:                    # drain the warm-up, then restart the clock
                 time.sleep(0.001)
             S.stats(reset=True)
             t_next = time.perf_counter()
-            warm_done_at = t_next
+            t_start = t_next
         t_next += gaps[i]
         while time.perf_counter() < t_next:
             pass
         m1, m2, N = int(M1[i]), int(M2[i]), int(Ns[i])
         o1, o2 = int(rng.integers(0, P - m1 + 1)), int(rng.integers(0, P - m2 + 1))
-        v, x = nodes[o1:o1 + m1], nodes[o2:o2 + m2]
+        v, x = pools["nodes"][o1:o1 + m1], pools["nodes"][o2:o2 + m2]
         dt, _ = B.tolerance_params(tols[i])
-        buf = out128[i % ring]
+        buf = pools["out"][i % len(pools["out"])]
         if kind[i]:
-            f = (c128 if dt == B.NNFFT_C128 else c64)[o1:o1 + m1]
-            y = buf.view(f.dtype)[:m2]
-            ids.append(S.submit_nnfft(N, v, x, f, y, tols[i]))
+            f = (pools["c128"] if dt == B.NNFFT_C128 else pools["c64"])[o1:o1 + m1]
+            ids.append(S.submit_nnfft(N, v, x, f, buf.view(f.dtype)[:m2], tols[i]))
         else:
-            N = min(N, 16384)
-            c = (r64 if dt == B.NNFFT_C128 else r32)[o1:o1 + m1]
-            h = buf.view(c.dtype)[:m2]
-            ids.append(S.submit_sinc(N, v, c, x, h, tols[i], "gl"))
+            c = (pools["r64"] if dt == B.NNFFT_C128 else pools["r32"])[o1:o1 + m1]
+            ids.append(S.submit_sinc(min(N, 16384), v, c, x, buf.view(c.dtype)[:m2], tols[i], "gl"))
+    t_arrivals = time.perf_counter() - t_start
     done.set()
     th.join()
-    st = S.stats()
+    offered = float(np.sum((M1 + M2)[warm:])) / max(t_arrivals, 1e-9)
+    return S.stats(), offered
+
+
+def _served_errors(S, rng, per_class=3):
+    """Error against the oracle per tolerance class: per class `per_class` NNFFT requests
+    and one sinc request of the served mix's size distribution (M capped at 2e5 so that the
+    oracle finishes), 48 sampled rows each; max |error| / 1-norm of the inputs."""
+    import oracle
+    from paper_2107_02671_gb300 import nnfft as B
+    from paper_2107_02671_gb300 import workloads as W
+    lN, lM = np.log([64, 16384]), np.log([1e3, 2e5])
+    out = {}
+    for tol in (1e-5, 1e-9, 1e-12):
+        dt, _ = B.tolerance_params(tol)
+        worst = 0.0
+        for k in range(per_class + 1):
+            N = int(np.rint(np.exp(rng.uniform(*lN))))
+            m1, m2 = (int(np.rint(np.exp(rng.uniform(*lM)))) for _ in range(2))
+            v, x = rng.uniform(-0.5, 0.5, m1), rng.uniform(-0.5, 0.5, m2)
+            rows = W.sample_rows(m2, 48, k)
+            if k < per_class:
+                f = W.draw_complex(rng, m1, np.complex128 if dt == B.NNFFT_C128 else np.complex64)
+                y = np.zeros(m2, f.dtype)
+                S.wait(S.submit_nnfft(N, v, x, f, y, tol))
+                want = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
+            else:
+                f = rng.standard_normal(m1).astype(np.float64 if dt == B.NNFFT_C128 else np.float32)
+                y = np.zeros(m2, f.dtype)
+                S.wait(S.submit_sinc(N, v, f, x, y, tol, "gl"))
+                want = oracle.sinc_direct(N, v, f.astype(np.complex128), x, rows=rows)
+            err = float(np.max(np.abs(y[rows].astype(np.complex128) - want)) / np.sum(np.abs(f)))
+            worst = max(worst, err)
+        out[f"{tol:g}"] = worst
+    return out
+
+
+def run_served(args, rank):
+    """The served mixed stream: Poisson arrivals at 2000 requests/s, 70% NNFFT and 30% sinc
+    transform, N log-uniform in [64, 16384], M1 and M2 log-uniform in [1e3, 4e6], tolerance
+    drawn from {1e-5, 1e-9, 1e-12}, 64 GB device budget, 4 slots, 10^5 timed requests.  Host
+    inputs are slices of pinned pools (synthetic uniform nodes, N(0,1) values).  The first
+    SERVE_WARM requests fill the plan cache and are not counted; latency is submit ->
+    completion.  Then a capacity sweep at higher offered rates and the error of sampled
+    requests of each tolerance class against the oracle."""
+    from paper_2107_02671_gb300 import nnfft as B
+    rng = np.random.default_rng(42 + rank)
+    pools = _serve_pools(rng)
+    S = B.Server(mem_budget_bytes=64 << 30, slots=4, max_points=SERVE_MAXP)
+    n_timed = args.serve_requests
+    st, offered = _serve_stream(S, pools, rng, SERVE_WARM + n_timed, SERVE_RATE, SERVE_WARM)
+    sweep = []
+    for rate in SERVE_SWEEP:
+        s2, off2 = _serve_stream(S, pools, rng, SERVE_SWEEP_N, rate, 0)
+        sweep.append({"offered_rate_per_s": rate, "offered_pts_per_s": off2,
+                      "completed_pts_per_s": s2["points"] / s2["seconds"] if s2["seconds"] > 0 else None,
+                      "p50_ms": s2["p50_ms"], "p99_ms": s2["p99_ms"], "requests": SERVE_SWEEP_N})
+    errs = None
+    if rank == 0:
+        try:
+            errs = _served_errors(S, rng)
+        except Exception as e:   # reported; the tests enforce the tolerances
+            errs = {"error": f"{type(e).__name__}: {e}"}
     S.close()
-    timed = n - SERVE_WARM
-    offered = float(np.sum((M1 + M2)[SERVE_WARM:]))
-    return {"requests_timed": timed, "requests_warmup": SERVE_WARM, "arrival_rate_per_s": SERVE_RATE,
+    return {"requests_timed": n_timed, "requests_warmup": SERVE_WARM, "arrival_rate_per_s": SERVE_RATE,
             "mix": "70% NNFFT / 30% sinc (GL), N in [64, 16384], M in [1e3, 4e6], tol {1e-5, 1e-9, 1e-12}",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
             "pts_per_s": st["points"] / st["seconds"] if st["seconds"] > 0 else None,
-            "offered_pts_per_s": offered / (time.perf_counter() - warm_done_at),
+            "offered_pts_per_s": offered,
             "completed": st["completed"], "failed": st["failed"], "plans_cached": st["plans_cached"],
             "plans_made": st["plans_made"], "plans_evicted": st["plans_evicted"],
-            "device_gb": st["device_bytes"] / 2**30, "slots": 4, "budget_gb": 64}
+            "device_gb": st["device_bytes"] / 2**30, "slots": 4, "budget_gb": 64,
+            "capacity_sweep": sweep,
+            "capacity_note": "completed points/s at rising offered rates (4000 requests each, no "
+                             "warm-up, plans already cached): where it stops following the "
+                             "offered load, the loop is at capacity",
+            "max_rel_err_by_tolerance": errs,
+            "max_rel_err_note": "per class: 3 NNFFT + 1 sinc request of the mix (M <= 2e5), 48 "
+                                "sampled rows each against the oracle's direct sums"}
 
 
 def whole_job_value(total_ms, steps, pts_step, world, device="cpu"):
@@ -732,6 +799,27 @@ def run_ours(args, rank, world):
                                "ms_per_step": float(np.mean(ms_e)),
                                "what": "forward + adjoint with resident plan (nodes already set)"}
 
+    # ---- evaluation kernels side by side: flat, flat with TMA-staged cell tiles, 32-lane ----
+    # (the sequential pass's per-stage event times; the other tuning choices kept)
+    tune_keys = ("moments_lanes_v", "moments_lanes_x", "fft_variant", "item_split",
+                 "eval_lanes_v", "eval_lanes_x", "item_cap", "sort_lsd")
+    base_t = {k: tuning[k] for k in tune_keys if k in tuning}
+    ab = {}
+    for name, el in (("flat", 1), ("flat_tma", 2), ("lanes32", 32)):
+        plan.set_tuning(**{**base_t, "eval_lanes_v": el, "eval_lanes_x": el})
+        for _ in range(2):
+            step_seq()
+        _, _, st_ab = timed(step_seq, max(3, args.steps // 4), plan, label=f"eval_{name}")
+        plan.sync()
+        ab[name] = {k: round(1e3 * tot / n, 2) for k, (tot, n) in st_ab.items()
+                    if n and k in ("fwd_eval", "adj_eval")}
+    plan.set_tuning(**base_t)
+    extra["eval_kernels_us"] = {**ab, "what": "per-launch device time (us) of the gather "
+                                               "evaluation at the headline size: one thread per "
+                                               "point, the same with each block's cell window "
+                                               "sums staged in shared memory by one TMA bulk "
+                                               "copy, one warp per work item"}
+
     # ---- Chebyshev nodes (fp64) ----------------------------------------------------------------
     vc, xc, _ = W.nnfft_inputs(M_PTS, M_PTS, rank, nodes="chebyshev")
     vcd, xcd = to_dev(vc), to_dev(xc)
@@ -768,7 +856,7 @@ def run_ours(args, rank, world):
     plan.set_arith(B.ARITH_FP64_SPLIT)
     plan.set_tuning(**{k: tuning[k] for k in ("moments_lanes_v", "moments_lanes_x", "fft_variant",
                                               "item_split", "eval_lanes_v", "eval_lanes_x",
-                                              "item_cap") if k in tuning})
+                                              "item_cap", "sort_lsd") if k in tuning})
 
     # ---- fp32 path (m = 4) -------------------------------------------------------------------
     f32 = fd.to(torch.complex64)
@@ -922,11 +1010,13 @@ def main():
                     help="headline step launched kernel by kernel instead of as one CUDA graph")
     ap.add_argument("--tuning", type=lambda t: [int(u) for u in t.split(",")], default=None,
                     help="headline kernel variants instead of autotuning: moments lanes v,x, "
-                         "fft variant, item split, evaluation lanes v,x[, item cap] "
+                         "fft variant, item split, evaluation lanes v,x[, item cap[, sort_lsd]] "
                          "(e.g. 8,8,0,0,1,1,64)")
     ap.add_argument("--no-serve", action="store_true", help="skip the served mixed stream")
     ap.add_argument("--only-served", action="store_true",
                     help="run only the served mixed stream and print its numbers")
+    ap.add_argument("--serve-requests", type=int, default=SERVE_TIMED,
+                    help="timed requests of the served stream (10^5)")
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
                     help="instances of the batched workload (512; fewer for profiling runs)")
     ap.add_argument("--only-fp32-batch", action="store_true",

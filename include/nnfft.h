@@ -187,23 +187,32 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
  */
 enum { NNFFT_TUNE_FLUSH_L2 = 1 };
 typedef struct {
-    int moments_lanes_v, moments_lanes_x;   /* 32, 16 or 8 */
+    int moments_lanes_v, moments_lanes_x;   /* 32, 16 or 8 lanes per work item; 4: the 8-lane
+                                               split-precision kernel with the point loads
+                                               software-pipelined across chunks */
     int fft_variant;                        /* 0 or 1 */
     int tuned;                              /* 1 after nnfft_autotune */
     double default_ms, best_ms;             /* per run: default and chosen config */
     int item_split;                         /* 1: small work items one thread each (default 0) */
     int timed_transform;                    /* 1: runs were full transforms */
-    int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8; 1 = flat */
+    int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8; 1 = flat
+                                               (thread per point); 2 = flat with each block's
+                                               cell window sums staged by a TMA bulk copy */
     int item_cap;                           /* points per work item at most: 256, 128, 64, 32 */
+    int sort_lsd;                           /* node sort of 9- to 16-bit cell keys: 0 two-stage
+                                               (high-digit scatter, then a shared-memory sort per
+                                               bucket; default for single instances), 1 LSD radix
+                                               passes (default for batches) */
 } nnfft_tuning;
 int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, const void *f_dev,
                    void *y_dev, const void *g_dev, void *z_dev, int reps, int flags);
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
- * moments_lanes_v / _x in {8, 16, 32}, eval_lanes_v / _x in {1, 8, 32} (0: 32), fft_variant in
- * {0, 1}, item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256); the other fields are
+ * moments_lanes_v / _x in {4, 8, 16, 32}, eval_lanes_v / _x in {1, 2, 8, 32} (0: 32), fft_variant in
+ * {0, 1}, item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256), sort_lsd in {0, 1}
+ * (both sorts give the same order: the same results bitwise); the other fields are
  * ignored (a lane count a kernel does not have runs as one warp per item).  EINVAL otherwise.
- * Takes effect for the work queued next; a changed item_split or item_cap needs
+ * Takes effect for the work queued next; a changed item_split, item_cap or sort_lsd needs
  * nnfft_set_nodes again. */
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t);
 
@@ -474,6 +483,19 @@ int nnfft_timing_read(nnfft_plan_t p, nnfft_timing *out, int reset);
  */
 int nnfft_selftest_fixed63(const int64_t *in_dev, float *out_dev, int64_t n);
 
+/*
+ * nnfft_selftest_bulk_copy: check of the bounded waits around the library's bulk (TMA)
+ * copies into shared memory.  One block arms a shared-memory barrier for n floats
+ * (0 < n <= 4096, n a multiple of 4), copies src_dev into shared memory with one bulk copy
+ * and writes it to dst_dev.  With arm_only the copy is not issued, so the wait on the
+ * barrier gives up after limit_cycles SM clock cycles: the block ORs the timeout bit (4)
+ * into *status_dev (a device int) and returns without writing dst_dev, as the evaluation
+ * kernels do, which turn that bit into NNFFT_ETIMEOUT.  Synchronous on the legacy default
+ * stream.  EINVAL for invalid arguments.
+ */
+int nnfft_selftest_bulk_copy(const float *src_dev, float *dst_dev, int n, int arm_only,
+                             int64_t limit_cycles, int *status_dev);
+
 /* nnfft_launch_count: number of kernels this library has launched in the process. */
 int64_t nnfft_launch_count(void);
 
@@ -537,6 +559,13 @@ int nnfft_server_create(nnfft_server_t *out, int64_t mem_budget_bytes, int slots
 int nnfft_server_submit(nnfft_server_t s, const nnfft_request *r, int64_t *id);
 /* Block until request id is done; returns its status (the id is then released). */
 int nnfft_server_wait(nnfft_server_t s, int64_t id, double *latency_ms);
+/* nnfft_server_wait that also returns where the request's work ran on the device: four
+ * times in ms since the server was created, from CUDA events on its slot stream, before its
+ * uploads, before its first kernel, after its last kernel and after its download (device_ms
+ * may be NULL; -1 for a failed request).  Requests whose [first, last] intervals intersect
+ * had work on the device at the same time (copies of one beside kernels of the other, or
+ * kernels of both). */
+int nnfft_server_wait_device(nnfft_server_t s, int64_t id, double *latency_ms, double *device_ms);
 /* Latency percentiles and throughput of the requests completed so far (reset: restart). */
 int nnfft_server_stats(nnfft_server_t s, nnfft_server_report *out, int reset);
 /* Finish the queued requests, stop the loop and free everything. */

@@ -25,6 +25,7 @@ constexpr int FFT_MAX_STAGES = 12;
 // Kernel status bits (OR-ed into the plan's device status word).
 constexpr int STATUS_RANGE = 1;      // node outside [-1/2, 1/2] or NaN
 constexpr int STATUS_INTERNAL = 2;   // inconsistent cell assignment (should not happen)
+constexpr int STATUS_TIMEOUT = 4;    // a bounded device-side wait gave up
 
 // Kernels launched by this library (nnfft_launch_count); bumped by every launch wrapper.
 void count_launches(int n);
@@ -177,10 +178,12 @@ size_t radix_sort_hist_len(int ntiles, int ninst);
 // totals in hist (radix_sort_hist_len ints).  tiles: a batch's instance-aligned tiles
 // (each point takes its instance's binning, keys offset by the instance's first cell), or
 // nullptr for one instance with binning `one` and ntiles = ceil(n / SORT_TILE).
+// two_stage: count the high digit (key >> local_sort_low_bits) for radix_sort_cells_local
+// instead of the low digit of the LSD passes.
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
                                const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
                                int yfmt, int key_bits, int ybytes, int *hist, int *status,
-                               cudaStream_t s);
+                               cudaStream_t s, bool two_stage = false);
 // Digits of the radix sort of key_bits-bit keys, ceil(key_bits / 8) passes.  A tile of
 // SORT_TILE keys leaves each digit's keys as one run of consecutive addresses, so a narrower
 // digit gives longer runs.  Where the coordinates travel with the keys in every pass
@@ -218,6 +221,28 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
                              int *hist, const SortTiles *tiles, int ntiles, int n, int key_bits,
                              const void *y_user, void *ys, void *y_tmp, int ybytes, cudaStream_t s,
                              uint32_t **keys_sorted, int **vals_sorted);
+// Two-stage sort of 9- to 16-bit cell keys: one stable scatter pass by
+// the high 8-bit digit (counts from launch_node_keys_y with two_stage), then one block per
+// bucket of 2^(key_bits - 8) cells sorts its bucket by the low bits in shared memory and
+// writes the cell offsets and work items of launch_cells_and_items (the scan-based item
+// builder follows, returning at once when every cell fits one item).  The same order as
+// radix_sort_cells; the sorted keys and values end in keys / vals, the coordinates in ys
+// (4-byte ones through y_tmp, 8-byte ones gathered from y_user).  prepare_local_sort
+// sets the kernels' shared-memory limits (once per device, outside stream capture).
+inline bool local_sort_ok(int key_bits) { return key_bits >= 9 && key_bits <= 16; }
+inline int local_sort_low_bits(int key_bits) { return key_bits - 8; }
+cudaError_t prepare_local_sort();
+// Batches (tiles != nullptr, their instance-aligned tiles): keys sorted within each
+// instance by the local cell, blk_first[i] = first second-stage block of instance i
+// (nblocks in all); per_cell_first must be false (the scan-based items follow).
+cudaError_t radix_sort_cells_local(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                                   int *hist, const SortTiles *tiles, int ntiles,
+                                   const int *blk_first, int nblocks, int n, int ncell,
+                                   int key_bits, const void *y_user,
+                                   void *ys, void *y_tmp, int ybytes, int cap, bool per_cell_first,
+                                   int *cell_off, int *item_off, int *item_cell, int *item_pb,
+                                   int *item_pe, int *nitems, int *scratch, cudaStream_t s,
+                                   uint32_t **keys_sorted, int **vals_sorted);
 // Cell offsets (cell_off[c] = first sorted point of cell c, cell_off[ncell] = n) and work
 // items (at most cap sorted points of one cell each, ITEM_CAP_MIN <= cap <= ITEM_CAP;
 // item_off[c] = first item of cell c, *nitems = total) from the sorted keys.  With
@@ -303,6 +328,9 @@ cudaError_t launch_complex_to_real(const void *in, int n, Real *out, cudaStream_
 cudaError_t launch_cc_extend(long long n, void *x, cudaStream_t s);
 cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half_z,
                              double *neg_half_z, cudaStream_t s);
+// Self-test of the bulk (TMA) copy helpers (see nnfft_selftest_bulk_copy).
+cudaError_t selftest_bulk_copy(const float *src, float *dst, int n, int arm_only,
+                               long long limit, int *status, cudaStream_t s);
 // Sharded transform: copy the n centered positions l in I_n of an N2 grid buffer (element
 // format fmt: 0 float2, 1 double2, 2 double-float float4; p at p mod N2) to out[l + n/2]
 // (complex64 for fmt 0, complex128 otherwise), or back (import writes every buffer

@@ -4,6 +4,7 @@
 // computation (Algorithm 5.4) around a length-2n FFT; and the grid export / import
 // of the sharded transform (Algorithm 2.2 split at its grid).
 #include "internal.h"
+#include "tma.cuh"
 
 namespace nnfft {
 
@@ -130,6 +131,28 @@ __global__ void k_grid_import(const typename GridElem<FMT>::X *__restrict__ in, 
     buf[q] = l < N2 ? GridElem<FMT>::in(in[l + n / 2]) : GridElem<FMT>::zero();
 }
 
+// Self-test of the bulk-copy helpers: one block stages n floats (n % 4 == 0, n <= 4096)
+// in shared memory with one bulk copy and writes them back to dst.  arm_only announces
+// the bytes on the barrier but issues no copy, so the bounded wait runs out: the block
+// sets STATUS_TIMEOUT in *status, waits once more and returns without writing dst.
+__global__ void k_selftest_bulk_copy(const float *__restrict__ src, float *__restrict__ dst,
+                                     int n, int arm_only, long long limit, int *status) {
+    __shared__ __align__(128) float buf[4096];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        tma::bar_init(&bar);
+        tma::bar_expect(&bar, (unsigned)n * 4u);
+        if (!arm_only) tma::copy_g2s(buf, src, (unsigned)n * 4u, &bar);
+    }
+    __syncthreads();
+    if (!tma::bar_wait(&bar, 0, limit)) {
+        if (threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+        tma::bar_wait(&bar, 0, limit);
+        return;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = buf[i];
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 std::atomic<long long> g_launches{0};
@@ -170,6 +193,14 @@ cudaError_t launch_cc_finish(long long n, const void *X, double *w, double *half
                              double *neg_half_z, cudaStream_t s) {
     k_cc_finish<<<cdiv(n + 1, 256), 256, 0, s>>>(n, static_cast<const double2 *>(X), w, half_z,
                                                   neg_half_z);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t selftest_bulk_copy(const float *src, float *dst, int n, int arm_only,
+                               long long limit, int *status, cudaStream_t s) {
+    if (n <= 0 || n > 4096 || (n & 3) || limit <= 0) return cudaErrorInvalidValue;
+    k_selftest_bulk_copy<<<1, 256, 0, s>>>(src, dst, n, arm_only, limit, status);
     count_launches(1);
     return cudaGetLastError();
 }

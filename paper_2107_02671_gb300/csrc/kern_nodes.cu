@@ -113,13 +113,15 @@ __device__ __forceinline__ TileSpan tile_span(const SortTiles &st, int t, int n)
 // Step 0 for one node side in a single pass over the nodes: validate each node,
 // compute its cell key (cell_base + c - c_lo) and local coordinate y = 2 (u - c) - 1
 // (c = floor(u), u = node * scale, node_fixed), store y (caller order) in the plan's
-// format, and count the digits of the first radix pass (of c - c_lo, the local cell) for
-// this block's tile (the tiles of the sort passes), into the per-tile counts and the
-// digit totals of the tile's instance.
+// format, and count the digits of the first radix pass (of c - c_lo, the local cell: its
+// low digit, or its high digit (c - c_lo) >> shift0 for the two-stage sort) for this
+// block's tile (the tiles of the sort passes), into the per-tile counts and the digit
+// totals of the tile's instance.
 __global__ void __launch_bounds__(SORT_THREADS)
 k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles st,
               uint32_t *__restrict__ keys, void *__restrict__ yout, int yfmt, int ntiles,
-              unsigned mask0, int *__restrict__ hist, int *__restrict__ tot, int *status) {
+              int shift0, unsigned mask0, int *__restrict__ hist, int *__restrict__ tot,
+              int *status) {
     __shared__ int h[256];
     h[threadIdx.x] = 0;
     const TileSpan sp = tile_span(st, blockIdx.x, n);
@@ -150,7 +152,7 @@ k_node_keys_y(const double *__restrict__ nodes, int n, NodeInst one, SortTiles s
         }
         keys[i] = (uint32_t)(ic + I.cell_base);
         store_y(yout, yfmt, i, Y);
-        atomicAdd(&h[ic & mask0], 1);
+        atomicAdd(&h[(ic >> shift0) & mask0], 1);
     }
     __syncthreads();
     hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -377,6 +379,297 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         vout[pos] = v;
         if constexpr (CARRY) yout[pos] = sy[i];
         else if constexpr (!std::is_void<Y>::value) yout[pos] = yin[v];
+    }
+}
+
+// Second stage of the two-stage sort (see radix_sort_cells_local): the keys arrive
+// stably partitioned by their high digit key >> lbits (bucket b is the position range
+// [hist[b ntiles], hist[(b + 1) ntiles]) of the first pass's scanned digit-major counts),
+// in input order within each bucket, and are sorted stably by the low lbits bits (the
+// cell within the bucket, NB = 2^lbits bins).  A block takes one range of a bucket:
+//   * a single instance splits every bucket into ranges of LOCAL_RANGE keys (clustered
+//     nodes make some buckets many times larger than others), each block finding its
+//     bucket and range from the bucket sizes;
+//   * a batch (st.inst != nullptr) takes one block per (instance, bucket), whole buckets.
+// The block counts the bucket's keys per bin (their first positions are the cell offsets
+// and, for dense plans (per_cell_first), one work item per cell; a cell above cap sets
+// *overflow and the scan-based item builder runs next; the bucket's first block writes
+// them) and the keys of its bucket before its range per bin (run[]).  Then its range in
+// chunks: ranks within the chunk as in k_sort_scatter (per-warp counters, ballots of the
+// digit bits), the chunk reordered by bin in shared memory and written out bin run by
+// bin run (coalesced) after the same bin's earlier keys.  So the result is the stable
+// sort by cell, the same order as the LSD passes.  The coordinates: 4-byte ones are
+// carried (yin in first-pass order), 8-byte ones gathered from the caller-order array
+// (yin[value]).
+// Blocks of 256 threads (several per SM, so that one block's barrier waits overlap another's
+// work); a single instance's buckets are split into ranges of LOCAL_RANGE keys.
+constexpr int LOCAL_ROUNDS = 4;
+constexpr int LOCAL_RANGE = 2048;
+
+__host__ __device__ constexpr size_t local_sort_smem(int threads, int lbits, int ybytes) {
+    return sizeof(int) * ((size_t)(threads / 32) * (1u << lbits) + 5u * (1u << lbits) + 32u) +
+           (size_t)threads * LOCAL_ROUNDS * (sizeof(uint32_t) + sizeof(int) + (ybytes == 4 ? 4u : 0u));
+}
+
+// A batch (st.inst != nullptr) sorts each instance by its local cell: block -> (instance
+// i, bucket b) through blk_first, the bucket's range from the instance's first tile's
+// scanned counts, bins of key - cell_base_i; ncell is then the side's total cell count.
+template <int LOCAL_THREADS, typename Y, bool CARRY>
+__global__ void __launch_bounds__(LOCAL_THREADS)
+k_sort_local(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+             const Y *__restrict__ yin, uint32_t *__restrict__ kout, int *__restrict__ vout,
+             Y *__restrict__ yout, int n, int lbits, int ncell, const int *__restrict__ hist,
+             int ntiles, SortTiles st, const int *__restrict__ blk_first, int cap,
+             int per_cell_first, int *__restrict__ off,
+             int *__restrict__ item_off, int *__restrict__ item_cell, int *__restrict__ item_pb,
+             int *__restrict__ item_pe, int *__restrict__ nitems, int *__restrict__ overflow) {
+    constexpr int LOCAL_CHUNK = LOCAL_THREADS * LOCAL_ROUNDS;
+    constexpr int LOCAL_WARPS = LOCAL_THREADS / 32;
+    extern __shared__ __align__(16) int smem_i[];
+    const int NB = 1 << lbits;
+    const unsigned lmask = (unsigned)NB - 1u;
+    int *cnt = smem_i;                           // [LOCAL_WARPS][NB] per-warp counts, then offsets
+    int *btot = cnt + LOCAL_WARPS * NB;          // [NB] keys of each bin in the bucket
+    int *bstart = btot + NB;                     // [NB] first bucket position of each bin
+    int *run = bstart + NB;                      // [NB] keys of each bin in earlier chunks
+    int *ctot = run + NB;                        // [NB] keys of each bin in this chunk
+    int *cst = ctot + NB;                        // [NB] first chunk slot of each bin
+    int *wtot = cst + NB;                        // [32]
+    uint32_t *skey = reinterpret_cast<uint32_t *>(wtot + 32);
+    int *sval = reinterpret_cast<int *>(skey + LOCAL_CHUNK);
+    Y *sy = reinterpret_cast<Y *>(sval + LOCAL_CHUNK);   // CARRY only
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int b = blockIdx.x, t0 = 0, ncell_i = ncell, j = 0;
+    unsigned cb = 0;
+    int s0, s1, r0, r1;
+    if (st.inst != nullptr) {
+        const int inst = block_instance(blk_first, st.ninst, blockIdx.x);
+        b = blockIdx.x - blk_first[inst];
+        t0 = st.inst_tile0[inst];
+        const NodeInst I = st.tab[inst];
+        cb = (unsigned)I.cell_base;
+        ncell_i = I.ncell;
+        const int p_beg = (int)st.pt_off[inst], p_end = (int)st.pt_off[inst + 1];
+        const int nb_i = ((ncell_i - 1) >> lbits) + 1;
+        s0 = s1 = p_beg;                         // an instance without points: empty buckets
+        if (p_end > p_beg) {
+            s0 = hist[(long long)b * ntiles + t0];
+            s1 = b + 1 < nb_i ? hist[(long long)(b + 1) * ntiles + t0] : p_end;
+        }
+        r0 = s0;
+        r1 = s1;
+    } else {
+        // bucket i holds [start(i), start(i + 1)) and takes max(1, ceil(size / range)) blocks
+        __shared__ int bmap[257];
+        const int nbk = ((ncell - 1) >> lbits) + 1;   // <= 256
+        if (w == 0) {
+            int carry = 0;
+            for (int i0 = 0; i0 < nbk; i0 += 32) {
+                const int i = i0 + lane;
+                int v = 0;
+                if (i < nbk) {
+                    const int a = hist[(long long)i * ntiles];
+                    const int e = i + 1 < nbk ? hist[(long long)(i + 1) * ntiles] : n;
+                    v = max(1, (e - a + LOCAL_RANGE - 1) / LOCAL_RANGE);
+                }
+                int incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += u;
+                }
+                if (i < nbk) bmap[i] = carry + incl - v;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            if (lane == 0) bmap[nbk] = carry;
+        }
+        __syncthreads();
+        if ((int)blockIdx.x >= bmap[nbk]) return;      // block-uniform: beyond the last range
+        int lo = 0, hi = nbk;                           // largest i with bmap[i] <= block
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (bmap[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+        }
+        b = lo;
+        j = (int)blockIdx.x - bmap[b];
+        s0 = hist[(long long)b * ntiles];
+        s1 = b + 1 < nbk ? hist[(long long)(b + 1) * ntiles] : n;
+        r0 = min(s0 + j * LOCAL_RANGE, s1);
+        r1 = min(r0 + LOCAL_RANGE, s1);
+    }
+    for (int i = tid; i < NB; i += LOCAL_THREADS) {
+        btot[i] = 0;
+        run[i] = 0;
+    }
+    __syncthreads();
+    for (int i0 = s0; i0 < s1; i0 += 4 * LOCAL_THREADS) {
+        uint32_t kk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {            // the loads first
+            const int i = i0 + q * LOCAL_THREADS + tid;
+            kk[q] = i < s1 ? kin[i] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + q * LOCAL_THREADS + tid;
+            if (i >= s1) break;
+            const unsigned d = (kk[q] - cb) & lmask;
+            atomicAdd(&btot[d], 1);
+            if (i < r0) atomicAdd(&run[d], 1);   // the bucket's keys before this range
+        }
+    }
+    __syncthreads();
+    if (w == 0) {                                // exclusive scan of the bin sizes
+        int carry = 0;
+        for (int i0 = 0; i0 < NB; i0 += 32) {
+            const int i = i0 + lane;
+            const int v = i < NB ? btot[i] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (i < NB) bstart[i] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    for (int d = tid; d < NB && j == 0; d += LOCAL_THREADS) {   // cell offsets (and items)
+        const int cl = (b << lbits) + d;
+        if (cl >= ncell_i) continue;
+        const int c = (int)cb + cl;
+        const int pb = s0 + bstart[d];
+        off[c] = pb;
+        if (per_cell_first) {
+            item_off[c] = c;
+            item_cell[c] = c;
+            item_pb[c] = pb;
+            item_pe[c] = pb + btot[d];
+            if (btot[d] > cap) *overflow = 1;
+        }
+    }
+    const bool last = st.inst != nullptr ? blockIdx.x == gridDim.x - 1
+                                         : (b == ((ncell - 1) >> lbits) && j == 0);
+    if (last && tid == 0) {
+        off[ncell] = n;
+        if (per_cell_first) {
+            item_off[ncell] = ncell;
+            *nitems = ncell;
+        }
+    }
+    const unsigned lt = lanemask_lt();
+    for (int c0 = r0; c0 < r1; c0 += LOCAL_CHUNK) {
+        const int cend = min(c0 + LOCAL_CHUNK, r1);
+        for (int i = lane; i < NB; i += 32) cnt[w * NB + i] = 0;
+        __syncwarp();
+        const int base = c0 + w * (32 * LOCAL_ROUNDS);
+        uint32_t key[LOCAL_ROUNDS];
+        int val[LOCAL_ROUNDS], rank[LOCAL_ROUNDS];
+        Y yv[CARRY ? LOCAL_ROUNDS : 1];
+#pragma unroll
+        for (int r = 0; r < LOCAL_ROUNDS; ++r) {
+            const int idx = base + r * 32 + lane;
+            const bool valid = idx < cend;
+            key[r] = valid ? kin[idx] : 0u;
+            val[r] = valid ? vin[idx] : 0;
+            if constexpr (CARRY) yv[r] = valid ? yin[idx] : Y(0);
+        }
+#pragma unroll
+        for (int r = 0; r < LOCAL_ROUNDS; ++r) {
+            const int idx = base + r * 32 + lane;
+            const bool valid = idx < cend;
+            const unsigned d = valid ? ((key[r] - cb) & lmask) : (unsigned)NB;   // NB: invalid
+            unsigned peers = 0xffffffffu;
+#pragma unroll
+            for (int bt = 0; bt < 9; ++bt) {         // the ballots of the bits of d
+                if (bt > lbits) break;
+                const unsigned bit = (d >> bt) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            const int before = valid ? cnt[w * NB + d] : 0;
+            __syncwarp();
+            if (valid && (peers & lt) == 0) cnt[w * NB + d] += __popc(peers);
+            __syncwarp();
+            rank[r] = before + __popc(peers & lt);
+        }
+        __syncthreads();
+        {   // one block-wide exclusive scan of the counters in (bin, warp) order: afterwards
+            // cnt[w NB + d] is the chunk slot of warp w's first key of bin d
+            const int total = NB * LOCAL_WARPS;
+            const int per = (total + LOCAL_THREADS - 1) / LOCAL_THREADS;   // <= 8
+            const int e0 = tid * per;
+            int v[8];
+            int sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = e0 + q;                                      // e = d * WARPS + w
+                v[q] = (q < per && e < total) ? cnt[(e % LOCAL_WARPS) * NB + e / LOCAL_WARPS] : 0;
+                sum += v[q];
+            }
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            if (lane == 31) wtot[w] = incl;
+            __syncthreads();
+            if (w == 0) {
+                const int x = lane < LOCAL_WARPS ? wtot[lane] : 0;
+                int xi = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int u = __shfl_up_sync(0xffffffffu, xi, o);
+                    if (lane >= o) xi += u;
+                }
+                if (lane < LOCAL_WARPS) wtot[lane] = xi - x;
+            }
+            __syncthreads();
+            int run_e = wtot[w] + incl - sum;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int e = e0 + q;
+                if (q < per && e < total) {
+                    cnt[(e % LOCAL_WARPS) * NB + e / LOCAL_WARPS] = run_e;
+                    run_e += v[q];
+                }
+            }
+        }
+        __syncthreads();
+        for (int d = tid; d < NB; d += LOCAL_THREADS) {   // chunk start and size of each bin
+            const int a = cnt[d];                           // warp 0's slot = the bin's start
+            cst[d] = a;
+            ctot[d] = (d + 1 < NB ? cnt[d + 1] : (cend - c0)) - a;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < LOCAL_ROUNDS; ++r) {
+            const int idx = base + r * 32 + lane;
+            if (idx < cend) {
+                const unsigned d = (key[r] - cb) & lmask;
+                const int loc = cnt[w * NB + d] + rank[r];
+                skey[loc] = key[r];
+                sval[loc] = val[r];
+                if constexpr (CARRY) sy[loc] = yv[r];
+            }
+        }
+        __syncthreads();
+        const int tn = cend - c0;
+        for (int i = tid; i < tn; i += LOCAL_THREADS) {
+            const uint32_t k = skey[i];
+            const int v = sval[i];
+            const unsigned d = (k - cb) & lmask;
+            const int pos = s0 + bstart[d] + run[d] + (i - cst[d]);
+            kout[pos] = k;
+            vout[pos] = v;
+            if constexpr (CARRY) yout[pos] = sy[i];
+            else yout[pos] = yin[v];
+        }
+        __syncthreads();
+        for (int d = tid; d < NB; d += LOCAL_THREADS) run[d] += ctot[d];
+        __syncthreads();
     }
 }
 
@@ -668,16 +961,17 @@ SortTiles single_tiles() {
 cudaError_t launch_node_keys_y(const double *nodes, int n, const NodeInst &one,
                                const SortTiles *tiles, int ntiles, uint32_t *keys, void *y_user,
                                int yfmt, int key_bits, int ybytes, int *hist, int *status,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool two_stage) {
     if (n <= 0) return cudaSuccess;
     const SortTiles st = tiles ? *tiles : single_tiles();
     if (!tiles) ntiles = cdiv(n, SORT_TILE);
     int *tot = hist + 256LL * ntiles;
     cudaError_t e = cudaMemsetAsync(tot, 0, 256 * sizeof(int) * (size_t)st.ninst, s);
     if (e != cudaSuccess) return e;
+    const int shift0 = two_stage ? local_sort_low_bits(key_bits) : 0;
+    const unsigned mask0 = two_stage ? 255u : radix_digit(key_bits, 0, radix_wide_first(ybytes)).mask;
     k_node_keys_y<<<ntiles, SORT_THREADS, 0, s>>>(nodes, n, one, st, keys, y_user, yfmt, ntiles,
-                                                  radix_digit(key_bits, 0, radix_wide_first(ybytes)).mask, hist, tot,
-                                                  status);
+                                                  shift0, mask0, hist, tot, status);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -784,6 +1078,105 @@ cudaError_t radix_sort_cells(uint32_t *keys, int *vals, uint32_t *keys_alt, int 
     *keys_sorted = ka;
     *vals_sorted = va;
     return cudaSuccess;
+}
+
+namespace {
+template <int T, typename Y, bool CARRY>
+void local_attr(int ybytes) {
+    cudaFuncSetAttribute(k_sort_local<T, Y, CARRY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)local_sort_smem(T, 8, ybytes));
+}
+
+template <int T>
+void local_launch(int nblocks, size_t sm, cudaStream_t s, int ybytes, const uint32_t *kin,
+                  const int *vin, const void *y_carried, const void *y_user, uint32_t *kout,
+                  int *vout, void *ys, int n, int lbits, int ncell, const int *hist, int ntiles,
+                  const SortTiles &st, const int *blk_first, int cap, int per_cell_first,
+                  int *off, int *item_off, int *item_cell, int *item_pb, int *item_pe,
+                  int *nitems, int *overflow) {
+    if (ybytes == 4)
+        k_sort_local<T, unsigned, true><<<nblocks, T, sm, s>>>(
+            kin, vin, static_cast<const unsigned *>(y_carried), kout, vout,
+            static_cast<unsigned *>(ys), n, lbits, ncell, hist, ntiles, st, blk_first, cap,
+            per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
+    else
+        k_sort_local<T, unsigned long long, false><<<nblocks, T, sm, s>>>(
+            kin, vin, static_cast<const unsigned long long *>(y_user), kout, vout,
+            static_cast<unsigned long long *>(ys), n, lbits, ncell, hist, ntiles, st, blk_first,
+            cap, per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
+}
+}  // namespace
+
+cudaError_t prepare_local_sort() {
+    local_attr<256, unsigned, true>(4);
+    local_attr<256, unsigned long long, false>(8);
+    return cudaGetLastError();
+}
+
+cudaError_t radix_sort_cells_local(uint32_t *keys, int *vals, uint32_t *keys_alt, int *vals_alt,
+                                   int *hist, const SortTiles *tiles, int ntiles,
+                                   const int *blk_first, int nblocks, int n, int ncell,
+                                   int key_bits, const void *y_user,
+                                   void *ys, void *y_tmp, int ybytes, int cap, bool per_cell_first,
+                                   int *cell_off, int *item_off, int *item_cell, int *item_pb,
+                                   int *item_pe, int *nitems, int *scratch, cudaStream_t s,
+                                   uint32_t **keys_sorted, int **vals_sorted) {
+    if (cap < ITEM_CAP_MIN || cap > ITEM_CAP || !local_sort_ok(key_bits) || n < 2 ||
+        (ybytes != 4 && ybytes != 8) || (tiles && (per_cell_first || !blk_first || nblocks < 1)) ||
+        (!tiles && ncell > (1 << key_bits)))
+        return cudaErrorInvalidValue;
+    const SortTiles st = tiles ? *tiles : single_tiles();
+    const int lbits = local_sort_low_bits(key_bits);
+    if (!tiles) {           // an upper bound of sum over buckets of max(1, ceil(size / range))
+        ntiles = cdiv(n, SORT_TILE);
+        nblocks = ((ncell - 1) >> lbits) + 1 + cdiv(n, LOCAL_RANGE);
+    }
+    int *tot = hist + 256LL * ntiles;
+    // first stage: stable scatter by the high digit (counts from k_node_keys_y); 4-byte
+    // coordinates move with their keys into y_tmp
+    if (tiles)
+        k_seg_scan<<<cdiv((long long)st.ninst * 256, 8), 256, 0, s>>>(hist, ntiles, tot, st);
+    else
+        k_sort_scan_rows<<<256, 256, 0, s>>>(hist, ntiles, tot);
+    scatter_dispatch<true>(ybytes == 4 ? 4 : 0, ntiles, s, keys, vals, keys_alt, vals_alt, n,
+                           lbits, 255u, st, hist, y_user, y_tmp);
+    count_launches(2);
+    int *overflow = nullptr;
+    if (per_cell_first) {
+        overflow = scratch + build_items_scratch_len(ncell) - 1;
+        cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
+    }
+    // second stage: each bucket sorted by its low bits, cell offsets and items
+    if (tiles)
+        local_launch<256>(nblocks, local_sort_smem(256, lbits, ybytes), s, ybytes, keys_alt,
+                          vals_alt, y_tmp, y_user, keys, vals, ys, n, lbits, ncell, hist, ntiles,
+                          st, blk_first, cap, 0, cell_off, item_off, item_cell, item_pb, item_pe,
+                          nitems, overflow);
+    else
+        local_launch<256>(nblocks, local_sort_smem(256, lbits, ybytes), s, ybytes, keys_alt,
+                          vals_alt, y_tmp, y_user, keys, vals, ys, n, lbits, ncell, hist, ntiles,
+                          st, blk_first, cap, per_cell_first ? 1 : 0, cell_off, item_off,
+                          item_cell, item_pb, item_pe, nitems, overflow);
+    count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // cells above cap (or sparse plans): items by a scan of ceil(count / cap) over the cells
+    if (ncell <= ITEMS_ONE_BLOCK_MAX) {
+        k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
+                                         nitems, cap, overflow);
+        count_launches(1);
+    } else {
+        const int nb = cdiv(ncell, 1024);
+        k_item_block_sums<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch, cap, overflow);
+        k_scan_exclusive<<<1, 1024, 0, s>>>(scratch, scratch, nb, overflow);
+        k_item_fill_blocks<<<nb, 1024, 0, s>>>(cell_off, ncell, scratch, nb, item_off, item_cell,
+                                               item_pb, item_pe, nitems, cap, overflow);
+        count_launches(3);
+    }
+    *keys_sorted = keys;
+    *vals_sorted = vals;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell, int cap,

@@ -16,6 +16,7 @@
 // accumulate or evaluate one Chebyshev series per point, and the O(m D) tap
 // algebra happens once per cell on the small grid.
 #include "internal.h"
+#include "tma.cuh"
 
 namespace nnfft {
 
@@ -580,6 +581,58 @@ k_eval_flat(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict_
     out[j] = mk2<Real>(sr, si);
 }
 
+// The flat evaluation with the block's cells [c0, c1] staged in shared memory by one bulk
+// (TMA) copy of Q[c0*D .. (c1+1)*D) (see k_eval_df_flat_tma); blocks spanning more than
+// TMA_MAX_CELLS cells read Q from global memory.
+template <typename Real, int D>
+__global__ void __launch_bounds__(256)
+k_eval_flat_tma(SideK<Real> S, const C2<Real> *__restrict__ Q, C2<Real> *__restrict__ out) {
+    __shared__ __align__(128) C2<Real> qs[TMA_MAX_CELLS * D];
+    __shared__ __align__(8) uint64_t bar;
+    const int p0 = blockIdx.x * blockDim.x;
+    const int p = p0 + threadIdx.x;
+    const int plast = min(p0 + (int)blockDim.x, S.M) - 1;
+    const int c0 = (int)S.keys[p0], c1 = (int)S.keys[plast];
+    const int nc = c1 - c0 + 1;
+    const bool staged = nc <= TMA_MAX_CELLS;          // block-uniform
+    if (staged) {
+        if (threadIdx.x == 0) {
+            tma::bar_init(&bar);
+            const unsigned bytes = (unsigned)nc * D * (unsigned)sizeof(C2<Real>);
+            tma::bar_expect(&bar, bytes);
+            tma::copy_g2s(qs, Q + (long long)c0 * D, bytes, &bar);
+        }
+        __syncthreads();
+    }
+    int c = 0, j = -1;
+    Real y = Real(0);
+    if (p < S.M) {
+        c = (int)S.keys[p];
+        y = S.ys[p];
+        j = S.perm[p];
+    }
+    const C2<Real> *q = Q + (long long)c * D;
+    if (staged) {
+        if (!tma::bar_wait(&bar, 0, tma::WAIT_LIMIT_CYCLES)) {
+            if (threadIdx.x == 0) atomicOr(S.status, STATUS_TIMEOUT);
+            tma::bar_wait(&bar, 0, tma::WAIT_LIMIT_CYCLES);
+            return;
+        }
+        q = qs + (c - c0) * D;
+    }
+    if (p >= S.M) return;
+    Real T[D];
+    cheb<Real, D>(y, T);
+    Real sr = Real(0), si = Real(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const C2<Real> qd = q[d];
+        sr = fma(qd.x, T[d], sr);
+        si = fma(qd.y, T[d], si);
+    }
+    out[j] = mk2<Real>(sr, si);
+}
+
 // Point evaluation of small work items: one thread per item.
 template <typename Real, int D>
 __global__ void __launch_bounds__(256)
@@ -709,6 +762,12 @@ cudaError_t launch_eval(const SideK<Real> &S, const void *Q, void *out, int lane
     if (lanes == EVAL_FLAT) {                       // covers every point: no small-item pass
         if (S.M <= 0) return cudaSuccess;
         NNFFT_DISPATCH_D(S.D, (k_eval_flat<Real, DD><<<cdiv(S.M, 256), 256, 0, s>>>(S, q, o)));
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    if (lanes == EVAL_FLAT_TMA) {
+        if (S.M <= 0) return cudaSuccess;
+        NNFFT_DISPATCH_D(S.D, (k_eval_flat_tma<Real, DD><<<cdiv(S.M, 256), 256, 0, s>>>(S, q, o)));
         count_launches(1);
         return cudaGetLastError();
     }

@@ -16,6 +16,7 @@
 // double-float complex values (float4) for the double-float grid stage.
 #include "df.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace nnfft {
 
@@ -359,6 +360,69 @@ k_eval_df_flat(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__
     out[j] = eval_point<B, F>(yv, qr, qi, fr, fi);
 }
 
+// The flat evaluation with the block's cells staged by the Tensor Memory Accelerator.
+// The block's 256 sorted points lie in the cells [c0, c1] (keys ascending); their window
+// sums Q4[c0*D .. (c1+1)*D) are one contiguous run, which thread 0 copies into shared
+// memory with one bulk copy while every thread loads its own point.  A block spanning more
+// than TMA_MAX_CELLS cells (sparse plans) reads Q4 from global memory instead.  A copy
+// that does not complete within the wait limit sets STATUS_TIMEOUT and the block returns
+// (after a second bounded wait so that no copy is left writing its shared memory).
+template <int D>
+__global__ void __launch_bounds__(256)
+k_eval_df_flat_tma(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restrict__ Q4,
+                   double2 *__restrict__ out) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    __shared__ __align__(128) float4 qs[TMA_MAX_CELLS * D];
+    __shared__ __align__(8) uint64_t bar;
+    const int p0 = blockIdx.x * blockDim.x;
+    const int p = p0 + threadIdx.x;
+    const int plast = min(p0 + (int)blockDim.x, S.M) - 1;
+    const int c0 = (int)S.keys[p0], c1 = (int)S.keys[plast];
+    const int nc = c1 - c0 + 1;
+    const bool staged = nc <= TMA_MAX_CELLS;          // block-uniform
+    if (staged) {
+        if (threadIdx.x == 0) {
+            tma::bar_init(&bar);
+            const unsigned bytes = (unsigned)nc * D * (unsigned)sizeof(float4);
+            tma::bar_expect(&bar, bytes);
+            tma::copy_g2s(qs, Q4 + (long long)c0 * D, bytes, &bar);
+        }
+        __syncthreads();
+    }
+    int c = 0, j = -1;
+    float2 yv = make_float2(0.f, 0.f);
+    if (p < S.M) {
+        c = (int)S.keys[p];
+        yv = ys2[p];
+        j = S.perm[p];
+    }
+    const float4 *q4 = Q4 + (long long)c * D;
+    if (staged) {
+        if (!tma::bar_wait(&bar, 0, tma::WAIT_LIMIT_CYCLES)) {
+            if (threadIdx.x == 0) atomicOr(S.status, STATUS_TIMEOUT);
+            tma::bar_wait(&bar, 0, tma::WAIT_LIMIT_CYCLES);
+            return;
+        }
+        q4 = qs + (c - c0) * D;
+    }
+    if (p >= S.M) return;
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float4 q = q4[d];
+        if (d < B) {
+            qr[d < B ? d : 0] = mk(q.x, q.y);
+            qi[d < B ? d : 0] = mk(q.z, q.w);
+        } else {
+            fr[d >= B ? d - B : 0] = q.x;
+            fi[d >= B ? d - B : 0] = q.z;
+        }
+    }
+    out[j] = eval_point<B, F>(yv, qr, qi, fr, fi);
+}
+
 // ---------------------------------------------------------------------------------
 // Team kernels: DTEAM = 8 lanes per work item, four items per warp (sparse cells).
 // Moments use the slot layout of the half-warp kernel; three exchange steps over slot
@@ -423,6 +487,99 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
 #pragma unroll
         for (int k = 0; k < CH; ++k)
             if (jv[k] >= 0) moments_point<B, F>(yv[k], vv2[k], ar, ai, br, bi);
+    }
+    df vd[16];
+    float vf[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
+#pragma unroll
+    for (int d = 0; d < B; ++d) {
+        vd[d] = norm(ar[d]);
+        vd[8 + d] = norm(ai[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < F; ++d) {
+        vf[d] = br[d];
+        vf[8 + d] = bi[d];
+    }
+    rs_mixed_team<8, 4>(vd, vf, sub);
+    rs_mixed_team<4, 2>(vd, vf, sub);
+    rs_mixed_team<2, 1>(vd, vf, sub);
+    if (item < 0) return;
+    float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int j = 2 * sub + t, deg = j & 7, part = j >> 3;   // part 0: real, 1: imaginary
+        if (deg < B) P2[2 * deg + part] = make_float2(vd[t].h, vd[t].l);
+        if (deg < F) P2[2 * (B + deg) + part] = make_float2(vf[t], 0.f);
+    }
+}
+
+// The same per-item moments as k_moments_df_team with the point loads software-pipelined
+// across chunks: the values of chunk k+1 (gathered through the permutation) and the
+// coordinates and permutation entries of chunk k+2 are in flight while chunk k is
+// accumulated, so the dependent loads (permutation, then value) do not stall the lane
+// (about 40 more registers; two blocks of 256 per SM).
+template <int D, int CH>
+__global__ void __launch_bounds__(256, 2)
+k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
+                     const double2 *__restrict__ vals, float4 *__restrict__ P4) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    static_assert(B <= 8 && F <= 8, "the slot layout holds at most 8 degrees of each kind");
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int item = big_item(S, gt / DTEAM);
+    const int sub = threadIdx.x & (DTEAM - 1);
+    int pb = 0, pe = 0;
+    if (item >= 0) {                                 // every lane stays for the exchanges
+        pb = S.item_pb[item];
+        pe = S.item_pe[item];
+    }
+    df ar[B], ai[B];
+    float br[F], bi[F];
+#pragma unroll
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+#pragma unroll
+    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
+    constexpr int STEP = DTEAM * CH;
+    float2 yB[CH], yA[CH];
+    int jB[CH], jA[CH];
+    double2 vB[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k) {                   // prologue: chunks 0 and 1
+        const int p = pb + sub + DTEAM * k, q = p + STEP;
+        yB[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+        jB[k] = p < pe ? S.perm[p] : -1;
+        yA[k] = q < pe ? ys2[q] : make_float2(0.f, 0.f);
+        jA[k] = q < pe ? S.perm[q] : -1;
+    }
+#pragma unroll
+    for (int k = 0; k < CH; ++k) vB[k] = jB[k] >= 0 ? vals[jB[k]] : make_double2(0.0, 0.0);
+    for (int c0 = pb; c0 < pe; c0 += STEP) {
+        double2 vN[CH];
+        float2 yN[CH];
+        int jN[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {               // values of the next chunk
+            vN[k] = jA[k] >= 0 ? vals[jA[k]] : make_double2(0.0, 0.0);
+            yN[k] = yA[k];
+            jN[k] = jA[k];
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {               // coordinates and indices two chunks on
+            const int q = c0 + 2 * STEP + sub + DTEAM * k;
+            yA[k] = q < pe ? ys2[q] : make_float2(0.f, 0.f);
+            jA[k] = q < pe ? S.perm[q] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+            if (jB[k] >= 0) moments_point<B, F>(yB[k], vB[k], ar, ai, br, bi);
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            yB[k] = yN[k];
+            jB[k] = jN[k];
+            vB[k] = vN[k];
+        }
     }
     df vd[16];
     float vf[16];
@@ -600,6 +757,9 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
     } else if (lanes == DTEAM) {
         const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD, TEAM_CH, TEAM_MINB><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+    } else if (lanes == MOM_TEAM_PF) {
+        const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team_pf<DD, TEAM_CH><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     } else {
         const int blocks = cdiv((long long)S.max_items * 32, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
@@ -618,6 +778,14 @@ cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, in
     if (lanes == EVAL_FLAT) {                       // covers every point: no small-item pass
         if (S.M <= 0) return cudaSuccess;
         NNFFT_DISPATCH_DF(S.D, (k_eval_df_flat<DD><<<cdiv(S.M, 256), 256, 0, s>>>(
+                                   S, reinterpret_cast<const float2 *>(S.ys),
+                                   static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    if (lanes == EVAL_FLAT_TMA) {
+        if (S.M <= 0) return cudaSuccess;
+        NNFFT_DISPATCH_DF(S.D, (k_eval_df_flat_tma<DD><<<cdiv(S.M, 256), 256, 0, s>>>(
                                    S, reinterpret_cast<const float2 *>(S.ys),
                                    static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
         count_launches(1);

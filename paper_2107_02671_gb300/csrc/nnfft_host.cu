@@ -62,6 +62,10 @@ struct Side {
     // instance (sort_bits: the largest instance's cells) instead of over all cells
     SortTiles tiles{};
     int sort_bits = 8;
+    // batches with 9- to 16-bit local keys: first block of each instance in the two-stage
+    // sort's second stage (one block per bucket of 2^(sort_bits - 8) cells)
+    int *local_blk = nullptr;
+    int local_blocks = 0;
     void *coef = nullptr;                  // [ninst][2m][D] real tap coefficients
     void *coef_df = nullptr;               // same as (hi, lo) float pairs
     void *rfit = nullptr;                  // x side: [ncell][NR] real 1/phihat1 fits
@@ -114,9 +118,12 @@ struct nnfft_plan_s {
     FftLaunch<FftDf> fftdf[2]{};
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
-    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point
+    int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point,
+                                     // EVAL_FLAT_TMA per point with TMA-staged cells
     int fft_variant = 0;
     int item_cap = ITEM_CAP;     // points per work item at most (ITEM_CAP_MIN .. ITEM_CAP)
+    int sort_lsd = 0;            // 1: LSD radix passes even where the two-stage sort applies
+                                 // (the default for batches, where it measured faster)
     int item_split = 0;          // 1: split small work items where the size rule says so
                                  // (off by default: the warp-per-item kernels measured faster
                                  // on the batched workload; the autotuner may turn it on)
@@ -367,6 +374,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
                nnfft_dtype dtype) {
     int rc;
     p->ninst = count;
+    p->sort_lsd = count > 1 ? 1 : 0;
     p->dbl = dtype == NNFFT_C128;
     p->inst_info.assign((size_t)count, nnfft_info{});
     std::vector<InstHost> H((size_t)count);
@@ -535,6 +543,14 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
             S.tiles.ntiles = (int)tinst.size();
             S.tiles.ninst = (int)count;
             S.sort_bits = key_bits_for(max_cells);
+            if (local_sort_ok(S.sort_bits)) {     // two-stage sort: blocks per (instance, bucket)
+                const int lb = local_sort_low_bits(S.sort_bits);
+                std::vector<int> bf((size_t)count + 1, 0);
+                for (int64_t i = 0; i < count; ++i)
+                    bf[(size_t)i + 1] = bf[(size_t)i] + ((tab[(size_t)i].ncell - 1) >> lb) + 1;
+                S.local_blocks = bf.back();
+                if ((rc = upload_vec(p, &S.local_blk, bf, "sort buckets"))) return rc;
+            }
         }
         if ((rc = upload_real(p, &S.coef, coef_all, "window coefficients"))) return rc;
         if (p->split_ok && (rc = upload_df2(p, &S.coef_df, coef_all, 1.0, "window coefficients (df)")))
@@ -779,7 +795,7 @@ int device_sm_count() {
 
 namespace {
 
-template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
+template <typename Real> SideK<Real> side_args(const Side &S, bool with_r, int *status) {
     SideK<Real> k;
     k.m = S.m;
     k.D = S.D;
@@ -801,6 +817,7 @@ template <typename Real> SideK<Real> side_args(const Side &S, bool with_r) {
     k.n_big = S.split_items ? S.n2 + 1 : nullptr;
     k.keys = S.keys_sorted;
     k.M = (int)S.M;
+    k.status = status;
     return k;
 }
 
@@ -838,11 +855,34 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     const int yfmt = !p->dbl ? 0 : (p->split ? 2 : 1);
     const int ybytes = p->dbl ? 8 : 4;
     const SortTiles *tiles = p->ninst > 1 ? &S.tiles : nullptr;
+    // one instance with 9- to 16-bit cell keys: the two-stage sort (high-digit scatter, then
+    // a shared-memory sort of each bucket that also writes the cell offsets and items)
+    const bool two_stage = !p->sort_lsd && S.M >= 2 && local_sort_ok(S.sort_bits) &&
+                           (p->ninst == 1 || S.local_blk != nullptr);
     NN_CUDA(launch_node_keys_y(nodes, S.M, S.one, tiles, S.tiles.ntiles, S.keys, S.y_user, yfmt,
-                               S.sort_bits, ybytes, S.hist, p->status, st),
+                               S.sort_bits, ybytes, S.hist, p->status, st, two_stage),
             "node keys");
     uint32_t *ks = nullptr;
     int *vs = nullptr;
+    if (two_stage) {
+        const bool per_cell = p->ninst == 1 && (int64_t)S.M >= 2LL * S.ncell;
+        NN_CUDA(radix_sort_cells_local(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, tiles,
+                                       S.tiles.ntiles, S.local_blk, S.local_blocks, S.M, S.ncell,
+                                       S.sort_bits, S.y_user, S.ys, S.y_tmp, ybytes, p->item_cap,
+                                       per_cell, S.cell_off, S.item_off, S.item_cell, S.item_pb,
+                                       S.item_pe, S.nitems, S.items_scratch, st, &ks, &vs),
+                "two-stage sort");
+        S.perm = vs;
+        S.keys_sorted = ks;
+        if (S.split_items) {
+            NN_CUDA(cudaMemsetAsync(S.n2, 0, 2 * sizeof(int), st), "memset");
+            NN_CUDA(launch_split_items(S.nitems, S.item_pb, S.item_pe, S.max_items, S.list_small,
+                                       S.list_big, S.n2, st),
+                    "item split");
+        }
+        S.set = true;
+        return NNFFT_OK;
+    }
     NN_CUDA(radix_sort_cells(S.keys, S.vals, S.keys_alt, S.vals_alt, S.hist, tiles, S.tiles.ntiles,
                              S.M, S.sort_bits, S.y_user, S.ys, S.y_tmp, ybytes, st, &ks, &vs),
             "radix sort");
@@ -869,8 +909,8 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     const Side &V = p->side[0], &X = p->side[1];
     // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
     if (X.M == 0 && part == 3) return NNFFT_OK;
-    const SideK<double> sv = side_args<double>(V, false);
-    const SideK<double> sx = side_args<double>(X, true);
+    const SideK<double> sv = side_args<double>(V, false, p->status);
+    const SideK<double> sx = side_args<double>(X, true, p->status);
     const SideDf tv{nullptr, nullptr};
     if (part & 1) {
         {
@@ -912,8 +952,8 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     const Side &V = p->side[0], &X = p->side[1];
     // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
     if (V.M == 0 && part == 3) return NNFFT_OK;
-    const SideK<double> sv = side_args<double>(V, false);
-    const SideK<double> sx = side_args<double>(X, true);
+    const SideK<double> sv = side_args<double>(V, false, p->status);
+    const SideK<double> sx = side_args<double>(X, true, p->status);
     const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
     if (part & 1) {
         {
@@ -955,8 +995,8 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
     const Side &V = p->side[0], &X = p->side[1];
     // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
     if (X.M == 0 && part == 3) return NNFFT_OK;
-    const SideK<Real> sv = side_args<Real>(V, false);
-    const SideK<Real> sx = side_args<Real>(X, true);
+    const SideK<Real> sv = side_args<Real>(V, false, p->status);
+    const SideK<Real> sx = side_args<Real>(X, true, p->status);
     if (part & 1) {
         {
             StageTimer t(p, 2, st);
@@ -998,8 +1038,8 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     const Side &V = p->side[0], &X = p->side[1];
     // part 1: steps 1-2 (spread into the grid buffer); part 2: steps 3-4 from it
     if (V.M == 0 && part == 3) return NNFFT_OK;
-    const SideK<Real> sv = side_args<Real>(V, false);
-    const SideK<Real> sx = side_args<Real>(X, true);
+    const SideK<Real> sv = side_args<Real>(V, false, p->status);
+    const SideK<Real> sx = side_args<Real>(X, true, p->status);
     if (part & 1) {
         {
             StageTimer t(p, 7, st);
@@ -1071,6 +1111,8 @@ int collect_status(nnfft_plan_s *p) {
     NN_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
     const int st = *p->status_host;
     if (st & STATUS_RANGE) return fail(NNFFT_ERANGE, "a node is outside [-1/2, 1/2] or NaN");
+    if (st & STATUS_TIMEOUT)
+        return fail(NNFFT_ETIMEOUT, "a bounded device-side wait (bulk copy) gave up");
     if (st & STATUS_INTERNAL)
         return fail(NNFFT_ECUDA, "internal error: inconsistent node cell assignment");
     return NNFFT_OK;
@@ -1167,6 +1209,7 @@ int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const i
         return bail(fail(NNFFT_ENOMEM, "cudaMallocHost(status)"));
     }
     if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype))) return bail(rc);
+    if (prepare_local_sort() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "sort setup"));
     *out = p;
     return NNFFT_OK;
 }
@@ -1342,8 +1385,9 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // ones (D <= 16); evaluation: 32 or 8 lanes per item, or flat (one thread per point)
     const bool dfk = p->dbl && p->split;
     const bool small_d = p->side[0].D <= 16 && p->side[1].D <= 16;
-    std::vector<int> lanes = dfk ? std::vector<int>{32, 16, 8} : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
-    std::vector<int> elanes{32, 8, EVAL_FLAT};
+    std::vector<int> lanes = dfk ? std::vector<int>{32, 16, 8, MOM_TEAM_PF}
+                                 : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
+    std::vector<int> elanes{32, 8, EVAL_FLAT, EVAL_FLAT_TMA};
     // splitting small items changes the node-time work lists: only with the nodes given,
     // and only where the size rule would split somewhere
     bool split_possible = false;
@@ -1373,17 +1417,21 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // interleaved rounds (best time kept) and the incumbent stays unless another value is
     // more than 3 % faster.  The item split and cap change the node-time work lists, so they
     // are searched only with the nodes given (every run is then a full transform).
-    struct Cfg { int lv, lx, el, fv, sp, cap; };
+    struct Cfg { int lv, lx, el, fv, sp, cap, lsd; };
     const std::vector<int> caps = with_nodes ? std::vector<int>{ITEM_CAP, 128, 64, ITEM_CAP_MIN}
                                              : std::vector<int>{p->item_cap};
-    const std::vector<std::vector<int>> dims{lanes, elanes, {0, 1}, splits, caps};
+    // the node sort (two-stage or LSD passes) only matters where the nodes are sorted
+    const std::vector<int> sorts = with_nodes ? std::vector<int>{p->sort_lsd, 1 - p->sort_lsd}
+                                              : std::vector<int>{p->sort_lsd};
+    const std::vector<std::vector<int>> dims{lanes, elanes, {0, 1}, splits, caps, sorts};
     auto set_dim = [](Cfg c, size_t d, int v) {
         switch (d) {
             case 0: c.lv = c.lx = v; break;
             case 1: c.el = v; break;
             case 2: c.fv = v; break;
             case 3: c.sp = v; break;
-            default: c.cap = v; break;
+            case 4: c.cap = v; break;
+            default: c.lsd = v; break;
         }
         return c;
     };
@@ -1394,6 +1442,7 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
         p->eval_lanes[0] = p->eval_lanes[1] = c.el;
         p->item_split = c.sp;
         p->item_cap = c.cap;
+        p->sort_lsd = c.lsd;
     };
     auto time_cfg = [&](const Cfg &c, double &ms) -> int {
         apply(c);
@@ -1418,7 +1467,8 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     constexpr int ROUNDS = 3;
     const bool timing = p->timing;
     p->timing = false;
-    Cfg cur{lanes[0], lanes[0], elanes[0], 0, splits[0], with_nodes ? ITEM_CAP : p->item_cap};
+    Cfg cur{lanes[0], lanes[0], elanes[0], 0, splits[0], with_nodes ? ITEM_CAP : p->item_cap,
+            sorts[0]};
     double cur_ms = 1e300, default_ms = -1.0;
     for (int sweep = 0; sweep < 2 && !rc; ++sweep)
         for (size_t d = 0; d < dims.size() && !rc; ++d) {
@@ -1434,7 +1484,8 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
                 }
             if (rc) break;
             int inc = 0;                                   // the incumbent's value index
-            int curv = d == 0 ? cur.lv : d == 1 ? cur.el : d == 2 ? cur.fv : d == 3 ? cur.sp : cur.cap;
+            int curv = d == 0 ? cur.lv : d == 1 ? cur.el : d == 2 ? cur.fv : d == 3 ? cur.sp
+                     : d == 4 ? cur.cap : cur.lsd;
             for (size_t i = 0; i < vals.size(); ++i)
                 if (vals[i] == curv) inc = (int)i;
             if (default_ms < 0) default_ms = best[inc];
@@ -1463,7 +1514,7 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
         default_ms = cur_ms = ms;
     }
     p->tuning = nnfft_tuning{cur.lv, cur.lx, cur.fv, 1, default_ms, cur_ms, cur.sp,
-                             with_nodes ? 1 : 0, cur.el, cur.el, cur.cap};
+                             with_nodes ? 1 : 0, cur.el, cur.el, cur.cap, cur.lsd};
     // the work lists of the current node set follow the chosen split and cap
     if (with_nodes && (rc = run())) return rc;
     return collect_status(p);
@@ -1479,18 +1530,21 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out) {
     out->eval_lanes_v = p->eval_lanes[0];
     out->eval_lanes_x = p->eval_lanes[1];
     out->item_cap = p->item_cap;
+    out->sort_lsd = p->sort_lsd;
     return NNFFT_OK;
 }
 
 int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
-    auto ok_lanes = [](int l) { return l == 8 || l == 16 || l == 32; };
-    auto ok_elanes = [](int l) { return l == 0 || l == EVAL_FLAT || l == 8 || l == 32; };
+    auto ok_lanes = [](int l) { return l == MOM_TEAM_PF || l == 8 || l == 16 || l == 32; };
+    auto ok_elanes = [](int l) {
+        return l == 0 || l == EVAL_FLAT || l == EVAL_FLAT_TMA || l == 8 || l == 32;
+    };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
         (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1) ||
         (t->item_cap != 0 && t->item_cap != 32 && t->item_cap != 64 && t->item_cap != 128 &&
-         t->item_cap != ITEM_CAP))
+         t->item_cap != ITEM_CAP) || (t->sort_lsd != 0 && t->sort_lsd != 1))
         return fail(NNFFT_EINVAL, "invalid tuning values");
     p->mom_lanes[0] = t->moments_lanes_v;
     p->mom_lanes[1] = t->moments_lanes_x;
@@ -1498,9 +1552,10 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     p->eval_lanes[1] = t->eval_lanes_x ? t->eval_lanes_x : 32;
     p->fft_variant = t->fft_variant;
     const int cap = t->item_cap ? t->item_cap : ITEM_CAP;
-    if (t->item_split != p->item_split || cap != p->item_cap) {   // work lists: built with the nodes
-        p->item_split = t->item_split;
+    if (t->item_split != p->item_split || cap != p->item_cap || t->sort_lsd != p->sort_lsd) {
+        p->item_split = t->item_split;   // work lists and sorted nodes: built with the nodes
         p->item_cap = cap;
+        p->sort_lsd = t->sort_lsd;
         p->side[0].set = p->side[1].set = false;
     }
     return NNFFT_OK;
@@ -1570,6 +1625,18 @@ int nnfft_selftest_fixed63(const int64_t *in_dev, float *out_dev, int64_t n) {
     NN_CUDA(selftest_fixed63(reinterpret_cast<const long long *>(in_dev), out_dev, (int)n, nullptr),
             "self-test launch");
     NN_CUDA(cudaStreamSynchronize(nullptr), "self-test");
+    return NNFFT_OK;
+}
+
+int nnfft_selftest_bulk_copy(const float *src_dev, float *dst_dev, int n, int arm_only,
+                             int64_t limit_cycles, int *status_dev) {
+    if (!dst_dev || !status_dev || (!src_dev && !arm_only) || n <= 0 || n > 4096 || (n & 3) ||
+        limit_cycles <= 0)
+        return fail(NNFFT_EINVAL, "invalid self-test arguments");
+    NN_CUDA(selftest_bulk_copy(src_dev, dst_dev, n, arm_only, (long long)limit_cycles, status_dev,
+                               nullptr),
+            "bulk-copy self-test");
+    NN_CUDA(cudaStreamSynchronize(nullptr), "bulk-copy self-test");
     return NNFFT_OK;
 }
 

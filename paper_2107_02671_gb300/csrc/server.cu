@@ -80,6 +80,8 @@ struct Req {
     int dtype = 0, m = 0;
     int64_t Ncap = 0;
     Clock::time_point t_submit, t_done;
+    double dev_ms[4] = {-1, -1, -1, -1};   // device times since the epoch: first upload,
+                                           // first kernel, after the last kernel, download end
     int status = NNFFT_OK;
     bool done = false;
 };
@@ -87,6 +89,8 @@ struct Req {
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_t[4] = {};   // timing: before the uploads, before the first kernel, after
+                                // the last kernel, after the download
     double *d1 = nullptr, *d2 = nullptr;   // nodes (v or a / x or b)
     void *c1 = nullptr, *c2 = nullptr;     // values (f or c / y or h), complex128-sized
     void *g = nullptr;                     // sinc: the quadrature-node values
@@ -129,6 +133,7 @@ struct nnfft_server_s {
     Clock::time_point t_first{}, t_last{};
     bool any = false;
     int device = 0;
+    cudaEvent_t epoch = nullptr;          // device time origin of the kernel intervals
 };
 
 namespace {
@@ -330,11 +335,15 @@ int launch_nnfft(Slot &sl, Req *q) {
     if ((rc = nnfft_set_stream(p, sl.st)) || (rc = nnfft_set_sizes(p, r.M1, r.M2)) ||
         (rc = nnfft_set_bandwidth(p, r.N)))
         return rc;
+    SV_CUDA(cudaEventRecord(sl.ev_t[0], sl.st));
     if (r.M1) SV_CUDA(cudaMemcpyAsync(sl.d1, r.v, 8 * (size_t)r.M1, cudaMemcpyHostToDevice, sl.st));
     if (r.M2) SV_CUDA(cudaMemcpyAsync(sl.d2, r.x, 8 * (size_t)r.M2, cudaMemcpyHostToDevice, sl.st));
     if (r.M1) SV_CUDA(cudaMemcpyAsync(sl.c1, r.f, cs * (size_t)r.M1, cudaMemcpyHostToDevice, sl.st));
+    SV_CUDA(cudaEventRecord(sl.ev_t[1], sl.st));
     if ((rc = nnfft_set_nodes(p, sl.d1, sl.d2)) || (rc = nnfft_exec(p, sl.c1, sl.c2))) return rc;
+    SV_CUDA(cudaEventRecord(sl.ev_t[2], sl.st));
     if (r.M2) SV_CUDA(cudaMemcpyAsync(r.y, sl.c2, cs * (size_t)r.M2, cudaMemcpyDeviceToHost, sl.st));
+    SV_CUDA(cudaEventRecord(sl.ev_t[3], sl.st));
     return NNFFT_OK;
 }
 
@@ -351,9 +360,11 @@ int launch_sinc(nnfft_server_s *S, Slot &sl, Req *q, Rule *R) {
         (rc = nnfft_set_bandwidth(p1, r.N)) || (rc = nnfft_set_stream(p2, sl.st)) ||
         (rc = nnfft_set_sizes(p2, R->nq, r.M2)) || (rc = nnfft_set_bandwidth(p2, r.N)))
         return rc;
+    SV_CUDA(cudaEventRecord(sl.ev_t[0], sl.st));
     if (r.M1) SV_CUDA(cudaMemcpyAsync(sl.d1, r.v, 8 * (size_t)r.M1, cudaMemcpyHostToDevice, sl.st));
     if (r.M2) SV_CUDA(cudaMemcpyAsync(sl.d2, r.x, 8 * (size_t)r.M2, cudaMemcpyHostToDevice, sl.st));
     if (r.M1) SV_CUDA(cudaMemcpyAsync(sl.c2, r.f, vs * (size_t)r.M1, cudaMemcpyHostToDevice, sl.st));
+    SV_CUDA(cudaEventRecord(sl.ev_t[1], sl.st));
     const void *cin = sl.c2;
     if (!r.is_complex) {
         SV_CUDA(dbl ? launch_real_to_complex<double>(static_cast<const double *>(sl.c2), (int)r.M1, sl.c1, sl.st)
@@ -367,20 +378,28 @@ int launch_sinc(nnfft_server_s *S, Slot &sl, Req *q, Rule *R) {
     if (!r.is_complex) {
         SV_CUDA(dbl ? launch_complex_to_real<double>(sl.c1, (int)r.M2, static_cast<double *>(sl.c2), sl.st)
                     : launch_complex_to_real<float>(sl.c1, (int)r.M2, static_cast<float *>(sl.c2), sl.st));
+        SV_CUDA(cudaEventRecord(sl.ev_t[2], sl.st));
         if (r.M2) SV_CUDA(cudaMemcpyAsync(r.y, sl.c2, rs * (size_t)r.M2, cudaMemcpyDeviceToHost, sl.st));
-    } else if (r.M2) {
-        SV_CUDA(cudaMemcpyAsync(r.y, sl.c1, cs * (size_t)r.M2, cudaMemcpyDeviceToHost, sl.st));
+    } else {
+        SV_CUDA(cudaEventRecord(sl.ev_t[2], sl.st));
+        if (r.M2) SV_CUDA(cudaMemcpyAsync(r.y, sl.c1, cs * (size_t)r.M2, cudaMemcpyDeviceToHost, sl.st));
     }
+    SV_CUDA(cudaEventRecord(sl.ev_t[3], sl.st));
     return NNFFT_OK;
 }
 
 // The slot's request is over (its event has completed, or it failed to start): collect
 // device-side status, release the plans and the slot.  No lock: slots and plans belong to
 // the worker thread.  Returns the request and its status.
-Req *retire(Slot &sl, int &status) {
+Req *retire(Slot &sl, int &status, cudaEvent_t epoch) {
     Req *q = sl.req;
     if (status == NNFFT_OK && sl.pa) status = nnfft_sync(sl.pa->p);
     if (status == NNFFT_OK && sl.pb) status = nnfft_sync(sl.pb->p);
+    for (int k = 0; k < 4 && status == NNFFT_OK && epoch; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, epoch, sl.ev_t[k]) == cudaSuccess) q->dev_ms[k] = t;
+    }
+    cudaGetLastError();
     release_plan(sl.pa);
     release_plan(sl.pb);
     sl.req = nullptr;
@@ -440,7 +459,7 @@ Admit admit(nnfft_server_s *S, Slot &sl, Req *q, int *status) {
     }
     if (rc == NNFFT_OK) return ADMITTED;
     if (sl.pa) cudaStreamSynchronize(sl.st);
-    retire(sl, rc);
+    retire(sl, rc, nullptr);
     *status = rc;
     return FAILED;
 }
@@ -462,7 +481,7 @@ void worker_loop(nnfft_server_s *S) {
             }
             if (e != cudaSuccess) cudaGetLastError();
             int st = e == cudaSuccess ? NNFFT_OK : NNFFT_ECUDA;
-            Req *q = retire(sl, st);
+            Req *q = retire(sl, st, S->epoch);
             {
                 std::lock_guard<std::mutex> g(S->mu);
                 record_done(S, q, st);
@@ -540,6 +559,7 @@ int nnfft_server_create(nnfft_server_t *out, int64_t mem_budget_bytes, int nslot
     for (Slot &sl : S->slots) {
         cudaError_t e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&sl.ev_t[k]);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d1, 8 * mp);
         if (e == cudaSuccess) e = cudaMalloc(&sl.d2, 8 * mp);
         if (e == cudaSuccess) e = cudaMalloc(&sl.c1, 16 * mp);
@@ -551,6 +571,12 @@ int nnfft_server_create(nnfft_server_t *out, int64_t mem_budget_bytes, int nslot
             return sfail(NNFFT_ENOMEM, "server: slot buffers");
         }
         S->fixed_bytes += 48 * mp + 16 * (8 * 16384 + 1);
+    }
+    if (cudaEventCreate(&S->epoch) != cudaSuccess || cudaEventRecord(S->epoch, nullptr) != cudaSuccess ||
+        cudaEventSynchronize(S->epoch) != cudaSuccess) {
+        cudaGetLastError();
+        nnfft_server_destroy(S);
+        return sfail(NNFFT_ECUDA, "server: timing event");
     }
     S->builder = std::thread(builder_loop, S);
     S->worker = std::thread(worker_loop, S);
@@ -599,6 +625,10 @@ int nnfft_server_submit(nnfft_server_t S, const nnfft_request *r, int64_t *id) {
 }
 
 int nnfft_server_wait(nnfft_server_t S, int64_t id, double *latency_ms) {
+    return nnfft_server_wait_device(S, id, latency_ms, nullptr);
+}
+
+int nnfft_server_wait_device(nnfft_server_t S, int64_t id, double *latency_ms, double *device_ms) {
     if (!S) return sfail(NNFFT_EINVAL, "null server");
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(id);
@@ -607,6 +637,8 @@ int nnfft_server_wait(nnfft_server_t S, int64_t id, double *latency_ms) {
     S->cv_done.wait(lk, [&] { return q->done; });
     const int st = q->status;
     if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    if (device_ms)
+        for (int k = 0; k < 4; ++k) device_ms[k] = q->dev_ms[k];
     S->reqs.erase(it);
     delete q;
     return st == NNFFT_OK ? NNFFT_OK : sfail(st, "request failed");
@@ -684,9 +716,12 @@ int nnfft_server_destroy(nnfft_server_t S) {
         cudaFree(sl.c2);
         cudaFree(sl.g);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        for (cudaEvent_t t : sl.ev_t)
+            if (t) cudaEventDestroy(t);
         if (sl.st) cudaStreamDestroy(sl.st);
     }
     for (auto &kv : S->rules) cudaFree(kv.second.x1);
+    if (S->epoch) cudaEventDestroy(S->epoch);
     for (auto &kv : S->reqs) delete kv.second;
     delete S;
     return NNFFT_OK;

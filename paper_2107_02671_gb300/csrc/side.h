@@ -46,9 +46,19 @@ template <typename Real> struct SideK {
     // the flat (one thread per point) evaluation kernels
     const uint32_t *keys;
     int M;
+    // the plan's device status word (kernels OR in STATUS_* bits)
+    int *status;
 };
+// Moments lanes value that selects the split-precision 8-lane team kernel with the point
+// loads software-pipelined across chunks.
+constexpr int MOM_TEAM_PF = 4;
 // Evaluation lanes value that selects the flat kernels: one thread per sorted point.
 constexpr int EVAL_FLAT = 1;
+// The flat kernels with each block's range of cell window sums staged in shared memory by
+// one bulk (TMA) copy.
+constexpr int EVAL_FLAT_TMA = 2;
+// Cells a staged block holds at most (blocks spanning more read global memory directly).
+constexpr int TMA_MAX_CELLS = 128;
 // Largest work item handled by one thread (no reduction) when a plan splits items.
 constexpr int SMALL_ITEM = 16;
 

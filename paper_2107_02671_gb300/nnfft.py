@@ -55,7 +55,7 @@ class Tuning(ctypes.Structure):
                 ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double),
                 ("item_split", ctypes.c_int), ("timed_transform", ctypes.c_int),
                 ("eval_lanes_v", ctypes.c_int), ("eval_lanes_x", ctypes.c_int),
-                ("item_cap", ctypes.c_int)]
+                ("item_cap", ctypes.c_int), ("sort_lsd", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -120,6 +120,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_server_create.argtypes = [P(vp), i64, cint, i64]
         lib.nnfft_server_submit.argtypes = [vp, P(Request), P(i64)]
         lib.nnfft_server_wait.argtypes = [vp, i64, P(dbl)]
+        lib.nnfft_server_wait_device.argtypes = [vp, i64, P(dbl), P(dbl)]
         lib.nnfft_server_stats.argtypes = [vp, P(ServerReport), cint]
         lib.nnfft_server_destroy.argtypes = [vp]
         lib.nnfft_set_stream.argtypes = [vp, vp]
@@ -159,6 +160,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_timing_enable.argtypes = [vp, cint]
         lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
         lib.nnfft_selftest_fixed63.argtypes = [vp, vp, i64]
+        lib.nnfft_selftest_bulk_copy.argtypes = [vp, vp, cint, cint, i64, vp]
         lib.nnfft_launch_count.argtypes = []
         lib.nnfft_launch_count.restype = i64
         lib.nnfft_last_error.restype = ctypes.c_char_p
@@ -366,11 +368,14 @@ class Plan:
         return self.tuning()
 
     def set_tuning(self, moments_lanes_v=32, moments_lanes_x=32, fft_variant=0, item_split=0,
-                   eval_lanes_v=32, eval_lanes_x=32, item_cap=256):
-        """Apply a kernel-variant configuration (see autotune); a changed item_split or
-        item_cap needs set_nodes again."""
+                   eval_lanes_v=32, eval_lanes_x=32, item_cap=256, sort_lsd=None):
+        """Apply a kernel-variant configuration (see autotune); a changed item_split,
+        item_cap or sort_lsd needs set_nodes again (sort_lsd None: keep the plan's)."""
+        if sort_lsd is None:
+            sort_lsd = self.tuning()["sort_lsd"]
         t = Tuning(int(moments_lanes_v), int(moments_lanes_x), int(fft_variant), 0, 0.0, 0.0,
-                   int(item_split), 0, int(eval_lanes_v), int(eval_lanes_x), int(item_cap))
+                   int(item_split), 0, int(eval_lanes_v), int(eval_lanes_x), int(item_cap),
+                   int(sort_lsd))
         _check(self._lib.nnfft_set_tuning(self._h, ctypes.byref(t)))
         return self
 
@@ -652,6 +657,18 @@ class Server:
             self._keep.pop(rid, None)
         return lat.value
 
+    def wait_device(self, rid):
+        """wait() that also returns where the request ran on the device: (latency_ms,
+        [before uploads, first kernel, after last kernel, after download]) in ms since the
+        server was made."""
+        lat = ctypes.c_double()
+        t = (ctypes.c_double * 4)()
+        try:
+            _check(self._lib.nnfft_server_wait_device(self._h, int(rid), ctypes.byref(lat), t))
+        finally:
+            self._keep.pop(rid, None)
+        return lat.value, list(t)
+
     def stats(self, reset=False) -> dict:
         rep = ServerReport()
         _check(self._lib.nnfft_server_stats(self._h, ctypes.byref(rep), int(bool(reset))))
@@ -729,6 +746,22 @@ def selftest_fixed63(y):
     _check(load_library().nnfft_selftest_fixed63(ctypes.c_void_p(y.data_ptr()),
                                                  ctypes.c_void_p(out.data_ptr()), y.numel()))
     return out
+
+
+def selftest_bulk_copy(src, arm_only=False, limit_cycles=2_000_000):
+    """Bounded-wait check of the bulk (TMA) copy helpers: returns (dst, status) where dst
+    is src staged through shared memory (zeros if the wait gave up) and status the bits the
+    block set (4: the wait gave up).  arm_only skips the copy, so the wait runs out."""
+    import torch
+    if src.dtype != torch.float32 or not src.is_cuda or not src.is_contiguous():
+        raise TypeError("src must be a contiguous float32 CUDA tensor")
+    dst = torch.zeros_like(src)
+    status = torch.zeros(1, dtype=torch.int32, device=src.device)
+    torch.cuda.synchronize()
+    _check(load_library().nnfft_selftest_bulk_copy(
+        ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), src.numel(),
+        int(bool(arm_only)), int(limit_cycles), ctypes.c_void_p(status.data_ptr())))
+    return dst, int(status.item())
 
 
 def launch_count() -> int:

@@ -148,10 +148,45 @@ def test_batch_flat_evaluation_bitwise(dtype, m):
     g = W.draw_complex(np.random.default_rng(6), int(M2.sum()), npd)
     P = B.BatchPlan(N, M1, M2, 2.0, 2.0, m, dtype=dtype)
     res = []
-    for el in (32, 1):
+    for el in (32, 1, 2):                      # 2: flat with TMA-staged cell tiles
         P.set_tuning(32, 32, 0, 0, el, el)
         P.set_nodes(dev(v), dev(x))
         y, z = P.exec_adjoint(dev(f), dev(g))
         P.sync()
         res.append((y.cpu().numpy(), z.cpu().numpy()))
+    for r in res[1:]:
+        assert np.array_equal(res[0][0], r[0]) and np.array_equal(res[0][1], r[1])
+
+
+@pytest.mark.parametrize("dtype,m,arith", [(torch.complex128, 8, None), (torch.complex128, 8, "fp64"),
+                                           (torch.complex64, 4, None)])
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_batch_two_stage_sort_equals_lsd_sort(dtype, m, arith, nodes):
+    """The two-stage node sort of a batch (per-instance high-digit scatter, then one block
+    per instance and bucket of cells) orders every instance's nodes exactly as the LSD
+    passes: bitwise equal transforms.  Instances without points, with one point, small and
+    large (clustered nodes: buckets over several shared-memory chunks)."""
+    N = np.array([2048, 64, 512, 7, 4096, 33, 300])
+    M1 = np.array([60000, 1, 0, 300, 90000, 77, 5000])
+    M2 = np.array([50000, 300, 50, 0, 70001, 1, 9000])
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, f = W.batch_inputs(M1, M2, 61, nodes=nodes, dtype=npd)
+    g = W.draw_complex(np.random.default_rng(8), int(M2.sum()), npd)
+    P = B.BatchPlan(N, M1, M2, 2.0, 2.0, m, dtype=dtype)
+    if arith == "fp64":
+        P.set_arith(B.ARITH_FP64)
+    res = []
+    for lsd in (1, 0):
+        P.set_tuning(32, 32, 0, 0, 32, 32, sort_lsd=lsd)
+        P.set_nodes(dev(v), dev(x))
+        y, z = P.exec_adjoint(dev(f), dev(g))
+        P.sync()
+        res.append((y.cpu().numpy(), z.cpu().numpy()))
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    tol = 1e-12 if dtype == torch.complex128 else 2e-5
+    i = 4                                      # the largest instance against the oracle
+    a1, b1, a2, b2 = P.off1[i], P.off1[i + 1], P.off2[i], P.off2[i + 1]
+    rows = W.sample_rows(int(M2[i]), 32, 3)
+    fi = f[a1:b1].astype(np.complex128)
+    want = oracle.nnfft_direct(int(N[i]), v[a1:b1], fi, x[a2:b2], rows=rows)
+    assert err(res[1][0][a2:b2][rows].astype(np.complex128), want, fi) <= tol

@@ -421,8 +421,8 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
     plan.set_nodes(dev(v), dev(x))
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
-    assert t["tuned"] == 1 and t["moments_lanes_v"] in (8, 16, 32) and t["moments_lanes_x"] in (8, 16, 32)
-    assert t["eval_lanes_v"] in (1, 8, 32) and t["eval_lanes_x"] in (1, 8, 32)
+    assert t["tuned"] == 1 and t["moments_lanes_v"] in (4, 8, 16, 32) and t["moments_lanes_x"] in (4, 8, 16, 32)
+    assert t["eval_lanes_v"] in (1, 2, 8, 32) and t["eval_lanes_x"] in (1, 2, 8, 32)
     assert t["fft_variant"] in (0, 1) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
     assert t["timed_transform"] == 0
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
@@ -453,7 +453,7 @@ def test_every_moments_and_fft_variant_is_correct():
     want_y = oracle.nnfft_direct(N, v, f, x, rows=rows2)
     want_z = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows1)
     for lanes, fv, split, el in ((16, 0, 1, 32), (16, 1, 0, 8), (32, 0, 0, 32), (32, 1, 1, 8),
-                                 (8, 0, 0, 8), (8, 1, 1, 32)):
+                                 (8, 0, 0, 8), (8, 1, 1, 32), (4, 0, 0, 1), (4, 1, 1, 2)):
         plan.set_tuning(lanes, lanes, fv, split, el, el)
         plan.set_nodes(dev(v), dev(x))
         y, z = plan.exec_adjoint(dev(f), dev(g))
@@ -584,23 +584,26 @@ def test_transform_device_equals_separate_calls(dtype):
 def test_figure_4_1b_protocol(sigma):
     """The Fig. 4.1(b) experiment with the sinh window itself: N = 1200, m1 = m2 = m in
     2..8, sigma1 = sigma2, M1 = 2400, M2 = 1600, x uniform in [-1/2, 1/2], v uniform in
-    [-1/(2a), 1/(2a)] with a = 1 + 2m/N1, complex N(0,1) coefficients; the maximum over
-    repetitions of the error eq. (4.5) lies below the bound E(phi_sinh)
-    of Theorem 4.1 and falls with m."""
-    N, M1, M2, reps = 1200, 2400, 1600, 4
+    [-1/(2a), 1/(2a)] with a = 1 + 2m/N1, complex N(0,1) coefficients, 100 repetitions as in
+    the paper; the maximum over the repetitions of the error eq. (4.5) lies below the
+    bound E(phi_sinh) of Theorem 4.1 and falls with m."""
+    N, M1, M2, reps = 1200, 2400, 1600, 100
     worst = {}
     for m in range(2, 9):
         P = oracle.make_params(N, sigma, sigma, m, m)
         a = 1.0 + 2.0 * m / P.N1
         E, _, _ = oracle.bound_sinh(P.N1, m, m, P.sigma1, P.sigma2)
+        plan = B.Plan(N, M1, M2, sigma, sigma, m, m, dtype=torch.complex128)
         err = 0.0
         for rep in range(reps):
             rng = np.random.default_rng(1000 * m + rep)
             x = rng.uniform(-0.5, 0.5, M2)
             v = rng.uniform(-0.5 / a, 0.5 / a, M1)
             f = rng.standard_normal(M1) + 1j * rng.standard_normal(M1)
-            y, _ = run_forward(N, v, x, f, m, torch.complex128, sigma=sigma)
+            plan.set_nodes(dev(v), dev(x))
+            y = plan.exec(dev(f)).cpu().numpy()
             err = max(err, oracle.relative_error(y, oracle.nnfft_direct(N, v, f, x), f))
+        plan.sync()
         worst[m] = err
         assert err <= E, (sigma, m, err, E)
     assert worst[8] < 1e-3 * worst[2]
@@ -647,13 +650,13 @@ def test_flat_evaluation_equals_item_evaluation(dtype, arith, m, tol, N, M1, M2)
     if arith == "fp64":
         plan.set_arith(B.ARITH_FP64)
     outs = {}
-    for el in (32, 8, 1):
+    for el in (32, 8, 1, 2):                   # 2: flat with TMA-staged cell tiles
         plan.set_tuning(32, 32, 0, 0, el, el)
         plan.set_nodes(dev(v), dev(x))
         y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
         plan.sync()
         outs[el] = (y.cpu().numpy(), z.cpu().numpy())
-    for el in (8, 1):
+    for el in (8, 1, 2):
         assert np.array_equal(outs[el][0], outs[32][0]) and np.array_equal(outs[el][1], outs[32][1]), el
     rows2, rows1 = W.sample_rows(M2, 64, 9), W.sample_rows(M1, 64, 10)
     y, z = (a.astype(np.complex128) for a in outs[1])
@@ -661,18 +664,33 @@ def test_flat_evaluation_equals_item_evaluation(dtype, arith, m, tol, N, M1, M2)
     want_z = oracle.nnfft_adjoint_direct(N, v, x, g.astype(np.complex128), rows=rows1)
     assert np.max(np.abs(y[rows2] - want_y)) / np.sum(np.abs(f)) <= tol
     assert np.max(np.abs(z[rows1] - want_z)) / np.sum(np.abs(g)) <= tol
-    # reduced active sizes: the flat kernel covers exactly the active points
+    # reduced active sizes: the flat kernels cover exactly the active points
     m1, m2 = M1 // 3, M2 // 2
     plan.set_sizes(m1, m2)
-    plan.set_nodes(dev(v[:m1]), dev(x[:m2]))
-    sentinel = torch.full((M2,), 7.0 + 7.0j, dtype=dtype, device="cuda")
-    plan.exec(dev(f[:m1], dtype), out=sentinel[:m2])
-    plan.sync()
-    ys = sentinel.cpu().numpy()
-    assert np.all(ys[m2:] == 7.0 + 7.0j)
-    rows = W.sample_rows(m2, 32, 11)
-    want = oracle.nnfft_direct(N, v[:m1], f[:m1].astype(np.complex128), x[:m2], rows=rows)
-    assert np.max(np.abs(ys[:m2][rows].astype(np.complex128) - want)) / np.sum(np.abs(f[:m1])) <= tol
+    for el in (1, 2):
+        plan.set_tuning(32, 32, 0, 0, el, el)
+        plan.set_nodes(dev(v[:m1]), dev(x[:m2]))
+        sentinel = torch.full((M2,), 7.0 + 7.0j, dtype=dtype, device="cuda")
+        plan.exec(dev(f[:m1], dtype), out=sentinel[:m2])
+        plan.sync()
+        ys = sentinel.cpu().numpy()
+        assert np.all(ys[m2:] == 7.0 + 7.0j)
+        rows = W.sample_rows(m2, 32, 11)
+        want = oracle.nnfft_direct(N, v[:m1], f[:m1].astype(np.complex128), x[:m2], rows=rows)
+        assert np.max(np.abs(ys[:m2][rows].astype(np.complex128) - want)) / np.sum(np.abs(f[:m1])) <= tol
+
+
+def test_bulk_copy_waits_are_bounded():
+    """The bulk (TMA) copy helpers: a staged copy arrives intact; a barrier armed for bytes
+    that never come gives up after its cycle limit, sets the timeout bit (4) and leaves the
+    context usable (the next copy works)."""
+    src = torch.arange(4096, dtype=torch.float32, device="cuda")
+    dst, st = B.selftest_bulk_copy(src)
+    assert st == 0 and torch.equal(dst, src)
+    dst, st = B.selftest_bulk_copy(src, arm_only=True, limit_cycles=2_000_000)
+    assert st == 4 and not torch.any(dst)
+    dst, st = B.selftest_bulk_copy(src[:1000])
+    assert st == 0 and torch.equal(dst, src[:1000])
 
 
 @pytest.mark.parametrize("dtype,m", [(torch.complex128, 8), (torch.complex64, 4)])
@@ -883,3 +901,35 @@ def test_three_pass_sort(dtype, m, tol, nodes):
     assert oracle.relative_error(y, oracle.nnfft_direct(N, v, f64, x), f64) <= tol
     assert oracle.relative_error(z, oracle.nnfft_adjoint_direct(N, v, x, g64), g64) <= tol
     plan.close()
+
+
+@pytest.mark.parametrize("dtype,arith,m", [(torch.complex128, None, 8), (torch.complex128, "fp64", 8),
+                                           (torch.complex64, None, 4)])
+@pytest.mark.parametrize("N,M1,M2,nodes", [(4096, 300000, 200001, "chebyshev"),
+                                            (700, 80000, 50000, "uniform"),
+                                            (3000, 5000, 4000, "uniform"),
+                                            (300, 60000, 3, "chebyshev")])
+def test_two_stage_sort_equals_lsd_sort(dtype, arith, m, N, M1, M2, nodes):
+    """The two-stage node sort (high-digit scatter, then a shared-memory sort per bucket that
+    also writes the cell offsets and work items) orders the nodes exactly as the LSD radix
+    passes: the transforms are bitwise equal.  Cases: clustered nodes whose edge buckets
+    span several shared-memory chunks and hold cells above the item cap, dense uniform
+    nodes (one item per cell), sparse nodes (scan-built items), a side of three points."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, f = W.nnfft_inputs(M1, M2, 95, nodes=nodes, dtype=npd)
+    g = W.adjoint_inputs(M2, 95, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    if arith == "fp64":
+        plan.set_arith(B.ARITH_FP64)
+    outs = []
+    for lsd in (1, 0):
+        plan.set_tuning(32, 32, 0, 0, 32, 32, sort_lsd=lsd)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f, dtype), dev(g, dtype))
+        plan.sync()
+        outs.append((y.cpu().numpy(), z.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    tol = 1e-12 if dtype == torch.complex128 else 2e-5
+    rows2 = W.sample_rows(M2, 48, 12, extremes=[int(np.argmin(x)), int(np.argmax(x))])
+    want = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows2)
+    assert np.max(np.abs(outs[1][0][rows2].astype(np.complex128) - want)) / np.sum(np.abs(f)) <= tol

@@ -1,6 +1,8 @@
 """The request loop (serving): NNFFT and sinc requests of mixed sizes and tolerances,
 each result identical alone and in a mix, within its tolerance of the oracle, under a
 device-memory budget that forces plan eviction."""
+import time
+
 import numpy as np
 import pytest
 
@@ -126,3 +128,70 @@ def test_request_errors_do_not_stop_the_loop():
     S.wait(S.submit_nnfft(64, v, x, f, y, 1e-12))          # the next request is served
     S.close()
     assert np.max(np.abs(y - exact(spec, v, x, f))) / np.sum(np.abs(f)) <= 1e-12
+
+
+@pytest.mark.parametrize("tol", [1e-5, 1e-9, 1e-12])
+@pytest.mark.parametrize("kind", ["nnfft", "sinc"])
+def test_tolerance_classes_at_the_largest_bandwidth_with_clustered_nodes(kind, tol):
+    """The stream's upper end: N = 16384 with Chebyshev-distributed nodes (cos(pi u)/2,
+    dense at +-1/2, where 1/phihat1(N x) and hence the second term of Theorem 4.1 is
+    largest).  Each tolerance class must hold on sampled and extreme rows."""
+    N, M1, M2 = 16384, 60000, 50000
+    S = B.Server(mem_budget_bytes=8 << 30, slots=2, max_points=1 << 17)
+    rng = np.random.default_rng(77)
+    v = np.cos(np.pi * rng.uniform(0, 1, M1)) / 2
+    x = np.cos(np.pi * rng.uniform(0, 1, M2)) / 2
+    dt, _ = B.tolerance_params(tol)
+    if kind == "nnfft":
+        f = W.draw_complex(rng, M1, np.complex128 if dt == B.NNFFT_C128 else np.complex64)
+        y = np.zeros(M2, f.dtype)
+        S.wait(S.submit_nnfft(N, v, x, f, y, tol))
+    else:
+        f = rng.standard_normal(M1).astype(np.float64 if dt == B.NNFFT_C128 else np.float32)
+        y = np.zeros(M2, f.dtype)
+        S.wait(S.submit_sinc(N, v, f, x, y, tol, "gl"))
+    S.close()
+    rows = W.sample_rows(M2, 200, 9, extremes=[int(np.argmin(x)), int(np.argmax(x))])
+    f64 = f.astype(np.complex128)
+    want = (oracle.nnfft_direct(N, v, f64, x, rows=rows) if kind == "nnfft"
+            else oracle.sinc_direct(N, v, f64, x, rows=rows))
+    err = np.max(np.abs(y[rows].astype(np.complex128) - want)) / np.sum(np.abs(f))
+    assert err <= tol, (kind, tol, err)
+
+
+def test_work_of_two_slots_overlaps_on_the_device():
+    """Continuous batching: two large requests submitted together run on two slots, and
+    their device intervals (CUDA events on the slot streams, from before the uploads to
+    after the download) intersect: the second request's work starts on the device before
+    the first one's has ended.  Pinned host buffers, so that every copy is asynchronous."""
+    M, N = 1 << 22, 4096
+    S = B.Server(mem_budget_bytes=16 << 30, slots=2, max_points=M)
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()      # noqa: E731
+    rng = np.random.default_rng(5)
+    reqs = []
+    for k in range(2):
+        v = pin(rng.uniform(-0.5, 0.5, M))
+        x = pin(rng.uniform(-0.5, 0.5, M))
+        f = pin(W.draw_complex(rng, M))
+        y = pin(np.zeros(M, np.complex128))
+        reqs.append((v, x, f, y))
+    # warm-up: two requests at once, so that the cache ends up with two plans of this
+    # bucket (a plan serves one slot at a time; the second is made on the builder thread
+    # while the first request runs); then the two requests back to back
+    for i in [S.submit_nnfft(N, v, x, f, y, 1e-12) for v, x, f, y in reqs]:
+        S.wait(i)
+    t_end = time.time() + 60
+    while S.stats()["plans_cached"] < 2 and time.time() < t_end:
+        time.sleep(0.01)
+    assert S.stats()["plans_cached"] >= 2
+    ids = [S.submit_nnfft(N, v, x, f, y, 1e-12) for v, x, f, y in reqs]
+    t = [S.wait_device(i)[1] for i in ids]
+    S.close()
+    for a in t:
+        assert 0 <= a[0] <= a[1] < a[2] <= a[3], t
+    (a0, _, _, a1), (b0, _, _, b1) = t
+    assert a0 < b1 and b0 < a1, t              # the two device intervals intersect
+    rows = W.sample_rows(M, 16, 1)
+    v, x, f, y = reqs[1]
+    want = oracle.nnfft_direct(N, v, f, x, rows=rows)
+    assert np.max(np.abs(y[rows] - want)) / np.sum(np.abs(f)) <= 1e-12
