@@ -291,19 +291,20 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------------------------------
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of every
 # split-precision point-kernel variant at the headline size, from ncu captures of
-# `python bench.py --steps 5 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
-# with T = 8,8,0,0,1,1 / 32,32,0,0,32,32 / 16,16,0,0,8,8 (the moments and evaluation captures).
-# The files the kernels are built from (their code, the double-float primitives, the side
-# descriptor) are hashed; a change since the capture reports null.
+# `python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
+# (NVTX range headline_seq) with T = 8,8,0,0,1,1,256,0 / 4,4,0,0,2,2,256,0 /
+# 16,16,0,0,32,32,256,0, averaged over the captured launches.  The files the kernels are
+# built from (their code, the double-float primitives, the side descriptor) are hashed; a
+# change since the capture reports null.
 NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "side.h"]
-NCU_HASH = "6655c79950a54511"
+NCU_HASH = "93ebd54f195ec588"
 NCU_TRAFFIC = {
-    "k_moments_df_team<14>": 29463808,          # 8 lanes per work item
-    "k_moments_df_half<14>": 29482752,          # 16
-    "k_moments_df_warp<14>": 29486080,          # 32
-    "k_eval_df_flat<14>": 20417024 + 1797632,   # one thread per point
-    "k_eval_df_team<14>": 14562048 + 768,       # 8 lanes per work item
-    "k_eval_df<14>": 16181248 + 1621504,        # 32
+    "k_moments_df_team<14>": 29461888,          # 8 lanes per work item
+    "k_moments_df_team_pf<14>": 29462144,       # 8 lanes, loads pipelined across chunks
+    "k_moments_df_half<14>": 29481088,          # 16
+    "k_eval_df_flat<14>": 20472576 + 1804352,   # one thread per point
+    "k_eval_df_flat_tma<14>": 20443840 + 1775232,   # the same, cells staged by TMA
+    "k_eval_df<14>": 16270464 + 1658560,        # 32
 }
 
 
@@ -312,9 +313,11 @@ def point_kernel(stage, tuning):
     side = "v" if stage in ("fwd_moments", "adj_eval") else "x"
     if stage.endswith("_moments"):
         lanes = tuning.get(f"moments_lanes_{side}", 32)
-        return {8: "k_moments_df_team<14>", 16: "k_moments_df_half<14>"}.get(lanes, "k_moments_df_warp<14>")
+        return {8: "k_moments_df_team<14>", 4: "k_moments_df_team_pf<14>",
+                16: "k_moments_df_half<14>"}.get(lanes, "k_moments_df_warp<14>")
     lanes = tuning.get(f"eval_lanes_{side}", 32)
-    return {1: "k_eval_df_flat<14>", 8: "k_eval_df_team<14>"}.get(lanes, "k_eval_df<14>")
+    return {1: "k_eval_df_flat<14>", 2: "k_eval_df_flat_tma<14>",
+            8: "k_eval_df_team<14>"}.get(lanes, "k_eval_df<14>")
 
 
 def ncu_traffic(stage, tuning):

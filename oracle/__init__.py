@@ -41,6 +41,7 @@ class Params(ctypes.Structure):
         ("m1", ctypes.c_int), ("m2", ctypes.c_int),
         ("sigma1", ctypes.c_double), ("sigma2", ctypes.c_double),
         ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("a", ctypes.c_double),
+        ("window", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -91,6 +92,16 @@ def _load():
         lib.orc_phi_hat.restype = ctypes.c_double
         lib.orc_make_params.argtypes = [i64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, ctypes.POINTER(Params)]
+        lib.orc_make_params_w.argtypes = [i64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.POINTER(Params)]
+        lib.orc_omega_w.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        lib.orc_omega_w.restype = ctypes.c_double
+        lib.orc_omega_hat_w.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int]
+        lib.orc_omega_hat_w.restype = ctypes.c_double
+        lib.orc_phi_hat_w.argtypes = [ctypes.c_int, ctypes.c_double, i64, ctypes.c_int,
+                                      ctypes.c_double]
+        lib.orc_phi_hat_w.restype = ctypes.c_double
         lib.orc_nnfft_alg22.argtypes = [ctypes.POINTER(Params), i64, dptr, dptr, i64, dptr,
                                         dptr, dptr, dptr, ctypes.c_int]
         lib.orc_nnfft_alg22_adjoint.argtypes = [ctypes.POINTER(Params), i64, dptr, i64, dptr,
@@ -246,13 +257,42 @@ def phi_hat(v, Nj, m, beta):
         np.asarray(v, float))
 
 
-def make_params(N, sigma1=2.0, sigma2=2.0, m1=4, m2=None):
-    """Parameters of Algorithm 2.2 for nodes in [-1/2,1/2] (Section 2) -> Params or ValueError."""
+WINDOWS = {"sinh": 0, "kaiser_bessel": 1, "bspline": 2, "algebraic": 3}
+
+
+def omega(window, x, beta, m):
+    """Window omega of the set Omega (Section 2): 'sinh' (Example 2.1 / Section 4),
+    'kaiser_bessel', 'bspline' or 'algebraic' (Example 2.1), vectorised over x."""
+    lib = _load()
+    w = WINDOWS[window]
+    return np.vectorize(lambda t: lib.orc_omega_w(w, float(t), float(beta), int(m)))(
+        np.asarray(x, float))
+
+
+def omega_hat(window, v, beta, m):
+    """Fourier transform of omega(window, ., beta, m) by its closed form (vectorised)."""
+    lib = _load()
+    w = WINDOWS[window]
+    return np.vectorize(lambda t: lib.orc_omega_hat_w(w, float(t), float(beta), int(m)))(
+        np.asarray(v, float))
+
+
+def phi_hat_w(window, v, Nj, m, beta):
+    """phihat_j(v) = (m_j/N_j) omegahat(m_j v / N_j) for any window (vectorised over v)."""
+    lib = _load()
+    w = WINDOWS[window]
+    return np.vectorize(lambda t: lib.orc_phi_hat_w(w, float(t), int(Nj), int(m), float(beta)))(
+        np.asarray(v, float))
+
+
+def make_params(N, sigma1=2.0, sigma2=2.0, m1=4, m2=None, window="sinh"):
+    """Parameters of Algorithm 2.2 for nodes in [-1/2,1/2] (Section 2) -> Params or ValueError.
+    ``window`` selects the window of both steps (see omega); Algorithm 2.2 then uses it."""
     lib = _load()
     m2 = m1 if m2 is None else m2
     P = Params()
-    rc = lib.orc_make_params(int(N), float(sigma1), float(sigma2), int(m1), int(m2),
-                             ctypes.byref(P))
+    rc = lib.orc_make_params_w(int(N), float(sigma1), float(sigma2), int(m1), int(m2),
+                               WINDOWS[window], ctypes.byref(P))
     if rc != 0:
         raise ValueError("invalid NNFFT parameters")
     return P

@@ -29,6 +29,10 @@
  *                       Algorithm 2.2 step by step (a naive DFT for step 3) and
  *                       its exact transpose.
  *   - orc_bound_sinh    the error constant E(phi_sinh) of Theorem 4.1.
+ *   - orc_omega_kb, orc_omega_bspline, orc_omega_alg (and their transforms)
+ *                       the other windows of Section 2 (Example 2.1: B-spline and
+ *                       algebraic; the Kaiser-Bessel window of Fig. 4.1(b)), used by
+ *                       Algorithm 2.2 through the window id of the parameters.
  *   - orc_cc_weights, orc_cc_bound
  *                       Clenshaw-Curtis weights, eq. (5.4), and the bound of
  *                       Theorem 5.3.
@@ -286,12 +290,115 @@ double orc_omega_sinh_hat(double v, double beta) {
     return pref * j1(r) / r;
 }
 
-/* Scaled windows of eq. (2.5): phi(t) = omega(N t / m), phihat(v) = (m/N) omegahat(m v / N). */
-double orc_phi(double t, i64 Nj, int m, double beta) {
-    return orc_omega_sinh((double)Nj * t / (double)m, beta);
+/* ------------------------------------------------------------------------ */
+/* The other windows of the set Omega (Section 2).                             */
+/* Window ids: 0 sinh-type (above), 1 Kaiser-Bessel, 2 B-spline, 3 algebraic. */
+/* ------------------------------------------------------------------------ */
+
+/* I0(z) = sum_k (z/2)^{2k} / (k!)^2 (all terms positive). */
+static double orc_i0(double z) {
+    double q = 0.25 * z * z, term = 1.0, sum = 1.0;
+    for (int k = 1; k < 4000; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
 }
+
+/* Kaiser-Bessel window on [-1, 1]: omega(x) = I0(beta sqrt(1 - x^2)) / I0(beta) (the standard
+ * window the paper's Fig. 4.1(b) uses beside the sinh-type one; shape parameter as there,
+ * beta = 2 pi m (1 - 1/(2 sigma))).  Its Fourier transform 2 int_0^1 omega(x) cos(2 pi v x) dx:
+ *   q = beta^2 - 4 pi^2 v^2 > 0:  (2 / I0(beta)) sinh(sqrt q) / sqrt q,
+ *   q = 0:                         2 / I0(beta),
+ *   q < 0:                         (2 / I0(beta)) sin(sqrt(-q)) / sqrt(-q). */
+double orc_omega_kb(double x, double beta) {
+    if (!(fabs(x) <= 1.0)) return 0.0;
+    return orc_i0(beta * sqrt(1.0 - x * x)) / orc_i0(beta);
+}
+double orc_omega_kb_hat(double v, double beta) {
+    double q = beta * beta - 4.0 * M_PI * M_PI * v * v;
+    double c = 2.0 / orc_i0(beta);
+    if (q > 0.0) { double r = sqrt(q); return c * sinh(r) / r; }
+    if (q == 0.0) return c;
+    double r = sqrt(-q);
+    return c * sin(r) / r;
+}
+
+/* Centered cardinal B-spline B_n of order n (degree n - 1, support [-n/2, n/2]) at t, by
+ * the Cox-de Boor recursion on the integer knots -n/2, ..., n/2 (positive terms only). */
+static double orc_bspline(int n, double t) {
+    double N_[64];
+    if (n < 1 || n > 63) return 0.0;
+    double a = -0.5 * n;                               /* knot i is a + i */
+    if (!(t >= a && t < -a)) return 0.0;
+    for (int i = 0; i < n; ++i) N_[i] = (t >= a + i && t < a + i + 1) ? 1.0 : 0.0;
+    for (int k = 1; k < n; ++k)                        /* degree k */
+        for (int i = 0; i + k < n; ++i)
+            N_[i] = ((t - (a + i)) * N_[i] + ((a + i + k + 1) - t) * N_[i + 1]) / (double)k;
+    return N_[0];
+}
+
+/* B-spline window of Example 2.1: omega(x) = B_{2m}(m x) / B_{2m}(0), and its Fourier
+ * transform omegahat(v) = (sinc(pi v / m))^{2m} / (m B_{2m}(0)), sinc(y) = sin(y)/y. */
+double orc_omega_bspline(double x, int m) {
+    return orc_bspline(2 * m, (double)m * x) / orc_bspline(2 * m, 0.0);
+}
+double orc_omega_bspline_hat(double v, int m) {
+    double y = M_PI * v / (double)m;
+    double sc = y == 0.0 ? 1.0 : sin(y) / y;
+    return pow(sc, 2 * m) / ((double)m * orc_bspline(2 * m, 0.0));
+}
+
+/* Algebraic window of Example 2.1 (beta = 3 m, beta integral): omega(x) = (1 - x^2)^{beta - 1/2}
+ * on [-1, 1], with omegahat(v) = pi (2 beta)! / (4^beta beta!) (pi v)^{-beta} J_beta(2 pi v), the
+ * last factor by its power series sum_k (-1)^k (pi v)^{2k} / (k! (k + beta)!) (value 1/beta!
+ * at v = 0).  The alternating series loses accuracy for large pi |v| against beta; the
+ * arguments used here (|v| <= m / (2 sigma)) keep pi |v| below about 2 sqrt(beta). */
+double orc_omega_alg(double x, double beta) {
+    if (!(fabs(x) < 1.0)) return 0.0;
+    return pow(1.0 - x * x, beta - 0.5);
+}
+double orc_omega_alg_hat(double v, double beta) {
+    int b = (int)floor(beta + 0.5);
+    double x2 = (M_PI * v) * (M_PI * v);
+    double term = 1.0, sum = 1.0;                      /* terms scaled by beta! */
+    for (int k = 1; k < 2000; ++k) {
+        term *= -x2 / ((double)k * (double)(k + b));
+        sum += term;
+        if (fabs(term) < 1e-18 * fabs(sum) && k > 4) break;
+    }
+    double logc = log(M_PI) + lgamma(2.0 * b + 1.0) - b * log(4.0) - 2.0 * lgamma(b + 1.0);
+    return exp(logc) * sum;
+}
+
+double orc_omega_w(int window, double x, double beta, int m) {
+    switch (window) {
+        case 1: return orc_omega_kb(x, beta);
+        case 2: return orc_omega_bspline(x, m);
+        case 3: return orc_omega_alg(x, beta);
+        default: return orc_omega_sinh(x, beta);
+    }
+}
+double orc_omega_hat_w(int window, double v, double beta, int m) {
+    switch (window) {
+        case 1: return orc_omega_kb_hat(v, beta);
+        case 2: return orc_omega_bspline_hat(v, m);
+        case 3: return orc_omega_alg_hat(v, beta);
+        default: return orc_omega_sinh_hat(v, beta);
+    }
+}
+
+/* Scaled windows of eq. (2.5): phi(t) = omega(N t / m), phihat(v) = (m/N) omegahat(m v / N). */
+double orc_phi_w(int window, double t, i64 Nj, int m, double beta) {
+    return orc_omega_w(window, (double)Nj * t / (double)m, beta, m);
+}
+double orc_phi_hat_w(int window, double v, i64 Nj, int m, double beta) {
+    return ((double)m / (double)Nj) * orc_omega_hat_w(window, (double)m * v / (double)Nj, beta, m);
+}
+double orc_phi(double t, i64 Nj, int m, double beta) { return orc_phi_w(0, t, Nj, m, beta); }
 double orc_phi_hat(double v, i64 Nj, int m, double beta) {
-    return ((double)m / (double)Nj) * orc_omega_sinh_hat((double)m * v / (double)Nj, beta);
+    return orc_phi_hat_w(0, v, Nj, m, beta);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -310,6 +417,7 @@ typedef struct {
     int m1, m2;
     double sigma1, sigma2;   /* effective */
     double beta1, beta2, a;
+    int window;              /* 0 sinh-type, 1 Kaiser-Bessel, 2 B-spline, 3 algebraic */
 } orc_params;
 
 static int is_5smooth(i64 n) {
@@ -342,6 +450,20 @@ int orc_make_params(i64 N, double sigma1, double sigma2, int m1, int m2, orc_par
     return 0;
 }
 
+/* The same parameters for another window of Omega: Kaiser-Bessel keeps the sinh-type shape
+ * parameter, the B-spline has none (beta = 0), the algebraic window takes beta = 3 m and
+ * needs sigma > pi / 3 (Example 2.1). */
+int orc_make_params_w(i64 N, double sigma1, double sigma2, int m1, int m2, int window,
+                      orc_params *P) {
+    if (window < 0 || window > 3) return 1;
+    if (window == 3 && (!(sigma1 > M_PI / 3.0) || !(sigma2 > M_PI / 3.0))) return 1;
+    int rc = orc_make_params(N, sigma1, sigma2, m1, m2, P);
+    P->window = window;
+    if (window == 2) P->beta1 = P->beta2 = 0.0;
+    if (window == 3) { P->beta1 = 3.0 * m1; P->beta2 = 3.0 * m2; }
+    return rc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 2.2 (NNFFT), step by step, for v_k, x_j in [-1/2,1/2]:           */
 /*   rescale v*_k = (N/N*) v_k so that N v_k = N* v*_k (after eq. (2.7));      */
@@ -366,7 +488,7 @@ static void alg22_spread_v(const orc_params *P, i64 M1, const double *v, const d
         i64 lo = (i64)ceil(u - m1), hi = (i64)floor(u + m1);
         for (i64 l = lo; l <= hi; ++l) {
             if (l < -K1 / 2 || l >= K1 / 2) continue;      /* outside I_{K1} */
-            double w = orc_phi((double)l / (double)N1 - vs, N1, m1, P->beta1);
+            double w = orc_phi_w(P->window, (double)l / (double)N1 - vs, N1, m1, P->beta1);
             g[2 * (l + K1 / 2)]     += f[2 * k] * w / (double)N1;
             g[2 * (l + K1 / 2) + 1] += f[2 * k + 1] * w / (double)N1;
         }
@@ -407,7 +529,7 @@ int orc_nnfft_alg22(const orc_params *P, i64 M1, const double *v, const double *
     if (g_out) memcpy(g_out, g, sizeof(double) * 2 * K1);
     /* step 2: ghat_l = g_l / phi2hat(l) */
     for (i64 li = 0; li < K1; ++li) {
-        double ph = orc_phi_hat((double)(li - K1 / 2), N2, P->m2, P->beta2);
+        double ph = orc_phi_hat_w(P->window, (double)(li - K1 / 2), N2, P->m2, P->beta2);
         g[2 * li] /= ph; g[2 * li + 1] /= ph;
     }
     /* step 3: h_s = (1/N2) sum_l ghat_l exp(-2 pi i l s / N2) */
@@ -422,12 +544,12 @@ int orc_nnfft_alg22(const orc_params *P, i64 M1, const double *v, const double *
         i64 lo = (i64)ceil(u - m2), hi = (i64)floor(u + m2);
         double sr = 0, si = 0;
         for (i64 s = lo; s <= hi; ++s) {
-            double w = orc_phi(xs - (double)s / (double)N2, N2, m2, P->beta2);
+            double w = orc_phi_w(P->window, xs - (double)s / (double)N2, N2, m2, P->beta2);
             i64 si_ = ((s % N2) + N2 + N2 / 2) % N2;          /* centered index of s mod N2 */
             sr += h[2 * si_] * w;
             si += h[2 * si_ + 1] * w;
         }
-        double ph1 = orc_phi_hat((double)P->Nstar * x[j], N1, P->m1, P->beta1);
+        double ph1 = orc_phi_hat_w(P->window, (double)P->Nstar * x[j], N1, P->m1, P->beta1);
         out[2 * j] = sr / ph1;
         out[2 * j + 1] = si / ph1;
     }
@@ -449,13 +571,13 @@ int orc_nnfft_alg22_adjoint(const orc_params *P, i64 M1, const double *v, i64 M2
     double *G = (double *)calloc(2 * K1, sizeof(double));
     if (!H || !G) { free(H); free(G); return 2; }
     for (i64 j = 0; j < M2; ++j) {
-        double ph1 = orc_phi_hat((double)P->Nstar * x[j], N1, m1, P->beta1);
+        double ph1 = orc_phi_hat_w(P->window, (double)P->Nstar * x[j], N1, m1, P->beta1);
         double gr = gin[2 * j] / ph1, gi = gin[2 * j + 1] / ph1;
         double xs = x[j] * (double)P->Nstar / (double)N1;
         double u = (double)N2 * xs;
         i64 lo = (i64)ceil(u - m2), hi = (i64)floor(u + m2);
         for (i64 s = lo; s <= hi; ++s) {
-            double w = orc_phi(xs - (double)s / (double)N2, N2, m2, P->beta2);
+            double w = orc_phi_w(P->window, xs - (double)s / (double)N2, N2, m2, P->beta2);
             i64 si_ = ((s % N2) + N2 + N2 / 2) % N2;
             H[2 * si_] += gr * w;
             H[2 * si_ + 1] += gi * w;
@@ -463,7 +585,7 @@ int orc_nnfft_alg22_adjoint(const orc_params *P, i64 M1, const double *v, i64 M2
     }
     dft_centered(N2, K1, N2, +1, H, G, nthreads);
     for (i64 li = 0; li < K1; ++li) {
-        double ph = orc_phi_hat((double)(li - K1 / 2), N2, m2, P->beta2);
+        double ph = orc_phi_hat_w(P->window, (double)(li - K1 / 2), N2, m2, P->beta2);
         G[2 * li] /= ((double)N2 * ph);
         G[2 * li + 1] /= ((double)N2 * ph);
     }
@@ -474,7 +596,7 @@ int orc_nnfft_alg22_adjoint(const orc_params *P, i64 M1, const double *v, i64 M2
         double zr = 0, zi = 0;
         for (i64 l = lo; l <= hi; ++l) {
             if (l < -K1 / 2 || l >= K1 / 2) continue;
-            double w = orc_phi((double)l / (double)N1 - vs, N1, m1, P->beta1);
+            double w = orc_phi_w(P->window, (double)l / (double)N1 - vs, N1, m1, P->beta1);
             zr += G[2 * (l + K1 / 2)] * w;
             zi += G[2 * (l + K1 / 2) + 1] * w;
         }

@@ -450,3 +450,76 @@ def test_bessel_envelope_used_for_the_tail():
     sp = pytest.importorskip("scipy.special")
     s = np.linspace(0.01, 2000.0, 400001)
     assert np.all(np.abs(sp.j1(s)) <= 1.04 * np.sqrt(2 / (np.pi * s)))
+
+
+# --------------------------------------------------------------------------------------
+# The other windows of Section 2 (Example 2.1: B-spline, algebraic; the Kaiser-Bessel window
+# of Fig. 4.1(b)) and Algorithm 2.2 with them
+# --------------------------------------------------------------------------------------
+WINDOWS = ["sinh", "kaiser_bessel", "bspline", "algebraic"]
+
+
+@pytest.mark.parametrize("window", WINDOWS)
+@pytest.mark.parametrize("m,sigma", [(2, 1.5), (4, 2.0), (6, 1.25), (8, 2.0)])
+def test_window_belongs_to_omega_and_transform_matches_quadrature(window, m, sigma):
+    """Each window is even, 1 at 0, decreasing on [0, 1], zero outside [-1, 1]; its closed-form
+    Fourier transform equals 2 int_0^1 omega(x) cos(2 pi v x) dx (scipy quadrature) and is
+    positive and decreasing on [0, m/(2 sigma)] (the set Omega of Section 2)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    P = oracle.make_params(64, sigma, sigma, m, m, window=window)
+    beta = P.beta1
+    xs = np.linspace(0, 1, 101)
+    w = oracle.omega(window, xs, beta, m)
+    assert w[0] == 1.0 and np.all(np.diff(w) <= 0)
+    assert np.allclose(oracle.omega(window, -xs, beta, m), w, rtol=0, atol=0)
+    assert np.all(oracle.omega(window, [1.0001, 1.5, -2.0], beta, m) == 0.0)
+    vs = np.linspace(0, m / (2 * P.sigma1), 9)
+    wh = oracle.omega_hat(window, vs, beta, m)
+    assert np.all(wh > 0) and np.all(np.diff(wh) < 0)
+    for v in (0.0, 0.3, m / (4 * P.sigma1), m / (2 * P.sigma1)):
+        q, _ = integrate.quad(lambda x: 2 * oracle.omega(window, x, beta, m) * math.cos(2 * math.pi * v * x),
+                              0, 1, limit=400, epsabs=1e-15, epsrel=1e-13)
+        assert abs(oracle.omega_hat(window, v, beta, m) - q) < 1e-12 * max(1.0, abs(q)), (v, q)
+
+
+def test_bspline_window_normalisation_from_textbook_values():
+    """omegahat_B(0) = 1 / (m B_{2m}(0)) with the centered cardinal B-spline values
+    B_4(0) = 2/3, B_6(0) = 11/20, B_8(0) = 151/315, B_10(0) = 15619/36288."""
+    for m, b0 in ((2, 2 / 3), (3, 11 / 20), (4, 151 / 315), (5, 15619 / 36288)):
+        assert abs(1.0 / (m * float(oracle.omega_hat("bspline", 0.0, 0.0, m))) - b0) < 1e-14
+    # omega_B(x) = B_{2m}(m x) / B_{2m}(0): at x = 1/m the value B_4(1)/B_4(0) = (1/6)/(2/3)
+    assert abs(float(oracle.omega("bspline", 0.5, 0.0, 2)) - 0.25) < 1e-15
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_algebraic_and_kaiser_bessel_against_scipy_bessel(m):
+    """The algebraic window's transform against scipy's J_beta (beta = 3m) closed form of
+    Example 2.1; the Kaiser-Bessel window against scipy's I0."""
+    sp = pytest.importorskip("scipy.special")
+    beta = 3 * m
+    for v in (0.05, 0.4, m / 4):
+        want = (math.pi * math.factorial(2 * beta) / (4 ** beta * math.factorial(beta))
+                * (math.pi * v) ** (-beta) * sp.jv(beta, 2 * math.pi * v))
+        assert abs(float(oracle.omega_hat("algebraic", v, beta, m)) - want) < 1e-12 * want
+    P = oracle.make_params(64, 2.0, 2.0, m, m, window="kaiser_bessel")
+    for x in (0.0, 0.3, 0.8, 0.99):
+        want = sp.i0(P.beta1 * math.sqrt(1 - x * x)) / sp.i0(P.beta1)
+        assert abs(float(oracle.omega("kaiser_bessel", x, P.beta1, m)) - want) < 1e-13
+
+
+@pytest.mark.parametrize("window", WINDOWS)
+def test_alg22_with_each_window_converges_to_the_direct_sum(window):
+    """Algorithm 2.2 with each window approximates eq. (1.2); the error falls with m, fastest
+    for the sinh-type and Kaiser-Bessel windows (exponential in m), which reach 1e-11 at m = 8."""
+    N, M = 128, 300
+    v, x, f = W.nnfft_inputs(M, M, 17)
+    y = oracle.nnfft_direct(N, v, f, x)
+    errs = []
+    for m in (2, 4, 6, 8):
+        P = oracle.make_params(N, 2.0, 2.0, m, m, window=window)
+        errs.append(oracle.relative_error(oracle.nnfft_alg22(P, v, f, x), y, f))
+    assert all(e2 < 0.5 * e1 for e1, e2 in zip(errs, errs[1:])), errs
+    if window in ("sinh", "kaiser_bessel"):
+        assert errs[-1] < 1e-11
+    else:
+        assert errs[-1] < 1e-4
