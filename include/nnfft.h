@@ -73,6 +73,7 @@ typedef struct {
     int64_t ncell1, ncell2;          /* node cells (bins) of the v side and the x side        */
     int64_t fft_n1, fft_n2;          /* N2 = fft_n1 * fft_n2 (four-step split)                */
     int arith;                       /* NNFFT_ARITH_* used by the point kernels (nnfft_plan only) */
+    int window;                      /* NNFFT_WINDOW_* of both steps                           */
 } nnfft_info;
 
 /*
@@ -126,6 +127,43 @@ int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2,
 int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
                      const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
                      nnfft_dtype dtype, void *stream);
+
+/*
+ * Window functions (Section 2): the set Omega of even windows supported on [-1, 1].
+ *   NNFFT_WINDOW_SINH:           sinh(beta sqrt(1 - x^2)) / sinh(beta), beta = 2 pi m (1 - 1/(2 sigma))
+ *                                (Example 2.1, Section 4; the default of nnfft_plan);
+ *   NNFFT_WINDOW_KAISER_BESSEL:  I0(beta sqrt(1 - x^2)) / I0(beta), the same beta (the standard
+ *                                window beside which the paper's Fig. 4.1(b) plots the sinh bound);
+ *   NNFFT_WINDOW_BSPLINE:        B_{2m}(m x) / B_{2m}(0), the centered cardinal B-spline of order 2m
+ *                                (Example 2.1; beta = 0 is reported);
+ *   NNFFT_WINDOW_ALGEBRAIC:      (1 - x^2)^{beta - 1/2}, beta = 3 m (Example 2.1; sigma1, sigma2 must
+ *                                exceed pi/3).
+ * Every window enters the kernels through the same per-cell Chebyshev fits of its 2m taps and
+ * the same deconvolution tables (built from its closed-form Fourier transform), so every other
+ * call works unchanged.  Only the sinh-type window carries the bound of Theorem 4.1; the
+ * B-spline and algebraic windows converge algebraically in m (errors about 3e-9 and 1e-8 at
+ * m = 8, sigma = 2, N = 128 in the oracle's Algorithm 2.2), the Kaiser-Bessel window like the
+ * sinh-type one.
+ */
+enum {
+    NNFFT_WINDOW_SINH = 0,
+    NNFFT_WINDOW_KAISER_BESSEL = 1,
+    NNFFT_WINDOW_BSPLINE = 2,
+    NNFFT_WINDOW_ALGEBRAIC = 3
+};
+/* nnfft_plan / nnfft_batch_plan / nnfft_params with a window; EINVAL for an unknown window or
+ * the algebraic window with sigma_j <= pi/3. */
+int nnfft_plan_window(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigma1,
+                      double sigma2, int m1, int m2, nnfft_dtype dtype, int window, void *stream);
+int nnfft_batch_plan_window(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
+                            const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
+                            nnfft_dtype dtype, int window, void *stream);
+int nnfft_params_window(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, int m1,
+                        int m2, int dtype, int window, nnfft_info *out);
+/* Host-only: the window's value omega(x) and Fourier transform omegahat(v) (2 int_0^1 omega(x)
+ * cos(2 pi v x) dx, closed forms) for truncation m and oversampling sigma. */
+int nnfft_window(int window, int m, double sigma, double x, double v, double *omega_x,
+                 double *omega_hat_v);
 
 /*
  * nnfft_set_sizes: use a single-instance plan for M1 <= (M1 at creation) frequency nodes

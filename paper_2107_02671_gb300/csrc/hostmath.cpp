@@ -39,6 +39,80 @@ double omega_sinh_hat(double v, double beta) {
     return pref * ::j1(r) / r;
 }
 
+// Centered cardinal B-spline M_n(t) of order n (support [-n/2, n/2]) from the two-sided
+// recursion M_k(s) = ((k/2 + s) M_{k-1}(s + 1/2) + (k/2 - s) M_{k-1}(s - 1/2)) / (k - 1):
+// level k holds M_k at the offsets t + (j - (n - k)/2), j = 0..n-k, built up from the box
+// M_1 (1 on [-1/2, 1/2), 0 elsewhere).
+static double cardinal_bspline(int n, double t) {
+    if (n < 1 || n > 62 || !(std::fabs(t) < 0.5 * n)) return 0.0;
+    std::vector<double> lev((size_t)n);
+    for (int j = 0; j < n; ++j) {                 // order 1 at t + j - (n - 1)/2
+        const double s = t + j - 0.5 * (n - 1);
+        lev[(size_t)j] = (s >= -0.5 && s < 0.5) ? 1.0 : 0.0;
+    }
+    for (int k = 2; k <= n; ++k) {                // order k at t + j - (n - k)/2, j <= n - k
+        for (int j = 0; j + k <= n; ++j) {
+            const double s = t + j - 0.5 * (n - k);
+            lev[(size_t)j] = ((0.5 * k + s) * lev[(size_t)j + 1] + (0.5 * k - s) * lev[(size_t)j]) /
+                             (double)(k - 1);
+        }
+    }
+    return lev[0];
+}
+
+double window_beta(int win, int m, double sigma) {
+    switch (win) {
+        case WIN_BSPLINE: return 0.0;
+        case WIN_ALG: return 3.0 * m;
+        default: return 2.0 * PI * m * (1.0 - 1.0 / (2.0 * sigma));
+    }
+}
+
+double omega_w(int win, double x, double beta, int m) {
+    switch (win) {
+        case WIN_KB: {
+            if (!(std::fabs(x) <= 1.0)) return 0.0;
+            return std::cyl_bessel_i(0.0, beta * std::sqrt(1.0 - x * x)) / std::cyl_bessel_i(0.0, beta);
+        }
+        case WIN_BSPLINE:
+            return cardinal_bspline(2 * m, m * x) / cardinal_bspline(2 * m, 0.0);
+        case WIN_ALG:
+            if (!(std::fabs(x) < 1.0)) return 0.0;
+            return std::exp((beta - 0.5) * std::log1p(-x * x));
+        default:
+            return omega_sinh(x, beta);
+    }
+}
+
+double omega_hat_w(int win, double v, double beta, int m) {
+    switch (win) {
+        case WIN_KB: {
+            // 2 int_0^1 I0(beta sqrt(1-x^2)) cos(2 pi v x) dx / I0(beta)
+            const double q = beta * beta - 4.0 * PI * PI * v * v;
+            const double c = 2.0 / std::cyl_bessel_i(0.0, beta);
+            if (q > 0.0) { const double r = std::sqrt(q); return c * std::sinh(r) / r; }
+            if (q == 0.0) return c;
+            const double r = std::sqrt(-q);
+            return c * std::sin(r) / r;
+        }
+        case WIN_BSPLINE: {
+            const double y = PI * v / m;
+            const double sc = y == 0.0 ? 1.0 : std::sin(y) / y;
+            return std::pow(sc, 2 * m) / (m * cardinal_bspline(2 * m, 0.0));
+        }
+        case WIN_ALG: {
+            // pi (2 beta)! / (4^beta beta!) (pi v)^{-beta} J_beta(2 pi v), 1/beta! at v = 0
+            const double lc = std::log(PI) + std::lgamma(2.0 * beta + 1.0) - beta * std::log(4.0) -
+                              std::lgamma(beta + 1.0);
+            if (v == 0.0) return std::exp(lc - std::lgamma(beta + 1.0));
+            const double a = PI * std::fabs(v);
+            return std::exp(lc - beta * std::log(a)) * std::cyl_bessel_j(beta, 2.0 * a);
+        }
+        default:
+            return omega_sinh_hat(v, beta);
+    }
+}
+
 bool smooth5(int64_t n) {
     if (n <= 0) return false;
     const int64_t p[3] = {2, 3, 5};
@@ -47,8 +121,12 @@ bool smooth5(int64_t n) {
     return n == 1;
 }
 
-const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *o) {
+const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *o,
+                   int window) {
     if (N < 1) return "N must be >= 1";
+    if (window < WIN_SINH || window > WIN_ALG) return "unknown window";
+    if (window == WIN_ALG && (!(sigma1 > PI / 3.0) || !(sigma2 > PI / 3.0)))
+        return "the algebraic window needs sigma1, sigma2 > pi/3";
     if (!(sigma1 > 1.0) || !(sigma2 > 1.0)) return "sigma1 and sigma2 must be > 1";
     if (!(sigma1 <= 16.0) || !(sigma2 <= 16.0)) return "sigma1 and sigma2 must be <= 16";
     if (m1 < 2 || m2 < 2) return "m1 and m2 must be >= 2";
@@ -70,8 +148,9 @@ const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Deri
     o->N2 = n2;
     o->sigma1 = (double)o->N1 / (double)o->Nstar;
     o->sigma2 = (double)o->N2 / (double)o->K1;
-    o->beta1 = 2.0 * PI * m1 * (1.0 - 1.0 / (2.0 * o->sigma1));
-    o->beta2 = 2.0 * PI * m2 * (1.0 - 1.0 / (2.0 * o->sigma2));
+    o->window = window;
+    o->beta1 = window_beta(window, m1, o->sigma1);
+    o->beta2 = window_beta(window, m2, o->sigma2);
     if (o->N2 > (int64_t(1) << 20)) return "N2 exceeds 2^20 (N too large for the grid FFT)";
     if ((double)(2 * m2) > (1.0 - 1.0 / o->sigma1) * (double)o->N2)
         return "step 4 of Algorithm 2.2 needs 2 m2 <= (1 - 1/sigma1) N2";
@@ -94,14 +173,14 @@ double cheb_eval(const double *c, int n, double y) {
     return y * b1 - b2 + c[0];
 }
 
-double fit_taps(int m, double beta, int D, std::vector<double> &coef) {
+double fit_taps(int m, double beta, int D, std::vector<double> &coef, int win) {
     coef.assign((size_t)2 * m * D, 0.0);
     double err = 0.0;
     constexpr int G = 241;
     for (int t = 0; t < 2 * m; ++t) {
         auto f = [&](double y) {
             const double z = 0.5 * (y + 1.0);
-            return omega_sinh((t - m + 1 - z) / m, beta);
+            return omega_w(win, (t - m + 1 - z) / m, beta, m);
         };
         double *c = coef.data() + (size_t)t * D;
         cheb_interp(f, D, c);
@@ -114,15 +193,15 @@ double fit_taps(int m, double beta, int D, std::vector<double> &coef) {
 }
 
 int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
-                  std::vector<double> &coef) {
+                  std::vector<double> &coef, int win) {
     static const int cand[] = {8, 10, 12, 14, 16, 20};
     std::vector<double> tmp;
-    const double floor_err = fit_taps(m, beta, 24, tmp);
+    const double floor_err = fit_taps(m, beta, 24, tmp, win);
     const double e1 = window_error_term(m, sigma);
     const double target = fp64 ? 1e-3 * e1 : std::fmax(1e-2 * e1, 5e-8);
     const double accept = std::fmax(target, 1.5 * floor_err);
     for (int D : cand) {
-        const double err = fit_taps(m, beta, D, coef);
+        const double err = fit_taps(m, beta, D, coef, win);
         if (err <= accept || D == 20) {
             *fit_err = err;
             return D;

@@ -18,13 +18,25 @@ double omega_sinh(double x, double beta);
 // series (all terms positive); beyond the branch point via J1.
 double omega_sinh_hat(double v, double beta);
 
+// Windows of the set Omega (Section 2): 0 sinh-type, 1 Kaiser-Bessel (I0(beta sqrt(1-x^2)) /
+// I0(beta), shape parameter as for sinh), 2 B-spline B_{2m}(m x) / B_{2m}(0) (Example 2.1, no
+// shape parameter), 3 algebraic (1 - x^2)^{beta - 1/2} with beta = 3m (Example 2.1, needs
+// sigma > pi/3).  omega_w and omega_hat_w evaluate any of them and its Fourier transform.
+enum { WIN_SINH = 0, WIN_KB = 1, WIN_BSPLINE = 2, WIN_ALG = 3 };
+double omega_w(int win, double x, double beta, int m);
+double omega_hat_w(int win, double v, double beta, int m);
+// The window's shape parameter for truncation m and oversampling sigma.
+double window_beta(int win, int m, double sigma);
+
 struct Derived {
     int64_t N, Nstar, N1, K1, N2;
     int m1, m2;
     double sigma1, sigma2, beta1, beta2;
+    int window;
 };
 // Section 2 / Section 4 parameter rules; returns an error message or nullptr.
-const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *out);
+const char *derive(int64_t N, double sigma1, double sigma2, int m1, int m2, Derived *out,
+                   int window = WIN_SINH);
 
 // Theorem 4.1's first term (24 m^{3/2} + 10) exp(-2 pi m sqrt(1 - 1/sigma)).
 double window_error_term(int m, double sigma);
@@ -46,11 +58,11 @@ double cheb_eval(const double *c, int n, double y);
 
 // Fit the 2m tap functions w_t(y) = omega((t - m + 1 - (y+1)/2)/m) with D
 // coefficients each (row-major [t][d]); returns the max abs error on a test grid.
-double fit_taps(int m, double beta, int D, std::vector<double> &coef);
+double fit_taps(int m, double beta, int D, std::vector<double> &coef, int win = WIN_SINH);
 // Pick the coefficient count D for a window: the smallest supported D whose fit
 // error is below the target for the dtype (or at the window's floor).
 int choose_degree(int m, double sigma, double beta, bool fp64, double *fit_err,
-                  std::vector<double> &coef);
+                  std::vector<double> &coef, int win = WIN_SINH);
 
 // n-point Gauss-Legendre rule on [-1/2, 1/2] (Newton on the Legendre recurrence).
 void gauss_legendre(int64_t n, double *tau, double *w);

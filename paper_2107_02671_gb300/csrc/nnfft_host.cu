@@ -233,13 +233,13 @@ std::vector<double> twiddles(int64_t n) {
 
 int fill_info(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, int m1, int m2,
               nnfft_dtype dtype, nnfft_info *info, hm::Derived *d, std::vector<double> *coef1,
-              std::vector<double> *coef2) {
+              std::vector<double> *coef2, int window = NNFFT_WINDOW_SINH) {
     if (!info) return fail(NNFFT_EINVAL, "null output pointer");
     if (M1 < 0 || M2 < 0) return fail(NNFFT_EINVAL, "M1 and M2 must be >= 0");
     if (M1 > (int64_t(1) << 30) || M2 > (int64_t(1) << 30))
         return fail(NNFFT_EINVAL, "M1 and M2 must be <= 2^30");
     if (dtype != NNFFT_C64 && dtype != NNFFT_C128) return fail(NNFFT_EINVAL, "unknown dtype");
-    const char *msg = hm::derive(N, sigma1, sigma2, m1, m2, d);
+    const char *msg = hm::derive(N, sigma1, sigma2, m1, m2, d, window);
     if (msg) return fail(NNFFT_EINVAL, msg);
     memset(info, 0, sizeof(*info));
     info->N = d->N;
@@ -256,12 +256,13 @@ int fill_info(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, i
     info->beta1 = d->beta1;
     info->beta2 = d->beta2;
     info->dtype = (int)dtype;
+    info->window = window;
     const bool fp64 = dtype == NNFFT_C128;
     std::vector<double> tmp1, tmp2;
     info->D1 = hm::choose_degree(m1, d->sigma1, d->beta1, fp64, &info->fit_err1,
-                                 coef1 ? *coef1 : tmp1);
+                                 coef1 ? *coef1 : tmp1, window);
     info->D2 = hm::choose_degree(m2, d->sigma2, d->beta2, fp64, &info->fit_err2,
-                                 coef2 ? *coef2 : tmp2);
+                                 coef2 ? *coef2 : tmp2, window);
     // cells: v side u = v * N1 N / N*, x side u = x * N2 N* / N1; |node| <= 1/2
     hm::CellMap c1, c2;
     if (!hm::cell_map(d->N1 * d->N, d->Nstar, &c1) || !hm::cell_map(d->N2 * d->Nstar, d->N1, &c2))
@@ -371,7 +372,7 @@ int upload_grid_tables(nnfft_plan_s *p, Side &S, int s, const void *coef_base, c
 // descriptors and block maps, and all device buffers.
 int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t *M1s,
                const int64_t *M2s, double sigma1, double sigma2, int m1, int m2,
-               nnfft_dtype dtype) {
+               nnfft_dtype dtype, int window) {
     int rc;
     p->ninst = count;
     p->sort_lsd = count > 1 ? 1 : 0;
@@ -382,7 +383,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
     long long Mtot[2] = {0, 0};
     for (int64_t i = 0; i < count; ++i) {
         rc = fill_info(Ns[i], M1s[i], M2s[i], sigma1, sigma2, m1, m2, dtype, &p->inst_info[(size_t)i],
-                       &H[(size_t)i].d, &H[(size_t)i].coef[0], &H[(size_t)i].coef[1]);
+                       &H[(size_t)i].d, &H[(size_t)i].coef[0], &H[(size_t)i].coef[1], window);
         if (rc) return count > 1 ? fail(rc, "instance " + std::to_string(i) + ": " + g_last_error) : rc;
         D[0] = std::max(D[0], (int)p->inst_info[(size_t)i].D1);
         D[1] = std::max(D[1], (int)p->inst_info[(size_t)i].D2);
@@ -394,8 +395,8 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
     // one degree per side for all instances: refit the instances that chose fewer terms
     for (int64_t i = 0; i < count; ++i) {
         nnfft_info &I = p->inst_info[(size_t)i];
-        if (I.D1 != D[0]) { I.fit_err1 = hm::fit_taps(m1, I.beta1, D[0], H[(size_t)i].coef[0]); I.D1 = D[0]; }
-        if (I.D2 != D[1]) { I.fit_err2 = hm::fit_taps(m2, I.beta2, D[1], H[(size_t)i].coef[1]); I.D2 = D[1]; }
+        if (I.D1 != D[0]) { I.fit_err1 = hm::fit_taps(m1, I.beta1, D[0], H[(size_t)i].coef[0], window); I.D1 = D[0]; }
+        if (I.D2 != D[1]) { I.fit_err2 = hm::fit_taps(m2, I.beta2, D[1], H[(size_t)i].coef[1], window); I.D2 = D[1]; }
     }
     if (!supported_degree(D[0]) || !supported_degree(D[1]))
         return fail(NNFFT_EINVAL, "unsupported window degree");
@@ -457,7 +458,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
         for (int64_t k = 0; k < I.K1; ++k) {
             const double l = (double)(k - I.K1 / 2);
             dec.push_back(1.0 / ((double)I.N1 * (double)m2 *
-                                 hm::omega_sinh_hat((double)m2 * l / (double)I.N2, I.beta2)));
+                                 hm::omega_hat_w(window, (double)m2 * l / (double)I.N2, I.beta2, m2)));
         }
     }
     void *dec_real = nullptr, *dec_df = nullptr;
@@ -498,7 +499,7 @@ int build_plan(nnfft_plan_s *p, int64_t count, const int64_t *Ns, const int64_t 
                     auto f = [&](double y) {
                         const double x = (cc + 0.5 * (y + 1.0)) / cm.scale;
                         const double w = (double)d.m1 * (double)d.Nstar * x / (double)d.N1;
-                        return (double)d.N1 / ((double)d.m1 * hm::omega_sinh_hat(w, d.beta1));
+                        return (double)d.N1 / ((double)d.m1 * hm::omega_hat_w(window, w, d.beta1, d.m1));
                     };
                     hm::cheb_interp(f, NR, rfit_all.data() + r0 + (size_t)ic * NR);
                 }
@@ -1168,15 +1169,33 @@ int nnfft_params(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2
     return fill_info(N, M1, M2, sigma1, sigma2, m1, m2, dtype, out, &d, nullptr, nullptr);
 }
 
+int nnfft_params_window(int64_t N, int64_t M1, int64_t M2, double sigma1, double sigma2, int m1,
+                        int m2, int dtype, int window, nnfft_info *out) {
+    hm::Derived d;
+    return fill_info(N, M1, M2, sigma1, sigma2, m1, m2, (nnfft_dtype)dtype, out, &d, nullptr,
+                     nullptr, window);
+}
+
+int nnfft_window(int window, int m, double sigma, double x, double v, double *omega_x,
+                 double *omega_hat_v) {
+    if (window < NNFFT_WINDOW_SINH || window > NNFFT_WINDOW_ALGEBRAIC || m < 2 || m > 16 ||
+        !(sigma > 1.0) || !omega_x || !omega_hat_v)
+        return fail(NNFFT_EINVAL, "invalid window arguments");
+    const double beta = hm::window_beta(window, m, sigma);
+    *omega_x = hm::omega_w(window, x, beta, m);
+    *omega_hat_v = hm::omega_hat_w(window, v, beta, m);
+    return NNFFT_OK;
+}
+
 int nnfft_gauss_legendre(int64_t n, double *tau_host, double *w_host) {
     if (n < 1 || !tau_host || !w_host) return fail(NNFFT_EINVAL, "invalid Gauss-Legendre request");
     hm::gauss_legendre(n, tau_host, w_host);
     return NNFFT_OK;
 }
 
-int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
-                     const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
-                     nnfft_dtype dtype, void *stream) {
+int nnfft_batch_plan_window(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
+                            const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
+                            nnfft_dtype dtype, int window, void *stream) {
     if (!out) return fail(NNFFT_EINVAL, "null plan pointer");
     *out = nullptr;
     if (count < 1 || !N || !M1 || !M2) return fail(NNFFT_EINVAL, "a plan needs >= 1 instance");
@@ -1208,15 +1227,29 @@ int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const i
         cudaGetLastError();
         return bail(fail(NNFFT_ENOMEM, "cudaMallocHost(status)"));
     }
-    if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype))) return bail(rc);
+    if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype, window))) return bail(rc);
     if (prepare_local_sort() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "sort setup"));
     *out = p;
     return NNFFT_OK;
 }
 
+int nnfft_batch_plan(nnfft_plan_t *out, int64_t count, const int64_t *N, const int64_t *M1,
+                     const int64_t *M2, double sigma1, double sigma2, int m1, int m2,
+                     nnfft_dtype dtype, void *stream) {
+    return nnfft_batch_plan_window(out, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype,
+                                   NNFFT_WINDOW_SINH, stream);
+}
+
 int nnfft_plan(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigma1,
                double sigma2, int m1, int m2, nnfft_dtype dtype, void *stream) {
-    return nnfft_batch_plan(out, 1, &N, &M1, &M2, sigma1, sigma2, m1, m2, dtype, stream);
+    return nnfft_batch_plan_window(out, 1, &N, &M1, &M2, sigma1, sigma2, m1, m2, dtype,
+                                   NNFFT_WINDOW_SINH, stream);
+}
+
+int nnfft_plan_window(nnfft_plan_t *out, int64_t N, int64_t M1, int64_t M2, double sigma1,
+                      double sigma2, int m1, int m2, nnfft_dtype dtype, int window, void *stream) {
+    return nnfft_batch_plan_window(out, 1, &N, &M1, &M2, sigma1, sigma2, m1, m2, dtype, window,
+                                   stream);
 }
 
 int nnfft_set_sizes(nnfft_plan_t p, int64_t M1, int64_t M2) {

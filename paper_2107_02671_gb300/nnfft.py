@@ -83,7 +83,7 @@ class Info(ctypes.Structure):
         ("fit_err1", ctypes.c_double), ("fit_err2", ctypes.c_double),
         ("ncell1", ctypes.c_int64), ("ncell2", ctypes.c_int64),
         ("fft_n1", ctypes.c_int64), ("fft_n2", ctypes.c_int64),
-        ("arith", ctypes.c_int),
+        ("arith", ctypes.c_int), ("window", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -109,6 +109,11 @@ def load_library(build_if_missing: bool = True):
         vp, i64, cint, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         P = ctypes.POINTER
         lib.nnfft_params.argtypes = [i64, i64, i64, dbl, dbl, cint, cint, cint, P(Info)]
+        lib.nnfft_params_window.argtypes = [i64, i64, i64, dbl, dbl, cint, cint, cint, cint, P(Info)]
+        lib.nnfft_plan_window.argtypes = [P(vp), i64, i64, i64, dbl, dbl, cint, cint, cint, cint, vp]
+        lib.nnfft_batch_plan_window.argtypes = [P(vp), i64, P(i64), P(i64), P(i64), dbl, dbl, cint,
+                                                cint, cint, cint, vp]
+        lib.nnfft_window.argtypes = [cint, cint, dbl, dbl, dbl, P(dbl), P(dbl)]
         lib.nnfft_plan.argtypes = [P(vp), i64, i64, i64, dbl, dbl, cint, cint, cint, vp]
         lib.nnfft_plan_info.argtypes = [vp, P(Info)]
         lib.nnfft_batch_plan.argtypes = [P(vp), i64, P(i64), P(i64), P(i64), dbl, dbl, cint, cint,
@@ -183,14 +188,35 @@ def _dtype_code(dtype):
     raise ValueError(f"unsupported dtype {dtype!r}")
 
 
-def params(N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype="complex128") -> dict:
+WINDOWS = {"sinh": 0, "kaiser_bessel": 1, "bspline": 2, "algebraic": 3}
+
+
+def _window_code(window):
+    try:
+        return WINDOWS[window]
+    except KeyError:
+        raise ValueError(f"unknown window {window!r} (use one of {sorted(WINDOWS)})") from None
+
+
+def params(N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype="complex128",
+           window="sinh") -> dict:
     """Derived plan parameters (no GPU needed)."""
     lib = load_library()
     info = Info()
     m2 = m1 if m2 is None else m2
-    _check(lib.nnfft_params(int(N), int(M1), int(M2), float(sigma1), float(sigma2), int(m1),
-                            int(m2), _dtype_code(dtype), ctypes.byref(info)))
+    _check(lib.nnfft_params_window(int(N), int(M1), int(M2), float(sigma1), float(sigma2),
+                                   int(m1), int(m2), _dtype_code(dtype), _window_code(window),
+                                   ctypes.byref(info)))
     return info.as_dict()
+
+
+def window(name, m, sigma, x, v):
+    """The library's window omega(x) and its Fourier transform omegahat(v) (host only)."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.nnfft_window(_window_code(name), int(m), float(sigma), float(x), float(v),
+                            ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def gauss_legendre(n):
@@ -228,7 +254,7 @@ class Plan:
     """
 
     def __init__(self, N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype=None,
-                 stream=None):
+                 stream=None, window="sinh"):
         import torch
         lib = load_library()
         dtype = torch.complex128 if dtype is None else dtype
@@ -239,9 +265,10 @@ class Plan:
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._h = ctypes.c_void_p()
         m2 = m1 if m2 is None else m2
-        _check(lib.nnfft_plan(ctypes.byref(self._h), int(N), int(M1), int(M2), float(sigma1),
-                              float(sigma2), int(m1), int(m2), _dtype_code(dtype),
-                              _stream_ptr(self.stream)))
+        _check(lib.nnfft_plan_window(ctypes.byref(self._h), int(N), int(M1), int(M2),
+                                     float(sigma1), float(sigma2), int(m1), int(m2),
+                                     _dtype_code(dtype), _window_code(window),
+                                     _stream_ptr(self.stream)))
         self._lib = lib
 
     @property
@@ -565,7 +592,7 @@ class BatchPlan(Plan):
     """
 
     def __init__(self, N, M1, M2, sigma1=2.0, sigma2=2.0, m1=8, m2=None, dtype=None,
-                 stream=None):
+                 stream=None, window="sinh"):
         import torch
         lib = load_library()
         N, M1, M2 = (np.ascontiguousarray(a, dtype=np.int64).ravel() for a in (N, M1, M2))
@@ -584,10 +611,11 @@ class BatchPlan(Plan):
         self._h = ctypes.c_void_p()
         m2 = m1 if m2 is None else m2
         pi = ctypes.POINTER(ctypes.c_int64)
-        _check(lib.nnfft_batch_plan(ctypes.byref(self._h), self.count,
-                                    N.ctypes.data_as(pi), M1.ctypes.data_as(pi),
-                                    M2.ctypes.data_as(pi), float(sigma1), float(sigma2), int(m1),
-                                    int(m2), _dtype_code(dtype), _stream_ptr(self.stream)))
+        _check(lib.nnfft_batch_plan_window(ctypes.byref(self._h), self.count,
+                                           N.ctypes.data_as(pi), M1.ctypes.data_as(pi),
+                                           M2.ctypes.data_as(pi), float(sigma1), float(sigma2),
+                                           int(m1), int(m2), _dtype_code(dtype),
+                                           _window_code(window), _stream_ptr(self.stream)))
         self._lib = lib
 
     def instance_info(self, i) -> dict:

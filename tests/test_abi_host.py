@@ -108,3 +108,28 @@ def test_tolerance_classes():
         _, m = B.tolerance_params(tol)
         term = lambda mm: (24 * mm ** 1.5 + 10) * math.exp(-2 * math.pi * mm * math.sqrt(0.5))  # noqa: E731
         assert term(m) <= tol and (m == 2 or term(m - 1) > tol)
+
+
+@pytest.mark.parametrize("window", ["sinh", "kaiser_bessel", "bspline", "algebraic"])
+def test_library_windows_match_the_oracle(window):
+    """The library's host-side windows and Fourier transforms (its own code: C++ special
+    functions, a different B-spline recursion) against the oracle's, m = 2..8."""
+    import oracle
+    worst = 0.0
+    for m in (2, 3, 4, 6, 8):
+        for sg in (1.25, 1.5, 2.0):
+            P = oracle.make_params(64, sg, sg, m, m, window=window)
+            beta = {"bspline": 0.0, "algebraic": 3.0 * m}.get(window, 2 * np.pi * m * (1 - 1 / (2 * sg)))
+            for x in np.linspace(-1.1, 1.1, 23):
+                a, _ = B.window(window, m, sg, x, 0.0)
+                worst = max(worst, abs(a - float(oracle.omega(window, x, beta, m))))
+            for v in np.linspace(0, m / (2 * sg), 7):
+                _, a = B.window(window, m, sg, 0.0, v)
+                b = float(oracle.omega_hat(window, v, beta, m))
+                worst = max(worst, abs(a - b) / abs(b))
+            info = B.params(64, 100, 100, sg, sg, m, m, window=window)
+            assert info["window"] == B.WINDOWS[window]
+            assert info["beta1"] == pytest.approx(P.beta1, rel=1e-12, abs=0)
+    assert worst < 1e-13
+    with pytest.raises(B.NNFFTError):
+        B.params(300, 10, 10, 1.04, 2.0, 4, 4, window="algebraic")   # sigma <= pi/3
