@@ -226,9 +226,9 @@ int nnfft_plan_info(nnfft_plan_t p, nnfft_info *out);
 enum { NNFFT_TUNE_FLUSH_L2 = 1 };
 typedef struct {
     int moments_lanes_v, moments_lanes_x;   /* 32, 16 or 8 lanes per work item; 4: the 8-lane
-                                               split-precision kernel with the point loads
-                                               software-pipelined across chunks */
-    int fft_variant;                        /* 0 or 1 */
+                                               split-precision kernel with two accumulator sets
+                                               per lane */
+    int fft_variant;                        /* 0 or 1 (two-pass FFT), 2 (cluster FFT) */
     int tuned;                              /* 1 after nnfft_autotune */
     double default_ms, best_ms;             /* per run: default and chosen config */
     int item_split;                         /* 1: small work items one thread each (default 0) */
@@ -247,7 +247,9 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
  * moments_lanes_v / _x in {4, 8, 16, 32}, eval_lanes_v / _x in {1, 2, 8, 32} (0: 32), fft_variant in
- * {0, 1}, item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256), sort_lsd in {0, 1}
+ * {0, 1} (two-pass FFT, two column packings) or 2 (single-instance plans whose grid fits, N2 up
+ * to about 32K: the FFT as one launch of an 8-CTA thread-block cluster holding the grid in
+ * distributed shared memory; bitwise the same result), item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256), sort_lsd in {0, 1}
  * (both sorts give the same order: the same results bitwise); the other fields are
  * ignored (a lane count a kernel does not have runs as one warp per item).  EINVAL otherwise.
  * Takes effect for the work queued next; a changed item_split, item_cap or sort_lsd needs

@@ -310,11 +310,30 @@ cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, 
                           int sign, cudaStream_t s);
 cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, void *Q4,
                                   cudaStream_t s);
+// The FFT of a single instance as one launch of a thread-block cluster (FFT_CLUSTER CTAs,
+// the grid in distributed shared memory; out may equal in).  fft_cluster_smem: shared memory
+// per CTA; usable while it is at most FFT_CLUSTER_SMEM_MAX.  prepare_fft_cluster_df sets the
+// kernel's shared-memory limit to that maximum (once per device and process suffices).
+constexpr int FFT_CLUSTER = 8;
+constexpr int FFT_CLUSTER_VARIANT = 2;   // nnfft_tuning.fft_variant value selecting it
+constexpr int FFT_CLUSTER_THREADS = 512;
+constexpr size_t FFT_CLUSTER_SMEM_MAX = 200 * 1024;
+size_t fft_cluster_smem(int n1, int n2);
+cudaError_t prepare_fft_cluster_df();
+cudaError_t launch_fft_cluster_df(const FftLaunch<FftDf> &F, int n1, int n2, const void *in,
+                                  void *out, int sign, cudaStream_t s);
 
 // ---- kern_fft.cu ------------------------------------------------------------------
 template <typename Real>
 cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,
                        int sign, cudaStream_t s);
+// The cluster FFT of a single instance (see launch_fft_cluster_df) for complex64 / complex128
+// grids.
+template <typename Real> size_t fft_cluster_smem_real(int n1, int n2);
+template <typename Real> cudaError_t prepare_fft_cluster();
+template <typename Real>
+cudaError_t launch_fft_cluster(const FftLaunch<FftPlanDev> &F, int n1, int n2, const void *in,
+                               void *out, int sign, cudaStream_t s);
 
 // ---- kern_misc.cu -----------------------------------------------------------------
 template <typename Real>

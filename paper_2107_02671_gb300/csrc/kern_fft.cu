@@ -7,6 +7,10 @@
 // 2, 3, 4, 5, so no bit reversal is needed.  Twiddles come from
 // host-computed tables exp(-2 pi i k / n); sign = +1 uses their conjugates.
 // The whole grid (N2 <= 2^20 points) stays resident in L2 between the passes.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "internal.h"
 
 namespace nnfft {
@@ -206,7 +210,92 @@ k_fft_pass2(const C2<Real> *__restrict__ Z_all, C2<Real> *__restrict__ Y_all,
     }
 }
 
+// The FFT of a single instance as one launch of a thread-block cluster, the grid in
+// distributed shared memory (the structure of k_fft_cluster_df in kern_grid_df.cu): pass 1
+// on CTA r's columns into its own shared memory, a cluster barrier, the rows gathered from
+// every CTA's shared memory, a second barrier, pass 2 on the rows, written out.
+template <typename Real>
+__global__ void __cluster_dims__(FFT_CLUSTER, 1, 1) __launch_bounds__(FFT_CLUSTER_THREADS)
+k_fft_cluster(const C2<Real> *__restrict__ X, C2<Real> *__restrict__ Y, FftLaunch<FftPlanDev> L,
+              int sign) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ unsigned char smem_raw[];
+    const int r = (int)cl.block_rank();
+    const FftPlanDev &F = L.inst[0];
+    const int n1 = F.n1, n2 = F.n2;
+    const int per1 = (n2 + FFT_CLUSTER - 1) / FFT_CLUSTER, per2 = (n1 + FFT_CLUSTER - 1) / FFT_CLUSTER;
+    const int cap = max(per1 * n1, per2 * n2);
+    C2<Real> *buf0 = reinterpret_cast<C2<Real> *>(smem_raw);
+    C2<Real> *buf1 = buf0 + cap, *buf2 = buf0 + 2 * cap;
+    C2<Real> *tw1 = buf0 + 3 * cap, *tw2 = tw1 + n1;
+    const C2<Real> *gtw1 = static_cast<const C2<Real> *>(F.tw1);
+    const C2<Real> *gtw2 = static_cast<const C2<Real> *>(F.tw2);
+    const C2<Real> *twN = static_cast<const C2<Real> *>(F.twN);
+    const int b0 = r * per1, cols1 = max(0, min(per1, n2 - b0));
+    for (int e = threadIdx.x; e < cols1 * n1; e += blockDim.x) {     // columns b0 + bb
+        const int a = e / cols1, bb = e - a * cols1;
+        buf0[bb * n1 + a] = X[(long long)n2 * a + b0 + bb];
+    }
+    for (int a = threadIdx.x; a < n1; a += blockDim.x) tw1[a] = gtw1[a];
+    for (int b = threadIdx.x; b < n2; b += blockDim.x) tw2[b] = gtw2[b];
+    __syncthreads();
+    C2<Real> *res1 = stockham<Real>(buf0, buf1, n1, cols1, F.r1, F.nr1, tw1, sign);
+    for (int e = threadIdx.x; e < cols1 * n1; e += blockDim.x) {
+        const int bb = e / n1, c = e - bb * n1;
+        res1[e] = cmul<Real>(res1[e], twid<Real>(twN, (b0 + bb) * c, sign));
+    }
+    cl.sync();                                   // every CTA's pass 1 is in its shared memory
+    C2<Real> *A2 = res1 == buf0 ? buf1 : buf0;   // the same buffer in every CTA
+    const int c0 = r * per2, cols2 = max(0, min(per2, n1 - c0));
+    for (int e = threadIdx.x; e < cols2 * n2; e += blockDim.x) {     // rows c0 + cc
+        const int b = e / cols2, cc = e - b * cols2;
+        const int owner = b / per1;
+        const C2<Real> *rem = cl.map_shared_rank(res1, owner);
+        A2[cc * n2 + b] = rem[(b - owner * per1) * n1 + c0 + cc];
+    }
+    cl.sync();                                   // no CTA leaves while its memory is read
+    const C2<Real> *res2 = stockham<Real>(A2, buf2, n2, cols2, F.r2, F.nr2, tw2, sign);
+    for (int e = threadIdx.x; e < cols2 * n2; e += blockDim.x) {
+        const int d = e / cols2, cc = e - d * cols2;
+        Y[c0 + cc + (long long)n1 * d] = res2[cc * n2 + d];
+    }
+}
+
 }  // namespace
+
+template <typename Real>
+size_t fft_cluster_smem_real(int n1, int n2) {
+    const int per1 = (n2 + FFT_CLUSTER - 1) / FFT_CLUSTER, per2 = (n1 + FFT_CLUSTER - 1) / FFT_CLUSTER;
+    const size_t cap = (size_t)std::max(per1 * n1, per2 * n2);
+    return sizeof(C2<Real>) * (3 * cap + (size_t)n1 + (size_t)n2);
+}
+
+template <typename Real>
+cudaError_t prepare_fft_cluster() {
+    return cudaFuncSetAttribute(k_fft_cluster<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FFT_CLUSTER_SMEM_MAX);
+}
+
+template <typename Real>
+cudaError_t launch_fft_cluster(const FftLaunch<FftPlanDev> &F, int n1, int n2, const void *in,
+                               void *out, int sign, cudaStream_t s) {
+    const size_t sm = fft_cluster_smem_real<Real>(n1, n2);
+    if (F.ninst != 1 || sm > FFT_CLUSTER_SMEM_MAX) return cudaErrorInvalidValue;
+    k_fft_cluster<Real><<<FFT_CLUSTER, FFT_CLUSTER_THREADS, sm, s>>>(
+        static_cast<const C2<Real> *>(in), static_cast<C2<Real> *>(out), F, sign);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template size_t fft_cluster_smem_real<double>(int, int);
+template size_t fft_cluster_smem_real<float>(int, int);
+template cudaError_t prepare_fft_cluster<double>();
+template cudaError_t prepare_fft_cluster<float>();
+template cudaError_t launch_fft_cluster<double>(const FftLaunch<FftPlanDev> &, int, int,
+                                                const void *, void *, int, cudaStream_t);
+template cudaError_t launch_fft_cluster<float>(const FftLaunch<FftPlanDev> &, int, int,
+                                               const void *, void *, int, cudaStream_t);
 
 template <typename Real>
 cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,

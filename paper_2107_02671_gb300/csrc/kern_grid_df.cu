@@ -6,6 +6,10 @@
 // complex value is a float4 (re.h, re.l, im.h, im.l).  Window degrees d >= B = D/2
 // (weights <= 2e-7) are accumulated in FP32 from the high parts, as in the point
 // kernels.  The FFT butterflies run fully in double-float.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "df.cuh"
 #include "internal.h"
 
@@ -466,6 +470,60 @@ k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, Fft
 }
 
 // ---------------------------------------------------------------------------------
+// The same four-step FFT of one instance in one launch: a cluster of FFT_CLUSTER CTAs keeps
+// the whole grid in distributed shared memory.  CTA r transforms the columns [r P1, (r+1) P1)
+// (pass 1, with the twiddles) into its own shared memory; after a cluster barrier it gathers
+// the rows [r P2, (r+1) P2) of the intermediate from every CTA's shared memory (DSMEM loads,
+// consecutive threads reading consecutive addresses of one CTA), waits for the cluster again
+// (no CTA may leave while others read its memory), transforms the rows (pass 2) and writes
+// them.  No intermediate goes through global memory and there is one launch instead of two.
+// Shared memory per CTA: three buffers of max(P1 n1, P2 n2) elements and both twiddle
+// tables (fft_cluster_smem).
+// ---------------------------------------------------------------------------------
+__global__ void __cluster_dims__(FFT_CLUSTER, 1, 1) __launch_bounds__(FFT_CLUSTER_THREADS)
+k_fft_cluster_df(const float4 *__restrict__ X, float4 *__restrict__ Y, FftLaunch<FftDf> L,
+                 int sign) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ float4 smem4[];
+    const int r = (int)cl.block_rank();
+    const FftDf &F = L.inst[0];
+    const int n1 = F.n1, n2 = F.n2;
+    const int per1 = (n2 + FFT_CLUSTER - 1) / FFT_CLUSTER, per2 = (n1 + FFT_CLUSTER - 1) / FFT_CLUSTER;
+    const int cap = max(per1 * n1, per2 * n2);
+    float4 *buf0 = smem4, *buf1 = smem4 + cap, *buf2 = smem4 + 2 * cap;
+    float4 *tw1 = smem4 + 3 * cap, *tw2 = tw1 + n1;
+    const int b0 = r * per1, cols1 = max(0, min(per1, n2 - b0));
+    for (int e = threadIdx.x; e < cols1 * n1; e += blockDim.x) {     // columns b0 + bb
+        const int a = e / cols1, bb = e - a * cols1;
+        buf0[bb * n1 + a] = X[(long long)n2 * a + b0 + bb];
+    }
+    for (int a = threadIdx.x; a < n1; a += blockDim.x) tw1[a] = F.tw1[a];
+    for (int b = threadIdx.x; b < n2; b += blockDim.x) tw2[b] = F.tw2[b];
+    __syncthreads();
+    float4 *res1 = stockham_df(buf0, buf1, n1, cols1, F.r1, F.nr1, tw1, sign);
+    for (int e = threadIdx.x; e < cols1 * n1; e += blockDim.x) {
+        const int bb = e / n1, c = e - bb * n1;
+        st(res1 + e, cmul(ld(res1 + e), twd(F.twN, (b0 + bb) * c, sign)));
+    }
+    cl.sync();                                   // every CTA's pass 1 is in its shared memory
+    float4 *A2 = res1 == buf0 ? buf1 : buf0;     // the same buffer in every CTA
+    const int c0 = r * per2, cols2 = max(0, min(per2, n1 - c0));
+    for (int e = threadIdx.x; e < cols2 * n2; e += blockDim.x) {     // rows c0 + cc
+        const int b = e / cols2, cc = e - b * cols2;
+        const int owner = b / per1;
+        const float4 *rem = cl.map_shared_rank(res1, owner);
+        A2[cc * n2 + b] = rem[(b - owner * per1) * n1 + c0 + cc];
+    }
+    cl.sync();                                   // no CTA leaves while its memory is read
+    const float4 *res2 = stockham_df(A2, buf2, n2, cols2, F.r2, F.nr2, tw2, sign);
+    for (int e = threadIdx.x; e < cols2 * n2; e += blockDim.x) {
+        const int d = e / cols2, cc = e - d * cols2;
+        Y[c0 + cc + (long long)n1 * d] = res2[cc * n2 + d];
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // Gather convolution:
 //   Q_c[d] = sum_t coef[t][d] * scale(p) * h[p mod N2],  p = c - m + 1 + t,
 // then (x side) the 1/phihat1 fold in the Chebyshev basis: the coefficients of
@@ -757,6 +815,28 @@ cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, 
     k_fft_pass2_df<<<F.nblk2, 128, sm2, s>>>(static_cast<const float4 *>(tmp),
                                               static_cast<float4 *>(out), F, sign);
     count_launches(2);
+    return cudaGetLastError();
+}
+
+size_t fft_cluster_smem(int n1, int n2) {
+    const int per1 = (n2 + FFT_CLUSTER - 1) / FFT_CLUSTER, per2 = (n1 + FFT_CLUSTER - 1) / FFT_CLUSTER;
+    const size_t cap = (size_t)std::max(per1 * n1, per2 * n2);
+    return sizeof(float4) * (3 * cap + (size_t)n1 + (size_t)n2);
+}
+
+cudaError_t prepare_fft_cluster_df() {
+    // the kernel's limit is one value for every plan: the largest any plan may use
+    return cudaFuncSetAttribute(k_fft_cluster_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FFT_CLUSTER_SMEM_MAX);
+}
+
+cudaError_t launch_fft_cluster_df(const FftLaunch<FftDf> &F, int n1, int n2, const void *in,
+                                  void *out, int sign, cudaStream_t s) {
+    const size_t sm = fft_cluster_smem(n1, n2);
+    if (F.ninst != 1 || sm > FFT_CLUSTER_SMEM_MAX) return cudaErrorInvalidValue;
+    k_fft_cluster_df<<<FFT_CLUSTER, FFT_CLUSTER_THREADS, sm, s>>>(
+        static_cast<const float4 *>(in), static_cast<float4 *>(out), F, sign);
+    count_launches(1);
     return cudaGetLastError();
 }
 

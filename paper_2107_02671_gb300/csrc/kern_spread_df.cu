@@ -515,11 +515,11 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
     }
 }
 
-// The same per-item moments as k_moments_df_team with the point loads software-pipelined
-// across chunks: the values of chunk k+1 (gathered through the permutation) and the
-// coordinates and permutation entries of chunk k+2 are in flight while chunk k is
-// accumulated, so the dependent loads (permutation, then value) do not stall the lane
-// (about 40 more registers; two blocks of 256 per SM).
+// The same per-item moments as k_moments_df_team with more independent work per lane: the
+// points of a chunk alternate between two sets of accumulators, so that consecutive points
+// do not wait on each other's compensated sums (the sets are added before the exchange).
+// More registers (two blocks of 256 per SM), for launches whose work items are too few to
+// fill the SMs anyway.
 template <int D, int CH>
 __global__ void __launch_bounds__(256, 2)
 k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
@@ -535,51 +535,40 @@ k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
         pb = S.item_pb[item];
         pe = S.item_pe[item];
     }
-    df ar[B], ai[B];
-    float br[F], bi[F];
+    df ar[B], ai[B], ar2[B], ai2[B];
+    float br[F], bi[F], br2[F], bi2[F];
 #pragma unroll
-    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); }
+    for (int d = 0; d < B; ++d) { ar[d] = mk(0.f); ai[d] = mk(0.f); ar2[d] = mk(0.f); ai2[d] = mk(0.f); }
 #pragma unroll
-    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; }
-    constexpr int STEP = DTEAM * CH;
-    float2 yB[CH], yA[CH];
-    int jB[CH], jA[CH];
-    double2 vB[CH];
+    for (int d = 0; d < F; ++d) { br[d] = 0.f; bi[d] = 0.f; br2[d] = 0.f; bi2[d] = 0.f; }
+    for (int c0 = pb; c0 < pe; c0 += DTEAM * CH) {
+        float2 yv[CH];
+        int jv[CH];
 #pragma unroll
-    for (int k = 0; k < CH; ++k) {                   // prologue: chunks 0 and 1
-        const int p = pb + sub + DTEAM * k, q = p + STEP;
-        yB[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
-        jB[k] = p < pe ? S.perm[p] : -1;
-        yA[k] = q < pe ? ys2[q] : make_float2(0.f, 0.f);
-        jA[k] = q < pe ? S.perm[q] : -1;
+        for (int q = 0; q < CH; ++q) {
+            const int p = c0 + sub + DTEAM * q;
+            yv[q] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+            jv[q] = p < pe ? S.perm[p] : -1;
+        }
+        double2 vv2[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) vv2[q] = jv[q] >= 0 ? vals[jv[q]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < CH; q += 2) {
+            if (jv[q] >= 0) moments_point<B, F>(yv[q], vv2[q], ar, ai, br, bi);
+            if (q + 1 < CH && jv[q + 1] >= 0)
+                moments_point<B, F>(yv[q + 1], vv2[q + 1], ar2, ai2, br2, bi2);
+        }
     }
 #pragma unroll
-    for (int k = 0; k < CH; ++k) vB[k] = jB[k] >= 0 ? vals[jB[k]] : make_double2(0.0, 0.0);
-    for (int c0 = pb; c0 < pe; c0 += STEP) {
-        double2 vN[CH];
-        float2 yN[CH];
-        int jN[CH];
+    for (int d = 0; d < B; ++d) {              // the two accumulator sets
+        ar[d] = add(norm(ar[d]), norm(ar2[d]));
+        ai[d] = add(norm(ai[d]), norm(ai2[d]));
+    }
 #pragma unroll
-        for (int k = 0; k < CH; ++k) {               // values of the next chunk
-            vN[k] = jA[k] >= 0 ? vals[jA[k]] : make_double2(0.0, 0.0);
-            yN[k] = yA[k];
-            jN[k] = jA[k];
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {               // coordinates and indices two chunks on
-            const int q = c0 + 2 * STEP + sub + DTEAM * k;
-            yA[k] = q < pe ? ys2[q] : make_float2(0.f, 0.f);
-            jA[k] = q < pe ? S.perm[q] : -1;
-        }
-#pragma unroll
-        for (int k = 0; k < CH; ++k)
-            if (jB[k] >= 0) moments_point<B, F>(yB[k], vB[k], ar, ai, br, bi);
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-            yB[k] = yN[k];
-            jB[k] = jN[k];
-            vB[k] = vN[k];
-        }
+    for (int d = 0; d < F; ++d) {
+        br[d] += br2[d];
+        bi[d] += bi2[d];
     }
     df vd[16];
     float vf[16];

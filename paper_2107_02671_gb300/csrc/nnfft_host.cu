@@ -120,7 +120,9 @@ struct nnfft_plan_s {
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
     int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point,
                                      // EVAL_FLAT_TMA per point with TMA-staged cells
-    int fft_variant = 0;
+    int fft_variant = 0;         // 0, 1: column packings of the two-pass FFT; 2: cluster FFT
+    bool fft_cluster_ok = false; // the cluster FFT applies (single instance, split precision,
+                                 // shared memory within FFT_CLUSTER_SMEM_MAX)
     int item_cap = ITEM_CAP;     // points per work item at most (ITEM_CAP_MIN .. ITEM_CAP)
     int sort_lsd = 0;            // 1: LSD radix passes even where the two-stage sort applies
                                  // (the default for batches, where it measured faster)
@@ -905,6 +907,24 @@ int set_side_nodes(nnfft_plan_s *p, int s, const double *nodes, cudaStream_t st)
     return NNFFT_OK;
 }
 
+// Step 3 of a split-precision plan, grid bufA -> bufC: the two-pass four-step FFT (column
+// packing fft_variant 0 or 1), or (FFT_CLUSTER_VARIANT) one launch of the cluster FFT.
+cudaError_t fft_df(const nnfft_plan_s *p, const Work &W, int sign, cudaStream_t st) {
+    if (p->fft_variant == FFT_CLUSTER_VARIANT)
+        return launch_fft_cluster_df(p->fftdf[0], (int)p->info.fft_n1, (int)p->info.fft_n2, W.bufA,
+                                     W.bufC, sign, st);
+    return launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, sign, st);
+}
+
+// Step 3 of an all-real (fp32 or all-FP64) plan: the two-pass FFT or the cluster FFT.
+template <typename Real>
+cudaError_t fft_native(const nnfft_plan_s *p, const Work &W, int sign, cudaStream_t st) {
+    if (p->fft_variant == FFT_CLUSTER_VARIANT)
+        return launch_fft_cluster<Real>(p->fft[0], (int)p->info.fft_n1, (int)p->info.fft_n2,
+                                        W.bufA, W.bufC, sign, st);
+    return launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, sign, st);
+}
+
 int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
                       cudaEvent_t mid = nullptr, int part = 3) {
     const Side &V = p->side[0], &X = p->side[1];
@@ -931,7 +951,7 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     if ((part & 2) && !(X.M == 0)) {
         {
             StageTimer t(p, 4, st);
-            NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
+            NN_CUDA(fft_df(p, W, -1, st), "fft");
         }
         // the gather side's nodes (sorted on another stream) are needed from here on
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
@@ -974,7 +994,7 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     if ((part & 2) && !(V.M == 0)) {
         {
             StageTimer t(p, 9, st);
-            NN_CUDA(launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+            NN_CUDA(fft_df(p, W, +1, st), "adjoint fft");
         }
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
@@ -1016,7 +1036,7 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
     if ((part & 2) && !(X.M == 0)) {
         {
             StageTimer t(p, 4, st);
-            NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, -1, st), "fft");
+            NN_CUDA(fft_native<Real>(p, W, -1, st), "fft");
         }
         // the gather side's nodes (sorted on another stream) are needed from here on
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
@@ -1059,7 +1079,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     if ((part & 2) && !(V.M == 0)) {
         {
             StageTimer t(p, 9, st);
-            NN_CUDA(launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, +1, st), "adjoint fft");
+            NN_CUDA(fft_native<Real>(p, W, +1, st), "adjoint fft");
         }
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
@@ -1229,6 +1249,17 @@ int nnfft_batch_plan_window(nnfft_plan_t *out, int64_t count, const int64_t *N, 
     }
     if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype, window))) return bail(rc);
     if (prepare_local_sort() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "sort setup"));
+    if (count == 1) {        // the cluster FFT: every arithmetic mode of the plan must fit
+        const int n1 = (int)p->info.fft_n1, n2 = (int)p->info.fft_n2;
+        const size_t need = p->dbl ? std::max(fft_cluster_smem(n1, n2), fft_cluster_smem_real<double>(n1, n2))
+                                   : fft_cluster_smem_real<float>(n1, n2);
+        if (need <= FFT_CLUSTER_SMEM_MAX) {
+            cudaError_t ce = p->dbl ? prepare_fft_cluster<double>() : prepare_fft_cluster<float>();
+            if (ce == cudaSuccess && p->dbl && p->split_ok) ce = prepare_fft_cluster_df();
+            if (ce != cudaSuccess) return bail(cuda_fail(ce, "cluster FFT setup"));
+            p->fft_cluster_ok = true;
+        }
+    }
     *out = p;
     return NNFFT_OK;
 }
@@ -1456,7 +1487,9 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // the node sort (two-stage or LSD passes) only matters where the nodes are sorted
     const std::vector<int> sorts = with_nodes ? std::vector<int>{p->sort_lsd, 1 - p->sort_lsd}
                                               : std::vector<int>{p->sort_lsd};
-    const std::vector<std::vector<int>> dims{lanes, elanes, {0, 1}, splits, caps, sorts};
+    const std::vector<int> ffts = p->fft_cluster_ok ? std::vector<int>{0, 1, FFT_CLUSTER_VARIANT}
+                                                    : std::vector<int>{0, 1};
+    const std::vector<std::vector<int>> dims{lanes, elanes, ffts, splits, caps, sorts};
     auto set_dim = [](Cfg c, size_t d, int v) {
         switch (d) {
             case 0: c.lv = c.lx = v; break;
@@ -1575,7 +1608,9 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
-        (t->fft_variant != 0 && t->fft_variant != 1) || (t->item_split != 0 && t->item_split != 1) ||
+        (t->fft_variant != 0 && t->fft_variant != 1 &&
+         !(t->fft_variant == FFT_CLUSTER_VARIANT && p->fft_cluster_ok)) ||
+        (t->item_split != 0 && t->item_split != 1) ||
         (t->item_cap != 0 && t->item_cap != 32 && t->item_cap != 64 && t->item_cap != 128 &&
          t->item_cap != ITEM_CAP) || (t->sort_lsd != 0 && t->sort_lsd != 1))
         return fail(NNFFT_EINVAL, "invalid tuning values");

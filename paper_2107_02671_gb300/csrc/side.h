@@ -49,8 +49,8 @@ template <typename Real> struct SideK {
     // the plan's device status word (kernels OR in STATUS_* bits)
     int *status;
 };
-// Moments lanes value that selects the split-precision 8-lane team kernel with the point
-// loads software-pipelined across chunks.
+// Moments lanes value that selects the split-precision 8-lane team kernel with two sets of
+// accumulators (consecutive points of a lane accumulate independently).
 constexpr int MOM_TEAM_PF = 4;
 // Evaluation lanes value that selects the flat kernels: one thread per sorted point.
 constexpr int EVAL_FLAT = 1;
