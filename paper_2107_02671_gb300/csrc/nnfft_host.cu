@@ -953,13 +953,14 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
             StageTimer t(p, 4, st);
             NN_CUDA(fft_df(p, W, -1, st), "fft");
         }
-        // the gather side's nodes (sorted on another stream) are needed from here on
-        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 5, st);
             NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
                     "gather convolution");
         }
+        // the gather side's sorted nodes (sorted on another stream) are needed from here on;
+        // the gather convolution reads only the plan's grid geometry
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 6, st);
             NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
@@ -996,12 +997,12 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
             StageTimer t(p, 9, st);
             NN_CUDA(fft_df(p, W, +1, st), "adjoint fft");
         }
-        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 10, st);
             NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
                     "adjoint gather convolution");
         }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 11, st);
             NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
@@ -1038,13 +1039,14 @@ int run_forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const 
             StageTimer t(p, 4, st);
             NN_CUDA(fft_native<Real>(p, W, -1, st), "fft");
         }
-        // the gather side's nodes (sorted on another stream) are needed from here on
-        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 5, st);
             NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 1, false, true), W.bufC, W.Q, st),
                     "gather convolution");
         }
+        // the gather side's sorted nodes (sorted on another stream) are needed from here on;
+        // the gather convolution reads only the plan's grid geometry
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 6, st);
             NN_CUDA(launch_eval<Real>(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
@@ -1081,12 +1083,12 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
             StageTimer t(p, 9, st);
             NN_CUDA(fft_native<Real>(p, W, +1, st), "adjoint fft");
         }
-        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 10, st);
             NN_CUDA(launch_gather_conv<Real>(grid_launch<Real>(p, 0, false, false), W.bufC, W.Q, st),
                     "adjoint gather convolution");
         }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 11, st);
             NN_CUDA(launch_eval<Real>(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
@@ -1095,7 +1097,7 @@ int run_adjoint(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, const 
     return NNFFT_OK;
 }
 
-// mid: an event the gather half (gather convolution + evaluation) waits for, or nullptr.
+// mid: an event the evaluation (the gather half's point kernel) waits for, or nullptr.
 // part: 1 the spread half only (into the grid buffer W.bufA), 2 the rest only (from W.bufA:
 // FFT, gather convolution, evaluation), 3 both.
 int forward(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
