@@ -391,6 +391,43 @@ def run_batched(args, rank, dev, flush, timed, pk):
             P.set_nodes(vd, xd)
             P.exec(fd, y)
             P.adjoint(gd, z)
+
+        # split precision: the grid stage as stage-wide launches and as one cooperative
+        # launch per direction (fft_variant 3), each timed as the graph step
+        grid_forms = None
+        if dt == torch.complex128:
+            grid_forms = {}
+            t0v = dict(P.tuning())
+            keep = (t0v["moments_lanes_v"], t0v["moments_lanes_x"])
+            rest = (t0v["item_split"], t0v["eval_lanes_v"], t0v["eval_lanes_x"], t0v["item_cap"],
+                    t0v["sort_lsd"])
+            base = t0v["fft_variant"] if t0v["fft_variant"] != 3 else 0
+            for label, fv in (("stage_launches", base), ("fused_cooperative", 3)):
+                try:
+                    P.set_tuning(*keep, fv, *rest)
+                except B.NNFFTError as e:
+                    grid_forms[label] = {"unavailable": str(e)}
+                    continue
+                gr = P.transform_graph(vd, xd, fd, gd, y, z)
+                for _ in range(2):
+                    gr.launch()
+                P.sync()
+                ms_g, _, _ = timed(gr.launch, k, label="batched_grid_form")
+                P.sync()
+                gr.close()
+                _, _, stf = timed(step_seq, k, P, label="batched_seq_form")
+                P.sync()
+                sus = {kk: 1e3 * tot / n for kk, (tot, n) in stf.items() if n}
+                grid_us = sum(sus.get(f"{d}_{s2}", 0.0) for d in ("fwd", "adj")
+                              for s2 in ("cell_fold", "spread_conv", "fft", "gather_conv"))
+                grid_forms[label] = {"fft_variant": fv, "graph_ms_per_step": float(np.mean(ms_g)),
+                                     "graph_value": 2 * pts / (np.mean(ms_g) / 1e3),
+                                     "grid_stage_us_sequential": round(grid_us, 1)}
+            P.set_tuning(*keep, t0v["fft_variant"], *rest)
+            grid_forms["what"] = ("grid stage (cell fold, spread convolution, FFT, gather "
+                                  "convolution) as stage-wide launches or as one cooperative "
+                                  "launch per direction with grid barriers; graph step and the "
+                                  "grid stages' device time in a sequential pass")
         # per-stage times (and kernel HBM fractions) from a pass with the two directions
         # one after the other: in the timed step they share the GPU
         _, _, st = timed(step_seq, k, P, label="batched_seq")
@@ -433,6 +470,8 @@ def run_batched(args, rank, dev, flush, timed, pk):
                                    "(set_nodes, exec, adjoint)",
                      "hbm_roofline_point_kernels": hbm, "plan_seconds": round(t_plan, 2),
                      "max_rel_err_sampled": acc, "tuning": tune}
+        if grid_forms is not None:
+            out[name]["grid_stage_forms"] = grid_forms
         del P, vd, xd, fd, gd, y, z
         torch.cuda.empty_cache()
     return out

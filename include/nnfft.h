@@ -228,7 +228,9 @@ typedef struct {
     int moments_lanes_v, moments_lanes_x;   /* 32, 16 or 8 lanes per work item; 4: the 8-lane
                                                split-precision kernel with two accumulator sets
                                                per lane */
-    int fft_variant;                        /* 0 or 1 (two-pass FFT), 2 (cluster FFT) */
+    int fft_variant;                        /* 0 or 1 (two-pass FFT), 2 (cluster FFT), 3 (the
+                                               split-precision grid stage as one cooperative
+                                               launch) */
     int tuned;                              /* 1 after nnfft_autotune */
     double default_ms, best_ms;             /* per run: default and chosen config */
     int item_split;                         /* 1: small work items one thread each (default 0) */
@@ -249,7 +251,12 @@ int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
  * moments_lanes_v / _x in {4, 8, 16, 32}, eval_lanes_v / _x in {1, 2, 8, 32} (0: 32), fft_variant in
  * {0, 1} (two-pass FFT, two column packings) or 2 (single-instance plans whose grid fits, N2 up
  * to about 32K: the FFT as one launch of an 8-CTA thread-block cluster holding the grid in
- * distributed shared memory; bitwise the same result), item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256), sort_lsd in {0, 1}
+ * distributed shared memory; bitwise the same result) or 3 (complex128 plans in split precision
+ * with D1 = D2: cell fold, spread convolution, both FFT passes and gather convolution of a
+ * direction in one cooperative launch whose persistent blocks meet at grid-wide barriers with
+ * bounded waits -- a wait that gives up makes the plan report NNFFT_ETIMEOUT; bitwise the same
+ * result; exec/adjoint and transforms only, the split entry points nnfft_spread_grid ... keep
+ * the separate launches), item_split in {0, 1}, item_cap in {32, 64, 128, 256} (0: 256), sort_lsd in {0, 1}
  * (both sorts give the same order: the same results bitwise); the other fields are
  * ignored (a lane count a kernel does not have runs as one warp per item).  EINVAL otherwise.
  * Takes effect for the work queued next; a changed item_split, item_cap or sort_lsd needs
@@ -535,6 +542,21 @@ int nnfft_selftest_fixed63(const int64_t *in_dev, float *out_dev, int64_t n);
  */
 int nnfft_selftest_bulk_copy(const float *src_dev, float *dst_dev, int n, int arm_only,
                              int64_t limit_cycles, int *status_dev);
+
+/*
+ * nnfft_selftest_grid_barrier: check of the bounded grid-wide barrier of the fused grid
+ * stage (nnfft_tuning.fft_variant 3).  A cooperative launch of `blocks` blocks (1 ..
+ * the device's SM count) passes two barriers that each expect blocks + extra arrivals.
+ * words_dev: two 64-bit device words, zero before the first call (an arrival counter that
+ * only grows, and an abort word).  extra = 0: both barriers complete and the counter grows
+ * by 2 * blocks.  extra > 0: nobody completes the first barrier, so every block's wait
+ * gives up after limit_cycles SM clock cycles (or on seeing another block give up): the
+ * timeout bit (4) is ORed into *status_dev, the abort word is set and the blocks return,
+ * as the fused grid stage does, whose plan then reports NNFFT_ETIMEOUT.  Synchronous on the
+ * legacy default stream.  EINVAL for invalid arguments, ECUDA if the launch fails.
+ */
+int nnfft_selftest_grid_barrier(int blocks, int extra, int64_t limit_cycles,
+                                uint64_t *words_dev, int *status_dev);
 
 /* nnfft_launch_count: number of kernels this library has launched in the process. */
 int64_t nnfft_launch_count(void);

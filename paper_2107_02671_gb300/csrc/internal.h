@@ -323,6 +323,42 @@ cudaError_t prepare_fft_cluster_df();
 cudaError_t launch_fft_cluster_df(const FftLaunch<FftDf> &F, int n1, int n2, const void *in,
                                   void *out, int sign, cudaStream_t s);
 
+// The whole grid stage of one direction (cell fold, spread convolution with the step-2
+// deconvolution, the two FFT passes of step 3, gather convolution) as one cooperative
+// launch: persistent blocks of D * 32 threads take each stage's blocks in turn and meet at
+// a grid-wide barrier with bounded waits (gridsync.cuh) between the stages.  Same
+// arithmetic as the stage-wide launches, so the results are bitwise equal.
+constexpr int GRID_FUSED_VARIANT = 3;   // nnfft_tuning.fft_variant value selecting it
+// barrier wait limit: about one second at the GB300's 2.07 GHz SM clock
+constexpr long long GRID_WAIT_LIMIT_CYCLES = 2000000000LL;
+struct GridStageDf {
+    SideK<double> fold_side;        // the spreading side's item lists (cell fold)
+    SideDf fold_tab;                // its fit tables (rfit: x side, adjoint)
+    const float4 *P4;               // per-item moments
+    float4 *Q4;                     // per-cell moments, then per-cell window sums
+    GridLaunch<float2> spread, gather;
+    FftLaunch<FftDf> fft;           // the first column packing
+    float4 *bufA, *bufB, *bufC;     // spread grid, FFT intermediate, FFT output
+    int sign;
+    unsigned long long *bar;        // barrier words (arrival counter, abort word)
+    int *status;
+    long long limit;                // barrier wait limit in SM clock cycles
+};
+// Dynamic shared memory of the fused kernel for degree D and window sizes m_spread,
+// m_gather with FFT blocks of smem1 / smem2 float4 elements.
+size_t grid_stage_df_smem(int D, int m_spread, int m_gather, int smem1, int smem2);
+// Sets the kernel's shared-memory limit and returns the blocks per SM that can be resident
+// (0: not launchable with this shared memory).
+int prepare_grid_stage_df(int D, size_t smem);
+cudaError_t launch_grid_stage_df(const GridStageDf &A, int D, int blocks, size_t smem,
+                                 cudaStream_t s);
+// Self-test of the grid barrier: a cooperative launch of `blocks` blocks passing two
+// barriers that expect blocks + extra arrivals (extra > 0: nobody completes them, every
+// wait gives up after `limit` cycles and sets STATUS_TIMEOUT in *status).  words: two
+// zeroed 64-bit words.
+cudaError_t selftest_grid_barrier(int blocks, int extra, long long limit,
+                                  unsigned long long *words, int *status, cudaStream_t s);
+
 // ---- kern_fft.cu ------------------------------------------------------------------
 template <typename Real>
 cudaError_t launch_fft(const FftLaunch<FftPlanDev> &F, const void *in, void *tmp, void *out,

@@ -11,6 +11,7 @@
 #include <algorithm>
 
 #include "df.cuh"
+#include "gridsync.cuh"
 #include "internal.h"
 
 namespace nnfft {
@@ -32,12 +33,11 @@ __device__ __forceinline__ cdf item_sum(const float4 *__restrict__ P4, int i0, i
     return m;
 }
 
-// one thread per (cell, degree d)
+// one thread per (cell, degree d): element idx = cell * D + d
 template <int D>
-__global__ void __launch_bounds__(128)
-k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
-               float4 *__restrict__ Pc4) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cell_fold_df_elem(const SideK<double> &S, const SideDf &T,
+                                                  const float4 *__restrict__ P4,
+                                                  float4 *__restrict__ Pc4, long long idx) {
     const int ic = (int)(idx / D), d = (int)(idx - (long long)ic * D);
     if (ic >= S.ncell) return;
     const int i0 = S.item_off[ic], i1 = S.item_off[ic + 1];
@@ -70,20 +70,28 @@ k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
     st(Pc4 + (long long)ic * D + d, o);
 }
 
+template <int D>
+__global__ void __launch_bounds__(128)
+k_cell_fold_df(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
+               float4 *__restrict__ Pc4) {
+    cell_fold_df_elem<D>(S, T, P4, Pc4, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // With the fit (x side, adjoint): a block of CFP = 32 cells and one warp per degree
 // (lane = cell).  The item sums M_d are formed once per (cell, degree) into shared memory,
 // the fold reads them there (the per-thread form above re-sums up to 2 NR of them), and
 // the outputs leave as coalesced rows.  Same sums in the same order.
 constexpr int CFP = 32;
 
+// block vb of D * CFP threads: cells [vb CFP, vb CFP + CFP)
 template <int D>
-__global__ void __launch_bounds__(512)
-k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
-                   float4 *__restrict__ Pc4) {
+__device__ __forceinline__ void cell_fold_df_fit_block(const SideK<double> &S, const SideDf &T,
+                                                       const float4 *__restrict__ P4,
+                                                       float4 *__restrict__ Pc4, int vb) {
     __shared__ float4 ms[D][CFP];
     __shared__ float4 os[CFP * D];
     const int k = threadIdx.x & (CFP - 1), d = threadIdx.x / CFP;
-    const int c0 = blockIdx.x * CFP;
+    const int c0 = vb * CFP;
     const int ic = c0 + k;
     int i0 = 0, i1 = 0;
     if (ic < S.ncell) {
@@ -121,6 +129,13 @@ k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
     for (int e = threadIdx.x; e < nc * D; e += D * CFP) dst[e] = os[e];
 }
 
+template <int D>
+__global__ void __launch_bounds__(512)
+k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
+                   float4 *__restrict__ Pc4) {
+    cell_fold_df_fit_block<D>(S, T, P4, Pc4, blockIdx.x);
+}
+
 // ---------------------------------------------------------------------------------
 // Spread convolution.  Grid position p = p_lo + i (centered; the taps of all cells
 // cover [p_lo, p_hi], never wider than N2) goes to buffer index p mod N2:
@@ -135,14 +150,15 @@ k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
 // ---------------------------------------------------------------------------------
 constexpr int SCP = 32;
 
+// block vb of D * SCP threads; smem4: the block's dynamic shared memory
 template <int D>
-__global__ void __launch_bounds__(512)
-k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
-                 float4 *__restrict__ out_all) {
+__device__ __forceinline__ void spread_conv_df_block(const GridLaunch<float2> &L,
+                                                     const float4 *__restrict__ Pc_all,
+                                                     float4 *__restrict__ out_all, int vb,
+                                                     float4 *smem4) {
     constexpr int B = D / 2;
     constexpr int NT = D * SCP;
-    extern __shared__ float4 smem4[];
-    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const int inst = block_instance(L.blk, L.ninst, vb);
     const GridInst<float2> G = L.inst[inst];
     const float4 *__restrict__ Pc4 = Pc_all + (long long)G.cell_base * D;
     float4 *__restrict__ out = out_all + G.grid_base;
@@ -153,7 +169,7 @@ k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
     float4 *part = Ps + D * ncl;                                 // [D][SCP] partial sums
     float2 *coef = reinterpret_cast<float2 *>(part + D * SCP);  // [ntap][D]
     const long long p_lo = G.c_lo - m + 1, p_hi = G.c_lo + G.ncell - 1 + m;
-    const long long i0 = (long long)(blockIdx.x - L.blk[inst]) * SCP;
+    const long long i0 = (long long)(vb - L.blk[inst]) * SCP;
     const long long p0 = p_lo + i0;
     const int k = threadIdx.x & (SCP - 1), d = threadIdx.x / SCP;   // position, degree
     const long long i = i0 + k;
@@ -214,6 +230,14 @@ k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
         g = cscale(g, mk(sc.x, sc.y));
     }
     st(out + q, g);
+}
+
+template <int D>
+__global__ void __launch_bounds__(512)
+k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
+                 float4 *__restrict__ out_all) {
+    extern __shared__ float4 smem4[];
+    spread_conv_df_block<D>(L, Pc_all, out_all, blockIdx.x, smem4);
 }
 
 // Position-major form of the same sum for launches with many blocks (batches): one
@@ -419,16 +443,16 @@ __device__ float4 *stockham_df(float4 *A, float4 *Bf, int n, int cols, const int
 
 // Block b of pass 1 holds columns [b0, b0 + cols1) of instance i (b0 = (b - blk1[i]) cols1),
 // block c of pass 2 rows [c0, c0 + cols2); shared memory A, B (cols x n) and twiddles (n).
-__global__ void __launch_bounds__(128)
-k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, FftLaunch<FftDf> L,
-               int sign) {
-    extern __shared__ float4 smem4[];
-    const int inst = block_instance(L.blk1, L.ninst, blockIdx.x);
+__device__ __forceinline__ void fft_pass1_df_block(const float4 *__restrict__ X_all,
+                                                   float4 *__restrict__ Z_all,
+                                                   const FftLaunch<FftDf> &L, int sign, int vb,
+                                                   float4 *smem4) {
+    const int inst = block_instance(L.blk1, L.ninst, vb);
     const FftDf &F = L.inst[inst];
     const float4 *__restrict__ X = X_all + F.grid_base;
     float4 *__restrict__ Z = Z_all + F.grid_base;
     const int n = F.n1, n2 = F.n2;
-    const int b0 = (blockIdx.x - L.blk1[inst]) * F.cols1;
+    const int b0 = (vb - L.blk1[inst]) * F.cols1;
     const int cols = min(F.cols1, n2 - b0);
     float4 *A = smem4, *Bf = smem4 + cols * n, *tw = smem4 + 2 * cols * n;
     for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
@@ -444,16 +468,16 @@ k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, Fft
     }
 }
 
-__global__ void __launch_bounds__(128)
-k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, FftLaunch<FftDf> L,
-               int sign) {
-    extern __shared__ float4 smem4[];
-    const int inst = block_instance(L.blk2, L.ninst, blockIdx.x);
+__device__ __forceinline__ void fft_pass2_df_block(const float4 *__restrict__ Z_all,
+                                                   float4 *__restrict__ Y_all,
+                                                   const FftLaunch<FftDf> &L, int sign, int vb,
+                                                   float4 *smem4) {
+    const int inst = block_instance(L.blk2, L.ninst, vb);
     const FftDf &F = L.inst[inst];
     const float4 *__restrict__ Z = Z_all + F.grid_base;
     float4 *__restrict__ Y = Y_all + F.grid_base;
     const int n = F.n2, n1 = F.n1;
-    const int c0 = (blockIdx.x - L.blk2[inst]) * F.cols2;
+    const int c0 = (vb - L.blk2[inst]) * F.cols2;
     const int cols = min(F.cols2, n1 - c0);
     float4 *A = smem4, *Bf = smem4 + cols * n, *tw = smem4 + 2 * cols * n;
     for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
@@ -467,6 +491,20 @@ k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, Fft
         const int d = e / cols, cc = e - d * cols;
         Y[c0 + cc + (long long)n1 * d] = res[cc * n + d];
     }
+}
+
+__global__ void __launch_bounds__(128)
+k_fft_pass1_df(const float4 *__restrict__ X_all, float4 *__restrict__ Z_all, FftLaunch<FftDf> L,
+               int sign) {
+    extern __shared__ float4 smem4[];
+    fft_pass1_df_block(X_all, Z_all, L, sign, blockIdx.x, smem4);
+}
+
+__global__ void __launch_bounds__(128)
+k_fft_pass2_df(const float4 *__restrict__ Z_all, float4 *__restrict__ Y_all, FftLaunch<FftDf> L,
+               int sign) {
+    extern __shared__ float4 smem4[];
+    fft_pass2_df_block(Z_all, Y_all, L, sign, blockIdx.x, smem4);
 }
 
 // ---------------------------------------------------------------------------------
@@ -536,14 +574,15 @@ k_fft_cluster_df(const float4 *__restrict__ X, float4 *__restrict__ Y, FftLaunch
 // ---------------------------------------------------------------------------------
 constexpr int GCP = 32;
 
+// block vb of D * GCP threads; smem4: the block's dynamic shared memory
 template <int D>
-__global__ void __launch_bounds__(512)
-k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
-                 float4 *__restrict__ Q_all) {
+__device__ __forceinline__ void gather_conv_df_block(const GridLaunch<float2> &L,
+                                                     const float4 *__restrict__ buf_all,
+                                                     float4 *__restrict__ Q_all, int vb,
+                                                     float4 *smem4) {
     constexpr int B = D / 2;
     constexpr int NT = D * GCP;
-    extern __shared__ float4 smem4[];
-    const int inst = block_instance(L.blk, L.ninst, blockIdx.x);
+    const int inst = block_instance(L.blk, L.ninst, vb);
     const GridInst<float2> G = L.inst[inst];
     const float4 *__restrict__ buf = buf_all + G.grid_base;
     float4 *__restrict__ Q4 = Q_all + (long long)G.cell_base * D;
@@ -556,7 +595,7 @@ k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
     float4 *qa = qs + GCP * D;                                   // [D][GCP] tap sums (fold only)
     float2 *coef = reinterpret_cast<float2 *>(qs + (L.fold ? 2 : 1) * GCP * D);   // [ntap][D]
     const int k = threadIdx.x & (GCP - 1), d = threadIdx.x / GCP;   // cell, degree
-    const int ic0 = (blockIdx.x - L.blk[inst]) * GCP;
+    const int ic0 = (vb - L.blk[inst]) * GCP;
     const int ncb = min(GCP, G.ncell - ic0);                     // cells of this block
     const long long pb = G.c_lo + ic0 - m + 1;                   // position of hs[0]
     for (int e = threadIdx.x; e < ntap * D; e += NT) coef[e] = G.coef[e];
@@ -633,6 +672,14 @@ k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
     __syncthreads();
     float4 *dst = Q4 + (long long)ic0 * D;
     for (int e = threadIdx.x; e < ncb * D; e += NT) dst[e] = qs[e];
+}
+
+template <int D>
+__global__ void __launch_bounds__(512)
+k_gather_conv_df(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
+                 float4 *__restrict__ Q_all) {
+    extern __shared__ float4 smem4[];
+    gather_conv_df_block<D>(L, buf_all, Q_all, blockIdx.x, smem4);
 }
 
 // Position-major form for launches with many blocks: one thread per cell with all D
@@ -753,6 +800,55 @@ k_gather_conv_df_pos(GridLaunch<float2> L, const float4 *__restrict__ buf_all,
 
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// ---------------------------------------------------------------------------------
+// The grid stage of one direction in one cooperative launch (GRID_FUSED_VARIANT): every
+// block of D * 32 threads is resident; the blocks take the cell fold, the spread
+// convolution, FFT pass 1, FFT pass 2 and the gather convolution in turn, each stage's
+// blocks (the same block bodies as the stage-wide kernels above) spread round-robin over
+// the launch, with a grid-wide barrier between two stages.  A barrier wait that gives up
+// (gridsync.cuh) ends every block before its next stage; the plan reports NNFFT_ETIMEOUT.
+// Two blocks per SM at most D * 32 threads each bound the registers; the launch takes half
+// the resident blocks, so that the two directions' launches fit on the GPU together.
+// ---------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(D * 32, 2) k_grid_stage_df(GridStageDf A) {
+    extern __shared__ float4 smem4[];
+    const unsigned nb = gridDim.x;
+    const int ncell = A.fold_side.ncell;
+    if (A.fold_tab.rfit != nullptr) {
+        const int nv = (ncell + CFP - 1) / CFP;
+        for (int vb = blockIdx.x; vb < nv; vb += gridDim.x) {
+            cell_fold_df_fit_block<D>(A.fold_side, A.fold_tab, A.P4, A.Q4, vb);
+            __syncthreads();
+        }
+    } else {
+        const long long tot = (long long)ncell * D;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += stride)
+            cell_fold_df_elem<D>(A.fold_side, A.fold_tab, A.P4, A.Q4, idx);
+    }
+    if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
+    for (int vb = blockIdx.x; vb < A.spread.nblocks; vb += gridDim.x) {
+        spread_conv_df_block<D>(A.spread, A.Q4, A.bufA, vb, smem4);
+        __syncthreads();
+    }
+    if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
+    for (int vb = blockIdx.x; vb < A.fft.nblk1; vb += gridDim.x) {
+        fft_pass1_df_block(A.bufA, A.bufB, A.fft, A.sign, vb, smem4);
+        __syncthreads();
+    }
+    if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
+    for (int vb = blockIdx.x; vb < A.fft.nblk2; vb += gridDim.x) {
+        fft_pass2_df_block(A.bufB, A.bufC, A.fft, A.sign, vb, smem4);
+        __syncthreads();
+    }
+    if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
+    for (int vb = blockIdx.x; vb < A.gather.nblocks; vb += gridDim.x) {
+        gather_conv_df_block<D>(A.gather, A.bufC, A.Q4, vb, smem4);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 #define NNFFT_DISPATCH_DF2(D_, ...)                             \
@@ -859,6 +955,74 @@ cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, 
     }
     count_launches(1);
     return cudaGetLastError();
+}
+
+size_t grid_stage_df_smem(int D, int m_spread, int m_gather, int smem1, int smem2) {
+    const int ts = 2 * m_spread, tg = 2 * m_gather;
+    const size_t spread = sizeof(float4) * (size_t)D * (SCP + ts - 1 + SCP) + sizeof(float2) * (size_t)ts * D;
+    const size_t gather = sizeof(float4) * (size_t)(GCP + tg - 1 + 2 * GCP * D) + sizeof(float2) * (size_t)tg * D;
+    const size_t fft = sizeof(float4) * (size_t)std::max(smem1, smem2);
+    return std::max(std::max(spread, gather), fft);
+}
+
+namespace {
+template <int D>
+int prepare_grid_stage_d(size_t smem) {
+    if (cudaFuncSetAttribute(k_grid_stage_df<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_grid_stage_df<D>, D * 32, smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <int D>
+cudaError_t launch_grid_stage_d(const GridStageDf &A, int blocks, size_t smem, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(D * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_grid_stage_df<D>, A);
+}
+}  // namespace
+
+int prepare_grid_stage_df(int D, size_t smem) {
+    switch (D) {
+        case 8: return prepare_grid_stage_d<8>(smem);
+        case 10: return prepare_grid_stage_d<10>(smem);
+        case 12: return prepare_grid_stage_d<12>(smem);
+        case 14: return prepare_grid_stage_d<14>(smem);
+        case 16: return prepare_grid_stage_d<16>(smem);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_grid_stage_df(const GridStageDf &A, int D, int blocks, size_t smem,
+                                 cudaStream_t s) {
+    if (blocks <= 0) return cudaErrorInvalidValue;
+    cudaError_t e;
+    switch (D) {
+        case 8: e = launch_grid_stage_d<8>(A, blocks, smem, s); break;
+        case 10: e = launch_grid_stage_d<10>(A, blocks, smem, s); break;
+        case 12: e = launch_grid_stage_d<12>(A, blocks, smem, s); break;
+        case 14: e = launch_grid_stage_d<14>(A, blocks, smem, s); break;
+        case 16: e = launch_grid_stage_d<16>(A, blocks, smem, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return e;
 }
 
 }  // namespace nnfft

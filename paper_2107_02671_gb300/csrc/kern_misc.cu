@@ -4,6 +4,7 @@
 // computation (Algorithm 5.4) around a length-2n FFT; and the grid export / import
 // of the sharded transform (Algorithm 2.2 split at its grid).
 #include "internal.h"
+#include "gridsync.cuh"
 #include "tma.cuh"
 
 namespace nnfft {
@@ -153,6 +154,14 @@ __global__ void k_selftest_bulk_copy(const float *__restrict__ src, float *__res
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = buf[i];
 }
 
+// two grid barriers that expect gridDim.x + extra arrivals each
+__global__ void k_selftest_grid_barrier(int extra, long long limit, unsigned long long *words,
+                                        int *status) {
+    const unsigned expect = gridDim.x + (unsigned)extra;
+    if (!gsync::grid_barrier(words, expect, limit, status)) return;
+    gsync::grid_barrier(words, expect, limit, status);
+}
+
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 std::atomic<long long> g_launches{0};
@@ -203,6 +212,23 @@ cudaError_t selftest_bulk_copy(const float *src, float *dst, int n, int arm_only
     k_selftest_bulk_copy<<<1, 256, 0, s>>>(src, dst, n, arm_only, limit, status);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t selftest_grid_barrier(int blocks, int extra, long long limit,
+                                  unsigned long long *words, int *status, cudaStream_t s) {
+    if (blocks <= 0 || extra < 0 || limit <= 0) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(64);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_selftest_grid_barrier, extra, limit, words, status);
+    count_launches(1);
+    return e;
 }
 
 cudaError_t launch_grid_export(int fmt, const void *buf, int N2, int n, void *out,

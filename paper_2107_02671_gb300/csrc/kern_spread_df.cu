@@ -433,6 +433,11 @@ constexpr int DTEAM = 8;
 // (4 and 3: 80 registers without spills, three 256-thread blocks per SM)
 constexpr int TEAM_CH = 4;
 constexpr int TEAM_MINB = 3;
+// Threads per block of the team moments kernels.  One item per cell at 2^20 points puts
+// 8224 x 8 lanes = 257 blocks of 256 threads on 152 SMs: half the SMs ran two blocks, the
+// rest one, and the kernel lasted as long as the loaded half.  Blocks of TEAM_BLOCK threads
+// spread the same warps evenly (the register bound stays 3 x 256 threads per SM).
+constexpr int TEAM_BLOCK = 64;
 
 template <int O, int LB>
 __device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int sub) {
@@ -452,7 +457,7 @@ __device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int
 }
 
 template <int D, int CH, int MINB>
-__global__ void __launch_bounds__(256, MINB)
+__global__ void __launch_bounds__(TEAM_BLOCK, MINB * 256 / TEAM_BLOCK)
 k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2 *__restrict__ vals,
                   float4 *__restrict__ P4) {
     constexpr int B = D / 2;
@@ -521,7 +526,7 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
 // More registers (two blocks of 256 per SM), for launches whose work items are too few to
 // fill the SMs anyway.
 template <int D, int CH>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(TEAM_BLOCK, 2 * 256 / TEAM_BLOCK)
 k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
                      const double2 *__restrict__ vals, float4 *__restrict__ P4) {
     constexpr int B = D / 2;
@@ -744,11 +749,11 @@ cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4
         const int blocks = cdiv((long long)S.max_items * MOM_LANES, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_half<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));
     } else if (lanes == DTEAM) {
-        const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
-        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD, TEAM_CH, TEAM_MINB><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+        const int blocks = cdiv((long long)S.max_items * DTEAM, TEAM_BLOCK);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team<DD, TEAM_CH, TEAM_MINB><<<blocks, TEAM_BLOCK, 0, s>>>(S, y2, v, o)));
     } else if (lanes == MOM_TEAM_PF) {
-        const int blocks = cdiv((long long)S.max_items * DTEAM, 256);
-        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team_pf<DD, TEAM_CH><<<blocks, 256, 0, s>>>(S, y2, v, o)));
+        const int blocks = cdiv((long long)S.max_items * DTEAM, TEAM_BLOCK);
+        NNFFT_DISPATCH_DF(S.D, (k_moments_df_team_pf<DD, TEAM_CH><<<blocks, TEAM_BLOCK, 0, s>>>(S, y2, v, o)));
     } else {
         const int blocks = cdiv((long long)S.max_items * 32, 256);
         NNFFT_DISPATCH_DF(S.D, (k_moments_df_warp<DD><<<blocks, 256, 0, s>>>(S, y2, v, o)));

@@ -96,6 +96,7 @@ struct Work {
     void *bufA = nullptr, *bufB = nullptr, *bufC = nullptr;   // grids (all instances)
     void *P = nullptr;   // per-item moments
     void *Q = nullptr;   // per-cell moments (spread) and per-cell window sums (gather)
+    unsigned long long *gbar = nullptr;   // the fused grid stage's barrier words (2, zeroed)
 };
 
 }  // namespace
@@ -120,9 +121,14 @@ struct nnfft_plan_s {
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
     int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point,
                                      // EVAL_FLAT_TMA per point with TMA-staged cells
-    int fft_variant = 0;         // 0, 1: column packings of the two-pass FFT; 2: cluster FFT
+    int fft_variant = 0;         // 0, 1: column packings of the two-pass FFT; 2: cluster FFT;
+                                 // 3: the split-precision grid stage as one cooperative launch
     bool fft_cluster_ok = false; // the cluster FFT applies (single instance, split precision,
                                  // shared memory within FFT_CLUSTER_SMEM_MAX)
+    bool grid_fused_ok = false;  // the fused grid stage applies (split precision, D1 = D2,
+                                 // two blocks per SM resident)
+    int fused_blocks = 0;        // its cooperative grid: half the resident blocks
+    size_t fused_smem = 0;       // its dynamic shared memory per block
     int item_cap = ITEM_CAP;     // points per work item at most (ITEM_CAP_MIN .. ITEM_CAP)
     int sort_lsd = 0;            // 1: LSD radix passes even where the two-stage sort applies
                                  // (the default for batches, where it measured faster)
@@ -325,8 +331,11 @@ int alloc_work(nnfft_plan_s *p, Work &W) {
         (rc = dalloc(p, &W.bufB, p->work_bytes[0], "grid")) ||
         (rc = dalloc(p, &W.bufC, p->work_bytes[0], "grid")) ||
         (rc = dalloc(p, &W.P, p->work_bytes[1], "moments")) ||
-        (rc = dalloc(p, &W.Q, p->work_bytes[2], "cell windows")))
+        (rc = dalloc(p, &W.Q, p->work_bytes[2], "cell windows")) ||
+        (rc = dalloc_n(p, &W.gbar, 2, "grid barrier")))
         return rc;
+    if (cudaMemset(W.gbar, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "memset");
     return NNFFT_OK;
 }
 
@@ -913,7 +922,7 @@ cudaError_t fft_df(const nnfft_plan_s *p, const Work &W, int sign, cudaStream_t 
     if (p->fft_variant == FFT_CLUSTER_VARIANT)
         return launch_fft_cluster_df(p->fftdf[0], (int)p->info.fft_n1, (int)p->info.fft_n2, W.bufA,
                                      W.bufC, sign, st);
-    return launch_fft_df(p->fftdf[p->fft_variant], W.bufA, W.bufB, W.bufC, sign, st);
+    return launch_fft_df(p->fftdf[p->fft_variant == 1 ? 1 : 0], W.bufA, W.bufB, W.bufC, sign, st);
 }
 
 // Step 3 of an all-real (fp32 or all-FP64) plan: the two-pass FFT or the cluster FFT.
@@ -922,7 +931,35 @@ cudaError_t fft_native(const nnfft_plan_s *p, const Work &W, int sign, cudaStrea
     if (p->fft_variant == FFT_CLUSTER_VARIANT)
         return launch_fft_cluster<Real>(p->fft[0], (int)p->info.fft_n1, (int)p->info.fft_n2,
                                         W.bufA, W.bufC, sign, st);
-    return launch_fft<Real>(p->fft[p->fft_variant], W.bufA, W.bufB, W.bufC, sign, st);
+    return launch_fft<Real>(p->fft[p->fft_variant == 1 ? 1 : 0], W.bufA, W.bufB, W.bufC, sign, st);
+}
+
+// The fused grid stage runs when the tuning selects it, the plan supports it and the work
+// buffers carry barrier words.
+bool use_grid_fused(const nnfft_plan_s *p, const Work &W) {
+    return p->fft_variant == GRID_FUSED_VARIANT && p->grid_fused_ok && W.gbar != nullptr;
+}
+
+// Arguments of the fused grid stage: spreading side s (0: v, forward; 1: x, adjoint) with its
+// kernel descriptor S and fit tables T, the other side gathering; FFT sign.
+GridStageDf grid_stage_args(const nnfft_plan_s *p, const Work &W, const SideK<double> &S,
+                            const SideDf &T, int s, int sign) {
+    GridStageDf A;
+    A.fold_side = S;
+    A.fold_tab = T;
+    A.P4 = static_cast<const float4 *>(W.P);
+    A.Q4 = static_cast<float4 *>(W.Q);
+    A.spread = grid_launch<float2>(p, s, true, false);
+    A.gather = grid_launch<float2>(p, 1 - s, false, s == 0);
+    A.fft = p->fftdf[0];
+    A.bufA = static_cast<float4 *>(W.bufA);
+    A.bufB = static_cast<float4 *>(W.bufB);
+    A.bufC = static_cast<float4 *>(W.bufC);
+    A.sign = sign;
+    A.bar = W.gbar;
+    A.status = p->status;
+    A.limit = GRID_WAIT_LIMIT_CYCLES;
+    return A;
 }
 
 int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, const Work &W,
@@ -933,6 +970,24 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
     const SideK<double> sv = side_args<double>(V, false, p->status);
     const SideK<double> sx = side_args<double>(X, true, p->status);
     const SideDf tv{nullptr, nullptr};
+    if (part == 3 && use_grid_fused(p, W) && X.M > 0) {
+        {
+            StageTimer t(p, 2, st);
+            NN_CUDA(launch_moments_df(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
+        }
+        {   // cell fold, spread convolution, FFT and gather convolution in one launch
+            StageTimer t(p, 4, st);
+            NN_CUDA(launch_grid_stage_df(grid_stage_args(p, W, sv, tv, 0, -1), sv.D, p->fused_blocks,
+                                         p->fused_smem, st),
+                    "fused grid stage");
+        }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 6, st);
+            NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+        }
+        return NNFFT_OK;
+    }
     if (part & 1) {
         {
             StageTimer t(p, 2, st);
@@ -977,6 +1032,24 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
     const SideK<double> sv = side_args<double>(V, false, p->status);
     const SideK<double> sx = side_args<double>(X, true, p->status);
     const SideDf tx{nullptr, static_cast<const float2 *>(X.rfit_df)};
+    if (part == 3 && use_grid_fused(p, W) && V.M > 0) {
+        {
+            StageTimer t(p, 7, st);
+            NN_CUDA(launch_moments_df(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
+        }
+        {
+            StageTimer t(p, 9, st);
+            NN_CUDA(launch_grid_stage_df(grid_stage_args(p, W, sx, tx, 1, +1), sx.D, p->fused_blocks,
+                                         p->fused_smem, st),
+                    "adjoint fused grid stage");
+        }
+        if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
+        {
+            StageTimer t(p, 11, st);
+            NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+        }
+        return NNFFT_OK;
+    }
     if (part & 1) {
         {
             StageTimer t(p, 7, st);
@@ -1134,8 +1207,14 @@ int collect_status(nnfft_plan_s *p) {
     NN_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
     const int st = *p->status_host;
     if (st & STATUS_RANGE) return fail(NNFFT_ERANGE, "a node is outside [-1/2, 1/2] or NaN");
-    if (st & STATUS_TIMEOUT)
-        return fail(NNFFT_ETIMEOUT, "a bounded device-side wait (bulk copy) gave up");
+    if (st & STATUS_TIMEOUT) {
+        // a fused grid stage that gave up leaves its barrier counter off a multiple of the
+        // block count: start both directions' counters afresh
+        for (const Work &W : p->work)
+            if (W.gbar) cudaMemset(W.gbar, 0, 2 * sizeof(unsigned long long));
+        return fail(NNFFT_ETIMEOUT,
+                    "a bounded device-side wait (bulk copy or grid barrier) gave up");
+    }
     if (st & STATUS_INTERNAL)
         return fail(NNFFT_ECUDA, "internal error: inconsistent node cell assignment");
     return NNFFT_OK;
@@ -1251,6 +1330,18 @@ int nnfft_batch_plan_window(nnfft_plan_t *out, int64_t count, const int64_t *N, 
     }
     if ((rc = build_plan(p, count, N, M1, M2, sigma1, sigma2, m1, m2, dtype, window))) return bail(rc);
     if (prepare_local_sort() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "sort setup"));
+    if (p->dbl && p->split_ok && p->side[0].D == p->side[1].D && df_supported_degree(p->side[0].D)) {
+        // the fused grid stage: two blocks per SM must be resident, the launch takes one
+        const int D = p->side[0].D;
+        const int mm = std::max(p->side[0].m, p->side[1].m);
+        const size_t sm = grid_stage_df_smem(D, mm, mm, p->fftdf[0].smem1, p->fftdf[0].smem2);
+        const int bps = prepare_grid_stage_df(D, sm);
+        if (bps >= 2) {
+            p->grid_fused_ok = true;
+            p->fused_blocks = device_sm_count() * (bps / 2);
+            p->fused_smem = sm;
+        }
+    }
     if (count == 1) {        // the cluster FFT: every arithmetic mode of the plan must fit
         const int n1 = (int)p->info.fft_n1, n2 = (int)p->info.fft_n2;
         const size_t need = p->dbl ? std::max(fft_cluster_smem(n1, n2), fft_cluster_smem_real<double>(n1, n2))
@@ -1489,8 +1580,9 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     // the node sort (two-stage or LSD passes) only matters where the nodes are sorted
     const std::vector<int> sorts = with_nodes ? std::vector<int>{p->sort_lsd, 1 - p->sort_lsd}
                                               : std::vector<int>{p->sort_lsd};
-    const std::vector<int> ffts = p->fft_cluster_ok ? std::vector<int>{0, 1, FFT_CLUSTER_VARIANT}
-                                                    : std::vector<int>{0, 1};
+    std::vector<int> ffts{0, 1};
+    if (p->fft_cluster_ok) ffts.push_back(FFT_CLUSTER_VARIANT);
+    if (p->grid_fused_ok && dfk) ffts.push_back(GRID_FUSED_VARIANT);
     const std::vector<std::vector<int>> dims{lanes, elanes, ffts, splits, caps, sorts};
     auto set_dim = [](Cfg c, size_t d, int v) {
         switch (d) {
@@ -1611,7 +1703,8 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||
         (t->fft_variant != 0 && t->fft_variant != 1 &&
-         !(t->fft_variant == FFT_CLUSTER_VARIANT && p->fft_cluster_ok)) ||
+         !(t->fft_variant == FFT_CLUSTER_VARIANT && p->fft_cluster_ok) &&
+         !(t->fft_variant == GRID_FUSED_VARIANT && p->grid_fused_ok)) ||
         (t->item_split != 0 && t->item_split != 1) ||
         (t->item_cap != 0 && t->item_cap != 32 && t->item_cap != 64 && t->item_cap != 128 &&
          t->item_cap != ITEM_CAP) || (t->sort_lsd != 0 && t->sort_lsd != 1))
@@ -1707,6 +1800,19 @@ int nnfft_selftest_bulk_copy(const float *src_dev, float *dst_dev, int n, int ar
                                nullptr),
             "bulk-copy self-test");
     NN_CUDA(cudaStreamSynchronize(nullptr), "bulk-copy self-test");
+    return NNFFT_OK;
+}
+
+int nnfft_selftest_grid_barrier(int blocks, int extra, int64_t limit_cycles,
+                                uint64_t *words_dev, int *status_dev) {
+    if (!words_dev || !status_dev || blocks <= 0 || blocks > device_sm_count() || extra < 0 ||
+        limit_cycles <= 0)
+        return fail(NNFFT_EINVAL, "invalid self-test arguments");
+    NN_CUDA(selftest_grid_barrier(blocks, extra, (long long)limit_cycles,
+                                  reinterpret_cast<unsigned long long *>(words_dev), status_dev,
+                                  nullptr),
+            "grid-barrier self-test");
+    NN_CUDA(cudaStreamSynchronize(nullptr), "grid-barrier self-test");
     return NNFFT_OK;
 }
 

@@ -166,6 +166,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_timing_read.argtypes = [vp, P(Timing), cint]
         lib.nnfft_selftest_fixed63.argtypes = [vp, vp, i64]
         lib.nnfft_selftest_bulk_copy.argtypes = [vp, vp, cint, cint, i64, vp]
+        lib.nnfft_selftest_grid_barrier.argtypes = [cint, cint, i64, vp, vp]
         lib.nnfft_launch_count.argtypes = []
         lib.nnfft_launch_count.restype = i64
         lib.nnfft_last_error.restype = ctypes.c_char_p
@@ -790,6 +791,25 @@ def selftest_bulk_copy(src, arm_only=False, limit_cycles=2_000_000):
         ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()), src.numel(),
         int(bool(arm_only)), int(limit_cycles), ctypes.c_void_p(status.data_ptr())))
     return dst, int(status.item())
+
+
+def selftest_grid_barrier(blocks=2, extra=0, limit_cycles=2_000_000, words=None):
+    """Bounded-wait check of the fused grid stage's grid barrier: a cooperative launch of
+    `blocks` blocks passes two barriers expecting blocks + extra arrivals.  Returns (words,
+    status): the barrier words after the launch (arrival counter, abort word) and the bits
+    the blocks set (4: a wait gave up, which extra > 0 forces).  words: a zeroed int64 CUDA
+    tensor of 2 elements to reuse across calls (None: a fresh one)."""
+    import torch
+    if words is None:
+        words = torch.zeros(2, dtype=torch.int64, device="cuda")
+    if words.dtype != torch.int64 or words.numel() != 2 or not words.is_cuda:
+        raise TypeError("words must be a CUDA int64 tensor of 2 elements")
+    status = torch.zeros(1, dtype=torch.int32, device=words.device)
+    torch.cuda.synchronize()
+    _check(load_library().nnfft_selftest_grid_barrier(
+        int(blocks), int(extra), int(limit_cycles), ctypes.c_void_p(words.data_ptr()),
+        ctypes.c_void_p(status.data_ptr())))
+    return words, int(status.item())
 
 
 def launch_count() -> int:

@@ -190,3 +190,36 @@ def test_batch_two_stage_sort_equals_lsd_sort(dtype, m, arith, nodes):
     fi = f[a1:b1].astype(np.complex128)
     want = oracle.nnfft_direct(int(N[i]), v[a1:b1], fi, x[a2:b2], rows=rows)
     assert err(res[1][0][a2:b2][rows].astype(np.complex128), want, fi) <= tol
+
+
+@pytest.mark.parametrize("nodes", ["uniform", "chebyshev"])
+def test_batch_fused_grid_stage_equals_stage_launches(nodes):
+    """fft_variant 3 on a batch: the persistent blocks of the cooperative grid-stage launch
+    take every instance's fold, spread, FFT and gather blocks in turn (instances without
+    points, with one point, small and large); bitwise the stage-wide launches, forward and
+    adjoint, also replayed from the transform graph."""
+    N = np.array([2048, 64, 512, 7, 4096, 33, 300])
+    M1 = np.array([60000, 1, 0, 300, 90000, 77, 5000])
+    M2 = np.array([50000, 300, 50, 0, 70001, 1, 9000])
+    v, x, f = W.batch_inputs(M1, M2, 67, nodes=nodes)
+    g = W.draw_complex(np.random.default_rng(9), int(M2.sum()), np.complex128)
+    P = B.BatchPlan(N, M1, M2, 2.0, 2.0, 8, dtype=torch.complex128)
+    res = []
+    for fv in (0, 3):
+        P.set_tuning(8, 8, fv, 0, 32, 32)
+        P.set_nodes(dev(v), dev(x))
+        y, z = P.exec_adjoint(dev(f), dev(g))
+        P.sync()
+        res.append((y.cpu().numpy(), z.cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    vd, xd, fd, gd = dev(v), dev(x), dev(f), dev(g)
+    graph = P.transform_graph(vd, xd, fd, gd)
+    yg, zg = graph.launch()
+    P.sync()
+    assert np.array_equal(yg.cpu().numpy(), res[0][0]) and np.array_equal(zg.cpu().numpy(), res[0][1])
+    graph.close()
+    i = 4
+    a1, b1, a2, b2 = P.off1[i], P.off1[i + 1], P.off2[i], P.off2[i + 1]
+    rows = W.sample_rows(int(M2[i]), 32, 5)
+    want = oracle.nnfft_direct(int(N[i]), v[a1:b1], f[a1:b1], x[a2:b2], rows=rows)
+    assert err(res[1][0][a2:b2][rows], want, f[a1:b1]) <= 1e-12

@@ -969,3 +969,65 @@ def test_cluster_fft_equals_two_pass_fft(N, dtype, m, arith):
     want = oracle.nnfft_direct(N, v, f.astype(np.complex128), x, rows=rows)
     tol = 1e-12 if dtype == torch.complex128 else 2e-5
     assert np.max(np.abs(outs[1][0][rows].astype(np.complex128) - want)) / np.sum(np.abs(f)) <= tol
+
+
+def test_grid_barrier_waits_are_bounded():
+    """The fused grid stage's barrier: blocks that all arrive pass both barriers (the arrival
+    counter grows by 2 x blocks and stays a multiple of the block count); a barrier expecting
+    one block more than were launched is never completed, so every wait gives up after its
+    cycle limit, sets the timeout bit (4) and the abort word, and the context stays usable
+    (the next launch over fresh words passes)."""
+    import torch as T
+    words, st = B.selftest_grid_barrier(blocks=8, extra=0)
+    assert st == 0 and words.tolist() == [16, 0]
+    words, st = B.selftest_grid_barrier(blocks=8, extra=0, words=words)
+    assert st == 0 and words.tolist() == [32, 0]
+    words, st = B.selftest_grid_barrier(blocks=4, extra=1, limit_cycles=2_000_000)
+    assert st == 4 and int(words[1].item()) == 1 and int(words[0].item()) == 4
+    words, st = B.selftest_grid_barrier(blocks=4, extra=0, words=T.zeros(2, dtype=T.int64, device="cuda"))
+    assert st == 0 and words.tolist() == [8, 0]
+
+
+@pytest.mark.parametrize("N,M1,M2,nodes", [(4096, 50000, 40000, "uniform"), (1000, 30000, 70000, "chebyshev"),
+                                           (64, 3000, 2000, "uniform")])
+def test_fused_grid_stage_equals_stage_launches(N, M1, M2, nodes):
+    """fft_variant 3 runs the cell fold, spread convolution, both FFT passes and the gather
+    convolution of each direction in one cooperative launch with grid barriers: the same
+    block bodies and arithmetic as the stage-wide launches, so exec, adjoint, the concurrent
+    pair and the transform graph are bitwise equal to them, and the result is within the
+    fp64 tolerance of the direct sum."""
+    v, x, f = W.nnfft_inputs(M1, M2, 61, nodes=nodes)
+    g = W.adjoint_inputs(M2, 61)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, 8, 8, dtype=torch.complex128)
+    outs = []
+    for fv in (0, 3):
+        plan.set_tuning(8, 8, fv, 0, 32, 32)
+        plan.set_nodes(dev(v), dev(x))
+        y = plan.exec(dev(f))
+        z = plan.adjoint(dev(g))
+        y2, z2 = plan.exec_adjoint(dev(f), dev(g))
+        plan.sync()
+        outs.append([a.cpu().numpy() for a in (y, z, y2, z2)])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    vd, xd, fd, gd = dev(v), dev(x), dev(f), dev(g)
+    graph = plan.transform_graph(vd, xd, fd, gd)
+    for _ in range(3):
+        yg, zg = graph.launch()
+    plan.sync()
+    assert np.array_equal(yg.cpu().numpy(), outs[0][0]) and np.array_equal(zg.cpu().numpy(), outs[0][1])
+    graph.close()
+    rows = W.sample_rows(M2, 32, 17)
+    want = oracle.nnfft_direct(N, v, f, x, rows=rows)
+    assert np.max(np.abs(outs[1][0][rows] - want)) / np.sum(np.abs(f)) <= 1e-12
+
+
+def test_fused_grid_stage_needs_equal_degrees():
+    """The fused kernel is instantiated for one Chebyshev degree D on both sides: a plan with
+    m1 != m2 (D1 != D2) rejects fft_variant 3 with EINVAL and keeps working."""
+    plan = B.Plan(256, 2000, 2000, 2.0, 2.0, 8, 5, dtype=torch.complex128)
+    if plan.info["D1"] == plan.info["D2"]:
+        pytest.skip("equal degrees for these window sizes")
+    with pytest.raises(B.NNFFTError):
+        plan.set_tuning(8, 8, 3, 0, 32, 32)
+    plan.set_tuning(8, 8, 0, 0, 32, 32)
