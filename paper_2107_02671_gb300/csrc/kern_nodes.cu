@@ -207,20 +207,55 @@ k_seg_scan(int *__restrict__ hist, int ntiles, const int *__restrict__ tot, Sort
 
 // Exclusive scan of the digit-major histogram: block d scans row d (the counts of
 // digit d in every tile) starting from the number of keys with a smaller digit,
-// sum_{d' < d} digit_tot[d'].  Warp w owns a contiguous eighth of the row: a first pass
-// sums it (independent coalesced loads), a block scan of the eight warp totals gives each
-// warp its start, and a second pass scans the warp's segment in chunks of 32 with a
-// running carry (a few dozen serial steps per warp for a row of tens of thousands).
+// sum_{d' < d} digit_tot[d'].  Rows of up to 8 x 256 tiles (2^22 keys): thread t loads its
+// contiguous share of at most 8 counts together with the digit totals (one round of
+// loads), a block scan of the 256 thread sums gives each thread its start, and the thread
+// writes its share.  Longer rows: warp w owns a contiguous eighth of the row, a first pass
+// sums it, a block scan of the eight warp totals gives each warp its start, and a second
+// pass scans the warp's segment in chunks of 32 with a running carry.
 __global__ void __launch_bounds__(256)
 k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ digit_tot) {
     __shared__ int wsum[8];
     __shared__ int dbase[8];
     const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int *row = hist + (long long)d * nblocks;
+    const int per = (nblocks + 255) / 256;
+    if (per <= 8) {
+        const int a = tid * per;
+        int v[8];
+        int t = tid < d ? digit_tot[tid] : 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (q < per && a + q < nblocks) ? row[a + q] : 0;
+        int s = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        int incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[w] = incl;
+        if (lane == 0) dbase[w] = t;
+        __syncthreads();
+        int pre = incl - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pre += dbase[k] + (k < w ? wsum[k] : 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < per && a + q < nblocks) {
+                row[a + q] = pre;
+                pre += v[q];
+            }
+        }
+        return;
+    }
     int t = tid < d ? digit_tot[tid] : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) dbase[w] = t;
-    int *row = hist + (long long)d * nblocks;
     const int seg = (((nblocks + 7) / 8) + 31) & ~31;
     const int a = min(w * seg, nblocks), b = min(a + seg, nblocks);
     int s = 0;
