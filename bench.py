@@ -297,14 +297,14 @@ def run_reference(args, rank, world):
 # built from (their code, the double-float primitives, the side descriptor) are hashed; a
 # change since the capture reports null.
 NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "side.h"]
-NCU_HASH = "93ebd54f195ec588"
+NCU_HASH = "c7864bebb5018b5f"
 NCU_TRAFFIC = {
-    "k_moments_df_team<14>": 29461888,          # 8 lanes per work item
-    "k_moments_df_team_pf<14>": 29462144,       # 8 lanes, loads pipelined across chunks
+    "k_moments_df_team<14>": 29460160,          # 8 lanes per work item
+    "k_moments_df_team_pf<14>": 29464576,       # 8 lanes, two accumulator sets per lane
     "k_moments_df_half<14>": 29481088,          # 16
-    "k_eval_df_flat<14>": 20472576 + 1804352,   # one thread per point
-    "k_eval_df_flat_tma<14>": 20443840 + 1775232,   # the same, cells staged by TMA
-    "k_eval_df<14>": 16270464 + 1658560,        # 32
+    "k_eval_df_flat<14>": 20470720 + 1801472,   # one thread per point
+    "k_eval_df_flat_tma<14>": 20447360 + 1776832,   # the same, cells staged by TMA
+    "k_eval_df<14>": 16265792 + 1654400,        # 32
 }
 
 
@@ -829,6 +829,24 @@ def run_ours(args, rank, world):
                            "stream around each stage, averaged over the timed steps")
 
     extra = {}
+    # the critical path in parts: graphs of the node sorts alone, of the sorts with one
+    # direction, and of the whole step (the same calls, fewer inputs), L2 flushed before each
+    parts = {}
+    if graph is not None:
+        for pname, pargs in (("sorts", (vd, xd)), ("sorts_forward", (vd, xd, fd, None, y, None)),
+                             ("sorts_adjoint", (vd, xd, None, gd, None, z)),
+                             ("step", (vd, xd, fd, gd, y, z))):
+            gp = plan.transform_graph(*pargs)
+            for _ in range(3):
+                gp.launch()
+            plan.sync()
+            msp, _, _ = timed(gp.launch, max(10, args.steps), label="graph_part")
+            plan.sync()
+            gp.close()
+            parts[pname] = round(1e3 * float(np.median(msp)), 1)
+        parts["what"] = ("median us of a CUDA graph of nnfft_transform with both node sets and: no "
+                         "values (sorts only), f only, g only, both (the step)")
+        extra["graph_parts_us"] = parts
     extra["stream_launched"] = {"value": pts_step / (np.mean(ms_str) / 1e3), "unit": "pts/s",
                                 "ms_per_step": float(np.mean(ms_str)),
                                 "what": "the headline step launched kernel by kernel (nnfft_transform "
