@@ -423,7 +423,7 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
     assert t["tuned"] == 1 and t["moments_lanes_v"] in (4, 8, 16, 32) and t["moments_lanes_x"] in (4, 8, 16, 32)
     assert t["eval_lanes_v"] in (1, 2, 8, 32) and t["eval_lanes_x"] in (1, 2, 8, 32)
-    assert t["fft_variant"] in (0, 1, 2) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
+    assert t["fft_variant"] in (0, 1, 2, 3) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
     assert t["timed_transform"] == 0
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
     assert t["timed_transform"] == 1 and t["item_split"] in (0, 1)
