@@ -187,6 +187,25 @@ class ClockSampler:
 # -------------------------------------------------------------------------------------------
 # the CPU oracle (baseline leg and reference arm)
 # -------------------------------------------------------------------------------------------
+def host_cpu():
+    """The host's CPU model and logical core count (lscpu when present)."""
+    import platform
+    import shutil
+    import subprocess
+    model = None
+    if shutil.which("lscpu"):
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            model = None
+    return {"model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine(), "nproc": os.cpu_count()}
+
+
 def oracle_sample(seconds_target=12.0, seed=0):
     """Time the oracle's direct sums on a bounded row sample of the workload; extrapolate."""
     import oracle
@@ -208,6 +227,7 @@ def oracle_sample(seconds_target=12.0, seed=0):
     t_adj = time.perf_counter() - t0
     full = (t_fwd + t_adj) * M_PTS / len(rows)
     return {"value": 4 * M_PTS / full, "unit": "pts/s", "cores": cores, "kind": "oracle",
+            "host": host_cpu(),
             "sample": (f"direct fp64 sums for {len(rows)} sampled output rows of the forward and "
                        f"of the adjoint at N=4096, M1=M2=2^20 (each row sums all 2^20 terms); "
                        f"extrapolated x{M_PTS / len(rows):.0f} to the full step"),
@@ -335,6 +355,60 @@ def ncu_traffic(stage, tuning):
 
 
 BATCH_COUNT = 512
+
+
+M_SWEEP = (1 << 22, 1 << 24, 1 << 26)
+
+
+def run_m_sweep(args, rank, dev, flush, timed, pk):
+    """fp64 (split precision), N = 4096, sigma = 2, m = 8, M1 = M2 = M uniform nodes for the
+    M of M_SWEEP: the step (one graph launch) after the autotuner's choice, and from a
+    sequential pass the point kernels' HBM fractions (24 B per point).  At 2^20 points a cell
+    holds ~128 points and the moments launch ~13 warps per SM; larger M fills the cells and the
+    GPU."""
+    import torch
+    from paper_2107_02671_gb300 import nnfft as B
+    from paper_2107_02671_gb300 import workloads as W
+    out = {"what": "fp64 N=4096 sigma=2 m=8, M1 = M2 = M uniform nodes; HBM fractions of the "
+                   "point kernels from a sequential pass, 24 B per point",
+           "runs": []}
+    for M in M_SWEEP:
+        v, x, f = W.nnfft_inputs(M, M, 50 + rank)
+        g = W.adjoint_inputs(M, 50 + rank)
+        vd, xd, fd, gd = (torch.from_numpy(a).to(dev) for a in (v, x, f, g))
+        del v, x, f, g
+        y = torch.empty(M, dtype=torch.complex128, device=dev)
+        z = torch.empty(M, dtype=torch.complex128, device=dev)
+        P = B.Plan(N_BW, M, M, 2.0, 2.0, 8, 8, dtype=torch.complex128)
+        tune = P.autotune(fd, gd, y, z, reps=2, v=vd, x=xd, flush_l2=True)
+        gr = P.transform_graph(vd, xd, fd, gd, y, z)
+        for _ in range(3):
+            gr.launch()
+        P.sync()
+        k = 10
+        ms, _, _ = timed(gr.launch, k, label="m_sweep")
+        P.sync()
+        gr.close()
+
+        def seq(P=P, vd=vd, xd=xd, fd=fd, gd=gd, y=y, z=z):
+            P.set_nodes(vd, xd)
+            P.exec(fd, y)
+            P.adjoint(gd, z)
+        _, _, st = timed(seq, k, P, label="m_sweep_seq")
+        P.sync()
+        stage = {kk: 1e3 * tot / n for kk, (tot, n) in st.items() if n}
+        hbm = {kk: round(24 * M / (stage[kk] / 1e6) / 1e9 / pk["hbm_gbs"], 3)
+               for kk in ("fwd_moments", "fwd_eval", "adj_moments", "adj_eval") if kk in stage}
+        out["runs"].append({"M": M, "value": 4 * M / (np.mean(ms) / 1e3), "unit": "pts/s",
+                            "ms_per_step": float(np.mean(ms)),
+                            "stage_us": {kk: round(vv, 1) for kk, vv in stage.items()},
+                            "hbm_frac_point_kernels": hbm,
+                            "tuning": {kk: tune[kk] for kk in ("moments_lanes_v", "eval_lanes_v",
+                                                               "fft_variant", "item_cap", "sort_lsd")}})
+        P.close()
+        del P, vd, xd, fd, gd, y, z
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args, rank, dev, flush, timed, pk):
@@ -953,6 +1027,10 @@ def run_ours(args, rank, world):
                         "algorithmic_bytes_per_point": 16}
     del plan32
 
+    # ---- the same transform at larger M: the point kernels' HBM fraction as cells fill ----
+    if not args.no_m_sweep:
+        extra["m_sweep"] = run_m_sweep(args, rank, dev, flush, timed, pk)
+
     # ---- batched workload: 512 instances, M1, M2 log-uniform in [1e3, 1e6], N in [64, 8192] ----
     if not args.no_batch:
         extra["batched"] = run_batched(args, rank, dev, flush, timed, pk)
@@ -1076,6 +1154,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--no-m-sweep", action="store_true",
+                    help="skip the fp64 transform at M = 2^22, 2^24, 2^26")
     ap.add_argument("--no-graph", action="store_true",
                     help="headline step launched kernel by kernel instead of as one CUDA graph")
     ap.add_argument("--tuning", type=lambda t: [int(u) for u in t.split(",")], default=None,
