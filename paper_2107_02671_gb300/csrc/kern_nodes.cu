@@ -459,14 +459,14 @@ __host__ __device__ constexpr size_t local_sort_smem(int threads, int lbits, int
 // i, bucket b) through blk_first, the bucket's range from the instance's first tile's
 // scanned counts, bins of key - cell_base_i; ncell is then the side's total cell count.
 template <int LOCAL_THREADS, typename Y, bool CARRY>
-__global__ void __launch_bounds__(LOCAL_THREADS, local_min_blocks(LOCAL_THREADS))
-k_sort_local(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
-             const Y *__restrict__ yin, uint32_t *__restrict__ kout, int *__restrict__ vout,
-             Y *__restrict__ yout, int n, int lbits, int ncell, const int *__restrict__ hist,
-             int ntiles, SortTiles st, const int *__restrict__ blk_first, int cap,
-             int per_cell_first, int *__restrict__ off,
-             int *__restrict__ item_off, int *__restrict__ item_cell, int *__restrict__ item_pb,
-             int *__restrict__ item_pe, int *__restrict__ nitems, int *__restrict__ overflow) {
+__device__ __forceinline__ void
+sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+                const Y *__restrict__ yin, uint32_t *__restrict__ kout, int *__restrict__ vout,
+                Y *__restrict__ yout, int n, int lbits, int ncell, const int *__restrict__ hist,
+                int ntiles, const SortTiles &st, const int *__restrict__ blk_first, int cap,
+                int per_cell_first, int *__restrict__ off,
+                int *__restrict__ item_off, int *__restrict__ item_cell, int *__restrict__ item_pb,
+                int *__restrict__ item_pe, int *__restrict__ nitems, int *__restrict__ overflow) {
     constexpr int LOCAL_CHUNK = LOCAL_THREADS * LOCAL_ROUNDS;
     constexpr int LOCAL_WARPS = LOCAL_THREADS / 32;
     constexpr int RANGE = local_range(LOCAL_THREADS);
@@ -739,6 +739,112 @@ k_sort_local(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         for (int d = tid; d < NB; d += LOCAL_THREADS) run[d] += ctot[d];
         __syncthreads();
     }
+}
+
+// Work items of every cell (as k_build_items) by one block of T threads, four cells per
+// thread per tile: for the last block of the local pass when a cell exceeds the item cap.
+// The cell offsets were written by the other blocks of the launch: read through L2.
+template <int T>
+__device__ __forceinline__ void build_items_block(const int *__restrict__ off, int ncell,
+                                                  int *__restrict__ item_off,
+                                                  int *__restrict__ item_cell,
+                                                  int *__restrict__ item_pb,
+                                                  int *__restrict__ item_pe,
+                                                  int *__restrict__ nitems, int cap) {
+    constexpr int PER = 4;
+    constexpr int WARPS = T / 32;
+    __shared__ int wsum[WARPS];
+    __shared__ int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < ncell; base += T * PER) {
+        const int c0 = base + tid * PER;
+        int p[PER + 1];
+#pragma unroll
+        for (int q = 0; q <= PER; ++q) p[q] = c0 + q <= ncell ? __ldcg(off + c0 + q) : 0;
+        int v[PER];
+        int sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            v[q] = c0 + q < ncell ? (p[q + 1] - p[q] + cap - 1) / cap : 0;
+            sum += v[q];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            const int x = lane < WARPS ? wsum[lane] : 0;
+            int xi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += u;
+            }
+            if (lane < WARPS) wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        int first = carry_s + wsum[w] + incl - sum;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int c = c0 + q;
+            if (c < ncell) {
+                item_off[c] = first;
+                for (int j = 0; j < v[q]; ++j) {
+                    const int pb = p[q] + j * cap;
+                    item_cell[first + j] = c;
+                    item_pb[first + j] = pb;
+                    item_pe[first + j] = pb + cap < p[q + 1] ? pb + cap : p[q + 1];
+                }
+            }
+            first += v[q];
+        }
+        __syncthreads();
+        if (tid == T - 1) carry_s = first;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        item_off[ncell] = carry_s;
+        *nitems = carry_s;
+    }
+}
+
+// The local pass as a kernel.  ticket != nullptr (single instance, one work item per cell,
+// ncell <= ITEMS_ONE_BLOCK_MAX; *ticket zero at launch): every block takes a ticket when it
+// is done, and the last one, if some cell exceeded the item cap (*overflow), rebuilds the work
+// items by the scan -- what k_build_items does in a launch of its own otherwise.  No block
+// waits for another.
+template <int LOCAL_THREADS, typename Y, bool CARRY>
+__global__ void __launch_bounds__(LOCAL_THREADS, local_min_blocks(LOCAL_THREADS))
+k_sort_local(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
+             const Y *__restrict__ yin, uint32_t *__restrict__ kout, int *__restrict__ vout,
+             Y *__restrict__ yout, int n, int lbits, int ncell, const int *__restrict__ hist,
+             int ntiles, SortTiles st, const int *__restrict__ blk_first, int cap,
+             int per_cell_first, int *__restrict__ off,
+             int *__restrict__ item_off, int *__restrict__ item_cell, int *__restrict__ item_pb,
+             int *__restrict__ item_pe, int *__restrict__ nitems, int *__restrict__ overflow,
+             int *__restrict__ ticket) {
+    sort_local_body<LOCAL_THREADS, Y, CARRY>(kin, vin, yin, kout, vout, yout, n, lbits, ncell,
+                                             hist, ntiles, st, blk_first, cap, per_cell_first,
+                                             off, item_off, item_cell, item_pb, item_pe, nitems,
+                                             overflow);
+    if (ticket == nullptr) return;
+    __shared__ int last_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    if (__ldcg(overflow) == 0) return;
+    build_items_block<LOCAL_THREADS>(off, ncell, item_off, item_cell, item_pb, item_pe, nitems, cap);
 }
 
 // Single-block exclusive scan of n ints: out[i] = sum_{j<i} in[j], out[n] = total.
@@ -1161,17 +1267,18 @@ void local_launch(int nblocks, size_t sm, cudaStream_t s, int ybytes, const uint
                   int *vout, void *ys, int n, int lbits, int ncell, const int *hist, int ntiles,
                   const SortTiles &st, const int *blk_first, int cap, int per_cell_first,
                   int *off, int *item_off, int *item_cell, int *item_pb, int *item_pe,
-                  int *nitems, int *overflow) {
+                  int *nitems, int *overflow, int *ticket) {
     if (ybytes == 4)
         k_sort_local<T, unsigned, true><<<nblocks, T, sm, s>>>(
             kin, vin, static_cast<const unsigned *>(y_carried), kout, vout,
             static_cast<unsigned *>(ys), n, lbits, ncell, hist, ntiles, st, blk_first, cap,
-            per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
+            per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow, ticket);
     else
         k_sort_local<T, unsigned long long, false><<<nblocks, T, sm, s>>>(
             kin, vin, static_cast<const unsigned long long *>(y_user), kout, vout,
             static_cast<unsigned long long *>(ys), n, lbits, ncell, hist, ntiles, st, blk_first,
-            cap, per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow);
+            cap, per_cell_first, off, item_off, item_cell, item_pb, item_pe, nitems, overflow,
+            ticket);
 }
 }  // namespace
 
@@ -1209,10 +1316,14 @@ cudaError_t radix_sort_cells_local(uint32_t *keys, int *vals, uint32_t *keys_alt
     scatter_dispatch<true>(ybytes == 4 ? 4 : 0, ntiles, s, keys, vals, keys_alt, vals_alt, n,
                            lbits, 255u, st, hist, y_user, y_tmp);
     count_launches(2);
-    int *overflow = nullptr;
+    int *overflow = nullptr, *ticket = nullptr;
+    // one work item per cell from the local pass; its last block rebuilds the items when a
+    // cell exceeds cap (up to ITEMS_ONE_BLOCK_MAX cells; more: the multi-block builder below)
+    const bool items_in_pass = per_cell_first && ncell <= ITEMS_ONE_BLOCK_MAX;
     if (per_cell_first) {
         overflow = scratch + build_items_scratch_len(ncell) - 1;
-        cudaError_t e = cudaMemsetAsync(overflow, 0, sizeof(int), s);
+        ticket = items_in_pass ? overflow - 1 : nullptr;
+        cudaError_t e = cudaMemsetAsync(overflow - 1, 0, 2 * sizeof(int), s);
         if (e != cudaSuccess) return e;
     }
     // second stage: each bucket sorted by its low bits, cell offsets and items
@@ -1220,18 +1331,20 @@ cudaError_t radix_sort_cells_local(uint32_t *keys, int *vals, uint32_t *keys_alt
         local_launch<256>(nblocks, local_sort_smem(256, lbits, ybytes), s, ybytes, keys_alt,
                           vals_alt, y_tmp, y_user, keys, vals, ys, n, lbits, ncell, hist, ntiles,
                           st, blk_first, cap, 0, cell_off, item_off, item_cell, item_pb, item_pe,
-                          nitems, overflow);
+                          nitems, overflow, nullptr);
     else
         local_launch<LOCAL_SINGLE_THREADS>(nblocks, local_sort_smem(LOCAL_SINGLE_THREADS, lbits, ybytes),
                           s, ybytes, keys_alt,
                           vals_alt, y_tmp, y_user, keys, vals, ys, n, lbits, ncell, hist, ntiles,
                           st, blk_first, cap, per_cell_first ? 1 : 0, cell_off, item_off,
-                          item_cell, item_pb, item_pe, nitems, overflow);
+                          item_cell, item_pb, item_pe, nitems, overflow, ticket);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // cells above cap (or sparse plans): items by a scan of ceil(count / cap) over the cells
-    if (ncell <= ITEMS_ONE_BLOCK_MAX) {
+    if (items_in_pass) {
+        // done by the local pass's last block
+    } else if (ncell <= ITEMS_ONE_BLOCK_MAX) {
         k_build_items<<<1, 1024, 0, s>>>(cell_off, ncell, item_off, item_cell, item_pb, item_pe,
                                          nitems, cap, overflow);
         count_launches(1);
@@ -1277,7 +1390,9 @@ cudaError_t launch_cells_and_items(const uint32_t *keys_sorted, int n, int ncell
     return cudaGetLastError();
 }
 
-size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 2; }
+// block sums of the multi-block builder (cdiv(ncell, 1024) + 1), the local pass's ticket, and
+// the overflow flag last
+size_t build_items_scratch_len(int ncell) { return (size_t)cdiv(ncell, 1024) + 3; }
 
 namespace {
 // four floats per input: the node kernel's fp32 coordinate, its float pair (h, l), and
