@@ -304,8 +304,18 @@ cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, in
                            cudaStream_t s);
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,
                                 void *Pc4, cudaStream_t s);
+// The cell fold done by the spread convolution: the side's work-item offsets per cell, the
+// per-item moments, and the fit tables (x side, adjoint) or nullptr.  P4 == nullptr: the
+// convolution reads the folded moments (Pc4) instead.
+struct SpreadFoldDf {
+    const int *item_off = nullptr;
+    const float4 *P4 = nullptr;
+    const float2 *rfit = nullptr;
+};
+// True when the spread convolution of L runs the degree-major blocks, which can fold.
+bool spread_df_folds(const GridLaunch<float2> &L);
 cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const SpreadFoldDf &F = SpreadFoldDf{});
 cudaError_t launch_fft_df(const FftLaunch<FftDf> &F, const void *in, void *tmp, void *out,
                           int sign, cudaStream_t s);
 cudaError_t launch_gather_conv_df(const GridLaunch<float2> &L, const void *buf, void *Q4,

@@ -150,12 +150,22 @@ k_cell_fold_df_fit(SideK<double> S, SideDf T, const float4 *__restrict__ P4,
 // ---------------------------------------------------------------------------------
 constexpr int SCP = 32;
 
-// block vb of D * SCP threads; smem4: the block's dynamic shared memory
+// Shared memory of a degree-major spread block: Ps [D][ncl] float4, part [D][SCP] float4,
+// coef [ntap][D] float2, then (cell fold with the fit) Ms [D][ncl] float4.
+template <int D>
+__device__ __forceinline__ float4 *coef_end_df(float4 *part, int ntap) {
+    return reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(part + D * SCP) + ntap * D);
+}
+
+// block vb of D * SCP threads; smem4: the block's dynamic shared memory.  With F.P4 the
+// block forms the cell moments of its staged cells itself from the work items (the cell
+// fold, k_cell_fold_df / k_cell_fold_df_fit, same sums in the same order) instead of
+// reading them from Pc_all.
 template <int D>
 __device__ __forceinline__ void spread_conv_df_block(const GridLaunch<float2> &L,
                                                      const float4 *__restrict__ Pc_all,
                                                      float4 *__restrict__ out_all, int vb,
-                                                     float4 *smem4) {
+                                                     float4 *smem4, const SpreadFoldDf &F) {
     constexpr int B = D / 2;
     constexpr int NT = D * SCP;
     const int inst = block_instance(L.blk, L.ninst, vb);
@@ -179,12 +189,61 @@ __device__ __forceinline__ void spread_conv_df_block(const GridLaunch<float2> &L
     }
     const long long cbase = p0 - m;
     for (int e = threadIdx.x; e < ntap * D; e += NT) coef[e] = G.coef[e];
-    for (int e = threadIdx.x; e < ncl * D; e += NT) {
-        const int lc = e / D, dd = e - lc * D;
-        const long long ic = cbase + lc - G.c_lo;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ic >= 0 && ic < G.ncell) v = Pc4[ic * D + dd];
-        Ps[dd * ncl + lc] = v;
+    if (F.P4 == nullptr) {
+        for (int e = threadIdx.x; e < ncl * D; e += NT) {
+            const int lc = e / D, dd = e - lc * D;
+            const long long ic = cbase + lc - G.c_lo;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ic >= 0 && ic < G.ncell) v = Pc4[ic * D + dd];
+            Ps[dd * ncl + lc] = v;
+        }
+    } else {
+        // item sums of the staged cells (into Ms with the 1/phihat1 fit, else straight into Ps)
+        float4 *Ms = F.rfit != nullptr ? coef_end_df<D>(part, ntap) : Ps;
+        for (int e = threadIdx.x; e < ncl * D; e += NT) {
+            const int lc = e / D, dd = e - lc * D;
+            const long long ic = cbase + lc - G.c_lo;
+            cdf mv = czero();
+            if (ic >= 0 && ic < G.ncell) {
+                const long long gc = G.cell_base + ic;
+                const int i0 = F.item_off[gc], i1 = F.item_off[gc + 1];
+                if (i1 > i0) mv = item_sum<D>(F.P4, i0, i1, dd);
+            }
+            st(Ms + dd * ncl + lc, mv);
+        }
+        if (F.rfit != nullptr) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < ncl * D; e += NT) {
+                const int lc = e / D, dd = e - lc * D;
+                const long long ic = cbase + lc - G.c_lo;
+                cdf o = czero();
+                if (ic >= 0 && ic < G.ncell) {
+                    const long long gc = G.cell_base + ic;
+                    if (F.item_off[gc + 1] > F.item_off[gc]) {
+                        df ar = mk(0.f), ai = mk(0.f);
+#pragma unroll
+                        for (int j = 0; j < NR; ++j) {
+                            const float2 rv = F.rfit[gc * NR + j];
+                            const df r = mk(rv.x, rv.y);
+                            const int hi = dd + j, lo = dd > j ? dd - j : j - dd;
+                            if (hi < D) {
+                                const cdf mm = ld(Ms + hi * ncl + lc);
+                                acc(ar, mul_u(r, mm.re));
+                                acc(ai, mul_u(r, mm.im));
+                            }
+                            if (lo < D) {
+                                const cdf mm = ld(Ms + lo * ncl + lc);
+                                acc(ar, mul_u(r, mm.re));
+                                acc(ai, mul_u(r, mm.im));
+                            }
+                        }
+                        o.re = norm(ar);
+                        o.im = norm(ai);
+                    }
+                }
+                st(Ps + dd * ncl + lc, o);
+            }
+        }
     }
     __syncthreads();
     const int lbase = k + ntap - 1;
@@ -235,9 +294,9 @@ __device__ __forceinline__ void spread_conv_df_block(const GridLaunch<float2> &L
 template <int D>
 __global__ void __launch_bounds__(512)
 k_spread_conv_df(GridLaunch<float2> L, const float4 *__restrict__ Pc_all,
-                 float4 *__restrict__ out_all) {
+                 float4 *__restrict__ out_all, SpreadFoldDf F) {
     extern __shared__ float4 smem4[];
-    spread_conv_df_block<D>(L, Pc_all, out_all, blockIdx.x, smem4);
+    spread_conv_df_block<D>(L, Pc_all, out_all, blockIdx.x, smem4, F);
 }
 
 // Position-major form of the same sum for launches with many blocks (batches): one
@@ -829,7 +888,7 @@ __global__ void __launch_bounds__(D * 32, 2) k_grid_stage_df(GridStageDf A) {
     }
     if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
     for (int vb = blockIdx.x; vb < A.spread.nblocks; vb += gridDim.x) {
-        spread_conv_df_block<D>(A.spread, A.Q4, A.bufA, vb, smem4);
+        spread_conv_df_block<D>(A.spread, A.Q4, A.bufA, vb, smem4, SpreadFoldDf{});
         __syncthreads();
     }
     if (!gsync::grid_barrier(A.bar, nb, A.limit, A.status)) return;
@@ -878,20 +937,26 @@ cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const v
 int spread_blocks_df(int N2, int D) { return cdiv(N2, SCP); }
 int gather_blocks_df(int ncell, int D) { return cdiv(ncell, GCP); }
 
+bool spread_df_folds(const GridLaunch<float2> &L) {
+    return L.nblocks > 0 && L.nblocks < POS_MAJOR_BLOCKS_PER_SM * device_sm_count();
+}
+
 cudaError_t launch_spread_conv_df(const GridLaunch<float2> &L, const void *Pc4, void *out,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const SpreadFoldDf &F) {
     if (L.nblocks <= 0) return cudaSuccess;
     const int ntap = 2 * L.m;
     const float4 *in = static_cast<const float4 *>(Pc4);
     float4 *o = static_cast<float4 *>(out);
+    if (F.P4 != nullptr && !spread_df_folds(L)) return cudaErrorInvalidValue;
     if (L.nblocks >= POS_MAJOR_BLOCKS_PER_SM * device_sm_count()) {
         const size_t sm = sizeof(float4) * (size_t)L.D * (SCP + ntap - 1) +
                           sizeof(float2) * (size_t)ntap * L.D;
         NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df_pos<DD><<<L.nblocks, SCP, sm, s>>>(L, in, o)));
     } else {
         const size_t sm = sizeof(float4) * (size_t)L.D * (SCP + ntap - 1 + SCP) +
-                          sizeof(float2) * (size_t)ntap * L.D;
-        NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df<DD><<<L.nblocks, DD * SCP, sm, s>>>(L, in, o)));
+                          sizeof(float2) * (size_t)ntap * L.D +
+                          (F.rfit != nullptr ? sizeof(float4) * (size_t)L.D * (SCP + ntap - 1) : 0);
+        NNFFT_DISPATCH_DF2(L.D, (k_spread_conv_df<DD><<<L.nblocks, DD * SCP, sm, s>>>(L, in, o, F)));
     }
     count_launches(1);
     return cudaGetLastError();

@@ -993,14 +993,21 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
             StageTimer t(p, 2, st);
             NN_CUDA(launch_moments_df(sv, f, W.P, p->mom_lanes[0], st), "spread moments");
         }
-        {
+        // the degree-major spread convolution folds the cells' items itself
+        const GridLaunch<float2> Ls = grid_launch<float2>(p, 0, true, false);
+        const bool fold_in = spread_df_folds(Ls);
+        if (!fold_in) {
             StageTimer t(p, 12, st);
             NN_CUDA(launch_cell_fold_df(sv, tv, W.P, W.Q, st), "cell fold");
         }
         {
             StageTimer t(p, 3, st);
-            NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 0, true, false), W.Q, W.bufA, st),
-                    "spread convolution");
+            SpreadFoldDf F;
+            if (fold_in) {
+                F.item_off = sv.item_off;
+                F.P4 = static_cast<const float4 *>(W.P);
+            }
+            NN_CUDA(launch_spread_conv_df(Ls, W.Q, W.bufA, st, F), "spread convolution");
         }
     }
     if ((part & 2) && !(X.M == 0)) {
@@ -1055,14 +1062,21 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
             StageTimer t(p, 7, st);
             NN_CUDA(launch_moments_df(sx, g, W.P, p->mom_lanes[1], st), "adjoint spread moments");
         }
-        {
+        const GridLaunch<float2> Ls = grid_launch<float2>(p, 1, true, false);
+        const bool fold_in = spread_df_folds(Ls);
+        if (!fold_in) {
             StageTimer t(p, 13, st);
             NN_CUDA(launch_cell_fold_df(sx, tx, W.P, W.Q, st), "adjoint cell fold");
         }
         {
             StageTimer t(p, 8, st);
-            NN_CUDA(launch_spread_conv_df(grid_launch<float2>(p, 1, true, false), W.Q, W.bufA, st),
-                    "adjoint spread convolution");
+            SpreadFoldDf F;
+            if (fold_in) {
+                F.item_off = sx.item_off;
+                F.P4 = static_cast<const float4 *>(W.P);
+                F.rfit = tx.rfit;
+            }
+            NN_CUDA(launch_spread_conv_df(Ls, W.Q, W.bufA, st, F), "adjoint spread convolution");
         }
     }
     if ((part & 2) && !(V.M == 0)) {
