@@ -237,7 +237,11 @@ typedef struct {
     int timed_transform;                    /* 1: runs were full transforms */
     int eval_lanes_v, eval_lanes_x;         /* evaluation lanes per item: 32 or 8; 1 = flat
                                                (thread per point); 2 = flat with each block's
-                                               cell window sums staged by a TMA bulk copy */
+                                               cell window sums staged by a TMA bulk copy;
+                                               3 = 32 lanes that also compute their cell's
+                                               window sums from the grid (the gather
+                                               convolution inside the evaluation; split
+                                               precision, single plans, else as 32) */
     int item_cap;                           /* points per work item at most: 256, 128, 64, 32 */
     int sort_lsd;                           /* node sort of 9- to 16-bit cell keys: 0 two-stage
                                                (high-digit scatter, then a shared-memory sort per
@@ -248,7 +252,7 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
                    void *y_dev, const void *g_dev, void *z_dev, int reps, int flags);
 int nnfft_get_tuning(nnfft_plan_t p, nnfft_tuning *out);
 /* nnfft_set_tuning: apply a configuration (e.g. one kept from an earlier nnfft_autotune):
- * moments_lanes_v / _x in {4, 8, 16, 32}, eval_lanes_v / _x in {1, 2, 8, 32} (0: 32), fft_variant in
+ * moments_lanes_v / _x in {4, 8, 16, 32}, eval_lanes_v / _x in {1, 2, 3, 8, 32} (0: 32), fft_variant in
  * {0, 1} (two-pass FFT, two column packings) or 2 (single-instance plans whose grid fits, N2 up
  * to about 32K: the FFT as one launch of an 8-CTA thread-block cluster holding the grid in
  * distributed shared memory; bitwise the same result) or 3 (complex128 plans in split precision

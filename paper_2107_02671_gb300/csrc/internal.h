@@ -300,6 +300,12 @@ bool df_supported_degree(int D);
 // the plan's autotuner picks.  Evaluation: 32 or 8.
 cudaError_t launch_moments_df(const SideK<double> &S, const void *vals, void *P4, int lanes,
                               cudaStream_t s);
+// The evaluation with the gather convolution done per work item (EVAL_GATHER): L is the
+// gathering side's grid launch (one instance), grid the FFT output.  eval_gather_df_ok: L
+// qualifies (one instance, 2m <= 32, D <= 16); the side must not split small items.
+bool eval_gather_df_ok(const GridLaunch<float2> &L);
+cudaError_t launch_eval_gather_df(const SideK<double> &S, const GridLaunch<float2> &L,
+                                  const void *grid, void *out, cudaStream_t s);
 cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, int lanes,
                            cudaStream_t s);
 cudaError_t launch_cell_fold_df(const SideK<double> &S, const SideDf &T, const void *P4,

@@ -330,6 +330,131 @@ k_eval_df(SideK<double> S, const float2 *__restrict__ ys2, const float4 *__restr
     }
 }
 
+// One warp per work item with the gather convolution of the item's cell done in the warp
+// (evaluation lanes value EVAL_GATHER, single instances): lanes t < 2m load and scale the grid
+// values h_{c-m+1+t}, lane d < D forms the window sum Q_c[d] = sum_t coef[t][d] h_t and, on
+// the x side, lane n the 1/phihat1 fold of the sums -- the arithmetic of k_gather_conv_df
+// for one cell, in the same order, so the results are bitwise those of the gather kernel
+// followed by k_eval_df -- then the warp evaluates its points as k_eval_df does.  The
+// separate gather launch and its per-cell output disappear; a cell with several items is
+// convolved once per item.
+constexpr int EG_HS = 32;   // grid values a warp stages (2m <= 32)
+template <int D>
+__global__ void __launch_bounds__(256, 3)
+k_eval_gather_df(SideK<double> S, const float2 *__restrict__ ys2, GridLaunch<float2> L,
+                 const float4 *__restrict__ buf_all, double2 *__restrict__ out) {
+    constexpr int B = D / 2;
+    constexpr int F = D - B;
+    __shared__ float4 wsm[8][EG_HS + 2 * 16];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = big_item(S, (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5));
+    if (item < 0) return;                                        // warp-uniform
+    const int c = S.item_cell[item], pb = S.item_pb[item], pe = S.item_pe[item];
+    float2 yv[PPL];
+    int jv[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {                              // the points' loads first
+        const int p = pb + lane + 32 * k;
+        yv[k] = p < pe ? ys2[p] : make_float2(0.f, 0.f);
+        jv[k] = p < pe ? S.perm[p] : -1;
+    }
+    const GridInst<float2> G = L.inst[0];
+    const float4 *__restrict__ buf = buf_all + G.grid_base;
+    const int m = L.m, ntap = 2 * L.m, N2 = G.N2;
+    const long long icl = (long long)c - G.cell_base;            // the instance's cell
+    float4 *hs = wsm[w], *qa = hs + EG_HS, *qq = qa + 16;
+    if (lane < ntap) {
+        const long long p = G.c_lo + icl - m + 1 + lane;
+        cdf h = ld(buf + wrap_index(p, N2));
+        if (G.scale != nullptr) {
+            const long long si = p + G.scale_off;
+            const float2 sc = (si >= 0 && si < G.scale_len) ? G.scale[si] : make_float2(0.f, 0.f);
+            h = cscale(h, mk(sc.x, sc.y));
+        }
+        st(hs + lane, h);
+    }
+    __syncwarp();
+    const float2 *__restrict__ rfit = L.fold ? G.rfit : nullptr;
+    if (lane < D) {
+        const int d = lane;
+        cdf q;
+        if (d < B) {
+            df qr = mk(0.f), qi = mk(0.f);
+            for (int t = 0; t < ntap; ++t) {
+                const cdf h = ld(hs + t);
+                const float2 c2 = G.coef[t * D + d];
+                const df cd = mk(c2.x, c2.y);
+                acc(qr, mul_u(cd, h.re));
+                acc(qi, mul_u(cd, h.im));
+            }
+            q.re = norm(qr);
+            q.im = norm(qi);
+        } else {
+            float fr = 0.f, fi = 0.f;
+            for (int t = 0; t < ntap; ++t) {
+                const float4 hv = hs[t];
+                const float cc = G.coef[t * D + d].x;
+                fr = fmaf(cc, hv.x, fr);
+                fi = fmaf(cc, hv.z, fi);
+            }
+            q.re = mk(fr);
+            q.im = mk(fi);
+        }
+        st((rfit == nullptr ? qq : qa) + d, q);
+    }
+    __syncwarp();
+    if (rfit != nullptr) {
+        if (lane < D) {
+            const int n = lane;
+            df ar = mk(0.f), ai = mk(0.f);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                const float2 rv = rfit[icl * NR + j];
+                const df r = mk(rv.x, rv.y);
+                if (j <= n) {
+                    const cdf v = ld(qa + (n - j));
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+                if (n + j < D) {
+                    const cdf v = ld(qa + (n + j));
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+                if (n > 0 && j >= n && j - n < D) {
+                    const cdf v = ld(qa + (j - n));
+                    acc(ar, mul_u(r, v.re));
+                    acc(ai, mul_u(r, v.im));
+                }
+            }
+            cdf o;
+            o.re = norm(ar);
+            o.im = norm(ai);
+            st(qq + n, o);
+        }
+        __syncwarp();
+    }
+    df qr[B], qi[B];
+    float fr[F], fi[F];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const float4 q = qq[d];
+        if (d < B) {
+            qr[d < B ? d : 0] = mk(q.x, q.y);
+            qi[d < B ? d : 0] = mk(q.z, q.w);
+        } else {
+            fr[d >= B ? d - B : 0] = q.x;
+            fi[d >= B ? d - B : 0] = q.z;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+        if (pb + 32 * k >= pe) break;
+        const double2 o = eval_point<B, F>(yv[k], qr, qi, fr, fi);
+        if (jv[k] >= 0) out[jv[k]] = o;
+    }
+}
+
 // Flat split-precision evaluation: one thread per sorted point, its cell from the sorted
 // cell keys (no work-item indirection; threads of one cell share Q4 through L1).
 template <int D>
@@ -803,6 +928,23 @@ cudaError_t launch_eval_df(const SideK<double> &S, const void *Q4, void *out, in
                                    static_cast<const float4 *>(Q4), static_cast<double2 *>(out))));
         count_launches(1);
     }
+    return cudaGetLastError();
+}
+
+bool eval_gather_df_ok(const GridLaunch<float2> &L) {
+    return L.ninst == 1 && 2 * L.m <= EG_HS && L.D <= 16 && df_supported_degree(L.D);
+}
+
+cudaError_t launch_eval_gather_df(const SideK<double> &S, const GridLaunch<float2> &L,
+                                  const void *grid, void *out, cudaStream_t s) {
+    // every item runs one warp: not with small-item splitting (the callers fall back)
+    if (S.list_small || !eval_gather_df_ok(L) || L.D != S.D) return cudaErrorInvalidValue;
+    if (S.max_items <= 0) return cudaSuccess;
+    const int blocks = cdiv((long long)S.max_items * 32, 256);
+    NNFFT_DISPATCH_DF(S.D, (k_eval_gather_df<DD><<<blocks, 256, 0, s>>>(
+                               S, reinterpret_cast<const float2 *>(S.ys), L,
+                               static_cast<const float4 *>(grid), static_cast<double2 *>(out))));
+    count_launches(1);
     return cudaGetLastError();
 }
 

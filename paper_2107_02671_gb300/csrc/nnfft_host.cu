@@ -120,7 +120,8 @@ struct nnfft_plan_s {
     // tuning (nnfft_autotune): moments kernel lanes per item per side, FFT packing variant
     int mom_lanes[2] = {32, 32};     // moments: 32, 16 (split precision only) or 8 lanes per item
     int eval_lanes[2] = {32, 32};    // evaluation: 32 or 8 per item, EVAL_FLAT per point,
-                                     // EVAL_FLAT_TMA per point with TMA-staged cells
+                                     // EVAL_FLAT_TMA per point with TMA-staged cells,
+                                     // EVAL_GATHER 32 per item with the gather convolution
     int fft_variant = 0;         // 0, 1: column packings of the two-pass FFT; 2: cluster FFT;
                                  // 3: the split-precision grid stage as one cooperative launch
     bool fft_cluster_ok = false; // the cluster FFT applies (single instance, split precision,
@@ -1015,17 +1016,22 @@ int run_forward_split(nnfft_plan_s *p, const void *f, void *y, cudaStream_t st, 
             StageTimer t(p, 4, st);
             NN_CUDA(fft_df(p, W, -1, st), "fft");
         }
-        {
+        // EVAL_GATHER: the evaluation computes each item's window sums from the grid itself
+        const GridLaunch<float2> Lg = grid_launch<float2>(p, 1, false, true);
+        const bool gather_in = p->eval_lanes[1] == EVAL_GATHER && sx.list_small == nullptr &&
+                               eval_gather_df_ok(Lg);
+        if (!gather_in) {
             StageTimer t(p, 5, st);
-            NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 1, false, true), W.bufC, W.Q, st),
-                    "gather convolution");
+            NN_CUDA(launch_gather_conv_df(Lg, W.bufC, W.Q, st), "gather convolution");
         }
         // the gather side's sorted nodes (sorted on another stream) are needed from here on;
         // the gather convolution reads only the plan's grid geometry
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 6, st);
-            NN_CUDA(launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st), "gather evaluation");
+            NN_CUDA(gather_in ? launch_eval_gather_df(sx, Lg, W.bufC, y, st)
+                              : launch_eval_df(sx, W.Q, y, p->eval_lanes[1], st),
+                    "gather evaluation");
         }
     }
     return NNFFT_OK;
@@ -1084,15 +1090,19 @@ int run_adjoint_split(nnfft_plan_s *p, const void *g, void *z, cudaStream_t st, 
             StageTimer t(p, 9, st);
             NN_CUDA(fft_df(p, W, +1, st), "adjoint fft");
         }
-        {
+        const GridLaunch<float2> Lg = grid_launch<float2>(p, 0, false, false);
+        const bool gather_in = p->eval_lanes[0] == EVAL_GATHER && sv.list_small == nullptr &&
+                               eval_gather_df_ok(Lg);
+        if (!gather_in) {
             StageTimer t(p, 10, st);
-            NN_CUDA(launch_gather_conv_df(grid_launch<float2>(p, 0, false, false), W.bufC, W.Q, st),
-                    "adjoint gather convolution");
+            NN_CUDA(launch_gather_conv_df(Lg, W.bufC, W.Q, st), "adjoint gather convolution");
         }
         if (mid) NN_CUDA(cudaStreamWaitEvent(st, mid, 0), "wait for the other side");
         {
             StageTimer t(p, 11, st);
-            NN_CUDA(launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st), "adjoint gather evaluation");
+            NN_CUDA(gather_in ? launch_eval_gather_df(sv, Lg, W.bufC, z, st)
+                              : launch_eval_df(sv, W.Q, z, p->eval_lanes[0], st),
+                    "adjoint gather evaluation");
         }
     }
     return NNFFT_OK;
@@ -1559,6 +1569,7 @@ int nnfft_autotune(nnfft_plan_t p, const double *v_dev, const double *x_dev, con
     std::vector<int> lanes = dfk ? std::vector<int>{32, 16, 8, MOM_TEAM_PF}
                                  : (small_d ? std::vector<int>{32, 8} : std::vector<int>{32});
     std::vector<int> elanes{32, 8, EVAL_FLAT, EVAL_FLAT_TMA};
+    if (dfk && p->ninst == 1) elanes.push_back(EVAL_GATHER);
     // splitting small items changes the node-time work lists: only with the nodes given,
     // and only where the size rule would split somewhere
     bool split_possible = false;
@@ -1712,7 +1723,8 @@ int nnfft_set_tuning(nnfft_plan_t p, const nnfft_tuning *t) {
     if (!p || !t) return fail(NNFFT_EINVAL, "null argument");
     auto ok_lanes = [](int l) { return l == MOM_TEAM_PF || l == 8 || l == 16 || l == 32; };
     auto ok_elanes = [](int l) {
-        return l == 0 || l == EVAL_FLAT || l == EVAL_FLAT_TMA || l == 8 || l == 32;
+        return l == 0 || l == EVAL_FLAT || l == EVAL_FLAT_TMA || l == EVAL_GATHER || l == 8 ||
+               l == 32;
     };
     if (!ok_lanes(t->moments_lanes_v) || !ok_lanes(t->moments_lanes_x) ||
         !ok_elanes(t->eval_lanes_v) || !ok_elanes(t->eval_lanes_x) ||

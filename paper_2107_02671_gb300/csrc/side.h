@@ -57,6 +57,9 @@ constexpr int EVAL_FLAT = 1;
 // The flat kernels with each block's range of cell window sums staged in shared memory by
 // one bulk (TMA) copy.
 constexpr int EVAL_FLAT_TMA = 2;
+// One warp per work item that computes its cell's window sums from the grid itself (the
+// gather convolution inside the evaluation; split precision, single instances).
+constexpr int EVAL_GATHER = 3;
 // Cells a staged block holds at most (blocks spanning more read global memory directly).
 constexpr int TMA_MAX_CELLS = 128;
 // Largest work item handled by one thread (no reduction) when a plan splits items.

@@ -422,7 +422,7 @@ def test_autotune_keeps_results_within_tolerance(dtype, m, tol):
     plan.set_nodes(dev(v), dev(x))
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=2)
     assert t["tuned"] == 1 and t["moments_lanes_v"] in (4, 8, 16, 32) and t["moments_lanes_x"] in (4, 8, 16, 32)
-    assert t["eval_lanes_v"] in (1, 2, 8, 32) and t["eval_lanes_x"] in (1, 2, 8, 32)
+    assert t["eval_lanes_v"] in (1, 2, 3, 8, 32) and t["eval_lanes_x"] in (1, 2, 3, 8, 32)
     assert t["fft_variant"] in (0, 1, 2, 3) and 0 < t["best_ms"] <= 1.1 * t["default_ms"]
     assert t["timed_transform"] == 0
     t = plan.autotune(dev(f, dtype), dev(g, dtype), reps=1, v=dev(v), x=dev(x), flush_l2=True)
@@ -1031,3 +1031,38 @@ def test_fused_grid_stage_needs_equal_degrees():
     with pytest.raises(B.NNFFTError):
         plan.set_tuning(8, 8, 3, 0, 32, 32)
     plan.set_tuning(8, 8, 0, 0, 32, 32)
+
+
+@pytest.mark.parametrize("N,M1,M2,nodes,split", [(4096, 50000, 40000, "uniform", 0),
+                                                 (1000, 300000, 200000, "chebyshev", 0),
+                                                 (700, 3000, 2000, "uniform", 1)])
+def test_gather_inside_evaluation_equals_gather_kernel(N, M1, M2, nodes, split):
+    """Evaluation lanes value 3: each work item's warp forms its cell's window sums from the
+    FFT output itself (scaled grid values, tap sums, the 1/phihat1 fold on the x side) in the
+    gather kernel's order, then evaluates its points: bitwise the gather kernel followed by
+    the 32-lane evaluation, forward and adjoint, with cells split into several items
+    (clustered nodes), with small-item splitting (where the gather kernel runs instead), and
+    replayed from the transform graph; within the fp64 tolerance of the direct sum."""
+    v, x, f = W.nnfft_inputs(M1, M2, 83, nodes=nodes)
+    g = W.adjoint_inputs(M2, 83)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, 8, 8, dtype=torch.complex128)
+    outs = []
+    for el in (32, 3):
+        plan.set_tuning(8, 8, 0, split, el, el)
+        plan.set_nodes(dev(v), dev(x))
+        y, z = plan.exec_adjoint(dev(f), dev(g))
+        plan.sync()
+        outs.append((y.cpu().numpy(), z.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    vd, xd, fd, gd = dev(v), dev(x), dev(f), dev(g)
+    graph = plan.transform_graph(vd, xd, fd, gd)
+    yg, zg = graph.launch()
+    plan.sync()
+    assert np.array_equal(yg.cpu().numpy(), outs[0][0]) and np.array_equal(zg.cpu().numpy(), outs[0][1])
+    graph.close()
+    rows = W.sample_rows(M2, 32, 19)
+    want = oracle.nnfft_direct(N, v, f, x, rows=rows)
+    assert np.max(np.abs(outs[1][0][rows] - want)) / np.sum(np.abs(f)) <= 1e-12
+    rows = W.sample_rows(M1, 32, 20)
+    want = oracle.nnfft_adjoint_direct(N, v, x, g, rows=rows)
+    assert np.max(np.abs(outs[1][1][rows] - want)) / np.sum(np.abs(g)) <= 1e-12
