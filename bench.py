@@ -311,20 +311,20 @@ def run_reference(args, rank, world):
 # -------------------------------------------------------------------------------------------
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of every
 # split-precision point-kernel variant at the headline size, from ncu captures of
-# `python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-serve --tuning T`
+# `python bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-serve --no-m-sweep --tuning T`
 # (NVTX range headline_seq) with T = 8,8,0,0,1,1,256,0 / 4,4,0,0,2,2,256,0 /
 # 16,16,0,0,32,32,256,0, averaged over the captured launches.  The files the kernels are
 # built from (their code, the double-float primitives, the side descriptor) are hashed; a
 # change since the capture reports null.
 NCU_SOURCES = ["kern_spread_df.cu", "df.cuh", "side.h"]
-NCU_HASH = "c7864bebb5018b5f"
+NCU_HASH = "6654037685dbfba2"
 NCU_TRAFFIC = {
-    "k_moments_df_team<14>": 29460160,          # 8 lanes per work item
-    "k_moments_df_team_pf<14>": 29464576,       # 8 lanes, two accumulator sets per lane
-    "k_moments_df_half<14>": 29481088,          # 16
-    "k_eval_df_flat<14>": 20470720 + 1801472,   # one thread per point
-    "k_eval_df_flat_tma<14>": 20447360 + 1776832,   # the same, cells staged by TMA
-    "k_eval_df<14>": 16265792 + 1654400,        # 32
+    "k_moments_df_team<14>": 29459968,          # 8 lanes per work item
+    "k_moments_df_team_pf<14>": 29464832,       # 8 lanes, two accumulator sets per lane
+    "k_moments_df_half<14>": 29481280,          # 16
+    "k_eval_df_flat<14>": 20461952 + 1792576,   # one thread per point
+    "k_eval_df_flat_tma<14>": 20427456 + 1756928,   # the same, cells staged by TMA
+    "k_eval_df<14>": 16253120 + 1643136,        # 32
 }
 
 
@@ -336,7 +336,7 @@ def point_kernel(stage, tuning):
         return {8: "k_moments_df_team<14>", 4: "k_moments_df_team_pf<14>",
                 16: "k_moments_df_half<14>"}.get(lanes, "k_moments_df_warp<14>")
     lanes = tuning.get(f"eval_lanes_{side}", 32)
-    return {1: "k_eval_df_flat<14>", 2: "k_eval_df_flat_tma<14>",
+    return {1: "k_eval_df_flat<14>", 2: "k_eval_df_flat_tma<14>", 3: "k_eval_gather_df<14>",
             8: "k_eval_df_team<14>"}.get(lanes, "k_eval_df<14>")
 
 
