@@ -554,14 +554,16 @@ k_eval_df_flat_tma(SideK<double> S, const float2 *__restrict__ ys2, const float4
 // bits 3..1 leave lane s with slots j = 2s and 2s+1 of each kind.
 // ---------------------------------------------------------------------------------
 constexpr int DTEAM = 8;
-// team moments: points per lane loaded at a time and blocks per SM the registers allow
-// (4 and 3: 80 registers without spills, three 256-thread blocks per SM)
+// team moments: points per lane loaded at a time and the register bound in 256-thread
+// blocks per SM (4 and 2: up to 128 registers; one item per cell at 2^20 points gives only
+// ~13 warps per SM, so occupancy is not what the registers limit.  Measured: the 80-register
+// bound of three blocks 1-3 % slower per step, 8 points per lane at a time 4-10 % slower)
 constexpr int TEAM_CH = 4;
-constexpr int TEAM_MINB = 3;
+constexpr int TEAM_MINB = 2;
 // Threads per block of the team moments kernels.  One item per cell at 2^20 points puts
 // 8224 x 8 lanes = 257 blocks of 256 threads on 152 SMs: half the SMs ran two blocks, the
 // rest one, and the kernel lasted as long as the loaded half.  Blocks of TEAM_BLOCK threads
-// spread the same warps evenly (the register bound stays 3 x 256 threads per SM).
+// spread the same warps evenly.
 constexpr int TEAM_BLOCK = 64;
 
 template <int O, int LB>
