@@ -514,6 +514,18 @@ __device__ __forceinline__ void fft_pass1_df_block(const float4 *__restrict__ X_
     const int b0 = (vb - L.blk1[inst]) * F.cols1;
     const int cols = min(F.cols1, n2 - b0);
     float4 *A = smem4, *Bf = smem4 + cols * n, *tw = smem4 + 2 * cols * n;
+    // the four-step twiddles of this thread's first outputs, loaded now so that their latency
+    // overlaps the column loads and the butterflies instead of following them
+    constexpr int PF = 2;
+    float4 twp[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < cols * n) {
+            const int bb = e / n, c = e - bb * n;
+            twp[q] = F.twN[(b0 + bb) * c];
+        }
+    }
     for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
         const int a = e / cols, bb = e - a * cols;
         A[bb * n + a] = X[(long long)n2 * a + b0 + bb];
@@ -521,9 +533,20 @@ __device__ __forceinline__ void fft_pass1_df_block(const float4 *__restrict__ X_
     for (int a = threadIdx.x; a < n; a += blockDim.x) tw[a] = F.tw1[a];
     __syncthreads();
     const float4 *res = stockham_df(A, Bf, n, cols, F.r1, F.nr1, tw, sign);
-    for (int e = threadIdx.x; e < cols * n; e += blockDim.x) {
+    int q = 0;
+    for (int e = threadIdx.x; e < cols * n; e += blockDim.x, ++q) {
         const int bb = e / n, c = e - bb * n, b = b0 + bb;
-        st(Z + (long long)b * n + c, cmul(ld(res + e), twd(F.twN, b * c, sign)));
+        cdf w;
+        if (q < PF) {
+            float4 t4 = twp[0];
+#pragma unroll
+            for (int r = 1; r < PF; ++r)
+                if (q == r) t4 = twp[r];
+            w = conj_if(ld(&t4), sign > 0);
+        } else {
+            w = twd(F.twN, b * c, sign);
+        }
+        st(Z + (long long)b * n + c, cmul(ld(res + e), w));
     }
 }
 
