@@ -648,10 +648,13 @@ sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
             const int idx = base + r * 32 + lane;
             const bool valid = idx < cend;
             const unsigned d = valid ? ((key[r] - cb) & lmask) : (unsigned)NB;   // NB: invalid
+            // a round without invalid lanes has d < NB in every lane: bit lbits is 0 for all
+            // of them and its ballot would change nothing
+            const int nbits = base + r * 32 + 31 < cend ? lbits : lbits + 1;
             unsigned peers = 0xffffffffu;
 #pragma unroll
             for (int bt = 0; bt < 9; ++bt) {         // the ballots of the bits of d
-                if (bt > lbits) break;
+                if (bt >= nbits) break;
                 const unsigned bit = (d >> bt) & 1u;
                 const unsigned bal = __ballot_sync(0xffffffffu, bit);
                 peers &= bit ? bal : ~bal;
