@@ -16,6 +16,37 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Rank of this lane's key among the warp's 32 keys of one round, stably by bin d: every
+// valid lane sets its bit in the warp's mask of bin d (one shared-memory atomicOr), and the
+// mask read back is the set of lanes with the same bin; the lowest of them adds their
+// number to the warp's bin counter and clears the mask for the next round.  rank = the
+// counter before this round + the lanes of the same bin below this one (the same ranks
+// as intersecting the ballots of the bits of d, in fewer issue slots).  mm: the warp's
+// masks, zero on entry and on return; cnt: the warp's counters.
+// The passes that move no carried 4-byte coordinates (the fp64 sorts) rank this way:
+// measured at 2^20 keys per side, both sides' sorts 70 -> 66 us and the fp64 step 166 -> 162
+// us; at 512 instances the fp64 node stage 3.56 -> 3.44 ms.  The passes that carry 4-byte
+// coordinates (fp32) keep the ballots: ranked this way the 512-instance fp32 node stage took
+// 3.41 ms against 3.14, and the single-instance sorts were no faster.
+__device__ __forceinline__ int rank_or(unsigned *mm, int *cnt, unsigned d, bool valid,
+                                       unsigned lt, int lane) {
+    if (valid) atomicOr(&mm[d], 1u << lane);
+    __syncwarp();
+    unsigned peers = 0u;
+    int before = 0;
+    if (valid) {
+        peers = mm[d];
+        before = cnt[d];
+    }
+    __syncwarp();
+    if (valid && (peers & lt) == 0) {
+        cnt[d] = before + __popc(peers);
+        mm[d] = 0u;
+    }
+    __syncwarp();
+    return before + __popc(peers & lt);
+}
+
 // Cell and local coordinate of a node t in fixed point, with integer operations only.
 // |t| is truncated to X = |t| 2^62 (exact for |t| >= 2^-10, absolute error < 2^-62), the
 // scale is S = scale 2^FX_SB, so A = X S = |u| 2^(62 + FX_SB) exactly in 128 bits
@@ -297,7 +328,9 @@ k_sort_scan_rows(int *__restrict__ hist, int nblocks, const int *__restrict__ di
 // tile's instance) >> shift & mask, is at most 8 bits wide (NARROW: mask < 255; else the
 // literal 255, measured cheaper for the fp64 batch's scatters).  MATCH: the lanes with the
 // same digit from one match instruction instead of nine ballots (measured: fewer issue
-// slots, faster for large sorts; longer latency, slower for small ones).  The ballot-ranked
+// slots, faster for large sorts; longer latency, slower for small ones).  Otherwise a pass
+// without carried coordinates ranks by shared-memory masks (rank_or), one that carries them
+// by the ballots.  The ballot-ranked
 // passes that move 8-byte coordinates (the sorts below 8M keys) are bounded to four blocks
 // per SM (64 registers, no spills; 73 unbounded, three blocks per SM, so that a 2^20-key
 // sort's 512 tiles took two waves on 152 SMs: node stage 95 -> 93.6 us per side); the others
@@ -323,8 +356,13 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     using YS = typename std::conditional<std::is_void<Y>::value, char, Y>::type;
     constexpr bool CARRY = !std::is_void<Y>::value && sizeof(YS) == 4;
     __shared__ YS sy[CARRY ? SORT_TILE : 1];
+    constexpr bool OR = !MATCH && !CARRY;       // ranked by rank_or
+    __shared__ unsigned mmask[OR ? WARPS : 1][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    for (int d = lane; d < 256; d += 32) {
+        cnt[w][d] = 0;
+        if constexpr (OR) mmask[w][d] = 0u;
+    }
     __syncwarp();
     const TileSpan sp = tile_span(st, blockIdx.x, n);
     const uint32_t cb = st.inst == nullptr ? 0u : (uint32_t)st.tab[sp.inst].cell_base;
@@ -349,6 +387,10 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         const long long idx = base + r * 32 + lane;
         const bool valid = idx < sp.end;
         const unsigned d = valid ? (((key[r] - cb) >> shift) & mask) : 256u;
+        if constexpr (OR) {
+            rank[r] = rank_or(mmask[w], cnt[w], d, valid, lt, lane);
+            continue;
+        }
         // lanes with the same 9-bit value d (256 marks an invalid lane)
         unsigned peers = 0xffffffffu;
         if constexpr (MATCH) {
@@ -430,8 +472,8 @@ k_sort_scatter(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
 // and, for dense plans (per_cell_first), one work item per cell; a cell above cap sets
 // *overflow and the scan-based item builder runs next; the bucket's first block writes
 // them) and the keys of its bucket before its range per bin (run[]).  Then its range in
-// chunks: ranks within the chunk as in k_sort_scatter (per-warp counters, ballots of the
-// digit bits), the chunk reordered by bin in shared memory and written out bin run by
+// chunks: ranks within the chunk as in k_sort_scatter (per-warp counters; rank_or, or the
+// ballots of the digit bits when 4-byte coordinates are carried), the chunk reordered by bin in shared memory and written out bin run by
 // bin run (coalesced) after the same bin's earlier keys.  So the result is the stable
 // sort by cell, the same order as the LSD passes.  The coordinates: 4-byte ones are
 // carried (yin in first-pass order), 8-byte ones gathered from the caller-order array
@@ -451,7 +493,8 @@ __host__ __device__ constexpr int local_min_blocks(int threads) { return threads
 constexpr int LOCAL_COUNT_UNROLL = 16;
 
 __host__ __device__ constexpr size_t local_sort_smem(int threads, int lbits, int ybytes) {
-    return sizeof(int) * ((size_t)(threads / 32) * (1u << lbits) + 5u * (1u << lbits) + 32u) +
+    return sizeof(int) * ((size_t)(threads / 32) * (1u << lbits) * (ybytes == 4 ? 1u : 2u) +
+                          5u * (1u << lbits) + 32u) +
            (size_t)threads * LOCAL_ROUNDS * (sizeof(uint32_t) + sizeof(int) + (ybytes == 4 ? 4u : 0u));
 }
 
@@ -470,6 +513,7 @@ sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     constexpr int LOCAL_CHUNK = LOCAL_THREADS * LOCAL_ROUNDS;
     constexpr int LOCAL_WARPS = LOCAL_THREADS / 32;
     constexpr int RANGE = local_range(LOCAL_THREADS);
+    constexpr bool RANK_OR = !CARRY;            // bins ranked by rank_or, else by ballots
     extern __shared__ __align__(16) int smem_i[];
     const int NB = 1 << lbits;
     const unsigned lmask = (unsigned)NB - 1u;
@@ -480,7 +524,8 @@ sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
     int *ctot = run + NB;                        // [NB] keys of each bin in this chunk
     int *cst = ctot + NB;                        // [NB] first chunk slot of each bin
     int *wtot = cst + NB;                        // [32]
-    uint32_t *skey = reinterpret_cast<uint32_t *>(wtot + 32);
+    unsigned *mm = reinterpret_cast<unsigned *>(wtot + 32);   // [LOCAL_WARPS][NB] bin masks
+    uint32_t *skey = reinterpret_cast<uint32_t *>(mm + (RANK_OR ? LOCAL_WARPS * NB : 0));
     int *sval = reinterpret_cast<int *>(skey + LOCAL_CHUNK);
     Y *sy = reinterpret_cast<Y *>(sval + LOCAL_CHUNK);   // CARRY only
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -562,6 +607,8 @@ sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
         btot[i] = 0;
         run[i] = 0;
     }
+    if constexpr (RANK_OR)
+        for (int i = tid; i < LOCAL_WARPS * NB; i += LOCAL_THREADS) mm[i] = 0u;
     // the first chunk's keys, values (and carried coordinates) are loaded before the
     // counting pass, so that their latency overlaps it
     uint32_t key[LOCAL_ROUNDS];
@@ -648,6 +695,10 @@ sort_local_body(const uint32_t *__restrict__ kin, const int *__restrict__ vin,
             const int idx = base + r * 32 + lane;
             const bool valid = idx < cend;
             const unsigned d = valid ? ((key[r] - cb) & lmask) : (unsigned)NB;   // NB: invalid
+            if constexpr (RANK_OR) {
+                rank[r] = rank_or(mm + w * NB, cnt + w * NB, d, valid, lt, lane);
+                continue;
+            }
             // a round without invalid lanes has d < NB in every lane: bit lbits is 0 for all
             // of them and its ballot would change nothing
             const int nbits = base + r * 32 + 31 < cend ? lbits : lbits + 1;
