@@ -45,6 +45,22 @@ __device__ __forceinline__ df add(df a, df b) {
     return fast2sum(s, e + (a.l + b.l));
 }
 
+// a + b with TwoSum on the high parts and the low parts added, not renormalised (for the
+// exchanges of partial sums, which are renormalised once at the end with norm_any)
+__device__ __forceinline__ df add_lazy(df a, df b) {
+    const float s = a.h + b.h;
+    const float bp = s - a.h;
+    const float e = (a.h - (s - bp)) + (b.h - bp);
+    return mk(s, (a.l + b.l) + e);
+}
+
+// normalise with TwoSum: no ordering requirement on |h| and |l|
+__device__ __forceinline__ df norm_any(df a) {
+    const float s = a.h + a.l;
+    const float bp = s - a.h;
+    return mk(s, (a.h - (s - bp)) + (a.l - bp));
+}
+
 __device__ __forceinline__ df neg(df a) { return mk(-a.h, -a.l); }
 __device__ __forceinline__ df sub(df a, df b) { return add(a, neg(b)); }
 

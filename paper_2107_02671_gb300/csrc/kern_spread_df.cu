@@ -47,7 +47,7 @@ __device__ __forceinline__ void rs_step_df(df (&v)[32], int lane) {
         df other;
         other.h = __shfl_xor_sync(0xffffffffu, send.h, O);
         other.l = __shfl_xor_sync(0xffffffffu, send.l, O);
-        v[i] = add(keep, other);
+        v[i] = add_lazy(keep, other);
     }
 }
 
@@ -173,8 +173,8 @@ k_moments_df_warp(SideK<double> S, const float2 *__restrict__ ys2, const double2
     for (int i = 0; i < 32; ++i) vv[i] = mk(0.f);
 #pragma unroll
     for (int d = 0; d < B; ++d) {
-        vv[d] = norm(ar[d]);
-        vv[D + d] = norm(ai[d]);
+        vv[d] = ar[d];
+        vv[D + d] = ai[d];
     }
 #pragma unroll
     for (int d = 0; d < F; ++d) {
@@ -187,8 +187,9 @@ k_moments_df_warp(SideK<double> S, const float2 *__restrict__ ys2, const double2
     rs_step_df<2>(vv, lane);
     rs_step_df<1>(vv, lane);
     float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
-    if (lane < D) P2[2 * lane] = make_float2(vv[0].h, vv[0].l);
-    else if (lane < 2 * D) P2[2 * (lane - D) + 1] = make_float2(vv[0].h, vv[0].l);
+    const df r = norm_any(vv[0]);
+    if (lane < D) P2[2 * lane] = make_float2(r.h, r.l);
+    else if (lane < 2 * D) P2[2 * (lane - D) + 1] = make_float2(r.h, r.l);
 }
 
 // ---------------------------------------------------------------------------------
@@ -211,7 +212,7 @@ __device__ __forceinline__ void rs_step_mixed(df (&vd)[16], float (&vf)[16], int
         df other;
         other.h = __shfl_xor_sync(0xffffffffu, send.h, O);
         other.l = __shfl_xor_sync(0xffffffffu, send.l, O);
-        vd[i] = add(keep, other);
+        vd[i] = add_lazy(keep, other);
         const float fs = up ? vf[i] : vf[O + i];
         const float fk = up ? vf[O + i] : vf[i];
         vf[i] = fk + __shfl_xor_sync(0xffffffffu, fs, O);
@@ -270,8 +271,8 @@ k_moments_df_half(SideK<double> S, const float2 *__restrict__ ys2, const double2
     for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
 #pragma unroll
     for (int d = 0; d < B; ++d) {
-        vd[d] = norm(ar[d]);
-        vd[8 + d] = norm(ai[d]);
+        vd[d] = ar[d];
+        vd[8 + d] = ai[d];
     }
 #pragma unroll
     for (int d = 0; d < F; ++d) {
@@ -285,7 +286,8 @@ k_moments_df_half(SideK<double> S, const float2 *__restrict__ ys2, const double2
     if (!live) return;
     float2 *P2 = reinterpret_cast<float2 *>(P4 + (long long)item * D);
     const int j = sub & 7, part = sub >> 3;          // part 0: real, 1: imaginary
-    if (j < B) P2[2 * j + part] = make_float2(vd[0].h, vd[0].l);
+    const df r = norm_any(vd[0]);
+    if (j < B) P2[2 * j + part] = make_float2(r.h, r.l);
     if (j < F) P2[2 * (B + j) + part] = make_float2(vf[0], 0.f);
 }
 
@@ -579,7 +581,7 @@ __device__ __forceinline__ void rs_mixed_team(df (&vd)[16], float (&vf)[16], int
         df other;
         other.h = __shfl_xor_sync(0xffffffffu, send.h, LB);
         other.l = __shfl_xor_sync(0xffffffffu, send.l, LB);
-        vd[i] = add(keep, other);
+        vd[i] = add_lazy(keep, other);
         const float fs = up ? vf[i] : vf[O + i];
         const float fk = up ? vf[O + i] : vf[i];
         vf[i] = fk + __shfl_xor_sync(0xffffffffu, fs, LB);
@@ -629,8 +631,8 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
     for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
 #pragma unroll
     for (int d = 0; d < B; ++d) {
-        vd[d] = norm(ar[d]);
-        vd[8 + d] = norm(ai[d]);
+        vd[d] = ar[d];
+        vd[8 + d] = ai[d];
     }
 #pragma unroll
     for (int d = 0; d < F; ++d) {
@@ -645,7 +647,8 @@ k_moments_df_team(SideK<double> S, const float2 *__restrict__ ys2, const double2
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int j = 2 * sub + t, deg = j & 7, part = j >> 3;   // part 0: real, 1: imaginary
-        if (deg < B) P2[2 * deg + part] = make_float2(vd[t].h, vd[t].l);
+        const df r = norm_any(vd[t]);
+        if (deg < B) P2[2 * deg + part] = make_float2(r.h, r.l);
         if (deg < F) P2[2 * (B + deg) + part] = make_float2(vf[t], 0.f);
     }
 }
@@ -697,8 +700,8 @@ k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
     }
 #pragma unroll
     for (int d = 0; d < B; ++d) {              // the two accumulator sets
-        ar[d] = add(norm(ar[d]), norm(ar2[d]));
-        ai[d] = add(norm(ai[d]), norm(ai2[d]));
+        ar[d] = add_lazy(ar[d], ar2[d]);
+        ai[d] = add_lazy(ai[d], ai2[d]);
     }
 #pragma unroll
     for (int d = 0; d < F; ++d) {
@@ -711,8 +714,8 @@ k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
     for (int j = 0; j < 16; ++j) { vd[j] = mk(0.f); vf[j] = 0.f; }
 #pragma unroll
     for (int d = 0; d < B; ++d) {
-        vd[d] = norm(ar[d]);
-        vd[8 + d] = norm(ai[d]);
+        vd[d] = ar[d];
+        vd[8 + d] = ai[d];
     }
 #pragma unroll
     for (int d = 0; d < F; ++d) {
@@ -727,7 +730,8 @@ k_moments_df_team_pf(SideK<double> S, const float2 *__restrict__ ys2,
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int j = 2 * sub + t, deg = j & 7, part = j >> 3;   // part 0: real, 1: imaginary
-        if (deg < B) P2[2 * deg + part] = make_float2(vd[t].h, vd[t].l);
+        const df r = norm_any(vd[t]);
+        if (deg < B) P2[2 * deg + part] = make_float2(r.h, r.l);
         if (deg < F) P2[2 * (B + deg) + part] = make_float2(vf[t], 0.f);
     }
 }
