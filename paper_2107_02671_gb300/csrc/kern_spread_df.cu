@@ -26,13 +26,18 @@ using namespace dfa;
 
 constexpr int PPL = ITEM_CAP / 32;   // points per lane of a work item
 
-// Chebyshev recurrence T_{d+1} = (2y) T_d - T_{d-1} in double-float
+// Chebyshev recurrence T_{d+1} = (2y) T_d - T_{d-1} in double-float, TwoSum on the high
+// parts, the result not renormalised: its low part is a sum of rounding errors of O(1)
+// quantities (|T_d| <= 1), so it stays within a few 2^-24 in absolute terms, and the next
+// product and the accumulations take unnormalised pairs at the same 2^-48 absolute accuracy.
+// (Measured against a Fast2Sum renormalisation per step: graph step 155.0 -> 154.2-154.5 us
+// with the two-set 8-lane moments, 159.9 -> 156.2-156.5 us with the 8-lane team kernel.)
 __device__ __forceinline__ df df_rec(df y2, df t1, df t0) {
     const df p = mul_u(y2, t1);
     const float s = p.h - t0.h;
     const float bp = s - p.h;
     const float e = (p.h - (s - bp)) + (-t0.h - bp);
-    return fast2sum(s, (p.l - t0.l) + e);
+    return mk(s, (p.l - t0.l) + e);
 }
 
 // reduce-scatter of 32 double-float values per lane: afterwards lane L holds the
