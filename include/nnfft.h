@@ -429,6 +429,25 @@ int nnfft_transform_host(nnfft_plan_t p, const double *v_host, const double *x_h
 /* nnfft_sync: wait for the plan's stream; return and clear the kernel status. */
 int nnfft_sync(nnfft_plan_t p);
 
+/*
+ * nnfft_node_order: the order step 0 of Algorithm 2.2 put one side's nodes in (the
+ * binning by grid cell and the stable sort by cell of nnfft_set_nodes), copied to host
+ * memory, for callers that keep their own data in the plan's cell order and for checks.
+ * side 0: the frequency nodes v (M1 points, cells of the window phi1's grid), side 1: the
+ * spatial nodes x (M2 points, cells of the N2-grid).  Cells are consecutive intervals of the
+ * node axis, in increasing order of the node.
+ * perm_host: NULL or M int32 (caller-owned host memory): perm[i] = caller index of sorted
+ *   position i; within a cell the caller indices increase (the sort is stable).
+ * off_host: NULL or ncell + 1 int32: the points of cell c are the sorted positions
+ *   off[c] .. off[c + 1] - 1 (off[0] = 0, off[ncell] = M).
+ * ncell_out: NULL or the number of cells of the side.
+ * Waits for the plan's stream (without reading or clearing the kernel status: nnfft_sync
+ * still reports it).  Single-instance plans only: EINVAL for a batch plan or a side other
+ * than 0 or 1; ESTATE when perm_host or off_host is given and the side's nodes were never set.
+ */
+int nnfft_node_order(nnfft_plan_t p, int side, int32_t *perm_host, int32_t *off_host,
+                     int64_t *ncell_out);
+
 /* nnfft_destroy: free the plan (waits for its stream first).  NULL is a no-op. */
 int nnfft_destroy(nnfft_plan_t p);
 

@@ -1849,6 +1849,27 @@ int nnfft_sync(nnfft_plan_t p) {
     return collect_status(p);
 }
 
+int nnfft_node_order(nnfft_plan_t p, int side, int32_t *perm_host, int32_t *off_host,
+                     int64_t *ncell_out) {
+    if (!p) return fail(NNFFT_EINVAL, "null plan");
+    if (side != 0 && side != 1) return fail(NNFFT_EINVAL, "node order: side must be 0 or 1");
+    if (p->ninst != 1) return fail(NNFFT_EINVAL, "node order: single-instance plans only");
+    const Side &S = p->side[side];
+    if (ncell_out) *ncell_out = S.ncell;
+    if (!perm_host && !off_host) return NNFFT_OK;
+    if (!S.set || !S.perm || !S.cell_off)
+        return fail(NNFFT_ESTATE, "node order: nnfft_set_nodes first");
+    NN_CUDA(cudaStreamSynchronize(p->stream), "stream synchronize");
+    if (perm_host && S.M > 0)
+        NN_CUDA(cudaMemcpy(perm_host, S.perm, (size_t)S.M * sizeof(int), cudaMemcpyDeviceToHost),
+                "node order copy");
+    if (off_host)
+        NN_CUDA(cudaMemcpy(off_host, S.cell_off, ((size_t)S.ncell + 1) * sizeof(int),
+                           cudaMemcpyDeviceToHost),
+                "cell offsets copy");
+    return NNFFT_OK;
+}
+
 int nnfft_destroy(nnfft_plan_t p) {
     free_plan(p);
     return NNFFT_OK;

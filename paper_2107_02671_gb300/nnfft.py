@@ -149,6 +149,7 @@ def load_library(build_if_missing: bool = True):
         lib.nnfft_exec_host.argtypes = [vp, vp, vp]
         lib.nnfft_adjoint_host.argtypes = [vp, vp, vp]
         lib.nnfft_sync.argtypes = [vp]
+        lib.nnfft_node_order.argtypes = [vp, cint, vp, vp, P(i64)]
         lib.nnfft_destroy.argtypes = [vp]
         lib.sinc_exec.argtypes = [i64, i64, i64, cint, cint, vp, vp, vp, vp, cint, vp]
         lib.sinc_exec_rule.argtypes = [i64, i64, i64, cint, cint, cint, i64, vp, vp, vp, vp, cint,
@@ -527,6 +528,18 @@ class Plan:
 
     def sync(self):
         _check(self._lib.nnfft_sync(self._h))
+
+    def node_order(self, side):
+        """(perm, off) of side 0 (v) or 1 (x) after set_nodes: perm[i] = caller index of
+        sorted position i, and cell c holds the sorted positions off[c] .. off[c + 1] - 1."""
+        ncell = ctypes.c_int64()
+        _check(self._lib.nnfft_node_order(self._h, int(side), None, None, ctypes.byref(ncell)))
+        M = self.M1 if side == 0 else self.M2
+        perm = np.empty(M, dtype=np.int32)
+        off = np.empty(ncell.value + 1, dtype=np.int32)
+        _check(self._lib.nnfft_node_order(self._h, int(side), perm.ctypes.data, off.ctypes.data,
+                                          None))
+        return perm, off
 
     def timing(self, enable=True):
         """Bracket every stage with CUDA events on the plan stream (tracing)."""

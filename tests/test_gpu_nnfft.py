@@ -936,6 +936,45 @@ def test_two_stage_sort_equals_lsd_sort(dtype, arith, m, N, M1, M2, nodes):
     assert np.max(np.abs(outs[1][0][rows2].astype(np.complex128) - want)) / np.sum(np.abs(f)) <= tol
 
 
+@pytest.mark.parametrize("dtype,m", [(torch.complex128, 8), (torch.complex64, 4)])
+@pytest.mark.parametrize("N,M1,M2,nodes", [(4096, 300000, 200001, "chebyshev"),
+                                            (700, 80000, 50000, "uniform"),
+                                            (300, 60000, 3, "chebyshev")])
+def test_node_order_is_the_stable_sort_by_cell(dtype, m, N, M1, M2, nodes):
+    """Step 0 read back through nnfft_node_order, for both node sorts: the order is a
+    permutation, the cell offsets run from 0 to M without decreasing, within every cell the
+    caller indices increase (the sort is stable), and the cells are consecutive intervals of
+    the node axis (the largest node of a non-empty cell is at most the smallest of the next).
+    The two sorts give the same order.  Cases: clustered nodes whose edge buckets span several
+    shared-memory chunks, dense uniform nodes, a side of three points; complex128 plans sort
+    without carrying coordinates, complex64 plans carry 4-byte ones."""
+    npd = np.complex128 if dtype == torch.complex128 else np.complex64
+    v, x, _ = W.nnfft_inputs(M1, M2, 96, nodes=nodes, dtype=npd)
+    plan = B.Plan(N, M1, M2, 2.0, 2.0, m, m, dtype=dtype)
+    orders = []
+    for lsd in (1, 0):
+        plan.set_tuning(32, 32, 0, 0, 32, 32, sort_lsd=lsd)
+        plan.set_nodes(dev(v), dev(x))
+        plan.sync()
+        sides = []
+        for side, t in ((0, v), (1, x)):
+            perm, off = plan.node_order(side)
+            M = len(t)
+            assert np.array_equal(np.sort(perm), np.arange(M))
+            assert off[0] == 0 and off[-1] == M and np.all(np.diff(off) >= 0)
+            cell = np.repeat(np.arange(len(off) - 1), np.diff(off))
+            same = cell[1:] == cell[:-1]
+            assert np.all(np.diff(perm)[same] > 0)
+            s = t[perm]
+            starts = off[:-1][np.diff(off) > 0]
+            assert np.all(np.maximum.reduceat(s, starts)[:-1] <= np.minimum.reduceat(s, starts)[1:])
+            sides.append((perm, off))
+        orders.append(sides)
+    for a, b in zip(orders[0], orders[1]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    plan.close()
+
+
 @pytest.mark.parametrize("N", [4096, 1000, 64])
 @pytest.mark.parametrize("dtype,m,arith", [(torch.complex128, 8, None), (torch.complex128, 8, "fp64"),
                                            (torch.complex64, 4, None)])
